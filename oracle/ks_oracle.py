@@ -1,0 +1,390 @@
+"""Plain FP64 CPU oracle for the Kohn-Sham hot path (arXiv 2106.03872, "INQ").
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.  It shares no code with
+the CUDA path (no kernels, headers, tables or helpers) and imports nothing from
+the package; it is written for a reader checking it against the paper by eye,
+not for speed.
+
+What it computes, each function citing the paper passage it follows:
+
+* own mixed-radix (2, 3) Cooley-Tukey FFT (the paper only says FFTs move between
+  the real-space grid and the plane-wave basis, Sec. "DFT and TDDFT implementation");
+* the plane-wave cutoff sphere, V_loc on the grid and the real-space projector
+  spheres (Sec. "Pseudopotentials", Eq. 9);
+* H psi = P_S (T + V + V_NL) P_S psi (Eq. 2, Sec. "Implementation of the KS Hamiltonian");
+* the density n = sum_k f_k |phi_k|^2 (Eq. 1);
+* Gram matrix, CholQR orthonormalisation and Rayleigh-Ritz rotation (Sec. "Ground-state solution");
+* one steepest-descent block iteration (Sec. "Ground-state solution");
+* periodic Poisson solve in Fourier space (Sec. "Poisson solver") and LDA Slater exchange;
+* the total energy with eigenvalues replaced by expectation values (Eq. 5);
+* the ETRS propagator with the 4th-order Taylor exponential and shared powers
+  (Eqs. 6-8, Sec. "Real-time propagation").
+
+Conventions where the paper is silent (each one a reading, listed in the design doc):
+cubic cell of side L, grid N^3, r_j = h j, h = L/N; G = (2 pi / L) m with
+m = j for j < N/2 else j - N; S = {G : |G|^2/2 <= E_cut} in grid-index order
+(j_x, j_y, j_z) row-major, z fastest; psi(r_j) = Omega^{-1/2} sum_{G in S} c_G e^{i G.r_j};
+c_G[f] = Omega^{1/2} N^{-3} sum_j e^{-i G.r_j} f(r_j).
+
+Parity: every function here is pinned by ``tests/test_oracle_*.py`` except the
+multi-iteration ground-state loop, whose converged eigenvalues have no external
+truth beyond the free-electron limit ("parity unpinned" beyond that limit).
+"""
+import numpy as np
+
+TWO_PI = 2.0 * np.pi
+
+
+# ----------------------------------------------------------------------------------------------
+# FFT: recursive decimation in time, radix 2 or 3, along the last axis.
+# ----------------------------------------------------------------------------------------------
+def fft_last_axis(x, sign):
+    """Unnormalised DFT along the last axis: X[k] = sum_j x[j] exp(sign * 2 pi i j k / n).
+
+    Decimation in time: split x into r interleaved subsequences x[q::r], transform each
+    (length m = n/r), then X[k] = sum_q exp(sign 2 pi i q k / n) Y_q[k mod m].
+    """
+    x = np.asarray(x, dtype=np.complex128)
+    n = x.shape[-1]
+    if n == 1:
+        return x.copy()
+    if n % 2 == 0:
+        r = 2
+    elif n % 3 == 0:
+        r = 3
+    else:
+        raise ValueError("oracle FFT supports lengths 2^a 3^b only, got %d" % n)
+    m = n // r
+    k = np.arange(n)
+    out = np.zeros(x.shape, dtype=np.complex128)
+    for q in range(r):
+        yq = fft_last_axis(x[..., q::r], sign)           # [..., m]
+        twiddle = np.exp(sign * 1j * TWO_PI * q * k / n)  # [n]
+        out += twiddle * yq[..., k % m]
+    return out
+
+
+def fft_axis(x, axis, sign):
+    return np.moveaxis(fft_last_axis(np.moveaxis(x, axis, -1), sign), -1, axis)
+
+
+def fft3(x, sign):
+    """Unnormalised 3D DFT over the last three axes, exponent sign ``sign``."""
+    y = fft_axis(x, -1, sign)
+    y = fft_axis(y, -2, sign)
+    return fft_axis(y, -3, sign)
+
+
+# ----------------------------------------------------------------------------------------------
+# Geometry: cutoff sphere, local potential, projector spheres
+# ----------------------------------------------------------------------------------------------
+def integer_frequencies(N):
+    """m_i = j_i for j_i < N/2 else j_i - N (FFT order)."""
+    j = np.arange(N)
+    return np.where(j < N / 2.0, j, j - N)
+
+
+class Cell:
+    """Everything the Hamiltonian needs for one periodic cubic cell.
+
+    Built from the same plain dict that ``paper_2106_03872_gb300.inputs`` produces:
+    L, N, ecut, pos [natoms,3], vloc_depth, vloc_width, nproj (1 or 4), proj_sigma,
+    proj_rc, proj_D, optional occ [nstates].
+    """
+
+    def __init__(self, desc):
+        self.L = float(desc["L"])
+        self.N = int(desc["N"])
+        self.ecut = float(desc["ecut"])
+        self.pos = np.asarray(desc["pos"], float).reshape(-1, 3)
+        self.natoms = len(self.pos)
+        self.depth = float(desc["vloc_depth"])
+        self.width = float(desc["vloc_width"])
+        self.nproj = int(desc["nproj"])
+        self.sigma_b = float(desc["proj_sigma"])
+        self.rc = float(desc["proj_rc"])
+        self.D = float(desc["proj_D"])
+        self.occ = desc.get("occ")
+        N, L = self.N, self.L
+        self.h = L / N
+        self.omega = L ** 3
+        self.dV = self.omega / N ** 3
+        self.build_sphere()
+        self.vloc = self.local_potential()
+        self.build_projectors()
+
+    # -- Plane-wave basis: S = {G : |G|^2 / 2 <= E_cut} ------------------------------------
+    def build_sphere(self):
+        N = self.N
+        m = integer_frequencies(N)
+        mx, my, mz = np.meshgrid(m, m, m, indexing="ij")            # [jx, jy, jz]
+        m2 = (mx ** 2 + my ** 2 + mz ** 2).ravel()
+        g2_all = (TWO_PI / self.L) ** 2 * m2
+        self.g2_full = g2_all.reshape(N, N, N)
+        keep = 0.5 * g2_all <= self.ecut
+        self.sphere_index = np.flatnonzero(keep)                    # row-major, z fastest
+        self.m = np.stack([mx.ravel(), my.ravel(), mz.ravel()], axis=1)[self.sphere_index]
+        self.g2 = g2_all[self.sphere_index]
+        self.nG = len(self.sphere_index)
+
+    def grid_points(self):
+        j = np.arange(self.N) * self.h
+        x, y, z = np.meshgrid(j, j, j, indexing="ij")
+        return np.stack([x, y, z], axis=-1)                          # [N,N,N,3]
+
+    # -- V_loc(r) = sum_a A exp(-|r - R_a - L n|^2 / (2 w^2)), 27 image shifts n -------------
+    def local_potential(self):
+        r = self.grid_points()
+        v = np.zeros((self.N,) * 3)
+        shifts = [np.array([a, b, c], float) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
+        for R in self.pos:
+            for s in shifts:
+                d = r - (R + self.L * s)
+                v += self.depth * np.exp(-np.sum(d * d, axis=-1) / (2.0 * self.width ** 2))
+        return v
+
+    # -- KB projectors on the real-space sphere |r - R_I| < R_c (Eq. 9) ----------------------
+    def build_projectors(self):
+        """Per atom: flat grid indices inside the sphere (grid order) and beta [nproj, npts],
+        s: exp(-d^2/(2 sigma^2)); p_alpha: d_alpha exp(-d^2/(2 sigma^2)); each normalised
+        so that dV sum_j beta(r_j)^2 = 1.  d is the minimum-image displacement."""
+        r = self.grid_points().reshape(-1, 3)
+        self.proj_index, self.proj_beta = [], []
+        for R in self.pos:
+            d = r - R
+            d -= self.L * np.round(d / self.L)
+            d2 = np.sum(d * d, axis=1)
+            inside = np.flatnonzero(d2 < self.rc ** 2)
+            dd = d[inside]
+            g = np.exp(-d2[inside] / (2.0 * self.sigma_b ** 2))
+            rows = [g] if self.nproj == 1 else [g, dd[:, 0] * g, dd[:, 1] * g, dd[:, 2] * g]
+            beta = np.array([b / np.sqrt(self.dV * np.sum(b * b)) for b in rows])
+            self.proj_index.append(inside)
+            self.proj_beta.append(beta)
+
+    def occupations(self, nstates):
+        if self.occ is None:
+            return np.ones(nstates)
+        return np.asarray(self.occ, float)[:nstates]
+
+    def sd_step_length(self):
+        """alpha = 1/(E_cut + (max V_loc - min V_loc) + D): bounds the steepest-descent
+        update factor of every eigencomponent to [0, 1) (a reading; the paper gives no step)."""
+        return 1.0 / (self.ecut + (self.vloc.max() - self.vloc.min()) + self.D)
+
+
+# ----------------------------------------------------------------------------------------------
+# Basis changes
+# ----------------------------------------------------------------------------------------------
+def to_real(cell, c):
+    """psi(r_j) = Omega^{-1/2} sum_{G in S} c_G exp(i G.r_j); c [n, nG] -> [n, N, N, N]."""
+    c = np.atleast_2d(c)
+    N = cell.N
+    grid = np.zeros((c.shape[0], N ** 3), dtype=np.complex128)
+    grid[:, cell.sphere_index] = c
+    return fft3(grid.reshape(-1, N, N, N), +1) / np.sqrt(cell.omega)
+
+
+def to_coeff(cell, f):
+    """c_G = Omega^{1/2} N^{-3} sum_j exp(-i G.r_j) f(r_j), kept on S; [n,N,N,N] -> [n, nG]."""
+    N = cell.N
+    F = fft3(np.asarray(f, dtype=np.complex128).reshape(-1, N, N, N), -1)
+    return F.reshape(-1, N ** 3)[:, cell.sphere_index] * np.sqrt(cell.omega) / N ** 3
+
+
+# ----------------------------------------------------------------------------------------------
+# Hamiltonian application (Eq. 2; kinetic in Fourier space, local and nonlocal in real space)
+# ----------------------------------------------------------------------------------------------
+def nonlocal_projections(cell, psi_r):
+    """p[k, I, l] = dV sum_{|r_j - R_I| < R_c} beta_Il(r_j) psi_k(r_j)  (the integral of Eq. 9)."""
+    flat = psi_r.reshape(psi_r.shape[0], -1)
+    p = np.zeros((flat.shape[0], cell.natoms, cell.nproj), dtype=np.complex128)
+    for I in range(cell.natoms):
+        vals = flat[:, cell.proj_index[I]]
+        p[:, I, :] = cell.dV * vals @ cell.proj_beta[I].T
+    return p
+
+
+def apply_nonlocal(cell, psi_r):
+    """V_NL psi(r) = sum_I sum_l D beta_Il(r) p_Il (Eq. 9 with KB coupling D), atoms in index order."""
+    p = nonlocal_projections(cell, psi_r)
+    out = np.zeros((psi_r.shape[0], cell.N ** 3), dtype=np.complex128)
+    for I in range(cell.natoms):
+        out[:, cell.proj_index[I]] += cell.D * p[:, I, :] @ cell.proj_beta[I]
+    return out.reshape(psi_r.shape)
+
+
+def apply_h(cell, c, v=None):
+    """H c = P_S (T + V + V_NL) P_S c for a block c [n, nG].
+
+    Steps as the paper describes them: transform to the real-space grid, apply the
+    multiplicative potential v (default V_loc) and the nonlocal projectors there,
+    transform back, keep G in S, and add the kinetic term |G|^2/2 (diagonal in
+    Fourier space)."""
+    c = np.atleast_2d(np.asarray(c, dtype=np.complex128))
+    v = cell.vloc if v is None else v
+    psi = to_real(cell, c)
+    u = v[None] * psi + apply_nonlocal(cell, psi)
+    return to_coeff(cell, u) + 0.5 * cell.g2[None, :] * c
+
+
+# ----------------------------------------------------------------------------------------------
+# Density (Eq. 1)
+# ----------------------------------------------------------------------------------------------
+def density(cell, c, occ=None):
+    """n(r_j) = sum_k f_k |psi_k(r_j)|^2, shape [N, N, N] in grid order (x, y, z)."""
+    c = np.atleast_2d(c)
+    f = cell.occupations(c.shape[0]) if occ is None else np.asarray(occ, float)
+    psi = to_real(cell, c)
+    return np.einsum("k,kxyz->xyz", f, np.abs(psi) ** 2)
+
+
+# ----------------------------------------------------------------------------------------------
+# Rotations in state space (Sec. "Ground-state solution": orthogonalisation and subspace diagonalisation)
+# ----------------------------------------------------------------------------------------------
+def gram(a, b=None):
+    """S_ij = sum_G conj(a_iG) b_jG  (S = Psi^H Psi for b = a)."""
+    b = a if b is None else b
+    return np.conj(a) @ b.T
+
+
+def cholqr(c):
+    """Orthonormalise the rows of c: S = L L^H, Psi <- Psi L^{-H} (rows: c <- conj(L^{-1}) c)."""
+    S = gram(c)
+    L = np.linalg.cholesky(S)
+    return np.conj(np.linalg.inv(L)) @ c, S
+
+
+def fix_phases(U):
+    """Make the largest-magnitude component of each column real and positive (lowest index on ties)."""
+    U = U.copy()
+    for j in range(U.shape[1]):
+        i = int(np.argmax(np.abs(U[:, j])))
+        U[:, j] *= np.conj(U[i, j]) / abs(U[i, j])
+    return U
+
+
+def rayleigh_ritz(c, hc):
+    """H_sub = Psi^H (H Psi), eigen-decomposed; returns (eps ascending, U, c U, (Hc) U)."""
+    Hs = gram(c, hc)
+    Hs = 0.5 * (Hs + np.conj(Hs.T))
+    eps, U = np.linalg.eigh(Hs)
+    U = fix_phases(U)
+    return eps, U, U.T @ c, U.T @ hc
+
+
+def block_iteration(cell, c, niter, v=None):
+    """Steepest-descent block iteration (Sec. "Ground-state solution"), per iteration:
+    CholQR -> H Psi -> Rayleigh-Ritz -> R = H Psi - Psi diag(eps) -> Psi <- Psi - alpha R.
+    Returns (eps of the last Rayleigh-Ritz, final c)."""
+    alpha = cell.sd_step_length()
+    eps = None
+    for _ in range(niter):
+        c, _ = cholqr(c)
+        hc = apply_h(cell, c, v)
+        eps, _, c, hc = rayleigh_ritz(c, hc)
+        c = c - alpha * (hc - eps[:, None] * c)
+    return eps, c
+
+
+# ----------------------------------------------------------------------------------------------
+# Hartree (Sec. "Poisson solver", periodic) and LDA Slater exchange
+# ----------------------------------------------------------------------------------------------
+def hartree(cell, n):
+    """v_H(G) = 4 pi n(G) / |G|^2 on the full grid, v_H(G=0) = 0 (neutralising background)."""
+    N = cell.N
+    nG = fft3(n.astype(np.complex128), -1) / N ** 3
+    g2 = cell.g2_full
+    vG = np.zeros_like(nG)
+    nz = g2 > 0
+    vG[nz] = 4.0 * np.pi * nG[nz] / g2[nz]
+    return np.real(fft3(vG, +1))
+
+
+def slater(n):
+    """Dirac/Slater exchange: v_x = -(3 n / pi)^{1/3}, eps_x = -3/4 (3 n / pi)^{1/3}; n clamped at 0."""
+    nn = np.maximum(n, 0.0)
+    vx = -np.cbrt(3.0 * nn / np.pi)
+    return vx, 0.75 * vx
+
+
+def hxc_potential(cell, n):
+    """V = V_loc + v_H[n] + v_x[n]; also returns the double-counting pieces for Eq. 5."""
+    vh = hartree(cell, n)
+    vx, ex = slater(n)
+    dV = cell.dV
+    parts = dict(eh=0.5 * dV * np.sum(n * vh), ex=dV * np.sum(n * ex), nvx=dV * np.sum(n * vx))
+    return cell.vloc + vh + vx, parts
+
+
+def total_energy(cell, c, hc, parts=None):
+    """E = sum_k f_k <psi_k|H|psi_k> - 1/2 int n v_H + E_x - int n v_x (Eq. 5, eigenvalues
+    replaced by expectation values).  Without Hartree/exchange only the first term remains."""
+    f = cell.occupations(c.shape[0])
+    band = float(np.sum(f * np.real(np.sum(np.conj(c) * hc, axis=1))))
+    if parts is None:
+        return band
+    return band - parts["eh"] + parts["ex"] - parts["nvx"]
+
+
+def total_norm(cell, c):
+    f = cell.occupations(c.shape[0])
+    return float(np.sum(f * np.sum(np.abs(c) ** 2, axis=1)))
+
+
+# ----------------------------------------------------------------------------------------------
+# Real-time propagation: ETRS with a 4th-order Taylor exponential, shared powers (Eqs. 6-8)
+# ----------------------------------------------------------------------------------------------
+TAYLOR_ORDER = 4
+
+
+def taylor_coefficients(lam):
+    """a_k = lam^k / k!, k = 0..4 (Eq. 8)."""
+    a, out = 1.0 + 0j, []
+    for k in range(TAYLOR_ORDER + 1):
+        out.append(a)
+        a = a * lam / (k + 1)
+    return out
+
+
+def potential_for(cell, c, hartree_xc):
+    if not hartree_xc:
+        return cell.vloc, None
+    return hxc_potential(cell, density(cell, c))
+
+
+def td_step(cell, c, dt, propagator="etrs", hartree_xc=True):
+    """One real-time step from t to t + dt; returns (c(t+dt), norm(t), energy(t)).
+
+    ETRS (Eq. 6): phi(t+dt) = exp(-i dt/2 H(t+dt)) exp(-i dt/2 H(t)) phi(t), with
+    H(t+dt) built from the density of the full step exp(-i dt H(t)) phi(t) (Eq. 7).
+    The powers H(t)^k phi are computed once and combined with both coefficient sets
+    lam = -i dt and lam = -i dt/2 (the shared-power saving).  'taylor' is the plain
+    4th-order step phi <- sum_k (-i dt H(t))^k / k! phi.
+    """
+    v_t, parts = potential_for(cell, c, hartree_xc)
+    powers = [c]
+    for _ in range(TAYLOR_ORDER):
+        powers.append(apply_h(cell, powers[-1], v_t))
+    norm_t = total_norm(cell, c)
+    energy_t = total_energy(cell, c, powers[1], parts)
+    full = sum(a * w for a, w in zip(taylor_coefficients(-1j * dt), powers))
+    if propagator == "taylor":
+        return full, norm_t, energy_t
+    half = sum(a * w for a, w in zip(taylor_coefficients(-0.5j * dt), powers))
+    v_next, _ = potential_for(cell, full, hartree_xc)
+    out, w = half.copy(), half
+    for a in taylor_coefficients(-0.5j * dt)[1:]:
+        w = apply_h(cell, w, v_next)
+        out = out + a * w
+    return out, norm_t, energy_t
+
+
+def td_run(cell, c, dt, nsteps, propagator="etrs", hartree_xc=True):
+    norms, energies = [], []
+    for _ in range(nsteps):
+        c, nrm, e = td_step(cell, c, dt, propagator, hartree_xc)
+        norms.append(nrm)
+        energies.append(e)
+    return c, np.array(norms), np.array(energies)

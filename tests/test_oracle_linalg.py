@@ -1,0 +1,76 @@
+"""Pins for the oracle's density, CholQR, Rayleigh-Ritz and block iteration (CPU only)."""
+import numpy as np
+
+from oracle import ks_oracle as ko
+from paper_2106_03872_gb300 import inputs
+
+
+def make_cell(L=10.0, N=24, natoms=4, depth=-2.0, seed=11, ecut=20.0, D=0.5):
+    pos = inputs.uniform_positions(seed, natoms, L)
+    return ko.Cell(dict(L=L, N=N, ecut=ecut, pos=pos, vloc_depth=depth, vloc_width=0.8, nproj=4,
+                        proj_sigma=0.5, proj_rc=2.0, proj_D=D))
+
+
+def mgs(c):
+    """Modified Gram-Schmidt on the rows of c."""
+    q = c.astype(complex).copy()
+    for i in range(q.shape[0]):
+        for j in range(i):
+            q[i] -= (np.vdot(q[j], q[i])) * q[j]
+        q[i] /= np.linalg.norm(q[i])
+    return q
+
+
+def test_cholqr_orthonormal_and_unique():
+    cell = make_cell()
+    c = inputs.random_coeffs(1, 9, cell.nG)
+    q, S = ko.cholqr(c)
+    assert np.max(np.abs(ko.gram(q) - np.eye(9))) <= 1e-13
+    assert np.max(np.abs(q - mgs(c))) <= 1e-12
+    assert np.allclose(S, np.conj(S.T))
+
+
+def test_density_integrates_to_occupations_and_plane_wave_uniform():
+    cell = make_cell()
+    c, _ = ko.cholqr(inputs.random_coeffs(2, 5, cell.nG))
+    n = ko.density(cell, c)
+    assert abs(cell.dV * n.sum() - 5.0) < 1e-12
+    occ = np.array([2.0, 1.0, 0.5, 0.0, 1.0])
+    assert abs(cell.dV * ko.density(cell, c, occ).sum() - occ.sum()) < 1e-12
+    pw = np.zeros((1, cell.nG), complex)
+    pw[0, 17] = 1.0
+    assert np.max(np.abs(ko.density(cell, pw) - 1.0 / cell.omega)) < 1e-15
+
+
+def test_rayleigh_ritz_recovers_exact_eigenvalues_of_invariant_subspace():
+    cell = make_cell(natoms=0)
+    picks = [0, 5, 40, 300, 2000]
+    c = np.zeros((5, cell.nG), complex)
+    for r, k in enumerate(picks):
+        c[r, k] = 1.0
+    rng = np.random.default_rng(4)
+    Q, _ = np.linalg.qr(rng.normal(size=(5, 5)) + 1j * rng.normal(size=(5, 5)))
+    mixed = Q @ c
+    eps, U, c2, hc2 = ko.rayleigh_ritz(mixed, ko.apply_h(cell, mixed))
+    assert np.allclose(eps, np.sort(0.5 * cell.g2[picks]), atol=1e-12)
+    assert np.allclose(hc2, eps[:, None] * c2, atol=1e-12)
+    for j in range(5):                                   # phase convention
+        i = np.argmax(np.abs(U[:, j]))
+        assert abs(U[i, j].imag) < 1e-15 and U[i, j].real > 0
+
+
+def test_block_iteration_free_electron_limit():
+    """V_loc = 0, D = 0: the lowest 7 eigenvalues are the G = 0 and |m| = 1 shells."""
+    cell = make_cell(L=4.0, N=12, natoms=0, ecut=20.0)
+    c = inputs.random_coeffs(3, 7, cell.nG)
+    eps, c = ko.block_iteration(cell, c, 250)
+    shells = np.sort(0.5 * cell.g2)[:7]
+    assert np.allclose(eps, shells, atol=1e-9)
+
+
+def test_block_iteration_lowers_ritz_values():
+    cell = make_cell(natoms=4, depth=-3.0)
+    c = inputs.random_coeffs(5, 6, cell.nG)
+    e1, c1 = ko.block_iteration(cell, c, 2)
+    e2, _ = ko.block_iteration(cell, c1, 10)
+    assert np.all(e2 <= e1 + 1e-12)

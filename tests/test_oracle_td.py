@@ -1,0 +1,119 @@
+"""Pins for the oracle's Poisson, Slater exchange, energy and real-time step (CPU only)."""
+import numpy as np
+import pytest
+
+from oracle import ks_oracle as ko
+from paper_2106_03872_gb300 import inputs
+
+
+def make_cell(L=10.0, N=24, natoms=4, depth=-2.0, seed=11, ecut=20.0, D=0.5):
+    pos = inputs.uniform_positions(seed, natoms, L)
+    return ko.Cell(dict(L=L, N=N, ecut=ecut, pos=pos, vloc_depth=depth, vloc_width=0.8, nproj=4,
+                        proj_sigma=0.5, proj_rc=2.0, proj_D=D))
+
+
+def test_hartree_of_cosine_density():
+    """n = n0 + cos(q.r) solves to v_H = 4 pi/|q|^2 cos(q.r) (the constant is removed by G=0)."""
+    cell = make_cell(natoms=0)
+    q = 2 * np.pi / cell.L * np.array([1, 2, -1])
+    r = cell.grid_points()
+    n = 0.3 + np.cos(r @ q)
+    vh = ko.hartree(cell, n)
+    assert np.max(np.abs(vh - 4 * np.pi / (q @ q) * np.cos(r @ q))) < 1e-12
+    _, parts = ko.hxc_potential(cell, n)
+    assert abs(parts["eh"] - 0.5 * 4 * np.pi / (q @ q) * cell.omega / 2) < 1e-10
+
+
+def test_slater_exchange_uniform_gas():
+    """Textbook uniform-gas exchange: eps_x = -0.458165293 / r_s Ha, v_x = 4/3 eps_x,
+    with n = 3 / (4 pi r_s^3)."""
+    for rs in (0.5, 1.0, 2.0, 5.0):
+        n = 3.0 / (4 * np.pi * rs ** 3)
+        vx, ex = ko.slater(np.array([n]))
+        assert abs(ex[0] - (-0.458165293283143 / rs)) < 1e-12
+        assert abs(vx[0] - 4.0 / 3.0 * ex[0]) < 1e-12
+    vx, ex = ko.slater(np.array([-1e-3, 0.0]))
+    assert np.all(vx == 0) and np.all(ex == 0)
+
+
+def test_taylor_factor_of_free_plane_wave():
+    """Plane-wave eigenstate, eigenvalue e: one Taylor step multiplies it by R = sum_k (-i x)^k/k!,
+    x = dt e, and |R|^2 = 1 - x^6/72 + x^8/576 (closed form)."""
+    cell = make_cell(natoms=0)
+    k = 900
+    c = np.zeros((1, cell.nG), complex)
+    c[0, k] = 1.0
+    e = 0.5 * cell.g2[k]
+    for dt in (0.05, 0.2):
+        x = dt * e
+        out, nrm, en = ko.td_step(cell, c, dt, propagator="taylor", hartree_xc=False)
+        amp = out[0, k]
+        assert abs(abs(amp) ** 2 - (1 - x ** 6 / 72 + x ** 8 / 576)) < 1e-13
+        assert abs(amp - np.exp(-1j * x)) < x ** 5 / 120 * 1.01
+        assert abs(en - e) < 1e-12 and abs(nrm - 1.0) < 1e-15
+        out, _, _ = ko.td_step(cell, c, dt, propagator="etrs", hartree_xc=False)
+        x2 = x / 2
+        half = 1 - 1j * x2 - x2 ** 2 / 2 + 1j * x2 ** 3 / 6 + x2 ** 4 / 24
+        assert abs(out[0, k] - half ** 2) < 1e-13
+
+
+def test_fixed_potential_steps_against_dense_eigenbasis():
+    """Dense matrix of H (after the paper's practice of testing with a plain Hermitian
+    matrix): the Taylor step is diag(R(-i dt eps)) in the eigenbasis, ETRS with a fixed H
+    is diag(R(-i dt eps/2)^2)."""
+    cell = make_cell(L=6.0, N=12, natoms=2, depth=-2.0, ecut=6.0)
+    H = ko.apply_h(cell, np.eye(cell.nG)).T
+    assert np.max(np.abs(H - H.conj().T)) < 1e-12
+    eps, V = np.linalg.eigh(0.5 * (H + H.conj().T))
+    c = inputs.random_coeffs(8, 2, cell.nG)
+    dt = 0.07
+
+    def Rpoly(x):
+        return 1 - 1j * x - x ** 2 / 2 + 1j * x ** 3 / 6 + x ** 4 / 24
+
+    coeffs = np.conj(V.T) @ c.T                     # eigen-components [nG, n]
+    taylor = (V @ (Rpoly(dt * eps)[:, None] * coeffs)).T
+    etrs = (V @ (Rpoly(dt * eps / 2)[:, None] ** 2 * coeffs)).T
+    out_t, _, _ = ko.td_step(cell, c, dt, "taylor", hartree_xc=False)
+    out_e, _, _ = ko.td_step(cell, c, dt, "etrs", hartree_xc=False)
+    assert np.max(np.abs(out_t - taylor)) < 1e-12
+    assert np.max(np.abs(out_e - etrs)) < 1e-12
+
+
+def test_etrs_shared_powers_equal_separate_exponentials():
+    """The shared-power ETRS step equals three separately evaluated Taylor exponentials."""
+    cell = make_cell(L=8.0, N=16, natoms=2, depth=-2.0)
+    c, _ = ko.cholqr(inputs.random_coeffs(4, 3, cell.nG))
+    dt = 0.05
+
+    def expo(v, lam, pot):
+        out, w = v.copy(), v
+        for k in range(1, 5):
+            w = ko.apply_h(cell, w, pot) * (lam / k)
+            out = out + w
+        return out
+
+    v_t, _ = ko.hxc_potential(cell, ko.density(cell, c))
+    full = expo(c, -1j * dt, v_t)
+    half = expo(c, -0.5j * dt, v_t)
+    v_n, _ = ko.hxc_potential(cell, ko.density(cell, full))
+    ref = expo(half, -0.5j * dt, v_n)
+    got, _, _ = ko.td_step(cell, c, dt, "etrs", hartree_xc=True)
+    assert np.max(np.abs(got - ref)) < 1e-12
+
+
+@pytest.mark.slow
+def test_energy_conserved_and_converges_with_dt():
+    cell = make_cell(L=8.0, N=16, natoms=2, depth=-2.0)
+    c0, _ = ko.cholqr(inputs.random_coeffs(6, 4, cell.nG))
+    # Start from a few steepest-descent iterations so the high-G content is small.
+    _, c0 = ko.block_iteration(cell, c0, 6)
+    c0, _ = ko.cholqr(c0)
+    drifts = []
+    T = 0.4
+    for dt in (0.04, 0.02):
+        _, norms, energies = ko.td_run(cell, c0, dt, int(round(T / dt)) + 1, "etrs", True)
+        drifts.append(abs(energies[-1] - energies[0]))
+        assert abs(norms[-1] - norms[0]) < 1e-5
+    assert drifts[0] < 1e-4
+    assert drifts[1] < drifts[0] / 10.0         # observed ~dt^4 (ratio 16-28); demand > 3rd order
