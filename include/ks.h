@@ -1,0 +1,194 @@
+/*
+ * ks.h — C ABI of the GB300 Kohn-Sham hot path (plane-wave DFT/TDDFT, arXiv 2106.03872).
+ *
+ * One periodic cubic cell of side L (bohr), an N^3 real-space grid (N = 2^a 3^b, even,
+ * 8 <= N <= 128), a kinetic cutoff sphere S = {G : |G|^2/2 <= ecut}, a local potential
+ * V_loc (sum of Gaussians) and separable Kleinman-Bylander projectors (Eq. 9).  The
+ * operator is H = P_S (-1/2 nabla^2 + V + V_NL) P_S (Eq. 2), applied in operator form:
+ * kinetic in Fourier space, potential and projectors on the real-space grid, two FFTs
+ * per application (Sec. "Implementation of the KS Hamiltonian").
+ *
+ * Units are atomic (bohr, hartree, hbar/hartree).  No call lets a C++ exception out.
+ * Every call returns a ks_status; ks_last_error() gives a thread-local message.
+ *
+ * Canonical layouts (host side of the boundary):
+ *   - state coefficients: [nstates][nG] complex128, interleaved (re, im) doubles, G in
+ *     the canonical sphere order: grid index (j_x, j_y, j_z) row-major, z fastest,
+ *     with m_i = j_i for j_i < N/2 else j_i - N and G = (2 pi / L) m;
+ *   - real-space fields: [N][N][N] in grid order (x, y, z), z fastest, r_j = (L/N) j;
+ *   - psi(r_j) = Omega^{-1/2} sum_{G in S} c_G exp(i G.r_j),  Omega = L^3.
+ * Device buffers passed in are borrowed (never freed by the library) and are used in
+ * stream order on the given stream (NULL = legacy default stream).
+ */
+#ifndef KS_H
+#define KS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ks_grid_s* ks_grid;
+typedef struct ks_server_s* ks_server;
+
+typedef enum {
+  KS_OK = 0,
+  KS_ERR_ARG = 1,         /* invalid argument; nothing was changed                     */
+  KS_ERR_NOMEM = 2,       /* device allocation failed or the memory budget is exceeded */
+  KS_ERR_NOT_POSDEF = 3,  /* Gram matrix not positive definite (dependent states)      */
+  KS_ERR_DIVERGED = 4,    /* real-time norm left [1 - 0.05, 1 + 0.05] x initial, or NaN */
+  KS_ERR_TIMEOUT = 5,     /* ks_serve_poll limit expired                               */
+  KS_ERR_CUDA = 6,        /* a CUDA runtime call or kernel failed                      */
+  KS_PENDING = 7,         /* ks_serve_poll: request not finished yet                   */
+  KS_ERR_STATE = 8        /* call not valid in the handle's current state              */
+} ks_status;
+
+/* Internal arithmetic of a handle.
+ *   KS_FP64          complex128 states, FP64 FFTs, FP64 everything (correctness anchor).
+ *   KS_MIXED_BF16X3  complex64 states and FFTs; projector and Gram/rotation GEMMs with
+ *                    each FP32 operand split into two bf16 terms (3 products), FP32
+ *                    accumulation; Cholesky, Rayleigh-Ritz eigenvalues, norms and
+ *                    energies in FP64.
+ *   KS_MIXED_TF32    as above with the GEMM operands split into two tf32 terms. */
+typedef enum { KS_FP64 = 0, KS_MIXED_BF16X3 = 1, KS_MIXED_TF32 = 2 } ks_precision;
+
+/* Cell description (all host memory, copied by ks_grid_create).
+ *   pos      [natoms][3] atom positions (bohr), any real values (wrapped periodically).
+ *   V_loc(r) = sum_a vloc_depth * exp(-|r - R_a - L n|^2 / (2 vloc_width^2)), n in {-1,0,1}^3.
+ *   nproj    1 (s) or 4 (s, p_x, p_y, p_z) Gaussian projectors per atom on the sphere
+ *            |d| < proj_rc (d the minimum-image displacement), beta_s = exp(-d^2/(2 s^2)),
+ *            beta_p = d_alpha exp(-d^2/(2 s^2)), s = proj_sigma, each normalised to
+ *            dV sum beta^2 = 1; V_NL psi = sum_{I,l} proj_D beta_Il <beta_Il|psi> (Eq. 9).
+ *   occ      [nstates] occupations f_k (NULL: all 1), used by the density (Eq. 1) and
+ *            by the norm and energy reductions. */
+typedef struct {
+  double L;
+  int N;
+  double ecut;
+  int natoms;
+  const double* pos;
+  double vloc_depth, vloc_width;
+  int nproj;
+  double proj_sigma, proj_rc, proj_D;
+  int nstates;
+  const double* occ;
+  ks_precision prec;
+} ks_cell_desc;
+
+/* Number of plane waves in the cutoff sphere for (L, N, ecut).  Host only: needs no GPU.
+ * KS_ERR_ARG if N is not an even 2^a 3^b in [8, 128] or the sphere leaves the grid's
+ * Nyquist box. */
+ks_status ks_count_gvectors(double L, int N, double ecut, int* nG);
+
+/* Build a handle: sphere tables, V_loc, projector tables and every device buffer the
+ * calls below need are allocated here (sized by desc->nstates).  *out is NULL on error.
+ * The handle owns its device memory; states start at zero. */
+ks_status ks_grid_create(const ks_cell_desc* desc, ks_grid* out);
+ks_status ks_grid_destroy(ks_grid g);
+
+/* nG, and optionally m[3*nG] (integer frequencies, canonical order); m may be NULL. */
+ks_status ks_grid_gvectors(ks_grid g, int* nG, int* m);
+
+/* Device bytes the handle holds (for admission control). */
+ks_status ks_grid_device_bytes(ks_grid g, size_t* bytes);
+
+/* V_loc on the grid, [N^3] doubles in grid order (host). */
+ks_status ks_get_vloc(ks_grid g, double* v_host);
+
+/* Copy host states in ([nstates][nG] complex128, converted to the handle's precision)
+ * or out (converted back to complex128).  Synchronous. */
+ks_status ks_set_states(ks_grid g, const double* c_host);
+ks_status ks_get_states(ks_grid g, double* c_host);
+
+/* Device pointer to the handle's resident states, [nstates][nG] complex of the handle's
+ * precision (double2 for KS_FP64, float2 otherwise).  Owned by the handle. */
+ks_status ks_states_device(ks_grid g, void** psi_dev);
+
+/* H psi for nstates <= desc->nstates states (Eq. 2): hpsi = P_S (T + V + V_NL) psi.
+ * psi_dev, hpsi_dev: device [nstates][nG] complex of the handle's precision; must not
+ * overlap.  V is the handle's current potential (V_loc, or V_loc + v_H + v_x after a
+ * real-time step with hartree_xc).  Asynchronous on stream. */
+ks_status ks_apply_h(ks_grid g, const void* psi_dev, void* hpsi_dev, int nstates, void* stream);
+
+/* Same operation end to end from host memory: psi_host / hpsi_host are
+ * [nstates][nG] complex128 (host); the copies in and out are part of the call.
+ * Synchronous. */
+ks_status ks_apply_h_host(ks_grid g, const double* psi_host, double* hpsi_host, int nstates);
+
+/* Density of the resident states, n(r) = sum_k f_k |psi_k(r)|^2 (Eq. 1), written to
+ * n_dev [N^3] in grid order; element type double for KS_FP64, float otherwise.
+ * Accumulated over states in a fixed order (deterministic). */
+ks_status ks_density(ks_grid g, void* n_dev, void* stream);
+
+/* CholQR of the resident states (Sec. "Ground-state solution", orthogonalisation):
+ * S = Psi^H Psi, S = L L^H (FP64 Cholesky on the GPU), Psi <- Psi L^{-H}.
+ * S_host_opt (may be NULL) receives S, [nstates][nstates] complex128 row-major,
+ * S_ij = sum_G conj(c_iG) c_jG.  KS_ERR_NOT_POSDEF if S is not positive definite
+ * (states unchanged then).  Synchronous (reads a status word). */
+ks_status ks_orthonormalize(ks_grid g, double* S_host_opt, void* stream);
+
+/* Rayleigh-Ritz on the resident states (subspace diagonalisation): H_sub = Psi^H H Psi,
+ * eigen-decomposed on the GPU (ascending), Psi <- Psi U, and the handle's H Psi buffer
+ * <- (H Psi) U.  eig_host [nstates] receives the Ritz values.  The states should be
+ * orthonormal.  Synchronous. */
+ks_status ks_rayleigh_ritz(ks_grid g, double* eig_host, void* stream);
+
+/* niter steepest-descent block iterations (Sec. "Ground-state solution"), each:
+ * CholQR -> H Psi -> Rayleigh-Ritz -> Psi <- Psi - alpha (H Psi - Psi diag(eps)),
+ * alpha = 1/(ecut + max V_loc - min V_loc + proj_D).  eig_host [nstates] receives the
+ * Ritz values of the last iteration.  Synchronous. */
+ks_status ks_block_iteration(ks_grid g, int niter, double* eig_host, void* stream);
+
+/* nsteps real-time steps of dt (Sec. "Real-time propagation").
+ *   propagator 0: ETRS (Eq. 6) with H(t+dt) from the density of the full step (Eq. 7);
+ *                 the powers H(t)^k psi, k = 1..4, are shared by the exp(-i dt H) and
+ *                 exp(-i dt/2 H) Taylor series (Eq. 8): 8 H applications per step.
+ *   propagator 1: plain 4th-order Taylor step psi <- sum_k (-i dt H(t))^k/k! psi.
+ *   hartree_xc 1: V(t) = V_loc + v_H[n(t)] + v_x[n(t)] recomputed from the density at the
+ *                 start of every step (periodic Poisson in Fourier space with v_H(G=0)=0,
+ *                 LDA Slater exchange); 0: V = V_loc fixed.
+ * norm_out[s] = sum_k f_k ||psi_k(t_s)||^2 and energy_out[s] = E(t_s) (Eq. 5 with the
+ * eigenvalue sum replaced by sum_k f_k <psi_k|H(t_s)|psi_k>), t_s the start of step s;
+ * both may be NULL.  KS_ERR_DIVERGED if a norm leaves 5% of the first one.
+ * Synchronous (copies norms and energies back at the end). */
+ks_status ks_td_step(ks_grid g, double dt, int nsteps, int propagator, int hartree_xc,
+                     double* norm_out, double* energy_out, void* stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* Serving: continuous batching of independent calculations on one GPU.               */
+/* ---------------------------------------------------------------------------------- */
+
+/* A server owns a scheduler thread and admits requests while the device memory they
+ * need fits in mem_budget_bytes (0: 80% of the free device memory at creation). */
+ks_status ks_serve_create(size_t mem_budget_bytes, ks_server* out);
+/* Stops the scheduler after the running requests finish; pending ones are dropped. */
+ks_status ks_serve_destroy(ks_server s);
+
+/* Queue one calculation: desc (copied; prec honoured) with initial states c0
+ * ([nstates][nG] complex128 host, copied now; NULL = seeded random start orthonormalised
+ * on the device), kind 0: `count` block iterations (result: Ritz values), kind 1: `count`
+ * ETRS steps of dt with Hartree + exchange (result: energies per step).
+ * KS_ERR_NOMEM if the request alone can never fit the budget. */
+ks_status ks_serve_submit(ks_server s, const ks_cell_desc* desc, const double* c0, int kind,
+                          int count, double dt, uint64_t* ticket);
+
+/* Wait up to timeout_ms (0: do not wait) for a ticket.  KS_PENDING if still queued or
+ * running after a zero wait, KS_ERR_TIMEOUT if the limit expired.  On KS_OK,
+ * result_out receives nstates Ritz values (kind 0) or count energies (kind 1), c_out_opt
+ * (may be NULL) the final states, latency_s_opt (may be NULL) submit-to-finish seconds;
+ * the ticket is then released. */
+ks_status ks_serve_poll(ks_server s, uint64_t ticket, int timeout_ms, double* result_out,
+                        double* c_out_opt, double* latency_s_opt);
+
+/* Result sizes for a ticket: number of doubles in result_out, nstates, nG. */
+ks_status ks_serve_result_info(ks_server s, uint64_t ticket, int* nresult, int* nstates, int* nG);
+
+/* Thread-local text of the last error of this thread (never NULL). */
+const char* ks_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KS_H */

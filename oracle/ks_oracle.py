@@ -135,13 +135,16 @@ class Cell:
 
     # -- V_loc(r) = sum_a A exp(-|r - R_a - L n|^2 / (2 w^2)), 27 image shifts n -------------
     def local_potential(self):
-        r = self.grid_points()
+        """Each Gaussian is evaluated in its separable form
+        exp(-|d|^2/(2w^2)) = prod_axis exp(-d_axis^2/(2w^2))."""
+        x = np.arange(self.N) * self.h
         v = np.zeros((self.N,) * 3)
         shifts = [np.array([a, b, c], float) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
         for R in self.pos:
             for s in shifts:
-                d = r - (R + self.L * s)
-                v += self.depth * np.exp(-np.sum(d * d, axis=-1) / (2.0 * self.width ** 2))
+                C = R + self.L * s
+                gx, gy, gz = (np.exp(-(x - C[k]) ** 2 / (2.0 * self.width ** 2)) for k in range(3))
+                v += self.depth * gx[:, None, None] * gy[None, :, None] * gz[None, None, :]
         return v
 
     # -- KB projectors on the real-space sphere |r - R_I| < R_c (Eq. 9) ----------------------

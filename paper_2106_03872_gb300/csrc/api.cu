@@ -1,0 +1,168 @@
+// The C ABI (include/ks.h): argument checks, handle lifetime, and translation of internal
+// errors into ks_status.  No exception crosses this boundary.
+#include <cstring>
+#include <memory>
+
+#include "engine.h"
+
+namespace ks {
+const char* last_error_cstr();
+}
+
+struct ks_grid_s {
+  std::unique_ptr<ks::EngineBase> eng;
+};
+
+namespace {
+
+template <typename F> ks_status guarded(F&& f) {
+  try {
+    f();
+    return KS_OK;
+  } catch (const ks::Error& e) {
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    ks::set_last_error("host allocation failed");
+    return KS_ERR_NOMEM;
+  } catch (...) {
+    ks::set_last_error("unexpected internal error");
+    return KS_ERR_CUDA;
+  }
+}
+
+inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+void need(bool ok, const char* what) {
+  if (!ok) ks::fail(KS_ERR_ARG, "%s", what);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ks_last_error(void) { return ks::last_error_cstr(); }
+
+ks_status ks_count_gvectors(double L, int N, double ecut, int* nG) {
+  return guarded([&] {
+    need(nG != nullptr, "nG is NULL");
+    ks::count_sphere(L, N, ecut, nG);
+  });
+}
+
+ks_status ks_grid_create(const ks_cell_desc* desc, ks_grid* out) {
+  if (out) *out = nullptr;
+  return guarded([&] {
+    need(desc != nullptr && out != nullptr, "desc/out is NULL");
+    std::unique_ptr<ks_grid_s> g(new ks_grid_s);
+    g->eng = ks::make_engine(*desc);
+    *out = g.release();
+  });
+}
+
+ks_status ks_grid_destroy(ks_grid g) {
+  return guarded([&] {
+    if (g) {
+      cudaDeviceSynchronize();
+      delete g;
+    }
+  });
+}
+
+ks_status ks_grid_gvectors(ks_grid g, int* nG, int* m) {
+  return guarded([&] {
+    need(g && nG, "grid/nG is NULL");
+    const auto& geo = g->eng->geo();
+    *nG = geo.nG;
+    if (m) std::memcpy(m, geo.mvec.data(), geo.mvec.size() * sizeof(int));
+  });
+}
+
+ks_status ks_grid_device_bytes(ks_grid g, size_t* bytes) {
+  return guarded([&] {
+    need(g && bytes, "grid/bytes is NULL");
+    *bytes = g->eng->device_bytes();
+  });
+}
+
+ks_status ks_get_vloc(ks_grid g, double* v_host) {
+  return guarded([&] {
+    need(g && v_host, "grid/v is NULL");
+    const auto& geo = g->eng->geo();
+    std::memcpy(v_host, geo.vloc.data(), geo.vloc.size() * sizeof(double));
+  });
+}
+
+ks_status ks_set_states(ks_grid g, const double* c_host) {
+  return guarded([&] {
+    need(g && c_host, "grid/c is NULL");
+    g->eng->set_states(c_host, 0);
+  });
+}
+
+ks_status ks_get_states(ks_grid g, double* c_host) {
+  return guarded([&] {
+    need(g && c_host, "grid/c is NULL");
+    g->eng->get_states(c_host, 0);
+  });
+}
+
+ks_status ks_states_device(ks_grid g, void** psi_dev) {
+  return guarded([&] {
+    need(g && psi_dev, "grid/psi_dev is NULL");
+    *psi_dev = g->eng->states_device();
+  });
+}
+
+ks_status ks_apply_h(ks_grid g, const void* psi_dev, void* hpsi_dev, int nstates, void* stream) {
+  return guarded([&] {
+    need(g && psi_dev && hpsi_dev, "grid/psi/hpsi is NULL");
+    need(psi_dev != hpsi_dev, "psi and hpsi must not overlap");
+    g->eng->apply_h(psi_dev, hpsi_dev, nstates, as_stream(stream));
+  });
+}
+
+ks_status ks_apply_h_host(ks_grid g, const double* psi_host, double* hpsi_host, int nstates) {
+  return guarded([&] {
+    need(g && psi_host && hpsi_host, "grid/psi/hpsi is NULL");
+    g->eng->apply_h_host(psi_host, hpsi_host, nstates);
+  });
+}
+
+ks_status ks_density(ks_grid g, void* n_dev, void* stream) {
+  return guarded([&] {
+    need(g && n_dev, "grid/n is NULL");
+    g->eng->density(n_dev, as_stream(stream));
+  });
+}
+
+ks_status ks_orthonormalize(ks_grid g, double* S_host_opt, void* stream) {
+  return guarded([&] {
+    need(g != nullptr, "grid is NULL");
+    g->eng->orthonormalize(S_host_opt, as_stream(stream));
+  });
+}
+
+ks_status ks_rayleigh_ritz(ks_grid g, double* eig_host, void* stream) {
+  return guarded([&] {
+    need(g != nullptr, "grid is NULL");
+    g->eng->rayleigh_ritz(eig_host, as_stream(stream));
+  });
+}
+
+ks_status ks_block_iteration(ks_grid g, int niter, double* eig_host, void* stream) {
+  return guarded([&] {
+    need(g != nullptr, "grid is NULL");
+    g->eng->block_iteration(niter, eig_host, as_stream(stream));
+  });
+}
+
+ks_status ks_td_step(ks_grid g, double dt, int nsteps, int propagator, int hartree_xc, double* norm_out,
+                     double* energy_out, void* stream) {
+  return guarded([&] {
+    need(g != nullptr, "grid is NULL");
+    need(dt > 0 && dt < 10, "dt must be in (0, 10)");
+    g->eng->td_steps(dt, nsteps, propagator, hartree_xc, norm_out, energy_out, as_stream(stream));
+  });
+}
+
+}  // extern "C"

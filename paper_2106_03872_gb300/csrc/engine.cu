@@ -1,0 +1,439 @@
+// Engine<T>: the device-resident state of one cell and the operations of the C ABI,
+// composed from the kernels.  T = double is the FP64 path; T = float the mixed path
+// (its fused Hamiltonian lives in fused.cu and plugs in through FusedOps).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+
+#include "engine.h"
+#include "fused.h"
+#include "kernels.h"
+
+namespace ks {
+
+DeviceArena::~DeviceArena() {
+  for (void* p : ptrs_) cudaFree(p);
+}
+
+void* DeviceArena::alloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) / 256 * 256;
+  KS_CUDA(cudaMalloc(&p, bytes));
+  ptrs_.push_back(p);
+  total_ += bytes;
+  return p;
+}
+
+namespace {
+
+constexpr int MAX_STEPS_CHUNK = 1024;
+constexpr size_t GRID_BUDGET = size_t(1) << 30;   // full-grid work buffer of the plain path
+
+template <typename T> size_t full_grid_batch(int N, int ns) {
+  const size_t per = (size_t)N * N * N * sizeof(cplx<T>);
+  size_t b = std::max<size_t>(1, GRID_BUDGET / per);
+  return std::min<size_t>(b, (size_t)ns);
+}
+
+template <typename T> class Engine final : public EngineBase {
+ public:
+  using C = cplx<T>;
+
+  explicit Engine(const ks_cell_desc& d) : prec_(d.prec), ns_(d.nstates) {
+    build_geometry(d, g_);
+    const int N = g_.N, nG = g_.nG;
+    const size_t N3 = (size_t)N * N * N;
+    const size_t sn = (size_t)ns_ * nG;
+    // ---- tables
+    t_.N = N;
+    t_.nG = nG;
+    t_.ncols = g_.ncols;
+    t_.natoms = g_.natoms;
+    t_.nproj = g_.nproj;
+    t_.ncov = (int)g_.cov_idx.size();
+    t_.xr = g_.xr;
+    t_.L = g_.L;
+    t_.omega = g_.omega;
+    t_.dV = g_.dV;
+    t_.D = g_.D;
+    t_.gidx = upload(g_.gidx);
+    t_.g2half = upload_real(g_.g2half);
+    std::vector<T> tw(2 * N);
+    for (int i = 0; i < 2 * N; ++i) tw[i] = (T)g_.tw[i];
+    t_.tw = reinterpret_cast<const C*>(upload(tw));
+    t_.col_xy = upload(g_.col_xy);
+    t_.col_off = upload(g_.col_off);
+    t_.col_half = upload(g_.col_half);
+    t_.sph_off = upload(g_.sph_off);
+    t_.sph_idx = upload(g_.sph_idx);
+    t_.sph_atom = upload(g_.sph_atom);
+    t_.sph_beta = upload_real(g_.sph_beta);
+    t_.cov_idx = upload(g_.cov_idx);
+    t_.cov_off = upload(g_.cov_off);
+    t_.cov_ent = upload(g_.cov_ent);
+    vloc_ = const_cast<T*>(upload_real(g_.vloc));
+    vtot_ = alloc<T>(N3);
+    KS_CUDA(cudaMemcpy(vtot_, vloc_, N3 * sizeof(T), cudaMemcpyDeviceToDevice));
+    occ_ = const_cast<double*>(upload(g_.occ));
+    // ---- states: 6 buffers (resident psi, H psi, and 4 work buffers for the real-time step)
+    for (int i = 0; i < 6; ++i) {
+      buf_[i] = alloc<C>(sn);
+      KS_CUDA(cudaMemset(buf_[i], 0, sn * sizeof(C)));
+    }
+    psi_ = buf_[0];
+    hpsi_ = buf_[1];
+    staging_ = alloc<double2>(sn);
+    // ---- Hamiltonian work
+    fused_ = make_fused_for(g_, t_, ns_, arena_);
+    if (!fused_) {
+      batch_ = (int)full_grid_batch<T>(N, ns_);
+      grid_ = alloc<C>((size_t)batch_ * N3);
+      proj_ = alloc<C>((size_t)batch_ * std::max(1, g_.natoms) * g_.nproj);
+    }
+    // ---- dense LA
+    const size_t nn = (size_t)ns_ * ns_;
+    part_elems_ = std::max<size_t>(nn * 8, 4096);
+    part_ = alloc<double2>(part_elems_);
+    mS_ = alloc<double2>(nn);
+    mA_ = alloc<double2>(nn);
+    mM_ = alloc<double2>(nn);
+    mV_ = alloc<double2>(nn);
+    eig_ = alloc<double>(ns_);
+    status_ = alloc<int>(4);
+    KS_CUDA(cudaMemset(status_, 0, 4 * sizeof(int)));
+    // ---- potentials / real-time
+    dens_ = alloc<T>(N3);
+    pwork_ = alloc<C>(N3);
+    hxc_partials_ = alloc<double>(HXC_BLOCKS * 3);
+    parts_ = alloc<double>(4);
+    dots_ = alloc<double2>(ns_);
+    norms_dev_ = alloc<double>(MAX_STEPS_CHUNK);
+    energies_dev_ = alloc<double>(MAX_STEPS_CHUNK);
+    KS_CUDA(cudaDeviceSynchronize());
+  }
+
+  const HostGeometry& geo() const override { return g_; }
+  int nstates() const override { return ns_; }
+  ks_precision precision() const override { return prec_; }
+  size_t device_bytes() const override { return arena_.bytes(); }
+  void* states_device() override { return psi_; }
+
+  void set_states(const double* c_host, cudaStream_t s) override {
+    const size_t sn = (size_t)ns_ * g_.nG;
+    KS_CUDA(cudaMemcpyAsync(staging_, c_host, sn * sizeof(double2), cudaMemcpyHostToDevice, s));
+    from_c128<T>(staging_, psi_, sn, s);
+    KS_CUDA(cudaStreamSynchronize(s));
+  }
+
+  void get_states(double* c_host, cudaStream_t s) override {
+    const size_t sn = (size_t)ns_ * g_.nG;
+    to_c128<T>(psi_, staging_, sn, s);
+    KS_CUDA(cudaMemcpyAsync(c_host, staging_, sn * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+  }
+
+  void randomize_states(uint64_t seed, cudaStream_t s) override {
+    random_states<T>(psi_, (size_t)ns_ * g_.nG, seed, s);
+  }
+
+  // ------------------------------------------------------------------------------------------
+  // H psi (Eq. 2): G -> r, V psi + V_NL psi on the grid, r -> G, keep S, + |G|^2/2 c.
+  // ------------------------------------------------------------------------------------------
+  void apply_h(const void* psi_v, void* hpsi_v, int n, cudaStream_t s) override {
+    const C* psi = static_cast<const C*>(psi_v);
+    C* hpsi = static_cast<C*>(hpsi_v);
+    if (n < 0 || n > ns_) fail(KS_ERR_ARG, "apply_h: nstates=%d outside [0, %d]", n, ns_);
+    if (n == 0) return;
+    if constexpr (std::is_same<T, float>::value) {
+      if (fused_) {
+        fused_->apply_h(psi, hpsi, n, vtot_, s);
+        return;
+      }
+    }
+    const int N = g_.N;
+    const size_t N3 = (size_t)N * N * N;
+    const T rs = T(1.0 / std::sqrt(g_.omega));
+    for (int b0 = 0; b0 < n; b0 += batch_) {
+      const int nb = std::min(batch_, n - b0);
+      const C* in = psi + (size_t)b0 * g_.nG;
+      KS_CUDA(cudaMemsetAsync(grid_, 0, (size_t)nb * N3 * sizeof(C), s));
+      scatter_sphere<T>(in, grid_, t_, nb, s);
+      for (int ax = 2; ax >= 0; --ax) fft_axis<T>(grid_, nb, N, ax, +1, t_.tw, s);
+      // grid holds psi' = Omega^{1/2} psi.  p = dV sum beta psi = dV Omega^{-1/2} sum beta psi'.
+      nl_project<T>(grid_, t_, proj_, nb, T(g_.dV) * rs, s);
+      multiply_potential<T>(grid_, vtot_, (int)N3, nb, s);
+      // u' = Omega^{1/2} u: add Omega^{1/2} D beta p
+      nl_add<T>(grid_, t_, proj_, nb, T(g_.D * std::sqrt(g_.omega)), s);
+      for (int ax = 0; ax < 3; ++ax) fft_axis<T>(grid_, nb, N, ax, -1, t_.tw, s);
+      gather_kinetic<T>(grid_, in, hpsi + (size_t)b0 * g_.nG, t_, nb, T(1.0 / double(N3)), s);
+    }
+  }
+
+  void apply_h_host(const double* psi_host, double* hpsi_host, int n) override {
+    if (n < 0 || n > ns_) fail(KS_ERR_ARG, "apply_h_host: nstates=%d outside [0, %d]", n, ns_);
+    cudaStream_t s = 0;
+    const size_t sn = (size_t)n * g_.nG;
+    C* in = spare(psi_, hpsi_);
+    C* out = spare3(psi_, hpsi_, in);
+    KS_CUDA(cudaMemcpyAsync(staging_, psi_host, sn * sizeof(double2), cudaMemcpyHostToDevice, s));
+    from_c128<T>(staging_, in, sn, s);
+    apply_h(in, out, n, s);
+    to_c128<T>(out, staging_, sn, s);
+    KS_CUDA(cudaMemcpyAsync(hpsi_host, staging_, sn * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // ------------------------------------------------------------------------------------------
+  // Density (Eq. 1) of n states of `psi`, into nout [N^3] (grid order), fixed state order.
+  // ------------------------------------------------------------------------------------------
+  void density_of(const C* psi, int n, T* nout, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (fused_) {
+        fused_->density(psi, n, occ_, nout, s);
+        return;
+      }
+    }
+    const int N = g_.N;
+    const size_t N3 = (size_t)N * N * N;
+    const T scale = T(1.0 / g_.omega);
+    for (int b0 = 0; b0 < n; b0 += batch_) {
+      const int nb = std::min(batch_, n - b0);
+      KS_CUDA(cudaMemsetAsync(grid_, 0, (size_t)nb * N3 * sizeof(C), s));
+      scatter_sphere<T>(psi + (size_t)b0 * g_.nG, grid_, t_, nb, s);
+      for (int ax = 2; ax >= 0; --ax) fft_axis<T>(grid_, nb, N, ax, +1, t_.tw, s);
+      density_accumulate<T>(grid_, occ_ + b0, nout, (int)N3, nb, scale, b0 == 0, s);
+    }
+  }
+
+  void density(void* n_out, cudaStream_t s) override { density_of(psi_, ns_, static_cast<T*>(n_out), s); }
+
+  // V = V_loc + v_H[n] + v_x[n] (periodic Poisson in Fourier space, v_H(G=0) = 0; Slater exchange)
+  void update_potential(const T* n, cudaStream_t s) {
+    const int N = g_.N;
+    const size_t N3 = (size_t)N * N * N;
+    real_to_complex<T>(n, pwork_, (int)N3, s);
+    for (int ax = 2; ax >= 0; --ax) fft_axis<T>(pwork_, 1, N, ax, -1, t_.tw, s);
+    poisson_multiply<T>(pwork_, N, g_.L, T(1.0 / double(N3)), s);
+    for (int ax = 0; ax < 3; ++ax) fft_axis<T>(pwork_, 1, N, ax, +1, t_.tw, s);
+    hxc_combine<T>(n, pwork_, vloc_, vtot_, hxc_partials_, (int)N3, HXC_BLOCKS, s);
+    hxc_finish(hxc_partials_, HXC_BLOCKS, g_.dV, parts_, s);
+  }
+
+  // ------------------------------------------------------------------------------------------
+  // CholQR: S = Psi^H Psi, S = L L^H, Psi <- Psi L^{-H}  (rows: psi <- conj(L^{-1}) psi)
+  // ------------------------------------------------------------------------------------------
+  void cholqr(cudaStream_t s, bool keep_S) {
+    const int n = ns_, nG = g_.nG;
+    gemm_cn<T>(psi_, nG, psi_, nG, n, n, nG, part_, part_elems_, mS_, s);
+    hermitize(mS_, n, s);
+    KS_CUDA(cudaMemcpyAsync(mA_, mS_, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    cholesky_inverse_tol(mA_, mM_, n, sizeof(T) == 8 ? 1e-12 : 1e-6, status_, s);
+    C* out = spare(psi_, hpsi_);
+    rotate<T>(mM_, n, psi_, nG, out, nG, n, nG, s);
+    swap_in(psi_, out);
+    (void)keep_S;
+  }
+
+  void orthonormalize(double* S_host, cudaStream_t s) override {
+    KS_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), s));
+    cholqr(s, S_host != nullptr);
+    int st = 0;
+    KS_CUDA(cudaMemcpyAsync(&st, status_, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (S_host) KS_CUDA(cudaMemcpyAsync(S_host, mS_, (size_t)ns_ * ns_ * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    if (st) fail(KS_ERR_NOT_POSDEF, "CholQR: Gram matrix not positive definite at column %d", st - 1);
+  }
+
+  // Rayleigh-Ritz on (psi_, hpsi_): H_sub = Psi^H H Psi, eigh, rotate both.
+  void rr_core(cudaStream_t s) {
+    const int n = ns_, nG = g_.nG;
+    gemm_cn<T>(psi_, nG, hpsi_, nG, n, n, nG, part_, part_elems_, mA_, s);
+    hermitize(mA_, n, s);
+    jacobi_eigh(mA_, mV_, eig_, mM_, n, s);
+    C* o1 = spare(psi_, hpsi_);
+    rotate<T>(mM_, n, psi_, nG, o1, nG, n, nG, s);
+    swap_in(psi_, o1);
+    C* o2 = spare(psi_, hpsi_);
+    rotate<T>(mM_, n, hpsi_, nG, o2, nG, n, nG, s);
+    swap_in(hpsi_, o2);
+  }
+
+  void rayleigh_ritz(double* eig_host, cudaStream_t s) override {
+    apply_h(psi_, hpsi_, ns_, s);
+    rr_core(s);
+    if (eig_host) KS_CUDA(cudaMemcpyAsync(eig_host, eig_, ns_ * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+  }
+
+  void block_iteration(int niter, double* eig_host, cudaStream_t s) override {
+    if (niter < 0) fail(KS_ERR_ARG, "niter=%d", niter);
+    const double alpha = 1.0 / (g_.ecut + (g_.vmax - g_.vmin) + g_.D);
+    KS_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), s));
+    for (int it = 0; it < niter; ++it) {
+      cholqr(s, false);
+      apply_h(psi_, hpsi_, ns_, s);
+      rr_core(s);
+      sd_update<T>(psi_, hpsi_, eig_, alpha, g_.nG, ns_, s);
+    }
+    int st = 0;
+    KS_CUDA(cudaMemcpyAsync(&st, status_, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (eig_host) KS_CUDA(cudaMemcpyAsync(eig_host, eig_, ns_ * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    if (st) fail(KS_ERR_NOT_POSDEF, "block iteration: Gram matrix not positive definite at column %d", st - 1);
+  }
+
+  // ------------------------------------------------------------------------------------------
+  // Real-time steps: ETRS + Taylor 4 with shared powers (Eqs. 6-8), or plain Taylor 4.
+  // ------------------------------------------------------------------------------------------
+  void td_steps(double dt, int nsteps, int propagator, int hartree_xc, double* norm_out, double* energy_out,
+                cudaStream_t s) override {
+    if (nsteps < 0 || (propagator != 0 && propagator != 1)) fail(KS_ERR_ARG, "td: nsteps=%d propagator=%d", nsteps, propagator);
+    const int n = ns_, nG = g_.nG;
+    const size_t sn = (size_t)n * nG;
+    if (!hartree_xc) KS_CUDA(cudaMemcpyAsync(vtot_, vloc_, (size_t)g_.N * g_.N * g_.N * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    double first_norm = 0;
+    bool have_first = false;
+    for (int c0 = 0; c0 < nsteps; c0 += MAX_STEPS_CHUNK) {
+      const int cn = std::min(MAX_STEPS_CHUNK, nsteps - c0);
+      for (int st = 0; st < cn; ++st) {
+        // roles: psi, two power buffers, acc_full, acc_half
+        C* others[5];
+        int k = 0;
+        for (int i = 0; i < 6; ++i)
+          if (buf_[i] != psi_) others[k++] = buf_[i];
+        C* wa = others[0];
+        C* wb = others[1];
+        C* acc_full = others[2];
+        C* acc_half = others[3];
+        if (hartree_xc) {
+          density_of(psi_, n, dens_, s);
+          update_potential(dens_, s);
+        }
+        state_dots<T>(psi_, psi_, nG, n, dots_, s);
+        weighted_energy(dots_, occ_, n, nullptr, norms_dev_ + st, s);
+        KS_CUDA(cudaMemcpyAsync(acc_full, psi_, sn * sizeof(C), cudaMemcpyDeviceToDevice, s));
+        KS_CUDA(cudaMemcpyAsync(acc_half, psi_, sn * sizeof(C), cudaMemcpyDeviceToDevice, s));
+        const C* w = psi_;
+        double2 af = make_double2(1, 0), ah = make_double2(1, 0);
+        for (int kk = 1; kk <= 4; ++kk) {
+          C* wn = (w == wa) ? wb : wa;
+          apply_h(w, wn, n, s);
+          if (kk == 1) {
+            state_dots<T>(psi_, wn, nG, n, dots_, s);
+            weighted_energy(dots_, occ_, n, hartree_xc ? parts_ : nullptr, energies_dev_ + st, s);
+          }
+          af = cmul_scalar(af, make_double2(0, -dt / kk));
+          ah = cmul_scalar(ah, make_double2(0, -0.5 * dt / kk));
+          axpy2<T>(acc_full, af, propagator == 0 ? acc_half : nullptr, ah, wn, sn, s);
+          w = wn;
+        }
+        if (propagator == 1) {
+          psi_ = acc_full;
+          continue;
+        }
+        if (hartree_xc) {
+          density_of(acc_full, n, dens_, s);
+          update_potential(dens_, s);
+        }
+        // second half: out = acc_half + sum_k (-i dt/2)^k/k! H(t+dt)^k acc_half
+        KS_CUDA(cudaMemcpyAsync(acc_full, acc_half, sn * sizeof(C), cudaMemcpyDeviceToDevice, s));
+        w = acc_half;
+        ah = make_double2(1, 0);
+        for (int kk = 1; kk <= 4; ++kk) {
+          C* wn = (w == wa) ? wb : wa;
+          apply_h(w, wn, n, s);
+          ah = cmul_scalar(ah, make_double2(0, -0.5 * dt / kk));
+          axpy2<T>(acc_full, ah, nullptr, ah, wn, sn, s);
+          w = wn;
+        }
+        psi_ = acc_full;
+      }
+      std::vector<double> nh(cn), eh(cn);
+      KS_CUDA(cudaMemcpyAsync(nh.data(), norms_dev_, cn * sizeof(double), cudaMemcpyDeviceToHost, s));
+      KS_CUDA(cudaMemcpyAsync(eh.data(), energies_dev_, cn * sizeof(double), cudaMemcpyDeviceToHost, s));
+      KS_CUDA(cudaStreamSynchronize(s));
+      if (norm_out) std::memcpy(norm_out + c0, nh.data(), cn * sizeof(double));
+      if (energy_out) std::memcpy(energy_out + c0, eh.data(), cn * sizeof(double));
+      for (int i = 0; i < cn; ++i) {
+        if (!have_first) {
+          first_norm = nh[i];
+          have_first = true;
+        }
+        if (!std::isfinite(nh[i]) || !std::isfinite(eh[i]) || std::fabs(nh[i] / first_norm - 1.0) > 0.05)
+          fail(KS_ERR_DIVERGED, "real-time step %d: norm %g vs initial %g", c0 + i, nh[i], first_norm);
+      }
+    }
+    // H psi buffer role: keep hpsi_ distinct from psi_
+    if (hpsi_ == psi_) hpsi_ = spare(psi_, nullptr);
+  }
+
+ private:
+  static double2 cmul_scalar(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  }
+
+  // A state buffer that is neither a nor b.
+  C* spare(const C* a, const C* b) {
+    for (int i = 0; i < 6; ++i)
+      if (buf_[i] != a && buf_[i] != b) return buf_[i];
+    fail(KS_ERR_STATE, "internal: no spare state buffer");
+  }
+  C* spare3(const C* a, const C* b, const C* c) {
+    for (int i = 0; i < 6; ++i)
+      if (buf_[i] != a && buf_[i] != b && buf_[i] != c) return buf_[i];
+    fail(KS_ERR_STATE, "internal: no spare state buffer");
+  }
+  void swap_in(C*& role, C* fresh) { role = fresh; }
+
+  template <typename U> U* alloc(size_t n) { return static_cast<U*>(arena_.alloc(n * sizeof(U))); }
+  template <typename U> const U* upload(const std::vector<U>& v) {
+    U* p = alloc<U>(std::max<size_t>(v.size(), 1));
+    if (!v.empty()) KS_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice));
+    return p;
+  }
+  const T* upload_real(const std::vector<double>& v) {
+    std::vector<T> t(v.begin(), v.end());
+    return upload(t);
+  }
+
+  HostGeometry g_;
+  ks_precision prec_;
+  int ns_;
+  DeviceArena arena_;
+  DevTables<T> t_;
+  std::unique_ptr<FusedOps> fused_;
+  T* vloc_ = nullptr;
+  T* vtot_ = nullptr;
+  double* occ_ = nullptr;
+  C* buf_[6] = {};
+  C* psi_ = nullptr;
+  C* hpsi_ = nullptr;
+  double2* staging_ = nullptr;
+  C* grid_ = nullptr;
+  C* proj_ = nullptr;
+  int batch_ = 1;
+  double2* part_ = nullptr;
+  size_t part_elems_ = 0;
+  double2 *mS_ = nullptr, *mA_ = nullptr, *mM_ = nullptr, *mV_ = nullptr;
+  double* eig_ = nullptr;
+  int* status_ = nullptr;
+  T* dens_ = nullptr;
+  C* pwork_ = nullptr;
+  double* hxc_partials_ = nullptr;
+  double* parts_ = nullptr;
+  double2* dots_ = nullptr;
+  double* norms_dev_ = nullptr;
+  double* energies_dev_ = nullptr;
+};
+
+}  // namespace
+
+std::unique_ptr<EngineBase> make_engine(const ks_cell_desc& d) {
+  if (d.prec == KS_FP64) return std::unique_ptr<EngineBase>(new Engine<double>(d));
+  if (d.prec == KS_MIXED_BF16X3 || d.prec == KS_MIXED_TF32) return std::unique_ptr<EngineBase>(new Engine<float>(d));
+  fail(KS_ERR_ARG, "unknown precision %d", (int)d.prec);
+}
+
+}  // namespace ks

@@ -1,0 +1,36 @@
+// Fused mixed-precision (complex64) Hamiltonian path: pruned z-column FFTs, one plane
+// kernel per z-plane holding the (x, y) plane in shared memory with the potential and
+// the projector add fused between the inverse and forward transforms, and the kinetic
+// term fused into the last transform.
+#pragma once
+
+#include <memory>
+
+#include "engine.h"
+#include "kernels.h"
+
+namespace ks {
+
+class FusedOps {
+ public:
+  virtual ~FusedOps() = default;
+  // hpsi = H psi for n states with potential v (grid order).
+  virtual void apply_h(const float2* psi, float2* hpsi, int n, const float* v, cudaStream_t s) = 0;
+  // nout = sum_k occ[k] |psi_k(r)|^2 (grid order).
+  virtual void density(const float2* psi, int n, const double* occ, float* nout, cudaStream_t s) = 0;
+};
+
+std::unique_ptr<FusedOps> make_fused_ops(const HostGeometry& g, const DevTables<float>& t, int nstates,
+                                         DeviceArena& arena);
+
+template <typename T>
+inline std::unique_ptr<FusedOps> make_fused_for(const HostGeometry&, const DevTables<T>&, int, DeviceArena&) {
+  return nullptr;
+}
+template <>
+inline std::unique_ptr<FusedOps> make_fused_for<float>(const HostGeometry& g, const DevTables<float>& t, int n,
+                                                       DeviceArena& a) {
+  return make_fused_ops(g, t, n, a);
+}
+
+}  // namespace ks

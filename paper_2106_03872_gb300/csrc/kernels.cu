@@ -1,0 +1,508 @@
+// Full-grid ("plain") path kernels: batched line FFTs, sphere scatter/gather with the
+// kinetic term, potential multiply, real-space KB projectors (Eq. 9), density (Eq. 1),
+// periodic Poisson + Slater exchange, and the FP64 reductions for norms and energies.
+#include "fft_device.cuh"
+#include "kernels.h"
+
+namespace ks {
+
+namespace {
+
+constexpr int RED_THREADS = 256;
+
+// Deterministic block sum of NV doubles per thread; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double red[32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[warp][i] = v[i];
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      v[i] = (lane < nw) ? red[lane][i] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
+// Line FFTs along one axis of [nb][N][N][N] grids.
+// Lines are addressed as (outer a, inner b): element k at a*N*B + k*B + b.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(LINE_THREADS) k_fft_lines(cplx<T>* __restrict__ data, int N, long nouter, int B,
+                                                            int TB, FftPlan plan, const cplx<T>* __restrict__ twg,
+                                                            int sign) {
+  using C = cplx<T>;
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* s = tw + N;
+  const int ld = N + 1;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    const C w = twg[t];
+    tw[t] = mk<C>(w.x, sign > 0 ? w.y : -w.y);
+  }
+  int lines;
+  size_t base;
+  if (B == 1) {
+    const long a0 = (long)blockIdx.x * TB;
+    lines = (int)min((long)TB, nouter - a0);
+    base = (size_t)a0 * N;
+    for (int e = threadIdx.x; e < lines * N; e += blockDim.x) {
+      const int l = e / N, k = e - (e / N) * N;
+      s[l * ld + k] = data[base + (size_t)l * N + k];
+    }
+  } else {
+    const int ntb = (B + TB - 1) / TB;
+    const long a = blockIdx.x / ntb;
+    const int b0 = (int)(blockIdx.x - a * ntb) * TB;
+    lines = min(TB, B - b0);
+    base = (size_t)a * N * B + b0;
+    for (int e = threadIdx.x; e < lines * N; e += blockDim.x) {
+      const int k = e / lines, l = e - (e / lines) * lines;
+      s[l * ld + k] = data[base + (size_t)k * B + l];
+    }
+  }
+  __syncthreads();
+  fft_lines_smem(s, lines, ld, N, plan, tw, sign);
+  if (B == 1) {
+    for (int e = threadIdx.x; e < lines * N; e += blockDim.x) {
+      const int l = e / N, k = e - (e / N) * N;
+      data[base + (size_t)l * N + k] = s[l * ld + k];
+    }
+  } else {
+    for (int e = threadIdx.x; e < lines * N; e += blockDim.x) {
+      const int k = e / lines, l = e - (e / lines) * lines;
+      data[base + (size_t)k * B + l] = s[l * ld + k];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_scatter(const cplx<T>* __restrict__ psi, cplx<T>* __restrict__ grid, const int* __restrict__ gidx,
+                          int nG, size_t N3) {
+  const int b = blockIdx.y;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nG; g += gridDim.x * blockDim.x)
+    grid[b * N3 + gidx[g]] = psi[(size_t)b * nG + g];
+}
+
+template <typename T>
+__global__ void k_gather_kinetic(const cplx<T>* __restrict__ grid, const cplx<T>* __restrict__ psi,
+                                 cplx<T>* __restrict__ hpsi, const int* __restrict__ gidx, const T* __restrict__ g2h,
+                                 int nG, size_t N3, T scale) {
+  const int b = blockIdx.y;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nG; g += gridDim.x * blockDim.x) {
+    const cplx<T> u = grid[b * N3 + gidx[g]];
+    const cplx<T> p = psi[(size_t)b * nG + g];
+    const T k = g2h[g];
+    hpsi[(size_t)b * nG + g] = mk<cplx<T>>(u.x * scale + k * p.x, u.y * scale + k * p.y);
+  }
+}
+
+template <typename T>
+__global__ void k_multiply_potential(cplx<T>* __restrict__ grid, const T* __restrict__ v, size_t N3) {
+  const int b = blockIdx.y;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
+    const T vj = v[j];
+    cplx<T> u = grid[b * N3 + j];
+    grid[b * N3 + j] = mk<cplx<T>>(u.x * vj, u.y * vj);
+  }
+}
+
+template <typename T, int NP>
+__global__ void k_nl_project(const cplx<T>* __restrict__ grid, size_t N3, const int* __restrict__ sph_off,
+                             const int* __restrict__ sph_idx, const T* __restrict__ beta, int natoms,
+                             cplx<T>* __restrict__ proj, T scale) {
+  const int I = blockIdx.x, b = blockIdx.y;
+  double acc[2 * NP];
+#pragma unroll
+  for (int i = 0; i < 2 * NP; ++i) acc[i] = 0.0;
+  for (int p = sph_off[I] + threadIdx.x; p < sph_off[I + 1]; p += blockDim.x) {
+    const cplx<T> v = grid[b * N3 + sph_idx[p]];
+#pragma unroll
+    for (int l = 0; l < NP; ++l) {
+      const double w = (double)beta[(size_t)p * NP + l];
+      acc[2 * l] += w * (double)v.x;
+      acc[2 * l + 1] += w * (double)v.y;
+    }
+  }
+  block_sum<2 * NP>(acc);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int l = 0; l < NP; ++l)
+      proj[((size_t)b * natoms + I) * NP + l] = mk<cplx<T>>(T(acc[2 * l] * scale), T(acc[2 * l + 1] * scale));
+}
+
+template <typename T, int NP>
+__global__ void k_nl_add(cplx<T>* __restrict__ grid, size_t N3, int ncov, const int* __restrict__ cov_idx,
+                         const int* __restrict__ cov_off, const int* __restrict__ cov_ent,
+                         const int* __restrict__ sph_atom, const T* __restrict__ beta, int natoms,
+                         const cplx<T>* __restrict__ proj, T scale) {
+  const int b = blockIdx.y;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncov; c += gridDim.x * blockDim.x) {
+    T ax = 0, ay = 0;
+    for (int e = cov_off[c]; e < cov_off[c + 1]; ++e) {
+      const int p = cov_ent[e];
+      const cplx<T>* pr = proj + ((size_t)b * natoms + sph_atom[p]) * NP;
+#pragma unroll
+      for (int l = 0; l < NP; ++l) {
+        const T w = beta[(size_t)p * NP + l];
+        ax += w * pr[l].x;
+        ay += w * pr[l].y;
+      }
+    }
+    const size_t j = b * N3 + cov_idx[c];
+    cplx<T> u = grid[j];
+    grid[j] = mk<cplx<T>>(u.x + scale * ax, u.y + scale * ay);
+  }
+}
+
+template <typename T>
+__global__ void k_density_acc(const cplx<T>* __restrict__ grid, const double* __restrict__ occ, T* __restrict__ n,
+                              size_t N3, int nb, T scale, int first) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
+    T acc = 0;
+    for (int b = 0; b < nb; ++b) {
+      const cplx<T> v = grid[b * N3 + j];
+      acc += T(occ[b]) * (v.x * v.x + v.y * v.y);
+    }
+    n[j] = (first ? T(0) : n[j]) + scale * acc;
+  }
+}
+
+template <typename T>
+__global__ void k_real_to_complex(const T* __restrict__ n, cplx<T>* __restrict__ w, size_t N3) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x)
+    w[j] = mk<cplx<T>>(n[j], T(0));
+}
+
+__device__ __forceinline__ int freq_of(int j, int N) { return (2 * j < N) ? j : j - N; }
+
+template <typename T>
+__global__ void k_poisson(cplx<T>* __restrict__ w, int N, double kf2, T scale) {
+  const size_t N3 = (size_t)N * N * N;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
+    const int jx = (int)(j / ((size_t)N * N)), jy = (int)((j / N) % N), jz = (int)(j % N);
+    const int mx = freq_of(jx, N), my = freq_of(jy, N), mz = freq_of(jz, N);
+    const int m2 = mx * mx + my * my + mz * mz;
+    if (m2 == 0) {
+      w[j] = mk<cplx<T>>(T(0), T(0));
+    } else {
+      const T f = T(4.0 * M_PI / (kf2 * m2)) * scale;
+      const cplx<T> v = w[j];
+      w[j] = mk<cplx<T>>(v.x * f, v.y * f);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_hxc_combine(const T* __restrict__ n, const cplx<T>* __restrict__ w, const T* __restrict__ vloc,
+                              T* __restrict__ vtot, double* __restrict__ partials, size_t N3) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
+    const T nj = n[j];
+    const T vh = w[j].x;
+    const T nn = nj > T(0) ? nj : T(0);
+    const T vx = -cbrt(T(3.0 / M_PI) * nn);
+    vtot[j] = vloc[j] + vh + vx;
+    acc[0] += (double)nj * (double)vh;
+    acc[1] += (double)nj * 0.75 * (double)vx;
+    acc[2] += (double)nj * (double)vx;
+  }
+  block_sum<3>(acc);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 3; ++i) partials[blockIdx.x * 3 + i] = acc[i];
+}
+
+__global__ void k_hxc_finish(const double* __restrict__ partials, int nblocks, double dV, double* __restrict__ parts) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s[3] = {0, 0, 0};
+    for (int b = 0; b < nblocks; ++b)
+      for (int i = 0; i < 3; ++i) s[i] += partials[b * 3 + i];
+    parts[0] = 0.5 * dV * s[0];
+    parts[1] = dV * s[1];
+    parts[2] = dV * s[2];
+  }
+}
+
+template <typename T>
+__global__ void k_state_dots(const cplx<T>* __restrict__ a, const cplx<T>* __restrict__ bb, int nG,
+                             double2* __restrict__ dots) {
+  const int b = blockIdx.x;
+  double acc[2] = {0.0, 0.0};
+  for (int g = threadIdx.x; g < nG; g += blockDim.x) {
+    const cplx<T> x = a[(size_t)b * nG + g], y = bb[(size_t)b * nG + g];
+    acc[0] += (double)x.x * y.x + (double)x.y * y.y;
+    acc[1] += (double)x.x * y.y - (double)x.y * y.x;
+  }
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) dots[b] = make_double2(acc[0], acc[1]);
+}
+
+__global__ void k_weighted_energy(const double2* __restrict__ dots, const double* __restrict__ occ, int nb,
+                                  const double* __restrict__ parts, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double e = 0;
+    for (int b = 0; b < nb; ++b) e += occ[b] * dots[b].x;
+    if (parts) e += -parts[0] + parts[1] - parts[2];
+    out[0] = e;
+  }
+}
+
+template <typename T>
+__global__ void k_axpy2(cplx<T>* __restrict__ acc1, double2 a1, cplx<T>* __restrict__ acc2, double2 a2,
+                        const cplx<T>* __restrict__ w, size_t n) {
+  const T a1x = T(a1.x), a1y = T(a1.y), a2x = T(a2.x), a2y = T(a2.y);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const cplx<T> v = w[i];
+    cplx<T> p = acc1[i];
+    p.x += a1x * v.x - a1y * v.y;
+    p.y += a1x * v.y + a1y * v.x;
+    acc1[i] = p;
+    if (acc2) {
+      cplx<T> q = acc2[i];
+      q.x += a2x * v.x - a2y * v.y;
+      q.y += a2x * v.y + a2y * v.x;
+      acc2[i] = q;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_sd_update(cplx<T>* __restrict__ psi, const cplx<T>* __restrict__ hpsi, const double* __restrict__ eps,
+                            double alpha, int nG) {
+  const int b = blockIdx.y;
+  const T e = T(eps[b]), a = T(alpha);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nG; g += gridDim.x * blockDim.x) {
+    const size_t i = (size_t)b * nG + g;
+    const cplx<T> p = psi[i], h = hpsi[i];
+    psi[i] = mk<cplx<T>>(p.x - a * (h.x - e * p.x), p.y - a * (h.y - e * p.y));
+  }
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014), used as a counter-based hash.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+template <typename T>
+__global__ void k_random_states(cplx<T>* __restrict__ psi, size_t n, uint64_t seed) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t a = splitmix64(seed ^ (2 * i)), b = splitmix64(seed ^ (2 * i + 1));
+    const double u = (double)(a >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    const double v = (double)(b >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    psi[i] = mk<cplx<T>>(T(u), T(v));
+  }
+}
+
+template <typename T>
+__global__ void k_from_c128(const double2* __restrict__ in, cplx<T>* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = mk<cplx<T>>(T(in[i].x), T(in[i].y));
+}
+template <typename T>
+__global__ void k_to_c128(const cplx<T>* __restrict__ in, double2* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = make_double2((double)in[i].x, (double)in[i].y);
+}
+template <typename T>
+__global__ void k_real_to_double(const T* __restrict__ in, double* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+inline unsigned blocks_for(size_t n, int threads, unsigned cap = 152u * 16u) {
+  size_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (unsigned)(b < cap ? b : cap);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// Launchers
+// ------------------------------------------------------------------------------------------
+template <typename T>
+void fft_axis(cplx<T>* grid, int nb, int N, int axis, int sign, const cplx<T>* tw, cudaStream_t s) {
+  const FftPlan plan = make_plan(N);
+  long nouter;
+  int B;
+  if (axis == 2) {
+    nouter = (long)nb * N * N;
+    B = 1;
+  } else if (axis == 1) {
+    nouter = (long)nb * N;
+    B = N;
+  } else {
+    nouter = nb;
+    B = N * N;
+  }
+  int TB = LINE_ELEMS / N;
+  if (B > 1 && TB > B) TB = B;
+  long nblocks = (B == 1) ? (nouter + TB - 1) / TB : nouter * ((B + TB - 1) / TB);
+  const size_t smem = (size_t)(N + TB * (N + 1)) * sizeof(cplx<T>);
+  k_fft_lines<T><<<(unsigned)nblocks, LINE_THREADS, smem, s>>>(grid, N, nouter, B, TB, plan, tw, sign);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void scatter_sphere(const cplx<T>* psi, cplx<T>* grid, const DevTables<T>& t, int nb, cudaStream_t s) {
+  dim3 g(blocks_for(t.nG, 256, 1024), nb);
+  k_scatter<T><<<g, 256, 0, s>>>(psi, grid, t.gidx, t.nG, (size_t)t.N * t.N * t.N);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void gather_kinetic(const cplx<T>* grid, const cplx<T>* psi, cplx<T>* hpsi, const DevTables<T>& t, int nb, T scale,
+                    cudaStream_t s) {
+  dim3 g(blocks_for(t.nG, 256, 1024), nb);
+  k_gather_kinetic<T><<<g, 256, 0, s>>>(grid, psi, hpsi, t.gidx, t.g2half, t.nG, (size_t)t.N * t.N * t.N, scale);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void multiply_potential(cplx<T>* grid, const T* v, int N3, int nb, cudaStream_t s) {
+  dim3 g(blocks_for(N3, 256, 2048), nb);
+  k_multiply_potential<T><<<g, 256, 0, s>>>(grid, v, (size_t)N3);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void nl_project(const cplx<T>* grid, const DevTables<T>& t, cplx<T>* proj, int nb, T scale, cudaStream_t s) {
+  if (t.natoms == 0) return;
+  dim3 g(t.natoms, nb);
+  const size_t N3 = (size_t)t.N * t.N * t.N;
+  if (t.nproj == 4)
+    k_nl_project<T, 4><<<g, RED_THREADS, 0, s>>>(grid, N3, t.sph_off, t.sph_idx, t.sph_beta, t.natoms, proj, scale);
+  else
+    k_nl_project<T, 1><<<g, RED_THREADS, 0, s>>>(grid, N3, t.sph_off, t.sph_idx, t.sph_beta, t.natoms, proj, scale);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void nl_add(cplx<T>* grid, const DevTables<T>& t, const cplx<T>* proj, int nb, T scale, cudaStream_t s) {
+  if (t.natoms == 0 || t.ncov == 0) return;
+  dim3 g(blocks_for(t.ncov, 256, 1024), nb);
+  const size_t N3 = (size_t)t.N * t.N * t.N;
+  if (t.nproj == 4)
+    k_nl_add<T, 4><<<g, 256, 0, s>>>(grid, N3, t.ncov, t.cov_idx, t.cov_off, t.cov_ent, t.sph_atom, t.sph_beta,
+                                     t.natoms, proj, scale);
+  else
+    k_nl_add<T, 1><<<g, 256, 0, s>>>(grid, N3, t.ncov, t.cov_idx, t.cov_off, t.cov_ent, t.sph_atom, t.sph_beta,
+                                     t.natoms, proj, scale);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void density_accumulate(const cplx<T>* grid, const double* occ, T* n, int N3, int nb, T scale, bool first,
+                        cudaStream_t s) {
+  k_density_acc<T><<<blocks_for(N3, 256, 4096), 256, 0, s>>>(grid, occ, n, (size_t)N3, nb, scale, first ? 1 : 0);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void real_to_complex(const T* n, cplx<T>* work, int N3, cudaStream_t s) {
+  k_real_to_complex<T><<<blocks_for(N3, 256, 4096), 256, 0, s>>>(n, work, (size_t)N3);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void poisson_multiply(cplx<T>* work, int N, double L, T scale, cudaStream_t s) {
+  const double kf = 2.0 * M_PI / L;
+  k_poisson<T><<<blocks_for((size_t)N * N * N, 256, 4096), 256, 0, s>>>(work, N, kf * kf, scale);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void hxc_combine(const T* n, const cplx<T>* work, const T* vloc, T* vtot, double* partials, int N3, int nblocks,
+                 cudaStream_t s) {
+  k_hxc_combine<T><<<nblocks, RED_THREADS, 0, s>>>(n, work, vloc, vtot, partials, (size_t)N3);
+  KS_CHECK_LAUNCH();
+}
+
+void hxc_finish(const double* partials, int nblocks, double dV, double* parts, cudaStream_t s) {
+  k_hxc_finish<<<1, 32, 0, s>>>(partials, nblocks, dV, parts);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void state_dots(const cplx<T>* a, const cplx<T>* b, int nG, int nb, double2* dots, cudaStream_t s) {
+  k_state_dots<T><<<nb, RED_THREADS, 0, s>>>(a, b, nG, dots);
+  KS_CHECK_LAUNCH();
+}
+
+void weighted_energy(const double2* dots, const double* occ, int nb, const double* parts, double* out, cudaStream_t s) {
+  k_weighted_energy<<<1, 32, 0, s>>>(dots, occ, nb, parts, out);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void axpy2(cplx<T>* acc1, double2 a1, cplx<T>* acc2, double2 a2, const cplx<T>* w, size_t n, cudaStream_t s) {
+  k_axpy2<T><<<blocks_for(n, 256, 152 * 32), 256, 0, s>>>(acc1, a1, acc2, a2, w, n);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void sd_update(cplx<T>* psi, const cplx<T>* hpsi, const double* eps, double alpha, int nG, int nb, cudaStream_t s) {
+  dim3 g(blocks_for(nG, 256, 512), nb);
+  k_sd_update<T><<<g, 256, 0, s>>>(psi, hpsi, eps, alpha, nG);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void random_states(cplx<T>* psi, size_t n, uint64_t seed, cudaStream_t s) {
+  k_random_states<T><<<blocks_for(n, 256), 256, 0, s>>>(psi, n, seed);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void from_c128(const double2* in, cplx<T>* out, size_t n, cudaStream_t s) {
+  k_from_c128<T><<<blocks_for(n, 256), 256, 0, s>>>(in, out, n);
+  KS_CHECK_LAUNCH();
+}
+template <typename T>
+void to_c128(const cplx<T>* in, double2* out, size_t n, cudaStream_t s) {
+  k_to_c128<T><<<blocks_for(n, 256), 256, 0, s>>>(in, out, n);
+  KS_CHECK_LAUNCH();
+}
+template <typename T>
+void real_to_double(const T* in, double* out, size_t n, cudaStream_t s) {
+  k_real_to_double<T><<<blocks_for(n, 256), 256, 0, s>>>(in, out, n);
+  KS_CHECK_LAUNCH();
+}
+
+#define KS_INSTANTIATE(T)                                                                                       \
+  template void fft_axis<T>(cplx<T>*, int, int, int, int, const cplx<T>*, cudaStream_t);                        \
+  template void scatter_sphere<T>(const cplx<T>*, cplx<T>*, const DevTables<T>&, int, cudaStream_t);            \
+  template void gather_kinetic<T>(const cplx<T>*, const cplx<T>*, cplx<T>*, const DevTables<T>&, int, T,        \
+                                  cudaStream_t);                                                                \
+  template void multiply_potential<T>(cplx<T>*, const T*, int, int, cudaStream_t);                              \
+  template void nl_project<T>(const cplx<T>*, const DevTables<T>&, cplx<T>*, int, T, cudaStream_t);             \
+  template void nl_add<T>(cplx<T>*, const DevTables<T>&, const cplx<T>*, int, T, cudaStream_t);                 \
+  template void density_accumulate<T>(const cplx<T>*, const double*, T*, int, int, T, bool, cudaStream_t);      \
+  template void real_to_complex<T>(const T*, cplx<T>*, int, cudaStream_t);                                      \
+  template void poisson_multiply<T>(cplx<T>*, int, double, T, cudaStream_t);                                    \
+  template void hxc_combine<T>(const T*, const cplx<T>*, const T*, T*, double*, int, int, cudaStream_t);        \
+  template void state_dots<T>(const cplx<T>*, const cplx<T>*, int, int, double2*, cudaStream_t);                \
+  template void axpy2<T>(cplx<T>*, double2, cplx<T>*, double2, const cplx<T>*, size_t, cudaStream_t);           \
+  template void sd_update<T>(cplx<T>*, const cplx<T>*, const double*, double, int, int, cudaStream_t);          \
+  template void random_states<T>(cplx<T>*, size_t, uint64_t, cudaStream_t);                                     \
+  template void from_c128<T>(const double2*, cplx<T>*, size_t, cudaStream_t);                                   \
+  template void to_c128<T>(const cplx<T>*, double2*, size_t, cudaStream_t);                                     \
+  template void real_to_double<T>(const T*, double*, size_t, cudaStream_t);
+
+KS_INSTANTIATE(float)
+KS_INSTANTIATE(double)
+
+}  // namespace ks

@@ -1,0 +1,95 @@
+// Launchers of the CUDA kernels (one per kernel), templated on the real type T
+// (float: mixed path, double: FP64 path).  All launches are asynchronous on `s`.
+#pragma once
+
+#include "common.h"
+
+namespace ks {
+
+// Raw device views of one cell's tables.
+template <typename T> struct DevTables {
+  int N = 0, nG = 0, ncols = 0, natoms = 0, nproj = 0, ncov = 0, xr = 0;
+  double L = 0, omega = 0, dV = 0, D = 0;
+  const int* gidx = nullptr;          // [nG]
+  const T* g2half = nullptr;          // [nG]
+  const cplx<T>* tw = nullptr;        // [N] exp(+2 pi i t/N)
+  const int* col_xy = nullptr;        // [ncols]
+  const int* col_off = nullptr;       // [ncols]
+  const int* col_half = nullptr;      // [ncols]
+  const int* sph_off = nullptr;       // [natoms+1]
+  const int* sph_idx = nullptr;       // [npts]
+  const int* sph_atom = nullptr;      // [npts]
+  const T* sph_beta = nullptr;        // [npts][nproj]
+  const int* cov_idx = nullptr;       // [ncov]
+  const int* cov_off = nullptr;       // [ncov+1]
+  const int* cov_ent = nullptr;       // [nent]
+};
+
+// ---- full-grid (plain) path --------------------------------------------------------------------
+// In-place batched 1D FFTs along one axis (0: x, 1: y, 2: z) of nb grids [N][N][N].
+template <typename T> void fft_axis(cplx<T>* grid, int nb, int N, int axis, int sign, const cplx<T>* tw, cudaStream_t s);
+// grid[b][gidx[g]] = psi[b][g] (grid must be zeroed before).
+template <typename T> void scatter_sphere(const cplx<T>* psi, cplx<T>* grid, const DevTables<T>& t, int nb, cudaStream_t s);
+// hpsi[b][g] = scale * grid[b][gidx[g]] + g2half[g] * psi[b][g]
+template <typename T> void gather_kinetic(const cplx<T>* grid, const cplx<T>* psi, cplx<T>* hpsi, const DevTables<T>& t,
+                                          int nb, T scale, cudaStream_t s);
+// grid[b][j] *= v[j]
+template <typename T> void multiply_potential(cplx<T>* grid, const T* v, int N3, int nb, cudaStream_t s);
+// proj[b][I][l] = scale * sum_{j in sphere I} beta_Il(j) grid[b][j]
+template <typename T> void nl_project(const cplx<T>* grid, const DevTables<T>& t, cplx<T>* proj, int nb, T scale, cudaStream_t s);
+// grid[b][j] += scale * sum_{(I,l) covering j} beta_Il(j) proj[b][I][l]
+template <typename T> void nl_add(cplx<T>* grid, const DevTables<T>& t, const cplx<T>* proj, int nb, T scale, cudaStream_t s);
+// n[j] (+)= scale * sum_b occ[b] |grid[b][j]|^2 (states in order; first batch overwrites)
+template <typename T> void density_accumulate(const cplx<T>* grid, const double* occ, T* n, int N3, int nb, T scale,
+                                              bool first, cudaStream_t s);
+
+// ---- potentials and reductions --------------------------------------------------------------
+// work[j] = n[j] (complex)
+template <typename T> void real_to_complex(const T* n, cplx<T>* work, int N3, cudaStream_t s);
+// work(G) *= 4 pi / |G|^2 * scale, 0 at G = 0 (full-grid FFT order)
+template <typename T> void poisson_multiply(cplx<T>* work, int N, double L, T scale, cudaStream_t s);
+// vtot = vloc + Re(work) + v_x(n); partials[blk][3] of (n v_H, n eps_x, n v_x) sums
+template <typename T> void hxc_combine(const T* n, const cplx<T>* work, const T* vloc, T* vtot, double* partials,
+                                       int N3, int nblocks, cudaStream_t s);
+// parts[0..2] = dV * (0.5 sum n vH, sum n eps_x, sum n v_x) from the partials
+void hxc_finish(const double* partials, int nblocks, double dV, double* parts, cudaStream_t s);
+constexpr int HXC_BLOCKS = 296;
+
+// dots[b] = sum_g conj(a[b][g]) b[b][g] (FP64 accumulation, fixed order)
+template <typename T> void state_dots(const cplx<T>* a, const cplx<T>* b, int nG, int nb, double2* dots, cudaStream_t s);
+// out[0] = sum_b occ[b] Re(dots[b]) - parts[0] + parts[1] - parts[2]   (parts may be NULL)
+void weighted_energy(const double2* dots, const double* occ, int nb, const double* parts, double* out, cudaStream_t s);
+
+// acc1 += a1 * w; acc2 += a2 * w  (complex constants)
+template <typename T> void axpy2(cplx<T>* acc1, double2 a1, cplx<T>* acc2, double2 a2, const cplx<T>* w, size_t n,
+                                 cudaStream_t s);
+// psi[b][g] -= alpha * (hpsi[b][g] - eps[b] psi[b][g])
+template <typename T> void sd_update(cplx<T>* psi, const cplx<T>* hpsi, const double* eps, double alpha, int nG, int nb,
+                                     cudaStream_t s);
+// psi[b][g] = seeded uniform(-0.5, 0.5) + i uniform(-0.5, 0.5)
+template <typename T> void random_states(cplx<T>* psi, size_t n, uint64_t seed, cudaStream_t s);
+// complex128 <-> internal precision
+template <typename T> void from_c128(const double2* in, cplx<T>* out, size_t n, cudaStream_t s);
+template <typename T> void to_c128(const cplx<T>* in, double2* out, size_t n, cudaStream_t s);
+template <typename T> void real_to_double(const T* in, double* out, size_t n, cudaStream_t s);
+
+// ---- dense linear algebra (dense.cu) ----------------------------------------------------------
+// out[i][j] = sum_k conj(A[i][k]) B[j][k] for i < m, j < n (row-major, FP64 out); split-K with
+// deterministic reduction through `part` (>= gemm_cn_parts(...) double2 elements).
+template <typename T> void gemm_cn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m, int n, int K,
+                                   double2* part, size_t part_elems, double2* out, cudaStream_t s);
+// Y[i][k] = sum_j M[i][j] X[j][k], i < m, j < nin, k < K; Y must not overlap X.
+template <typename T> void rotate(const double2* M, int nin, const cplx<T>* X, int ldx, cplx<T>* Y, int ldy, int m, int K,
+                                  cudaStream_t s);
+// A := (A + A^H)/2
+void hermitize(double2* A, int n, cudaStream_t s);
+// Cholesky S = L L^H of A (in place, lower) then M = conj(L^{-1}); on failure status = 1 and
+// M = I.  FP64, one CTA.
+void cholesky_inverse(double2* A, double2* M, int n, int* status, cudaStream_t s);
+// Same with an explicit relative pivot tolerance (pivot <= tol * S_jj fails).
+void cholesky_inverse_tol(double2* A, double2* M, int n, double tol, int* status, cudaStream_t s);
+// Hermitian eigen-decomposition of A (destroyed) by cyclic Jacobi; eig ascending, rows of
+// Vt = eigenvectors (largest-magnitude component real positive).  `V` is n*n workspace.
+void jacobi_eigh(double2* A, double2* V, double* eig, double2* Vt, int n, cudaStream_t s);
+
+}  // namespace ks

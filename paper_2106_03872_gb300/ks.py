@@ -1,0 +1,229 @@
+"""Thin ctypes binding of the C ABI in include/ks.h (argument marshalling only).
+
+Every compute step runs in the CUDA library ``libks_gb300.so``; loading fails loudly if
+it has not been built (``python -c "import __graft_entry__ as g; g.build()"``).  There is
+no CPU fallback.  The functions keep the C names; ``Grid`` is a small convenience wrapper
+that owns a handle and marshals numpy arrays and torch device tensors.
+"""
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libks_gb300.so")
+
+KS_OK, KS_ERR_ARG, KS_ERR_NOMEM, KS_ERR_NOT_POSDEF, KS_ERR_DIVERGED, KS_ERR_TIMEOUT, KS_ERR_CUDA, KS_PENDING, \
+    KS_ERR_STATE = range(9)
+STATUS_NAMES = ["KS_OK", "KS_ERR_ARG", "KS_ERR_NOMEM", "KS_ERR_NOT_POSDEF", "KS_ERR_DIVERGED", "KS_ERR_TIMEOUT",
+                "KS_ERR_CUDA", "KS_PENDING", "KS_ERR_STATE"]
+KS_FP64, KS_MIXED_BF16X3, KS_MIXED_TF32 = 0, 1, 2
+PRECISIONS = {"fp64": KS_FP64, "bf16x3": KS_MIXED_BF16X3, "tf32": KS_MIXED_TF32}
+
+# Every symbol declared in include/ks.h.
+EXPORTS = ["ks_count_gvectors", "ks_grid_create", "ks_grid_destroy", "ks_grid_gvectors", "ks_grid_device_bytes",
+           "ks_get_vloc", "ks_set_states", "ks_get_states", "ks_states_device", "ks_apply_h", "ks_apply_h_host",
+           "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_td_step",
+           "ks_serve_create", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info",
+           "ks_last_error"]
+
+
+class KsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status, msg))
+        self.status = status
+
+
+class CellDesc(ct.Structure):
+    _fields_ = [("L", ct.c_double), ("N", ct.c_int), ("ecut", ct.c_double), ("natoms", ct.c_int),
+                ("pos", ct.POINTER(ct.c_double)), ("vloc_depth", ct.c_double), ("vloc_width", ct.c_double),
+                ("nproj", ct.c_int), ("proj_sigma", ct.c_double), ("proj_rc", ct.c_double),
+                ("proj_D", ct.c_double), ("nstates", ct.c_int), ("occ", ct.POINTER(ct.c_double)),
+                ("prec", ct.c_int)]
+
+
+_lib = None
+
+
+def load():
+    """Load the built library (raises if missing: the product path has no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("CUDA library %s is not built; run paper_2106_03872_gb300.build.build()" % LIB_PATH)
+    lib = ct.CDLL(LIB_PATH)
+    P = ct.c_void_p
+    dp = ct.POINTER(ct.c_double)
+    ip = ct.POINTER(ct.c_int)
+    sig = {
+        "ks_count_gvectors": [ct.c_double, ct.c_int, ct.c_double, ip],
+        "ks_grid_create": [ct.POINTER(CellDesc), ct.POINTER(P)],
+        "ks_grid_destroy": [P],
+        "ks_grid_gvectors": [P, ip, ip],
+        "ks_grid_device_bytes": [P, ct.POINTER(ct.c_size_t)],
+        "ks_get_vloc": [P, dp],
+        "ks_set_states": [P, dp],
+        "ks_get_states": [P, dp],
+        "ks_states_device": [P, ct.POINTER(P)],
+        "ks_apply_h": [P, P, P, ct.c_int, P],
+        "ks_apply_h_host": [P, dp, dp, ct.c_int],
+        "ks_density": [P, P, P],
+        "ks_orthonormalize": [P, dp, P],
+        "ks_rayleigh_ritz": [P, dp, P],
+        "ks_block_iteration": [P, ct.c_int, dp, P],
+        "ks_td_step": [P, ct.c_double, ct.c_int, ct.c_int, ct.c_int, dp, dp, P],
+        "ks_serve_create": [ct.c_size_t, ct.POINTER(P)],
+        "ks_serve_destroy": [P],
+        "ks_serve_submit": [P, ct.POINTER(CellDesc), dp, ct.c_int, ct.c_int, ct.c_double,
+                            ct.POINTER(ct.c_uint64)],
+        "ks_serve_poll": [P, ct.c_uint64, ct.c_int, dp, dp, dp],
+        "ks_serve_result_info": [P, ct.c_uint64, ip, ip, ip],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ct.c_int
+    lib.ks_last_error.argtypes = []
+    lib.ks_last_error.restype = ct.c_char_p
+    _lib = lib
+    return lib
+
+
+def check(status):
+    if status != KS_OK:
+        raise KsError(status, load().ks_last_error().decode())
+    return status
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_double)) if a is not None else None
+
+
+def make_desc(cell, prec="bf16x3", nstates=None, occ=None):
+    """CellDesc from an input dict (see inputs.py); keeps the arrays alive on the struct."""
+    pos = np.ascontiguousarray(np.asarray(cell["pos"], float).reshape(-1, 3))
+    d = CellDesc()
+    d.L, d.N, d.ecut = float(cell["L"]), int(cell["N"]), float(cell["ecut"])
+    d.natoms = len(pos)
+    d.pos = _dptr(pos)
+    d.vloc_depth, d.vloc_width = float(cell["vloc_depth"]), float(cell["vloc_width"])
+    d.nproj = int(cell["nproj"])
+    d.proj_sigma, d.proj_rc, d.proj_D = float(cell["proj_sigma"]), float(cell["proj_rc"]), float(cell["proj_D"])
+    d.nstates = int(nstates if nstates is not None else cell["nstates"])
+    occ = cell.get("occ") if occ is None else occ
+    occ_arr = None if occ is None else np.ascontiguousarray(np.asarray(occ, float))
+    d.occ = _dptr(occ_arr)
+    d.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    d._keep = (pos, occ_arr)
+    return d
+
+
+def count_gvectors(L, N, ecut):
+    n = ct.c_int()
+    check(load().ks_count_gvectors(L, N, ecut, ct.byref(n)))
+    return n.value
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ct.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Grid:
+    """Owns a ks_grid handle."""
+
+    def __init__(self, cell, prec="bf16x3", nstates=None, occ=None):
+        lib = load()
+        self.desc = make_desc(cell, prec, nstates, occ)
+        self.h = ct.c_void_p()
+        check(lib.ks_grid_create(ct.byref(self.desc), ct.byref(self.h)))
+        self.nstates = self.desc.nstates
+        self.N = self.desc.N
+        self.prec = self.desc.prec
+        n = ct.c_int()
+        check(lib.ks_grid_gvectors(self.h, ct.byref(n), None))
+        self.nG = n.value
+
+    def close(self):
+        if self.h:
+            check(load().ks_grid_destroy(self.h))
+            self.h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- host-side queries
+    def gvectors(self):
+        m = np.zeros((self.nG, 3), dtype=np.int32)
+        n = ct.c_int()
+        check(load().ks_grid_gvectors(self.h, ct.byref(n), m.ctypes.data_as(ct.POINTER(ct.c_int))))
+        return m
+
+    def device_bytes(self):
+        b = ct.c_size_t()
+        check(load().ks_grid_device_bytes(self.h, ct.byref(b)))
+        return b.value
+
+    def vloc(self):
+        v = np.zeros(self.N ** 3)
+        check(load().ks_get_vloc(self.h, _dptr(v)))
+        return v.reshape(self.N, self.N, self.N)
+
+    # --- states
+    def set_states(self, c):
+        c = np.ascontiguousarray(np.asarray(c, np.complex128).reshape(self.nstates, self.nG))
+        check(load().ks_set_states(self.h, c.ctypes.data_as(ct.POINTER(ct.c_double))))
+
+    def get_states(self):
+        c = np.zeros((self.nstates, self.nG), np.complex128)
+        check(load().ks_get_states(self.h, c.ctypes.data_as(ct.POINTER(ct.c_double))))
+        return c
+
+    def states_device_ptr(self):
+        p = ct.c_void_p()
+        check(load().ks_states_device(self.h, ct.byref(p)))
+        return p.value
+
+    # --- operations
+    def apply_h(self, psi_ptr, hpsi_ptr, nstates, stream=None):
+        check(load().ks_apply_h(self.h, ct.c_void_p(psi_ptr), ct.c_void_p(hpsi_ptr), int(nstates),
+                                _stream_ptr(stream)))
+
+    def apply_h_host(self, c):
+        c = np.ascontiguousarray(np.asarray(c, np.complex128))
+        out = np.zeros_like(c)
+        check(load().ks_apply_h_host(self.h, c.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                     out.ctypes.data_as(ct.POINTER(ct.c_double)), c.shape[0]))
+        return out
+
+    def density(self, n_ptr, stream=None):
+        check(load().ks_density(self.h, ct.c_void_p(n_ptr), _stream_ptr(stream)))
+
+    def orthonormalize(self, want_S=False, stream=None):
+        S = np.zeros((self.nstates, self.nstates), np.complex128) if want_S else None
+        check(load().ks_orthonormalize(self.h, S.ctypes.data_as(ct.POINTER(ct.c_double)) if want_S else None,
+                                       _stream_ptr(stream)))
+        return S
+
+    def rayleigh_ritz(self, stream=None):
+        e = np.zeros(self.nstates)
+        check(load().ks_rayleigh_ritz(self.h, _dptr(e), _stream_ptr(stream)))
+        return e
+
+    def block_iteration(self, niter, stream=None):
+        e = np.zeros(self.nstates)
+        check(load().ks_block_iteration(self.h, int(niter), _dptr(e), _stream_ptr(stream)))
+        return e
+
+    def td_step(self, dt, nsteps, propagator="etrs", hartree_xc=True, stream=None):
+        norms = np.zeros(nsteps)
+        energies = np.zeros(nsteps)
+        prop = {"etrs": 0, "taylor": 1}[propagator] if isinstance(propagator, str) else int(propagator)
+        check(load().ks_td_step(self.h, float(dt), int(nsteps), prop, 1 if hartree_xc else 0, _dptr(norms),
+                                _dptr(energies), _stream_ptr(stream)))
+        return norms, energies

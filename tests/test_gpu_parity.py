@@ -1,0 +1,240 @@
+"""GPU parity: every C-ABI operation against the FP64 oracle on the same seeded inputs.
+
+Tolerances: FP64 path 1e-12 relative; FP32 (mixed) H psi 2e-5 relative L2 per block.
+Other mixed-path tolerances are derived from FP32 rounding (unit roundoff 6e-8, grown by
+the FFT depth and the reductions) and stated beside each check.
+"""
+import numpy as np
+import pytest
+
+from oracle import ks_oracle as ko
+from paper_2106_03872_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ks():
+    from paper_2106_03872_gb300 import ks as mod
+    mod.load()
+    assert torch.cuda.is_available()
+    return mod
+
+
+TOL_H = {"fp64": 1e-12, "bf16x3": 2e-5, "tf32": 2e-5}
+CDT = {"fp64": torch.complex128, "bf16x3": torch.complex64, "tf32": torch.complex64}
+
+
+_CELLS = {}
+
+
+def oracle_cell(name):
+    if name not in _CELLS:
+        cell = inputs.cell(name)
+        _CELLS[name] = (cell, ko.Cell(cell))
+    return _CELLS[name]
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def apply_dev(ks, g, c, prec):
+    psi = torch.from_numpy(c).to("cuda", CDT[prec])
+    h = torch.empty_like(psi)
+    g.apply_h(psi.data_ptr(), h.data_ptr(), c.shape[0])
+    torch.cuda.synchronize()
+    return h.cpu().numpy().astype(np.complex128)
+
+
+CASES = [
+    # (L, N, natoms, nstates, nproj, seed)
+    (10.0, 24, 4, 8, 4, 1),
+    (10.0, 24, 0, 1, 4, 2),          # free electrons, one state
+    (12.0, 32, 3, 5, 1, 3),          # s projectors only
+    (15.0, 48, 6, 17, 4, 4),         # ragged state count
+    (9.0, 36, 2, 3, 4, 5),           # radix-3 grid (36 = 4*9)
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("case", CASES)
+def test_apply_h_parity(ks, prec, case):
+    L, N, na, ns, nproj, seed = case
+    cell = inputs.small_cell(L, N, na, ns, seed, nproj=nproj)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec=prec)
+    assert g.nG == ref.nG
+    assert np.array_equal(g.gvectors(), ref.m)
+    assert np.max(np.abs(g.vloc() - ref.vloc)) <= 1e-13 * max(1.0, np.max(np.abs(ref.vloc)))
+    c = inputs.random_coeffs(seed, ns, ref.nG)
+    expect = ko.apply_h(ref, c)
+    got = apply_dev(ks, g, c, prec)
+    for k in range(ns):
+        assert rel(got[k], expect[k]) <= TOL_H[prec], (k, rel(got[k], expect[k]))
+    # the host entry point gives the same numbers
+    got_h = g.apply_h_host(c)
+    assert rel(got_h, expect) <= TOL_H[prec]
+    # fewer states than the handle holds
+    if ns > 2:
+        part = apply_dev(ks, g, c[:2].copy(), prec)
+        assert rel(part, expect[:2]) <= TOL_H[prec]
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_apply_h_full_size_sampled(ks, prec):
+    """96^3 grid, 128 states, 64 atoms: all states on the GPU, 3 sampled states by the oracle."""
+    cell, ref = oracle_cell("gs96")
+    g = ks.Grid(cell, prec=prec)
+    c = inputs.random_coeffs(cell["seed"], cell["nstates"], ref.nG)
+    got = apply_dev(ks, g, c, prec)
+    for k in (0, 63, 127):
+        e = ko.apply_h(ref, c[k:k + 1])[0]
+        assert rel(got[k], e) <= TOL_H[prec], (k, rel(got[k], e))
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_density_parity(ks, prec):
+    cell = inputs.small_cell(12.0, 32, 3, 6, 7)
+    occ = np.array([2.0, 2.0, 1.0, 0.5, 0.0, 1.0])
+    ref = ko.Cell(dict(cell, occ=occ))
+    g = ks.Grid(cell, prec=prec, occ=occ)
+    c = inputs.random_coeffs(7, 6, ref.nG)
+    g.set_states(c)
+    n = torch.empty(32 ** 3, dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+    g.density(n.data_ptr())
+    torch.cuda.synchronize()
+    expect = ko.density(ref, c, occ).reshape(-1)
+    # FP32: |psi|^2 from an FP32 FFT, relative error ~ 2 * 7 stages * 6e-8 -> 1e-6 L2; bound 1e-5
+    assert rel(n.cpu().numpy().astype(float), expect) <= (1e-12 if prec == "fp64" else 1e-5)
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_orthonormalize_parity(ks, prec):
+    cell = inputs.small_cell(10.0, 24, 4, 9, 8)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec=prec)
+    c = inputs.random_coeffs(8, 9, ref.nG)
+    g.set_states(c)
+    S = g.orthonormalize(want_S=True)
+    q_ref, S_ref = ko.cholqr(c)
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    assert np.max(np.abs(S - S_ref)) <= tol * np.max(np.abs(S_ref))
+    q = g.get_states()
+    assert rel(q, q_ref) <= tol
+    assert np.max(np.abs(ko.gram(q) - np.eye(9))) <= (1e-12 if prec == "fp64" else 1e-5)
+    g.close()
+
+
+def test_orthonormalize_rejects_dependent_states(ks):
+    cell = inputs.small_cell(10.0, 24, 2, 4, 9)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec="fp64")
+    c = inputs.random_coeffs(9, 4, ref.nG)
+    c[2] = c[1]
+    g.set_states(c)
+    with pytest.raises(ks.KsError) as e:
+        g.orthonormalize()
+    assert e.value.status == ks.KS_ERR_NOT_POSDEF
+    assert rel(g.get_states(), c) <= 1e-15          # unchanged
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_rayleigh_ritz_parity(ks, prec):
+    cell = inputs.small_cell(10.0, 24, 4, 12, 10)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec=prec)
+    q, _ = ko.cholqr(inputs.random_coeffs(10, 12, ref.nG))
+    g.set_states(q)
+    eps = g.rayleigh_ritz()
+    eps_ref, U, c_ref, _ = ko.rayleigh_ritz(q, ko.apply_h(ref, q))
+    # FP32: H_sub entries carry ~1e-6 relative error of ||H|| <= 25 Ha -> 2.5e-5 Ha bound
+    assert np.max(np.abs(eps - eps_ref)) <= (1e-11 if prec == "fp64" else 2.5e-5)
+    # rotated states equal up to the phase convention: compare |<ref_i|got_i>|
+    got = g.get_states()
+    ov = np.abs(np.sum(np.conj(c_ref) * got, axis=1))
+    gaps = np.min(np.abs(eps_ref[:, None] - eps_ref[None, :]) + np.eye(12) * 1e9, axis=1)
+    well = gaps > 1e-3
+    assert np.all(np.abs(ov[well] - 1) <= (1e-10 if prec == "fp64" else 1e-3))
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_block_iteration_parity(ks, prec):
+    cell = inputs.small_cell(12.0, 32, 4, 10, 11, depth=-3.0)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec=prec)
+    c = inputs.random_coeffs(11, 10, ref.nG)
+    g.set_states(c)
+    eps = g.block_iteration(8)
+    eps_ref, c_ref = ko.block_iteration(ref, c, 8)
+    if prec == "fp64":
+        assert np.max(np.abs(eps - eps_ref)) <= 1e-10
+    else:
+        # refinement: Rayleigh-Ritz of the mixed-precision subspace with the FP64 H
+        q, _ = ko.cholqr(g.get_states())
+        e_ref_sub, _, _, _ = ko.rayleigh_ritz(q, ko.apply_h(ref, q))
+        q2, _ = ko.cholqr(c_ref)
+        e_ora, _, _, _ = ko.rayleigh_ritz(q2, ko.apply_h(ref, q2))
+        assert np.max(np.abs(e_ref_sub - e_ora)) <= 1e-6
+        assert np.max(np.abs(eps - eps_ref)) <= 1e-4
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("propagator", ["etrs", "taylor"])
+@pytest.mark.parametrize("hxc", [True, False])
+def test_td_step_parity(ks, prec, propagator, hxc):
+    cell = inputs.small_cell(10.0, 24, 4, 6, 12)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec=prec)
+    q, _ = ko.cholqr(inputs.random_coeffs(12, 6, ref.nG))
+    g.set_states(q)
+    nsteps, dt = 3, 0.05
+    norms, energies = g.td_step(dt, nsteps, propagator, hxc)
+    c_ref, n_ref, e_ref = ko.td_run(ref, q, dt, nsteps, propagator, hxc)
+    got = g.get_states()
+    if prec == "fp64":
+        assert rel(got, c_ref) <= 1e-11
+        assert np.max(np.abs(norms - n_ref)) <= 1e-11 * n_ref[0]
+        assert np.max(np.abs(energies - e_ref)) <= 1e-10 * max(1, np.max(np.abs(e_ref)))
+    else:
+        assert rel(got, c_ref) <= 5e-5
+        assert np.max(np.abs(norms - n_ref)) <= 1e-5 * n_ref[0]
+        assert np.max(np.abs(energies - e_ref)) <= 1e-4 * max(1, np.max(np.abs(e_ref)))
+    g.close()
+
+
+def test_td_divergence_detected(ks):
+    """dt far beyond the Taylor-4 stability bound (x = dt*E > 2 sqrt 2) must report KS_ERR_DIVERGED."""
+    cell = inputs.small_cell(10.0, 24, 2, 3, 13)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec="fp64")
+    q, _ = ko.cholqr(inputs.random_coeffs(13, 3, ref.nG))
+    g.set_states(q)
+    with pytest.raises(ks.KsError) as e:
+        g.td_step(2.0, 20, "taylor", False)
+    assert e.value.status == ks.KS_ERR_DIVERGED
+    g.close()
+
+
+def test_bad_arguments(ks):
+    cell = inputs.small_cell(10.0, 24, 2, 3, 14)
+    g = ks.Grid(cell, prec="fp64")
+    psi = torch.zeros((3, g.nG), dtype=torch.complex128, device="cuda")
+    with pytest.raises(ks.KsError) as e:
+        g.apply_h(psi.data_ptr(), psi.data_ptr(), 3)
+    assert e.value.status == ks.KS_ERR_ARG
+    h = torch.empty_like(psi)
+    with pytest.raises(ks.KsError):
+        g.apply_h(psi.data_ptr(), h.data_ptr(), 4)
+    g.close()
+    bad = dict(cell, nproj=2)
+    with pytest.raises(ks.KsError):
+        ks.Grid(bad, prec="fp64")
