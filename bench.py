@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the Kohn-Sham hot path on one GB300 (N GPUs: independent replicas).
+
+Workload ``gs96`` (the ground-state block-iteration cell): L = 30 bohr, 96^3 grid,
+|S| = 115,313 plane waves (20 Ha), 128 states, 64 atoms on a perturbed fcc lattice,
+Gaussian V_loc (depth -3 Ha, width 0.8 bohr), 4 KB projectors per atom.  One step is one
+steepest-descent block iteration through the C ABI: CholQR (Gram GEMM, FP64 Cholesky,
+rotation) -> H psi for all 128 states -> Rayleigh-Ritz (GEMM, eigensolver, two
+rotations) -> SD update.  Mixed precision (complex64 states and FFTs).
+
+value = 128 * 96^3 state-gridpoints per step / step time (device CUDA events, L2 flushed
+between timed steps).  Extra keys: H psi alone, the all-FP64 GPU path, a real-time ETRS
+step of the 128^3 / 512-state cell, the live per-kernel roofline, the CPU oracle timed on
+a bounded sample, and the end-to-end figure with host buffers.
+
+--impl reference times the FP64 CPU oracle (plain numpy, tests' reference) on the same
+workload, one block iteration on a bounded sample of the states per step.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hψ state·gridpts/s & %HBM roofline, mixed vs FP64; TD steps/s; serve p50/p99"
+UNIT = "state·gridpts/s"
+WORKLOAD = "gs96"
+CPU_SAMPLE_STATES = 4
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_sus=d["bf16_tflops_sustained"],
+                    sm_max_mhz=d.get("sm_max_mhz", 2070.0), src="measured")
+    return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, sm_max_mhz=2070.0, src="fallback")
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU leg: the oracle as it stands, on a bounded sample (runs in a child process, 1 thread)
+# ------------------------------------------------------------------------------------------------
+def cpu_leg(nsteps, warmup, nsample):
+    from oracle import ks_oracle as ko
+    from paper_2106_03872_gb300 import inputs
+    cell = inputs.cell(WORKLOAD)
+    ref = ko.Cell(cell)
+    c = inputs.random_coeffs(cell["seed"], cell["nstates"], ref.nG)[:nsample]
+    for _ in range(warmup):
+        ko.block_iteration(ref, c, 1)
+    times = []
+    for _ in range(nsteps):
+        t0 = time.perf_counter()
+        ko.block_iteration(ref, c, 1)
+        times.append(time.perf_counter() - t0)
+    return dict(times=times, nsample=nsample, N=ref.N)
+
+
+def run_cpu_leg(nsteps, warmup, nsample):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", "--steps", str(nsteps), "--warmup", str(warmup),
+           "--sample", str(nsample)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("cpu leg failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_obj(leg):
+    t = sum(leg["times"]) / len(leg["times"])
+    return {"value": leg["nsample"] * leg["N"] ** 3 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one block iteration (CholQR, H psi, Rayleigh-Ritz, SD update) of %d of the 128 states of "
+                      "the %s cell, FP64 numpy oracle, 1 thread; mean of %d steps" % (
+                          leg["nsample"], WORKLOAD, len(leg["times"]))}
+
+
+# ------------------------------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ------------------------------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# Roofline of the dominant kernel (stage timings from the library's CUDA events)
+# ------------------------------------------------------------------------------------------------
+def stage_model(name, geo, pk, fp32_tflops):
+    """(bound, algorithmic amount per launch, peak, unit) for a timed stage, or None."""
+    N, nG, ns, ncols = geo["N"], geo["nG"], geo["nstates"], geo.get("ncols", 0)
+    c64 = 8
+    if name == "apply_h":
+        # packed psi in + packed H psi out per state (the per-state algorithmic bytes of H psi)
+        return "hbm", 2 * nG * c64 * ns + N ** 3 * 4, pk["hbm"], "GB/s"
+    if name == "fft_lines":
+        # one launch = one 1D-FFT pass over a batch of grids; bytes = read + write of the batch
+        return "hbm", 2 * geo["batch"] * N ** 3 * c64, pk["hbm"], "GB/s"
+    if name == "plane":
+        # read + write of the pruned column buffer of every state, plus V once
+        return "hbm", 2 * ns * ncols * N * c64 + N ** 3 * 4, pk["hbm"], "GB/s"
+    if name in ("zinv", "zfwd"):
+        return "hbm", ns * (ncols * N + 2 * nG) * c64, pk["hbm"], "GB/s"
+    if name == "gram":
+        # complex Psi^H Psi: 8 real flops per complex MAC
+        return "tensor", 8.0 * ns * ns * nG, pk["bf16"], "TFLOP/s"
+    if name == "rotate":
+        return "tensor", 8.0 * ns * ns * nG, pk["bf16"], "TFLOP/s"
+    return None
+
+
+def roofline(entries, geo, pk, steps):
+    leaf = {k: v for k, v in entries.items() if k != "apply_h"}
+    if not leaf:
+        return None, None
+    name = max(leaf, key=lambda k: leaf[k][0])
+    ms, count = leaf[name]
+    model = stage_model(name, geo, pk, None)
+    per_launch_ms = ms / max(count, 1)
+    out = {"kernel": name, "launch_ms": per_launch_ms, "launches": count}
+    if model is None:
+        out.update({"bound": "unknown", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
+        return out, name
+    bound, amount, peak, unit = model
+    if unit == "GB/s":
+        achieved = amount / (per_launch_ms * 1e-3) / 1e9
+    else:
+        achieved = amount / (per_launch_ms * 1e-3) / 1e12
+    out.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": None, "peak_src": pk["src"]})
+    return out, name
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+def main_gpu(args):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = run_cpu_leg(args.cpu_steps, 1, CPU_SAMPLE_STATES)     # before any CUDA work
+
+    torch.cuda.set_device(local)
+    from paper_2106_03872_gb300 import inputs, ks
+    pk = peaks()
+    stream = torch.cuda.Stream()
+    cell = inputs.cell(WORKLOAD)
+    N, ns = cell["N"], cell["nstates"]
+    nG = ks.count_gvectors(cell["L"], N, cell["ecut"])
+    c0 = inputs.random_coeffs(cell["seed"], ns, nG)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed_steps(g, nsteps, warmup, fn, profile=False):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if profile:
+            g.profile(2)
+            g.profile(1)
+        launches0 = ks.kernel_launches()
+        times = []
+        for _ in range(nsteps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            fn()
+            ev1.record(stream)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+        torch.cuda.synchronize()
+        launches = ks.kernel_launches() - launches0
+        entries = g.profile_entries() if profile else {}
+        if profile:
+            g.profile(0)
+        return times, launches, entries
+
+    # ---- main arm: mixed precision block iteration
+    g = ks.Grid(cell, prec="bf16x3")
+    g.set_states(c0)
+    g.orthonormalize()
+    geo = dict(N=N, nG=g.nG, nstates=ns, batch=ns, ncols=0)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        times, launches, entries = timed_steps(g, args.steps, args.warmup,
+                                               lambda: g.block_iteration(1, stream), profile=True)
+    if dist is not None:
+        t = torch.tensor([sum(times)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    else:
+        total_ms = sum(times)
+    ms_per_step = total_ms / args.steps
+    value = world * ns * N ** 3 * args.steps / (total_ms * 1e-3)
+
+    rl, rl_name = roofline(entries, geo, pk, args.steps)
+
+    # ---- H psi alone (device buffers)
+    psi = torch.from_numpy(c0).to("cuda", torch.complex64)
+    hpsi = torch.empty_like(psi)
+    h_times, _, h_entries = timed_steps(g, args.steps, 2,
+                                        lambda: g.apply_h(psi.data_ptr(), hpsi.data_ptr(), ns, stream), profile=True)
+    h_ms = statistics.median(h_times)
+    h_bytes = 2 * g.nG * 8 * ns + N ** 3 * 4
+    hpsi_only = {"value": ns * N ** 3 / (h_ms * 1e-3), "unit": UNIT, "ms": h_ms,
+                 "hbm_frac_algorithmic": h_bytes / (h_ms * 1e-3) / 1e9 / pk["hbm"],
+                 "stages_ms_per_call": {k: v[0] / args.steps for k, v in h_entries.items()}}
+
+    # ---- end to end through the public API with host buffers
+    pinned = torch.empty((ns, g.nG), dtype=torch.complex128, pin_memory=True)
+    pinned.numpy()[:] = c0
+    pin_np = pinned.numpy()
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_states(pin_np)
+        eig = g.block_iteration(1, stream)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_times.append(t1 - t0)
+    e2e = {"value": world * ns * N ** 3 / statistics.mean(e2e_times), "unit": UNIT,
+           "h2d_bytes_per_step": ns * g.nG * 16, "d2h_bytes_per_step": ns * 8,
+           "note": "set_states (pinned complex128 host -> device) + one block iteration + Ritz values to host"}
+    assert np.all(np.isfinite(eig))
+    g.close()
+
+    # ---- all-FP64 GPU path, same workload
+    fp64 = None
+    if not args.no_fp64:
+        g64 = ks.Grid(cell, prec="fp64")
+        g64.set_states(c0)
+        g64.orthonormalize()
+        t64, _, e64 = timed_steps(g64, max(2, args.steps // 5), 1, lambda: g64.block_iteration(1, stream),
+                                  profile=True)
+        ms64 = statistics.mean(t64)
+        fp64 = {"value": ns * N ** 3 / (ms64 * 1e-3), "ms_per_step": ms64, "speedup_mixed_vs_fp64": ms64 / ms_per_step,
+                "stages_ms_per_step": {k: v[0] / len(t64) for k, v in e64.items()}}
+        g64.close()
+
+    # ---- real-time ETRS step of the 128^3 / 512-state cell (Hartree + Slater each step)
+    td = None
+    if not args.no_td:
+        tcell = inputs.cell("td128")
+        gt = ks.Grid(tcell, prec="bf16x3")
+        ntg = gt.nG
+        gt.set_states(inputs.random_coeffs(tcell["seed"], tcell["nstates"], ntg))
+        gt.orthonormalize()
+        tt, _, te = timed_steps(gt, 2, 1, lambda: gt.td_step(0.05, 1, "etrs", True, stream), profile=True)
+        tms = statistics.mean(tt)
+        td = {"workload": "td128: L=40, N=128, 512 states, 128 atoms, ETRS + Taylor 4, Hartree + Slater, dt=0.05",
+              "steps_per_s": 1e3 / tms, "ms_per_step": tms,
+              "stages_ms_per_step": {k: v[0] / len(tt) for k, v in te.items()}}
+        gt.close()
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": "gs96: L=30 bohr, N=96, |S|=%d, 128 states, 64 atoms (perturbed fcc), 4 KB "
+                               "projectors/atom, one SD block iteration per step (CholQR + H psi + Rayleigh-Ritz + "
+                               "update), mixed precision" % g.nG,
+                   "global_batch": ns * world, "grid": N, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between timed steps (256 MB device write)"},
+        "roofline": rl, "cpu_baseline": cpu_baseline_obj(cpu) if cpu else None, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk.summary(), "hpsi_only": hpsi_only, "fp64_gpu": fp64, "td": td,
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in entries.items()},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    leg = cpu_leg(args.steps, args.warmup, CPU_SAMPLE_STATES)
+    base = cpu_baseline_obj(leg)
+    t = sum(leg["times"]) / len(leg["times"])
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "gs96 (bounded sample: %d of 128 states per step)" % CPU_SAMPLE_STATES},
+            "cpu_baseline": base, "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-leg", action="store_true")
+    ap.add_argument("--sample", type=int, default=CPU_SAMPLE_STATES)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-td", action="store_true")
+    args = ap.parse_args()
+    if args.cpu_leg:
+        print(json.dumps(cpu_leg(args.steps, args.warmup, args.sample)))
+        return
+    if args.impl == "reference":
+        main_reference(args)
+        return
+    main_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

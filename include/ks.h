@@ -185,6 +185,23 @@ ks_status ks_serve_poll(ks_server s, uint64_t ticket, int timeout_ms, double* re
 /* Result sizes for a ticket: number of doubles in result_out, nstates, nG. */
 ks_status ks_serve_result_info(ks_server s, uint64_t ticket, int* nresult, int* nstates, int* nG);
 
+/* ---------------------------------------------------------------------------------- */
+/* Instrumentation (no counterpart in the paper).                                      */
+/* ---------------------------------------------------------------------------------- */
+
+/* mode 1: record a CUDA event pair on the launching stream around every stage of the
+ * handle's calls (H application, line FFTs, Gram, rotations, Cholesky, eigensolver, ...);
+ * mode 0: stop recording; mode 2: drop the accumulated entries. */
+ks_status ks_profile(ks_grid g, int mode);
+
+/* Entry idx (0-based) of the accumulated stage timings: name (NUL-terminated, truncated to
+ * name_len), total milliseconds and number of timed scopes.  Waits for pending events.
+ * KS_ERR_ARG once idx passes the last entry. */
+ks_status ks_profile_read(ks_grid g, int idx, char* name, int name_len, double* ms, long* count);
+
+/* Number of kernels this library has launched in this process so far. */
+uint64_t ks_kernel_launches(void);
+
 /* Thread-local text of the last error of this thread (never NULL). */
 const char* ks_last_error(void);
 

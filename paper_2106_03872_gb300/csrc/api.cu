@@ -1,5 +1,6 @@
 // The C ABI (include/ks.h): argument checks, handle lifetime, and translation of internal
 // errors into ks_status.  No exception crosses this boundary.
+#include <cstdio>
 #include <cstring>
 #include <memory>
 
@@ -7,6 +8,7 @@
 
 namespace ks {
 const char* last_error_cstr();
+uint64_t launch_count();
 }
 
 struct ks_grid_s {
@@ -164,5 +166,29 @@ ks_status ks_td_step(ks_grid g, double dt, int nsteps, int propagator, int hartr
     g->eng->td_steps(dt, nsteps, propagator, hartree_xc, norm_out, energy_out, as_stream(stream));
   });
 }
+
+ks_status ks_profile(ks_grid g, int mode) {
+  return guarded([&] {
+    need(g != nullptr && mode >= 0 && mode <= 2, "grid is NULL or mode not in {0,1,2}");
+    if (mode == 2)
+      g->eng->prof.reset();
+    else
+      g->eng->prof.enable(mode == 1);
+  });
+}
+
+ks_status ks_profile_read(ks_grid g, int idx, char* name, int name_len, double* ms, long* count) {
+  return guarded([&] {
+    need(g && name && name_len > 0 && ms && count, "bad profile_read arguments");
+    g->eng->prof.collect();
+    const auto& e = g->eng->prof.entries();
+    if (idx < 0 || idx >= (int)e.size()) ks::fail(KS_ERR_ARG, "profile entry %d of %d", idx, (int)e.size());
+    std::snprintf(name, name_len, "%s", e[idx].name.c_str());
+    *ms = e[idx].ms;
+    *count = e[idx].count;
+  });
+}
+
+uint64_t ks_kernel_launches(void) { return ks::launch_count(); }
 
 }  // extern "C"

@@ -30,7 +30,14 @@ void set_last_error(const std::string& msg);
     if (e_ != cudaSuccess) ks::fail_cuda(e_, #call, __FILE__, __LINE__); \
   } while (0)
 
-#define KS_CHECK_LAUNCH() KS_CUDA(cudaGetLastError())
+// Every kernel launch is followed by KS_CHECK_LAUNCH(): it counts the launch (reported by
+// ks_kernel_launches) and turns a launch error into ks::Error.
+void note_launch();
+#define KS_CHECK_LAUNCH()          \
+  do {                             \
+    ks::note_launch();             \
+    KS_CUDA(cudaGetLastError());   \
+  } while (0)
 
 // ---------------------------------------------------------------------------------------------
 // Complex types: float2 / double2 with the few operations the kernels use.

@@ -26,6 +26,59 @@ void* DeviceArena::alloc(size_t bytes) {
   return p;
 }
 
+StageProfiler::~StageProfiler() {
+  for (auto& p : pending_) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : free_) cudaEventDestroy(e);
+}
+
+void StageProfiler::enable(bool on) {
+  if (!on) collect();
+  on_ = on;
+}
+
+cudaEvent_t StageProfiler::get_event() {
+  if (!free_.empty()) {
+    cudaEvent_t e = free_.back();
+    free_.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  KS_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+int StageProfiler::begin(const char* name, cudaStream_t s) {
+  int idx = -1;
+  for (size_t i = 0; i < entries_.size(); ++i)
+    if (entries_[i].name == name) idx = (int)i;
+  if (idx < 0) {
+    entries_.push_back(Entry{name, 0.0, 0});
+    idx = (int)entries_.size() - 1;
+  }
+  Pending p{idx, get_event(), get_event()};
+  KS_CUDA(cudaEventRecord(p.a, s));
+  pending_.push_back(p);
+  return (int)pending_.size() - 1;
+}
+
+void StageProfiler::end(int slot, cudaStream_t s) { KS_CUDA(cudaEventRecord(pending_[slot].b, s)); }
+
+void StageProfiler::collect() {
+  for (auto& p : pending_) {
+    KS_CUDA(cudaEventSynchronize(p.b));
+    float ms = 0;
+    KS_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+    entries_[p.entry].ms += ms;
+    entries_[p.entry].count += 1;
+    free_.push_back(p.a);
+    free_.push_back(p.b);
+  }
+  pending_.clear();
+}
+
 namespace {
 
 constexpr int MAX_STEPS_CHUNK = 1024;
@@ -146,6 +199,7 @@ template <typename T> class Engine final : public EngineBase {
     C* hpsi = static_cast<C*>(hpsi_v);
     if (n < 0 || n > ns_) fail(KS_ERR_ARG, "apply_h: nstates=%d outside [0, %d]", n, ns_);
     if (n == 0) return;
+    ProfScope scope(prof, "apply_h", s);
     if constexpr (std::is_same<T, float>::value) {
       if (fused_) {
         fused_->apply_h(psi, hpsi, n, vtot_, s);
@@ -160,13 +214,19 @@ template <typename T> class Engine final : public EngineBase {
       const C* in = psi + (size_t)b0 * g_.nG;
       KS_CUDA(cudaMemsetAsync(grid_, 0, (size_t)nb * N3 * sizeof(C), s));
       scatter_sphere<T>(in, grid_, t_, nb, s);
-      for (int ax = 2; ax >= 0; --ax) fft_axis<T>(grid_, nb, N, ax, +1, t_.tw, s);
+      {
+        ProfScope f(prof, "fft_lines", s);
+        for (int ax = 2; ax >= 0; --ax) fft_axis<T>(grid_, nb, N, ax, +1, t_.tw, s);
+      }
       // grid holds psi' = Omega^{1/2} psi.  p = dV sum beta psi = dV Omega^{-1/2} sum beta psi'.
       nl_project<T>(grid_, t_, proj_, nb, T(g_.dV) * rs, s);
       multiply_potential<T>(grid_, vtot_, (int)N3, nb, s);
       // u' = Omega^{1/2} u: add Omega^{1/2} D beta p
       nl_add<T>(grid_, t_, proj_, nb, T(g_.D * std::sqrt(g_.omega)), s);
-      for (int ax = 0; ax < 3; ++ax) fft_axis<T>(grid_, nb, N, ax, -1, t_.tw, s);
+      {
+        ProfScope f(prof, "fft_lines", s);
+        for (int ax = 0; ax < 3; ++ax) fft_axis<T>(grid_, nb, N, ax, -1, t_.tw, s);
+      }
       gather_kinetic<T>(grid_, in, hpsi + (size_t)b0 * g_.nG, t_, nb, T(1.0 / double(N3)), s);
     }
   }
@@ -189,6 +249,7 @@ template <typename T> class Engine final : public EngineBase {
   // Density (Eq. 1) of n states of `psi`, into nout [N^3] (grid order), fixed state order.
   // ------------------------------------------------------------------------------------------
   void density_of(const C* psi, int n, T* nout, cudaStream_t s) {
+    ProfScope scope(prof, "density", s);
     if constexpr (std::is_same<T, float>::value) {
       if (fused_) {
         fused_->density(psi, n, occ_, nout, s);
@@ -211,6 +272,7 @@ template <typename T> class Engine final : public EngineBase {
 
   // V = V_loc + v_H[n] + v_x[n] (periodic Poisson in Fourier space, v_H(G=0) = 0; Slater exchange)
   void update_potential(const T* n, cudaStream_t s) {
+    ProfScope scope(prof, "hartree_xc", s);
     const int N = g_.N;
     const size_t N3 = (size_t)N * N * N;
     real_to_complex<T>(n, pwork_, (int)N3, s);
@@ -226,12 +288,21 @@ template <typename T> class Engine final : public EngineBase {
   // ------------------------------------------------------------------------------------------
   void cholqr(cudaStream_t s, bool keep_S) {
     const int n = ns_, nG = g_.nG;
-    gemm_cn<T>(psi_, nG, psi_, nG, n, n, nG, part_, part_elems_, mS_, s);
-    hermitize(mS_, n, s);
+    {
+      ProfScope p(prof, "gram", s);
+      gemm_cn<T>(psi_, nG, psi_, nG, n, n, nG, part_, part_elems_, mS_, s);
+      hermitize(mS_, n, s);
+    }
     KS_CUDA(cudaMemcpyAsync(mA_, mS_, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-    cholesky_inverse_tol(mA_, mM_, n, sizeof(T) == 8 ? 1e-12 : 1e-6, status_, s);
+    {
+      ProfScope p(prof, "cholesky", s);
+      cholesky_inverse_tol(mA_, mM_, n, sizeof(T) == 8 ? 1e-12 : 1e-6, status_, s);
+    }
     C* out = spare(psi_, hpsi_);
-    rotate<T>(mM_, n, psi_, nG, out, nG, n, nG, s);
+    {
+      ProfScope p(prof, "rotate", s);
+      rotate<T>(mM_, n, psi_, nG, out, nG, n, nG, s);
+    }
     swap_in(psi_, out);
     (void)keep_S;
   }
@@ -249,9 +320,16 @@ template <typename T> class Engine final : public EngineBase {
   // Rayleigh-Ritz on (psi_, hpsi_): H_sub = Psi^H H Psi, eigh, rotate both.
   void rr_core(cudaStream_t s) {
     const int n = ns_, nG = g_.nG;
-    gemm_cn<T>(psi_, nG, hpsi_, nG, n, n, nG, part_, part_elems_, mA_, s);
-    hermitize(mA_, n, s);
-    jacobi_eigh(mA_, mV_, eig_, mM_, n, s);
+    {
+      ProfScope p(prof, "gram", s);
+      gemm_cn<T>(psi_, nG, hpsi_, nG, n, n, nG, part_, part_elems_, mA_, s);
+      hermitize(mA_, n, s);
+    }
+    {
+      ProfScope p(prof, "eigh", s);
+      jacobi_eigh(mA_, mV_, eig_, mM_, n, s);
+    }
+    ProfScope p(prof, "rotate", s);
     C* o1 = spare(psi_, hpsi_);
     rotate<T>(mM_, n, psi_, nG, o1, nG, n, nG, s);
     swap_in(psi_, o1);
@@ -275,6 +353,7 @@ template <typename T> class Engine final : public EngineBase {
       cholqr(s, false);
       apply_h(psi_, hpsi_, ns_, s);
       rr_core(s);
+      ProfScope p(prof, "sd_update", s);
       sd_update<T>(psi_, hpsi_, eig_, alpha, g_.nG, ns_, s);
     }
     int st = 0;

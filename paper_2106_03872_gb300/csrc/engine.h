@@ -23,8 +23,56 @@ class DeviceArena {
 // Device bytes an engine for this cell would hold (used by the serving admission).
 size_t engine_device_bytes(const ks_cell_desc& d, int nG, int ncols);
 
+// Per-stage CUDA-event timing of an engine's kernels (off by default).  Each stage scope
+// records an event pair on the launching stream; collect() waits for them and accumulates
+// milliseconds and launch counts per stage name.
+class StageProfiler {
+ public:
+  struct Entry {
+    std::string name;
+    double ms = 0;
+    long count = 0;
+  };
+  ~StageProfiler();
+  void enable(bool on);
+  bool on() const { return on_; }
+  int begin(const char* name, cudaStream_t s);
+  void end(int slot, cudaStream_t s);
+  void collect();
+  const std::vector<Entry>& entries() const { return entries_; }
+  void reset() {
+    collect();
+    entries_.clear();
+  }
+
+ private:
+  struct Pending {
+    int entry;
+    cudaEvent_t a, b;
+  };
+  cudaEvent_t get_event();
+  bool on_ = false;
+  std::vector<Entry> entries_;
+  std::vector<Pending> pending_;
+  std::vector<cudaEvent_t> free_;
+};
+
+class ProfScope {
+ public:
+  ProfScope(StageProfiler& p, const char* name, cudaStream_t s) : p_(p), s_(s) { slot_ = p_.on() ? p_.begin(name, s) : -1; }
+  ~ProfScope() {
+    if (slot_ >= 0) p_.end(slot_, s_);
+  }
+
+ private:
+  StageProfiler& p_;
+  cudaStream_t s_;
+  int slot_;
+};
+
 class EngineBase {
  public:
+  StageProfiler prof;
   virtual ~EngineBase() = default;
   virtual const HostGeometry& geo() const = 0;
   virtual int nstates() const = 0;

@@ -2,6 +2,7 @@
 // potential on the grid, and the real-space projector spheres (Sec. "Pseudopotentials",
 // Eq. 9).  Built once per handle in FP64 and copied to the device.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <map>
@@ -11,6 +12,10 @@
 namespace ks {
 
 static thread_local std::string g_last_error = "no error";
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 const char* last_error_cstr() { return g_last_error.c_str(); }

@@ -25,7 +25,7 @@ EXPORTS = ["ks_count_gvectors", "ks_grid_create", "ks_grid_destroy", "ks_grid_gv
            "ks_get_vloc", "ks_set_states", "ks_get_states", "ks_states_device", "ks_apply_h", "ks_apply_h_host",
            "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_td_step",
            "ks_serve_create", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info",
-           "ks_last_error"]
+           "ks_profile", "ks_profile_read", "ks_kernel_launches", "ks_last_error"]
 
 
 class KsError(RuntimeError):
@@ -84,6 +84,12 @@ def load():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ct.c_int
+    lib.ks_profile.argtypes = [P, ct.c_int]
+    lib.ks_profile.restype = ct.c_int
+    lib.ks_profile_read.argtypes = [P, ct.c_int, ct.c_char_p, ct.c_int, dp, ct.POINTER(ct.c_long)]
+    lib.ks_profile_read.restype = ct.c_int
+    lib.ks_kernel_launches.argtypes = []
+    lib.ks_kernel_launches.restype = ct.c_uint64
     lib.ks_last_error.argtypes = []
     lib.ks_last_error.restype = ct.c_char_p
     _lib = lib
@@ -117,6 +123,10 @@ def make_desc(cell, prec="bf16x3", nstates=None, occ=None):
     d.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     d._keep = (pos, occ_arr)
     return d
+
+
+def kernel_launches():
+    return int(load().ks_kernel_launches())
 
 
 def count_gvectors(L, N, ecut):
@@ -219,6 +229,21 @@ class Grid:
         e = np.zeros(self.nstates)
         check(load().ks_block_iteration(self.h, int(niter), _dptr(e), _stream_ptr(stream)))
         return e
+
+    def profile(self, mode):
+        check(load().ks_profile(self.h, int(mode)))
+
+    def profile_entries(self):
+        """{stage name: (total ms, count)} of the accumulated stage timings."""
+        out = {}
+        buf = ct.create_string_buffer(128)
+        ms = ct.c_double()
+        cnt = ct.c_long()
+        i = 0
+        while load().ks_profile_read(self.h, i, buf, 128, ct.byref(ms), ct.byref(cnt)) == KS_OK:
+            out[buf.value.decode()] = (ms.value, cnt.value)
+            i += 1
+        return out
 
     def td_step(self, dt, nsteps, propagator="etrs", hartree_xc=True, stream=None):
         norms = np.zeros(nsteps)
