@@ -25,7 +25,7 @@ EXPORTS = ["ks_count_gvectors", "ks_grid_create", "ks_grid_destroy", "ks_grid_gv
            "ks_get_vloc", "ks_set_states", "ks_get_states", "ks_states_device", "ks_apply_h", "ks_apply_h_host",
            "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_td_step",
            "ks_serve_create", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info",
-           "ks_profile", "ks_profile_read", "ks_kernel_launches", "ks_last_error"]
+           "ks_profile", "ks_profile_read", "ks_kernel_launches", "ks_overlap_noalloc", "ks_last_error"]
 
 
 class KsError(RuntimeError):
@@ -79,6 +79,7 @@ def load():
                             ct.POINTER(ct.c_uint64)],
         "ks_serve_poll": [P, ct.c_uint64, ct.c_int, dp, dp, dp],
         "ks_serve_result_info": [P, ct.c_uint64, ip, ip, ip],
+        "ks_overlap_noalloc": [P, P, ct.c_int, ct.c_int, ct.c_int, ct.c_int, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -123,6 +124,12 @@ def make_desc(cell, prec="bf16x3", nstates=None, occ=None):
     d.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     d._keep = (pos, occ_arr)
     return d
+
+
+def overlap_noalloc(a_ptr, b_ptr, m, n, nG, fp64, out_ptr, stream=None):
+    """out = A^H B ([m][n] complex128, device) without any device allocation (see ks.h)."""
+    check(load().ks_overlap_noalloc(ct.c_void_p(a_ptr), ct.c_void_p(b_ptr), int(m), int(n), int(nG),
+                                    1 if fp64 else 0, ct.c_void_p(out_ptr), _stream_ptr(stream)))
 
 
 def kernel_launches():
