@@ -307,6 +307,240 @@ __global__ void __launch_bounds__(1024) k_jacobi(double2* __restrict__ A, double
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP32 cyclic Jacobi with the packed upper triangle of A and the eigenvector matrix in shared
+// memory (n <= 128), followed by FP64 Rayleigh quotients of the FP32 vectors on the FP64
+// matrix (many CTAs), then sorting and the phase convention.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int pk_index(int i, int j, int n) { return i * n - (i * (i - 1)) / 2 + (j - i); }
+__device__ __forceinline__ float2 fconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 fmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 fadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 fscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+constexpr int JS_MAXN = 128;
+
+__global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__ H, int n, double2* __restrict__ Vout,
+                                                     float tol) {
+  extern __shared__ float2 jsm[];
+  const int npk = n * (n + 1) / 2;
+  float2* Ap = jsm;                 // packed upper triangle (i <= j)
+  float2* V = jsm + npk;            // V[i*n + j], column j = eigenvector j
+  __shared__ int sp[JS_MAXN / 2], sq[JS_MAXN / 2];
+  __shared__ float sc[JS_MAXN / 2], ss[JS_MAXN / 2];
+  __shared__ float2 se[JS_MAXN / 2];
+  __shared__ float red[32];
+  __shared__ float s_fro, s_off;
+  const int P = n + (n & 1);
+  const int np = P / 2;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    if (i <= j) {
+      const double2 h = H[e];
+      Ap[pk_index(i, j, n)] = make_float2((float)h.x, i == j ? 0.f : (float)h.y);
+    }
+    V[e] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  auto block_sum_f = [&](float v) -> float {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x == 0)
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    __syncthreads();
+    return t;
+  };
+  {
+    float f = 0.f;
+    for (int e = threadIdx.x; e < npk; e += blockDim.x) {
+      // diagonal entries sit where j == i; weight 2 for off-diagonal (Hermitian pair)
+      f += Ap[e].x * Ap[e].x + Ap[e].y * Ap[e].y;
+    }
+    const float t = block_sum_f(f);
+    if (threadIdx.x == 0) s_fro = t;
+  }
+  __syncthreads();
+  const float tiny = 1e-30f;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    {
+      float o = 0.f;
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        if (i < j) {
+          const float2 a = Ap[pk_index(i, j, n)];
+          o += 2.f * (a.x * a.x + a.y * a.y);
+        }
+      }
+      const float t = block_sum_f(o);
+      if (threadIdx.x == 0) s_off = t;
+      __syncthreads();
+      if (s_off <= tol * tol * s_fro) break;
+    }
+    for (int r = 0; r < P - 1; ++r) {
+      if (threadIdx.x < np) {
+        const int k = threadIdx.x;
+        const int pa = k, pb = P - 1 - k;
+        const int ua = (pa == 0) ? 0 : 1 + ((pa - 1 + r) % (P - 1));
+        const int ub = (pb == 0) ? 0 : 1 + ((pb - 1 + r) % (P - 1));
+        const int p = min(ua, ub), q = max(ua, ub);
+        sp[k] = p;
+        sq[k] = q;
+        float c = 1.f, sv = 0.f;
+        float2 e = make_float2(1.f, 0.f);
+        if (q < n) {
+          const float2 b = Ap[pk_index(p, q, n)];
+          const float mag = hypotf(b.x, b.y);
+          if (mag > tiny) {
+            const float alpha = Ap[pk_index(p, p, n)].x, gamma = Ap[pk_index(q, q, n)].x;
+            const float tau = (gamma - alpha) / (2.f * mag);
+            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + t * t);
+            sv = t * c;
+            e = make_float2(b.x / mag, b.y / mag);
+          }
+        }
+        sc[k] = c;
+        ss[k] = sv;
+        se[k] = e;
+      }
+      __syncthreads();
+      // A <- J^H A J, one 2x2 block (pair PP rows, pair QQ columns) per job, PP <= QQ
+      for (int job = threadIdx.x; job < np * np; job += blockDim.x) {
+        const int PP = job / np, QQ = job % np;
+        if (PP > QQ) continue;
+        const int r0 = sp[PP], r1 = sq[PP], c0 = sp[QQ], c1 = sq[QQ];
+        const int rows[2] = {r0, r1}, cols[2] = {c0, c1};
+        float2 B[2][2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            const int i = rows[a], j = cols[b];
+            if (i >= n || j >= n) {
+              B[a][b] = make_float2(0.f, 0.f);
+            } else {
+              B[a][b] = (i <= j) ? Ap[pk_index(i, j, n)] : fconj(Ap[pk_index(j, i, n)]);
+            }
+          }
+        // left: J_P^H = [[c, -s e], [s conj(e), c]]
+        {
+          const float c = sc[PP], sv = ss[PP];
+          const float2 e = se[PP];
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            const float2 x0 = B[0][b], x1 = B[1][b];
+            B[0][b] = fadd(fscale(x0, c), fscale(fmul(e, x1), -sv));
+            B[1][b] = fadd(fscale(fmul(fconj(e), x0), sv), fscale(x1, c));
+          }
+        }
+        // right: J_Q = [[c, s e], [-s conj(e), c]]
+        {
+          const float c = sc[QQ], sv = ss[QQ];
+          const float2 e = se[QQ];
+#pragma unroll
+          for (int a = 0; a < 2; ++a) {
+            const float2 y0 = B[a][0], y1 = B[a][1];
+            B[a][0] = fadd(fscale(y0, c), fscale(fmul(fconj(e), y1), -sv));
+            B[a][1] = fadd(fscale(fmul(e, y0), sv), fscale(y1, c));
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            const int i = rows[a], j = cols[b];
+            if (i >= n || j >= n) continue;
+            if (PP == QQ && i > j) continue;          // diagonal block: write the upper entries once
+            if (i <= j)
+              Ap[pk_index(i, j, n)] = (i == j) ? make_float2(B[a][b].x, 0.f) : B[a][b];
+            else
+              Ap[pk_index(j, i, n)] = fconj(B[a][b]);
+          }
+      }
+      // V <- V J
+      for (int job = threadIdx.x; job < np * n; job += blockDim.x) {
+        const int k = job / n, i = job % n;
+        const int p = sp[k], q = sq[k];
+        if (q >= n) continue;
+        const float c = sc[k], sv = ss[k];
+        const float2 e = se[k];
+        const float2 vp = V[i * n + p], vq = V[i * n + q];
+        V[i * n + p] = fadd(fscale(vp, c), fscale(fmul(fconj(e), vq), -sv));
+        V[i * n + q] = fadd(fscale(fmul(e, vp), sv), fscale(vq, c));
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const float2 v = V[e];
+    Vout[e] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+// lam[i] = v_i^H H v_i / v_i^H v_i in FP64 (column i of V), one CTA per i.
+__global__ void k_rayleigh_quotients(const double2* __restrict__ H, const double2* __restrict__ V, int n,
+                                     double* __restrict__ lam) {
+  const int i = blockIdx.x;
+  __shared__ double2 vi[512];
+  __shared__ double red[2][32];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) vi[k] = V[(size_t)k * n + i];
+  __syncthreads();
+  double num = 0.0, den = 0.0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int j = e / n, k = e % n;
+    // conj(v_j) H_jk v_k
+    const double2 hv = zmul(H[e], vi[k]);
+    num += vi[j].x * hv.x + vi[j].y * hv.y;
+    if (j == k) den += vi[k].x * vi[k].x + vi[k].y * vi[k].y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_down_sync(0xffffffffu, num, o);
+    den += __shfl_down_sync(0xffffffffu, den, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = num;
+    red[1][threadIdx.x >> 5] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    lam[i] = a / b;
+  }
+}
+
+// Sort by lam (ties by index), normalise, fix phases; Vt row r = eigenvector of rank r.
+__global__ void k_sort_vectors(const double* __restrict__ lam, const double2* __restrict__ V, int n,
+                               double* __restrict__ eig, double2* __restrict__ Vt) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double li = lam[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) rank += (lam[j] < li) || (lam[j] == li && j < i);
+    int kmax = 0;
+    double best = -1.0, nrm = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double2 v = V[(size_t)j * n + i];
+      const double m2 = v.x * v.x + v.y * v.y;
+      nrm += m2;
+      if (m2 > best) {
+        best = m2;
+        kmax = j;
+      }
+    }
+    const double2 vk = V[(size_t)kmax * n + i];
+    const double mag = sqrt(best);
+    const double sc = 1.0 / (mag * sqrt(nrm));
+    const double2 ph = make_double2(vk.x * sc, -vk.y * sc);
+    eig[rank] = li;
+    for (int j = 0; j < n; ++j) Vt[(size_t)rank * n + j] = zmul(V[(size_t)j * n + i], ph);
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -348,6 +582,22 @@ void cholesky_inverse(double2* A, double2* M, int n, int* status, cudaStream_t s
 void cholesky_inverse_tol(double2* A, double2* M, int n, double tol, int* status, cudaStream_t s) {
   if (n > 512) fail(KS_ERR_ARG, "cholesky: n=%d > 512", n);
   k_cholesky_inverse<<<1, 512, 0, s>>>(A, M, n, tol, status);
+  KS_CHECK_LAUNCH();
+}
+
+void jacobi_eigh_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, int n, cudaStream_t s) {
+  if (n > JS_MAXN) fail(KS_ERR_ARG, "jacobi_eigh_mixed: n=%d > %d", n, JS_MAXN);
+  const size_t smem = (size_t)(n * (n + 1) / 2 + n * n) * sizeof(float2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    KS_CUDA(cudaFuncSetAttribute(k_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  k_jacobi_f32<<<1, 1024, smem, s>>>(A, n, V, 1e-5f);
+  KS_CHECK_LAUNCH();
+  k_rayleigh_quotients<<<n, 256, 0, s>>>(A, V, n, lam);
+  KS_CHECK_LAUNCH();
+  k_sort_vectors<<<1, 128, 0, s>>>(lam, V, n, eig, Vt);
   KS_CHECK_LAUNCH();
 }
 

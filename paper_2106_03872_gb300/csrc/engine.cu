@@ -139,7 +139,9 @@ template <typename T> class Engine final : public EngineBase {
     hpsi_ = buf_[1];
     staging_ = alloc<double2>(sn);
     // ---- Hamiltonian work
-    fused_ = make_fused_for(g_, t_, ns_, arena_);
+    status_ = alloc<int>(4);
+    KS_CUDA(cudaMemset(status_, 0, 4 * sizeof(int)));
+    fused_ = make_fused_for(g_, t_, ns_, arena_, prof, status_ + 1);
     if (!fused_) {
       batch_ = (int)full_grid_batch<T>(N, ns_);
       grid_ = alloc<C>((size_t)batch_ * N3);
@@ -148,14 +150,18 @@ template <typename T> class Engine final : public EngineBase {
     // ---- dense LA
     const size_t nn = (size_t)ns_ * ns_;
     part_elems_ = std::max<size_t>(nn * 8, 4096);
+    if (use_tc()) {
+      part_elems_ = std::max(part_elems_, tc_overlap_part_elems(ns_, ns_));
+      rotws_bytes_ = tc_rotation_workspace_bytes(ns_, ns_);
+      rotws_ = arena_.alloc(rotws_bytes_);
+    }
     part_ = alloc<double2>(part_elems_);
     mS_ = alloc<double2>(nn);
     mA_ = alloc<double2>(nn);
     mM_ = alloc<double2>(nn);
     mV_ = alloc<double2>(nn);
     eig_ = alloc<double>(ns_);
-    status_ = alloc<int>(4);
-    KS_CUDA(cudaMemset(status_, 0, 4 * sizeof(int)));
+    lam_ = alloc<double>(ns_);
     // ---- potentials / real-time
     dens_ = alloc<T>(N3);
     pwork_ = alloc<C>(N3);
@@ -242,7 +248,7 @@ template <typename T> class Engine final : public EngineBase {
     apply_h(in, out, n, s);
     to_c128<T>(out, staging_, sn, s);
     KS_CUDA(cudaMemcpyAsync(hpsi_host, staging_, sn * sizeof(double2), cudaMemcpyDeviceToHost, s));
-    KS_CUDA(cudaStreamSynchronize(s));
+    check_tc_status(s);
   }
 
   // ------------------------------------------------------------------------------------------
@@ -290,7 +296,7 @@ template <typename T> class Engine final : public EngineBase {
     const int n = ns_, nG = g_.nG;
     {
       ProfScope p(prof, "gram", s);
-      gemm_cn<T>(psi_, nG, psi_, nG, n, n, nG, part_, part_elems_, mS_, s);
+      overlap(psi_, psi_, n, mS_, s);
       hermitize(mS_, n, s);
     }
     KS_CUDA(cudaMemcpyAsync(mA_, mS_, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
@@ -301,7 +307,7 @@ template <typename T> class Engine final : public EngineBase {
     C* out = spare(psi_, hpsi_);
     {
       ProfScope p(prof, "rotate", s);
-      rotate<T>(mM_, n, psi_, nG, out, nG, n, nG, s);
+      rot(mM_, psi_, out, s);
     }
     swap_in(psi_, out);
     (void)keep_S;
@@ -314,6 +320,7 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaMemcpyAsync(&st, status_, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (S_host) KS_CUDA(cudaMemcpyAsync(S_host, mS_, (size_t)ns_ * ns_ * sizeof(double2), cudaMemcpyDeviceToHost, s));
     KS_CUDA(cudaStreamSynchronize(s));
+    check_tc_status(s);
     if (st) fail(KS_ERR_NOT_POSDEF, "CholQR: Gram matrix not positive definite at column %d", st - 1);
   }
 
@@ -322,19 +329,22 @@ template <typename T> class Engine final : public EngineBase {
     const int n = ns_, nG = g_.nG;
     {
       ProfScope p(prof, "gram", s);
-      gemm_cn<T>(psi_, nG, hpsi_, nG, n, n, nG, part_, part_elems_, mA_, s);
+      overlap(psi_, hpsi_, n, mA_, s);
       hermitize(mA_, n, s);
     }
     {
       ProfScope p(prof, "eigh", s);
-      jacobi_eigh(mA_, mV_, eig_, mM_, n, s);
+      if (sizeof(T) == 4 && n <= 128)
+        jacobi_eigh_mixed(mA_, mV_, lam_, eig_, mM_, n, s);
+      else
+        jacobi_eigh(mA_, mV_, eig_, mM_, n, s);
     }
     ProfScope p(prof, "rotate", s);
     C* o1 = spare(psi_, hpsi_);
-    rotate<T>(mM_, n, psi_, nG, o1, nG, n, nG, s);
+    rot(mM_, psi_, o1, s);
     swap_in(psi_, o1);
     C* o2 = spare(psi_, hpsi_);
-    rotate<T>(mM_, n, hpsi_, nG, o2, nG, n, nG, s);
+    rot(mM_, hpsi_, o2, s);
     swap_in(hpsi_, o2);
   }
 
@@ -342,7 +352,7 @@ template <typename T> class Engine final : public EngineBase {
     apply_h(psi_, hpsi_, ns_, s);
     rr_core(s);
     if (eig_host) KS_CUDA(cudaMemcpyAsync(eig_host, eig_, ns_ * sizeof(double), cudaMemcpyDeviceToHost, s));
-    KS_CUDA(cudaStreamSynchronize(s));
+    check_tc_status(s);
   }
 
   void block_iteration(int niter, double* eig_host, cudaStream_t s) override {
@@ -360,6 +370,7 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaMemcpyAsync(&st, status_, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (eig_host) KS_CUDA(cudaMemcpyAsync(eig_host, eig_, ns_ * sizeof(double), cudaMemcpyDeviceToHost, s));
     KS_CUDA(cudaStreamSynchronize(s));
+    check_tc_status(s);
     if (st) fail(KS_ERR_NOT_POSDEF, "block iteration: Gram matrix not positive definite at column %d", st - 1);
   }
 
@@ -433,6 +444,7 @@ template <typename T> class Engine final : public EngineBase {
       KS_CUDA(cudaMemcpyAsync(nh.data(), norms_dev_, cn * sizeof(double), cudaMemcpyDeviceToHost, s));
       KS_CUDA(cudaMemcpyAsync(eh.data(), energies_dev_, cn * sizeof(double), cudaMemcpyDeviceToHost, s));
       KS_CUDA(cudaStreamSynchronize(s));
+      check_tc_status(s);
       if (norm_out) std::memcpy(norm_out + c0, nh.data(), cn * sizeof(double));
       if (energy_out) std::memcpy(energy_out + c0, eh.data(), cn * sizeof(double));
       for (int i = 0; i < cn; ++i) {
@@ -459,6 +471,40 @@ template <typename T> class Engine final : public EngineBase {
       if (buf_[i] != a && buf_[i] != b) return buf_[i];
     fail(KS_ERR_STATE, "internal: no spare state buffer");
   }
+  bool use_tc() const { return sizeof(T) == 4 && prec_ == KS_MIXED_BF16X3; }
+
+  // out = A^H B over the sphere (n x n), tensor cores on the bf16x3 mixed path
+  void overlap(const C* A, const C* B, int n, double2* out, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (use_tc()) {
+        tc_overlap(A, g_.nG, B, g_.nG, n, n, g_.nG, part_, part_elems_, out, status_ + 1, s);
+        return;
+      }
+    }
+    gemm_cn<T>(A, g_.nG, B, g_.nG, n, n, g_.nG, part_, part_elems_, out, s);
+  }
+
+  // Y = M X (rows of states)
+  void rot(const double2* M, const C* X, C* Y, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (use_tc()) {
+        tc_rotate(M, ns_, X, g_.nG, Y, g_.nG, ns_, g_.nG, rotws_, rotws_bytes_, status_ + 1, s);
+        return;
+      }
+    }
+    rotate<T>(M, ns_, X, g_.nG, Y, g_.nG, ns_, g_.nG, s);
+  }
+
+  void check_tc_status(cudaStream_t s) {
+    int e = 0;
+    KS_CUDA(cudaMemcpyAsync(&e, status_ + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    if (e) {
+      KS_CUDA(cudaMemsetAsync(status_ + 1, 0, sizeof(int), s));
+      fail(KS_ERR_CUDA, "tensor-core GEMM: a bounded wait expired (error flag %d)", e);
+    }
+  }
+
   C* spare3(const C* a, const C* b, const C* c) {
     for (int i = 0; i < 6; ++i)
       if (buf_[i] != a && buf_[i] != b && buf_[i] != c) return buf_[i];
@@ -497,6 +543,9 @@ template <typename T> class Engine final : public EngineBase {
   size_t part_elems_ = 0;
   double2 *mS_ = nullptr, *mA_ = nullptr, *mM_ = nullptr, *mV_ = nullptr;
   double* eig_ = nullptr;
+  double* lam_ = nullptr;
+  void* rotws_ = nullptr;
+  size_t rotws_bytes_ = 0;
   int* status_ = nullptr;
   T* dens_ = nullptr;
   C* pwork_ = nullptr;

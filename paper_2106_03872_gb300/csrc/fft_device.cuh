@@ -127,3 +127,144 @@ __device__ __forceinline__ void fft_lines_smem(C* s, int lines, int ld, int N, c
 }
 
 }  // namespace ks
+
+// ---------------------------------------------------------------------------------------------
+// Generalised stages for the fused kernels: line l, element k at s[l*lstride + k*kstride];
+// radices 8, 4, 2, 3; THREADS threads; one call transforms up to CAP elements (lines * N).
+// LINE_FAST maps consecutive threads to consecutive lines (for lines that are columns of a
+// row-major plane, so that shared-memory accesses of a warp are contiguous).
+// The twiddle table holds exp(+2 pi i t/N); sign < 0 conjugates it on the fly.
+// ---------------------------------------------------------------------------------------------
+namespace ks {
+
+inline FftPlan make_plan8(int N) {
+  FftPlan p{};
+  int n = N;
+  while (n % 8 == 0) { p.radix[p.nstages++] = 8; n /= 8; }
+  while (n % 4 == 0) { p.radix[p.nstages++] = 4; n /= 4; }
+  while (n % 2 == 0) { p.radix[p.nstages++] = 2; n /= 2; }
+  while (n % 3 == 0) { p.radix[p.nstages++] = 3; n /= 3; }
+  return p;
+}
+
+template <typename C> struct SmallDft<8, C> {
+  static __device__ __forceinline__ void run(C* v, int sign) {
+    using R = decltype(C::x);
+    const R h = R(0.70710678118654752440);
+    const R sg = R(sign);
+    C a[4], b[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      a[r] = v[r] + v[r + 4];
+      b[r] = v[r] - v[r + 4];
+    }
+    // b_r *= w^r, w = exp(sign i pi/4)
+    {
+      const C z = b[1];
+      b[1] = mk<C>(h * (z.x - sg * z.y), h * (z.y + sg * z.x));
+    }
+    {
+      const C z = b[2];
+      b[2] = mk<C>(-sg * z.y, sg * z.x);
+    }
+    {
+      const C z = b[3];
+      b[3] = mk<C>(h * (-z.x - sg * z.y), h * (-z.y + sg * z.x));
+    }
+    SmallDft<4, C>::run(a, sign);
+    SmallDft<4, C>::run(b, sign);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      v[2 * m] = a[m];
+      v[2 * m + 1] = b[m];
+    }
+  }
+};
+
+template <int R, int Q, int THREADS, bool LINE_FAST, typename C>
+__device__ __forceinline__ void stage_g(C* s, int lines, int lstride, int kstride, int N, int Ns, const C* tw,
+                                        int sign) {
+  const int M = N / R;
+  const int jobs = lines * M;
+  const int step = N / (Ns * R);
+  C v[Q][R];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int job = threadIdx.x + q * THREADS;
+    if (job < jobs) {
+      int l, j;
+      if (LINE_FAST) {
+        j = job / lines;
+        l = job - j * lines;
+      } else {
+        l = job / M;
+        j = job - l * M;
+      }
+      const int k = j % Ns;
+      const C* line = s + l * lstride;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = line[(j + r * M) * kstride];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C w = tw[k * r * step];
+          if (sign < 0) w.y = -w.y;
+          v[q][r] = cmul(v[q][r], w);
+        }
+      }
+      SmallDft<R, C>::run(v[q], sign);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int job = threadIdx.x + q * THREADS;
+    if (job < jobs) {
+      int l, j;
+      if (LINE_FAST) {
+        j = job / lines;
+        l = job - j * lines;
+      } else {
+        l = job / M;
+        j = job - l * M;
+      }
+      const int k = j % Ns;
+      C* line = s + l * lstride;
+      const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) line[(base + r * Ns) * kstride] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int THREADS, int CAP, bool LINE_FAST, typename C>
+__device__ __forceinline__ void fft_lines_g(C* s, int lines, int lstride, int kstride, int N, const FftPlan& plan,
+                                            const C* tw, int sign) {
+  int Ns = 1;
+  for (int i = 0; i < plan.nstages; ++i) {
+    const int R = plan.radix[i];
+    if (R == 8)
+      stage_g<8, (CAP / 8 + THREADS - 1) / THREADS, THREADS, LINE_FAST, C>(s, lines, lstride, kstride, N, Ns, tw, sign);
+    else if (R == 4)
+      stage_g<4, (CAP / 4 + THREADS - 1) / THREADS, THREADS, LINE_FAST, C>(s, lines, lstride, kstride, N, Ns, tw, sign);
+    else if (R == 2)
+      stage_g<2, (CAP / 2 + THREADS - 1) / THREADS, THREADS, LINE_FAST, C>(s, lines, lstride, kstride, N, Ns, tw, sign);
+    else
+      stage_g<3, (CAP / 3 + THREADS - 1) / THREADS, THREADS, LINE_FAST, C>(s, lines, lstride, kstride, N, Ns, tw, sign);
+    Ns *= R;
+  }
+}
+
+// Transform `lines` lines in groups that fit CAP elements per call.
+template <int THREADS, int CAP, bool LINE_FAST, typename C>
+__device__ __forceinline__ void fft_lines_grouped(C* s, int lines, int lstride, int kstride, int N,
+                                                  const FftPlan& plan, const C* tw, int sign) {
+  const int per = CAP / N;
+  for (int l0 = 0; l0 < lines; l0 += per) {
+    const int nl = min(per, lines - l0);
+    fft_lines_g<THREADS, CAP, LINE_FAST, C>(s + l0 * lstride, nl, lstride, kstride, N, plan, tw, sign);
+  }
+}
+
+}  // namespace ks

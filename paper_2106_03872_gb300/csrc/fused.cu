@@ -1,9 +1,474 @@
+// Fused mixed-precision H psi (complex64), three kernels per application:
+//
+//   k_zinv   packed sphere coefficients -> inverse z-FFT of the sphere's z-columns only
+//            -> column buffer [state][z][column]
+//   k_plane  one (state, z-plane) per CTA, the N x N plane in shared memory: scatter the
+//            columns, inverse y-FFT on the rows that hold columns, inverse x-FFT on every
+//            line, u = V psi + sum_{I,l} D beta_Il p_Il (projector add on the sphere points
+//            of this plane), forward x-FFT, forward y-FFT on the rows that hold columns,
+//            gather the columns -> second column buffer
+//   k_zfwd   forward z-FFT of the columns, keep G in S, scale N^-3, add |G|^2/2 c
+//
+// The projections p_Il = dV sum_j beta_Il(r_j) psi(r_j) (Eq. 9) are computed before the
+// plane pass, in Fourier space: on the grid, by Parseval, p_Il = sum_{G in S}
+// conj(b_Il(G)) c_G with b_Il the sphere coefficients of the grid function beta_Il (built
+// once at setup with the FP64 FFT).  That is one overlap GEMM of the projector block with
+// the state block; the add stays in real space, fused into the plane kernel.
+#include <algorithm>
+#include <cmath>
+
+#include "fft_device.cuh"
 #include "fused.h"
 
 namespace ks {
 
-std::unique_ptr<FusedOps> make_fused_ops(const HostGeometry&, const DevTables<float>&, int, DeviceArena&) {
-  return nullptr;
+namespace {
+
+constexpr int Z_THREADS = 512;
+constexpr int Z_CAP = 4096;        // elements per line-FFT call in the column kernels
+constexpr int P_THREADS = 1024;
+constexpr int P_CAP = 8192;        // elements per line-FFT call in the plane kernel
+
+struct PlaneNL {
+  const int* pt_off;     // [N+1] covered points of plane z
+  const int* pt_xy;      // jx*N + jy
+  const int* ent_off;    // [npts+1]
+  const int* ent_proj;   // first projector row (atom * nproj)
+  const float* ent_beta; // [nent][nproj]
+  int nproj;
+};
+
+__global__ void __launch_bounds__(Z_THREADS) k_zinv(const float2* __restrict__ psi, int nG, const int* __restrict__ g_col,
+                                                    const int* __restrict__ g_z, const int* __restrict__ col_off,
+                                                    int ncols, int N, int CT, float2* __restrict__ colbuf, FftPlan plan,
+                                                    const float2* __restrict__ twg) {
+  extern __shared__ float2 zsm[];
+  float2* tw = zsm;
+  float2* s = zsm + N;
+  const int ld = N + 1;
+  const int b = blockIdx.y;
+  const int c0 = blockIdx.x * CT;
+  const int nl = min(CT, ncols - c0);
+  for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = twg[t];
+  for (int e = threadIdx.x; e < nl * ld; e += blockDim.x) s[e] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const int g0 = col_off[c0];
+  const int g1 = (c0 + nl < ncols) ? col_off[c0 + nl] : nG;
+  const float2* in = psi + (size_t)b * nG;
+  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) s[(g_col[g] - c0) * ld + g_z[g]] = in[g];
+  __syncthreads();
+  fft_lines_grouped<Z_THREADS, Z_CAP, false>(s, nl, ld, 1, N, plan, tw, +1);
+  float2* out = colbuf + (size_t)b * N * ncols + c0;
+  for (int e = threadIdx.x; e < N * nl; e += blockDim.x) {
+    const int z = e / nl, l = e - z * nl;
+    out[(size_t)z * ncols + l] = s[l * ld + z];
+  }
+}
+
+__global__ void __launch_bounds__(Z_THREADS) k_zfwd(const float2* __restrict__ colbuf, const float2* __restrict__ psi,
+                                                    float2* __restrict__ hpsi, int nG, const int* __restrict__ g_col,
+                                                    const int* __restrict__ g_z, const int* __restrict__ col_off,
+                                                    const float* __restrict__ g2half, int ncols, int N, int CT,
+                                                    float scale, FftPlan plan, const float2* __restrict__ twg) {
+  extern __shared__ float2 zsm[];
+  float2* tw = zsm;
+  float2* s = zsm + N;
+  const int ld = N + 1;
+  const int b = blockIdx.y;
+  const int c0 = blockIdx.x * CT;
+  const int nl = min(CT, ncols - c0);
+  for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = twg[t];
+  const float2* in = colbuf + (size_t)b * N * ncols + c0;
+  for (int e = threadIdx.x; e < N * nl; e += blockDim.x) {
+    const int z = e / nl, l = e - z * nl;
+    s[l * ld + z] = in[(size_t)z * ncols + l];
+  }
+  __syncthreads();
+  fft_lines_grouped<Z_THREADS, Z_CAP, false>(s, nl, ld, 1, N, plan, tw, -1);
+  const int g0 = col_off[c0];
+  const int g1 = (c0 + nl < ncols) ? col_off[c0 + nl] : nG;
+  const size_t off = (size_t)b * nG;
+  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+    const float2 u = s[(g_col[g] - c0) * ld + g_z[g]];
+    const float2 p = psi[off + g];
+    const float k = g2half[g];
+    hpsi[off + g] = make_float2(u.x * scale + k * p.x, u.y * scale + k * p.y);
+  }
+}
+
+// Inverse (x, y) transform of one plane held as scattered columns.
+__device__ __forceinline__ void plane_inverse(float2* P, int ld, int N, int xr, const FftPlan& plan, const float2* tw) {
+  // rows jx in [0, xr] and [N - xr, N - 1] hold columns: y-lines of those rows
+  fft_lines_grouped<P_THREADS, P_CAP, false>(P, xr + 1, ld, 1, N, plan, tw, +1);
+  if (xr > 0) fft_lines_grouped<P_THREADS, P_CAP, false>(P + (N - xr) * ld, xr, ld, 1, N, plan, tw, +1);
+  // x-lines: every column jy, element jx at P[jx*ld + jy]
+  fft_lines_grouped<P_THREADS, P_CAP, true>(P, N, 1, ld, N, plan, tw, +1);
+}
+
+__global__ void __launch_bounds__(P_THREADS, 1)
+    k_plane(const float2* __restrict__ colbuf1, float2* __restrict__ colbuf2, int ncols, const int* __restrict__ col_xy,
+            int N, int xr, const float* __restrict__ vplane, PlaneNL nl, const float2* __restrict__ pf, int nprojtot,
+            FftPlan plan, const float2* __restrict__ twg) {
+  extern __shared__ float2 psm[];
+  float2* tw = psm;
+  float2* P = psm + N;
+  const int ld = N + 1;
+  const int z = blockIdx.x, b = blockIdx.y;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = twg[t];
+  for (int e = threadIdx.x; e < N * ld; e += blockDim.x) P[e] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const size_t row = ((size_t)b * N + z) * ncols;
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    const int xy = col_xy[c];
+    const int jx = xy / N, jy = xy - jx * N;
+    P[jx * ld + jy] = colbuf1[row + c];
+  }
+  __syncthreads();
+  plane_inverse(P, ld, N, xr, plan, tw);
+  // u = V psi
+  const float* v = vplane + (size_t)z * N * N;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int jx = e / N, jy = e - jx * N;
+    const float vv = v[e];
+    float2 u = P[jx * ld + jy];
+    P[jx * ld + jy] = make_float2(u.x * vv, u.y * vv);
+  }
+  __syncthreads();
+  // + sum_{I,l} D Omega^{1/2} beta_Il p_Il  (pf already carries D Omega^{1/2})
+  if (nprojtot > 0) {
+    const float2* pb = pf + (size_t)b * nprojtot;
+    for (int pt = nl.pt_off[z] + threadIdx.x; pt < nl.pt_off[z + 1]; pt += blockDim.x) {
+      float ax = 0.f, ay = 0.f;
+      for (int e = nl.ent_off[pt]; e < nl.ent_off[pt + 1]; ++e) {
+        const float2* pp = pb + nl.ent_proj[e];
+        const float* bt = nl.ent_beta + (size_t)e * nl.nproj;
+        for (int l = 0; l < nl.nproj; ++l) {
+          ax += bt[l] * pp[l].x;
+          ay += bt[l] * pp[l].y;
+        }
+      }
+      const int xy = nl.pt_xy[pt];
+      const int jx = xy / N, jy = xy - jx * N;
+      float2 u = P[jx * ld + jy];
+      P[jx * ld + jy] = make_float2(u.x + ax, u.y + ay);
+    }
+  }
+  __syncthreads();
+  // forward x-lines (all), then y-lines of the rows that hold columns
+  fft_lines_grouped<P_THREADS, P_CAP, true>(P, N, 1, ld, N, plan, tw, -1);
+  fft_lines_grouped<P_THREADS, P_CAP, false>(P, xr + 1, ld, 1, N, plan, tw, -1);
+  if (xr > 0) fft_lines_grouped<P_THREADS, P_CAP, false>(P + (N - xr) * ld, xr, ld, 1, N, plan, tw, -1);
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    const int xy = col_xy[c];
+    const int jx = xy / N, jy = xy - jx * N;
+    colbuf2[row + c] = P[jx * ld + jy];
+  }
+}
+
+// Density partial sums: one (z-plane, chunk of states) per CTA, states in order.
+constexpr int D_MAXACC = 16;   // plane points per thread (N^2 <= 16 * 1024)
+
+__global__ void __launch_bounds__(P_THREADS, 1)
+    k_plane_density(const float2* __restrict__ colbuf1, int ncols, const int* __restrict__ col_xy, int N, int xr,
+                    int nstates, int chunk, const double* __restrict__ occ, float scale, float* __restrict__ partial,
+                    FftPlan plan, const float2* __restrict__ twg) {
+  extern __shared__ float2 psm[];
+  float2* tw = psm;
+  float2* P = psm + N;
+  const int ld = N + 1;
+  const int z = blockIdx.x, ch = blockIdx.y;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = twg[t];
+  float acc[D_MAXACC];
+#pragma unroll
+  for (int k = 0; k < D_MAXACC; ++k) acc[k] = 0.f;
+  const int b0 = ch * chunk, b1 = min(nstates, b0 + chunk);
+  for (int b = b0; b < b1; ++b) {
+    for (int e = threadIdx.x; e < N * ld; e += blockDim.x) P[e] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const size_t row = ((size_t)b * N + z) * ncols;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+      const int xy = col_xy[c];
+      const int jx = xy / N, jy = xy - jx * N;
+      P[jx * ld + jy] = colbuf1[row + c];
+    }
+    __syncthreads();
+    plane_inverse(P, ld, N, xr, plan, tw);
+    const float f = (float)occ[b];
+#pragma unroll
+    for (int k = 0; k < D_MAXACC; ++k) {
+      const int e = threadIdx.x + k * P_THREADS;
+      if (e < N * N) {
+        const int jx = e / N, jy = e - jx * N;
+        const float2 u = P[jx * ld + jy];
+        acc[k] += f * (u.x * u.x + u.y * u.y);
+      }
+    }
+    __syncthreads();
+  }
+  float* out = partial + ((size_t)ch * N + z) * N * N;
+#pragma unroll
+  for (int k = 0; k < D_MAXACC; ++k) {
+    const int e = threadIdx.x + k * P_THREADS;
+    if (e < N * N) out[e] = acc[k] * scale;
+  }
+}
+
+// n[(jx*N + jy)*N + z] = sum_ch partial[ch][z][jx*N + jy]
+__global__ void k_density_reduce(const float* __restrict__ partial, int nch, int N, float* __restrict__ n) {
+  const size_t N3 = (size_t)N * N * N;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
+    const int z = (int)(j % N);
+    const size_t xy = j / N;
+    float s = 0.f;
+    for (int ch = 0; ch < nch; ++ch) s += partial[((size_t)ch * N + z) * N * N + xy];
+    n[j] = s;
+  }
+}
+
+// vplane[z][jx*N + jy] = v[(jx*N + jy)*N + z]
+__global__ void k_to_planes(const float* __restrict__ v, int N, float* __restrict__ vplane) {
+  const size_t N3 = (size_t)N * N * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N3; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t z = e / ((size_t)N * N), xy = e % ((size_t)N * N);
+    vplane[e] = v[xy * N + z];
+  }
+}
+
+// pf[b][ip] = scale * (float) pout[ip][b]
+__global__ void k_proj_to_states(const double2* __restrict__ pout, int nprojtot, int nst, float scale,
+                                 float2* __restrict__ pf) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nprojtot * nst; e += gridDim.x * blockDim.x) {
+    const int b = e / nprojtot, ip = e - b * nprojtot;
+    const double2 v = pout[(size_t)ip * nst + b];
+    pf[e] = make_float2((float)(v.x * scale), (float)(v.y * scale));
+  }
+}
+
+// Setup: projector grid functions -> sphere coefficients (FP64), then rounded to complex64.
+__global__ void k_scatter_projectors(const int* __restrict__ sph_off, const int* __restrict__ sph_idx,
+                                     const double* __restrict__ beta, int nproj, int p0, int np, size_t N3,
+                                     double2* __restrict__ grid) {
+  const int k = blockIdx.y;            // projector row p0 + k = atom * nproj + l
+  const int row = p0 + k;
+  const int atom = row / nproj, l = row % nproj;
+  for (int p = sph_off[atom] + blockIdx.x * blockDim.x + threadIdx.x; p < sph_off[atom + 1];
+       p += gridDim.x * blockDim.x)
+    grid[k * N3 + sph_idx[p]] = make_double2(beta[(size_t)p * nproj + l], 0.0);
+  (void)np;
+}
+
+__global__ void k_gather_projectors(const double2* __restrict__ grid, const int* __restrict__ gidx, int nG, size_t N3,
+                                    double scale, float2* __restrict__ B) {
+  const int k = blockIdx.y;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nG; g += gridDim.x * blockDim.x) {
+    const double2 v = grid[k * N3 + gidx[g]];
+    B[(size_t)k * nG + g] = make_float2((float)(v.x * scale), (float)(v.y * scale));
+  }
+}
+
+unsigned nblk(size_t n, int t, unsigned cap = 4096) {
+  size_t b = (n + t - 1) / t;
+  return (unsigned)std::max<size_t>(1, std::min<size_t>(b, cap));
+}
+
+class FusedImpl final : public FusedOps {
+ public:
+  FusedImpl(const HostGeometry& g, const DevTables<float>& t, int nstates, DeviceArena& arena, StageProfiler& prof,
+            int* err)
+      : g_(g), t_(t), ns_(nstates), arena_(arena), prof_(prof), err_(err) {
+    N_ = g.N;
+    ncols_ = g.ncols;
+    nprojtot_ = g.natoms * g.nproj;
+    plan_ = make_plan8(N_);
+    const size_t N3 = (size_t)N_ * N_ * N_;
+    // per-G column id and z
+    std::vector<int> gcol(g.nG), gz(g.nG);
+    for (int c = 0; c < g.ncols; ++c) {
+      const int cnt = 2 * g.col_half[c] + 1;
+      for (int k = 0; k < cnt; ++k) {
+        gcol[g.col_off[c] + k] = c;
+        gz[g.col_off[c] + k] = g.gidx[g.col_off[c] + k] % N_;
+      }
+    }
+    g_col_ = upload(gcol);
+    g_z_ = upload(gz);
+    // columns per CTA in the z kernels: all of a column tile's lines in one FFT call
+    CT_ = std::max(1, std::min(32, Z_CAP / N_));
+    // per-plane projector lists
+    std::vector<int> pt_off(N_ + 1, 0), pt_xy, ent_off(1, 0), ent_proj;
+    std::vector<float> ent_beta;
+    {
+      std::vector<std::vector<int>> byz(N_);
+      for (size_t c = 0; c < g.cov_idx.size(); ++c) byz[g.cov_idx[c] % N_].push_back((int)c);
+      for (int z = 0; z < N_; ++z) {
+        for (int c : byz[z]) {
+          pt_xy.push_back(g.cov_idx[c] / N_);
+          for (int e = g.cov_off[c]; e < g.cov_off[c + 1]; ++e) {
+            const int p = g.cov_ent[e];
+            ent_proj.push_back(g.sph_atom[p] * g.nproj);
+            for (int l = 0; l < g.nproj; ++l) ent_beta.push_back((float)g.sph_beta[(size_t)p * g.nproj + l]);
+          }
+          ent_off.push_back((int)ent_proj.size());
+        }
+        pt_off[z + 1] = (int)pt_xy.size();
+      }
+    }
+    nl_.pt_off = upload(pt_off);
+    nl_.pt_xy = upload(pt_xy);
+    nl_.ent_off = upload(ent_off);
+    nl_.ent_proj = upload(ent_proj);
+    nl_.ent_beta = upload(ent_beta);
+    nl_.nproj = g.nproj;
+    // buffers
+    colbuf1_ = alloc<float2>((size_t)ns_ * N_ * ncols_);
+    colbuf2_ = alloc<float2>((size_t)ns_ * N_ * ncols_);
+    vplane_ = alloc<float>(N3);
+    if (nprojtot_ > 0) {
+      B_ = alloc<float2>((size_t)nprojtot_ * g.nG);
+      pout_ = alloc<double2>((size_t)nprojtot_ * ns_);
+      pf_ = alloc<float2>((size_t)nprojtot_ * ns_);
+      part_elems_ = std::max<size_t>(tc_overlap_part_elems(nprojtot_, ns_), 4096);
+      part_ = alloc<double2>(part_elems_);
+      build_projector_block();
+    }
+    dchunk_ = std::max(1, std::min(32, (ns_ + 7) / 8));
+    nch_max_ = (ns_ + dchunk_ - 1) / dchunk_;
+    dpartial_ = alloc<float>((size_t)nch_max_ * N3);
+    set_smem_limits();
+  }
+
+  void apply_h(const float2* psi, float2* hpsi, int n, const float* v, cudaStream_t s) override {
+    const size_t N3 = (size_t)N_ * N_ * N_;
+    k_to_planes<<<nblk(N3, 256), 256, 0, s>>>(v, N_, vplane_);
+    KS_CHECK_LAUNCH();
+    if (nprojtot_ > 0) {
+      ProfScope ps(prof_, "proj_gemm", s);
+      tc_overlap(B_, g_.nG, psi, g_.nG, nprojtot_, n, g_.nG, part_, part_elems_, pout_, err_, s);
+      const float scale = (float)(g_.D * std::sqrt(g_.omega));
+      k_proj_to_states<<<nblk((size_t)nprojtot_ * n, 256), 256, 0, s>>>(pout_, nprojtot_, n, scale, pf_);
+      KS_CHECK_LAUNCH();
+    }
+    zinv(psi, n, s);
+    {
+      ProfScope ps(prof_, "plane", s);
+      const size_t smem = (size_t)(N_ + N_ * (N_ + 1)) * sizeof(float2);
+      dim3 grid(N_, n);
+      k_plane<<<grid, P_THREADS, smem, s>>>(colbuf1_, colbuf2_, ncols_, t_.col_xy, N_, g_.xr, vplane_, nl_, pf_,
+                                            nprojtot_, plan_, t_.tw);
+      KS_CHECK_LAUNCH();
+    }
+    {
+      ProfScope ps(prof_, "zfwd", s);
+      const size_t smem = (size_t)(N_ + CT_ * (N_ + 1)) * sizeof(float2);
+      dim3 grid((ncols_ + CT_ - 1) / CT_, n);
+      k_zfwd<<<grid, Z_THREADS, smem, s>>>(colbuf2_, psi, hpsi, g_.nG, g_col_, g_z_, t_.col_off, t_.g2half, ncols_, N_,
+                                           CT_, (float)(1.0 / double(N3)), plan_, t_.tw);
+      KS_CHECK_LAUNCH();
+    }
+  }
+
+  void density(const float2* psi, int n, const double* occ, float* nout, cudaStream_t s) override {
+    zinv(psi, n, s);
+    ProfScope ps(prof_, "plane_density", s);
+    const int nch = (n + dchunk_ - 1) / dchunk_;
+    const size_t smem = (size_t)(N_ + N_ * (N_ + 1)) * sizeof(float2);
+    dim3 grid(N_, nch);
+    k_plane_density<<<grid, P_THREADS, smem, s>>>(colbuf1_, ncols_, t_.col_xy, N_, g_.xr, n, dchunk_, occ,
+                                                  (float)(1.0 / g_.omega), dpartial_, plan_, t_.tw);
+    KS_CHECK_LAUNCH();
+    k_density_reduce<<<nblk((size_t)N_ * N_ * N_, 256), 256, 0, s>>>(dpartial_, nch, N_, nout);
+    KS_CHECK_LAUNCH();
+  }
+
+ private:
+  void zinv(const float2* psi, int n, cudaStream_t s) {
+    ProfScope ps(prof_, "zinv", s);
+    const size_t smem = (size_t)(N_ + CT_ * (N_ + 1)) * sizeof(float2);
+    dim3 grid((ncols_ + CT_ - 1) / CT_, n);
+    k_zinv<<<grid, Z_THREADS, smem, s>>>(psi, g_.nG, g_col_, g_z_, t_.col_off, ncols_, N_, CT_, colbuf1_, plan_, t_.tw);
+    KS_CHECK_LAUNCH();
+  }
+
+  void set_smem_limits() {
+    const int plane = (int)((N_ + N_ * (N_ + 1)) * sizeof(float2));
+    KS_CUDA(cudaFuncSetAttribute(k_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(plane, 48 * 1024)));
+    KS_CUDA(cudaFuncSetAttribute(k_plane_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 std::max(plane, 48 * 1024)));
+  }
+
+  // B[atom*nproj + l][G] = c_G[beta_Il] = Omega^{1/2} N^-3 sum_j exp(-iG.r_j) beta_Il(r_j), FP64 FFT.
+  void build_projector_block() {
+    const int N = N_;
+    const size_t N3 = (size_t)N * N * N;
+    const int batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)nprojtot_, (size_t(512) << 20) / (N3 * 16)));
+    double2* grid = nullptr;
+    int* sph_off = nullptr;
+    int* sph_idx = nullptr;
+    double* beta = nullptr;
+    double2* tw = nullptr;
+    KS_CUDA(cudaMalloc(&grid, (size_t)batch * N3 * sizeof(double2)));
+    KS_CUDA(cudaMalloc(&sph_off, g_.sph_off.size() * sizeof(int)));
+    KS_CUDA(cudaMalloc(&sph_idx, std::max<size_t>(1, g_.sph_idx.size()) * sizeof(int)));
+    KS_CUDA(cudaMalloc(&beta, std::max<size_t>(1, g_.sph_beta.size()) * sizeof(double)));
+    KS_CUDA(cudaMalloc(&tw, N * sizeof(double2)));
+    KS_CUDA(cudaMemcpy(sph_off, g_.sph_off.data(), g_.sph_off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    KS_CUDA(cudaMemcpy(sph_idx, g_.sph_idx.data(), g_.sph_idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    KS_CUDA(cudaMemcpy(beta, g_.sph_beta.data(), g_.sph_beta.size() * sizeof(double), cudaMemcpyHostToDevice));
+    KS_CUDA(cudaMemcpy(tw, g_.tw.data(), N * sizeof(double2), cudaMemcpyHostToDevice));
+    const double scale = std::sqrt(g_.omega) / double(N3);
+    for (int p0 = 0; p0 < nprojtot_; p0 += batch) {
+      const int nb = std::min(batch, nprojtot_ - p0);
+      KS_CUDA(cudaMemset(grid, 0, (size_t)nb * N3 * sizeof(double2)));
+      k_scatter_projectors<<<dim3(8, nb), 256>>>(sph_off, sph_idx, beta, g_.nproj, p0, nb, N3, grid);
+      KS_CHECK_LAUNCH();
+      for (int ax = 2; ax >= 0; --ax) fft_axis<double>(grid, nb, N, ax, -1, tw, 0);
+      k_gather_projectors<<<dim3(nblk(g_.nG, 256, 1024), nb), 256>>>(grid, t_.gidx, g_.nG, N3, scale,
+                                                                    B_ + (size_t)p0 * g_.nG);
+      KS_CHECK_LAUNCH();
+    }
+    KS_CUDA(cudaDeviceSynchronize());
+    cudaFree(grid);
+    cudaFree(sph_off);
+    cudaFree(sph_idx);
+    cudaFree(beta);
+    cudaFree(tw);
+  }
+
+  template <typename U> U* alloc(size_t n) { return static_cast<U*>(arena_.alloc(n * sizeof(U))); }
+  template <typename U> const U* upload(const std::vector<U>& v) {
+    U* p = alloc<U>(std::max<size_t>(v.size(), 1));
+    if (!v.empty()) KS_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice));
+    return p;
+  }
+
+  const HostGeometry& g_;
+  DevTables<float> t_;
+  int ns_;
+  DeviceArena& arena_;
+  StageProfiler& prof_;
+  int* err_;
+  int N_ = 0, ncols_ = 0, nprojtot_ = 0, CT_ = 32;
+  FftPlan plan_{};
+  const int* g_col_ = nullptr;
+  const int* g_z_ = nullptr;
+  PlaneNL nl_{};
+  float2* colbuf1_ = nullptr;
+  float2* colbuf2_ = nullptr;
+  float* vplane_ = nullptr;
+  float2* B_ = nullptr;
+  double2* pout_ = nullptr;
+  float2* pf_ = nullptr;
+  double2* part_ = nullptr;
+  size_t part_elems_ = 0;
+  int dchunk_ = 1, nch_max_ = 1;
+  float* dpartial_ = nullptr;
+};
+
+}  // namespace
+
+std::unique_ptr<FusedOps> make_fused_ops(const HostGeometry& g, const DevTables<float>& t, int nstates,
+                                         DeviceArena& arena, StageProfiler& prof, int* err) {
+  return std::unique_ptr<FusedOps>(new FusedImpl(g, t, nstates, arena, prof, err));
 }
 
 }  // namespace ks

@@ -21,16 +21,17 @@ class FusedOps {
 };
 
 std::unique_ptr<FusedOps> make_fused_ops(const HostGeometry& g, const DevTables<float>& t, int nstates,
-                                         DeviceArena& arena);
+                                         DeviceArena& arena, StageProfiler& prof, int* err);
 
 template <typename T>
-inline std::unique_ptr<FusedOps> make_fused_for(const HostGeometry&, const DevTables<T>&, int, DeviceArena&) {
+inline std::unique_ptr<FusedOps> make_fused_for(const HostGeometry&, const DevTables<T>&, int, DeviceArena&,
+                                                StageProfiler&, int*) {
   return nullptr;
 }
 template <>
 inline std::unique_ptr<FusedOps> make_fused_for<float>(const HostGeometry& g, const DevTables<float>& t, int n,
-                                                       DeviceArena& a) {
-  return make_fused_ops(g, t, n, a);
+                                                       DeviceArena& a, StageProfiler& prof, int* err) {
+  return make_fused_ops(g, t, n, a, prof, err);
 }
 
 }  // namespace ks

@@ -91,5 +91,19 @@ void cholesky_inverse_tol(double2* A, double2* M, int n, double tol, int* status
 // Hermitian eigen-decomposition of A (destroyed) by cyclic Jacobi; eig ascending, rows of
 // Vt = eigenvectors (largest-magnitude component real positive).  `V` is n*n workspace.
 void jacobi_eigh(double2* A, double2* V, double* eig, double2* Vt, int n, cudaStream_t s);
+// Mixed: FP32 Jacobi in shared memory (n <= 128) on a copy of the FP64 Hermitian A (kept),
+// eigenvalues = FP64 Rayleigh quotients of the FP32 vectors on A; same outputs as jacobi_eigh.
+// V is n*n workspace, lam n doubles of workspace.
+void jacobi_eigh_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, int n, cudaStream_t s);
+
+// ---- tensor-core GEMMs (tc_gemm.cu), split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulation ---------
+// Same contract as gemm_cn<float> / rotate<float>; err receives 1 if a bounded wait expired.
+void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n, int K, double2* part,
+                size_t part_elems, double2* out, int* err, cudaStream_t s);
+// Partial-buffer elements tc_overlap wants for an m x n output (one wave of CTAs).
+size_t tc_overlap_part_elems(int m, int n);
+void tc_rotate(const double2* M, int nin, const float2* X, int ldx, float2* Y, int ldy, int m, int K, void* work,
+               size_t work_bytes, int* err, cudaStream_t s);
+size_t tc_rotation_workspace_bytes(int m, int nin);
 
 }  // namespace ks

@@ -1,0 +1,476 @@
+// Tensor-core (tcgen05, sm_103a) complex GEMMs of the mixed path, split-BF16:
+// every FP32 operand x is split into hi = bf16(x) and lo = bf16(x - hi), and each real
+// product is accumulated as hi*hi + hi*lo + lo*hi in FP32 in tensor memory (TMEM).
+//
+//   tc_overlap:  out[i][j] = sum_k conj(A[i][k]) B[j][k]       (Gram S, H_sub, projections)
+//   tc_rotate:   Y[i][k]   = sum_j M[i][j] X[j][k]             (CholQR and Rayleigh-Ritz rotations)
+//
+// Complex arithmetic as real GEMMs.  Overlap: A is read as a real row of interleaved
+// (re, im); B contributes two real rows per complex row, (re, im) and (im, -re), so the
+// accumulator column 2j holds Re out[i][j] and column 2j+1 holds Im out[i][j].  Rotation:
+// the MMA rows are grid coefficients k, the reduction runs over (j, re|im) and B holds the
+// four real blocks of M, so column 2i is Re Y[i][k] and 2i+1 is Im Y[i][k].
+//
+// One CTA computes a 128 x 256 real tile (M = 128 rows, N = 256 columns) with a two-stage
+// shared-memory ring: all 256 threads load and split the next K-chunk while one thread
+// issues the MMAs of the current one; tcgen05.commit arrives on a per-stage mbarrier.
+// Operand tiles use the K-major no-swizzle canonical layout (8-row x 16-byte core
+// matrices; LBO = distance between core matrices along K, SBO = along rows).
+// Every mbarrier wait is bounded; on expiry the kernel records an error code and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace ks {
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr int TC_M = 128;           // MMA rows
+constexpr int TC_N = 256;           // MMA columns
+constexpr int TC_KR = 64;           // real K per stage (bf16 elements)
+constexpr int TC_KC = TC_KR / 2;    // complex K per stage
+constexpr int A_BYTES = TC_M * TC_KR * 2;          // one bf16 tile (hi or lo) of A: 16 KB
+constexpr int B_BYTES = TC_N * TC_KR * 2;          // one bf16 tile of B: 32 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // hi + lo of A and B: 96 KB
+constexpr int NSTAGE = 2;
+constexpr int TC_SMEM = NSTAGE * STAGE_BYTES + 1024;     // + barriers / TMEM slot / alignment
+constexpr uint32_t TMEM_COLS = 256;
+constexpr long WAIT_LIMIT = 1L << 28;                    // spin bound of every mbarrier wait
+
+// ---- PTX wrappers -----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, P1;\n\t}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait; false if the limit expired.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (long it = 0; it < WAIT_LIMIT; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 16 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---- descriptors ------------------------------------------------------------------------------
+// Shared-memory matrix descriptor: start >> 4 [0,14), LBO >> 4 [16,30), SBO >> 4 [32,46),
+// fixed 0b001 at [46,49), base offset 0, relative LBO, no swizzle.
+__host__ __device__ constexpr uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32 [4,6), A = B = BF16 [7,10) [10,13), both K-major,
+// N >> 3 at [17,23), M >> 4 at [24,29).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (row, k) in a K-major no-swizzle tile with R rows and TC_KR columns:
+// core matrix (row/8, k/8) at (k/8) * R * 16 + (row/8) * 128; inside it, row%8 * 16 + k%8 * 2.
+__host__ __device__ constexpr uint32_t tile_off(int R, int row, int k) {
+  return (uint32_t)((k >> 3) * R * 16 + (row >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Split 8 floats into hi and lo bf16 rows of 16 bytes each.
+__device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
+  float h[8], l[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(x[i]);
+    h[i] = __bfloat162float(b);
+    l[i] = x[i] - h[i];
+  }
+  hi = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
+  lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+}
+
+__device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+
+struct StageAddr {
+  uint32_t a_hi, a_lo, b_hi, b_lo;
+};
+__device__ __forceinline__ StageAddr stage_addr(uint32_t base, int st) {
+  const uint32_t s = base + st * STAGE_BYTES;
+  return StageAddr{s, s + A_BYTES, s + 2 * A_BYTES, s + 2 * A_BYTES + B_BYTES};
+}
+
+// Issue the 3 x 4 MMAs of one stage (K = 64 real = 4 steps of 16).
+__device__ __forceinline__ void issue_stage(const StageAddr& sa, uint32_t tmem_d, bool first) {
+  constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+  constexpr uint32_t a_lbo = TC_M * 16, b_lbo = TC_N * 16;
+#pragma unroll
+  for (int s = 0; s < TC_KR / 16; ++s) {
+    const uint32_t ao = 2 * s * a_lbo, bo = 2 * s * b_lbo;
+    const uint64_t ahi = smem_desc(sa.a_hi + ao, a_lbo, 128), alo = smem_desc(sa.a_lo + ao, a_lbo, 128);
+    const uint64_t bhi = smem_desc(sa.b_hi + bo, b_lbo, 128), blo = smem_desc(sa.b_lo + bo, b_lbo, 128);
+    mma_bf16(tmem_d, ahi, bhi, idesc, (first && s == 0) ? 0u : 1u);
+    mma_bf16(tmem_d, ahi, blo, idesc, 1u);
+    mma_bf16(tmem_d, alo, bhi, idesc, 1u);
+  }
+}
+
+// Common prologue: barriers and TMEM.  Returns the TMEM base address.
+__device__ __forceinline__ uint32_t tc_setup(unsigned char* smem, uint32_t& bar0) {
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + NSTAGE * STAGE_BYTES + 64);
+  bar0 = smem_u32(bars);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NSTAGE; ++i) mbar_init(bar0 + 8 * i, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(smem_u32(slot), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return *slot;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Overlap: part[ks][i][j] = sum_{k in chunk ks} conj(A[i][k]) B[j][k], tile 128 (i) x 128 (j).
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_overlap(const float2* __restrict__ A, int lda, const float2* __restrict__ B, int ldb, int m, int n, int K,
+                 int kchunk, double2* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  const uint32_t base = smem_u32(tsm);
+  uint32_t bar0;
+  const uint32_t tmem = tc_setup(tsm, bar0);
+  const int i0 = blockIdx.y * TC_M, j0 = blockIdx.x * (TC_N / 2);
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int nk = (kend - kbeg + TC_KC - 1) / TC_KC;
+  const int t = threadIdx.x;
+  const int kq = t & 7;            // 4 complex = 8 real K values = one core-matrix row
+  bool ok = true;
+  for (int it = 0; it < nk; ++it) {
+    const int st = it & 1;
+    if (it >= NSTAGE) {
+      // every thread waits; the CTA continues only if all of them saw the stage free
+      ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * st, ((it - NSTAGE) / NSTAGE) & 1)) != 0;
+      if (!ok) break;
+    }
+    const StageAddr sa = stage_addr(base, st);
+    const int kc = kbeg + it * TC_KC + 4 * kq;
+    // A rows
+    for (int r = t >> 3; r < TC_M; r += TC_THREADS / 8) {
+      float x[8];
+      const int i = i0 + r;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = kc + q;
+        const float2 v = (i < m && k < kend) ? A[(size_t)i * lda + k] : make_float2(0.f, 0.f);
+        x[2 * q] = v.x;
+        x[2 * q + 1] = v.y;
+      }
+      uint4 hi, lo;
+      split8(x, hi, lo);
+      const uint32_t o = tile_off(TC_M, r, 8 * kq);
+      sts128(sa.a_hi + o, hi);
+      sts128(sa.a_lo + o, lo);
+    }
+    // B rows: 2j <- (re, im), 2j+1 <- (im, -re)
+    for (int r = t >> 3; r < TC_N / 2; r += TC_THREADS / 8) {
+      float x[8], y[8];
+      const int j = j0 + r;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = kc + q;
+        const float2 v = (j < n && k < kend) ? B[(size_t)j * ldb + k] : make_float2(0.f, 0.f);
+        x[2 * q] = v.x;
+        x[2 * q + 1] = v.y;
+        y[2 * q] = v.y;
+        y[2 * q + 1] = -v.x;
+      }
+      uint4 hi, lo;
+      split8(x, hi, lo);
+      uint32_t o = tile_off(TC_N, 2 * r, 8 * kq);
+      sts128(sa.b_hi + o, hi);
+      sts128(sa.b_lo + o, lo);
+      split8(y, hi, lo);
+      o = tile_off(TC_N, 2 * r + 1, 8 * kq);
+      sts128(sa.b_hi + o, hi);
+      sts128(sa.b_lo + o, lo);
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      issue_stage(sa, tmem, it == 0);
+      mma_commit(bar0 + 8 * st);
+    }
+  }
+  // wait for the last commit (it covers every earlier MMA of this thread)
+  if (ok && nk > 0) ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ((nk - 1) & 1), ((nk - 1) / NSTAGE) & 1)) != 0;
+  if (!ok && t == 0) atomicExch(err, 1);
+  tc_fence_after();
+  // epilogue: warp w reads TMEM lanes 32*(w%4).., columns [128*(w/4), +128)
+  const int w = t >> 5, lane = t & 31;
+  const int row = 32 * (w & 3) + lane;
+  const int i = i0 + row;
+  if (ok) {
+    for (int c0 = 128 * (w >> 2); c0 < 128 * (w >> 2) + 128; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + c0, v);
+      if (i < m && nk > 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = j0 + c0 / 2 + q;
+          if (j < n) part[((size_t)blockIdx.z * m + i) * n + j] = make_double2((double)v[2 * q], (double)v[2 * q + 1]);
+        }
+      }
+      if (i < m && nk == 0) {
+        for (int q = 0; q < 8; ++q) {
+          const int j = j0 + c0 / 2 + q;
+          if (j < n) part[((size_t)blockIdx.z * m + i) * n + j] = make_double2(0.0, 0.0);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (w == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Rotation: Y[i][k] = sum_j M[i][j] X[j][k].  CTA tile: 128 grid columns k x 128 outputs i.
+// Mb holds M pre-split into the B-tile images, per (i-tile, j-chunk): hi tile then lo tile.
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_rotate(const uint4* __restrict__ Mb, int njc, const float2* __restrict__ X, int ldx, float2* __restrict__ Y,
+                int ldy, int m, int nin, int K, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  const uint32_t base = smem_u32(tsm);
+  uint32_t bar0;
+  const uint32_t tmem = tc_setup(tsm, bar0);
+  const int k0 = blockIdx.x * TC_M;
+  const int it_i = blockIdx.y;
+  const int i0 = it_i * (TC_N / 2);
+  const int t = threadIdx.x;
+  const int r = t & (TC_M - 1);          // grid coefficient row of the A tile
+  const int half = t >> 7;               // which 16 of the 32 states of a chunk
+  const int kk = k0 + r;
+  bool ok = true;
+  for (int it = 0; it < njc; ++it) {
+    const int st = it & 1;
+    if (it >= NSTAGE) {
+      // every thread waits; the CTA continues only if all of them saw the stage free
+      ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * st, ((it - NSTAGE) / NSTAGE) & 1)) != 0;
+      if (!ok) break;
+    }
+    const StageAddr sa = stage_addr(base, st);
+    const int jc0 = it * TC_KC;
+    // A: row r = grid coefficient kk; real K: [0,32) re of states jc0.., [32,64) im
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int jb = 2 * half + g;       // group of 8 states
+      float re[8], im[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = jc0 + 8 * jb + q;
+        const float2 v = (j < nin && kk < K) ? X[(size_t)j * ldx + kk] : make_float2(0.f, 0.f);
+        re[q] = v.x;
+        im[q] = v.y;
+      }
+      uint4 hi, lo;
+      split8(re, hi, lo);
+      uint32_t o = tile_off(TC_M, r, 8 * jb);
+      sts128(sa.a_hi + o, hi);
+      sts128(sa.a_lo + o, lo);
+      split8(im, hi, lo);
+      o = tile_off(TC_M, r, 32 + 8 * jb);
+      sts128(sa.a_hi + o, hi);
+      sts128(sa.a_lo + o, lo);
+    }
+    // B: copy the pre-split images (hi then lo, B_BYTES each)
+    const uint4* src = Mb + ((size_t)it_i * njc + it) * (2 * B_BYTES / 16);
+    for (int v = t; v < 2 * B_BYTES / 16; v += TC_THREADS) sts128(sa.b_hi + 16 * v, src[v]);
+    fence_proxy_async();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      issue_stage(sa, tmem, it == 0);
+      mma_commit(bar0 + 8 * st);
+    }
+  }
+  if (ok && njc > 0) ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ((njc - 1) & 1), ((njc - 1) / NSTAGE) & 1)) != 0;
+  if (!ok && t == 0) atomicExch(err, 1);
+  tc_fence_after();
+  const int w = t >> 5, lane = t & 31;
+  const int row = 32 * (w & 3) + lane;
+  const int k = k0 + row;
+  if (ok) {
+    for (int c0 = 128 * (w >> 2); c0 < 128 * (w >> 2) + 128; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + c0, v);
+      if (k < K) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = i0 + c0 / 2 + q;
+          if (i < m) Y[(size_t)i * ldy + k] = make_float2(v[2 * q], v[2 * q + 1]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (w == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// Mb images: B row 2i (output Re Y_i) = [Re M_ij | -Im M_ij], row 2i+1 (Im Y_i) = [Im M_ij | Re M_ij]
+// over the 32 states of chunk jc (K index kk: kk < 32 -> X_re of state jc*32+kk, else X_im).
+__global__ void k_tc_prep_rotation(const double2* __restrict__ M, int m, int nin, int nit, int njc,
+                                   unsigned char* __restrict__ Mb) {
+  const size_t total = (size_t)nit * njc * TC_N * TC_KR;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int kk = (int)(e % TC_KR);
+    const int row = (int)((e / TC_KR) % TC_N);
+    const size_t tile = e / ((size_t)TC_KR * TC_N);
+    const int it_i = (int)(tile / njc), jc = (int)(tile % njc);
+    const int i = it_i * (TC_N / 2) + row / 2;
+    const int j = jc * TC_KC + (kk & 31);
+    const int part = kk >> 5;           // 0: multiplies Re X, 1: Im X
+    float x = 0.f;
+    if (i < m && j < nin) {
+      const double2 v = M[(size_t)i * nin + j];
+      if ((row & 1) == 0)
+        x = (float)(part == 0 ? v.x : -v.y);
+      else
+        x = (float)(part == 0 ? v.y : v.x);
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    unsigned char* img = Mb + tile * (2 * B_BYTES);
+    const uint32_t o = tile_off(TC_N, row, kk);
+    *reinterpret_cast<__nv_bfloat16*>(img + o) = h;
+    *reinterpret_cast<__nv_bfloat16*>(img + B_BYTES + o) = l;
+  }
+}
+
+__global__ void k_reduce_parts_tc(const double2* __restrict__ part, int nks, size_t mn, double2* __restrict__ out) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < mn; e += (size_t)gridDim.x * blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < nks; ++k) {
+      const double2 p = part[(size_t)k * mn + e];
+      s.x += p.x;
+      s.y += p.y;
+    }
+    out[e] = s;
+  }
+}
+
+bool g_attr_done = false;
+void set_attrs() {
+  if (g_attr_done) return;
+  KS_CUDA(cudaFuncSetAttribute(k_tc_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  KS_CUDA(cudaFuncSetAttribute(k_tc_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  g_attr_done = true;
+}
+
+}  // namespace
+
+size_t tc_overlap_part_elems(int m, int n) {
+  const int tm = (m + TC_M - 1) / TC_M, tn = (n + TC_N / 2 - 1) / (TC_N / 2);
+  return (size_t)m * n * (size_t)std::max(1, 148 / (tm * tn));
+}
+
+size_t tc_rotation_workspace_bytes(int m, int nin) {
+  const int nit = (m + TC_N / 2 - 1) / (TC_N / 2), njc = (nin + TC_KC - 1) / TC_KC;
+  return (size_t)nit * njc * 2 * B_BYTES;
+}
+
+void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n, int K, double2* part,
+                size_t part_elems, double2* out, int* err, cudaStream_t s) {
+  set_attrs();
+  const int tm = (m + TC_M - 1) / TC_M, tn = (n + TC_N / 2 - 1) / (TC_N / 2);
+  int ks = std::max(1, 148 / (tm * tn));
+  ks = std::min(ks, std::max(1, K / (4 * TC_KC)));
+  ks = (int)std::min<long>(ks, (long)(part_elems / ((size_t)m * n)));
+  if (ks < 1) fail(KS_ERR_ARG, "tc_overlap: partial buffer too small");
+  int kchunk = (K + ks - 1) / ks;
+  kchunk = (kchunk + TC_KC - 1) / TC_KC * TC_KC;
+  ks = (K + kchunk - 1) / kchunk;
+  dim3 g(tn, tm, ks);
+  k_tc_overlap<<<g, TC_THREADS, TC_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, part, err);
+  KS_CHECK_LAUNCH();
+  const size_t mn = (size_t)m * n;
+  k_reduce_parts_tc<<<(unsigned)std::min<size_t>((mn + 255) / 256, 1024), 256, 0, s>>>(part, ks, mn, out);
+  KS_CHECK_LAUNCH();
+}
+
+void tc_rotate(const double2* M, int nin, const float2* X, int ldx, float2* Y, int ldy, int m, int K, void* work,
+               size_t work_bytes, int* err, cudaStream_t s) {
+  set_attrs();
+  const int nit = (m + TC_N / 2 - 1) / (TC_N / 2), njc = (nin + TC_KC - 1) / TC_KC;
+  if (tc_rotation_workspace_bytes(m, nin) > work_bytes) fail(KS_ERR_ARG, "tc_rotate: workspace too small");
+  const size_t total = (size_t)nit * njc * TC_N * TC_KR;
+  k_tc_prep_rotation<<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0, s>>>(
+      M, m, nin, nit, njc, static_cast<unsigned char*>(work));
+  KS_CHECK_LAUNCH();
+  dim3 g((K + TC_M - 1) / TC_M, nit);
+  k_tc_rotate<<<g, TC_THREADS, TC_SMEM, s>>>(static_cast<const uint4*>(work), njc, X, ldx, Y, ldy, m, nin, K, err);
+  KS_CHECK_LAUNCH();
+}
+
+}  // namespace ks

@@ -238,3 +238,21 @@ def test_bad_arguments(ks):
     bad = dict(cell, nproj=2)
     with pytest.raises(ks.KsError):
         ks.Grid(bad, prec="fp64")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_orthonormalize_parity_two_tiles(ks, prec):
+    """150 states: the overlap and rotation GEMMs span two 128-row tiles with a ragged edge."""
+    cell = inputs.small_cell(14.0, 40, 3, 150, 15)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec=prec)
+    c = inputs.random_coeffs(15, 150, ref.nG)
+    g.set_states(c)
+    S = g.orthonormalize(want_S=True)
+    q_ref, S_ref = ko.cholqr(c)
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    assert np.max(np.abs(S - S_ref)) <= tol * np.max(np.abs(S_ref))
+    q = g.get_states()
+    assert rel(q, q_ref) <= (1e-11 if prec == "fp64" else 1e-4)
+    assert np.max(np.abs(ko.gram(q) - np.eye(150))) <= (1e-11 if prec == "fp64" else 1e-4)
+    g.close()
