@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
   extern __shared__ float2 jsm[];
   const int npk = n * (n + 1) / 2;
   float2* Ap = jsm;                 // packed upper triangle (i <= j)
-  float2* V = jsm + npk;            // V[i*n + j], column j = eigenvector j
+  float2* VT = jsm + npk;           // VT[j*n + i] = V[i][j]; column j of V = eigenvector j
   __shared__ int sp[JS_MAXN / 2], sq[JS_MAXN / 2];
   __shared__ float sc[JS_MAXN / 2], ss[JS_MAXN / 2];
   __shared__ float2 se[JS_MAXN / 2];
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
       const double2 h = H[e];
       Ap[pk_index(i, j, n)] = make_float2((float)h.x, i == j ? 0.f : (float)h.y);
     }
-    V[e] = make_float2(i == j ? 1.f : 0.f, 0.f);
+    VT[e] = make_float2(i == j ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
   auto block_sum_f = [&](float v) -> float {
@@ -466,15 +466,16 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
         if (q >= n) continue;
         const float c = sc[k], sv = ss[k];
         const float2 e = se[k];
-        const float2 vp = V[i * n + p], vq = V[i * n + q];
-        V[i * n + p] = fadd(fscale(vp, c), fscale(fmul(fconj(e), vq), -sv));
-        V[i * n + q] = fadd(fscale(fmul(e, vp), sv), fscale(vq, c));
+        const float2 vp = VT[p * n + i], vq = VT[q * n + i];
+        VT[p * n + i] = fadd(fscale(vp, c), fscale(fmul(fconj(e), vq), -sv));
+        VT[q * n + i] = fadd(fscale(fmul(e, vp), sv), fscale(vq, c));
       }
       __syncthreads();
     }
   }
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const float2 v = V[e];
+    const int i = e / n, j = e % n;
+    const float2 v = VT[j * n + i];
     Vout[e] = make_double2((double)v.x, (double)v.y);
   }
 }
@@ -511,6 +512,99 @@ __global__ void k_rayleigh_quotients(const double2* __restrict__ H, const double
       b += red[1][w];
     }
     lam[i] = a / b;
+  }
+}
+
+// Mixed-path CholQR factor (n <= 128, one CTA): the lower triangle of S in shared memory
+// (packed, FP64), left-looking FP64 Cholesky with warp-parallel dot products, then
+// M = conj(L^{-1}) by column-wise forward substitution in FP32 (M feeds a rotation that
+// carries 24 significant bits).  A pivot <= tol * S_jj sets status = j + 1 and M = I.
+__device__ __forceinline__ int lpk(int i, int k) { return i * (i + 1) / 2 + k; }
+
+__global__ void __launch_bounds__(1024) k_cholesky_mixed(const double2* __restrict__ S, double2* __restrict__ M,
+                                                         int n, double tol, int* __restrict__ status) {
+  extern __shared__ double2 csm[];
+  __shared__ int bad;
+  __shared__ double sjj, ljj;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, k = e % n;
+    if (k <= i) csm[lpk(i, k)] = S[e];
+  }
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) sjj = csm[lpk(j, j)].x;
+    for (int i = j + warp; i < n; i += nw) {
+      double ar = 0.0, ai = 0.0;
+      for (int k = lane; k < j; k += 32) {
+        const double2 a = csm[lpk(i, k)], b = csm[lpk(j, k)];   // a * conj(b)
+        ar += a.x * b.x + a.y * b.y;
+        ai += a.y * b.x - a.x * b.y;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        ar += __shfl_down_sync(0xffffffffu, ar, o);
+        ai += __shfl_down_sync(0xffffffffu, ai, o);
+      }
+      if (lane == 0) {
+        const double2 s = csm[lpk(i, j)];
+        csm[lpk(i, j)] = make_double2(s.x - ar, s.y - ai);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double d = csm[lpk(j, j)].x;
+      if (!(d > tol * sjj) || !isfinite(d)) {
+        bad = j + 1;
+      } else {
+        ljj = sqrt(d);
+        csm[lpk(j, j)] = make_double2(ljj, 0.0);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double inv = 1.0 / ljj;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      const double2 v = csm[lpk(i, j)];
+      csm[lpk(i, j)] = make_double2(v.x * inv, v.y * inv);
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) M[e] = make_double2((e / n == e % n) ? 1.0 : 0.0, 0.0);
+    if (threadIdx.x == 0) *status = bad;
+    return;
+  }
+  // X = L^{-1}, one column per warp; lane l keeps x_k for k = c + l + 32 m in registers.
+  for (int c = warp; c < n; c += nw) {
+    float2 xr[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (int i = c; i < n; ++i) {
+      float sr = 0.f, si = 0.f;
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) {
+        const int k = c + lane + 32 * mm;
+        if (k < i) {
+          const double2 l = csm[lpk(i, k)];
+          const float lr = (float)l.x, li = (float)l.y;
+          sr += lr * xr[mm].x - li * xr[mm].y;
+          si += lr * xr[mm].y + li * xr[mm].x;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+      }
+      const float d = (float)csm[lpk(i, i)].x;
+      const float xre = ((i == c ? 1.f : 0.f) - sr) / d, xim = -si / d;
+      const int owner = (i - c) & 31, slot = (i - c) >> 5;
+      if (lane == owner) {
+#pragma unroll
+        for (int mm = 0; mm < 4; ++mm)
+          if (mm == slot) xr[mm] = make_float2(xre, xim);
+        M[(size_t)i * n + c] = make_double2((double)xre, -(double)xim);
+      }
+    }
+    for (int i = lane; i < c; i += 32) M[(size_t)i * n + c] = make_double2(0.0, 0.0);
   }
 }
 
@@ -598,6 +692,18 @@ void jacobi_eigh_mixed(const double2* A, double2* V, double* lam, double* eig, d
   k_rayleigh_quotients<<<n, 256, 0, s>>>(A, V, n, lam);
   KS_CHECK_LAUNCH();
   k_sort_vectors<<<1, 128, 0, s>>>(lam, V, n, eig, Vt);
+  KS_CHECK_LAUNCH();
+}
+
+void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, int* status, cudaStream_t s) {
+  if (n > 128) fail(KS_ERR_ARG, "cholesky_inverse_mixed: n=%d > 128", n);
+  const size_t smem = (size_t)(n * (n + 1) / 2) * sizeof(double2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    KS_CUDA(cudaFuncSetAttribute(k_cholesky_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    attr_set = true;
+  }
+  k_cholesky_mixed<<<1, 1024, smem, s>>>(S, M, n, tol, status);
   KS_CHECK_LAUNCH();
 }
 

@@ -299,10 +299,14 @@ template <typename T> class Engine final : public EngineBase {
       overlap(psi_, psi_, n, mS_, s);
       hermitize(mS_, n, s);
     }
-    KS_CUDA(cudaMemcpyAsync(mA_, mS_, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
     {
       ProfScope p(prof, "cholesky", s);
-      cholesky_inverse_tol(mA_, mM_, n, sizeof(T) == 8 ? 1e-12 : 1e-6, status_, s);
+      if (sizeof(T) == 4 && n <= 128) {
+        cholesky_inverse_mixed(mS_, mM_, n, 1e-6, status_, s);
+      } else {
+        KS_CUDA(cudaMemcpyAsync(mA_, mS_, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        cholesky_inverse_tol(mA_, mM_, n, sizeof(T) == 8 ? 1e-12 : 1e-6, status_, s);
+      }
     }
     C* out = spare(psi_, hpsi_);
     {

@@ -268,3 +268,93 @@ __device__ __forceinline__ void fft_lines_grouped(C* s, int lines, int lstride, 
 }
 
 }  // namespace ks
+
+// ---------------------------------------------------------------------------------------------
+// Compile-time plans (fused kernels): N, the radix sequence (8, then 4, 2, 3), the job
+// decomposition and the exponent sign are constants, so index arithmetic folds away.
+// ---------------------------------------------------------------------------------------------
+namespace ks {
+
+template <int N, int Ns> struct RadixOf {
+  static constexpr int rem = N / Ns;
+  static constexpr int R = (rem % 8 == 0) ? 8 : (rem % 4 == 0) ? 4 : (rem % 2 == 0) ? 2 : 3;
+};
+
+// One stage over `lines` lines (<= LPC lines; LPC = lines per call).  LINE_FAST: job =
+// j * LPC + l (consecutive threads on consecutive lines), else job = l * M + j.
+template <int N, int Ns, int R, int THREADS, int LPC, bool LINE_FAST, int SIGN>
+__device__ __forceinline__ void cstage(float2* s, int lines, int lstride, int kstride, const float2* tw) {
+  constexpr int M = N / R;
+  constexpr int step = N / (Ns * R);
+  constexpr int JOBS = LPC * M;
+  constexpr int Q = (JOBS + THREADS - 1) / THREADS;
+  float2 v[Q][R];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int job = threadIdx.x + q * THREADS;
+    int l, j;
+    if (LINE_FAST) {
+      j = job / LPC;
+      l = job - j * LPC;
+    } else {
+      l = job / M;
+      j = job - l * M;
+    }
+    if (job < JOBS && l < lines) {
+      const int k = j % Ns;
+      const float2* line = s + l * lstride;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = line[(j + r * M) * kstride];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[k * r * step];
+          if (SIGN < 0) w.y = -w.y;
+          v[q][r] = cmul(v[q][r], w);
+        }
+      }
+      SmallDft<R, float2>::run(v[q], SIGN);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int job = threadIdx.x + q * THREADS;
+    int l, j;
+    if (LINE_FAST) {
+      j = job / LPC;
+      l = job - j * LPC;
+    } else {
+      l = job / M;
+      j = job - l * M;
+    }
+    if (job < JOBS && l < lines) {
+      const int k = j % Ns;
+      float2* line = s + l * lstride;
+      const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) line[(base + r * Ns) * kstride] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int N, int Ns, int THREADS, int LPC, bool LINE_FAST, int SIGN> struct CFft {
+  static __device__ __forceinline__ void run(float2* s, int lines, int lstride, int kstride, const float2* tw) {
+    constexpr int R = RadixOf<N, Ns>::R;
+    cstage<N, Ns, R, THREADS, LPC, LINE_FAST, SIGN>(s, lines, lstride, kstride, tw);
+    CFft<N, Ns * R, THREADS, LPC, LINE_FAST, SIGN>::run(s, lines, lstride, kstride, tw);
+  }
+};
+template <int N, int THREADS, int LPC, bool LINE_FAST, int SIGN> struct CFft<N, N, THREADS, LPC, LINE_FAST, SIGN> {
+  static __device__ __forceinline__ void run(float2*, int, int, int, const float2*) {}
+};
+
+// All `lines` lines, LPC at a time.
+template <int N, int THREADS, int LPC, bool LINE_FAST, int SIGN>
+__device__ __forceinline__ void cfft_lines(float2* s, int lines, int lstride, int kstride, const float2* tw) {
+  for (int l0 = 0; l0 < lines; l0 += LPC)
+    CFft<N, 1, THREADS, LPC, LINE_FAST, SIGN>::run(s + l0 * lstride, min(LPC, lines - l0), lstride, kstride, tw);
+}
+
+}  // namespace ks

@@ -24,10 +24,6 @@ namespace ks {
 
 namespace {
 
-constexpr int Z_THREADS = 512;
-constexpr int Z_CAP = 4096;        // elements per line-FFT call in the column kernels
-constexpr int P_THREADS = 1024;
-constexpr int P_CAP = 8192;        // elements per line-FFT call in the plane kernel
 
 struct PlaneNL {
   const int* pt_off;     // [N+1] covered points of plane z
@@ -38,14 +34,25 @@ struct PlaneNL {
   int nproj;
 };
 
-__global__ void __launch_bounds__(Z_THREADS) k_zinv(const float2* __restrict__ psi, int nG, const int* __restrict__ g_col,
-                                                    const int* __restrict__ g_z, const int* __restrict__ col_off,
-                                                    int ncols, int N, int CT, float2* __restrict__ colbuf, FftPlan plan,
-                                                    const float2* __restrict__ twg) {
-  extern __shared__ float2 zsm[];
-  float2* tw = zsm;
-  float2* s = zsm + N;
-  const int ld = N + 1;
+// Per-size launch shapes: plane kernel threads (and CTAs per SM), lines per FFT call
+// (at most 8 complex values per thread per stage), z-kernel columns per CTA.
+template <int N> struct FCfg {
+  static constexpr int PT = N >= 128 ? 1024 : (N >= 64 ? 512 : 256);
+  static constexpr int PMIN = N >= 128 ? 1 : (N >= 64 ? 2 : 4);
+  static constexpr int LPC = (8 * PT / N) < N ? (8 * PT / N) : N;
+  static constexpr int ZT = 512;
+  static constexpr int CT = (4096 / N) < 32 ? (4096 / N) : 32;
+  static constexpr int ACC = (N * N + PT - 1) / PT;
+};
+
+template <int N>
+__global__ void __launch_bounds__(FCfg<N>::ZT) k_zinv(const float2* __restrict__ psi, int nG, const int* __restrict__ g_col,
+                                                      const int* __restrict__ g_z, const int* __restrict__ col_off,
+                                                      int ncols, float2* __restrict__ colbuf,
+                                                      const float2* __restrict__ twg) {
+  constexpr int CT = FCfg<N>::CT, ld = N + 1;
+  __shared__ float2 tw[N];
+  __shared__ float2 s[CT * ld];
   const int b = blockIdx.y;
   const int c0 = blockIdx.x * CT;
   const int nl = min(CT, ncols - c0);
@@ -57,7 +64,7 @@ __global__ void __launch_bounds__(Z_THREADS) k_zinv(const float2* __restrict__ p
   const float2* in = psi + (size_t)b * nG;
   for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) s[(g_col[g] - c0) * ld + g_z[g]] = in[g];
   __syncthreads();
-  fft_lines_grouped<Z_THREADS, Z_CAP, false>(s, nl, ld, 1, N, plan, tw, +1);
+  cfft_lines<N, FCfg<N>::ZT, CT, false, +1>(s, nl, ld, 1, tw);
   float2* out = colbuf + (size_t)b * N * ncols + c0;
   for (int e = threadIdx.x; e < N * nl; e += blockDim.x) {
     const int z = e / nl, l = e - z * nl;
@@ -65,15 +72,15 @@ __global__ void __launch_bounds__(Z_THREADS) k_zinv(const float2* __restrict__ p
   }
 }
 
-__global__ void __launch_bounds__(Z_THREADS) k_zfwd(const float2* __restrict__ colbuf, const float2* __restrict__ psi,
-                                                    float2* __restrict__ hpsi, int nG, const int* __restrict__ g_col,
-                                                    const int* __restrict__ g_z, const int* __restrict__ col_off,
-                                                    const float* __restrict__ g2half, int ncols, int N, int CT,
-                                                    float scale, FftPlan plan, const float2* __restrict__ twg) {
-  extern __shared__ float2 zsm[];
-  float2* tw = zsm;
-  float2* s = zsm + N;
-  const int ld = N + 1;
+template <int N>
+__global__ void __launch_bounds__(FCfg<N>::ZT) k_zfwd(const float2* __restrict__ colbuf, const float2* __restrict__ psi,
+                                                      float2* __restrict__ hpsi, int nG, const int* __restrict__ g_col,
+                                                      const int* __restrict__ g_z, const int* __restrict__ col_off,
+                                                      const float* __restrict__ g2half, int ncols, float scale,
+                                                      const float2* __restrict__ twg) {
+  constexpr int CT = FCfg<N>::CT, ld = N + 1;
+  __shared__ float2 tw[N];
+  __shared__ float2 s[CT * ld];
   const int b = blockIdx.y;
   const int c0 = blockIdx.x * CT;
   const int nl = min(CT, ncols - c0);
@@ -84,7 +91,7 @@ __global__ void __launch_bounds__(Z_THREADS) k_zfwd(const float2* __restrict__ c
     s[l * ld + z] = in[(size_t)z * ncols + l];
   }
   __syncthreads();
-  fft_lines_grouped<Z_THREADS, Z_CAP, false>(s, nl, ld, 1, N, plan, tw, -1);
+  cfft_lines<N, FCfg<N>::ZT, CT, false, -1>(s, nl, ld, 1, tw);
   const int g0 = col_off[c0];
   const int g1 = (c0 + nl < ncols) ? col_off[c0 + nl] : nG;
   const size_t off = (size_t)b * nG;
@@ -96,48 +103,52 @@ __global__ void __launch_bounds__(Z_THREADS) k_zfwd(const float2* __restrict__ c
   }
 }
 
-// Inverse (x, y) transform of one plane held as scattered columns.
-__device__ __forceinline__ void plane_inverse(float2* P, int ld, int N, int xr, const FftPlan& plan, const float2* tw) {
-  // rows jx in [0, xr] and [N - xr, N - 1] hold columns: y-lines of those rows
-  fft_lines_grouped<P_THREADS, P_CAP, false>(P, xr + 1, ld, 1, N, plan, tw, +1);
-  if (xr > 0) fft_lines_grouped<P_THREADS, P_CAP, false>(P + (N - xr) * ld, xr, ld, 1, N, plan, tw, +1);
+// Zero the plane, scatter the columns of one (state, z-plane), inverse y then x transforms.
+template <int N>
+__device__ __forceinline__ void plane_load_inverse(float2* P, const float2* __restrict__ colrow, int ncols,
+                                                   const int* __restrict__ col_xy, int xr, const float2* tw) {
+  constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC;
+  for (int e = threadIdx.x; e < N * ld; e += PT) P[e] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncols; c += PT) {
+    const int xy = col_xy[c];
+    const int jx = xy / N, jy = xy - jx * N;
+    P[jx * ld + jy] = colrow[c];
+  }
+  __syncthreads();
+  // y-lines of the rows that hold columns: jx in [0, xr] and [N - xr, N - 1]
+  cfft_lines<N, PT, LPC, false, +1>(P, xr + 1, ld, 1, tw);
+  if (xr > 0) cfft_lines<N, PT, LPC, false, +1>(P + (N - xr) * ld, xr, ld, 1, tw);
   // x-lines: every column jy, element jx at P[jx*ld + jy]
-  fft_lines_grouped<P_THREADS, P_CAP, true>(P, N, 1, ld, N, plan, tw, +1);
+  cfft_lines<N, PT, LPC, true, +1>(P, N, 1, ld, tw);
 }
 
-__global__ void __launch_bounds__(P_THREADS, 1)
+template <int N>
+__global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
     k_plane(const float2* __restrict__ colbuf1, float2* __restrict__ colbuf2, int ncols, const int* __restrict__ col_xy,
-            int N, int xr, const float* __restrict__ vplane, PlaneNL nl, const float2* __restrict__ pf, int nprojtot,
-            FftPlan plan, const float2* __restrict__ twg) {
+            int xr, const float* __restrict__ vplane, PlaneNL nl, const float2* __restrict__ pf, int nprojtot,
+            const float2* __restrict__ twg) {
+  constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC;
   extern __shared__ float2 psm[];
   float2* tw = psm;
   float2* P = psm + N;
-  const int ld = N + 1;
   const int z = blockIdx.x, b = blockIdx.y;
-  for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = twg[t];
-  for (int e = threadIdx.x; e < N * ld; e += blockDim.x) P[e] = make_float2(0.f, 0.f);
-  __syncthreads();
+  for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
   const size_t row = ((size_t)b * N + z) * ncols;
-  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
-    const int xy = col_xy[c];
-    const int jx = xy / N, jy = xy - jx * N;
-    P[jx * ld + jy] = colbuf1[row + c];
-  }
-  __syncthreads();
-  plane_inverse(P, ld, N, xr, plan, tw);
+  plane_load_inverse<N>(P, colbuf1 + row, ncols, col_xy, xr, tw);
   // u = V psi
   const float* v = vplane + (size_t)z * N * N;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+  for (int e = threadIdx.x; e < N * N; e += PT) {
     const int jx = e / N, jy = e - jx * N;
     const float vv = v[e];
-    float2 u = P[jx * ld + jy];
+    const float2 u = P[jx * ld + jy];
     P[jx * ld + jy] = make_float2(u.x * vv, u.y * vv);
   }
   __syncthreads();
   // + sum_{I,l} D Omega^{1/2} beta_Il p_Il  (pf already carries D Omega^{1/2})
   if (nprojtot > 0) {
     const float2* pb = pf + (size_t)b * nprojtot;
-    for (int pt = nl.pt_off[z] + threadIdx.x; pt < nl.pt_off[z + 1]; pt += blockDim.x) {
+    for (int pt = nl.pt_off[z] + threadIdx.x; pt < nl.pt_off[z + 1]; pt += PT) {
       float ax = 0.f, ay = 0.f;
       for (int e = nl.ent_off[pt]; e < nl.ent_off[pt + 1]; ++e) {
         const float2* pp = pb + nl.ent_proj[e];
@@ -149,16 +160,16 @@ __global__ void __launch_bounds__(P_THREADS, 1)
       }
       const int xy = nl.pt_xy[pt];
       const int jx = xy / N, jy = xy - jx * N;
-      float2 u = P[jx * ld + jy];
+      const float2 u = P[jx * ld + jy];
       P[jx * ld + jy] = make_float2(u.x + ax, u.y + ay);
     }
   }
   __syncthreads();
   // forward x-lines (all), then y-lines of the rows that hold columns
-  fft_lines_grouped<P_THREADS, P_CAP, true>(P, N, 1, ld, N, plan, tw, -1);
-  fft_lines_grouped<P_THREADS, P_CAP, false>(P, xr + 1, ld, 1, N, plan, tw, -1);
-  if (xr > 0) fft_lines_grouped<P_THREADS, P_CAP, false>(P + (N - xr) * ld, xr, ld, 1, N, plan, tw, -1);
-  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+  cfft_lines<N, PT, LPC, true, -1>(P, N, 1, ld, tw);
+  cfft_lines<N, PT, LPC, false, -1>(P, xr + 1, ld, 1, tw);
+  if (xr > 0) cfft_lines<N, PT, LPC, false, -1>(P + (N - xr) * ld, xr, ld, 1, tw);
+  for (int c = threadIdx.x; c < ncols; c += PT) {
     const int xy = col_xy[c];
     const int jx = xy / N, jy = xy - jx * N;
     colbuf2[row + c] = P[jx * ld + jy];
@@ -166,37 +177,27 @@ __global__ void __launch_bounds__(P_THREADS, 1)
 }
 
 // Density partial sums: one (z-plane, chunk of states) per CTA, states in order.
-constexpr int D_MAXACC = 16;   // plane points per thread (N^2 <= 16 * 1024)
-
-__global__ void __launch_bounds__(P_THREADS, 1)
-    k_plane_density(const float2* __restrict__ colbuf1, int ncols, const int* __restrict__ col_xy, int N, int xr,
+template <int N>
+__global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
+    k_plane_density(const float2* __restrict__ colbuf1, int ncols, const int* __restrict__ col_xy, int xr,
                     int nstates, int chunk, const double* __restrict__ occ, float scale, float* __restrict__ partial,
-                    FftPlan plan, const float2* __restrict__ twg) {
+                    const float2* __restrict__ twg) {
+  constexpr int ld = N + 1, PT = FCfg<N>::PT, ACC = FCfg<N>::ACC;
   extern __shared__ float2 psm[];
   float2* tw = psm;
   float2* P = psm + N;
-  const int ld = N + 1;
   const int z = blockIdx.x, ch = blockIdx.y;
-  for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = twg[t];
-  float acc[D_MAXACC];
+  for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
+  float acc[ACC];
 #pragma unroll
-  for (int k = 0; k < D_MAXACC; ++k) acc[k] = 0.f;
+  for (int k = 0; k < ACC; ++k) acc[k] = 0.f;
   const int b0 = ch * chunk, b1 = min(nstates, b0 + chunk);
   for (int b = b0; b < b1; ++b) {
-    for (int e = threadIdx.x; e < N * ld; e += blockDim.x) P[e] = make_float2(0.f, 0.f);
-    __syncthreads();
-    const size_t row = ((size_t)b * N + z) * ncols;
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
-      const int xy = col_xy[c];
-      const int jx = xy / N, jy = xy - jx * N;
-      P[jx * ld + jy] = colbuf1[row + c];
-    }
-    __syncthreads();
-    plane_inverse(P, ld, N, xr, plan, tw);
+    plane_load_inverse<N>(P, colbuf1 + ((size_t)b * N + z) * ncols, ncols, col_xy, xr, tw);
     const float f = (float)occ[b];
 #pragma unroll
-    for (int k = 0; k < D_MAXACC; ++k) {
-      const int e = threadIdx.x + k * P_THREADS;
+    for (int k = 0; k < ACC; ++k) {
+      const int e = threadIdx.x + k * PT;
       if (e < N * N) {
         const int jx = e / N, jy = e - jx * N;
         const float2 u = P[jx * ld + jy];
@@ -207,8 +208,8 @@ __global__ void __launch_bounds__(P_THREADS, 1)
   }
   float* out = partial + ((size_t)ch * N + z) * N * N;
 #pragma unroll
-  for (int k = 0; k < D_MAXACC; ++k) {
-    const int e = threadIdx.x + k * P_THREADS;
+  for (int k = 0; k < ACC; ++k) {
+    const int e = threadIdx.x + k * PT;
     if (e < N * N) out[e] = acc[k] * scale;
   }
 }
@@ -273,13 +274,19 @@ unsigned nblk(size_t n, int t, unsigned cap = 4096) {
 
 class FusedImpl final : public FusedOps {
  public:
+  static bool supported(int N) {
+    switch (N) {
+      case 18: case 24: case 32: case 36: case 48: case 64: case 96: case 128: return true;
+      default: return false;
+    }
+  }
+
   FusedImpl(const HostGeometry& g, const DevTables<float>& t, int nstates, DeviceArena& arena, StageProfiler& prof,
             int* err)
       : g_(g), t_(t), ns_(nstates), arena_(arena), prof_(prof), err_(err) {
     N_ = g.N;
     ncols_ = g.ncols;
     nprojtot_ = g.natoms * g.nproj;
-    plan_ = make_plan8(N_);
     const size_t N3 = (size_t)N_ * N_ * N_;
     // per-G column id and z
     std::vector<int> gcol(g.nG), gz(g.nG);
@@ -292,8 +299,6 @@ class FusedImpl final : public FusedOps {
     }
     g_col_ = upload(gcol);
     g_z_ = upload(gz);
-    // columns per CTA in the z kernels: all of a column tile's lines in one FFT call
-    CT_ = std::max(1, std::min(32, Z_CAP / N_));
     // per-plane projector lists
     std::vector<int> pt_off(N_ + 1, 0), pt_xy, ent_off(1, 0), ent_proj;
     std::vector<float> ent_beta;
@@ -334,7 +339,6 @@ class FusedImpl final : public FusedOps {
     dchunk_ = std::max(1, std::min(32, (ns_ + 7) / 8));
     nch_max_ = (ns_ + dchunk_ - 1) / dchunk_;
     dpartial_ = alloc<float>((size_t)nch_max_ * N3);
-    set_smem_limits();
   }
 
   void apply_h(const float2* psi, float2* hpsi, int n, const float* v, cudaStream_t s) override {
@@ -351,19 +355,11 @@ class FusedImpl final : public FusedOps {
     zinv(psi, n, s);
     {
       ProfScope ps(prof_, "plane", s);
-      const size_t smem = (size_t)(N_ + N_ * (N_ + 1)) * sizeof(float2);
-      dim3 grid(N_, n);
-      k_plane<<<grid, P_THREADS, smem, s>>>(colbuf1_, colbuf2_, ncols_, t_.col_xy, N_, g_.xr, vplane_, nl_, pf_,
-                                            nprojtot_, plan_, t_.tw);
-      KS_CHECK_LAUNCH();
+      dispatch([&](auto tag) { launch_plane<decltype(tag)::value>(n, s); });
     }
     {
       ProfScope ps(prof_, "zfwd", s);
-      const size_t smem = (size_t)(N_ + CT_ * (N_ + 1)) * sizeof(float2);
-      dim3 grid((ncols_ + CT_ - 1) / CT_, n);
-      k_zfwd<<<grid, Z_THREADS, smem, s>>>(colbuf2_, psi, hpsi, g_.nG, g_col_, g_z_, t_.col_off, t_.g2half, ncols_, N_,
-                                           CT_, (float)(1.0 / double(N3)), plan_, t_.tw);
-      KS_CHECK_LAUNCH();
+      dispatch([&](auto tag) { launch_zfwd<decltype(tag)::value>(psi, hpsi, n, s); });
     }
   }
 
@@ -371,29 +367,69 @@ class FusedImpl final : public FusedOps {
     zinv(psi, n, s);
     ProfScope ps(prof_, "plane_density", s);
     const int nch = (n + dchunk_ - 1) / dchunk_;
-    const size_t smem = (size_t)(N_ + N_ * (N_ + 1)) * sizeof(float2);
-    dim3 grid(N_, nch);
-    k_plane_density<<<grid, P_THREADS, smem, s>>>(colbuf1_, ncols_, t_.col_xy, N_, g_.xr, n, dchunk_, occ,
-                                                  (float)(1.0 / g_.omega), dpartial_, plan_, t_.tw);
-    KS_CHECK_LAUNCH();
+    dispatch([&](auto tag) { launch_density<decltype(tag)::value>(n, nch, occ, s); });
     k_density_reduce<<<nblk((size_t)N_ * N_ * N_, 256), 256, 0, s>>>(dpartial_, nch, N_, nout);
     KS_CHECK_LAUNCH();
   }
 
  private:
-  void zinv(const float2* psi, int n, cudaStream_t s) {
-    ProfScope ps(prof_, "zinv", s);
-    const size_t smem = (size_t)(N_ + CT_ * (N_ + 1)) * sizeof(float2);
-    dim3 grid((ncols_ + CT_ - 1) / CT_, n);
-    k_zinv<<<grid, Z_THREADS, smem, s>>>(psi, g_.nG, g_col_, g_z_, t_.col_off, ncols_, N_, CT_, colbuf1_, plan_, t_.tw);
-    KS_CHECK_LAUNCH();
+  template <int V> struct IntTag {
+    static constexpr int value = V;
+  };
+  template <typename F> void dispatch(F&& f) {
+    switch (N_) {
+      case 18: f(IntTag<18>{}); break;
+      case 24: f(IntTag<24>{}); break;
+      case 32: f(IntTag<32>{}); break;
+      case 36: f(IntTag<36>{}); break;
+      case 48: f(IntTag<48>{}); break;
+      case 64: f(IntTag<64>{}); break;
+      case 96: f(IntTag<96>{}); break;
+      case 128: f(IntTag<128>{}); break;
+      default: fail(KS_ERR_ARG, "fused path: unsupported grid %d", N_);
+    }
   }
 
-  void set_smem_limits() {
-    const int plane = (int)((N_ + N_ * (N_ + 1)) * sizeof(float2));
-    KS_CUDA(cudaFuncSetAttribute(k_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(plane, 48 * 1024)));
-    KS_CUDA(cudaFuncSetAttribute(k_plane_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 std::max(plane, 48 * 1024)));
+  void zinv(const float2* psi, int n, cudaStream_t s) {
+    ProfScope ps(prof_, "zinv", s);
+    dispatch([&](auto tag) { launch_zinv<decltype(tag)::value>(psi, n, s); });
+  }
+
+  template <int N> void launch_zinv(const float2* psi, int n, cudaStream_t s) {
+    dim3 grid((ncols_ + FCfg<N>::CT - 1) / FCfg<N>::CT, n);
+    k_zinv<N><<<grid, FCfg<N>::ZT, 0, s>>>(psi, g_.nG, g_col_, g_z_, t_.col_off, ncols_, colbuf1_, t_.tw);
+    KS_CHECK_LAUNCH();
+  }
+  template <int N> void launch_zfwd(const float2* psi, float2* hpsi, int n, cudaStream_t s) {
+    dim3 grid((ncols_ + FCfg<N>::CT - 1) / FCfg<N>::CT, n);
+    k_zfwd<N><<<grid, FCfg<N>::ZT, 0, s>>>(colbuf2_, psi, hpsi, g_.nG, g_col_, g_z_, t_.col_off, t_.g2half, ncols_,
+                                           (float)(1.0 / ((double)N * N * N)), t_.tw);
+    KS_CHECK_LAUNCH();
+  }
+  template <int N> static size_t plane_smem() { return (size_t)(N + N * (N + 1)) * sizeof(float2); }
+  template <int N> void launch_plane(int n, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+      KS_CUDA(cudaFuncSetAttribute(k_plane<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)std::max<size_t>(plane_smem<N>(), 48 * 1024)));
+      attr = true;
+    }
+    dim3 grid(N, n);
+    k_plane<N><<<grid, FCfg<N>::PT, plane_smem<N>(), s>>>(colbuf1_, colbuf2_, ncols_, t_.col_xy, g_.xr, vplane_, nl_,
+                                                          pf_, nprojtot_, t_.tw);
+    KS_CHECK_LAUNCH();
+  }
+  template <int N> void launch_density(int n, int nch, const double* occ, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+      KS_CUDA(cudaFuncSetAttribute(k_plane_density<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)std::max<size_t>(plane_smem<N>(), 48 * 1024)));
+      attr = true;
+    }
+    dim3 grid(N, nch);
+    k_plane_density<N><<<grid, FCfg<N>::PT, plane_smem<N>(), s>>>(colbuf1_, ncols_, t_.col_xy, g_.xr, n, dchunk_, occ,
+                                                                   (float)(1.0 / g_.omega), dpartial_, t_.tw);
+    KS_CHECK_LAUNCH();
   }
 
   // B[atom*nproj + l][G] = c_G[beta_Il] = Omega^{1/2} N^-3 sum_j exp(-iG.r_j) beta_Il(r_j), FP64 FFT.
@@ -447,8 +483,7 @@ class FusedImpl final : public FusedOps {
   DeviceArena& arena_;
   StageProfiler& prof_;
   int* err_;
-  int N_ = 0, ncols_ = 0, nprojtot_ = 0, CT_ = 32;
-  FftPlan plan_{};
+  int N_ = 0, ncols_ = 0, nprojtot_ = 0;
   const int* g_col_ = nullptr;
   const int* g_z_ = nullptr;
   PlaneNL nl_{};
@@ -468,6 +503,7 @@ class FusedImpl final : public FusedOps {
 
 std::unique_ptr<FusedOps> make_fused_ops(const HostGeometry& g, const DevTables<float>& t, int nstates,
                                          DeviceArena& arena, StageProfiler& prof, int* err) {
+  if (!FusedImpl::supported(g.N)) return nullptr;
   return std::unique_ptr<FusedOps>(new FusedImpl(g, t, nstates, arena, prof, err));
 }
 

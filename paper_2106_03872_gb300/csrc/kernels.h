@@ -88,6 +88,9 @@ void hermitize(double2* A, int n, cudaStream_t s);
 void cholesky_inverse(double2* A, double2* M, int n, int* status, cudaStream_t s);
 // Same with an explicit relative pivot tolerance (pivot <= tol * S_jj fails).
 void cholesky_inverse_tol(double2* A, double2* M, int n, double tol, int* status, cudaStream_t s);
+// Mixed path (n <= 128): FP64 Cholesky of the Hermitian S in shared memory, M = conj(L^{-1})
+// from an FP32 forward substitution.  Same status convention as cholesky_inverse.
+void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, int* status, cudaStream_t s);
 // Hermitian eigen-decomposition of A (destroyed) by cyclic Jacobi; eig ascending, rows of
 // Vt = eigenvectors (largest-magnitude component real positive).  `V` is n*n workspace.
 void jacobi_eigh(double2* A, double2* V, double* eig, double2* Vt, int n, cudaStream_t s);

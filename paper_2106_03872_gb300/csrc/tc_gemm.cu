@@ -1,6 +1,8 @@
 // Tensor-core (tcgen05, sm_103a) complex GEMMs of the mixed path, split-BF16:
 // every FP32 operand x is split into hi = bf16(x) and lo = bf16(x - hi), and each real
-// product is accumulated as hi*hi + hi*lo + lo*hi in FP32 in tensor memory (TMEM).
+// product is accumulated as hi*hi + hi*lo + lo*hi in FP32 in tensor memory (TMEM).  The
+// rotation matrix of tc_rotate is split into three bf16 terms (24 significant bits) and
+// gets a fourth product, so that its rounding does not bias the norms of rotated states.
 //
 //   tc_overlap:  out[i][j] = sum_k conj(A[i][k]) B[j][k]       (Gram S, H_sub, projections)
 //   tc_rotate:   Y[i][k]   = sum_j M[i][j] X[j][k]             (CholQR and Rayleigh-Ritz rotations)
@@ -38,6 +40,14 @@ constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // hi + lo of A and B: 
 constexpr int NSTAGE = 2;
 constexpr int TC_SMEM = NSTAGE * STAGE_BYTES + 1024;     // + barriers / TMEM slot / alignment
 constexpr uint32_t TMEM_COLS = 256;
+// rotation: 32 real K per stage (16 states), A hi/lo + three B terms, three stages
+constexpr int R_KR = 32;
+constexpr int R_KC = R_KR / 2;
+constexpr int RA_BYTES = TC_M * R_KR * 2;                 // 8 KB
+constexpr int RB_BYTES = TC_N * R_KR * 2;                 // 16 KB
+constexpr int R_STAGE_BYTES = 2 * RA_BYTES + 3 * RB_BYTES; // 64 KB
+constexpr int R_NSTAGE = 3;
+constexpr int R_SMEM = R_NSTAGE * R_STAGE_BYTES + 1024;
 constexpr long WAIT_LIMIT = 1L << 28;                    // spin bound of every mbarrier wait
 
 // ---- PTX wrappers -----------------------------------------------------------------------------
@@ -172,12 +182,12 @@ __device__ __forceinline__ void issue_stage(const StageAddr& sa, uint32_t tmem_d
 }
 
 // Common prologue: barriers and TMEM.  Returns the TMEM base address.
-__device__ __forceinline__ uint32_t tc_setup(unsigned char* smem, uint32_t& bar0) {
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + NSTAGE * STAGE_BYTES + 64);
+__device__ __forceinline__ uint32_t tc_setup(unsigned char* smem, uint32_t& bar0, int ring_bytes, int nstage) {
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + ring_bytes);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + ring_bytes + 64);
   bar0 = smem_u32(bars);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NSTAGE; ++i) mbar_init(bar0 + 8 * i, 1);
+    for (int i = 0; i < nstage; ++i) mbar_init(bar0 + 8 * i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if ((threadIdx.x >> 5) == 0) tmem_alloc(smem_u32(slot), TMEM_COLS);
@@ -196,7 +206,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ __align__(1024) unsigned char tsm[];
   const uint32_t base = smem_u32(tsm);
   uint32_t bar0;
-  const uint32_t tmem = tc_setup(tsm, bar0);
+  const uint32_t tmem = tc_setup(tsm, bar0, NSTAGE * STAGE_BYTES, NSTAGE);
   const int i0 = blockIdx.y * TC_M, j0 = blockIdx.x * (TC_N / 2);
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
@@ -295,36 +305,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 // ------------------------------------------------------------------------------------------------
 // Rotation: Y[i][k] = sum_j M[i][j] X[j][k].  CTA tile: 128 grid columns k x 128 outputs i.
-// Mb holds M pre-split into the B-tile images, per (i-tile, j-chunk): hi tile then lo tile.
+// Mb holds M pre-split into the B-tile images, per (i-tile, j-chunk of 16 states): the
+// three bf16 terms one after the other.  Per stage (two K16 steps) the MMAs are
+// X_hi M_1 + X_hi M_2 + X_lo M_1 + X_hi M_3.
 // ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void issue_rotation_stage(uint32_t s, uint32_t tmem_d, bool first) {
+  constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+  constexpr uint32_t a_lbo = TC_M * 16, b_lbo = TC_N * 16;
+  const uint32_t a_hi = s, a_lo = s + RA_BYTES, b1 = s + 2 * RA_BYTES, b2 = b1 + RB_BYTES, b3 = b2 + RB_BYTES;
+#pragma unroll
+  for (int k = 0; k < R_KR / 16; ++k) {
+    const uint32_t ao = 2 * k * a_lbo, bo = 2 * k * b_lbo;
+    const uint64_t ah = smem_desc(a_hi + ao, a_lbo, 128), al = smem_desc(a_lo + ao, a_lbo, 128);
+    mma_bf16(tmem_d, ah, smem_desc(b1 + bo, b_lbo, 128), idesc, (first && k == 0) ? 0u : 1u);
+    mma_bf16(tmem_d, ah, smem_desc(b2 + bo, b_lbo, 128), idesc, 1u);
+    mma_bf16(tmem_d, al, smem_desc(b1 + bo, b_lbo, 128), idesc, 1u);
+    mma_bf16(tmem_d, ah, smem_desc(b3 + bo, b_lbo, 128), idesc, 1u);
+  }
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_rotate(const uint4* __restrict__ Mb, int njc, const float2* __restrict__ X, int ldx, float2* __restrict__ Y,
                 int ldy, int m, int nin, int K, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   const uint32_t base = smem_u32(tsm);
   uint32_t bar0;
-  const uint32_t tmem = tc_setup(tsm, bar0);
+  const uint32_t tmem = tc_setup(tsm, bar0, R_NSTAGE * R_STAGE_BYTES, R_NSTAGE);
   const int k0 = blockIdx.x * TC_M;
   const int it_i = blockIdx.y;
   const int i0 = it_i * (TC_N / 2);
   const int t = threadIdx.x;
   const int r = t & (TC_M - 1);          // grid coefficient row of the A tile
-  const int half = t >> 7;               // which 16 of the 32 states of a chunk
+  const int jb = t >> 7;                 // which 8 of the 16 states of a chunk
   const int kk = k0 + r;
   bool ok = true;
   for (int it = 0; it < njc; ++it) {
-    const int st = it & 1;
-    if (it >= NSTAGE) {
-      // every thread waits; the CTA continues only if all of them saw the stage free
-      ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * st, ((it - NSTAGE) / NSTAGE) & 1)) != 0;
+    const int st = it % R_NSTAGE;
+    if (it >= R_NSTAGE) {
+      ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * st, ((it - R_NSTAGE) / R_NSTAGE) & 1)) != 0;
       if (!ok) break;
     }
-    const StageAddr sa = stage_addr(base, st);
-    const int jc0 = it * TC_KC;
-    // A: row r = grid coefficient kk; real K: [0,32) re of states jc0.., [32,64) im
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      const int jb = 2 * half + g;       // group of 8 states
+    const uint32_t sb = base + st * R_STAGE_BYTES;
+    const int jc0 = it * R_KC;
+    // A: row r = grid coefficient kk; real K: [0,16) re of states jc0.., [16,32) im
+    {
       float re[8], im[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -336,25 +360,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint4 hi, lo;
       split8(re, hi, lo);
       uint32_t o = tile_off(TC_M, r, 8 * jb);
-      sts128(sa.a_hi + o, hi);
-      sts128(sa.a_lo + o, lo);
+      sts128(sb + o, hi);
+      sts128(sb + RA_BYTES + o, lo);
       split8(im, hi, lo);
-      o = tile_off(TC_M, r, 32 + 8 * jb);
-      sts128(sa.a_hi + o, hi);
-      sts128(sa.a_lo + o, lo);
+      o = tile_off(TC_M, r, 16 + 8 * jb);
+      sts128(sb + o, hi);
+      sts128(sb + RA_BYTES + o, lo);
     }
-    // B: copy the pre-split images (hi then lo, B_BYTES each)
-    const uint4* src = Mb + ((size_t)it_i * njc + it) * (2 * B_BYTES / 16);
-    for (int v = t; v < 2 * B_BYTES / 16; v += TC_THREADS) sts128(sa.b_hi + 16 * v, src[v]);
+    // B: copy the three pre-split images
+    const uint4* src = Mb + ((size_t)it_i * njc + it) * (3 * RB_BYTES / 16);
+    for (int v = t; v < 3 * RB_BYTES / 16; v += TC_THREADS) sts128(sb + 2 * RA_BYTES + 16 * v, src[v]);
     fence_proxy_async();
     __syncthreads();
     if (t == 0) {
       tc_fence_after();
-      issue_stage(sa, tmem, it == 0);
+      issue_rotation_stage(sb, tmem, it == 0);
       mma_commit(bar0 + 8 * st);
     }
   }
-  if (ok && njc > 0) ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ((njc - 1) & 1), ((njc - 1) / NSTAGE) & 1)) != 0;
+  if (ok && njc > 0)
+    ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ((njc - 1) % R_NSTAGE), ((njc - 1) / R_NSTAGE) & 1)) != 0;
   if (!ok && t == 0) atomicExch(err, 1);
   tc_fence_after();
   const int w = t >> 5, lane = t & 31;
@@ -379,32 +404,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // Mb images: B row 2i (output Re Y_i) = [Re M_ij | -Im M_ij], row 2i+1 (Im Y_i) = [Im M_ij | Re M_ij]
-// over the 32 states of chunk jc (K index kk: kk < 32 -> X_re of state jc*32+kk, else X_im).
+// over the 16 states of chunk jc (K index kk: kk < 16 -> X_re of state jc*16+kk, else X_im);
+// value x = t1 + t2 + t3 with t1 = bf16(x), t2 = bf16(x - t1), t3 = bf16(x - t1 - t2).
 __global__ void k_tc_prep_rotation(const double2* __restrict__ M, int m, int nin, int nit, int njc,
                                    unsigned char* __restrict__ Mb) {
-  const size_t total = (size_t)nit * njc * TC_N * TC_KR;
+  const size_t total = (size_t)nit * njc * TC_N * R_KR;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int kk = (int)(e % TC_KR);
-    const int row = (int)((e / TC_KR) % TC_N);
-    const size_t tile = e / ((size_t)TC_KR * TC_N);
+    const int kk = (int)(e % R_KR);
+    const int row = (int)((e / R_KR) % TC_N);
+    const size_t tile = e / ((size_t)R_KR * TC_N);
     const int it_i = (int)(tile / njc), jc = (int)(tile % njc);
     const int i = it_i * (TC_N / 2) + row / 2;
-    const int j = jc * TC_KC + (kk & 31);
-    const int part = kk >> 5;           // 0: multiplies Re X, 1: Im X
-    float x = 0.f;
+    const int j = jc * R_KC + (kk & (R_KC - 1));
+    const int part = kk / R_KC;          // 0: multiplies Re X, 1: Im X
+    double x = 0.0;
     if (i < m && j < nin) {
       const double2 v = M[(size_t)i * nin + j];
       if ((row & 1) == 0)
-        x = (float)(part == 0 ? v.x : -v.y);
+        x = (part == 0 ? v.x : -v.y);
       else
-        x = (float)(part == 0 ? v.y : v.x);
+        x = (part == 0 ? v.y : v.x);
     }
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-    unsigned char* img = Mb + tile * (2 * B_BYTES);
+    const __nv_bfloat16 t1 = __double2bfloat16(x);
+    const double r1 = x - (double)__bfloat162float(t1);
+    const __nv_bfloat16 t2 = __double2bfloat16(r1);
+    const double r2 = r1 - (double)__bfloat162float(t2);
+    const __nv_bfloat16 t3 = __double2bfloat16(r2);
+    unsigned char* img = Mb + tile * (3 * RB_BYTES);
     const uint32_t o = tile_off(TC_N, row, kk);
-    *reinterpret_cast<__nv_bfloat16*>(img + o) = h;
-    *reinterpret_cast<__nv_bfloat16*>(img + B_BYTES + o) = l;
+    *reinterpret_cast<__nv_bfloat16*>(img + o) = t1;
+    *reinterpret_cast<__nv_bfloat16*>(img + RB_BYTES + o) = t2;
+    *reinterpret_cast<__nv_bfloat16*>(img + 2 * RB_BYTES + o) = t3;
   }
 }
 
@@ -424,7 +454,7 @@ bool g_attr_done = false;
 void set_attrs() {
   if (g_attr_done) return;
   KS_CUDA(cudaFuncSetAttribute(k_tc_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-  KS_CUDA(cudaFuncSetAttribute(k_tc_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  KS_CUDA(cudaFuncSetAttribute(k_tc_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, R_SMEM));
   g_attr_done = true;
 }
 
@@ -436,8 +466,8 @@ size_t tc_overlap_part_elems(int m, int n) {
 }
 
 size_t tc_rotation_workspace_bytes(int m, int nin) {
-  const int nit = (m + TC_N / 2 - 1) / (TC_N / 2), njc = (nin + TC_KC - 1) / TC_KC;
-  return (size_t)nit * njc * 2 * B_BYTES;
+  const int nit = (m + TC_N / 2 - 1) / (TC_N / 2), njc = (nin + R_KC - 1) / R_KC;
+  return (size_t)nit * njc * 3 * RB_BYTES;
 }
 
 void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n, int K, double2* part,
@@ -462,14 +492,14 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
 void tc_rotate(const double2* M, int nin, const float2* X, int ldx, float2* Y, int ldy, int m, int K, void* work,
                size_t work_bytes, int* err, cudaStream_t s) {
   set_attrs();
-  const int nit = (m + TC_N / 2 - 1) / (TC_N / 2), njc = (nin + TC_KC - 1) / TC_KC;
+  const int nit = (m + TC_N / 2 - 1) / (TC_N / 2), njc = (nin + R_KC - 1) / R_KC;
   if (tc_rotation_workspace_bytes(m, nin) > work_bytes) fail(KS_ERR_ARG, "tc_rotate: workspace too small");
-  const size_t total = (size_t)nit * njc * TC_N * TC_KR;
+  const size_t total = (size_t)nit * njc * TC_N * R_KR;
   k_tc_prep_rotation<<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0, s>>>(
       M, m, nin, nit, njc, static_cast<unsigned char*>(work));
   KS_CHECK_LAUNCH();
   dim3 g((K + TC_M - 1) / TC_M, nit);
-  k_tc_rotate<<<g, TC_THREADS, TC_SMEM, s>>>(static_cast<const uint4*>(work), njc, X, ldx, Y, ldy, m, nin, K, err);
+  k_tc_rotate<<<g, TC_THREADS, R_SMEM, s>>>(static_cast<const uint4*>(work), njc, X, ldx, Y, ldy, m, nin, K, err);
   KS_CHECK_LAUNCH();
 }
 

@@ -182,8 +182,30 @@ def test_block_iteration_parity(ks, prec):
         e_ref_sub, _, _, _ = ko.rayleigh_ritz(q, ko.apply_h(ref, q))
         q2, _ = ko.cholqr(c_ref)
         e_ora, _, _, _ = ko.rayleigh_ritz(q2, ko.apply_h(ref, q2))
-        assert np.max(np.abs(e_ref_sub - e_ora)) <= 1e-6
+        # 8 iterations from a random start are far from converged, so the iterate itself
+        # carries the mixed-precision error at first order (bf16x3 products ~3e-6 relative)
+        assert np.max(np.abs(e_ref_sub - e_ora)) <= 1e-5
         assert np.max(np.abs(eps - eps_ref)) <= 1e-4
+    g.close()
+
+
+def test_block_iteration_converged_eigenvalues_after_refinement(ks):
+    """Mixed path to convergence, then one FP64 Rayleigh-Ritz of its final subspace: the
+    converged eigenvalues match the oracle's to 1e-6 Ha (Ritz values are second order in
+    the subspace error once converged)."""
+    cell = inputs.small_cell(6.0, 18, 2, 4, 17, depth=-3.0)
+    ref = ko.Cell(cell)
+    c = inputs.random_coeffs(17, 4, ref.nG)
+    e250, c250 = ko.block_iteration(ref, c, 250)
+    e_ora, _ = ko.block_iteration(ref, c250, 50)
+    converged = np.abs(e_ora - e250) < 1e-7
+    assert converged[0]
+    g = ks.Grid(cell, prec="bf16x3")
+    g.set_states(c)
+    g.block_iteration(300)
+    q, _ = ko.cholqr(g.get_states())
+    e_ref, _, _, _ = ko.rayleigh_ritz(q, ko.apply_h(ref, q))
+    assert np.max(np.abs(e_ref[converged] - e_ora[converged])) <= 1e-6
     g.close()
 
 
@@ -243,7 +265,7 @@ def test_bad_arguments(ks):
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_orthonormalize_parity_two_tiles(ks, prec):
     """150 states: the overlap and rotation GEMMs span two 128-row tiles with a ragged edge."""
-    cell = inputs.small_cell(14.0, 40, 3, 150, 15)
+    cell = inputs.small_cell(16.0, 48, 3, 150, 15)
     ref = ko.Cell(cell)
     g = ks.Grid(cell, prec=prec)
     c = inputs.random_coeffs(15, 150, ref.nG)
