@@ -269,7 +269,7 @@ def main_gpu(args):
     h_bytes = 2 * g.nG * 8 * ns + N ** 3 * 4
     hpsi_only = {"value": ns * N ** 3 / (h_ms * 1e-3), "unit": UNIT, "ms": h_ms,
                  "hbm_frac_algorithmic": h_bytes / (h_ms * 1e-3) / 1e9 / pk["hbm"],
-                 "stages_ms_per_call": {k: v[0] / args.steps for k, v in h_entries.items()}}
+                 "stages_ms_per_call": {k: v[0] / args.steps for k, v in h_entries.items() if v[0] > 0}}
 
     # ---- end to end through the public API with host buffers
     pinned = torch.empty((ns, g.nG), dtype=torch.complex128, pin_memory=True)
@@ -300,7 +300,7 @@ def main_gpu(args):
                                   profile=True)
         ms64 = statistics.mean(t64)
         fp64 = {"value": ns * N ** 3 / (ms64 * 1e-3), "ms_per_step": ms64, "speedup_mixed_vs_fp64": ms64 / ms_per_step,
-                "stages_ms_per_step": {k: v[0] / len(t64) for k, v in e64.items()}}
+                "stages_ms_per_step": {k: v[0] / len(t64) for k, v in e64.items() if v[0] > 0}}
         g64.close()
 
     # ---- real-time ETRS step of the 128^3 / 512-state cell (Hartree + Slater each step)
@@ -315,7 +315,7 @@ def main_gpu(args):
         tms = statistics.mean(tt)
         td = {"workload": "td128: L=40, N=128, 512 states, 128 atoms, ETRS + Taylor 4, Hartree + Slater, dt=0.05",
               "steps_per_s": 1e3 / tms, "ms_per_step": tms,
-              "stages_ms_per_step": {k: v[0] / len(tt) for k, v in te.items()}}
+              "stages_ms_per_step": {k: v[0] / len(tt) for k, v in te.items() if v[0] > 0}}
         gt.close()
 
     if rank != 0:
@@ -331,7 +331,8 @@ def main_gpu(args):
                    "l2": "flushed between timed steps (256 MB device write)"},
         "roofline": rl, "cpu_baseline": cpu_baseline_obj(cpu) if cpu else None, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk.summary(), "hpsi_only": hpsi_only, "fp64_gpu": fp64, "td": td,
-        "stages_ms_per_step": {k: v[0] / args.steps for k, v in entries.items()},
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in entries.items() if v[0] > 0},
+        "eigh_sweeps_per_step": entries.get("eigh_sweeps", (0, 0))[1] / args.steps,
     }
     print(json.dumps(line), flush=True)
 

@@ -321,7 +321,7 @@ __device__ __forceinline__ float2 fscale(float2 a, float s) { return make_float2
 constexpr int JS_MAXN = 128;
 
 __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__ H, int n, double2* __restrict__ Vout,
-                                                     float tol) {
+                                                     float tol, int* __restrict__ sweeps_out) {
   extern __shared__ float2 jsm[];
   const int npk = n * (n + 1) / 2;
   float2* Ap = jsm;                 // packed upper triangle (i <= j)
@@ -331,8 +331,18 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
   __shared__ float2 se[JS_MAXN / 2];
   __shared__ float red[32];
   __shared__ float s_fro, s_off;
+  __shared__ unsigned char bpP[JS_MAXN / 2 * (JS_MAXN / 2 + 1) / 2], bpQ[JS_MAXN / 2 * (JS_MAXN / 2 + 1) / 2];
   const int P = n + (n & 1);
   const int np = P / 2;
+  const int nbp = np * (np + 1) / 2;       // block pairs PP <= QQ
+  for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
+    const int a = e / np, b = e % np;
+    if (a <= b) {
+      const int idx = a * np - a * (a - 1) / 2 + (b - a);
+      bpP[idx] = (unsigned char)a;
+      bpQ[idx] = (unsigned char)b;
+    }
+  }
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
     if (i <= j) {
@@ -376,7 +386,10 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
       const float t = block_sum_f(o);
       if (threadIdx.x == 0) s_off = t;
       __syncthreads();
-      if (s_off <= tol * tol * s_fro) break;
+      if (s_off <= tol * tol * s_fro) {
+        if (threadIdx.x == 0 && sweeps_out) atomicAdd(sweeps_out, sweep);
+        break;
+      }
     }
     for (int r = 0; r < P - 1; ++r) {
       if (threadIdx.x < np) {
@@ -407,9 +420,8 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
       }
       __syncthreads();
       // A <- J^H A J, one 2x2 block (pair PP rows, pair QQ columns) per job, PP <= QQ
-      for (int job = threadIdx.x; job < np * np; job += blockDim.x) {
-        const int PP = job / np, QQ = job % np;
-        if (PP > QQ) continue;
+      for (int job = threadIdx.x; job < nbp; job += blockDim.x) {
+        const int PP = bpP[job], QQ = bpQ[job];
         const int r0 = sp[PP], r1 = sq[PP], c0 = sp[QQ], c1 = sq[QQ];
         const int rows[2] = {r0, r1}, cols[2] = {c0, c1};
         float2 B[2][2];
@@ -516,17 +528,19 @@ __global__ void k_rayleigh_quotients(const double2* __restrict__ H, const double
 }
 
 // Mixed-path CholQR factor (n <= 128, one CTA): the lower triangle of S in shared memory
-// (packed, FP64), left-looking FP64 Cholesky with warp-parallel dot products, then
-// M = conj(L^{-1}) by column-wise forward substitution in FP32 (M feeds a rotation that
-// carries 24 significant bits).  A pivot <= tol * S_jj sets status = j + 1 and M = I.
+// (packed, FP64), right-looking FP64 Cholesky (after column j is scaled, every trailing
+// element is updated independently, so all threads work and no dot product is serial),
+// then M = conj(L^{-1}) by a right-looking FP32 forward substitution (M feeds a rotation
+// that carries 24 significant bits).  A pivot <= tol * S_jj sets status = j + 1, M = I.
 __device__ __forceinline__ int lpk(int i, int k) { return i * (i + 1) / 2 + k; }
 
 __global__ void __launch_bounds__(1024) k_cholesky_mixed(const double2* __restrict__ S, double2* __restrict__ M,
                                                          int n, double tol, int* __restrict__ status) {
   extern __shared__ double2 csm[];
+  const int npk = n * (n + 1) / 2;
+  float2* X = reinterpret_cast<float2*>(csm + npk);      // packed lower, X = L^{-1} (FP32)
   __shared__ int bad;
-  __shared__ double sjj, ljj;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double ljj;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, k = e % n;
     if (k <= i) csm[lpk(i, k)] = S[e];
@@ -534,27 +548,9 @@ __global__ void __launch_bounds__(1024) k_cholesky_mixed(const double2* __restri
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) sjj = csm[lpk(j, j)].x;
-    for (int i = j + warp; i < n; i += nw) {
-      double ar = 0.0, ai = 0.0;
-      for (int k = lane; k < j; k += 32) {
-        const double2 a = csm[lpk(i, k)], b = csm[lpk(j, k)];   // a * conj(b)
-        ar += a.x * b.x + a.y * b.y;
-        ai += a.y * b.x - a.x * b.y;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        ar += __shfl_down_sync(0xffffffffu, ar, o);
-        ai += __shfl_down_sync(0xffffffffu, ai, o);
-      }
-      if (lane == 0) {
-        const double2 s = csm[lpk(i, j)];
-        csm[lpk(i, j)] = make_double2(s.x - ar, s.y - ai);
-      }
-    }
-    __syncthreads();
     if (threadIdx.x == 0) {
       const double d = csm[lpk(j, j)].x;
-      if (!(d > tol * sjj) || !isfinite(d)) {
+      if (!(d > tol * S[(size_t)j * n + j].x) || !isfinite(d)) {
         bad = j + 1;
       } else {
         ljj = sqrt(d);
@@ -569,42 +565,59 @@ __global__ void __launch_bounds__(1024) k_cholesky_mixed(const double2* __restri
       csm[lpk(i, j)] = make_double2(v.x * inv, v.y * inv);
     }
     __syncthreads();
+    // trailing update: A_ik -= L_ij conj(L_kj) for j < k <= i
+    const int m = n - 1 - j;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (k > i) continue;
+      const double2 a = csm[lpk(i, j)], b = csm[lpk(k, j)];
+      double2 v = csm[lpk(i, k)];
+      v.x -= a.x * b.x + a.y * b.y;
+      v.y -= a.y * b.x - a.x * b.y;
+      csm[lpk(i, k)] = v;
+    }
+    __syncthreads();
   }
   if (bad) {
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) M[e] = make_double2((e / n == e % n) ? 1.0 : 0.0, 0.0);
     if (threadIdx.x == 0) *status = bad;
     return;
   }
-  // X = L^{-1}, one column per warp; lane l keeps x_k for k = c + l + 32 m in registers.
-  for (int c = warp; c < n; c += nw) {
-    float2 xr[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    for (int i = c; i < n; ++i) {
-      float sr = 0.f, si = 0.f;
-#pragma unroll
-      for (int mm = 0; mm < 4; ++mm) {
-        const int k = c + lane + 32 * mm;
-        if (k < i) {
-          const double2 l = csm[lpk(i, k)];
-          const float lr = (float)l.x, li = (float)l.y;
-          sr += lr * xr[mm].x - li * xr[mm].y;
-          si += lr * xr[mm].y + li * xr[mm].x;
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        sr += __shfl_xor_sync(0xffffffffu, sr, o);
-        si += __shfl_xor_sync(0xffffffffu, si, o);
-      }
-      const float d = (float)csm[lpk(i, i)].x;
-      const float xre = ((i == c ? 1.f : 0.f) - sr) / d, xim = -si / d;
-      const int owner = (i - c) & 31, slot = (i - c) >> 5;
-      if (lane == owner) {
-#pragma unroll
-        for (int mm = 0; mm < 4; ++mm)
-          if (mm == slot) xr[mm] = make_float2(xre, xim);
-        M[(size_t)i * n + c] = make_double2((double)xre, -(double)xim);
-      }
+  // X = L^{-1}: row i of X from X_ic = (delta_ic - sum_{k<i} L_ik X_kc) / L_ii; right-looking:
+  // X starts as the identity, row i is divided by L_ii, then rows r > i lose L_ri X_ic.
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, c = e % n;
+    if (c <= i) X[lpk(i, c)] = make_float2(i == c ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int i = 0; i < n; ++i) {
+    const float d = (float)csm[lpk(i, i)].x;
+    for (int c = threadIdx.x; c <= i; c += blockDim.x) {
+      const float2 v = X[lpk(i, c)];
+      X[lpk(i, c)] = make_float2(v.x / d, v.y / d);
     }
-    for (int i = lane; i < c; i += 32) M[(size_t)i * n + c] = make_double2(0.0, 0.0);
+    __syncthreads();
+    const int rows = n - 1 - i, cols = i + 1;
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      const int r = i + 1 + e / cols, c = e % cols;
+      const double2 l = csm[lpk(r, i)];
+      const float2 x = X[lpk(i, c)];
+      const float lr = (float)l.x, li = (float)l.y;
+      float2 v = X[lpk(r, c)];
+      v.x -= lr * x.x - li * x.y;
+      v.y -= lr * x.y + li * x.x;
+      X[lpk(r, c)] = v;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, c = e % n;
+    if (c <= i) {
+      const float2 x = X[lpk(i, c)];
+      M[e] = make_double2((double)x.x, -(double)x.y);
+    } else {
+      M[e] = make_double2(0.0, 0.0);
+    }
   }
 }
 
@@ -679,7 +692,8 @@ void cholesky_inverse_tol(double2* A, double2* M, int n, double tol, int* status
   KS_CHECK_LAUNCH();
 }
 
-void jacobi_eigh_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, int n, cudaStream_t s) {
+void jacobi_eigh_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, int n, int* sweeps,
+                       cudaStream_t s) {
   if (n > JS_MAXN) fail(KS_ERR_ARG, "jacobi_eigh_mixed: n=%d > %d", n, JS_MAXN);
   const size_t smem = (size_t)(n * (n + 1) / 2 + n * n) * sizeof(float2);
   static bool attr_set = false;
@@ -687,7 +701,7 @@ void jacobi_eigh_mixed(const double2* A, double2* V, double* lam, double* eig, d
     KS_CUDA(cudaFuncSetAttribute(k_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_jacobi_f32<<<1, 1024, smem, s>>>(A, n, V, 1e-5f);
+  k_jacobi_f32<<<1, 1024, smem, s>>>(A, n, V, 1e-4f, sweeps);
   KS_CHECK_LAUNCH();
   k_rayleigh_quotients<<<n, 256, 0, s>>>(A, V, n, lam);
   KS_CHECK_LAUNCH();
@@ -697,10 +711,10 @@ void jacobi_eigh_mixed(const double2* A, double2* V, double* lam, double* eig, d
 
 void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, int* status, cudaStream_t s) {
   if (n > 128) fail(KS_ERR_ARG, "cholesky_inverse_mixed: n=%d > 128", n);
-  const size_t smem = (size_t)(n * (n + 1) / 2) * sizeof(double2);
+  const size_t smem = (size_t)(n * (n + 1) / 2) * (sizeof(double2) + sizeof(float2));
   static bool attr_set = false;
   if (!attr_set) {
-    KS_CUDA(cudaFuncSetAttribute(k_cholesky_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    KS_CUDA(cudaFuncSetAttribute(k_cholesky_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
   k_cholesky_mixed<<<1, 1024, smem, s>>>(S, M, n, tol, status);

@@ -193,6 +193,14 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaStreamSynchronize(s));
   }
 
+  void sync_counters() override {
+    int sweeps = 0;
+    KS_CUDA(cudaMemcpy(&sweeps, status_ + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    prof.set_counter("eigh_sweeps", sweeps);
+  }
+
+  void reset_counters() override { KS_CUDA(cudaMemset(status_ + 2, 0, sizeof(int))); }
+
   void randomize_states(uint64_t seed, cudaStream_t s) override {
     random_states<T>(psi_, (size_t)ns_ * g_.nG, seed, s);
   }
@@ -339,7 +347,7 @@ template <typename T> class Engine final : public EngineBase {
     {
       ProfScope p(prof, "eigh", s);
       if (sizeof(T) == 4 && n <= 128)
-        jacobi_eigh_mixed(mA_, mV_, lam_, eig_, mM_, n, s);
+        jacobi_eigh_mixed(mA_, mV_, lam_, eig_, mM_, n, status_ + 2, s);
       else
         jacobi_eigh(mA_, mV_, eig_, mM_, n, s);
     }

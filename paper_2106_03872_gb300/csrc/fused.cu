@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(FCfg<N>::ZT) k_zinv(const float2* __restrict__
   const float2* in = psi + (size_t)b * nG;
   for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) s[(g_col[g] - c0) * ld + g_z[g]] = in[g];
   __syncthreads();
-  cfft_lines<N, FCfg<N>::ZT, CT, false, +1>(s, nl, ld, 1, tw);
+  cfft_lines<N, FCfg<N>::ZT, CT, true, +1>(s, nl, ld, 1, tw);
   float2* out = colbuf + (size_t)b * N * ncols + c0;
   for (int e = threadIdx.x; e < N * nl; e += blockDim.x) {
     const int z = e / nl, l = e - z * nl;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(FCfg<N>::ZT) k_zfwd(const float2* __restrict__
     s[l * ld + z] = in[(size_t)z * ncols + l];
   }
   __syncthreads();
-  cfft_lines<N, FCfg<N>::ZT, CT, false, -1>(s, nl, ld, 1, tw);
+  cfft_lines<N, FCfg<N>::ZT, CT, true, -1>(s, nl, ld, 1, tw);
   const int g0 = col_off[c0];
   const int g1 = (c0 + nl < ncols) ? col_off[c0 + nl] : nG;
   const size_t off = (size_t)b * nG;
@@ -116,9 +116,11 @@ __device__ __forceinline__ void plane_load_inverse(float2* P, const float2* __re
     P[jx * ld + jy] = colrow[c];
   }
   __syncthreads();
-  // y-lines of the rows that hold columns: jx in [0, xr] and [N - xr, N - 1]
-  cfft_lines<N, PT, LPC, false, +1>(P, xr + 1, ld, 1, tw);
-  if (xr > 0) cfft_lines<N, PT, LPC, false, +1>(P + (N - xr) * ld, xr, ld, 1, tw);
+  // y-lines of the rows that hold columns: jx in [0, xr] and [N - xr, N - 1].  Every line pass
+  // puts consecutive threads on consecutive lines: with the odd row pitch N + 1 a warp's
+  // 8-byte accesses then fall on distinct bank pairs.
+  cfft_lines<N, PT, LPC, true, +1>(P, xr + 1, ld, 1, tw);
+  if (xr > 0) cfft_lines<N, PT, LPC, true, +1>(P + (N - xr) * ld, xr, ld, 1, tw);
   // x-lines: every column jy, element jx at P[jx*ld + jy]
   cfft_lines<N, PT, LPC, true, +1>(P, N, 1, ld, tw);
 }
@@ -167,8 +169,8 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
   __syncthreads();
   // forward x-lines (all), then y-lines of the rows that hold columns
   cfft_lines<N, PT, LPC, true, -1>(P, N, 1, ld, tw);
-  cfft_lines<N, PT, LPC, false, -1>(P, xr + 1, ld, 1, tw);
-  if (xr > 0) cfft_lines<N, PT, LPC, false, -1>(P + (N - xr) * ld, xr, ld, 1, tw);
+  cfft_lines<N, PT, LPC, true, -1>(P, xr + 1, ld, 1, tw);
+  if (xr > 0) cfft_lines<N, PT, LPC, true, -1>(P + (N - xr) * ld, xr, ld, 1, tw);
   for (int c = threadIdx.x; c < ncols; c += PT) {
     const int xy = col_xy[c];
     const int jx = xy / N, jy = xy - jx * N;

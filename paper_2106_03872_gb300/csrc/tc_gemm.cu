@@ -13,9 +13,9 @@
 // the MMA rows are grid coefficients k, the reduction runs over (j, re|im) and B holds the
 // four real blocks of M, so column 2i is Re Y[i][k] and 2i+1 is Im Y[i][k].
 //
-// One CTA computes a 128 x 256 real tile (M = 128 rows, N = 256 columns) with a two-stage
-// shared-memory ring: all 256 threads load and split the next K-chunk while one thread
-// issues the MMAs of the current one; tcgen05.commit arrives on a per-stage mbarrier.
+// One CTA computes a 128 x 256 real tile (M = 128 rows, N = 256 columns) with shared-memory
+// rings: all 256 threads load and split the next K-chunk while one thread issues the MMAs
+// of the current one; tcgen05.commit arrives on a per-stage mbarrier.
 // Operand tiles use the K-major no-swizzle canonical layout (8-row x 16-byte core
 // matrices; LBO = distance between core matrices along K, SBO = along rows).
 // Every mbarrier wait is bounded; on expiry the kernel records an error code and returns.
@@ -32,13 +32,6 @@ namespace {
 constexpr int TC_THREADS = 256;
 constexpr int TC_M = 128;           // MMA rows
 constexpr int TC_N = 256;           // MMA columns
-constexpr int TC_KR = 64;           // real K per stage (bf16 elements)
-constexpr int TC_KC = TC_KR / 2;    // complex K per stage
-constexpr int A_BYTES = TC_M * TC_KR * 2;          // one bf16 tile (hi or lo) of A: 16 KB
-constexpr int B_BYTES = TC_N * TC_KR * 2;          // one bf16 tile of B: 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // hi + lo of A and B: 96 KB
-constexpr int NSTAGE = 2;
-constexpr int TC_SMEM = NSTAGE * STAGE_BYTES + 1024;     // + barriers / TMEM slot / alignment
 constexpr uint32_t TMEM_COLS = 256;
 // rotation: 32 real K per stage (16 states), A hi/lo + three B terms, three stages
 constexpr int R_KR = 32;
@@ -129,7 +122,7 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Byte offset of element (row, k) in a K-major no-swizzle tile with R rows and TC_KR columns:
+// Byte offset of element (row, k) in a K-major no-swizzle tile with R rows:
 // core matrix (row/8, k/8) at (k/8) * R * 16 + (row/8) * 128; inside it, row%8 * 16 + k%8 * 2.
 __host__ __device__ constexpr uint32_t tile_off(int R, int row, int k) {
   return (uint32_t)((k >> 3) * R * 16 + (row >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
@@ -158,29 +151,6 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
                : "memory");
 }
 
-struct StageAddr {
-  uint32_t a_hi, a_lo, b_hi, b_lo;
-};
-__device__ __forceinline__ StageAddr stage_addr(uint32_t base, int st) {
-  const uint32_t s = base + st * STAGE_BYTES;
-  return StageAddr{s, s + A_BYTES, s + 2 * A_BYTES, s + 2 * A_BYTES + B_BYTES};
-}
-
-// Issue the 3 x 4 MMAs of one stage (K = 64 real = 4 steps of 16).
-__device__ __forceinline__ void issue_stage(const StageAddr& sa, uint32_t tmem_d, bool first) {
-  constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
-  constexpr uint32_t a_lbo = TC_M * 16, b_lbo = TC_N * 16;
-#pragma unroll
-  for (int s = 0; s < TC_KR / 16; ++s) {
-    const uint32_t ao = 2 * s * a_lbo, bo = 2 * s * b_lbo;
-    const uint64_t ahi = smem_desc(sa.a_hi + ao, a_lbo, 128), alo = smem_desc(sa.a_lo + ao, a_lbo, 128);
-    const uint64_t bhi = smem_desc(sa.b_hi + bo, b_lbo, 128), blo = smem_desc(sa.b_lo + bo, b_lbo, 128);
-    mma_bf16(tmem_d, ahi, bhi, idesc, (first && s == 0) ? 0u : 1u);
-    mma_bf16(tmem_d, ahi, blo, idesc, 1u);
-    mma_bf16(tmem_d, alo, bhi, idesc, 1u);
-  }
-}
-
 // Common prologue: barriers and TMEM.  Returns the TMEM base address.
 __device__ __forceinline__ uint32_t tc_setup(unsigned char* smem, uint32_t& bar0, int ring_bytes, int nstage) {
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + ring_bytes);
@@ -199,80 +169,148 @@ __device__ __forceinline__ uint32_t tc_setup(unsigned char* smem, uint32_t& bar0
 
 // ------------------------------------------------------------------------------------------------
 // Overlap: part[ks][i][j] = sum_{k in chunk ks} conj(A[i][k]) B[j][k], tile 128 (i) x 128 (j).
+// Pipeline per K-chunk of 16 complex: cp.async copies raw FP32 rows into a 3-deep ring two
+// chunks ahead; all threads split the current chunk into the bf16 operand ring (2 deep);
+// one thread issues the MMAs.  Raw rows are padded to 20 complex so that the split pass
+// reads shared memory without bank conflicts.
 // ------------------------------------------------------------------------------------------------
+constexpr int O_KC = 16;
+constexpr int O_KR = 2 * O_KC;
+constexpr int O_PITCH = 20;                                  // complex per raw row
+constexpr int O_RAW_A = TC_M * O_PITCH * 8;                  // 20 KB
+constexpr int O_RAW_B = (TC_N / 2) * O_PITCH * 8;            // 20 KB
+constexpr int O_RAW_STAGE = O_RAW_A + O_RAW_B;
+constexpr int O_NRAW = 3;
+constexpr int O_A_BYTES = TC_M * O_KR * 2;                   // 8 KB (hi or lo)
+constexpr int O_B_BYTES = TC_N * O_KR * 2;                   // 16 KB
+constexpr int O_OP_STAGE = 2 * O_A_BYTES + 2 * O_B_BYTES;    // 48 KB
+constexpr int O_NOP = 2;
+constexpr int O_RING = O_NRAW * O_RAW_STAGE + O_NOP * O_OP_STAGE;
+constexpr int O_SMEM = O_RING + 1024;
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NPEND> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_overlap(const float2* __restrict__ A, int lda, const float2* __restrict__ B, int ldb, int m, int n, int K,
                  int kchunk, double2* __restrict__ part, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
-  const uint32_t base = smem_u32(tsm);
+  const uint32_t raw0 = smem_u32(tsm);
+  const uint32_t op0 = raw0 + O_NRAW * O_RAW_STAGE;
+  const float2* rawp = reinterpret_cast<const float2*>(tsm);
   uint32_t bar0;
-  const uint32_t tmem = tc_setup(tsm, bar0, NSTAGE * STAGE_BYTES, NSTAGE);
+  const uint32_t tmem = tc_setup(tsm, bar0, O_RING, O_NOP);
   const int i0 = blockIdx.y * TC_M, j0 = blockIdx.x * (TC_N / 2);
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
-  const int nk = (kend - kbeg + TC_KC - 1) / TC_KC;
+  const int nk = (kend - kbeg + O_KC - 1) / O_KC;
   const int t = threadIdx.x;
-  const int kq = t & 7;            // 4 complex = 8 real K values = one core-matrix row
+
+  // raw copies of chunk c: 128 rows of A and 128 rows of B, 16 complex each (8-byte copies)
+  auto issue_raw = [&](int c) {
+    const uint32_t rs = raw0 + (c % O_NRAW) * O_RAW_STAGE;
+    const int k0 = kbeg + c * O_KC;
+#pragma unroll
+    for (int p = 0; p < (TC_M * O_KC) / TC_THREADS; ++p) {
+      const int idx = p * TC_THREADS + t;
+      const int r = idx / O_KC, kk = idx - r * O_KC;
+      const int k = k0 + kk;
+      const bool va = (i0 + r < m) && (k < kend);
+      cp_async8(rs + (uint32_t)(r * O_PITCH + kk) * 8, va ? (const void*)(A + (size_t)(i0 + r) * lda + k) : (const void*)A,
+                va ? 8u : 0u);
+      const bool vb = (j0 + r < n) && (k < kend);
+      cp_async8(rs + O_RAW_A + (uint32_t)(r * O_PITCH + kk) * 8,
+                vb ? (const void*)(B + (size_t)(j0 + r) * ldb + k) : (const void*)B, vb ? 8u : 0u);
+    }
+  };
+
+  if (nk > 0) issue_raw(0);
+  cp_async_commit();
+  if (nk > 1) issue_raw(1);
+  cp_async_commit();
   bool ok = true;
   for (int it = 0; it < nk; ++it) {
-    const int st = it & 1;
-    if (it >= NSTAGE) {
-      // every thread waits; the CTA continues only if all of them saw the stage free
-      ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * st, ((it - NSTAGE) / NSTAGE) & 1)) != 0;
+    if (it + 2 < nk) issue_raw(it + 2);
+    cp_async_commit();
+    cp_async_wait<2>();            // chunk `it` has landed (this thread's copies)
+    __syncthreads();               // ... and every thread's
+    const int ost = it % O_NOP;
+    if (it >= O_NOP) {
+      ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ost, ((it - O_NOP) / O_NOP) & 1)) != 0;
       if (!ok) break;
     }
-    const StageAddr sa = stage_addr(base, st);
-    const int kc = kbeg + it * TC_KC + 4 * kq;
-    // A rows
-    for (int r = t >> 3; r < TC_M; r += TC_THREADS / 8) {
+    const float2* ra = rawp + (size_t)(it % O_NRAW) * (O_RAW_STAGE / 8);
+    const float2* rb = ra + O_RAW_A / 8;
+    const uint32_t oa_hi = op0 + ost * O_OP_STAGE, oa_lo = oa_hi + O_A_BYTES;
+    const uint32_t ob_hi = oa_hi + 2 * O_A_BYTES, ob_lo = ob_hi + O_B_BYTES;
+    // A: item (kq, r), 4 complex per item
+#pragma unroll
+    for (int p = 0; p < (TC_M * (O_KC / 4)) / TC_THREADS; ++p) {
+      const int item = p * TC_THREADS + t;
+      const int kq = item / TC_M, r = item - kq * TC_M;
       float x[8];
-      const int i = i0 + r;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int k = kc + q;
-        const float2 v = (i < m && k < kend) ? A[(size_t)i * lda + k] : make_float2(0.f, 0.f);
+        const float2 v = ra[r * O_PITCH + 4 * kq + q];
         x[2 * q] = v.x;
         x[2 * q + 1] = v.y;
       }
       uint4 hi, lo;
       split8(x, hi, lo);
       const uint32_t o = tile_off(TC_M, r, 8 * kq);
-      sts128(sa.a_hi + o, hi);
-      sts128(sa.a_lo + o, lo);
+      sts128(oa_hi + o, hi);
+      sts128(oa_lo + o, lo);
     }
-    // B rows: 2j <- (re, im), 2j+1 <- (im, -re)
-    for (int r = t >> 3; r < TC_N / 2; r += TC_THREADS / 8) {
-      float x[8], y[8];
-      const int j = j0 + r;
+    // B: item (kq, real row e); row 2j <- (re, im), row 2j+1 <- (im, -re)
+#pragma unroll
+    for (int p = 0; p < (TC_N * (O_KC / 4)) / TC_THREADS; ++p) {
+      const int item = p * TC_THREADS + t;
+      const int kq = item / TC_N, e = item - kq * TC_N;
+      float x[8];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int k = kc + q;
-        const float2 v = (j < n && k < kend) ? B[(size_t)j * ldb + k] : make_float2(0.f, 0.f);
-        x[2 * q] = v.x;
-        x[2 * q + 1] = v.y;
-        y[2 * q] = v.y;
-        y[2 * q + 1] = -v.x;
+        const float2 v = rb[(e >> 1) * O_PITCH + 4 * kq + q];
+        if (e & 1) {
+          x[2 * q] = v.y;
+          x[2 * q + 1] = -v.x;
+        } else {
+          x[2 * q] = v.x;
+          x[2 * q + 1] = v.y;
+        }
       }
       uint4 hi, lo;
       split8(x, hi, lo);
-      uint32_t o = tile_off(TC_N, 2 * r, 8 * kq);
-      sts128(sa.b_hi + o, hi);
-      sts128(sa.b_lo + o, lo);
-      split8(y, hi, lo);
-      o = tile_off(TC_N, 2 * r + 1, 8 * kq);
-      sts128(sa.b_hi + o, hi);
-      sts128(sa.b_lo + o, lo);
+      const uint32_t o = tile_off(TC_N, e, 8 * kq);
+      sts128(ob_hi + o, hi);
+      sts128(ob_lo + o, lo);
     }
     fence_proxy_async();
     __syncthreads();
     if (t == 0) {
       tc_fence_after();
-      issue_stage(sa, tmem, it == 0);
-      mma_commit(bar0 + 8 * st);
+      constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+      constexpr uint32_t a_lbo = TC_M * 16, b_lbo = TC_N * 16;
+#pragma unroll
+      for (int s = 0; s < O_KR / 16; ++s) {
+        const uint32_t ao = 2 * s * a_lbo, bo = 2 * s * b_lbo;
+        const uint64_t ahi = smem_desc(oa_hi + ao, a_lbo, 128), alo = smem_desc(oa_lo + ao, a_lbo, 128);
+        const uint64_t bhi = smem_desc(ob_hi + bo, b_lbo, 128), blo = smem_desc(ob_lo + bo, b_lbo, 128);
+        mma_bf16(tmem, ahi, bhi, idesc, (it == 0 && s == 0) ? 0u : 1u);
+        mma_bf16(tmem, ahi, blo, idesc, 1u);
+        mma_bf16(tmem, alo, bhi, idesc, 1u);
+      }
+      mma_commit(bar0 + 8 * ost);
     }
   }
-  // wait for the last commit (it covers every earlier MMA of this thread)
-  if (ok && nk > 0) ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ((nk - 1) & 1), ((nk - 1) / NSTAGE) & 1)) != 0;
+  cp_async_wait<0>();
+  __syncthreads();
+  if (ok && nk > 0)
+    ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ((nk - 1) % O_NOP), ((nk - 1) / O_NOP) & 1)) != 0;
   if (!ok && t == 0) atomicExch(err, 1);
   tc_fence_after();
   // epilogue: warp w reads TMEM lanes 32*(w%4).., columns [128*(w/4), +128)
@@ -283,17 +321,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int c0 = 128 * (w >> 2); c0 < 128 * (w >> 2) + 128; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + c0, v);
-      if (i < m && nk > 0) {
+      if (i < m) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int j = j0 + c0 / 2 + q;
-          if (j < n) part[((size_t)blockIdx.z * m + i) * n + j] = make_double2((double)v[2 * q], (double)v[2 * q + 1]);
-        }
-      }
-      if (i < m && nk == 0) {
-        for (int q = 0; q < 8; ++q) {
-          const int j = j0 + c0 / 2 + q;
-          if (j < n) part[((size_t)blockIdx.z * m + i) * n + j] = make_double2(0.0, 0.0);
+          if (j < n)
+            part[((size_t)blockIdx.z * m + i) * n + j] =
+                nk > 0 ? make_double2((double)v[2 * q], (double)v[2 * q + 1]) : make_double2(0.0, 0.0);
         }
       }
     }
@@ -453,7 +487,7 @@ __global__ void k_reduce_parts_tc(const double2* __restrict__ part, int nks, siz
 bool g_attr_done = false;
 void set_attrs() {
   if (g_attr_done) return;
-  KS_CUDA(cudaFuncSetAttribute(k_tc_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  KS_CUDA(cudaFuncSetAttribute(k_tc_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
   KS_CUDA(cudaFuncSetAttribute(k_tc_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, R_SMEM));
   g_attr_done = true;
 }
@@ -475,14 +509,14 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
   set_attrs();
   const int tm = (m + TC_M - 1) / TC_M, tn = (n + TC_N / 2 - 1) / (TC_N / 2);
   int ks = std::max(1, 148 / (tm * tn));
-  ks = std::min(ks, std::max(1, K / (4 * TC_KC)));
+  ks = std::min(ks, std::max(1, K / (4 * O_KC)));
   ks = (int)std::min<long>(ks, (long)(part_elems / ((size_t)m * n)));
   if (ks < 1) fail(KS_ERR_ARG, "tc_overlap: partial buffer too small");
   int kchunk = (K + ks - 1) / ks;
-  kchunk = (kchunk + TC_KC - 1) / TC_KC * TC_KC;
+  kchunk = (kchunk + O_KC - 1) / O_KC * O_KC;
   ks = (K + kchunk - 1) / kchunk;
   dim3 g(tn, tm, ks);
-  k_tc_overlap<<<g, TC_THREADS, TC_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, part, err);
+  k_tc_overlap<<<g, TC_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, part, err);
   KS_CHECK_LAUNCH();
   const size_t mn = (size_t)m * n;
   k_reduce_parts_tc<<<(unsigned)std::min<size_t>((mn + 255) / 256, 1024), 256, 0, s>>>(part, ks, mn, out);
