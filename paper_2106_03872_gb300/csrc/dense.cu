@@ -324,37 +324,39 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
                                                      float tol, int* __restrict__ sweeps_out) {
   extern __shared__ float2 jsm[];
   const int npk = n * (n + 1) / 2;
-  float2* Ap = jsm;                 // packed upper triangle (i <= j)
+  float2* Ap = jsm;                 // packed upper triangle: (i, j), i <= j, at roff[i] + j
   float2* VT = jsm + npk;           // VT[j*n + i] = V[i][j]; column j of V = eigenvector j
   __shared__ int sp[JS_MAXN / 2], sq[JS_MAXN / 2];
   __shared__ float sc[JS_MAXN / 2], ss[JS_MAXN / 2];
   __shared__ float2 se[JS_MAXN / 2];
   __shared__ float red[32];
   __shared__ float s_fro, s_off;
+  __shared__ int roff[JS_MAXN];
   __shared__ unsigned char bpP[JS_MAXN / 2 * (JS_MAXN / 2 + 1) / 2], bpQ[JS_MAXN / 2 * (JS_MAXN / 2 + 1) / 2];
   const int P = n + (n & 1);
   const int np = P / 2;
   const int nbp = np * (np + 1) / 2;       // block pairs PP <= QQ
-  for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
-    const int a = e / np, b = e % np;
-    if (a <= b) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int a = warp; a < np; a += 32)
+    for (int b = a + lane; b < np; b += 32) {
       const int idx = a * np - a * (a - 1) / 2 + (b - a);
       bpP[idx] = (unsigned char)a;
       bpQ[idx] = (unsigned char)b;
     }
-  }
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    if (i <= j) {
-      const double2 h = H[e];
-      Ap[pk_index(i, j, n)] = make_float2((float)h.x, i == j ? 0.f : (float)h.y);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) roff[i] = i * n - i * (i - 1) / 2 - i;
+  __syncthreads();
+  for (int i = warp; i < n; i += 32)
+    for (int j = lane; j < n; j += 32) {
+      if (j >= i) {
+        const double2 h = H[(size_t)i * n + j];
+        Ap[roff[i] + j] = make_float2((float)h.x, i == j ? 0.f : (float)h.y);
+      }
+      VT[(size_t)i * n + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
     }
-    VT[e] = make_float2(i == j ? 1.f : 0.f, 0.f);
-  }
   __syncthreads();
   auto block_sum_f = [&](float v) -> float {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    if (lane == 0) red[warp] = v;
     __syncthreads();
     float t = 0.f;
     if (threadIdx.x == 0)
@@ -364,25 +366,26 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
   };
   {
     float f = 0.f;
-    for (int e = threadIdx.x; e < npk; e += blockDim.x) {
-      // diagonal entries sit where j == i; weight 2 for off-diagonal (Hermitian pair)
-      f += Ap[e].x * Ap[e].x + Ap[e].y * Ap[e].y;
-    }
+    for (int i = warp; i < n; i += 32)
+      for (int j = i + lane; j < n; j += 32) {
+        const float2 a = Ap[roff[i] + j];
+        f += a.x * a.x + a.y * a.y;
+      }
     const float t = block_sum_f(f);
     if (threadIdx.x == 0) s_fro = t;
   }
   __syncthreads();
   const float tiny = 1e-30f;
+  // V jobs: thread -> row i = t % 128, pair slots k = t / 128 + 8 m
+  const int vi = threadIdx.x & (JS_MAXN - 1), vk0 = threadIdx.x >> 7;
   for (int sweep = 0; sweep < 30; ++sweep) {
     {
       float o = 0.f;
-      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        if (i < j) {
-          const float2 a = Ap[pk_index(i, j, n)];
+      for (int i = warp; i < n; i += 32)
+        for (int j = i + 1 + lane; j < n; j += 32) {
+          const float2 a = Ap[roff[i] + j];
           o += 2.f * (a.x * a.x + a.y * a.y);
         }
-      }
       const float t = block_sum_f(o);
       if (threadIdx.x == 0) s_off = t;
       __syncthreads();
@@ -403,10 +406,10 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
         float c = 1.f, sv = 0.f;
         float2 e = make_float2(1.f, 0.f);
         if (q < n) {
-          const float2 b = Ap[pk_index(p, q, n)];
+          const float2 b = Ap[roff[p] + q];
           const float mag = hypotf(b.x, b.y);
           if (mag > tiny) {
-            const float alpha = Ap[pk_index(p, p, n)].x, gamma = Ap[pk_index(q, q, n)].x;
+            const float alpha = Ap[roff[p] + p].x, gamma = Ap[roff[q] + q].x;
             const float tau = (gamma - alpha) / (2.f * mag);
             const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             c = rsqrtf(1.f + t * t);
@@ -422,21 +425,18 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
       // A <- J^H A J, one 2x2 block (pair PP rows, pair QQ columns) per job, PP <= QQ
       for (int job = threadIdx.x; job < nbp; job += blockDim.x) {
         const int PP = bpP[job], QQ = bpQ[job];
-        const int r0 = sp[PP], r1 = sq[PP], c0 = sp[QQ], c1 = sq[QQ];
-        const int rows[2] = {r0, r1}, cols[2] = {c0, c1};
+        const int rows[2] = {sp[PP], sq[PP]}, cols[2] = {sp[QQ], sq[QQ]};
         float2 B[2][2];
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
           for (int b = 0; b < 2; ++b) {
             const int i = rows[a], j = cols[b];
-            if (i >= n || j >= n) {
+            if (i >= n || j >= n)
               B[a][b] = make_float2(0.f, 0.f);
-            } else {
-              B[a][b] = (i <= j) ? Ap[pk_index(i, j, n)] : fconj(Ap[pk_index(j, i, n)]);
-            }
+            else
+              B[a][b] = (i <= j) ? Ap[roff[i] + j] : fconj(Ap[roff[j] + i]);
           }
-        // left: J_P^H = [[c, -s e], [s conj(e), c]]
         {
           const float c = sc[PP], sv = ss[PP];
           const float2 e = se[PP];
@@ -447,7 +447,6 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
             B[1][b] = fadd(fscale(fmul(fconj(e), x0), sv), fscale(x1, c));
           }
         }
-        // right: J_Q = [[c, s e], [-s conj(e), c]]
         {
           const float c = sc[QQ], sv = ss[QQ];
           const float2 e = se[QQ];
@@ -466,30 +465,31 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
             if (i >= n || j >= n) continue;
             if (PP == QQ && i > j) continue;          // diagonal block: write the upper entries once
             if (i <= j)
-              Ap[pk_index(i, j, n)] = (i == j) ? make_float2(B[a][b].x, 0.f) : B[a][b];
+              Ap[roff[i] + j] = (i == j) ? make_float2(B[a][b].x, 0.f) : B[a][b];
             else
-              Ap[pk_index(j, i, n)] = fconj(B[a][b]);
+              Ap[roff[j] + i] = fconj(B[a][b]);
           }
       }
       // V <- V J
-      for (int job = threadIdx.x; job < np * n; job += blockDim.x) {
-        const int k = job / n, i = job % n;
-        const int p = sp[k], q = sq[k];
-        if (q >= n) continue;
-        const float c = sc[k], sv = ss[k];
-        const float2 e = se[k];
-        const float2 vp = VT[p * n + i], vq = VT[q * n + i];
-        VT[p * n + i] = fadd(fscale(vp, c), fscale(fmul(fconj(e), vq), -sv));
-        VT[q * n + i] = fadd(fscale(fmul(e, vp), sv), fscale(vq, c));
+      if (vi < n) {
+        for (int k = vk0; k < np; k += 1024 / JS_MAXN) {
+          const int p = sp[k], q = sq[k];
+          if (q >= n) continue;
+          const float c = sc[k], sv = ss[k];
+          const float2 e = se[k];
+          const float2 vp = VT[p * n + vi], vq = VT[q * n + vi];
+          VT[p * n + vi] = fadd(fscale(vp, c), fscale(fmul(fconj(e), vq), -sv));
+          VT[q * n + vi] = fadd(fscale(fmul(e, vp), sv), fscale(vq, c));
+        }
       }
       __syncthreads();
     }
   }
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    const float2 v = VT[j * n + i];
-    Vout[e] = make_double2((double)v.x, (double)v.y);
-  }
+  for (int i = warp; i < n; i += 32)
+    for (int j = lane; j < n; j += 32) {
+      const float2 v = VT[(size_t)j * n + i];
+      Vout[(size_t)i * n + j] = make_double2((double)v.x, (double)v.y);
+    }
 }
 
 // lam[i] = v_i^H H v_i / v_i^H v_i in FP64 (column i of V), one CTA per i.
@@ -565,11 +565,14 @@ __global__ void __launch_bounds__(1024) k_cholesky_mixed(const double2* __restri
       csm[lpk(i, j)] = make_double2(v.x * inv, v.y * inv);
     }
     __syncthreads();
-    // trailing update: A_ik -= L_ij conj(L_kj) for j < k <= i
+    // trailing update: A_ik -= L_ij conj(L_kj) for j < k <= i, the m(m+1)/2 elements
+    // enumerated exactly (ra = i - j - 1, e = ra(ra+1)/2 + k - j - 1) so no lane idles.
     const int m = n - 1 - j;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = j + 1 + e / m, k = j + 1 + e % m;
-      if (k > i) continue;
+    for (int e = threadIdx.x; e < m * (m + 1) / 2; e += blockDim.x) {
+      int ra = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      if (ra * (ra + 1) / 2 > e) --ra;
+      if ((ra + 1) * (ra + 2) / 2 <= e) ++ra;
+      const int i = j + 1 + ra, k = j + 1 + (e - ra * (ra + 1) / 2);
       const double2 a = csm[lpk(i, j)], b = csm[lpk(k, j)];
       double2 v = csm[lpk(i, k)];
       v.x -= a.x * b.x + a.y * b.y;

@@ -20,9 +20,6 @@ class DeviceArena {
   size_t total_ = 0;
 };
 
-// Device bytes an engine for this cell would hold (used by the serving admission).
-size_t engine_device_bytes(const ks_cell_desc& d, int nG, int ncols);
-
 // Per-stage CUDA-event timing of an engine's kernels (off by default).  Each stage scope
 // records an event pair on the launching stream; collect() waits for them and accumulates
 // milliseconds and launch counts per stage name.

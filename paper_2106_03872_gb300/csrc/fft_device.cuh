@@ -275,9 +275,84 @@ __device__ __forceinline__ void fft_lines_grouped(C* s, int lines, int lstride, 
 // ---------------------------------------------------------------------------------------------
 namespace ks {
 
+// cos(2 pi m / N) for the composite in-register DFTs (N = 12, 16).
+__host__ __device__ constexpr double cos_frac(int m, int N) {
+  if (N == 16) {
+    switch (((m % 16) + 16) % 16) {
+      case 0: return 1.0;
+      case 1: case 15: return 0.92387953251128675613;
+      case 2: case 14: return 0.70710678118654752440;
+      case 3: case 13: return 0.38268343236508977173;
+      case 4: case 12: return 0.0;
+      case 5: case 11: return -0.38268343236508977173;
+      case 6: case 10: return -0.70710678118654752440;
+      case 7: case 9: return -0.92387953251128675613;
+      default: return -1.0;
+    }
+  }
+  switch (((m % 12) + 12) % 12) {
+    case 0: return 1.0;
+    case 1: case 11: return 0.86602540378443864676;
+    case 2: case 10: return 0.5;
+    case 3: case 9: return 0.0;
+    case 4: case 8: return -0.5;
+    case 5: case 7: return -0.86602540378443864676;
+    default: return -1.0;
+  }
+}
+
+// In-register DFT of size R1*R2 by one Cooley-Tukey split: n = R2 n1 + n2, k = k1 + R1 k2:
+// DFT_R1 over n1 for each n2, twiddle exp(sign 2 pi i n2 k1 / N), DFT_R2 over n2 for each k1.
+template <int R1, int R2, typename C> __device__ __forceinline__ void dft_composite(C* v, int sign) {
+  using T = decltype(C::x);
+  constexpr int N = R1 * R2;
+  C y[R2][R1];
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    C t[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) t[n1] = v[R2 * n1 + n2];
+    SmallDft<R1, C>::run(t, sign);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      const int m = n2 * k1;
+      if (m == 0) {
+        y[n2][k1] = t[k1];
+      } else {
+        const C w = mk<C>(T(cos_frac(m, N)), T(sign) * T(cos_frac(m - N / 4, N)));
+        y[n2][k1] = cmul(t[k1], w);
+      }
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    C t[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) t[n2] = y[n2][k1];
+    SmallDft<R2, C>::run(t, sign);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = t[k2];
+  }
+}
+
+template <typename C> struct SmallDft<16, C> {
+  static __device__ __forceinline__ void run(C* v, int sign) { dft_composite<4, 4, C>(v, sign); }
+};
+template <typename C> struct SmallDft<12, C> {
+  static __device__ __forceinline__ void run(C* v, int sign) { dft_composite<4, 3, C>(v, sign); }
+};
+
+// Radix sequence: a final 12- or 16-point stage where it fits (96 = 8 x 12, 128 = 8 x 16,
+// 48 = 4 x 12, 36 = 12 x 3), else 8, 4, 2, 3.
 template <int N, int Ns> struct RadixOf {
   static constexpr int rem = N / Ns;
-  static constexpr int R = (rem % 8 == 0) ? 8 : (rem % 4 == 0) ? 4 : (rem % 2 == 0) ? 2 : 3;
+  static constexpr int R = (rem == 12 || rem == 16) ? rem
+                           : (rem == 48)            ? 4
+                           : (rem == 36)            ? 12
+                           : (rem % 8 == 0)         ? 8
+                           : (rem % 4 == 0)         ? 4
+                           : (rem % 2 == 0)         ? 2
+                                                    : 3;
 };
 
 // One stage over `lines` lines (<= LPC lines; LPC = lines per call).  LINE_FAST: job =

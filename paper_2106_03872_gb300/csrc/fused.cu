@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
 
 // Density partial sums: one (z-plane, chunk of states) per CTA, states in order.
 template <int N>
-__global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
+__global__ void __launch_bounds__(FCfg<N>::PT, 1)
     k_plane_density(const float2* __restrict__ colbuf1, int ncols, const int* __restrict__ col_xy, int xr,
                     int nstates, int chunk, const double* __restrict__ occ, float scale, float* __restrict__ partial,
                     const float2* __restrict__ twg) {

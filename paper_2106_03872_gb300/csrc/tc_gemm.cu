@@ -171,12 +171,13 @@ __device__ __forceinline__ uint32_t tc_setup(unsigned char* smem, uint32_t& bar0
 // Overlap: part[ks][i][j] = sum_{k in chunk ks} conj(A[i][k]) B[j][k], tile 128 (i) x 128 (j).
 // Pipeline per K-chunk of 16 complex: cp.async copies raw FP32 rows into a 3-deep ring two
 // chunks ahead; all threads split the current chunk into the bf16 operand ring (2 deep);
-// one thread issues the MMAs.  Raw rows are padded to 20 complex so that the split pass
-// reads shared memory without bank conflicts.
+// one thread issues the MMAs.  Raw rows are padded to 18 complex (144 bytes) so that the
+// split pass's 16-byte reads from consecutive rows hit distinct bank groups.
 // ------------------------------------------------------------------------------------------------
 constexpr int O_KC = 16;
 constexpr int O_KR = 2 * O_KC;
-constexpr int O_PITCH = 20;                                  // complex per raw row
+constexpr int O_PITCH = 18;                                  // complex per raw row (144 B)
+constexpr int O_THREADS = 512;
 constexpr int O_RAW_A = TC_M * O_PITCH * 8;                  // 20 KB
 constexpr int O_RAW_B = (TC_N / 2) * O_PITCH * 8;            // 20 KB
 constexpr int O_RAW_STAGE = O_RAW_A + O_RAW_B;
@@ -196,7 +197,7 @@ template <int NPEND> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(O_THREADS, 1)
     k_tc_overlap(const float2* __restrict__ A, int lda, const float2* __restrict__ B, int ldb, int m, int n, int K,
                  int kchunk, double2* __restrict__ part, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
@@ -216,8 +217,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t rs = raw0 + (c % O_NRAW) * O_RAW_STAGE;
     const int k0 = kbeg + c * O_KC;
 #pragma unroll
-    for (int p = 0; p < (TC_M * O_KC) / TC_THREADS; ++p) {
-      const int idx = p * TC_THREADS + t;
+    for (int p = 0; p < (TC_M * O_KC) / O_THREADS; ++p) {
+      const int idx = p * O_THREADS + t;
       const int r = idx / O_KC, kk = idx - r * O_KC;
       const int k = k0 + kk;
       const bool va = (i0 + r < m) && (k < kend);
@@ -250,16 +251,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t ob_hi = oa_hi + 2 * O_A_BYTES, ob_lo = ob_hi + O_B_BYTES;
     // A: item (kq, r), 4 complex per item
 #pragma unroll
-    for (int p = 0; p < (TC_M * (O_KC / 4)) / TC_THREADS; ++p) {
-      const int item = p * TC_THREADS + t;
+    for (int p = 0; p < (TC_M * (O_KC / 4)) / O_THREADS; ++p) {
+      const int item = p * O_THREADS + t;
       const int kq = item / TC_M, r = item - kq * TC_M;
       float x[8];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float2 v = ra[r * O_PITCH + 4 * kq + q];
-        x[2 * q] = v.x;
-        x[2 * q + 1] = v.y;
-      }
+      const float4* src = reinterpret_cast<const float4*>(ra + r * O_PITCH + 4 * kq);
+      const float4 v0 = src[0], v1 = src[1];
+      x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+      x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
       uint4 hi, lo;
       split8(x, hi, lo);
       const uint32_t o = tile_off(TC_M, r, 8 * kq);
@@ -268,19 +267,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     // B: item (kq, real row e); row 2j <- (re, im), row 2j+1 <- (im, -re)
 #pragma unroll
-    for (int p = 0; p < (TC_N * (O_KC / 4)) / TC_THREADS; ++p) {
-      const int item = p * TC_THREADS + t;
+    for (int p = 0; p < (TC_N * (O_KC / 4)) / O_THREADS; ++p) {
+      const int item = p * O_THREADS + t;
       const int kq = item / TC_N, e = item - kq * TC_N;
       float x[8];
+      const float4* src = reinterpret_cast<const float4*>(rb + (e >> 1) * O_PITCH + 4 * kq);
+      const float4 v0 = src[0], v1 = src[1];
+      const float y[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float2 v = rb[(e >> 1) * O_PITCH + 4 * kq + q];
         if (e & 1) {
-          x[2 * q] = v.y;
-          x[2 * q + 1] = -v.x;
+          x[2 * q] = y[2 * q + 1];
+          x[2 * q + 1] = -y[2 * q];
         } else {
-          x[2 * q] = v.x;
-          x[2 * q + 1] = v.y;
+          x[2 * q] = y[2 * q];
+          x[2 * q + 1] = y[2 * q + 1];
         }
       }
       uint4 hi, lo;
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int row = 32 * (w & 3) + lane;
   const int i = i0 + row;
   if (ok) {
-    for (int c0 = 128 * (w >> 2); c0 < 128 * (w >> 2) + 128; c0 += 16) {
+    for (int c0 = 64 * (w >> 2); c0 < 64 * (w >> 2) + 64; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + c0, v);
       if (i < m) {
@@ -516,7 +517,7 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
   kchunk = (kchunk + O_KC - 1) / O_KC * O_KC;
   ks = (K + kchunk - 1) / kchunk;
   dim3 g(tn, tm, ks);
-  k_tc_overlap<<<g, TC_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, part, err);
+  k_tc_overlap<<<g, O_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, part, err);
   KS_CHECK_LAUNCH();
   const size_t mn = (size_t)m * n;
   k_reduce_parts_tc<<<(unsigned)std::min<size_t>((mn + 255) / 256, 1024), 256, 0, s>>>(part, ks, mn, out);

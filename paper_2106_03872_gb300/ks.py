@@ -259,3 +259,51 @@ class Grid:
         check(load().ks_td_step(self.h, float(dt), int(nsteps), prop, 1 if hartree_xc else 0, _dptr(norms),
                                 _dptr(energies), _stream_ptr(stream)))
         return norms, energies
+
+
+class Server:
+    """Owns a ks_server (continuous batching of independent calculations)."""
+
+    def __init__(self, budget_bytes=0):
+        self.h = ct.c_void_p()
+        check(load().ks_serve_create(ct.c_size_t(int(budget_bytes)), ct.byref(self.h)))
+        self._descs = {}
+
+    def close(self):
+        if self.h:
+            load().ks_serve_destroy(self.h)
+            self.h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, cell, kind, count, dt=0.05, c0=None, prec="bf16x3", nstates=None):
+        """kind 0: `count` block iterations; kind 1: `count` ETRS steps (Hartree + exchange)."""
+        d = make_desc(cell, prec, nstates)
+        arr = None
+        if c0 is not None:
+            arr = np.ascontiguousarray(np.asarray(c0, np.complex128))
+        t = ct.c_uint64()
+        check(load().ks_serve_submit(self.h, ct.byref(d), arr.ctypes.data_as(ct.POINTER(ct.c_double))
+                                     if arr is not None else None, int(kind), int(count), float(dt), ct.byref(t)))
+        self._descs[t.value] = d
+        return t.value
+
+    def poll(self, ticket, timeout_ms=0, want_states=False):
+        """(status, result, states or None, latency_s); status KS_PENDING while running."""
+        nres, ns, nG = ct.c_int(), ct.c_int(), ct.c_int()
+        st = load().ks_serve_result_info(self.h, ct.c_uint64(ticket), ct.byref(nres), ct.byref(ns), ct.byref(nG))
+        if st != KS_OK:
+            return st, None, None, None
+        res = np.zeros(nres.value)
+        states = np.zeros((ns.value, nG.value), np.complex128) if want_states else None
+        lat = ct.c_double()
+        st = load().ks_serve_poll(self.h, ct.c_uint64(ticket), int(timeout_ms), _dptr(res),
+                                  states.ctypes.data_as(ct.POINTER(ct.c_double)) if want_states else None,
+                                  ct.byref(lat))
+        if st == KS_OK:
+            self._descs.pop(ticket, None)
+        return st, res, states, lat.value

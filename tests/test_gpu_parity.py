@@ -97,6 +97,19 @@ def test_apply_h_full_size_sampled(ks, prec):
     g.close()
 
 
+def test_apply_h_128_grid_sampled(ks):
+    """128^3 grid (the real-time workload's size, radix plan 8 x 16), 6 states, 8 atoms."""
+    cell = inputs.small_cell(40.0, 128, 8, 6, 18, depth=-3.0)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec="bf16x3")
+    c = inputs.random_coeffs(18, 6, ref.nG)
+    got = apply_dev(ks, g, c, "bf16x3")
+    for k in (0, 5):
+        e = ko.apply_h(ref, c[k:k + 1])[0]
+        assert rel(got[k], e) <= TOL_H["bf16x3"], (k, rel(got[k], e))
+    g.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_density_parity(ks, prec):
     cell = inputs.small_cell(12.0, 32, 3, 6, 7)
