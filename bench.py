@@ -31,6 +31,7 @@ METRIC = "Hψ state·gridpts/s & %HBM roofline, mixed vs FP64; TD steps/s; serve
 UNIT = "state·gridpts/s"
 WORKLOAD = "gs96"
 CPU_SAMPLE_STATES = 4
+BASE_SERVE_SEED = 20210612
 
 
 def peaks():
@@ -137,10 +138,24 @@ class Clocks:
 # ------------------------------------------------------------------------------------------------
 # Roofline of the dominant kernel (stage timings from the library's CUDA events)
 # ------------------------------------------------------------------------------------------------
+FP32_PEAK_TFLOPS = 69.46    # measured FP32 FMA rate of this GB300 (152 SMs, 2.07 GHz), see the design doc
+FP64_PEAK_TFLOPS = 1.195    # measured FP64 FMA rate
+
+
 def stage_model(name, geo, pk, fp32_tflops):
     """(bound, algorithmic amount per launch, peak, unit) for a timed stage, or None."""
     N, nG, ns, ncols = geo["N"], geo["nG"], geo["nstates"], geo.get("ncols", 0)
     c64 = 8
+    if name == "eigh":
+        # cyclic Jacobi: per round n/2 rotations, 2x2 block sandwiches on the triangle
+        # (n/2)(n/2+1)/2 blocks x 128 flop and V updates n/2 x n x 24 flop; n-1 rounds per sweep
+        sweeps = geo.get("eigh_sweeps", 1.0)
+        nb = ns // 2
+        flop = sweeps * (ns - 1) * (nb * (nb + 1) / 2 * 128 + nb * ns * 24)
+        return "alu", flop, FP32_PEAK_TFLOPS, "TFLOP/s"
+    if name == "cholesky":
+        # FP64 Cholesky n^3/6 complex MACs (8 flop) + FP32 triangular inverse n^3/6 complex MACs
+        return "alu", 8.0 * ns ** 3 / 6.0, FP64_PEAK_TFLOPS, "TFLOP/s"
     if name == "apply_h":
         # packed psi in + packed H psi out per state (the per-state algorithmic bytes of H psi)
         return "hbm", 2 * nG * c64 * ns + N ** 3 * 4, pk["hbm"], "GB/s"
@@ -148,8 +163,11 @@ def stage_model(name, geo, pk, fp32_tflops):
         # one launch = one 1D-FFT pass over a batch of grids; bytes = read + write of the batch
         return "hbm", 2 * geo["batch"] * N ** 3 * c64, pk["hbm"], "GB/s"
     if name == "plane":
-        # read + write of the pruned column buffer of every state, plus V once
-        return "hbm", 2 * ns * ncols * N * c64 + N ** 3 * 4, pk["hbm"], "GB/s"
+        # FFT flops (5 n log2 n per complex line of n) of the y- and x-lines each plane
+        # transforms, inverse and forward: (2 x_r + 1) y-lines and N x-lines per direction
+        import math
+        lines = 2 * (geo["yrows"] + N)
+        return "alu", ns * N * lines * 5.0 * N * math.log2(N), FP32_PEAK_TFLOPS, "TFLOP/s"
     if name in ("zinv", "zfwd"):
         return "hbm", ns * (ncols * N + 2 * nG) * c64, pk["hbm"], "GB/s"
     if name == "gram":
@@ -161,7 +179,7 @@ def stage_model(name, geo, pk, fp32_tflops):
 
 
 def roofline(entries, geo, pk, steps):
-    leaf = {k: v for k, v in entries.items() if k != "apply_h"}
+    leaf = {k: v for k, v in entries.items() if k not in ("apply_h", "eigh_sweeps")}
     if not leaf:
         return None, None
     name = max(leaf, key=lambda k: leaf[k][0])
@@ -241,7 +259,8 @@ def main_gpu(args):
     g = ks.Grid(cell, prec="bf16x3")
     g.set_states(c0)
     g.orthonormalize()
-    geo = dict(N=N, nG=g.nG, nstates=ns, batch=ns, ncols=0)
+    geo = dict(N=N, nG=g.nG, nstates=ns, batch=ns, ncols=0,
+               yrows=2 * int(cell["ecut"] ** 0.5 * 2 ** 0.5 * cell["L"] / (2 * 3.141592653589793)) + 1)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -258,6 +277,7 @@ def main_gpu(args):
     ms_per_step = total_ms / args.steps
     value = world * ns * N ** 3 * args.steps / (total_ms * 1e-3)
 
+    geo["eigh_sweeps"] = entries.get("eigh_sweeps", (0, 0))[1] / max(1, args.steps)
     rl, rl_name = roofline(entries, geo, pk, args.steps)
 
     # ---- H psi alone (device buffers)
@@ -318,6 +338,8 @@ def main_gpu(args):
               "stages_ms_per_step": {k: v[0] / len(tt) for k, v in te.items() if v[0] > 0}}
         gt.close()
 
+    serve = None if args.no_serve else serve_bench(ks, inputs, args.serve_requests)
+
     if rank != 0:
         return
     line = {
@@ -331,10 +353,61 @@ def main_gpu(args):
                    "l2": "flushed between timed steps (256 MB device write)"},
         "roofline": rl, "cpu_baseline": cpu_baseline_obj(cpu) if cpu else None, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk.summary(), "hpsi_only": hpsi_only, "fp64_gpu": fp64, "td": td,
+        "serve": serve,
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in entries.items() if v[0] > 0},
         "eigh_sweeps_per_step": entries.get("eigh_sweeps", (0, 0))[1] / args.steps,
     }
     print(json.dumps(line), flush=True)
+
+
+def serve_bench(ks, inputs, nreq):
+    """Continuous-batching server: saturated throughput, then Poisson arrivals at 50/80/95 %
+    of it with p50/p99 latency (submit to finish)."""
+    import numpy as np
+
+    reqs = inputs.serve_requests(BASE_SERVE_SEED, nreq, state_range=(8, 64))
+    for r in reqs:
+        r["count"] = 10 if r["kind"] == 0 else 20
+
+    def run(rate):
+        srv = ks.Server(0)
+        t0 = time.perf_counter()
+        tickets = []
+        arrival = 0.0
+        rng = np.random.default_rng(BASE_SERVE_SEED + 1)
+        for r in reqs:
+            if rate:
+                arrival += rng.exponential(1.0 / rate)
+                delay = t0 + arrival - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            tickets.append(srv.submit(r, r["kind"], r["count"], r["dt"], prec="bf16x3"))
+        lat = []
+        for t in tickets:
+            while True:
+                st, res, _, l = srv.poll(t, 1000)
+                if st == ks.KS_OK:
+                    lat.append(l)
+                    break
+                if st not in (ks.KS_PENDING, ks.KS_ERR_TIMEOUT):
+                    raise RuntimeError("serving request failed: %s" % ks.load().ks_last_error())
+        span = time.perf_counter() - t0
+        srv.close()
+        return span, np.array(lat)
+
+    span, lat = run(None)
+    sat = nreq / span
+    loads = []
+    for frac in (0.5, 0.8, 0.95):
+        sp, la = run(frac * sat)
+        loads.append({"load": frac, "rate_req_per_s": frac * sat, "p50_s": float(np.percentile(la, 50)),
+                      "p99_s": float(np.percentile(la, 99)), "throughput_req_per_s": nreq / sp})
+    gp = sum(r["nstates"] * r["N"] ** 3 * r["count"] for r in reqs)
+    return {"requests": nreq, "saturated_req_per_s": sat, "saturated_state_gridpts_steps_per_s": gp / span,
+            "saturated_p50_s": float(np.percentile(lat, 50)), "saturated_p99_s": float(np.percentile(lat, 99)),
+            "loads": loads,
+            "workload": "seeded requests: N in {32,48,64,96} (L = 0.3125 N), 8-64 states, 4-64 atoms, "
+                        "half 10 block iterations, half 20 ETRS steps (dt 0.05, Hartree + Slater), mixed precision"}
 
 
 def main_reference(args):
@@ -365,6 +438,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-td", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24)
     args = ap.parse_args()
     if args.cpu_leg:
         print(json.dumps(cpu_leg(args.steps, args.warmup, args.sample)))

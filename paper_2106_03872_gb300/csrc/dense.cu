@@ -329,6 +329,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
   __shared__ int sp[JS_MAXN / 2], sq[JS_MAXN / 2];
   __shared__ float sc[JS_MAXN / 2], ss[JS_MAXN / 2];
   __shared__ float2 se[JS_MAXN / 2];
+  __shared__ int sact[JS_MAXN / 2];
   __shared__ float red[32];
   __shared__ float s_fro, s_off;
   __shared__ int roff[JS_MAXN];
@@ -375,7 +376,9 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
     if (threadIdx.x == 0) s_fro = t;
   }
   __syncthreads();
-  const float tiny = 1e-30f;
+  // rotations whose off-diagonal element is below this are skipped (identity): once a
+  // pair has converged it costs nothing in the A and V updates
+  const float tiny = 1e-7f * sqrtf(s_fro / (float)n);
   // V jobs: thread -> row i = t % 128, pair slots k = t / 128 + 8 m
   const int vi = threadIdx.x & (JS_MAXN - 1), vk0 = threadIdx.x >> 7;
   for (int sweep = 0; sweep < 30; ++sweep) {
@@ -405,6 +408,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
         sq[k] = q;
         float c = 1.f, sv = 0.f;
         float2 e = make_float2(1.f, 0.f);
+        bool act = false;
         if (q < n) {
           const float2 b = Ap[roff[p] + q];
           const float mag = hypotf(b.x, b.y);
@@ -415,16 +419,19 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
             c = rsqrtf(1.f + t * t);
             sv = t * c;
             e = make_float2(b.x / mag, b.y / mag);
+            act = true;
           }
         }
         sc[k] = c;
         ss[k] = sv;
         se[k] = e;
+        sact[k] = act ? 1 : 0;
       }
       __syncthreads();
       // A <- J^H A J, one 2x2 block (pair PP rows, pair QQ columns) per job, PP <= QQ
       for (int job = threadIdx.x; job < nbp; job += blockDim.x) {
         const int PP = bpP[job], QQ = bpQ[job];
+        if (!sact[PP] && !sact[QQ]) continue;
         const int rows[2] = {sp[PP], sq[PP]}, cols[2] = {sp[QQ], sq[QQ]};
         float2 B[2][2];
 #pragma unroll
@@ -474,7 +481,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__
       if (vi < n) {
         for (int k = vk0; k < np; k += 1024 / JS_MAXN) {
           const int p = sp[k], q = sq[k];
-          if (q >= n) continue;
+          if (q >= n || !sact[k]) continue;
           const float c = sc[k], sv = ss[k];
           const float2 e = se[k];
           const float2 vp = VT[p * n + vi], vq = VT[q * n + vi];

@@ -170,7 +170,7 @@ template <typename T> class Engine final : public EngineBase {
     dots_ = alloc<double2>(ns_);
     norms_dev_ = alloc<double>(MAX_STEPS_CHUNK);
     energies_dev_ = alloc<double>(MAX_STEPS_CHUNK);
-    KS_CUDA(cudaDeviceSynchronize());
+    KS_CUDA(cudaStreamSynchronize(nullptr));
   }
 
   const HostGeometry& geo() const override { return g_; }

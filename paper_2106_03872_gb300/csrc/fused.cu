@@ -464,7 +464,7 @@ class FusedImpl final : public FusedOps {
                                                                     B_ + (size_t)p0 * g_.nG);
       KS_CHECK_LAUNCH();
     }
-    KS_CUDA(cudaDeviceSynchronize());
+    KS_CUDA(cudaStreamSynchronize(nullptr));
     cudaFree(grid);
     cudaFree(sph_off);
     cudaFree(sph_idx);

@@ -98,6 +98,9 @@ def test_poll_reports_pending_then_result(ks):
     assert st == ks.KS_PENDING
     st, res, _, lat = wait(srv, ks, t, want_states=False)
     assert st == ks.KS_OK and len(res) == 30 and np.all(np.isfinite(res))
-    # energy is conserved to ~1e-4 relative over 30 steps at dt = 0.05
-    assert np.max(np.abs(res - res[0])) <= 1e-3 * abs(res[0])
+    # random CN(0,1) states weigh mostly near the cutoff, where the Taylor-4 factor
+    # |R|^2 = 1 - x^6/72 + x^8/576 (x = dt E <~ 1.2) damps every step: the energy falls
+    # monotonically, by well under 1 % over 30 steps
+    assert np.all(np.diff(res) < 0)
+    assert abs(res[-1] - res[0]) <= 1e-2 * abs(res[0])
     srv.close()
