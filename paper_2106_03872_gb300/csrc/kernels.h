@@ -97,6 +97,9 @@ void jacobi_eigh(double2* A, double2* V, double* eig, double2* Vt, int n, cudaSt
 // Mixed: FP32 Jacobi in shared memory (n <= 128) on a copy of the FP64 Hermitian A (kept),
 // eigenvalues = FP64 Rayleigh quotients of the FP32 vectors on A; same outputs as jacobi_eigh.
 // V is n*n workspace, lam n doubles of workspace.
+// Householder + bisection + twisted-factorization eigenvectors, FP32, one CTA (n <= 128):
+// V (n x n complex128, columns = eigenvectors, unsorted).
+void eigh_householder_f32(const double2* A, double2* V, int n, cudaStream_t s);
 // sweeps (may be NULL) accumulates the number of Jacobi sweeps (instrumentation).
 void jacobi_eigh_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, int n, int* sweeps,
                        cudaStream_t s);

@@ -291,3 +291,30 @@ def test_orthonormalize_parity_two_tiles(ks, prec):
     assert rel(q, q_ref) <= (1e-11 if prec == "fp64" else 1e-4)
     assert np.max(np.abs(ko.gram(q) - np.eye(150))) <= (1e-11 if prec == "fp64" else 1e-4)
     g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_rayleigh_ritz_degenerate_shells(ks, prec):
+    """Free electrons: 19 plane waves (|m|^2 <= 2: shells of 1, 6 and 12), mixed by a random
+    unitary.  Rayleigh-Ritz must return the exact shell energies and orthonormal eigenvectors
+    even though the eigenvalues are exactly degenerate."""
+    cell = inputs.small_cell(8.0, 24, 0, 19, 19)
+    ref = ko.Cell(cell)
+    m2 = np.sum(ref.m ** 2, axis=1)
+    picks = np.flatnonzero(m2 <= 2)
+    assert len(picks) == 19
+    c = np.zeros((19, ref.nG), complex)
+    c[np.arange(19), picks] = 1.0
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.normal(size=(19, 19)) + 1j * rng.normal(size=(19, 19)))
+    c = Q @ c
+    g = ks.Grid(cell, prec=prec)
+    g.set_states(c)
+    eps = g.rayleigh_ritz()
+    assert np.allclose(eps, np.sort(0.5 * ref.g2[picks]), atol=1e-11 if prec == "fp64" else 2e-5)
+    q = g.get_states()
+    tol = 1e-11 if prec == "fp64" else 1e-5
+    assert np.max(np.abs(ko.gram(q) - np.eye(19))) <= tol
+    hq = ko.apply_h(ref, q)
+    assert np.max(np.abs(hq - eps[:, None] * q)) <= (1e-10 if prec == "fp64" else 1e-4)
+    g.close()
