@@ -147,15 +147,13 @@ def stage_model(name, geo, pk, fp32_tflops):
     N, nG, ns, ncols = geo["N"], geo["nG"], geo["nstates"], geo.get("ncols", 0)
     c64 = 8
     if name == "eigh":
-        # cyclic Jacobi: per round n/2 rotations, 2x2 block sandwiches on the triangle
-        # (n/2)(n/2+1)/2 blocks x 128 flop and V updates n/2 x n x 24 flop; n-1 rounds per sweep
-        sweeps = geo.get("eigh_sweeps", 1.0)
-        nb = ns // 2
-        flop = sweeps * (ns - 1) * (nb * (nb + 1) / 2 * 128 + nb * ns * 24)
-        return "alu", flop, FP32_PEAK_TFLOPS, "TFLOP/s"
+        # Householder tridiagonalisation (16/3) n^3 + back-transformation 8 n^3 real flops
+        # (complex), Newton-Schulz/bisection/twisted factorisation are lower order
+        return "alu", (16.0 / 3.0 + 8.0) * ns ** 3, FP32_PEAK_TFLOPS, "TFLOP/s"
     if name == "cholesky":
-        # FP64 Cholesky n^3/6 complex MACs (8 flop) + FP32 triangular inverse n^3/6 complex MACs
-        return "alu", 8.0 * ns ** 3 / 6.0, FP64_PEAK_TFLOPS, "TFLOP/s"
+        # two FP32 passes, each a complex Cholesky + triangular inverse (2 x n^3/6 complex
+        # MACs = 8 n^3 / 3 flop), plus FP64 triangular products (n^3 complex MACs, 8 n^3 flop)
+        return "alu", 2 * 8.0 * ns ** 3 / 3.0 + 8.0 * ns ** 3, FP32_PEAK_TFLOPS, "TFLOP/s"
     if name == "apply_h":
         # packed psi in + packed H psi out per state (the per-state algorithmic bytes of H psi)
         return "hbm", 2 * nG * c64 * ns + N ** 3 * 4, pk["hbm"], "GB/s"
@@ -179,7 +177,7 @@ def stage_model(name, geo, pk, fp32_tflops):
 
 
 def roofline(entries, geo, pk, steps):
-    leaf = {k: v for k, v in entries.items() if k not in ("apply_h", "eigh_sweeps")}
+    leaf = {k: v for k, v in entries.items() if k != "apply_h"}
     if not leaf:
         return None, None
     name = max(leaf, key=lambda k: leaf[k][0])
@@ -277,7 +275,6 @@ def main_gpu(args):
     ms_per_step = total_ms / args.steps
     value = world * ns * N ** 3 * args.steps / (total_ms * 1e-3)
 
-    geo["eigh_sweeps"] = entries.get("eigh_sweeps", (0, 0))[1] / max(1, args.steps)
     rl, rl_name = roofline(entries, geo, pk, args.steps)
 
     # ---- H psi alone (device buffers)
@@ -355,7 +352,6 @@ def main_gpu(args):
         "gpu_launches": launches, "clocks": clk.summary(), "hpsi_only": hpsi_only, "fp64_gpu": fp64, "td": td,
         "serve": serve,
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in entries.items() if v[0] > 0},
-        "eigh_sweeps_per_step": entries.get("eigh_sweeps", (0, 0))[1] / args.steps,
     }
     print(json.dumps(line), flush=True)
 

@@ -123,7 +123,8 @@ ks_status ks_apply_h_host(ks_grid g, const double* psi_host, double* hpsi_host, 
 ks_status ks_density(ks_grid g, void* n_dev, void* stream);
 
 /* CholQR of the resident states (Sec. "Ground-state solution", orthogonalisation):
- * S = Psi^H Psi, S = L L^H (FP64 Cholesky on the GPU), Psi <- Psi L^{-H}.
+ * S = Psi^H Psi, S = L L^H, Psi <- Psi L^{-H}.  KS_FP64 factors S in FP64; the mixed
+ * paths (nstates <= 160) take two FP32 Cholesky passes refined by FP64 triangular products.
  * S_host_opt (may be NULL) receives S, [nstates][nstates] complex128 row-major,
  * S_ij = sum_G conj(c_iG) c_jG.  KS_ERR_NOT_POSDEF if S is not positive definite
  * (states unchanged then).  Synchronous (reads a status word). */

@@ -252,9 +252,11 @@ def gram(a, b=None):
     return np.conj(a) @ b.T
 
 
-def cholqr(c):
-    """Orthonormalise the rows of c: S = L L^H, Psi <- Psi L^{-H} (rows: c <- conj(L^{-1}) c)."""
-    S = gram(c)
+def cholqr(c, S=None):
+    """Orthonormalise the rows of c: S = L L^H, Psi <- Psi L^{-H} (rows: c <- conj(L^{-1}) c).
+    S defaults to gram(c); a given S (e.g. one computed elsewhere in lower precision) is
+    factored as is."""
+    S = gram(c) if S is None else S
     L = np.linalg.cholesky(S)
     return np.conj(np.linalg.inv(L)) @ c, S
 

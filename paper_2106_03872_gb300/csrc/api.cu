@@ -170,10 +170,8 @@ ks_status ks_td_step(ks_grid g, double dt, int nsteps, int propagator, int hartr
 ks_status ks_profile(ks_grid g, int mode) {
   return guarded([&] {
     need(g != nullptr && mode >= 0 && mode <= 2, "grid is NULL or mode not in {0,1,2}");
-    if (mode == 2) {
+    if (mode == 2)
       g->eng->prof.reset();
-      g->eng->reset_counters();
-    }
     else
       g->eng->prof.enable(mode == 1);
   });
@@ -183,7 +181,6 @@ ks_status ks_profile_read(ks_grid g, int idx, char* name, int name_len, double* 
   return guarded([&] {
     need(g && name && name_len > 0 && ms && count, "bad profile_read arguments");
     g->eng->prof.collect();
-    if (idx == 0) g->eng->sync_counters();
     const auto& e = g->eng->prof.entries();
     if (idx < 0 || idx >= (int)e.size()) ks::fail(KS_ERR_ARG, "profile entry %d of %d", idx, (int)e.size());
     std::snprintf(name, name_len, "%s", e[idx].name.c_str());

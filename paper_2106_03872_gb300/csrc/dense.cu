@@ -1,6 +1,7 @@
 // Dense linear algebra of the state-space rotations (Sec. "Ground-state solution":
 // orthogonalisation and subspace diagonalisation): overlap GEMMs, rotations, FP64
-// Cholesky + triangular inverse, and a cyclic Jacobi Hermitian eigensolver.
+// Cholesky + triangular inverse, a cyclic Jacobi Hermitian eigensolver (FP64 path), and the
+// FP64 Rayleigh quotients / sorting that finish the mixed path's FP32 eigenvectors.
 // CUDA-core versions templated on the real type of the states.
 #include <algorithm>
 
@@ -307,198 +308,6 @@ __global__ void __launch_bounds__(1024) k_jacobi(double2* __restrict__ A, double
   }
 }
 
-// ---------------------------------------------------------------------------------------------
-// FP32 cyclic Jacobi with the packed upper triangle of A and the eigenvector matrix in shared
-// memory (n <= 128), followed by FP64 Rayleigh quotients of the FP32 vectors on the FP64
-// matrix (many CTAs), then sorting and the phase convention.
-// ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ int pk_index(int i, int j, int n) { return i * n - (i * (i - 1)) / 2 + (j - i); }
-__device__ __forceinline__ float2 fconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 fmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ float2 fadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 fscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-
-constexpr int JS_MAXN = 128;
-
-__global__ void __launch_bounds__(1024) k_jacobi_f32(const double2* __restrict__ H, int n, double2* __restrict__ Vout,
-                                                     float tol, int* __restrict__ sweeps_out) {
-  extern __shared__ float2 jsm[];
-  const int npk = n * (n + 1) / 2;
-  float2* Ap = jsm;                 // packed upper triangle: (i, j), i <= j, at roff[i] + j
-  float2* VT = jsm + npk;           // VT[j*n + i] = V[i][j]; column j of V = eigenvector j
-  __shared__ int sp[JS_MAXN / 2], sq[JS_MAXN / 2];
-  __shared__ float sc[JS_MAXN / 2], ss[JS_MAXN / 2];
-  __shared__ float2 se[JS_MAXN / 2];
-  __shared__ int sact[JS_MAXN / 2];
-  __shared__ float red[32];
-  __shared__ float s_fro, s_off;
-  __shared__ int roff[JS_MAXN];
-  __shared__ unsigned char bpP[JS_MAXN / 2 * (JS_MAXN / 2 + 1) / 2], bpQ[JS_MAXN / 2 * (JS_MAXN / 2 + 1) / 2];
-  const int P = n + (n & 1);
-  const int np = P / 2;
-  const int nbp = np * (np + 1) / 2;       // block pairs PP <= QQ
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int a = warp; a < np; a += 32)
-    for (int b = a + lane; b < np; b += 32) {
-      const int idx = a * np - a * (a - 1) / 2 + (b - a);
-      bpP[idx] = (unsigned char)a;
-      bpQ[idx] = (unsigned char)b;
-    }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) roff[i] = i * n - i * (i - 1) / 2 - i;
-  __syncthreads();
-  for (int i = warp; i < n; i += 32)
-    for (int j = lane; j < n; j += 32) {
-      if (j >= i) {
-        const double2 h = H[(size_t)i * n + j];
-        Ap[roff[i] + j] = make_float2((float)h.x, i == j ? 0.f : (float)h.y);
-      }
-      VT[(size_t)i * n + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
-    }
-  __syncthreads();
-  auto block_sum_f = [&](float v) -> float {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    float t = 0.f;
-    if (threadIdx.x == 0)
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    __syncthreads();
-    return t;
-  };
-  {
-    float f = 0.f;
-    for (int i = warp; i < n; i += 32)
-      for (int j = i + lane; j < n; j += 32) {
-        const float2 a = Ap[roff[i] + j];
-        f += a.x * a.x + a.y * a.y;
-      }
-    const float t = block_sum_f(f);
-    if (threadIdx.x == 0) s_fro = t;
-  }
-  __syncthreads();
-  // rotations whose off-diagonal element is below this are skipped (identity): once a
-  // pair has converged it costs nothing in the A and V updates
-  const float tiny = 1e-7f * sqrtf(s_fro / (float)n);
-  // V jobs: thread -> row i = t % 128, pair slots k = t / 128 + 8 m
-  const int vi = threadIdx.x & (JS_MAXN - 1), vk0 = threadIdx.x >> 7;
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    {
-      float o = 0.f;
-      for (int i = warp; i < n; i += 32)
-        for (int j = i + 1 + lane; j < n; j += 32) {
-          const float2 a = Ap[roff[i] + j];
-          o += 2.f * (a.x * a.x + a.y * a.y);
-        }
-      const float t = block_sum_f(o);
-      if (threadIdx.x == 0) s_off = t;
-      __syncthreads();
-      if (s_off <= tol * tol * s_fro) {
-        if (threadIdx.x == 0 && sweeps_out) atomicAdd(sweeps_out, sweep);
-        break;
-      }
-    }
-    for (int r = 0; r < P - 1; ++r) {
-      if (threadIdx.x < np) {
-        const int k = threadIdx.x;
-        const int pa = k, pb = P - 1 - k;
-        const int ua = (pa == 0) ? 0 : 1 + ((pa - 1 + r) % (P - 1));
-        const int ub = (pb == 0) ? 0 : 1 + ((pb - 1 + r) % (P - 1));
-        const int p = min(ua, ub), q = max(ua, ub);
-        sp[k] = p;
-        sq[k] = q;
-        float c = 1.f, sv = 0.f;
-        float2 e = make_float2(1.f, 0.f);
-        bool act = false;
-        if (q < n) {
-          const float2 b = Ap[roff[p] + q];
-          const float mag = hypotf(b.x, b.y);
-          if (mag > tiny) {
-            const float alpha = Ap[roff[p] + p].x, gamma = Ap[roff[q] + q].x;
-            const float tau = (gamma - alpha) / (2.f * mag);
-            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = rsqrtf(1.f + t * t);
-            sv = t * c;
-            e = make_float2(b.x / mag, b.y / mag);
-            act = true;
-          }
-        }
-        sc[k] = c;
-        ss[k] = sv;
-        se[k] = e;
-        sact[k] = act ? 1 : 0;
-      }
-      __syncthreads();
-      // A <- J^H A J, one 2x2 block (pair PP rows, pair QQ columns) per job, PP <= QQ
-      for (int job = threadIdx.x; job < nbp; job += blockDim.x) {
-        const int PP = bpP[job], QQ = bpQ[job];
-        if (!sact[PP] && !sact[QQ]) continue;
-        const int rows[2] = {sp[PP], sq[PP]}, cols[2] = {sp[QQ], sq[QQ]};
-        float2 B[2][2];
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-          for (int b = 0; b < 2; ++b) {
-            const int i = rows[a], j = cols[b];
-            if (i >= n || j >= n)
-              B[a][b] = make_float2(0.f, 0.f);
-            else
-              B[a][b] = (i <= j) ? Ap[roff[i] + j] : fconj(Ap[roff[j] + i]);
-          }
-        {
-          const float c = sc[PP], sv = ss[PP];
-          const float2 e = se[PP];
-#pragma unroll
-          for (int b = 0; b < 2; ++b) {
-            const float2 x0 = B[0][b], x1 = B[1][b];
-            B[0][b] = fadd(fscale(x0, c), fscale(fmul(e, x1), -sv));
-            B[1][b] = fadd(fscale(fmul(fconj(e), x0), sv), fscale(x1, c));
-          }
-        }
-        {
-          const float c = sc[QQ], sv = ss[QQ];
-          const float2 e = se[QQ];
-#pragma unroll
-          for (int a = 0; a < 2; ++a) {
-            const float2 y0 = B[a][0], y1 = B[a][1];
-            B[a][0] = fadd(fscale(y0, c), fscale(fmul(fconj(e), y1), -sv));
-            B[a][1] = fadd(fscale(fmul(e, y0), sv), fscale(y1, c));
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-          for (int b = 0; b < 2; ++b) {
-            const int i = rows[a], j = cols[b];
-            if (i >= n || j >= n) continue;
-            if (PP == QQ && i > j) continue;          // diagonal block: write the upper entries once
-            if (i <= j)
-              Ap[roff[i] + j] = (i == j) ? make_float2(B[a][b].x, 0.f) : B[a][b];
-            else
-              Ap[roff[j] + i] = fconj(B[a][b]);
-          }
-      }
-      // V <- V J
-      if (vi < n) {
-        for (int k = vk0; k < np; k += 1024 / JS_MAXN) {
-          const int p = sp[k], q = sq[k];
-          if (q >= n || !sact[k]) continue;
-          const float c = sc[k], sv = ss[k];
-          const float2 e = se[k];
-          const float2 vp = VT[p * n + vi], vq = VT[q * n + vi];
-          VT[p * n + vi] = fadd(fscale(vp, c), fscale(fmul(fconj(e), vq), -sv));
-          VT[q * n + vi] = fadd(fscale(fmul(e, vp), sv), fscale(vq, c));
-        }
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = warp; i < n; i += 32)
-    for (int j = lane; j < n; j += 32) {
-      const float2 v = VT[(size_t)j * n + i];
-      Vout[(size_t)i * n + j] = make_double2((double)v.x, (double)v.y);
-    }
-}
-
 // lam[i] = v_i^H H v_i / v_i^H v_i in FP64 (column i of V), one CTA per i.
 __global__ void k_rayleigh_quotients(const double2* __restrict__ H, const double2* __restrict__ V, int n,
                                      double* __restrict__ lam) {
@@ -531,103 +340,6 @@ __global__ void k_rayleigh_quotients(const double2* __restrict__ H, const double
       b += red[1][w];
     }
     lam[i] = a / b;
-  }
-}
-
-// Mixed-path CholQR factor (n <= 128, one CTA): the lower triangle of S in shared memory
-// (packed, FP64), right-looking FP64 Cholesky (after column j is scaled, every trailing
-// element is updated independently, so all threads work and no dot product is serial),
-// then M = conj(L^{-1}) by a right-looking FP32 forward substitution (M feeds a rotation
-// that carries 24 significant bits).  A pivot <= tol * S_jj sets status = j + 1, M = I.
-__device__ __forceinline__ int lpk(int i, int k) { return i * (i + 1) / 2 + k; }
-
-__global__ void __launch_bounds__(1024) k_cholesky_mixed(const double2* __restrict__ S, double2* __restrict__ M,
-                                                         int n, double tol, int* __restrict__ status) {
-  extern __shared__ double2 csm[];
-  const int npk = n * (n + 1) / 2;
-  float2* X = reinterpret_cast<float2*>(csm + npk);      // packed lower, X = L^{-1} (FP32)
-  __shared__ int bad;
-  __shared__ double ljj;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, k = e % n;
-    if (k <= i) csm[lpk(i, k)] = S[e];
-  }
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      const double d = csm[lpk(j, j)].x;
-      if (!(d > tol * S[(size_t)j * n + j].x) || !isfinite(d)) {
-        bad = j + 1;
-      } else {
-        ljj = sqrt(d);
-        csm[lpk(j, j)] = make_double2(ljj, 0.0);
-      }
-    }
-    __syncthreads();
-    if (bad) break;
-    const double inv = 1.0 / ljj;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      const double2 v = csm[lpk(i, j)];
-      csm[lpk(i, j)] = make_double2(v.x * inv, v.y * inv);
-    }
-    __syncthreads();
-    // trailing update: A_ik -= L_ij conj(L_kj) for j < k <= i, the m(m+1)/2 elements
-    // enumerated exactly (ra = i - j - 1, e = ra(ra+1)/2 + k - j - 1) so no lane idles.
-    const int m = n - 1 - j;
-    for (int e = threadIdx.x; e < m * (m + 1) / 2; e += blockDim.x) {
-      int ra = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-      if (ra * (ra + 1) / 2 > e) --ra;
-      if ((ra + 1) * (ra + 2) / 2 <= e) ++ra;
-      const int i = j + 1 + ra, k = j + 1 + (e - ra * (ra + 1) / 2);
-      const double2 a = csm[lpk(i, j)], b = csm[lpk(k, j)];
-      double2 v = csm[lpk(i, k)];
-      v.x -= a.x * b.x + a.y * b.y;
-      v.y -= a.y * b.x - a.x * b.y;
-      csm[lpk(i, k)] = v;
-    }
-    __syncthreads();
-  }
-  if (bad) {
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) M[e] = make_double2((e / n == e % n) ? 1.0 : 0.0, 0.0);
-    if (threadIdx.x == 0) *status = bad;
-    return;
-  }
-  // X = L^{-1}: row i of X from X_ic = (delta_ic - sum_{k<i} L_ik X_kc) / L_ii; right-looking:
-  // X starts as the identity, row i is divided by L_ii, then rows r > i lose L_ri X_ic.
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, c = e % n;
-    if (c <= i) X[lpk(i, c)] = make_float2(i == c ? 1.f : 0.f, 0.f);
-  }
-  __syncthreads();
-  for (int i = 0; i < n; ++i) {
-    const float d = (float)csm[lpk(i, i)].x;
-    for (int c = threadIdx.x; c <= i; c += blockDim.x) {
-      const float2 v = X[lpk(i, c)];
-      X[lpk(i, c)] = make_float2(v.x / d, v.y / d);
-    }
-    __syncthreads();
-    const int rows = n - 1 - i, cols = i + 1;
-    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-      const int r = i + 1 + e / cols, c = e % cols;
-      const double2 l = csm[lpk(r, i)];
-      const float2 x = X[lpk(i, c)];
-      const float lr = (float)l.x, li = (float)l.y;
-      float2 v = X[lpk(r, c)];
-      v.x -= lr * x.x - li * x.y;
-      v.y -= lr * x.y + li * x.x;
-      X[lpk(r, c)] = v;
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, c = e % n;
-    if (c <= i) {
-      const float2 x = X[lpk(i, c)];
-      M[e] = make_double2((double)x.x, -(double)x.y);
-    } else {
-      M[e] = make_double2(0.0, 0.0);
-    }
   }
 }
 
@@ -702,33 +414,11 @@ void cholesky_inverse_tol(double2* A, double2* M, int n, double tol, int* status
   KS_CHECK_LAUNCH();
 }
 
-void jacobi_eigh_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, int n, int* sweeps,
-                       cudaStream_t s) {
-  if (n > JS_MAXN) fail(KS_ERR_ARG, "jacobi_eigh_mixed: n=%d > %d", n, JS_MAXN);
-  const size_t smem = (size_t)(n * (n + 1) / 2 + n * n) * sizeof(float2);
-  static bool attr_set = false;
-  if (!attr_set) {
-    KS_CUDA(cudaFuncSetAttribute(k_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
-  (void)smem;
-  (void)sweeps;
+void eigh_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, int n, cudaStream_t s) {
   eigh_householder_f32(A, V, n, s);
   k_rayleigh_quotients<<<n, 256, 0, s>>>(A, V, n, lam);
   KS_CHECK_LAUNCH();
   k_sort_vectors<<<1, 128, 0, s>>>(lam, V, n, eig, Vt);
-  KS_CHECK_LAUNCH();
-}
-
-void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, int* status, cudaStream_t s) {
-  if (n > 128) fail(KS_ERR_ARG, "cholesky_inverse_mixed: n=%d > 128", n);
-  const size_t smem = (size_t)(n * (n + 1) / 2) * (sizeof(double2) + sizeof(float2));
-  static bool attr_set = false;
-  if (!attr_set) {
-    KS_CUDA(cudaFuncSetAttribute(k_cholesky_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
-  k_cholesky_mixed<<<1, 1024, smem, s>>>(S, M, n, tol, status);
   KS_CHECK_LAUNCH();
 }
 

@@ -1,16 +1,24 @@
 // Hermitian eigen-decomposition of the Rayleigh-Ritz matrix on the mixed path (n <= 128),
-// one CTA, FP32, matrix in shared memory:
+// one CTA of 1024 threads, FP32, matrix in shared memory:
 //
 //   1. Householder reduction A = Q T Q^H to a real symmetric tridiagonal T: for column k the
 //      reflector H_k = I - tau_k v_k v_k^H (v_k[0] = 1) maps A[k+1:, k] to (beta_k, 0, ...)
 //      with real beta_k; the trailing block is updated as A -= v w^H + w v^H with
-//      w = tau A v - (tau/2)(w'^H v) v (the classic two-sided Hermitian update).
+//      w = tau A v - (tau/2)(w'^H v) v (the classic two-sided Hermitian update).  The update
+//      of step k-1 is applied in the same pass over the trailing block as the product A v_k
+//      of step k, so each step is one pass and one barrier; every warp forms v_k itself from
+//      column k (identical arithmetic in every warp).
 //   2. T is split where an off-diagonal element is negligible; every block's eigenvalues are
-//      found by multisection on its Sturm count (8 lanes per eigenvalue, 9-way split per step).
-//   3. Eigenvectors of each block by twisted factorization (forward and backward pivots,
-//      twist index at the smallest |gamma|), then modified Gram-Schmidt inside clusters of
-//      close eigenvalues of a block.
-//   4. Back-transformation V = H_0 H_1 ... H_{n-2} Z.
+//      found by multisection on its Sturm count (8 lanes per eigenvalue, 9-way split per
+//      step) until the bracket is a few ulps of |T| wide.
+//   3. Eigenvectors of each block by twisted factorization (backward and forward pivots,
+//      twist index at the smallest |gamma|); inside numerically degenerate clusters, inverse
+//      iteration from pseudo-random starts with Gram-Schmidt against the earlier members;
+//      then Newton-Schulz steps Z <- Z (3I - Z^T Z) / 2 until Z^T Z = I
+//      to FP32 accuracy (close but separated eigenvalues leave twisted-factorization vectors
+//      orthogonal only to ~eps |T| / gap).
+//   4. Back-transformation V = H_0 H_1 ... H_{n-2} Z, each thread holding 16 rows of one
+//      column of V in registers (8 threads per column).
 //
 // The FP32 vectors are written as complex128 columns; the caller takes the eigenvalues as
 // FP64 Rayleigh quotients of these vectors on the FP64 matrix, then sorts and fixes phases.
@@ -22,10 +30,21 @@ namespace {
 
 constexpr int EH_MAXN = 128;
 constexpr int EH_THREADS = 1024;
+constexpr int EH_WARPS = EH_THREADS / 32;
+constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ float2 cm(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ float2 cmc(float2 a, float2 b) {   // conj(a) * b
   return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 warp_sum(float2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(FULL, v.x, o);
+    v.y += __shfl_xor_sync(FULL, v.y, o);
+  }
+  return v;
 }
 
 // Number of eigenvalues of T[b0..b1] below x (Sturm count of the LDL^T pivots).
@@ -35,7 +54,7 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
   if (fabsf(q) < pivmin) q = -pivmin;
   c += q < 0.f;
   for (int i = b0 + 1; i <= b1; ++i) {
-    q = d[i] - x - e2[i - 1] / q;
+    q = d[i] - x - __fdividef(e2[i - 1], q);
     if (fabsf(q) < pivmin) q = -pivmin;
     c += q < 0.f;
   }
@@ -46,15 +65,12 @@ __global__ void __launch_bounds__(EH_THREADS, 1)
     k_eigh_householder(const double2* __restrict__ H, int n, double2* __restrict__ Vout) {
   extern __shared__ __align__(16) unsigned char esm[];
   const int ld = n + 1;
-  float2* A = reinterpret_cast<float2*>(esm);                       // [n][ld], later Z
+  float2* A = reinterpret_cast<float2*>(esm);                       // [n][ld]
   float2* R = A + (size_t)EH_MAXN * (EH_MAXN + 1);                  // packed reflectors
   __shared__ float d[EH_MAXN], e[EH_MAXN], e2[EH_MAXN], lam[EH_MAXN];
-  __shared__ float2 tau[EH_MAXN], wv[EH_MAXN];
+  __shared__ float2 tau[EH_MAXN], wvp[2][EH_MAXN], red[2][EH_WARPS];
   __shared__ int blk_lo[EH_MAXN], blk_hi[EH_MAXN];
-  __shared__ float red[32][2];
-  __shared__ float2 s_alpha, s_scale;
-  __shared__ float s_beta;
-  __shared__ int s_skip;
+  __shared__ float s_err[EH_WARPS];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
 
   for (int idx = t; idx < n * n; idx += EH_THREADS) {
@@ -65,126 +81,155 @@ __global__ void __launch_bounds__(EH_THREADS, 1)
   __syncthreads();
 
   // ---- 1. tridiagonalization ---------------------------------------------------------------
-  int roff = 0;
+  // Entering step k, A[k:, k:] holds the updates of steps < k-1; the update of step k-1
+  // (v_{k-1} at R + rprev, w_{k-1} = wvp[(k-1)&1] + ap v_{k-1}) is still to be applied.
+  // Lane-owned indices: rows / columns k+1+lane+32q, q < 4.
+  int rprev = 0, roff = 0;
   for (int k = 0; k + 1 < n; ++k) {
-    const int m = n - k - 1;                 // reflector length, rows k+1..n-1
-    float2* v = R + roff;
-    // xnorm^2 over x[1:], alpha = x[0]
-    float s = 0.f;
-    for (int i = 1 + t; i < m; i += EH_THREADS) {
-      const float2 x = A[(k + 1 + i) * ld + k];
-      s += x.x * x.x + x.y * x.y;
+    const int m = n - k - 1;
+    const bool hp = k > 0;
+    const int pb = (k + 1) & 1;                                     // buffer of step k-1
+    float2 ap = make_float2(0.f, 0.f);
+    if (hp) {
+      const float2 s = warp_sum(red[pb][lane]);
+      const float2 h = cm(tau[k - 1], s);
+      ap = make_float2(-0.5f * h.x, -0.5f * h.y);
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) red[warp][0] = s;
-    __syncthreads();
-    if (t == 0) {
-      float xn2 = 0.f;
-      for (int w = 0; w < EH_THREADS / 32; ++w) xn2 += red[w][0];
-      const float2 al = A[(k + 1) * ld + k];
-      d[k] = A[k * ld + k].x;
-      if (xn2 == 0.f && al.y == 0.f) {
-        tau[k] = make_float2(0.f, 0.f);
-        e[k] = al.x;
-        s_skip = 1;
-      } else {
-        const float beta = -copysignf(sqrtf(al.x * al.x + al.y * al.y + xn2), al.x);
-        tau[k] = make_float2((beta - al.x) / beta, -al.y / beta);
-        const float2 dn = make_float2(al.x - beta, al.y);          // 1 / (alpha - beta)
-        const float inv = 1.f / (dn.x * dn.x + dn.y * dn.y);
-        s_scale = make_float2(dn.x * inv, -dn.y * inv);
-        e[k] = beta;
-        s_skip = 0;
+    // pending-update vectors at the lane's indices and at k
+    float2 vp[4], wp[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = k + 1 + lane + 32 * q;
+      vp[q] = make_float2(0.f, 0.f);
+      wp[q] = make_float2(0.f, 0.f);
+      if (hp && j < n) {
+        vp[q] = R[rprev + j - k];
+        wp[q] = cadd(wvp[pb][j], cm(ap, vp[q]));
       }
     }
-    __syncthreads();
-    if (s_skip) {
-      for (int i = t; i < m; i += EH_THREADS) v[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
-      roff += m;
-      __syncthreads();
-      continue;
+    const float2 wk = hp ? cadd(wvp[pb][k], ap) : make_float2(0.f, 0.f);   // v_{k-1}[k] = 1
+    // column k after the pending update: x_i = A_ik - (v_i conj(w_k) + w_i)
+    float2 x[4];
+    float xn2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = k + 1 + lane + 32 * q;
+      x[q] = make_float2(0.f, 0.f);
+      if (i < n) {
+        const float2 a = A[i * ld + k];
+        const float2 u = cadd(make_float2(vp[q].x * wk.x + vp[q].y * wk.y, vp[q].y * wk.x - vp[q].x * wk.y), wp[q]);
+        x[q] = csub(a, u);
+        if (q > 0 || lane > 0) xn2 += x[q].x * x[q].x + x[q].y * x[q].y;
+      }
     }
-    const float2 sc = s_scale;
-    for (int i = t; i < m; i += EH_THREADS) v[i] = (i == 0) ? make_float2(1.f, 0.f) : cm(A[(k + 1 + i) * ld + k], sc);
-    __syncthreads();
-    // w' = tau * A_t v  (A_t = A[k+1:, k+1:]); 8 threads per row
-    const float2 tk = tau[k];
-    {
-      const int row = t >> 3, sub = t & 7;
-      float2 acc = make_float2(0.f, 0.f);
-      if (row < m) {
-        const float2* arow = A + (k + 1 + row) * ld + (k + 1);
-        for (int j = sub; j < m; j += 8) {
-          const float2 a = arow[j], b = v[j];
-          acc.x += a.x * b.x - a.y * b.y;
-          acc.y += a.x * b.y + a.y * b.x;
-        }
-      }
-      for (int o = 4; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-      }
-      if (row < m && sub == 0) wv[row] = cm(tk, acc);
+    for (int o = 16; o > 0; o >>= 1) xn2 += __shfl_xor_sync(FULL, xn2, o);
+    const float2 al = make_float2(__shfl_sync(FULL, x[0].x, 0), __shfl_sync(FULL, x[0].y, 0));
+    float2 tk, sc = make_float2(0.f, 0.f);
+    float ek;
+    if (xn2 == 0.f && al.y == 0.f) {
+      tk = make_float2(0.f, 0.f);
+      ek = al.x;
+    } else {
+      const float beta = -copysignf(sqrtf(al.x * al.x + al.y * al.y + xn2), al.x);
+      const float rb = __frcp_rn(beta);
+      tk = make_float2((beta - al.x) * rb, -al.y * rb);
+      const float2 dn = make_float2(al.x - beta, al.y);            // 1 / (alpha - beta)
+      const float inv = __frcp_rn(dn.x * dn.x + dn.y * dn.y);
+      sc = make_float2(dn.x * inv, -dn.y * inv);
+      ek = beta;
     }
-    __syncthreads();
-    // alpha = -1/2 tau (w'^H v)
-    {
-      float2 p = make_float2(0.f, 0.f);
-      for (int i = t; i < m; i += EH_THREADS) {
-        const float2 q = cmc(wv[i], v[i]);
-        p.x += q.x;
-        p.y += q.y;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        p.x += __shfl_down_sync(0xffffffffu, p.x, o);
-        p.y += __shfl_down_sync(0xffffffffu, p.y, o);
+    float2 vk[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = k + 1 + lane + 32 * q;
+      vk[q] = (q == 0 && lane == 0) ? make_float2(1.f, 0.f) : (i < n ? cm(x[q], sc) : make_float2(0.f, 0.f));
+    }
+    if (warp == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = k + 1 + lane + 32 * q;
+        if (i < n) R[roff + i - k - 1] = vk[q];
       }
       if (lane == 0) {
-        red[warp][0] = p.x;
-        red[warp][1] = p.y;
+        tau[k] = tk;
+        e[k] = ek;
+        d[k] = A[k * ld + k].x - 2.f * wk.x;
       }
-      __syncthreads();
-      if (t == 0) {
-        float2 tot = make_float2(0.f, 0.f);
-        for (int w = 0; w < EH_THREADS / 32; ++w) {
-          tot.x += red[w][0];
-          tot.y += red[w][1];
+    }
+    // trailing block: apply the update of step k-1, then w'_i = tau_k sum_j A_ij v_j; the
+    // four rows' sums are reduced together so their shuffle latencies overlap
+    float2 acc[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = k + 1 + warp + 32 * r;
+      acc[r] = make_float2(0.f, 0.f);
+      if (i < n) {                                                   // warp-uniform
+        float2 vi = make_float2(0.f, 0.f), wi = make_float2(0.f, 0.f);
+        if (hp) {
+          vi = R[rprev + i - k];
+          wi = cadd(wvp[pb][i], cm(ap, vi));
         }
-        const float2 h = cm(tk, tot);
-        s_alpha = make_float2(-0.5f * h.x, -0.5f * h.y);
+        float2* arow = A + i * ld;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = k + 1 + lane + 32 * q;
+          if (j < n) {
+            float2 a = arow[j];
+            if (hp) {
+              // v_i conj(w_j) + w_i conj(v_j)
+              a.x -= (vi.x * wp[q].x + vi.y * wp[q].y) + (wi.x * vp[q].x + wi.y * vp[q].y);
+              a.y -= (vi.y * wp[q].x - vi.x * wp[q].y) + (wi.y * vp[q].x - wi.x * vp[q].y);
+            }
+            if (i == j) a.y = 0.f;
+            arow[j] = a;
+            acc[r].x += a.x * vk[q].x - a.y * vk[q].y;
+            acc[r].y += a.x * vk[q].y + a.y * vk[q].x;
+          }
+        }
       }
-      __syncthreads();
     }
-    {
-      const float2 al = s_alpha;
-      for (int i = t; i < m; i += EH_THREADS) {
-        const float2 a = cm(al, v[i]);
-        wv[i] = make_float2(wv[i].x + a.x, wv[i].y + a.y);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        acc[r].x += __shfl_xor_sync(FULL, acc[r].x, o);
+        acc[r].y += __shfl_xor_sync(FULL, acc[r].y, o);
+      }
+    float2 pw = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = k + 1 + warp + 32 * r;
+      // v_k at row i lives in lane (i - k - 1) & 31 = warp, slot r
+      const float2 vr = make_float2(__shfl_sync(FULL, vk[r].x, warp), __shfl_sync(FULL, vk[r].y, warp));
+      if (i < n) {
+        const float2 w = cm(tk, acc[r]);
+        if (lane == 0) wvp[k & 1][i] = w;
+        const float2 c = cmc(w, vr);
+        pw.x += c.x;
+        pw.y += c.y;
       }
     }
-    __syncthreads();
-    // A_t -= v w^H + w v^H
-    for (int idx = t; idx < m * m; idx += EH_THREADS) {
-      const int i = idx / m, j = idx - (idx / m) * m;
-      const float2 vi = v[i], vj = v[j], wi = wv[i], wj = wv[j];
-      float2 a = A[(k + 1 + i) * ld + (k + 1 + j)];
-      // v_i conj(w_j) + w_i conj(v_j)
-      a.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
-      a.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
-      if (i == j) a.y = 0.f;
-      A[(k + 1 + i) * ld + (k + 1 + j)] = a;
-    }
+    if (lane == 0) red[k & 1][warp] = pw;
+    rprev = roff;
     roff += m;
     __syncthreads();
   }
   if (t == 0) {
-    d[n - 1] = A[(n - 1) * ld + (n - 1)].x;
+    if (n >= 2) {
+      // last pending update (v_{n-2} = (1)), then d_{n-1}
+      float2 s = make_float2(0.f, 0.f);
+      for (int w = 0; w < EH_WARPS; ++w) s = cadd(s, red[n & 1][w]);
+      const float2 h = cm(tau[n - 2], s);
+      const float wl = wvp[n & 1][n - 1].x - 0.5f * h.x;
+      d[n - 1] = A[(n - 1) * ld + (n - 1)].x - 2.f * wl;
+    } else {
+      d[0] = A[0].x;
+    }
     e[n - 1] = 0.f;
   }
   __syncthreads();
 
   // ---- 2. split and eigenvalues ------------------------------------------------------------
-  float tnorm = 0.f;
   if (t == 0) {
     // blocks: e[i] negligible against its neighbours -> boundary after i
     int b0 = 0;
@@ -202,6 +247,7 @@ __global__ void __launch_bounds__(EH_THREADS, 1)
     for (int i = 0; i < n; ++i) e2[i] = e[i] * e[i];
   }
   __syncthreads();
+  float tnorm = 0.f;
   for (int i = 0; i < n; ++i) tnorm = fmaxf(tnorm, fabsf(d[i]) + fabsf(e[i]) + (i > 0 ? fabsf(e[i - 1]) : 0.f));
   {
     // slot = t / 8 (one eigenvalue), 8 lanes evaluate 8 interior points of the interval
@@ -224,15 +270,18 @@ __global__ void __launch_bounds__(EH_THREADS, 1)
       lo -= pad;
       hi += pad;
     }
-    for (int iter = 0; iter < 14; ++iter) {
-      const float x = lo + (hi - lo) * (float)(sub + 1) / 9.f;
-      const int c = active ? sturm_count(d, e2, b0, b1, x, 1e-30f) : 0;
+    const float width = 4.8e-7f * tnorm + 1e-30f;                    // ~4 ulps of |T|
+    for (int iter = 0; iter < 24; ++iter) {
+      const bool need = active && (hi - lo > width);
+      if (!__any_sync(FULL, need)) break;
+      const float x = lo + (hi - lo) * (float)(sub + 1) * (1.f / 9.f);
+      const int c = need ? sturm_count(d, e2, b0, b1, x, 1e-30f) : 0;
       // new lo: largest x with count <= kth; new hi: smallest x with count >= kth + 1
-      float nlo = (c <= kth) ? x : -1e30f;
-      float nhi = (c >= kth + 1) ? x : 1e30f;
+      float nlo = (need && c <= kth) ? x : -1e30f;
+      float nhi = (need && c >= kth + 1) ? x : 1e30f;
       for (int o = 4; o > 0; o >>= 1) {
-        nlo = fmaxf(nlo, __shfl_xor_sync(0xffffffffu, nlo, o));
-        nhi = fminf(nhi, __shfl_xor_sync(0xffffffffu, nhi, o));
+        nlo = fmaxf(nlo, __shfl_xor_sync(FULL, nlo, o));
+        nhi = fminf(nhi, __shfl_xor_sync(FULL, nhi, o));
       }
       if (nlo > lo) lo = nlo;
       if (nhi < hi) hi = nhi;
@@ -241,191 +290,248 @@ __global__ void __launch_bounds__(EH_THREADS, 1)
   }
   __syncthreads();
 
-  // ---- 3. eigenvectors of T by twisted factorization -------------------------------------------
-  // Z (real) in the upper half of the A region; D+ and D- scratch in the lower half.
-  const int zld = n + 1;                                            // padded: row-parallel solves
-  float* Zr = reinterpret_cast<float*>(esm) + EH_MAXN * EH_MAXN;     // [n][zld] real, Z[i][slot]
-  float* scratch = reinterpret_cast<float*>(esm);                   // 64 slots x 2n floats
+  // ---- 3. eigenvectors of T ----------------------------------------------------------------
+  // Z (real, [n][zld]) in the upper half of the A region; D- pivots [n][n] and later
+  // Z^T Z in the lower half.
+  const int zld = n + 1;
+  const float tiny = 1e-30f + 1e-13f * tnorm;                        // pivot floor
+  float* Zr = reinterpret_cast<float*>(esm) + EH_MAXN * EH_MAXN;
+  float* low = reinterpret_cast<float*>(esm);
   for (int idx = t; idx < n * zld; idx += EH_THREADS) Zr[idx] = 0.f;
   __syncthreads();
-  for (int base = 0; base < n; base += 64) {
-    const int slot = base + t;
-    if (t < 64 && slot < n) {
-      float* dp = scratch + (size_t)t * 2 * EH_MAXN;
-      float* dm = dp + EH_MAXN;
-      const int b0 = blk_lo[slot], b1 = blk_hi[slot];
-      const float x = lam[slot];
-      const float tiny = 1e-30f + 1e-7f * tnorm * 1e-6f;
-      if (b0 == b1) {
-        Zr[b0 * zld + slot] = 1.f;
-      } else {
-        float q = d[b0] - x;
+  if (t < n) {
+    const int slot = t;
+    const int b0 = blk_lo[slot], b1 = blk_hi[slot];
+    const float x = lam[slot];
+    if (b0 == b1) {
+      Zr[b0 * zld + slot] = 1.f;
+    } else {
+      // backward pivots D-: dm_i = d_i - x - e_i^2 / dm_{i+1}, kept in low[i][slot]
+      float q = d[b1] - x;
+      if (fabsf(q) < tiny) q = tiny;
+      low[b1 * n + slot] = q;
+      for (int i = b1 - 1; i >= b0; --i) {
+        q = d[i] - x - __fdividef(e2[i], q);
         if (fabsf(q) < tiny) q = tiny;
-        dp[b0] = q;
-        for (int i = b0 + 1; i <= b1; ++i) {
-          q = d[i] - x - e2[i - 1] / q;
-          if (fabsf(q) < tiny) q = tiny;
-          dp[i] = q;
-        }
-        q = d[b1] - x;
-        if (fabsf(q) < tiny) q = tiny;
-        dm[b1] = q;
-        for (int i = b1 - 1; i >= b0; --i) {
-          q = d[i] - x - e2[i] / q;
-          if (fabsf(q) < tiny) q = tiny;
-          dm[i] = q;
-        }
-        int r = b0;
-        float best = 3.4e38f;
-        for (int i = b0; i <= b1; ++i) {
-          const float g = fabsf(dp[i] + dm[i] - (d[i] - x));
-          if (g < best) {
-            best = g;
-            r = i;
-          }
-        }
-        float nrm = 1.f;
-        Zr[r * zld + slot] = 1.f;
-        float z = 1.f;
-        for (int i = r - 1; i >= b0; --i) {
-          z = -(e[i] / dp[i]) * z;
-          Zr[i * zld + slot] = z;
-          nrm += z * z;
-        }
-        z = 1.f;
-        for (int i = r + 1; i <= b1; ++i) {
-          z = -(e[i - 1] / dm[i]) * z;
-          Zr[i * zld + slot] = z;
-          nrm += z * z;
-        }
-        const float inv = rsqrtf(nrm);
-        for (int i = b0; i <= b1; ++i) Zr[i * zld + slot] *= inv;
+        low[i * n + slot] = q;
       }
+      // forward pivots D+ with gamma_i = dp_i + dm_i - (d_i - x); the ratios -e_i / dp_i
+      // go to Z's column until the twist index r (argmin |gamma|) is known
+      int r = b0;
+      float best = 3.4e38f;
+      q = d[b0] - x;
+      if (fabsf(q) < tiny) q = tiny;
+      for (int i = b0; i <= b1; ++i) {
+        if (i > b0) {
+          q = d[i] - x - __fdividef(e2[i - 1], q);
+          if (fabsf(q) < tiny) q = tiny;
+        }
+        const float g = fabsf(q + low[i * n + slot] - (d[i] - x));
+        if (g < best) {
+          best = g;
+          r = i;
+        }
+        if (i < b1) Zr[i * zld + slot] = -__fdividef(e[i], q);
+      }
+      float nrm = 1.f, z = 1.f;
+      for (int i = r - 1; i >= b0; --i) {
+        z *= Zr[i * zld + slot];
+        Zr[i * zld + slot] = z;
+        nrm += z * z;
+      }
+      Zr[r * zld + slot] = 1.f;
+      z = 1.f;
+      for (int i = r + 1; i <= b1; ++i) {
+        z *= -__fdividef(e[i - 1], low[i * n + slot]);
+        Zr[i * zld + slot] = z;
+        nrm += z * z;
+      }
+      const float inv = rsqrtf(nrm);
+      for (int i = b0; i <= b1; ++i) Zr[i * zld + slot] *= inv;
     }
-    __syncthreads();
   }
-  // Gram-Schmidt inside numerically degenerate clusters of a block (lam gaps <= 1e-5 |T|),
-  // where twisted-factorization vectors can be nearly parallel.  One warp per block.
-  for (int b = warp; b < n; b += EH_THREADS / 32) {
+  __syncthreads();
+  // Degenerate clusters of a block (lam gaps <= 1e-5 |T|): twisted factorization returns
+  // (nearly) the same vector for every member, so each member after the first is recomputed
+  // by inverse iteration -- two LDL^T solves of (T - lam_j) y = x from a pseudo-random start,
+  // each followed by Gram-Schmidt against the earlier members of the cluster (the scheme of
+  // LAPACK's stein).  One warp per block; lane 0 runs the serial solves.
+  for (int b = warp; b < n; b += EH_WARPS) {
     if (blk_lo[b] != b) continue;
     const int b1 = blk_hi[b];
+    float* Lc = low + warp * EH_MAXN;                                // L's subdiagonal
     for (int j = b + 1; j <= b1; ++j) {
       int c0 = j;
       while (c0 > b && lam[c0] - lam[c0 - 1] <= 1e-5f * tnorm) --c0;
       if (c0 == j) continue;
-      for (int p = c0; p < j; ++p) {
-        float s = 0.f;
-        for (int i = b + lane; i <= b1; i += 32) s += Zr[i * zld + p] * Zr[i * zld + j];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        for (int i = b + lane; i <= b1; i += 32) Zr[i * zld + j] -= s * Zr[i * zld + p];
+      for (int i = b + lane; i <= b1; i += 32) {
+        const unsigned hsh = (unsigned)(i * 131 + j * 7919) * 2654435761u;
+        Zr[i * zld + j] = (float)(hsh >> 16) * (1.f / 32768.f) - 1.f;
+      }
+      __syncwarp();
+      const float lj = lam[j];
+      for (int it = 0; it < 2; ++it) {
+        if (lane == 0) {
+          float piv = d[b] - lj;
+          if (fabsf(piv) < tiny) piv = tiny;
+          float u = Zr[b * zld + j];
+          Zr[b * zld + j] = __fdividef(u, piv);
+          for (int i = b + 1; i <= b1; ++i) {
+            const float l = __fdividef(e[i - 1], piv);
+            Lc[i - 1] = l;
+            piv = d[i] - lj - l * e[i - 1];
+            if (fabsf(piv) < tiny) piv = tiny;
+            u = Zr[i * zld + j] - l * u;
+            Zr[i * zld + j] = __fdividef(u, piv);
+          }
+          for (int i = b1 - 1; i >= b; --i) Zr[i * zld + j] -= Lc[i] * Zr[(i + 1) * zld + j];
+        }
+        __syncwarp();
+        for (int p = c0; p < j; ++p) {
+          float sd = 0.f;
+          for (int i = b + lane; i <= b1; i += 32) sd += Zr[i * zld + p] * Zr[i * zld + j];
+          for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(FULL, sd, o);
+          for (int i = b + lane; i <= b1; i += 32) Zr[i * zld + j] -= sd * Zr[i * zld + p];
+          __syncwarp();
+        }
+        float sn = 0.f;
+        for (int i = b + lane; i <= b1; i += 32) sn += Zr[i * zld + j] * Zr[i * zld + j];
+        for (int o = 16; o > 0; o >>= 1) sn += __shfl_xor_sync(FULL, sn, o);
+        const float inv = rsqrtf(fmaxf(sn, 1e-30f));
+        for (int i = b + lane; i <= b1; i += 32) Zr[i * zld + j] *= inv;
         __syncwarp();
       }
-      float s = 0.f;
-      for (int i = b + lane; i <= b1; i += 32) s += Zr[i * zld + j] * Zr[i * zld + j];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      const float inv = rsqrtf(fmaxf(s, 1e-30f));
-      for (int i = b + lane; i <= b1; i += 32) Zr[i * zld + j] *= inv;
-      __syncwarp();
     }
   }
   __syncthreads();
-  // Cholesky-QR of Z (real): G = Z^T Z = L L^T, Z <- Z L^{-T}.  Close but separated
-  // eigenvalues leave Z orthogonal only to ~eps |T| / gap; this restores orthonormality
-  // (G = I + O(1e-4), so L is well conditioned and the columns stay eigenvectors).
+  // Newton-Schulz: G = Z^T Z; while max |G - I| > 2e-6: Z <- 1.5 Z - 0.5 Z G.
+  // Thread tiles: rows warp + 32u, columns lane + 32v (u, v < 4).
   {
-    float* G = scratch;                                              // [n][n] real, lower
-    for (int idx = t; idx < n * n; idx += EH_THREADS) {
-      const int i = idx / n, j = idx - (idx / n) * n;
-      if (j > i) continue;
-      float acc = 0.f;
-      for (int r = 0; r < n; ++r) acc += Zr[r * zld + i] * Zr[r * zld + j];
-      G[i * n + j] = acc;
-    }
-    __syncthreads();
-    for (int j = 0; j < n; ++j) {
-      if (t == 0) G[j * n + j] = sqrtf(fmaxf(G[j * n + j], 1e-30f));
+    float* G = low;                                                  // [n][n]
+    for (int it = 0; it < 4; ++it) {
+      float g[4][4] = {};
+      for (int i = 0; i < n; ++i) {
+        float za[4], zb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int a = warp + 32 * u, b = lane + 32 * u;
+          za[u] = a < n ? Zr[i * zld + a] : 0.f;
+          zb[u] = b < n ? Zr[i * zld + b] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) g[u][v] += za[u] * zb[v];
+      }
+      float err = 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int a = warp + 32 * u, b = lane + 32 * v;
+          if (a < n && b < n) {
+            G[a * n + b] = g[u][v];
+            err = fmaxf(err, fabsf(g[u][v] - (a == b ? 1.f : 0.f)));
+          }
+        }
+      for (int o = 16; o > 0; o >>= 1) err = fmaxf(err, __shfl_xor_sync(FULL, err, o));
+      if (lane == 0) s_err[warp] = err;
       __syncthreads();
-      const float inv = 1.f / G[j * n + j];
-      for (int i = j + 1 + t; i < n; i += EH_THREADS) G[i * n + j] *= inv;
-      __syncthreads();
-      const int mm = n - 1 - j;
-      for (int idx = t; idx < mm * mm; idx += EH_THREADS) {
-        const int i = j + 1 + idx / mm, k = j + 1 + idx % mm;
-        if (k <= i) G[i * n + k] -= G[i * n + j] * G[k * n + j];
+      float emax = 0.f;
+      for (int w = 0; w < EH_WARPS; ++w) emax = fmaxf(emax, s_err[w]);
+      if (!(emax > 2e-6f)) break;                                    // uniform
+      float z[4][4] = {};
+      for (int b = 0; b < n; ++b) {
+        float zr[4], gb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = warp + 32 * u, a = lane + 32 * u;
+          zr[u] = i < n ? Zr[i * zld + b] : 0.f;
+          gb[u] = a < n ? G[b * n + a] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) z[u][v] += zr[u] * gb[v];
       }
       __syncthreads();
-    }
-    // row r of Z: x L^T = z  ->  x_j = (z_j - sum_{k<j} x_k L_jk) / L_jj
-    if (t < n) {
-      float* zrow = Zr + t * zld;
-      for (int j = 0; j < n; ++j) {
-        float acc = zrow[j];
-        for (int k = 0; k < j; ++k) acc -= zrow[k] * G[j * n + k];
-        zrow[j] = acc / G[j * n + j];
-      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int i = warp + 32 * u, a = lane + 32 * v;
+          if (i < n && a < n) Zr[i * zld + a] = 1.5f * Zr[i * zld + a] - 0.5f * z[u][v];
+        }
+      __syncthreads();
     }
   }
-  __syncthreads();
 
   // ---- 4. V = H_0 ... H_{n-2} Z ------------------------------------------------------------
-  // expand Z to complex in the A region (row-major, ld = n)
-  float2* V = A;
+  // thread (column j = t / 8, s = t % 8) holds rows s + 8p, p < 16.  The reflectors are
+  // expanded into a zero-padded [n-1][EH_MAXN] layout in the A region (v_k[i] = 0 for i <= k
+  // and i >= n), so no row needs a bounds test.
   {
-    float zr[EH_MAXN * EH_MAXN / EH_THREADS];
+    const int j = t >> 3, s = t & 7;
+    float2 V[16];
 #pragma unroll
-    for (int q = 0; q < EH_MAXN * EH_MAXN / EH_THREADS; ++q) {
-      const int idx = t + q * EH_THREADS;
-      zr[q] = idx < n * n ? Zr[(idx / n) * zld + idx % n] : 0.f;
+    for (int p = 0; p < 16; ++p) {
+      const int i = s + 8 * p;
+      V[p] = make_float2((i < n && j < n) ? Zr[i * zld + j] : 0.f, 0.f);
     }
     __syncthreads();
+    float2* Rf = A;
+    for (int idx = t; idx < (n - 1) * EH_MAXN; idx += EH_THREADS) {
+      const int k = idx / EH_MAXN, i = idx - k * EH_MAXN;
+      const int ro = k * (n - 1) - (k * (k - 1)) / 2;
+      Rf[idx] = (i > k && i < n) ? R[ro + i - k - 1] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int k = n - 2; k >= 0; --k) {
+      const float2 tk = tau[k];
+      if (tk.x == 0.f && tk.y == 0.f) continue;                      // uniform
+      const float2* v = Rf + k * EH_MAXN + s;                        // v[8p] = v_k at row s + 8p
+      const int pskip = (k + 1) >> 3;                                // rows s + 8p < k+1 below
+      float2 dot = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < EH_MAXN * EH_MAXN / EH_THREADS; ++q) {
-      const int idx = t + q * EH_THREADS;
-      if (idx < n * n) V[idx] = make_float2(zr[q], 0.f);
+      for (int p = 0; p < 16; ++p) {
+        if (p >= pskip) {
+          const float2 c = cmc(v[8 * p], V[p]);
+          dot.x += c.x;
+          dot.y += c.y;
+        }
+      }
+      for (int o = 4; o > 0; o >>= 1) {
+        dot.x += __shfl_xor_sync(FULL, dot.x, o);
+        dot.y += __shfl_xor_sync(FULL, dot.y, o);
+      }
+      const float2 c = cm(tk, dot);
+#pragma unroll
+      for (int p = 0; p < 16; ++p)
+        if (p >= pskip) V[p] = csub(V[p], cm(v[8 * p], c));
+    }
+    // stage through shared memory (the A region) for coalesced complex128 stores
+    __syncthreads();
+    float2* Vs = A;                                                  // [n][ld]
+    if (j < n) {
+#pragma unroll
+      for (int p = 0; p < 16; ++p) {
+        const int i = s + 8 * p;
+        if (i < n) Vs[i * ld + j] = V[p];
+      }
     }
   }
   __syncthreads();
-  for (int k = n - 2; k >= 0; --k) {
-    const int m = n - k - 1;
-    roff -= m;
-    const float2 tk = tau[k];
-    if (tk.x == 0.f && tk.y == 0.f) continue;
-    const float2* v = R + roff;
-    // s_j = sum_i conj(v_i) V[k+1+i][j]; 8 threads per column
-    {
-      const int col = t >> 3, sub = t & 7;
-      float2 acc = make_float2(0.f, 0.f);
-      if (col < n)
-        for (int i = sub; i < m; i += 8) {
-          const float2 q = cmc(v[i], V[(k + 1 + i) * n + col]);
-          acc.x += q.x;
-          acc.y += q.y;
-        }
-      for (int o = 4; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-      }
-      if (col < n && sub == 0) wv[col] = cm(tk, acc);
-    }
-    __syncthreads();
-    for (int idx = t; idx < m * n; idx += EH_THREADS) {
-      const int i = idx / n, j = idx - (idx / n) * n;
-      const float2 a = cm(v[i], wv[j]);
-      float2 x = V[(k + 1 + i) * n + j];
-      V[(k + 1 + i) * n + j] = make_float2(x.x - a.x, x.y - a.y);
-    }
-    __syncthreads();
-  }
   for (int idx = t; idx < n * n; idx += EH_THREADS) {
-    const float2 x = V[idx];
-    Vout[idx] = make_double2((double)x.x, (double)x.y);
+    const int i = idx / n, j = idx - (idx / n) * n;
+    const float2 v = A[i * ld + j];
+    Vout[idx] = make_double2((double)v.x, (double)v.y);
   }
 }
 
 }  // namespace
 
 void eigh_householder_f32(const double2* A, double2* V, int n, cudaStream_t s) {
-  if (n > EH_MAXN) fail(KS_ERR_ARG, "eigh_householder_f32: n=%d > %d", n, EH_MAXN);
+  if (n > EH_MAXN || n < 1) fail(KS_ERR_ARG, "eigh_householder_f32: n=%d not in [1, %d]", n, EH_MAXN);
   const size_t smem = ((size_t)EH_MAXN * (EH_MAXN + 1) + (size_t)EH_MAXN * (EH_MAXN - 1) / 2) * sizeof(float2);
   static bool attr = false;
   if (!attr) {

@@ -162,6 +162,7 @@ template <typename T> class Engine final : public EngineBase {
     mV_ = alloc<double2>(nn);
     eig_ = alloc<double>(ns_);
     lam_ = alloc<double>(ns_);
+    if (mixed_cholesky()) chw_ = alloc<double2>(cholesky_mixed_workspace(ns_));
     // ---- potentials / real-time
     dens_ = alloc<T>(N3);
     pwork_ = alloc<C>(N3);
@@ -192,14 +193,6 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaMemcpyAsync(c_host, staging_, sn * sizeof(double2), cudaMemcpyDeviceToHost, s));
     KS_CUDA(cudaStreamSynchronize(s));
   }
-
-  void sync_counters() override {
-    int sweeps = 0;
-    KS_CUDA(cudaMemcpy(&sweeps, status_ + 2, sizeof(int), cudaMemcpyDeviceToHost));
-    prof.set_counter("eigh_sweeps", sweeps);
-  }
-
-  void reset_counters() override { KS_CUDA(cudaMemset(status_ + 2, 0, sizeof(int))); }
 
   void randomize_states(uint64_t seed, cudaStream_t s) override {
     random_states<T>(psi_, (size_t)ns_ * g_.nG, seed, s);
@@ -300,40 +293,51 @@ template <typename T> class Engine final : public EngineBase {
   // ------------------------------------------------------------------------------------------
   // CholQR: S = Psi^H Psi, S = L L^H, Psi <- Psi L^{-H}  (rows: psi <- conj(L^{-1}) psi)
   // ------------------------------------------------------------------------------------------
-  void cholqr(cudaStream_t s, bool keep_S) {
-    const int n = ns_, nG = g_.nG;
+  void cholqr_factor(cudaStream_t s) {
+    const int n = ns_;
     {
       ProfScope p(prof, "gram", s);
       overlap(psi_, psi_, n, mS_, s);
       hermitize(mS_, n, s);
     }
-    {
-      ProfScope p(prof, "cholesky", s);
-      if (sizeof(T) == 4 && n <= 128) {
-        cholesky_inverse_mixed(mS_, mM_, n, 1e-6, status_, s);
-      } else {
-        KS_CUDA(cudaMemcpyAsync(mA_, mS_, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-        cholesky_inverse_tol(mA_, mM_, n, sizeof(T) == 8 ? 1e-12 : 1e-6, status_, s);
-      }
+    ProfScope p(prof, "cholesky", s);
+    if (mixed_cholesky()) {
+      cholesky_inverse_mixed(mS_, mM_, n, 1e-6, chw_, status_, s);
+    } else {
+      KS_CUDA(cudaMemcpyAsync(mA_, mS_, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+      cholesky_inverse_tol(mA_, mM_, n, sizeof(T) == 8 ? 1e-12 : 1e-6, status_, s);
     }
+  }
+
+  void cholqr_rotate(cudaStream_t s) {
     C* out = spare(psi_, hpsi_);
     {
       ProfScope p(prof, "rotate", s);
       rot(mM_, psi_, out, s);
     }
     swap_in(psi_, out);
-    (void)keep_S;
   }
 
+  // Inside the block iteration a failed factor leaves M = I (the status is read at the end).
+  void cholqr(cudaStream_t s) {
+    cholqr_factor(s);
+    cholqr_rotate(s);
+  }
+
+  // The public call reads the status before rotating, so a failure leaves the states as they
+  // were on every precision path.
   void orthonormalize(double* S_host, cudaStream_t s) override {
     KS_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), s));
-    cholqr(s, S_host != nullptr);
+    cholqr_factor(s);
     int st = 0;
     KS_CUDA(cudaMemcpyAsync(&st, status_, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (S_host) KS_CUDA(cudaMemcpyAsync(S_host, mS_, (size_t)ns_ * ns_ * sizeof(double2), cudaMemcpyDeviceToHost, s));
     KS_CUDA(cudaStreamSynchronize(s));
     check_tc_status(s);
     if (st) fail(KS_ERR_NOT_POSDEF, "CholQR: Gram matrix not positive definite at column %d", st - 1);
+    cholqr_rotate(s);
+    KS_CUDA(cudaStreamSynchronize(s));
+    check_tc_status(s);
   }
 
   // Rayleigh-Ritz on (psi_, hpsi_): H_sub = Psi^H H Psi, eigh, rotate both.
@@ -347,7 +351,7 @@ template <typename T> class Engine final : public EngineBase {
     {
       ProfScope p(prof, "eigh", s);
       if (sizeof(T) == 4 && n <= 128)
-        jacobi_eigh_mixed(mA_, mV_, lam_, eig_, mM_, n, status_ + 2, s);
+        eigh_mixed(mA_, mV_, lam_, eig_, mM_, n, s);
       else
         jacobi_eigh(mA_, mV_, eig_, mM_, n, s);
     }
@@ -372,7 +376,7 @@ template <typename T> class Engine final : public EngineBase {
     const double alpha = 1.0 / (g_.ecut + (g_.vmax - g_.vmin) + g_.D);
     KS_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), s));
     for (int it = 0; it < niter; ++it) {
-      cholqr(s, false);
+      cholqr(s);
       apply_h(psi_, hpsi_, ns_, s);
       rr_core(s);
       ProfScope p(prof, "sd_update", s);
@@ -484,6 +488,7 @@ template <typename T> class Engine final : public EngineBase {
     fail(KS_ERR_STATE, "internal: no spare state buffer");
   }
   bool use_tc() const { return sizeof(T) == 4 && prec_ == KS_MIXED_BF16X3; }
+  bool mixed_cholesky() const { return sizeof(T) == 4 && ns_ <= 160; }
 
   // out = A^H B over the sphere (n x n), tensor cores on the bf16x3 mixed path
   void overlap(const C* A, const C* B, int n, double2* out, cudaStream_t s) {
@@ -556,6 +561,7 @@ template <typename T> class Engine final : public EngineBase {
   double2 *mS_ = nullptr, *mA_ = nullptr, *mM_ = nullptr, *mV_ = nullptr;
   double* eig_ = nullptr;
   double* lam_ = nullptr;
+  double2* chw_ = nullptr;   // two-pass FP32 Cholesky workspace (mixed path)
   void* rotws_ = nullptr;
   size_t rotws_bytes_ = 0;
   int* status_ = nullptr;

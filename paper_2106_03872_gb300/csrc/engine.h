@@ -37,15 +37,6 @@ class StageProfiler {
   void end(int slot, cudaStream_t s);
   void collect();
   const std::vector<Entry>& entries() const { return entries_; }
-  // An entry that carries a count only (ms = 0), e.g. iteration counts of a kernel.
-  void set_counter(const char* name, long value) {
-    for (auto& e : entries_)
-      if (e.name == name) {
-        e.count = value;
-        return;
-      }
-    entries_.push_back(Entry{name, 0.0, value});
-  }
   void reset() {
     collect();
     entries_.clear();
@@ -96,9 +87,6 @@ class EngineBase {
   virtual void td_steps(double dt, int nsteps, int propagator, int hartree_xc, double* norm_out,
                         double* energy_out, cudaStream_t s) = 0;
   virtual void randomize_states(uint64_t seed, cudaStream_t s) = 0;
-  // Copy device-side instrumentation counters into the profiler (no-op by default).
-  virtual void sync_counters() {}
-  virtual void reset_counters() {}
 };
 
 std::unique_ptr<EngineBase> make_engine(const ks_cell_desc& d);

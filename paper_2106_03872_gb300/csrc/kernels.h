@@ -88,21 +88,22 @@ void hermitize(double2* A, int n, cudaStream_t s);
 void cholesky_inverse(double2* A, double2* M, int n, int* status, cudaStream_t s);
 // Same with an explicit relative pivot tolerance (pivot <= tol * S_jj fails).
 void cholesky_inverse_tol(double2* A, double2* M, int n, double tol, int* status, cudaStream_t s);
-// Mixed path (n <= 128): FP64 Cholesky of the Hermitian S in shared memory, M = conj(L^{-1})
-// from an FP32 forward substitution.  Same status convention as cholesky_inverse.
-void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, int* status, cudaStream_t s);
+// Mixed path (n <= 160): M = conj(L^{-1}) for S = L L^H from two FP32 Cholesky passes
+// refined by FP64 triangular products (cholqr_mixed.cu); work holds
+// cholesky_mixed_workspace(n) complex128.  Same status convention as cholesky_inverse.
+size_t cholesky_mixed_workspace(int n);
+void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, double2* work, int* status,
+                            cudaStream_t s);
 // Hermitian eigen-decomposition of A (destroyed) by cyclic Jacobi; eig ascending, rows of
 // Vt = eigenvectors (largest-magnitude component real positive).  `V` is n*n workspace.
 void jacobi_eigh(double2* A, double2* V, double* eig, double2* Vt, int n, cudaStream_t s);
-// Mixed: FP32 Jacobi in shared memory (n <= 128) on a copy of the FP64 Hermitian A (kept),
-// eigenvalues = FP64 Rayleigh quotients of the FP32 vectors on A; same outputs as jacobi_eigh.
-// V is n*n workspace, lam n doubles of workspace.
 // Householder + bisection + twisted-factorization eigenvectors, FP32, one CTA (n <= 128):
 // V (n x n complex128, columns = eigenvectors, unsorted).
 void eigh_householder_f32(const double2* A, double2* V, int n, cudaStream_t s);
-// sweeps (may be NULL) accumulates the number of Jacobi sweeps (instrumentation).
-void jacobi_eigh_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, int n, int* sweeps,
-                       cudaStream_t s);
+// Mixed path (n <= 128): eigh_householder_f32 on the FP64 Hermitian A (kept), eigenvalues =
+// FP64 Rayleigh quotients of the FP32 vectors on A; same outputs as jacobi_eigh.
+// V is n*n workspace, lam n doubles of workspace.
+void eigh_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, int n, cudaStream_t s);
 
 // ---- tensor-core GEMMs (tc_gemm.cu), split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulation ---------
 // Same contract as gemm_cn<float> / rotate<float>; err receives 1 if a bounded wait expired.

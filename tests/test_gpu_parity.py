@@ -144,17 +144,40 @@ def test_orthonormalize_parity(ks, prec):
     g.close()
 
 
-def test_orthonormalize_rejects_dependent_states(ks):
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32"])
+def test_orthonormalize_rejects_dependent_states(ks, prec):
     cell = inputs.small_cell(10.0, 24, 2, 4, 9)
     ref = ko.Cell(cell)
-    g = ks.Grid(cell, prec="fp64")
+    g = ks.Grid(cell, prec=prec)
     c = inputs.random_coeffs(9, 4, ref.nG)
     c[2] = c[1]
     g.set_states(c)
+    before = g.get_states()
     with pytest.raises(ks.KsError) as e:
         g.orthonormalize()
     assert e.value.status == ks.KS_ERR_NOT_POSDEF
-    assert rel(g.get_states(), c) <= 1e-15          # unchanged
+    assert np.array_equal(g.get_states(), before)          # unchanged
+    assert rel(before, c) <= (1e-15 if prec == "fp64" else 1e-7)
+    g.close()
+
+
+@pytest.mark.parametrize("n", [64, 150])
+def test_mixed_cholesky_matches_fp64_factor_of_same_S(ks, n):
+    """The two-pass FP32 factor against an FP64 Cholesky of the very S the GPU formed, on a
+    block with cond(S) ~ 1e4: one FP32 pass would be off by ~eps_32 cond(S) ~ 1e-3."""
+    cell = inputs.small_cell(12.0, 32, 2, n, 31)
+    ref = ko.Cell(cell)
+    rng = np.random.default_rng(31)
+    u, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    v, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    c = (u * np.logspace(0.0, -2.0, n)) @ v @ inputs.random_coeffs(31, n, ref.nG)
+    g = ks.Grid(cell, prec="tf32")
+    g.set_states(c)
+    c32 = g.get_states()
+    S = g.orthonormalize(want_S=True)
+    q_ref, _ = ko.cholqr(c32, S=S)
+    # FP32 rotation by M = L^{-1} (cond 1e2) of FP32 states: ~eps_32 cond(L) sqrt(n)
+    assert rel(g.get_states(), q_ref) <= 3e-5
     g.close()
 
 
@@ -294,19 +317,20 @@ def test_orthonormalize_parity_two_tiles(ks, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
-def test_rayleigh_ritz_degenerate_shells(ks, prec):
-    """Free electrons: 19 plane waves (|m|^2 <= 2: shells of 1, 6 and 12), mixed by a random
-    unitary.  Rayleigh-Ritz must return the exact shell energies and orthonormal eigenvectors
-    even though the eigenvalues are exactly degenerate."""
-    cell = inputs.small_cell(8.0, 24, 0, 19, 19)
+@pytest.mark.parametrize("m2max,nshell", [(2, 19), (5, 57), (9, 123)])
+def test_rayleigh_ritz_degenerate_shells(ks, prec, m2max, nshell):
+    """Free electrons: the plane waves with |m|^2 <= m2max (shells of 1, 6, 12, 8, 6, 24, ...
+    states), mixed by a random unitary.  Rayleigh-Ritz must return the exact shell energies and
+    orthonormal eigenvectors even though the eigenvalues are exactly degenerate."""
+    cell = inputs.small_cell(8.0, 24, 0, nshell, 19)
     ref = ko.Cell(cell)
     m2 = np.sum(ref.m ** 2, axis=1)
-    picks = np.flatnonzero(m2 <= 2)
-    assert len(picks) == 19
-    c = np.zeros((19, ref.nG), complex)
-    c[np.arange(19), picks] = 1.0
+    picks = np.flatnonzero(m2 <= m2max)
+    assert len(picks) == nshell
+    c = np.zeros((nshell, ref.nG), complex)
+    c[np.arange(nshell), picks] = 1.0
     rng = np.random.default_rng(3)
-    Q, _ = np.linalg.qr(rng.normal(size=(19, 19)) + 1j * rng.normal(size=(19, 19)))
+    Q, _ = np.linalg.qr(rng.normal(size=(nshell, nshell)) + 1j * rng.normal(size=(nshell, nshell)))
     c = Q @ c
     g = ks.Grid(cell, prec=prec)
     g.set_states(c)
@@ -314,7 +338,7 @@ def test_rayleigh_ritz_degenerate_shells(ks, prec):
     assert np.allclose(eps, np.sort(0.5 * ref.g2[picks]), atol=1e-11 if prec == "fp64" else 2e-5)
     q = g.get_states()
     tol = 1e-11 if prec == "fp64" else 1e-5
-    assert np.max(np.abs(ko.gram(q) - np.eye(19))) <= tol
+    assert np.max(np.abs(ko.gram(q) - np.eye(nshell))) <= tol
     hq = ko.apply_h(ref, q)
     assert np.max(np.abs(hq - eps[:, None] * q)) <= (1e-10 if prec == "fp64" else 1e-4)
     g.close()
