@@ -138,8 +138,26 @@ class Clocks:
 # ------------------------------------------------------------------------------------------------
 # Roofline of the dominant kernel (stage timings from the library's CUDA events)
 # ------------------------------------------------------------------------------------------------
-FP32_PEAK_TFLOPS = 69.46    # measured FP32 FMA rate of this GB300 (152 SMs, 2.07 GHz), see the design doc
-FP64_PEAK_TFLOPS = 1.195    # measured FP64 FMA rate
+# ALU peaks from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; FP64 is
+# GB300's nominal 1.25 TFLOP/s (an FMA probe measured 69.5 and 1.195 TFLOP/s)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def max_over_ranks(ms, dist, device):
+    """Job time of replicas: the slowest rank's time (every rank must call this)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_throughput(world, units_per_rank, job_ms):
+    """Whole-job throughput: units every rank processed / the job time (weak scaling)."""
+    return world * units_per_rank / (job_ms * 1e-3)
 
 
 def stage_model(name, geo, pk, fp32_tflops):
@@ -194,7 +212,8 @@ def roofline(entries, geo, pk, steps):
     else:
         achieved = amount / (per_launch_ms * 1e-3) / 1e12
     out.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": None, "peak_src": pk["src"]})
+                "traffic": None,
+                "peak_src": "derived: unit counts x max SM clock" if bound == "alu" else pk["src"]})
     return out, name
 
 
@@ -265,15 +284,9 @@ def main_gpu(args):
     with Clocks(local) as clk:
         times, launches, entries = timed_steps(g, args.steps, args.warmup,
                                                lambda: g.block_iteration(1, stream), profile=True)
-    if dist is not None:
-        t = torch.tensor([sum(times)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    else:
-        total_ms = sum(times)
+    total_ms = max_over_ranks(sum(times), dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * ns * N ** 3 * args.steps / (total_ms * 1e-3)
+    value = replica_throughput(world, ns * N ** 3 * args.steps, total_ms)
 
     rl, rl_name = roofline(entries, geo, pk, args.steps)
 
@@ -301,7 +314,8 @@ def main_gpu(args):
         t1 = time.perf_counter()
         if i >= args.warmup:
             e2e_times.append(t1 - t0)
-    e2e = {"value": world * ns * N ** 3 / statistics.mean(e2e_times), "unit": UNIT,
+    e2e_ms = max_over_ranks(1e3 * statistics.mean(e2e_times), dist, "cuda")
+    e2e = {"value": replica_throughput(world, ns * N ** 3, e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": ns * g.nG * 16, "d2h_bytes_per_step": ns * 8,
            "note": "set_states (pinned complex128 host -> device) + one block iteration + Ritz values to host"}
     assert np.all(np.isfinite(eig))
