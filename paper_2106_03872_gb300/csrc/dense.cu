@@ -4,6 +4,7 @@
 // FP64 Rayleigh quotients / sorting that finish the mixed path's FP32 eigenvectors.
 // CUDA-core versions templated on the real type of the states.
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -343,6 +344,58 @@ __global__ void k_rayleigh_quotients(const double2* __restrict__ H, const double
   }
 }
 
+// C = opA(A) opB(B) for n x n complex128 matrices (row-major).  flags: bit 0 conjugates A,
+// bit 1 transposes B (opB(B)_kj = B_jk), bit 2 conjugates B.  8 x 8 output tiles, K staged
+// through shared memory 32 at a time.  MIXED: products and sums in FP32 inside a 32-wide K
+// chunk, FP64 across chunks; otherwise FP64 throughout.
+template <bool MIXED>
+__global__ void __launch_bounds__(64) k_small_product(const double2* __restrict__ A, const double2* __restrict__ B,
+                                                      int n, int flags, double2* __restrict__ C) {
+  constexpr int KC = 32;
+  using R = typename std::conditional<MIXED, float, double>::type;
+  __shared__ double2 As[8][KC + 1];
+  __shared__ double2 Bs[8][KC + 1];                                  // Bs[j][k] = opB(B)_kj
+  const int ty = threadIdx.x >> 3, tx = threadIdx.x & 7;
+  const int I = blockIdx.y * 8, J = blockIdx.x * 8;
+  const bool ca = flags & 1, tb = flags & 2, cb = flags & 4;
+  double re = 0.0, im = 0.0;
+  for (int kc = 0; kc < n; kc += KC) {
+    for (int e = threadIdx.x; e < 8 * KC; e += 64) {
+      const int r = e / KC, k = kc + e % KC;
+      double2 a = (I + r < n && k < n) ? A[(size_t)(I + r) * n + k] : make_double2(0.0, 0.0);
+      if (ca) a.y = -a.y;
+      As[r][e % KC] = a;
+      double2 b;
+      int jj, kk;
+      if (tb) {                                                      // opB(B)_kj = B_jk: rows J..J+7
+        jj = r;
+        kk = e % KC;
+        b = (J + r < n && k < n) ? B[(size_t)(J + r) * n + k] : make_double2(0.0, 0.0);
+      } else {                                                       // B rows k, columns J..J+7
+        jj = e % 8;
+        kk = e / 8;
+        b = (kc + kk < n && J + jj < n) ? B[(size_t)(kc + kk) * n + J + jj] : make_double2(0.0, 0.0);
+      }
+      if (cb) b.y = -b.y;
+      Bs[jj][kk] = b;
+    }
+    __syncthreads();
+    R cr = 0, ci = 0;
+#pragma unroll 8
+    for (int kk = 0; kk < KC; ++kk) {
+      const double2 a = As[ty][kk], b = Bs[tx][kk];
+      const R ax = (R)a.x, ay = (R)a.y, bx = (R)b.x, by = (R)b.y;
+      cr += ax * bx - ay * by;
+      ci += ax * by + ay * bx;
+    }
+    re += (double)cr;
+    im += (double)ci;
+    __syncthreads();
+  }
+  const int i = I + ty, j = J + tx;
+  if (i < n && j < n) C[(size_t)i * n + j] = make_double2(re, im);
+}
+
 // Sort by lam (ties by index), normalise, fix phases; Vt row r = eigenvector of rank r.
 __global__ void k_sort_vectors(const double* __restrict__ lam, const double2* __restrict__ V, int n,
                                double* __restrict__ eig, double2* __restrict__ Vt) {
@@ -419,6 +472,15 @@ void eigh_mixed(const double2* A, double2* V, double* lam, double* eig, double2*
   k_rayleigh_quotients<<<n, 256, 0, s>>>(A, V, n, lam);
   KS_CHECK_LAUNCH();
   k_sort_vectors<<<1, 128, 0, s>>>(lam, V, n, eig, Vt);
+  KS_CHECK_LAUNCH();
+}
+
+void small_product(const double2* A, const double2* B, int n, int flags, bool mixed, double2* C, cudaStream_t s) {
+  const dim3 grid((n + 7) / 8, (n + 7) / 8);
+  if (mixed)
+    k_small_product<true><<<grid, 64, 0, s>>>(A, B, n, flags, C);
+  else
+    k_small_product<false><<<grid, 64, 0, s>>>(A, B, n, flags, C);
   KS_CHECK_LAUNCH();
 }
 

@@ -160,6 +160,9 @@ template <typename T> class Engine final : public EngineBase {
     mA_ = alloc<double2>(nn);
     mM_ = alloc<double2>(nn);
     mV_ = alloc<double2>(nn);
+    mT_ = alloc<double2>(nn);
+    mC_ = alloc<double2>(nn);
+    mF_ = alloc<double2>(nn);
     eig_ = alloc<double>(ns_);
     lam_ = alloc<double>(ns_);
     if (mixed_cholesky()) chw_ = alloc<double2>(cholesky_mixed_workspace(ns_));
@@ -171,7 +174,22 @@ template <typename T> class Engine final : public EngineBase {
     dots_ = alloc<double2>(ns_);
     norms_dev_ = alloc<double>(MAX_STEPS_CHUNK);
     energies_dev_ = alloc<double>(MAX_STEPS_CHUNK);
+    // side stream (highest priority) for the CholQR factor that overlaps H psi
+    int lo = 0, hi = 0;
+    KS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    KS_CUDA(cudaStreamCreateWithPriority(&aux_, cudaStreamNonBlocking, hi));
+    KS_CUDA(cudaEventCreateWithFlags(&ev_gram_, cudaEventDisableTiming));
+    KS_CUDA(cudaEventCreateWithFlags(&ev_chol_, cudaEventDisableTiming));
     KS_CUDA(cudaStreamSynchronize(nullptr));
+  }
+
+  ~Engine() override {
+    if (aux_) {
+      cudaStreamSynchronize(aux_);
+      cudaStreamDestroy(aux_);
+    }
+    if (ev_gram_) cudaEventDestroy(ev_gram_);
+    if (ev_chol_) cudaEventDestroy(ev_chol_);
   }
 
   const HostGeometry& geo() const override { return g_; }
@@ -293,20 +311,25 @@ template <typename T> class Engine final : public EngineBase {
   // ------------------------------------------------------------------------------------------
   // CholQR: S = Psi^H Psi, S = L L^H, Psi <- Psi L^{-H}  (rows: psi <- conj(L^{-1}) psi)
   // ------------------------------------------------------------------------------------------
-  void cholqr_factor(cudaStream_t s) {
+  // M = conj(L^{-1}) for S = L L^H (mS_ -> mM_), on stream st
+  void factor(cudaStream_t st) {
     const int n = ns_;
+    ProfScope p(prof, "cholesky", st);
+    if (mixed_cholesky()) {
+      cholesky_inverse_mixed(mS_, mM_, n, 1e-6, chw_, status_, st);
+    } else {
+      KS_CUDA(cudaMemcpyAsync(mF_, mS_, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      cholesky_inverse_tol(mF_, mM_, n, sizeof(T) == 8 ? 1e-12 : 1e-6, status_, st);
+    }
+  }
+
+  void cholqr_factor(cudaStream_t s) {
     {
       ProfScope p(prof, "gram", s);
-      overlap(psi_, psi_, n, mS_, s);
-      hermitize(mS_, n, s);
+      overlap(psi_, psi_, ns_, mS_, s);
+      hermitize(mS_, ns_, s);
     }
-    ProfScope p(prof, "cholesky", s);
-    if (mixed_cholesky()) {
-      cholesky_inverse_mixed(mS_, mM_, n, 1e-6, chw_, status_, s);
-    } else {
-      KS_CUDA(cudaMemcpyAsync(mA_, mS_, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-      cholesky_inverse_tol(mA_, mM_, n, sizeof(T) == 8 ? 1e-12 : 1e-6, status_, s);
-    }
+    factor(s);
   }
 
   void cholqr_rotate(cudaStream_t s) {
@@ -316,12 +339,6 @@ template <typename T> class Engine final : public EngineBase {
       rot(mM_, psi_, out, s);
     }
     swap_in(psi_, out);
-  }
-
-  // Inside the block iteration a failed factor leaves M = I (the status is read at the end).
-  void cholqr(cudaStream_t s) {
-    cholqr_factor(s);
-    cholqr_rotate(s);
   }
 
   // The public call reads the status before rotating, so a failure leaves the states as they
@@ -375,10 +392,54 @@ template <typename T> class Engine final : public EngineBase {
     if (niter < 0) fail(KS_ERR_ARG, "niter=%d", niter);
     const double alpha = 1.0 / (g_.ecut + (g_.vmax - g_.vmin) + g_.D);
     KS_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), s));
+    // Per iteration (Sec. Ground-state solution): CholQR, H psi, Rayleigh-Ritz, SD update.
+    // H is linear, so H is applied to the block before the orthonormalising rotation
+    // (H M psi = M H psi) while the factor M runs on the side stream; H_sub is then
+    // conj(M) (psi^H H psi) M^T, and one rotation by Vt M gives the Ritz block and its H image.
+    const int n = ns_;
+    const bool mixed = sizeof(T) == 4;
     for (int it = 0; it < niter; ++it) {
-      cholqr(s);
-      apply_h(psi_, hpsi_, ns_, s);
-      rr_core(s);
+      {
+        ProfScope p(prof, "gram", s);
+        overlap(psi_, psi_, n, mS_, s);
+        hermitize(mS_, n, s);
+      }
+      KS_CUDA(cudaEventRecord(ev_gram_, s));
+      KS_CUDA(cudaStreamWaitEvent(aux_, ev_gram_, 0));
+      factor(aux_);
+      KS_CUDA(cudaEventRecord(ev_chol_, aux_));
+      apply_h(psi_, hpsi_, n, s);
+      {
+        ProfScope p(prof, "gram", s);
+        overlap(psi_, hpsi_, n, mA_, s);
+      }
+      KS_CUDA(cudaStreamWaitEvent(s, ev_chol_, 0));
+      {
+        ProfScope p(prof, "subspace", s);
+        small_product(mA_, mM_, n, SP_TRANS_B, mixed, mT_, s);      // H_raw M^T
+        small_product(mM_, mT_, n, SP_CONJ_A, mixed, mA_, s);       // conj(M) H_raw M^T
+        hermitize(mA_, n, s);
+      }
+      {
+        ProfScope p(prof, "eigh", s);
+        if (mixed && n <= 128)
+          eigh_mixed(mA_, mV_, lam_, eig_, mT_, n, s);
+        else
+          jacobi_eigh(mA_, mV_, eig_, mT_, n, s);
+      }
+      {
+        ProfScope p(prof, "subspace", s);
+        small_product(mT_, mM_, n, 0, mixed, mC_, s);               // Vt M
+      }
+      {
+        ProfScope p(prof, "rotate", s);
+        C* o1 = spare(psi_, hpsi_);
+        rot(mC_, psi_, o1, s);
+        swap_in(psi_, o1);
+        C* o2 = spare(psi_, hpsi_);
+        rot(mC_, hpsi_, o2, s);
+        swap_in(hpsi_, o2);
+      }
       ProfScope p(prof, "sd_update", s);
       sd_update<T>(psi_, hpsi_, eig_, alpha, g_.nG, ns_, s);
     }
@@ -562,6 +623,9 @@ template <typename T> class Engine final : public EngineBase {
   double* eig_ = nullptr;
   double* lam_ = nullptr;
   double2* chw_ = nullptr;   // two-pass FP32 Cholesky workspace (mixed path)
+  double2 *mT_ = nullptr, *mC_ = nullptr, *mF_ = nullptr;   // subspace products, FP64 factor scratch
+  cudaStream_t aux_ = nullptr;
+  cudaEvent_t ev_gram_ = nullptr, ev_chol_ = nullptr;
   void* rotws_ = nullptr;
   size_t rotws_bytes_ = 0;
   int* status_ = nullptr;

@@ -83,6 +83,10 @@ template <typename T> void rotate(const double2* M, int nin, const cplx<T>* X, i
                                   cudaStream_t s);
 // A := (A + A^H)/2
 void hermitize(double2* A, int n, cudaStream_t s);
+// C = opA(A) opB(B), n x n complex128 (row-major); flags: 1 conj(A), 2 B transposed, 4 conj(B).
+// mixed: FP32 products within 32-wide K chunks, FP64 chunk sums; else FP64.
+constexpr int SP_CONJ_A = 1, SP_TRANS_B = 2, SP_CONJ_B = 4;
+void small_product(const double2* A, const double2* B, int n, int flags, bool mixed, double2* C, cudaStream_t s);
 // Cholesky S = L L^H of A (in place, lower) then M = conj(L^{-1}); on failure status = 1 and
 // M = I.  FP64, one CTA.
 void cholesky_inverse(double2* A, double2* M, int n, int* status, cudaStream_t s);
