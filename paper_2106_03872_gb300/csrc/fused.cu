@@ -34,6 +34,15 @@ struct PlaneNL {
   int nproj;
 };
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Per-size launch shapes: plane kernel threads (and CTAs per SM), lines per FFT call
 // (at most 8 complex values per thread per stage), z-kernel columns per CTA.
 template <int N> struct FCfg {
@@ -104,13 +113,32 @@ __global__ void __launch_bounds__(FCfg<N>::ZT) k_zfwd(const float2* __restrict__
 }
 
 // Zero the plane, scatter the columns of one (state, z-plane), inverse y then x transforms.
+// The first column loads are issued before the plane is cleared, so their latency overlaps it.
 template <int N>
 __device__ __forceinline__ void plane_load_inverse(float2* P, const float2* __restrict__ colrow, int ncols,
                                                    const int* __restrict__ col_xy, int xr, const float2* tw) {
-  constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC;
+  constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC, EARLY = 4;
+  float2 cv[EARLY];
+  int cxy[EARLY];
+#pragma unroll
+  for (int e = 0; e < EARLY; ++e) {
+    const int c = threadIdx.x + e * PT;
+    if (c < ncols) {
+      cv[e] = colrow[c];
+      cxy[e] = col_xy[c];
+    }
+  }
   for (int e = threadIdx.x; e < N * ld; e += PT) P[e] = make_float2(0.f, 0.f);
   __syncthreads();
-  for (int c = threadIdx.x; c < ncols; c += PT) {
+#pragma unroll
+  for (int e = 0; e < EARLY; ++e) {
+    const int c = threadIdx.x + e * PT;
+    if (c < ncols) {
+      const int jx = cxy[e] / N, jy = cxy[e] - (cxy[e] / N) * N;
+      P[jx * ld + jy] = cv[e];
+    }
+  }
+  for (int c = threadIdx.x + EARLY * PT; c < ncols; c += PT) {
     const int xy = col_xy[c];
     const int jx = xy / N, jy = xy - jx * N;
     P[jx * ld + jy] = colrow[c];
@@ -125,34 +153,52 @@ __device__ __forceinline__ void plane_load_inverse(float2* P, const float2* __re
   cfft_lines<N, PT, LPC, true, +1>(P, N, 1, ld, tw);
 }
 
+// Dynamic shared memory: twiddles [N], plane [N][N+1], V plane [N*N] (float), then this
+// state's projections [nprojtot] when pf_smem.  V and the projections are fetched with
+// cp.async at entry and land while the inverse transforms run.
 template <int N>
 __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
     k_plane(const float2* __restrict__ colbuf1, float2* __restrict__ colbuf2, int ncols, const int* __restrict__ col_xy,
             int xr, const float* __restrict__ vplane, PlaneNL nl, const float2* __restrict__ pf, int nprojtot,
-            const float2* __restrict__ twg) {
+            int pf_smem, const float2* __restrict__ twg) {
   constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC;
-  extern __shared__ float2 psm[];
+  extern __shared__ __align__(16) float2 psm[];
   float2* tw = psm;
   float2* P = psm + N;
+  float* Vs = reinterpret_cast<float*>(P + N * ld);
+  float2* pfs = reinterpret_cast<float2*>(Vs + N * N);
   const int z = blockIdx.x, b = blockIdx.y;
+  const float* vsrc = vplane + (size_t)z * N * N;
+  for (int c = threadIdx.x; c < N * N / 4; c += PT) cp_async16(Vs + 4 * c, vsrc + 4 * c);
+  if (pf_smem)
+    for (int q = threadIdx.x; q < nprojtot; q += PT) cp_async8(pfs + q, pf + (size_t)b * nprojtot + q);
+  cp_async_commit();
+  int pt0 = 0, pt1 = 0;
+  if (nprojtot > 0) {
+    pt0 = nl.pt_off[z];
+    pt1 = nl.pt_off[z + 1];
+  }
   for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
   const size_t row = ((size_t)b * N + z) * ncols;
   plane_load_inverse<N>(P, colbuf1 + row, ncols, col_xy, xr, tw);
+  cp_async_wait_all();
+  __syncthreads();
   // u = V psi
-  const float* v = vplane + (size_t)z * N * N;
   for (int e = threadIdx.x; e < N * N; e += PT) {
     const int jx = e / N, jy = e - jx * N;
-    const float vv = v[e];
+    const float vv = Vs[e];
     const float2 u = P[jx * ld + jy];
     P[jx * ld + jy] = make_float2(u.x * vv, u.y * vv);
   }
   __syncthreads();
   // + sum_{I,l} D Omega^{1/2} beta_Il p_Il  (pf already carries D Omega^{1/2})
   if (nprojtot > 0) {
-    const float2* pb = pf + (size_t)b * nprojtot;
-    for (int pt = nl.pt_off[z] + threadIdx.x; pt < nl.pt_off[z + 1]; pt += PT) {
+    const float2* pb = pf_smem ? pfs : pf + (size_t)b * nprojtot;
+    for (int pt = pt0 + threadIdx.x; pt < pt1; pt += PT) {
+      const int xy = nl.pt_xy[pt];
+      const int e0 = nl.ent_off[pt], e1 = nl.ent_off[pt + 1];
       float ax = 0.f, ay = 0.f;
-      for (int e = nl.ent_off[pt]; e < nl.ent_off[pt + 1]; ++e) {
+      for (int e = e0; e < e1; ++e) {
         const float2* pp = pb + nl.ent_proj[e];
         const float* bt = nl.ent_beta + (size_t)e * nl.nproj;
         for (int l = 0; l < nl.nproj; ++l) {
@@ -160,7 +206,6 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
           ay += bt[l] * pp[l].y;
         }
       }
-      const int xy = nl.pt_xy[pt];
       const int jx = xy / N, jy = xy - jx * N;
       const float2 u = P[jx * ld + jy];
       P[jx * ld + jy] = make_float2(u.x + ax, u.y + ay);
@@ -178,42 +223,35 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
   }
 }
 
-// Density partial sums: one (z-plane, chunk of states) per CTA, states in order.
+// Density partial sums: one (z-plane, chunk of states) per CTA, states in order.  The
+// accumulator plane lives in shared memory after the transform plane (each thread owns the
+// same elements for every state, so the sums are race-free and in a fixed order).
 template <int N>
 __global__ void __launch_bounds__(FCfg<N>::PT, 1)
     k_plane_density(const float2* __restrict__ colbuf1, int ncols, const int* __restrict__ col_xy, int xr,
                     int nstates, int chunk, const double* __restrict__ occ, float scale, float* __restrict__ partial,
                     const float2* __restrict__ twg) {
-  constexpr int ld = N + 1, PT = FCfg<N>::PT, ACC = FCfg<N>::ACC;
-  extern __shared__ float2 psm[];
+  constexpr int ld = N + 1, PT = FCfg<N>::PT;
+  extern __shared__ __align__(16) float2 psm[];
   float2* tw = psm;
   float2* P = psm + N;
+  float* acc = reinterpret_cast<float*>(P + N * ld);
   const int z = blockIdx.x, ch = blockIdx.y;
   for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
-  float acc[ACC];
-#pragma unroll
-  for (int k = 0; k < ACC; ++k) acc[k] = 0.f;
+  for (int e = threadIdx.x; e < N * N; e += PT) acc[e] = 0.f;
   const int b0 = ch * chunk, b1 = min(nstates, b0 + chunk);
   for (int b = b0; b < b1; ++b) {
     plane_load_inverse<N>(P, colbuf1 + ((size_t)b * N + z) * ncols, ncols, col_xy, xr, tw);
     const float f = (float)occ[b];
-#pragma unroll
-    for (int k = 0; k < ACC; ++k) {
-      const int e = threadIdx.x + k * PT;
-      if (e < N * N) {
-        const int jx = e / N, jy = e - jx * N;
-        const float2 u = P[jx * ld + jy];
-        acc[k] += f * (u.x * u.x + u.y * u.y);
-      }
+    for (int e = threadIdx.x; e < N * N; e += PT) {
+      const int jx = e / N, jy = e - jx * N;
+      const float2 u = P[jx * ld + jy];
+      acc[e] += f * (u.x * u.x + u.y * u.y);
     }
     __syncthreads();
   }
   float* out = partial + ((size_t)ch * N + z) * N * N;
-#pragma unroll
-  for (int k = 0; k < ACC; ++k) {
-    const int e = threadIdx.x + k * PT;
-    if (e < N * N) out[e] = acc[k] * scale;
-  }
+  for (int e = threadIdx.x; e < N * N; e += PT) out[e] = acc[e] * scale;
 }
 
 // n[(jx*N + jy)*N + z] = sum_ch partial[ch][z][jx*N + jy]
@@ -409,27 +447,30 @@ class FusedImpl final : public FusedOps {
     KS_CHECK_LAUNCH();
   }
   template <int N> static size_t plane_smem() { return (size_t)(N + N * (N + 1)) * sizeof(float2); }
+  static constexpr size_t SMEM_MAX = 227 * 1024;
   template <int N> void launch_plane(int n, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-      KS_CUDA(cudaFuncSetAttribute(k_plane<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)std::max<size_t>(plane_smem<N>(), 48 * 1024)));
+      KS_CUDA(cudaFuncSetAttribute(k_plane<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX));
       attr = true;
     }
+    const size_t base = plane_smem<N>() + (size_t)N * N * sizeof(float);
+    const size_t with_pf = base + (size_t)nprojtot_ * sizeof(float2);
+    const int pf_smem = with_pf <= SMEM_MAX;
+    if (base > SMEM_MAX) fail(KS_ERR_ARG, "plane kernel: %zu bytes of shared memory for N=%d", base, N);
     dim3 grid(N, n);
-    k_plane<N><<<grid, FCfg<N>::PT, plane_smem<N>(), s>>>(colbuf1_, colbuf2_, ncols_, t_.col_xy, g_.xr, vplane_, nl_,
-                                                          pf_, nprojtot_, t_.tw);
+    k_plane<N><<<grid, FCfg<N>::PT, pf_smem ? with_pf : base, s>>>(colbuf1_, colbuf2_, ncols_, t_.col_xy, g_.xr,
+                                                                   vplane_, nl_, pf_, nprojtot_, pf_smem, t_.tw);
     KS_CHECK_LAUNCH();
   }
   template <int N> void launch_density(int n, int nch, const double* occ, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-      KS_CUDA(cudaFuncSetAttribute(k_plane_density<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)std::max<size_t>(plane_smem<N>(), 48 * 1024)));
+      KS_CUDA(cudaFuncSetAttribute(k_plane_density<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX));
       attr = true;
     }
     dim3 grid(N, nch);
-    k_plane_density<N><<<grid, FCfg<N>::PT, plane_smem<N>(), s>>>(colbuf1_, ncols_, t_.col_xy, g_.xr, n, dchunk_, occ,
+    k_plane_density<N><<<grid, FCfg<N>::PT, plane_smem<N>() + (size_t)N * N * sizeof(float), s>>>(colbuf1_, ncols_, t_.col_xy, g_.xr, n, dchunk_, occ,
                                                                    (float)(1.0 / g_.omega), dpartial_, t_.tw);
     KS_CHECK_LAUNCH();
   }
