@@ -78,7 +78,8 @@ __global__ void k_reduce_parts(const double2* __restrict__ part, int nks, size_t
 // Y[i][k] = sum_j M[i][j] X[j][k]; tile 32 rows x 64 columns, each thread 2 x 4 outputs.
 template <typename T>
 __global__ void __launch_bounds__(256) k_rotate(const double2* __restrict__ M, int nin, const cplx<T>* __restrict__ X,
-                                                int ldx, cplx<T>* __restrict__ Y, int ldy, int m, int K) {
+                                                const cplx<T>* __restrict__ X2, int nin1, int ldx, cplx<T>* __restrict__ Y,
+                                                int ldy, int m, int K) {
   using C = cplx<T>;
   __shared__ C Ms[32][KT + 1];
   __shared__ C Xs[KT][64 + 1];
@@ -93,7 +94,10 @@ __global__ void __launch_bounds__(256) k_rotate(const double2* __restrict__ M, i
     }
     for (int e = threadIdx.x; e < KT * 64; e += 256) {
       const int jj = e / 64, c = e % 64;
-      Xs[jj][c] = (j0 + jj < nin && k0 + c < K) ? X[(size_t)(j0 + jj) * ldx + k0 + c] : mk<C>(T(0), T(0));
+      const int j = j0 + jj;
+      Xs[jj][c] = (j < nin && k0 + c < K)
+                      ? (j < nin1 ? X[(size_t)j * ldx + k0 + c] : X2[(size_t)(j - nin1) * ldx + k0 + c])
+                      : mk<C>(T(0), T(0));
     }
     __syncthreads();
 #pragma unroll
@@ -396,6 +400,19 @@ __global__ void __launch_bounds__(64) k_small_product(const double2* __restrict_
   if (i < n && j < n) C[(size_t)i * n + j] = make_double2(re, im);
 }
 
+// Mcat = [ (I + alpha Lambda) C | -alpha C ] (n x 2n): one steepest-descent step of the Ritz
+// block, psi_new = Mcat [psi; H psi] with the Ritz rotation C folded in.
+__global__ void k_sd_matrix(const double2* __restrict__ C, const double* __restrict__ eig, double alpha, int n,
+                            double2* __restrict__ Mcat) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    const double2 c = C[e];
+    const double f = 1.0 + alpha * eig[i];
+    Mcat[(size_t)i * 2 * n + j] = make_double2(f * c.x, f * c.y);
+    Mcat[(size_t)i * 2 * n + n + j] = make_double2(-alpha * c.x, -alpha * c.y);
+  }
+}
+
 // Sort by lam (ties by index), normalise, fix phases; Vt row r = eigenvector of rank r.
 __global__ void k_sort_vectors(const double* __restrict__ lam, const double2* __restrict__ V, int n,
                                double* __restrict__ eig, double2* __restrict__ Vt) {
@@ -445,9 +462,11 @@ void gemm_cn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m, int n,
 }
 
 template <typename T>
-void rotate(const double2* M, int nin, const cplx<T>* X, int ldx, cplx<T>* Y, int ldy, int m, int K, cudaStream_t s) {
+void rotate(const double2* M, int nin, const cplx<T>* X, const cplx<T>* X2, int nin1, int ldx, cplx<T>* Y, int ldy,
+            int m, int K, cudaStream_t s) {
+  if (!X2) nin1 = nin;
   dim3 g((K + 63) / 64, (m + 31) / 32);
-  k_rotate<T><<<g, 256, 0, s>>>(M, nin, X, ldx, Y, ldy, m, K);
+  k_rotate<T><<<g, 256, 0, s>>>(M, nin, X, X2, nin1, ldx, Y, ldy, m, K);
   KS_CHECK_LAUNCH();
 }
 
@@ -484,6 +503,11 @@ void small_product(const double2* A, const double2* B, int n, int flags, bool mi
   KS_CHECK_LAUNCH();
 }
 
+void sd_matrix(const double2* C, const double* eig, double alpha, int n, double2* Mcat, cudaStream_t s) {
+  k_sd_matrix<<<std::max(1, std::min(256, (n * n + 255) / 256)), 256, 0, s>>>(C, eig, alpha, n, Mcat);
+  KS_CHECK_LAUNCH();
+}
+
 void jacobi_eigh(double2* A, double2* V, double* eig, double2* Vt, int n, cudaStream_t s) {
   if (n > 512) fail(KS_ERR_ARG, "jacobi: n=%d > 512", n);
   k_jacobi<<<1, 1024, 0, s>>>(A, V, eig, Vt, n);
@@ -494,7 +518,9 @@ template void gemm_cn<float>(const float2*, int, const float2*, int, int, int, i
                              cudaStream_t);
 template void gemm_cn<double>(const double2*, int, const double2*, int, int, int, int, double2*, size_t, double2*,
                               cudaStream_t);
-template void rotate<float>(const double2*, int, const float2*, int, float2*, int, int, int, cudaStream_t);
-template void rotate<double>(const double2*, int, const double2*, int, double2*, int, int, int, cudaStream_t);
+template void rotate<float>(const double2*, int, const float2*, const float2*, int, int, float2*, int, int, int,
+                            cudaStream_t);
+template void rotate<double>(const double2*, int, const double2*, const double2*, int, int, double2*, int, int, int,
+                             cudaStream_t);
 
 }  // namespace ks

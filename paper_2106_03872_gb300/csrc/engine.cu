@@ -152,7 +152,7 @@ template <typename T> class Engine final : public EngineBase {
     part_elems_ = std::max<size_t>(nn * 8, 4096);
     if (use_tc()) {
       part_elems_ = std::max(part_elems_, tc_overlap_part_elems(ns_, ns_));
-      rotws_bytes_ = tc_rotation_workspace_bytes(ns_, ns_);
+      rotws_bytes_ = tc_rotation_workspace_bytes(ns_, 2 * ns_);
       rotws_ = arena_.alloc(rotws_bytes_);
     }
     part_ = alloc<double2>(part_elems_);
@@ -163,6 +163,7 @@ template <typename T> class Engine final : public EngineBase {
     mT_ = alloc<double2>(nn);
     mC_ = alloc<double2>(nn);
     mF_ = alloc<double2>(nn);
+    mCat_ = alloc<double2>(2 * nn);
     eig_ = alloc<double>(ns_);
     lam_ = alloc<double>(ns_);
     if (mixed_cholesky()) chw_ = alloc<double2>(cholesky_mixed_workspace(ns_));
@@ -179,6 +180,7 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     KS_CUDA(cudaStreamCreateWithPriority(&aux_, cudaStreamNonBlocking, hi));
     KS_CUDA(cudaEventCreateWithFlags(&ev_gram_, cudaEventDisableTiming));
+    KS_CUDA(cudaEventCreateWithFlags(&ev_hraw_, cudaEventDisableTiming));
     KS_CUDA(cudaEventCreateWithFlags(&ev_chol_, cudaEventDisableTiming));
     KS_CUDA(cudaStreamSynchronize(nullptr));
   }
@@ -189,6 +191,7 @@ template <typename T> class Engine final : public EngineBase {
       cudaStreamDestroy(aux_);
     }
     if (ev_gram_) cudaEventDestroy(ev_gram_);
+    if (ev_hraw_) cudaEventDestroy(ev_hraw_);
     if (ev_chol_) cudaEventDestroy(ev_chol_);
   }
 
@@ -196,12 +199,16 @@ template <typename T> class Engine final : public EngineBase {
   int nstates() const override { return ns_; }
   ks_precision precision() const override { return prec_; }
   size_t device_bytes() const override { return arena_.bytes(); }
-  void* states_device() override { return psi_; }
+  void* states_device() override {
+    hpsi_valid_ = false;   // the caller may write the block
+    return psi_;
+  }
 
   void set_states(const double* c_host, cudaStream_t s) override {
     const size_t sn = (size_t)ns_ * g_.nG;
     KS_CUDA(cudaMemcpyAsync(staging_, c_host, sn * sizeof(double2), cudaMemcpyHostToDevice, s));
     from_c128<T>(staging_, psi_, sn, s);
+    hpsi_valid_ = false;
     KS_CUDA(cudaStreamSynchronize(s));
   }
 
@@ -214,6 +221,7 @@ template <typename T> class Engine final : public EngineBase {
 
   void randomize_states(uint64_t seed, cudaStream_t s) override {
     random_states<T>(psi_, (size_t)ns_ * g_.nG, seed, s);
+    hpsi_valid_ = false;
   }
 
   // ------------------------------------------------------------------------------------------
@@ -344,6 +352,7 @@ template <typename T> class Engine final : public EngineBase {
   // The public call reads the status before rotating, so a failure leaves the states as they
   // were on every precision path.
   void orthonormalize(double* S_host, cudaStream_t s) override {
+    hpsi_valid_ = false;
     KS_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), s));
     cholqr_factor(s);
     int st = 0;
@@ -382,6 +391,7 @@ template <typename T> class Engine final : public EngineBase {
   }
 
   void rayleigh_ritz(double* eig_host, cudaStream_t s) override {
+    hpsi_valid_ = false;
     apply_h(psi_, hpsi_, ns_, s);
     rr_core(s);
     if (eig_host) KS_CUDA(cudaMemcpyAsync(eig_host, eig_, ns_ * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -392,56 +402,71 @@ template <typename T> class Engine final : public EngineBase {
     if (niter < 0) fail(KS_ERR_ARG, "niter=%d", niter);
     const double alpha = 1.0 / (g_.ecut + (g_.vmax - g_.vmin) + g_.D);
     KS_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), s));
-    // Per iteration (Sec. Ground-state solution): CholQR, H psi, Rayleigh-Ritz, SD update.
-    // H is linear, so H is applied to the block before the orthonormalising rotation
-    // (H M psi = M H psi) while the factor M runs on the side stream; H_sub is then
-    // conj(M) (psi^H H psi) M^T, and one rotation by Vt M gives the Ritz block and its H image.
+    // Per iteration (Sec. Ground-state solution): CholQR, H psi, Rayleigh-Ritz, SD update,
+    // reorganised around the linearity of H:
+    //  - S = psi^H psi and H_raw = psi^H (H psi) are formed on the raw block; the factor M of S,
+    //    H_sub = conj(M) H_raw M^T, its eigenvectors Vt, C = Vt M and the step matrix
+    //    Mcat = [(I + alpha Lambda) C | -alpha C] run on the side stream (one SM), while
+    //  - the main stream applies H to H psi (H^2 psi);
+    //  - then psi <- Mcat [psi; H psi] and H psi <- Mcat [H psi; H^2 psi].
+    // H psi enters the next iteration without a new application of H to psi; it is recomputed
+    // directly on entry to a call whose block changed and every HPSI_REFRESH iterations.
     const int n = ns_;
     const bool mixed = sizeof(T) == 4;
     for (int it = 0; it < niter; ++it) {
+      if (!hpsi_valid_ || hpsi_age_ >= HPSI_REFRESH) {
+        apply_h(psi_, hpsi_, n, s);
+        hpsi_age_ = 0;
+      }
       {
         ProfScope p(prof, "gram", s);
         overlap(psi_, psi_, n, mS_, s);
         hermitize(mS_, n, s);
       }
       KS_CUDA(cudaEventRecord(ev_gram_, s));
-      KS_CUDA(cudaStreamWaitEvent(aux_, ev_gram_, 0));
-      factor(aux_);
-      KS_CUDA(cudaEventRecord(ev_chol_, aux_));
-      apply_h(psi_, hpsi_, n, s);
       {
         ProfScope p(prof, "gram", s);
         overlap(psi_, hpsi_, n, mA_, s);
       }
+      KS_CUDA(cudaEventRecord(ev_hraw_, s));
+      // side stream: factor, subspace matrix, eigenpairs, step matrix
+      KS_CUDA(cudaStreamWaitEvent(aux_, ev_gram_, 0));
+      factor(aux_);
+      KS_CUDA(cudaStreamWaitEvent(aux_, ev_hraw_, 0));
+      {
+        ProfScope p(prof, "subspace", aux_);
+        small_product(mA_, mM_, n, SP_TRANS_B, mixed, mT_, aux_);   // H_raw M^T
+        small_product(mM_, mT_, n, SP_CONJ_A, mixed, mA_, aux_);    // conj(M) H_raw M^T
+        hermitize(mA_, n, aux_);
+      }
+      {
+        ProfScope p(prof, "eigh", aux_);
+        if (mixed && n <= 128)
+          eigh_mixed(mA_, mV_, lam_, eig_, mT_, n, aux_);
+        else
+          jacobi_eigh(mA_, mV_, eig_, mT_, n, aux_);
+      }
+      {
+        ProfScope p(prof, "subspace", aux_);
+        small_product(mT_, mM_, n, 0, mixed, mC_, aux_);            // C = Vt M
+        sd_matrix(mC_, eig_, alpha, n, mCat_, aux_);
+      }
+      KS_CUDA(cudaEventRecord(ev_chol_, aux_));
+      // main stream: H^2 psi meanwhile
+      C* h2 = spare(psi_, hpsi_);
+      apply_h(hpsi_, h2, n, s);
       KS_CUDA(cudaStreamWaitEvent(s, ev_chol_, 0));
       {
-        ProfScope p(prof, "subspace", s);
-        small_product(mA_, mM_, n, SP_TRANS_B, mixed, mT_, s);      // H_raw M^T
-        small_product(mM_, mT_, n, SP_CONJ_A, mixed, mA_, s);       // conj(M) H_raw M^T
-        hermitize(mA_, n, s);
-      }
-      {
-        ProfScope p(prof, "eigh", s);
-        if (mixed && n <= 128)
-          eigh_mixed(mA_, mV_, lam_, eig_, mT_, n, s);
-        else
-          jacobi_eigh(mA_, mV_, eig_, mT_, n, s);
-      }
-      {
-        ProfScope p(prof, "subspace", s);
-        small_product(mT_, mM_, n, 0, mixed, mC_, s);               // Vt M
-      }
-      {
         ProfScope p(prof, "rotate", s);
-        C* o1 = spare(psi_, hpsi_);
-        rot(mC_, psi_, o1, s);
-        swap_in(psi_, o1);
-        C* o2 = spare(psi_, hpsi_);
-        rot(mC_, hpsi_, o2, s);
-        swap_in(hpsi_, o2);
+        C* o1 = spare3(psi_, hpsi_, h2);
+        rot(mCat_, psi_, o1, s, hpsi_);
+        C* o2 = spare4(psi_, hpsi_, h2, o1);
+        rot(mCat_, hpsi_, o2, s, h2);
+        psi_ = o1;
+        hpsi_ = o2;
       }
-      ProfScope p(prof, "sd_update", s);
-      sd_update<T>(psi_, hpsi_, eig_, alpha, g_.nG, ns_, s);
+      hpsi_valid_ = true;
+      ++hpsi_age_;
     }
     int st = 0;
     KS_CUDA(cudaMemcpyAsync(&st, status_, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -456,6 +481,7 @@ template <typename T> class Engine final : public EngineBase {
   // ------------------------------------------------------------------------------------------
   void td_steps(double dt, int nsteps, int propagator, int hartree_xc, double* norm_out, double* energy_out,
                 cudaStream_t s) override {
+    hpsi_valid_ = false;
     if (nsteps < 0 || (propagator != 0 && propagator != 1)) fail(KS_ERR_ARG, "td: nsteps=%d propagator=%d", nsteps, propagator);
     const int n = ns_, nG = g_.nG;
     const size_t sn = (size_t)n * nG;
@@ -562,15 +588,16 @@ template <typename T> class Engine final : public EngineBase {
     gemm_cn<T>(A, g_.nG, B, g_.nG, n, n, g_.nG, part_, part_elems_, out, s);
   }
 
-  // Y = M X (rows of states)
-  void rot(const double2* M, const C* X, C* Y, cudaStream_t s) {
+  // Y = M X (rows of states); with X2, M is n x 2n and X = [X; X2]
+  void rot(const double2* M, const C* X, C* Y, cudaStream_t s, const C* X2 = nullptr) {
+    const int nin = X2 ? 2 * ns_ : ns_;
     if constexpr (std::is_same<T, float>::value) {
       if (use_tc()) {
-        tc_rotate(M, ns_, X, g_.nG, Y, g_.nG, ns_, g_.nG, rotws_, rotws_bytes_, status_ + 1, s);
+        tc_rotate(M, nin, X, X2, ns_, g_.nG, Y, g_.nG, ns_, g_.nG, rotws_, rotws_bytes_, status_ + 1, s);
         return;
       }
     }
-    rotate<T>(M, ns_, X, g_.nG, Y, g_.nG, ns_, g_.nG, s);
+    rotate<T>(M, nin, X, X2, ns_, g_.nG, Y, g_.nG, ns_, g_.nG, s);
   }
 
   void check_tc_status(cudaStream_t s) {
@@ -586,6 +613,11 @@ template <typename T> class Engine final : public EngineBase {
   C* spare3(const C* a, const C* b, const C* c) {
     for (int i = 0; i < 6; ++i)
       if (buf_[i] != a && buf_[i] != b && buf_[i] != c) return buf_[i];
+    fail(KS_ERR_STATE, "internal: no spare state buffer");
+  }
+  C* spare4(const C* a, const C* b, const C* c, const C* d) {
+    for (int i = 0; i < 6; ++i)
+      if (buf_[i] != a && buf_[i] != b && buf_[i] != c && buf_[i] != d) return buf_[i];
     fail(KS_ERR_STATE, "internal: no spare state buffer");
   }
   void swap_in(C*& role, C* fresh) { role = fresh; }
@@ -624,8 +656,14 @@ template <typename T> class Engine final : public EngineBase {
   double* lam_ = nullptr;
   double2* chw_ = nullptr;   // two-pass FP32 Cholesky workspace (mixed path)
   double2 *mT_ = nullptr, *mC_ = nullptr, *mF_ = nullptr;   // subspace products, FP64 factor scratch
+  double2* mCat_ = nullptr;                                   // [n][2n] steepest-descent step matrix
+  // hpsi_ = H psi_ for the resident block (kept by the block iteration between calls); after
+  // HPSI_REFRESH iterations that derived it by recurrence, H is applied to psi_ afresh.
+  static constexpr int HPSI_REFRESH = 16;
+  bool hpsi_valid_ = false;
+  int hpsi_age_ = 0;
   cudaStream_t aux_ = nullptr;
-  cudaEvent_t ev_gram_ = nullptr, ev_chol_ = nullptr;
+  cudaEvent_t ev_gram_ = nullptr, ev_hraw_ = nullptr, ev_chol_ = nullptr;
   void* rotws_ = nullptr;
   size_t rotws_bytes_ = 0;
   int* status_ = nullptr;

@@ -355,10 +355,18 @@ template <int N, int Ns> struct RadixOf {
                                                     : 3;
 };
 
+// Identity epilogue of the last stage.
+struct NoEpi {
+  __device__ __forceinline__ float2 operator()(float2 v, int, int) const { return v; }
+};
+
 // One stage over `lines` lines (<= LPC lines; LPC = lines per call).  LINE_FAST: job =
-// j * LPC + l (consecutive threads on consecutive lines), else job = l * M + j.
-template <int N, int Ns, int R, int THREADS, int LPC, bool LINE_FAST, int SIGN>
-__device__ __forceinline__ void cstage(float2* s, int lines, int lstride, int kstride, const float2* tw) {
+// j * LPC + l (consecutive threads on consecutive lines), else job = l * M + j.  The last
+// stage (Ns * R == N) passes every output through epi(value, element index, line index
+// within the call) before storing it.
+template <int N, int Ns, int R, int THREADS, int LPC, bool LINE_FAST, int SIGN, class Epi>
+__device__ __forceinline__ void cstage(float2* s, int lines, int lstride, int kstride, const float2* tw,
+                                       const Epi& epi) {
   constexpr int M = N / R;
   constexpr int step = N / (Ns * R);
   constexpr int JOBS = LPC * M;
@@ -408,28 +416,42 @@ __device__ __forceinline__ void cstage(float2* s, int lines, int lstride, int ks
       float2* line = s + l * lstride;
       const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) line[(base + r * Ns) * kstride] = v[q][r];
+      for (int r = 0; r < R; ++r) {
+        const int x = base + r * Ns;
+        line[x * kstride] = (Ns * R == N) ? epi(v[q][r], x, l) : v[q][r];
+      }
     }
   }
   __syncthreads();
 }
 
-template <int N, int Ns, int THREADS, int LPC, bool LINE_FAST, int SIGN> struct CFft {
-  static __device__ __forceinline__ void run(float2* s, int lines, int lstride, int kstride, const float2* tw) {
+template <int N, int Ns, int THREADS, int LPC, bool LINE_FAST, int SIGN, class Epi> struct CFft {
+  static __device__ __forceinline__ void run(float2* s, int lines, int lstride, int kstride, const float2* tw,
+                                             const Epi& epi) {
     constexpr int R = RadixOf<N, Ns>::R;
-    cstage<N, Ns, R, THREADS, LPC, LINE_FAST, SIGN>(s, lines, lstride, kstride, tw);
-    CFft<N, Ns * R, THREADS, LPC, LINE_FAST, SIGN>::run(s, lines, lstride, kstride, tw);
+    cstage<N, Ns, R, THREADS, LPC, LINE_FAST, SIGN, Epi>(s, lines, lstride, kstride, tw, epi);
+    CFft<N, Ns * R, THREADS, LPC, LINE_FAST, SIGN, Epi>::run(s, lines, lstride, kstride, tw, epi);
   }
 };
-template <int N, int THREADS, int LPC, bool LINE_FAST, int SIGN> struct CFft<N, N, THREADS, LPC, LINE_FAST, SIGN> {
-  static __device__ __forceinline__ void run(float2*, int, int, int, const float2*) {}
+template <int N, int THREADS, int LPC, bool LINE_FAST, int SIGN, class Epi>
+struct CFft<N, N, THREADS, LPC, LINE_FAST, SIGN, Epi> {
+  static __device__ __forceinline__ void run(float2*, int, int, int, const float2*, const Epi&) {}
 };
 
-// All `lines` lines, LPC at a time.
-template <int N, int THREADS, int LPC, bool LINE_FAST, int SIGN>
-__device__ __forceinline__ void cfft_lines(float2* s, int lines, int lstride, int kstride, const float2* tw) {
+// Shifts the line index of an epilogue by the first line of a call.
+template <class Epi> struct EpiAt {
+  const Epi& e;
+  int l0;
+  __device__ __forceinline__ float2 operator()(float2 v, int x, int l) const { return e(v, x, l0 + l); }
+};
+
+// All `lines` lines, LPC at a time; epi(value, element, line) on the last stage's outputs.
+template <int N, int THREADS, int LPC, bool LINE_FAST, int SIGN, class Epi = NoEpi>
+__device__ __forceinline__ void cfft_lines(float2* s, int lines, int lstride, int kstride, const float2* tw,
+                                           const Epi& epi = Epi()) {
   for (int l0 = 0; l0 < lines; l0 += LPC)
-    CFft<N, 1, THREADS, LPC, LINE_FAST, SIGN>::run(s + l0 * lstride, min(LPC, lines - l0), lstride, kstride, tw);
+    CFft<N, 1, THREADS, LPC, LINE_FAST, SIGN, EpiAt<Epi>>::run(s + l0 * lstride, min(LPC, lines - l0), lstride,
+                                                                kstride, tw, EpiAt<Epi>{epi, l0});
 }
 
 }  // namespace ks

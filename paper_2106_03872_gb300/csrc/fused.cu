@@ -112,11 +112,12 @@ __global__ void __launch_bounds__(FCfg<N>::ZT) k_zfwd(const float2* __restrict__
   }
 }
 
-// Zero the plane, scatter the columns of one (state, z-plane), inverse y then x transforms.
-// The first column loads are issued before the plane is cleared, so their latency overlaps it.
+// Zero the plane, scatter the columns of one (state, z-plane), inverse y transforms of the
+// rows that hold columns.  The first column loads are issued before the plane is cleared, so
+// their latency overlaps it.
 template <int N>
-__device__ __forceinline__ void plane_load_inverse(float2* P, const float2* __restrict__ colrow, int ncols,
-                                                   const int* __restrict__ col_xy, int xr, const float2* tw) {
+__device__ __forceinline__ void plane_load_y(float2* P, const float2* __restrict__ colrow, int ncols,
+                                             const int* __restrict__ col_xy, int xr, const float2* tw) {
   constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC, EARLY = 4;
   float2 cv[EARLY];
   int cxy[EARLY];
@@ -149,9 +150,24 @@ __device__ __forceinline__ void plane_load_inverse(float2* P, const float2* __re
   // 8-byte accesses then fall on distinct bank pairs.
   cfft_lines<N, PT, LPC, true, +1>(P, xr + 1, ld, 1, tw);
   if (xr > 0) cfft_lines<N, PT, LPC, true, +1>(P + (N - xr) * ld, xr, ld, 1, tw);
-  // x-lines: every column jy, element jx at P[jx*ld + jy]
-  cfft_lines<N, PT, LPC, true, +1>(P, N, 1, ld, tw);
 }
+
+// ... then the inverse x transforms: every column jy, element jx at P[jx*ld + jy].
+template <int N>
+__device__ __forceinline__ void plane_load_inverse(float2* P, const float2* __restrict__ colrow, int ncols,
+                                                   const int* __restrict__ col_xy, int xr, const float2* tw) {
+  plane_load_y<N>(P, colrow, ncols, col_xy, xr, tw);
+  cfft_lines<N, FCfg<N>::PT, FCfg<N>::LPC, true, +1>(P, N, 1, N + 1, tw);
+}
+
+// u = V psi as the last stage of the inverse x transform stores it (x = jx, line = jy).
+template <int N> struct VMul {
+  const float* V;
+  __device__ __forceinline__ float2 operator()(float2 v, int x, int l) const {
+    const float vv = V[x * N + l];
+    return make_float2(v.x * vv, v.y * vv);
+  }
+};
 
 // Dynamic shared memory: twiddles [N], plane [N][N+1], V plane [N*N] (float), then this
 // state's projections [nprojtot] when pf_smem.  V and the projections are fetched with
@@ -180,17 +196,11 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
   }
   for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
   const size_t row = ((size_t)b * N + z) * ncols;
-  plane_load_inverse<N>(P, colbuf1 + row, ncols, col_xy, xr, tw);
+  plane_load_y<N>(P, colbuf1 + row, ncols, col_xy, xr, tw);
   cp_async_wait_all();
   __syncthreads();
-  // u = V psi
-  for (int e = threadIdx.x; e < N * N; e += PT) {
-    const int jx = e / N, jy = e - jx * N;
-    const float vv = Vs[e];
-    const float2 u = P[jx * ld + jy];
-    P[jx * ld + jy] = make_float2(u.x * vv, u.y * vv);
-  }
-  __syncthreads();
+  // inverse x transforms; the last stage stores u = V psi
+  cfft_lines<N, PT, LPC, true, +1>(P, N, 1, ld, tw, VMul<N>{Vs});
   // + sum_{I,l} D Omega^{1/2} beta_Il p_Il  (pf already carries D Omega^{1/2})
   if (nprojtot > 0) {
     const float2* pb = pf_smem ? pfs : pf + (size_t)b * nprojtot;

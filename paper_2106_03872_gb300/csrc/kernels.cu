@@ -276,18 +276,6 @@ __global__ void k_axpy2(cplx<T>* __restrict__ acc1, double2 a1, cplx<T>* __restr
   }
 }
 
-template <typename T>
-__global__ void k_sd_update(cplx<T>* __restrict__ psi, const cplx<T>* __restrict__ hpsi, const double* __restrict__ eps,
-                            double alpha, int nG) {
-  const int b = blockIdx.y;
-  const T e = T(eps[b]), a = T(alpha);
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nG; g += gridDim.x * blockDim.x) {
-    const size_t i = (size_t)b * nG + g;
-    const cplx<T> p = psi[i], h = hpsi[i];
-    psi[i] = mk<cplx<T>>(p.x - a * (h.x - e * p.x), p.y - a * (h.y - e * p.y));
-  }
-}
-
 // SplitMix64 (Steele, Lea, Flood 2014), used as a counter-based hash.
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
@@ -453,12 +441,6 @@ void axpy2(cplx<T>* acc1, double2 a1, cplx<T>* acc2, double2 a2, const cplx<T>* 
   KS_CHECK_LAUNCH();
 }
 
-template <typename T>
-void sd_update(cplx<T>* psi, const cplx<T>* hpsi, const double* eps, double alpha, int nG, int nb, cudaStream_t s) {
-  dim3 g(blocks_for(nG, 256, 512), nb);
-  k_sd_update<T><<<g, 256, 0, s>>>(psi, hpsi, eps, alpha, nG);
-  KS_CHECK_LAUNCH();
-}
 
 template <typename T>
 void random_states(cplx<T>* psi, size_t n, uint64_t seed, cudaStream_t s) {
@@ -496,7 +478,6 @@ void real_to_double(const T* in, double* out, size_t n, cudaStream_t s) {
   template void hxc_combine<T>(const T*, const cplx<T>*, const T*, T*, double*, int, int, cudaStream_t);        \
   template void state_dots<T>(const cplx<T>*, const cplx<T>*, int, int, double2*, cudaStream_t);                \
   template void axpy2<T>(cplx<T>*, double2, cplx<T>*, double2, const cplx<T>*, size_t, cudaStream_t);           \
-  template void sd_update<T>(cplx<T>*, const cplx<T>*, const double*, double, int, int, cudaStream_t);          \
   template void random_states<T>(cplx<T>*, size_t, uint64_t, cudaStream_t);                                     \
   template void from_c128<T>(const double2*, cplx<T>*, size_t, cudaStream_t);                                   \
   template void to_c128<T>(const cplx<T>*, double2*, size_t, cudaStream_t);                                     \

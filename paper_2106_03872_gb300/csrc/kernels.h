@@ -63,9 +63,6 @@ void weighted_energy(const double2* dots, const double* occ, int nb, const doubl
 // acc1 += a1 * w; acc2 += a2 * w  (complex constants)
 template <typename T> void axpy2(cplx<T>* acc1, double2 a1, cplx<T>* acc2, double2 a2, const cplx<T>* w, size_t n,
                                  cudaStream_t s);
-// psi[b][g] -= alpha * (hpsi[b][g] - eps[b] psi[b][g])
-template <typename T> void sd_update(cplx<T>* psi, const cplx<T>* hpsi, const double* eps, double alpha, int nG, int nb,
-                                     cudaStream_t s);
 // psi[b][g] = seeded uniform(-0.5, 0.5) + i uniform(-0.5, 0.5)
 template <typename T> void random_states(cplx<T>* psi, size_t n, uint64_t seed, cudaStream_t s);
 // complex128 <-> internal precision
@@ -78,15 +75,18 @@ template <typename T> void real_to_double(const T* in, double* out, size_t n, cu
 // deterministic reduction through `part` (>= gemm_cn_parts(...) double2 elements).
 template <typename T> void gemm_cn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m, int n, int K,
                                    double2* part, size_t part_elems, double2* out, cudaStream_t s);
-// Y[i][k] = sum_j M[i][j] X[j][k], i < m, j < nin, k < K; Y must not overlap X.
-template <typename T> void rotate(const double2* M, int nin, const cplx<T>* X, int ldx, cplx<T>* Y, int ldy, int m, int K,
-                                  cudaStream_t s);
+// Y[i][k] = sum_j M[i][j] X[j][k], i < m, j < nin, k < K; rows j >= nin1 of X come from X2
+// (row j - nin1) when X2 is non-NULL.  Y must not overlap X or X2.
+template <typename T> void rotate(const double2* M, int nin, const cplx<T>* X, const cplx<T>* X2, int nin1, int ldx,
+                                  cplx<T>* Y, int ldy, int m, int K, cudaStream_t s);
 // A := (A + A^H)/2
 void hermitize(double2* A, int n, cudaStream_t s);
 // C = opA(A) opB(B), n x n complex128 (row-major); flags: 1 conj(A), 2 B transposed, 4 conj(B).
 // mixed: FP32 products within 32-wide K chunks, FP64 chunk sums; else FP64.
 constexpr int SP_CONJ_A = 1, SP_TRANS_B = 2, SP_CONJ_B = 4;
 void small_product(const double2* A, const double2* B, int n, int flags, bool mixed, double2* C, cudaStream_t s);
+// Mcat [n][2n] = [ (I + alpha diag(eig)) C | -alpha C ]
+void sd_matrix(const double2* C, const double* eig, double alpha, int n, double2* Mcat, cudaStream_t s);
 // Cholesky S = L L^H of A (in place, lower) then M = conj(L^{-1}); on failure status = 1 and
 // M = I.  FP64, one CTA.
 void cholesky_inverse(double2* A, double2* M, int n, int* status, cudaStream_t s);
@@ -115,8 +115,8 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
                 size_t part_elems, double2* out, int* err, cudaStream_t s);
 // Partial-buffer elements tc_overlap wants for an m x n output (one wave of CTAs).
 size_t tc_overlap_part_elems(int m, int n);
-void tc_rotate(const double2* M, int nin, const float2* X, int ldx, float2* Y, int ldy, int m, int K, void* work,
-               size_t work_bytes, int* err, cudaStream_t s);
+void tc_rotate(const double2* M, int nin, const float2* X, const float2* X2, int nin1, int ldx, float2* Y, int ldy,
+               int m, int K, void* work, size_t work_bytes, int* err, cudaStream_t s);
 size_t tc_rotation_workspace_bytes(int m, int nin);
 
 }  // namespace ks

@@ -5,7 +5,8 @@
 // gets a fourth product, so that its rounding does not bias the norms of rotated states.
 //
 //   tc_overlap:  out[i][j] = sum_k conj(A[i][k]) B[j][k]       (Gram S, H_sub, projections)
-//   tc_rotate:   Y[i][k]   = sum_j M[i][j] X[j][k]             (CholQR and Rayleigh-Ritz rotations)
+//   tc_rotate:   Y[i][k]   = sum_j M[i][j] X[j][k]             (CholQR and Rayleigh-Ritz rotations;
+//                X's rows j >= nin1 may come from a second block X2)
 //
 // Complex arithmetic as real GEMMs.  Overlap: A is read as a real row of interleaved
 // (re, im); B contributes two real rows per complex row, (re, im) and (im, -re), so the
@@ -360,8 +361,8 @@ __device__ __forceinline__ void issue_rotation_stage(uint32_t s, uint32_t tmem_d
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_tc_rotate(const uint4* __restrict__ Mb, int njc, const float2* __restrict__ X, int ldx, float2* __restrict__ Y,
-                int ldy, int m, int nin, int K, int* __restrict__ err) {
+    k_tc_rotate(const uint4* __restrict__ Mb, int njc, const float2* __restrict__ X, const float2* __restrict__ X2,
+                int nin1, int ldx, float2* __restrict__ Y, int ldy, int m, int nin, int K, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   const uint32_t base = smem_u32(tsm);
   uint32_t bar0;
@@ -388,7 +389,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int j = jc0 + 8 * jb + q;
-        const float2 v = (j < nin && kk < K) ? X[(size_t)j * ldx + kk] : make_float2(0.f, 0.f);
+        const float2 v = (j < nin && kk < K) ? (j < nin1 ? X[(size_t)j * ldx + kk] : X2[(size_t)(j - nin1) * ldx + kk])
+                                             : make_float2(0.f, 0.f);
         re[q] = v.x;
         im[q] = v.y;
       }
@@ -524,8 +526,9 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
   KS_CHECK_LAUNCH();
 }
 
-void tc_rotate(const double2* M, int nin, const float2* X, int ldx, float2* Y, int ldy, int m, int K, void* work,
-               size_t work_bytes, int* err, cudaStream_t s) {
+void tc_rotate(const double2* M, int nin, const float2* X, const float2* X2, int nin1, int ldx, float2* Y, int ldy,
+               int m, int K, void* work, size_t work_bytes, int* err, cudaStream_t s) {
+  if (!X2) nin1 = nin;
   set_attrs();
   const int nit = (m + TC_N / 2 - 1) / (TC_N / 2), njc = (nin + R_KC - 1) / R_KC;
   if (tc_rotation_workspace_bytes(m, nin) > work_bytes) fail(KS_ERR_ARG, "tc_rotate: workspace too small");
@@ -534,7 +537,8 @@ void tc_rotate(const double2* M, int nin, const float2* X, int ldx, float2* Y, i
       M, m, nin, nit, njc, static_cast<unsigned char*>(work));
   KS_CHECK_LAUNCH();
   dim3 g((K + TC_M - 1) / TC_M, nit);
-  k_tc_rotate<<<g, TC_THREADS, R_SMEM, s>>>(static_cast<const uint4*>(work), njc, X, ldx, Y, ldy, m, nin, K, err);
+  k_tc_rotate<<<g, TC_THREADS, R_SMEM, s>>>(static_cast<const uint4*>(work), njc, X, X2, nin1, ldx, Y, ldy, m, nin, K,
+                                            err);
   KS_CHECK_LAUNCH();
 }
 
