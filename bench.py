@@ -194,6 +194,11 @@ def stage_model(name, geo, pk, fp32_tflops):
     return None
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from one ncu capture
+# of the current kernels on the gs96 cell
+NCU_TRAFFIC_GS96 = {"plane": 287881216 + 236261376, "zinv": 119076864 + 219228416, "zfwd": 401628416 + 97060096}
+
+
 def roofline(entries, geo, pk, steps):
     leaf = {k: v for k, v in entries.items() if k != "apply_h"}
     if not leaf:
@@ -212,7 +217,7 @@ def roofline(entries, geo, pk, steps):
     else:
         achieved = amount / (per_launch_ms * 1e-3) / 1e12
     out.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": None,
+                "traffic": NCU_TRAFFIC_GS96.get(name) if geo.get("N") == 96 else None,
                 "peak_src": "derived: unit counts x max SM clock" if bound == "alu" else pk["src"]})
     return out, name
 
