@@ -506,8 +506,7 @@ template <typename T> class Engine final : public EngineBase {
         }
         state_dots<T>(psi_, psi_, nG, n, dots_, s);
         weighted_energy(dots_, occ_, n, nullptr, norms_dev_ + st, s);
-        KS_CUDA(cudaMemcpyAsync(acc_full, psi_, sn * sizeof(C), cudaMemcpyDeviceToDevice, s));
-        KS_CUDA(cudaMemcpyAsync(acc_half, psi_, sn * sizeof(C), cudaMemcpyDeviceToDevice, s));
+        // the accumulators start from psi in the first power's update (no copies)
         const C* w = psi_;
         double2 af = make_double2(1, 0), ah = make_double2(1, 0);
         for (int kk = 1; kk <= 4; ++kk) {
@@ -519,7 +518,7 @@ template <typename T> class Engine final : public EngineBase {
           }
           af = cmul_scalar(af, make_double2(0, -dt / kk));
           ah = cmul_scalar(ah, make_double2(0, -0.5 * dt / kk));
-          axpy2<T>(acc_full, af, propagator == 0 ? acc_half : nullptr, ah, wn, sn, s);
+          axpy2<T>(acc_full, af, propagator == 0 ? acc_half : nullptr, ah, wn, kk == 1 ? psi_ : nullptr, sn, s);
           w = wn;
         }
         if (propagator == 1) {
@@ -531,14 +530,13 @@ template <typename T> class Engine final : public EngineBase {
           update_potential(dens_, s);
         }
         // second half: out = acc_half + sum_k (-i dt/2)^k/k! H(t+dt)^k acc_half
-        KS_CUDA(cudaMemcpyAsync(acc_full, acc_half, sn * sizeof(C), cudaMemcpyDeviceToDevice, s));
         w = acc_half;
         ah = make_double2(1, 0);
         for (int kk = 1; kk <= 4; ++kk) {
           C* wn = (w == wa) ? wb : wa;
           apply_h(w, wn, n, s);
           ah = cmul_scalar(ah, make_double2(0, -0.5 * dt / kk));
-          axpy2<T>(acc_full, ah, nullptr, ah, wn, sn, s);
+          axpy2<T>(acc_full, ah, nullptr, ah, wn, kk == 1 ? acc_half : nullptr, sn, s);
           w = wn;
         }
         psi_ = acc_full;

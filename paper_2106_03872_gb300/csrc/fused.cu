@@ -51,31 +51,51 @@ template <int N> struct FCfg {
   static constexpr int LPC = (8 * PT / N) < N ? (8 * PT / N) : N;
   static constexpr int ZT = 512;
   static constexpr int CT = (4096 / N) < 32 ? (4096 / N) : 32;
-  static constexpr int ACC = (N * N + PT - 1) / PT;
 };
 
+// Column c of the sphere holds 2h+1 consecutive coefficients (h = col_half[c]) starting at
+// col_off[c], z-indices 0..h then N-h..N-1: coefficient k has z = k for k <= h, else
+// k + N - 2h - 1.  The z-kernels derive a coefficient's (column, z) from these two numbers.
 template <int N>
-__global__ void __launch_bounds__(FCfg<N>::ZT) k_zinv(const float2* __restrict__ psi, int nG, const int* __restrict__ g_col,
-                                                      const int* __restrict__ g_z, const int* __restrict__ col_off,
-                                                      int ncols, float2* __restrict__ colbuf,
-                                                      const float2* __restrict__ twg) {
-  constexpr int CT = FCfg<N>::CT, ld = N + 1;
+__global__ void __launch_bounds__(FCfg<N>::ZT) k_zinv(const float2* __restrict__ psi, int nG, const int* __restrict__ col_off,
+                                                      const int* __restrict__ col_half, int ncols,
+                                                      float2* __restrict__ colbuf, const float2* __restrict__ twg) {
+  constexpr int CT = FCfg<N>::CT, ld = N + 1, ZT = FCfg<N>::ZT;
   __shared__ float2 tw[N];
   __shared__ float2 s[CT * ld];
+  __shared__ int coff[CT], chalf[CT];
   const int b = blockIdx.y;
   const int c0 = blockIdx.x * CT;
   const int nl = min(CT, ncols - c0);
-  for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = twg[t];
-  for (int e = threadIdx.x; e < nl * ld; e += blockDim.x) s[e] = make_float2(0.f, 0.f);
+  for (int t = threadIdx.x; t < N; t += ZT) tw[t] = twg[t];
+  for (int t = threadIdx.x; t < nl; t += ZT) {
+    coff[t] = col_off[c0 + t];
+    chalf[t] = col_half[c0 + t];
+  }
   __syncthreads();
-  const int g0 = col_off[c0];
-  const int g1 = (c0 + nl < ncols) ? col_off[c0 + nl] : nG;
+  // a group of TPC threads per column fills the column's N slots: the coefficient where z is in
+  // the column's range, else zero (all loads of a thread are independent and issued together)
+  constexpr int TPC = ZT / CT, SLOTS = (N + TPC - 1) / TPC;
   const float2* in = psi + (size_t)b * nG;
-  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) s[(g_col[g] - c0) * ld + g_z[g]] = in[g];
+  {
+    const int l = threadIdx.x / TPC, sub = threadIdx.x - (threadIdx.x / TPC) * TPC;
+    if (l < nl) {
+      const int h = chalf[l];
+      const float2* col = in + coff[l];
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q) {
+        const int z = sub + q * TPC;
+        if (z < N) {
+          const int k = z <= h ? z : (z >= N - h ? z - (N - 2 * h - 1) : -1);
+          s[l * ld + z] = k >= 0 ? col[k] : make_float2(0.f, 0.f);
+        }
+      }
+    }
+  }
   __syncthreads();
-  cfft_lines<N, FCfg<N>::ZT, CT, true, +1>(s, nl, ld, 1, tw);
+  cfft_lines<N, ZT, CT, true, +1>(s, nl, ld, 1, tw);
   float2* out = colbuf + (size_t)b * N * ncols + c0;
-  for (int e = threadIdx.x; e < N * nl; e += blockDim.x) {
+  for (int e = threadIdx.x; e < N * nl; e += ZT) {
     const int z = e / nl, l = e - z * nl;
     out[(size_t)z * ncols + l] = s[l * ld + z];
   }
@@ -83,32 +103,42 @@ __global__ void __launch_bounds__(FCfg<N>::ZT) k_zinv(const float2* __restrict__
 
 template <int N>
 __global__ void __launch_bounds__(FCfg<N>::ZT) k_zfwd(const float2* __restrict__ colbuf, const float2* __restrict__ psi,
-                                                      float2* __restrict__ hpsi, int nG, const int* __restrict__ g_col,
-                                                      const int* __restrict__ g_z, const int* __restrict__ col_off,
-                                                      const float* __restrict__ g2half, int ncols, float scale,
-                                                      const float2* __restrict__ twg) {
-  constexpr int CT = FCfg<N>::CT, ld = N + 1;
+                                                      float2* __restrict__ hpsi, int nG, const int* __restrict__ col_off,
+                                                      const int* __restrict__ col_half, const float* __restrict__ g2half,
+                                                      int ncols, float scale, const float2* __restrict__ twg) {
+  constexpr int CT = FCfg<N>::CT, ld = N + 1, ZT = FCfg<N>::ZT;
   __shared__ float2 tw[N];
   __shared__ float2 s[CT * ld];
+  __shared__ int coff[CT], chalf[CT];
   const int b = blockIdx.y;
   const int c0 = blockIdx.x * CT;
   const int nl = min(CT, ncols - c0);
-  for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = twg[t];
+  for (int t = threadIdx.x; t < N; t += ZT) tw[t] = twg[t];
+  for (int t = threadIdx.x; t < nl; t += ZT) {
+    coff[t] = col_off[c0 + t];
+    chalf[t] = col_half[c0 + t];
+  }
   const float2* in = colbuf + (size_t)b * N * ncols + c0;
-  for (int e = threadIdx.x; e < N * nl; e += blockDim.x) {
+  for (int e = threadIdx.x; e < N * nl; e += ZT) {
     const int z = e / nl, l = e - z * nl;
     s[l * ld + z] = in[(size_t)z * ncols + l];
   }
   __syncthreads();
-  cfft_lines<N, FCfg<N>::ZT, CT, true, -1>(s, nl, ld, 1, tw);
-  const int g0 = col_off[c0];
-  const int g1 = (c0 + nl < ncols) ? col_off[c0 + nl] : nG;
+  cfft_lines<N, ZT, CT, true, -1>(s, nl, ld, 1, tw);
+  // a group of TPC threads per column gathers the column's coefficients
+  constexpr int TPC = ZT / CT;
   const size_t off = (size_t)b * nG;
-  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-    const float2 u = s[(g_col[g] - c0) * ld + g_z[g]];
-    const float2 p = psi[off + g];
-    const float k = g2half[g];
-    hpsi[off + g] = make_float2(u.x * scale + k * p.x, u.y * scale + k * p.y);
+  const int l = threadIdx.x / TPC, sub = threadIdx.x - (threadIdx.x / TPC) * TPC;
+  if (l < nl) {
+    const int h = chalf[l], g0 = coff[l];
+    for (int k = sub; k <= 2 * h; k += TPC) {
+      const int z = k <= h ? k : k + N - 2 * h - 1;
+      const float2 u = s[l * ld + z];
+      const int g = g0 + k;
+      const float2 p = psi[off + g];
+      const float kf = g2half[g];
+      hpsi[off + g] = make_float2(u.x * scale + kf * p.x, u.y * scale + kf * p.y);
+    }
   }
 }
 
@@ -338,17 +368,6 @@ class FusedImpl final : public FusedOps {
     ncols_ = g.ncols;
     nprojtot_ = g.natoms * g.nproj;
     const size_t N3 = (size_t)N_ * N_ * N_;
-    // per-G column id and z
-    std::vector<int> gcol(g.nG), gz(g.nG);
-    for (int c = 0; c < g.ncols; ++c) {
-      const int cnt = 2 * g.col_half[c] + 1;
-      for (int k = 0; k < cnt; ++k) {
-        gcol[g.col_off[c] + k] = c;
-        gz[g.col_off[c] + k] = g.gidx[g.col_off[c] + k] % N_;
-      }
-    }
-    g_col_ = upload(gcol);
-    g_z_ = upload(gz);
     // per-plane projector lists
     std::vector<int> pt_off(N_ + 1, 0), pt_xy, ent_off(1, 0), ent_proj;
     std::vector<float> ent_beta;
@@ -447,12 +466,12 @@ class FusedImpl final : public FusedOps {
 
   template <int N> void launch_zinv(const float2* psi, int n, cudaStream_t s) {
     dim3 grid((ncols_ + FCfg<N>::CT - 1) / FCfg<N>::CT, n);
-    k_zinv<N><<<grid, FCfg<N>::ZT, 0, s>>>(psi, g_.nG, g_col_, g_z_, t_.col_off, ncols_, colbuf1_, t_.tw);
+    k_zinv<N><<<grid, FCfg<N>::ZT, 0, s>>>(psi, g_.nG, t_.col_off, t_.col_half, ncols_, colbuf1_, t_.tw);
     KS_CHECK_LAUNCH();
   }
   template <int N> void launch_zfwd(const float2* psi, float2* hpsi, int n, cudaStream_t s) {
     dim3 grid((ncols_ + FCfg<N>::CT - 1) / FCfg<N>::CT, n);
-    k_zfwd<N><<<grid, FCfg<N>::ZT, 0, s>>>(colbuf2_, psi, hpsi, g_.nG, g_col_, g_z_, t_.col_off, t_.g2half, ncols_,
+    k_zfwd<N><<<grid, FCfg<N>::ZT, 0, s>>>(colbuf2_, psi, hpsi, g_.nG, t_.col_off, t_.col_half, t_.g2half, ncols_,
                                            (float)(1.0 / ((double)N * N * N)), t_.tw);
     KS_CHECK_LAUNCH();
   }
@@ -537,8 +556,6 @@ class FusedImpl final : public FusedOps {
   StageProfiler& prof_;
   int* err_;
   int N_ = 0, ncols_ = 0, nprojtot_ = 0;
-  const int* g_col_ = nullptr;
-  const int* g_z_ = nullptr;
   PlaneNL nl_{};
   float2* colbuf1_ = nullptr;
   float2* colbuf2_ = nullptr;

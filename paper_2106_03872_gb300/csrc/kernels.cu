@@ -259,16 +259,17 @@ __global__ void k_weighted_energy(const double2* __restrict__ dots, const double
 
 template <typename T>
 __global__ void k_axpy2(cplx<T>* __restrict__ acc1, double2 a1, cplx<T>* __restrict__ acc2, double2 a2,
-                        const cplx<T>* __restrict__ w, size_t n) {
+                        const cplx<T>* __restrict__ w, const cplx<T>* __restrict__ base, size_t n) {
   const T a1x = T(a1.x), a1y = T(a1.y), a2x = T(a2.x), a2y = T(a2.y);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const cplx<T> v = w[i];
-    cplx<T> p = acc1[i];
+    const cplx<T> b = base ? base[i] : acc1[i];
+    cplx<T> p = b;
     p.x += a1x * v.x - a1y * v.y;
     p.y += a1x * v.y + a1y * v.x;
     acc1[i] = p;
     if (acc2) {
-      cplx<T> q = acc2[i];
+      cplx<T> q = base ? b : acc2[i];
       q.x += a2x * v.x - a2y * v.y;
       q.y += a2x * v.y + a2y * v.x;
       acc2[i] = q;
@@ -436,8 +437,9 @@ void weighted_energy(const double2* dots, const double* occ, int nb, const doubl
 }
 
 template <typename T>
-void axpy2(cplx<T>* acc1, double2 a1, cplx<T>* acc2, double2 a2, const cplx<T>* w, size_t n, cudaStream_t s) {
-  k_axpy2<T><<<blocks_for(n, 256, 152 * 32), 256, 0, s>>>(acc1, a1, acc2, a2, w, n);
+void axpy2(cplx<T>* acc1, double2 a1, cplx<T>* acc2, double2 a2, const cplx<T>* w, const cplx<T>* base, size_t n,
+           cudaStream_t s) {
+  k_axpy2<T><<<blocks_for(n, 256, 152 * 32), 256, 0, s>>>(acc1, a1, acc2, a2, w, base, n);
   KS_CHECK_LAUNCH();
 }
 
@@ -477,7 +479,7 @@ void real_to_double(const T* in, double* out, size_t n, cudaStream_t s) {
   template void poisson_multiply<T>(cplx<T>*, int, double, T, cudaStream_t);                                    \
   template void hxc_combine<T>(const T*, const cplx<T>*, const T*, T*, double*, int, int, cudaStream_t);        \
   template void state_dots<T>(const cplx<T>*, const cplx<T>*, int, int, double2*, cudaStream_t);                \
-  template void axpy2<T>(cplx<T>*, double2, cplx<T>*, double2, const cplx<T>*, size_t, cudaStream_t);           \
+  template void axpy2<T>(cplx<T>*, double2, cplx<T>*, double2, const cplx<T>*, const cplx<T>*, size_t, cudaStream_t);           \
   template void random_states<T>(cplx<T>*, size_t, uint64_t, cudaStream_t);                                     \
   template void from_c128<T>(const double2*, cplx<T>*, size_t, cudaStream_t);                                   \
   template void to_c128<T>(const cplx<T>*, double2*, size_t, cudaStream_t);                                     \

@@ -60,9 +60,10 @@ template <typename T> void state_dots(const cplx<T>* a, const cplx<T>* b, int nG
 // out[0] = sum_b occ[b] Re(dots[b]) - parts[0] + parts[1] - parts[2]   (parts may be NULL)
 void weighted_energy(const double2* dots, const double* occ, int nb, const double* parts, double* out, cudaStream_t s);
 
-// acc1 += a1 * w; acc2 += a2 * w  (complex constants)
-template <typename T> void axpy2(cplx<T>* acc1, double2 a1, cplx<T>* acc2, double2 a2, const cplx<T>* w, size_t n,
-                                 cudaStream_t s);
+// acc1 += a1 * w; acc2 += a2 * w  (complex constants; acc2 may be NULL).  With base non-NULL
+// the accumulators start from it instead: acc1 = base + a1 w, acc2 = base + a2 w.
+template <typename T> void axpy2(cplx<T>* acc1, double2 a1, cplx<T>* acc2, double2 a2, const cplx<T>* w,
+                                 const cplx<T>* base, size_t n, cudaStream_t s);
 // psi[b][g] = seeded uniform(-0.5, 0.5) + i uniform(-0.5, 0.5)
 template <typename T> void random_states(cplx<T>* psi, size_t n, uint64_t seed, cudaStream_t s);
 // complex128 <-> internal precision
