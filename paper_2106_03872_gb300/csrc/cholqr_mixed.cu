@@ -2,18 +2,16 @@
 // the Cholesky factor of its overlap S = Psi^H Psi, Psi <- Psi L^{-H}).
 //
 // The FP64 factorisation of an n <= 160 matrix in one CTA is bound by GB300's FP64 rate, so
-// the factor is refined in two FP32 passes instead (the two-pass idea of CholeskyQR2,
-// applied to the small factor only):
+// the factor comes from one FP32 pass refined in FP64:
 //
 //   1. L1 L1^H = S       FP32 Cholesky in shared memory, M1 = L1^{-1}        (one CTA)
-//   2. S2 = M1 S M1^H    FP64 triangular products, S2 = I + O(eps_32 kappa)   (many CTAs)
-//   3. L2 L2^H = S2      FP32 Cholesky, M2 = L2^{-1}                          (one CTA)
-//   4. M = conj(M2 M1)   lower triangular, FP32 (M2 = I + O(eps_32 kappa))  (many CTAs)
+//   2. S2 = M1 S M1^H    FP64 triangular products, S2 = I + E with |E| ~ eps_32 kappa(S)
+//   3. M = conj((I - Phi(E)) M1), Phi(E) = strictly lower part of E plus half its diagonal
 //
-// L1 L2 is lower triangular with a positive diagonal and (L1 L2)(L1 L2)^H = S, so M2 M1 is
-// the inverse of S's Cholesky factor; pass 3 factors a matrix within eps_32 kappa(S) of the
-// identity, so M carries ~eps_32 relative error, which the 24-bit rotation cannot resolve
-// anyway.  A pivot <= tol * S_jj in either pass sets status = j + 1 and M = I.
+// (I + Phi(E)) is the Cholesky factor of I + E to first order, so (I - Phi(E)) M1 is the
+// inverse Cholesky factor of S up to O(E^2) ~ (eps_32 kappa(S))^2 -- below the 24-bit
+// precision of the states for kappa(S) up to ~1e4.  A pivot <= tol * S_jj sets status = j + 1
+// and M = I.
 #include <type_traits>
 
 #include "kernels.h"
@@ -256,9 +254,10 @@ __global__ void __launch_bounds__(C32_THREADS, 1)
 // shared memory in chunks of 32 with coalesced loads:
 //   MODE 0: C = S M^H             C_ij = sum_{k <= j} S_ik conj(M_jk)          (all tiles, FP64)
 //   MODE 1: C = M T (lower part)  C_ij = sum_{k <= i} M_ik T_kj, i >= j          (FP64)
-//   MODE 2: C = conj(A B)         C_ij = conj(sum_{j <= k <= i} A_ik B_kj), i >= j; 0 above;
-//           C = I once *status is set.  A = L2^{-1} is within eps_32 kappa of I, so FP32
-//           arithmetic keeps the 24-bit accuracy the rotation uses.
+//   MODE 2: C = conj(B - Phi(A - I) B) with A = S2 (lower) and B = M1:
+//           C_ij = conj(B_ij - sum_{j <= k <= i} Phi_ik B_kj), Phi_ik = A_ik for k < i and
+//           (A_ii - 1)/2 for k = i; i >= j, 0 above; C = I once *status is set.  Phi is
+//           O(eps_32 kappa), so FP32 products keep the 24-bit accuracy of the rotation.
 template <int MODE>
 __global__ void __launch_bounds__(64) k_tri_product(const double2* __restrict__ A, const double2* __restrict__ B,
                                                     int n, const int* __restrict__ status, double2* __restrict__ C) {
@@ -309,7 +308,12 @@ __global__ void __launch_bounds__(64) k_tri_product(const double2* __restrict__ 
         }
       } else {
         if (k >= j && k <= i) {
-          const R ax = (R)a.x, ay = (R)a.y, bx = (R)b.x, by = (R)b.y;
+          R ax = (R)a.x, ay = (R)a.y;
+          if (k == i) {                                              // Phi_ii = (A_ii - 1) / 2
+            ax = (R)(0.5 * (a.x - 1.0));
+            ay = 0;
+          }
+          const R bx = (R)b.x, by = (R)b.y;
           re += ax * bx - ay * by;
           im += ax * by + ay * bx;
         }
@@ -318,9 +322,16 @@ __global__ void __launch_bounds__(64) k_tri_product(const double2* __restrict__ 
     __syncthreads();
   }
   if (i >= n || j >= n) return;
-  if (MODE == 0) C[(size_t)i * n + j] = make_double2((double)re, (double)im);
-  else if (j <= i) C[(size_t)i * n + j] = make_double2((double)re, MODE == 2 ? -(double)im : (double)im);
-  else if (MODE == 2) C[(size_t)i * n + j] = make_double2(0.0, 0.0);
+  if (MODE == 0) {
+    C[(size_t)i * n + j] = make_double2((double)re, (double)im);
+  } else if (MODE == 1) {
+    if (j <= i) C[(size_t)i * n + j] = make_double2((double)re, (double)im);
+  } else if (j <= i) {
+    const double2 bij = B[(size_t)i * n + j];
+    C[(size_t)i * n + j] = make_double2(bij.x - (double)re, -(bij.y - (double)im));
+  } else {
+    C[(size_t)i * n + j] = make_double2(0.0, 0.0);
+  }
 }
 
 }  // namespace
@@ -339,18 +350,16 @@ void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, dou
   }
   double2* M1 = work;
   double2* T = work + (size_t)n * n;
-  double2* M2 = work + (size_t)2 * n * n;
+  double2* S2 = work + (size_t)2 * n * n;
   const int nt = (n + 7) / 8;
   const dim3 grid(nt, nt);
   k_chol32_inverse<<<1, C32_THREADS, smem, s>>>(S, n, tol, 0, status, M1);
   KS_CHECK_LAUNCH();
   k_tri_product<0><<<grid, 64, 0, s>>>(S, M1, n, status, T);
   KS_CHECK_LAUNCH();
-  k_tri_product<1><<<grid, 64, 0, s>>>(M1, T, n, status, M2);      // S2 (lower) into M2's storage
+  k_tri_product<1><<<grid, 64, 0, s>>>(M1, T, n, status, S2);      // S2 = M1 S M1^H (lower)
   KS_CHECK_LAUNCH();
-  k_chol32_inverse<<<1, C32_THREADS, smem, s>>>(M2, n, tol, 0, status, T);
-  KS_CHECK_LAUNCH();
-  k_tri_product<2><<<grid, 64, 0, s>>>(T, M1, n, status, M);
+  k_tri_product<2><<<grid, 64, 0, s>>>(S2, M1, n, status, M);
   KS_CHECK_LAUNCH();
 }
 
