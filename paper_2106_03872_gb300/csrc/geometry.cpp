@@ -84,7 +84,8 @@ void build_geometry(const ks_cell_desc& d, HostGeometry& g) {
   g.h = L / N;
   g.omega = L * L * L;
   g.dV = g.omega / (double(N) * N * N);
-  if (2.0 * d.proj_rc >= L) fail(KS_ERR_ARG, "projector sphere diameter %g exceeds the cell %g", 2 * d.proj_rc, L);
+  if (d.natoms > 0 && 2.0 * d.proj_rc >= L)
+    fail(KS_ERR_ARG, "projector sphere diameter %g exceeds the cell %g", 2 * d.proj_rc, L);
 
   // ---- sphere in canonical order, with its z-columns --------------------------------------
   const double kf = 2.0 * M_PI / L;

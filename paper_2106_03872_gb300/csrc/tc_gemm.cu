@@ -193,6 +193,9 @@ constexpr int O_SMEM = O_RING + 1024;
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t src_bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int NPEND> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
@@ -374,25 +377,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int r = t & (TC_M - 1);          // grid coefficient row of the A tile
   const int jb = t >> 7;                 // which 8 of the 16 states of a chunk
   const int kk = k0 + r;
+  // pipeline: the three M images of chunk c+1 are copied with cp.async into their stage and
+  // the X rows of chunk c+1 are loaded into registers while the MMAs of chunk c run
+  float2 xr[8];
+  auto load_x = [&](int c) {
+    const int jc0 = c * R_KC;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = jc0 + 8 * jb + q;
+      xr[q] = (j < nin && kk < K) ? (j < nin1 ? X[(size_t)j * ldx + kk] : X2[(size_t)(j - nin1) * ldx + kk])
+                                  : make_float2(0.f, 0.f);
+    }
+  };
+  auto issue_b = [&](int c) {
+    const uint32_t sb = base + (c % R_NSTAGE) * R_STAGE_BYTES + 2 * RA_BYTES;
+    const uint4* src = Mb + ((size_t)it_i * njc + c) * (3 * RB_BYTES / 16);
+    for (int v = t; v < 3 * RB_BYTES / 16; v += TC_THREADS) cp_async16(sb + 16 * v, src + v);
+  };
+  if (njc > 0) {
+    issue_b(0);
+    load_x(0);
+  }
+  cp_async_commit();
   bool ok = true;
   for (int it = 0; it < njc; ++it) {
     const int st = it % R_NSTAGE;
-    if (it >= R_NSTAGE) {
-      ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * st, ((it - R_NSTAGE) / R_NSTAGE) & 1)) != 0;
+    // chunk it+1's stage was last read by the MMAs of chunk it-2
+    if (it + 1 < njc && it >= 2) {
+      ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ((it + 1) % R_NSTAGE), ((it - 2) / R_NSTAGE) & 1)) != 0;
       if (!ok) break;
     }
+    if (it + 1 < njc) issue_b(it + 1);
+    cp_async_commit();
     const uint32_t sb = base + st * R_STAGE_BYTES;
-    const int jc0 = it * R_KC;
     // A: row r = grid coefficient kk; real K: [0,16) re of states jc0.., [16,32) im
     {
       float re[8], im[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const int j = jc0 + 8 * jb + q;
-        const float2 v = (j < nin && kk < K) ? (j < nin1 ? X[(size_t)j * ldx + kk] : X2[(size_t)(j - nin1) * ldx + kk])
-                                             : make_float2(0.f, 0.f);
-        re[q] = v.x;
-        im[q] = v.y;
+        re[q] = xr[q].x;
+        im[q] = xr[q].y;
       }
       uint4 hi, lo;
       split8(re, hi, lo);
@@ -404,17 +428,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       sts128(sb + o, hi);
       sts128(sb + RA_BYTES + o, lo);
     }
-    // B: copy the three pre-split images
-    const uint4* src = Mb + ((size_t)it_i * njc + it) * (3 * RB_BYTES / 16);
-    for (int v = t; v < 3 * RB_BYTES / 16; v += TC_THREADS) sts128(sb + 2 * RA_BYTES + 16 * v, src[v]);
+    if (it + 1 < njc) load_x(it + 1);
+    cp_async_wait<1>();              // chunk it's images have landed (this thread's copies)
     fence_proxy_async();
-    __syncthreads();
+    __syncthreads();                 // ... and every thread's, with the A tile stored
     if (t == 0) {
       tc_fence_after();
       issue_rotation_stage(sb, tmem, it == 0);
       mma_commit(bar0 + 8 * st);
     }
   }
+  cp_async_wait<0>();
+  __syncthreads();
   if (ok && njc > 0)
     ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ((njc - 1) % R_NSTAGE), ((njc - 1) / R_NSTAGE) & 1)) != 0;
   if (!ok && t == 0) atomicExch(err, 1);

@@ -342,3 +342,91 @@ def test_rayleigh_ritz_degenerate_shells(ks, prec, m2max, nshell):
     hq = ko.apply_h(ref, q)
     assert np.max(np.abs(hq - eps[:, None] * q)) <= (1e-10 if prec == "fp64" else 1e-4)
     g.close()
+
+
+@pytest.mark.parametrize("N,L,natoms", [(54, 12.0, 2), (8, 3.0, 0)])
+def test_apply_h_plain_path_grids(ks, N, L, natoms):
+    """Grid sizes outside the fused kernels' list (54 = 2 * 27, the smallest grid 8) take the
+    plain FP32 path: same operator, same tolerance.  (An 8^3 grid holding the 20 Ha sphere
+    needs L < 4 bohr, smaller than a projector sphere's diameter, so that cell has no atoms.)"""
+    cell = inputs.small_cell(L, N, natoms, 3, 41)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec="bf16x3")
+    c = inputs.random_coeffs(41, 3, ref.nG)
+    assert rel(apply_dev(ks, g, c, "bf16x3"), ko.apply_h(ref, c)) <= 2e-5
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_apply_h_partial_block_and_empty(ks, prec):
+    """ks_apply_h on the first n of the handle's states (n = 0 is a no-op)."""
+    cell = inputs.small_cell(10.0, 24, 3, 9, 42)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec=prec)
+    c = inputs.random_coeffs(42, 4, ref.nG)
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    assert rel(apply_dev(ks, g, c, prec), ko.apply_h(ref, c)) <= tol
+    psi = torch.zeros((1, ref.nG), dtype=CDT[prec], device="cuda")
+    out = torch.full_like(psi, 7.0)
+    g.apply_h(psi.data_ptr(), out.data_ptr(), 0)
+    torch.cuda.synchronize()
+    assert torch.all(out == 7.0)                     # untouched
+    g.close()
+
+
+def test_zero_work_calls(ks):
+    cell = inputs.small_cell(10.0, 24, 2, 4, 43)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec="bf16x3")
+    c = inputs.random_coeffs(43, 4, ref.nG)
+    g.set_states(c)
+    before = g.get_states()
+    assert g.block_iteration(0).shape == (4,)
+    n, e = g.td_step(0.05, 0)
+    assert n.shape == (0,) and e.shape == (0,)
+    assert np.array_equal(g.get_states(), before)
+    g.close()
+
+
+def test_block_iteration_split_calls_bit_identical(ks):
+    """The H psi a block iteration carries to the next call is exactly what one longer call
+    uses, and new states discard it: split and fresh runs are bit-identical."""
+    cell = inputs.small_cell(12.0, 32, 4, 10, 44, depth=-3.0)
+    ref = ko.Cell(cell)
+    c = inputs.random_coeffs(44, 10, ref.nG)
+    c2 = inputs.random_coeffs(45, 10, ref.nG)
+    a = ks.Grid(cell, prec="bf16x3")
+    b = ks.Grid(cell, prec="bf16x3")
+    a.set_states(c)
+    b.set_states(c)
+    a.block_iteration(3)
+    ea = a.block_iteration(4)
+    eb = b.block_iteration(7)
+    assert np.array_equal(ea, eb)
+    assert np.array_equal(a.get_states(), b.get_states())
+    a.set_states(c2)
+    b.close()
+    b = ks.Grid(cell, prec="bf16x3")
+    b.set_states(c2)
+    assert np.array_equal(a.block_iteration(2), b.block_iteration(2))
+    assert np.array_equal(a.get_states(), b.get_states())
+    a.close()
+    b.close()
+
+
+def test_block_iteration_mixed_beyond_128_states(ks):
+    """150 states on the mixed path: the factor keeps the two-pass FP32 scheme (n <= 160) and
+    the eigensolver falls back to FP64 Jacobi (n > 128)."""
+    cell = inputs.small_cell(16.0, 48, 3, 150, 46, depth=-3.0)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec="bf16x3")
+    c = inputs.random_coeffs(46, 150, ref.nG)
+    g.set_states(c)
+    eps = g.block_iteration(2)
+    eps_ref, c_ref = ko.block_iteration(ref, c, 2)
+    assert np.max(np.abs(eps - eps_ref)) <= 1e-4 * max(1.0, np.max(np.abs(eps_ref)))
+    q = g.get_states()
+    s = ko.gram(q)
+    # not orthonormal (the SD step follows the rotation), but Hermitian positive definite
+    assert np.all(np.linalg.eigvalsh(0.5 * (s + s.conj().T)) > 0)
+    g.close()
