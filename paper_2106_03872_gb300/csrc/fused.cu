@@ -48,7 +48,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int N> struct FCfg {
   static constexpr int PT = N >= 128 ? 1024 : (N >= 64 ? 512 : 256);
   static constexpr int PMIN = N >= 128 ? 1 : (N >= 64 ? 2 : 4);
-  static constexpr int LPC = (8 * PT / N) < N ? (8 * PT / N) : N;
+  // lines per call: at most 8 complex per thread per stage; 96 takes 32 so that three calls
+  // cover the 96 x-lines exactly and no warp straddles two lines' radix jobs
+  static constexpr int LPC = N == 96 ? 32 : ((8 * PT / N) < N ? (8 * PT / N) : N);
   static constexpr int ZT = 512;
   static constexpr int CT = (4096 / N) < 32 ? (4096 / N) : 32;
 };
