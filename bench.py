@@ -168,6 +168,10 @@ def stage_model(name, geo, pk, fp32_tflops):
         # Householder tridiagonalisation (16/3) n^3 + back-transformation 8 n^3 real flops
         # (complex), Newton-Schulz/bisection/twisted factorisation are lower order
         return "alu", (16.0 / 3.0 + 8.0) * ns ** 3, FP32_PEAK_TFLOPS, "TFLOP/s"
+    if name == "rr_step":
+        # eigh above, plus the triangular subspace products conj(M) (H_raw M^T) and C = Vt M
+        # (three products of n^3/2 complex MACs: 12 n^3 flop)
+        return "alu", (16.0 / 3.0 + 8.0 + 12.0) * ns ** 3, FP32_PEAK_TFLOPS, "TFLOP/s"
     if name == "cholesky":
         # two FP32 passes, each a complex Cholesky + triangular inverse (2 x n^3/6 complex
         # MACs = 8 n^3 / 3 flop), plus FP64 triangular products (n^3 complex MACs, 8 n^3 flop)
@@ -201,7 +205,7 @@ NCU_TRAFFIC_GS96 = {"plane": 287898368 + 236069376, "zinv": 118125312 + 22149043
 
 # Stages that run as single-CTA kernels on the side stream, concurrently with the main stream's
 # whole-GPU kernels: rated against one SM's share of the peak, not chosen as the dominant kernel
-SIDE_STREAM = ("cholesky", "subspace", "eigh")
+SIDE_STREAM = ("cholesky", "subspace", "eigh", "rr_step", "rot_prep", "ritz_values")
 
 
 def _rate(name, ms, count, geo, pk, peak_scale=1.0):
@@ -232,7 +236,7 @@ def roofline(entries, geo, pk, steps):
     out = _rate(name, leaf[name][0], leaf[name][1], geo, pk)
     out["traffic"] = NCU_TRAFFIC_GS96.get(name) if geo.get("N") == 96 else None
     side = [dict(_rate(k, entries[k][0], entries[k][1], geo, pk, 1.0 / 152), peak_note="one SM of 152")
-            for k in SIDE_STREAM if k in entries and k != "subspace"]
+            for k in SIDE_STREAM if k in entries and stage_model(k, geo, pk, None) is not None]
     return out, name, side
 
 

@@ -192,13 +192,22 @@ ks_status ks_serve_result_info(ks_server s, uint64_t ticket, int* nresult, int* 
 
 /* mode 1: record a CUDA event pair on the launching stream around every stage of the
  * handle's calls (H application, line FFTs, Gram, rotations, Cholesky, eigensolver, ...);
- * mode 0: stop recording; mode 2: drop the accumulated entries. */
+ * mode 0: stop recording; mode 2: drop the accumulated entries and spans; mode 3: also keep
+ * every recorded stage as a span on a common clock (restarts the clock, drops old spans);
+ * mode 4: stop keeping spans.  Spans need mode 1 as well. */
 ks_status ks_profile(ks_grid g, int mode);
 
 /* Entry idx (0-based) of the accumulated stage timings: name (NUL-terminated, truncated to
  * name_len), total milliseconds and number of timed scopes.  Waits for pending events.
  * KS_ERR_ARG once idx passes the last entry. */
 ks_status ks_profile_read(ks_grid g, int idx, char* name, int name_len, double* ms, long* count);
+
+/* Span idx (0-based, in order of completion collection) of the timeline started by mode 3:
+ * stage name (NUL-terminated, truncated to name_len) and its start and end in milliseconds
+ * after the first stage recorded since mode 3.  Stages on the side stream of the block
+ * iteration appear beside the main stream's, so their overlap can be read off.  Waits for
+ * pending events.  KS_ERR_ARG once idx passes the last span. */
+ks_status ks_profile_span(ks_grid g, int idx, char* name, int name_len, double* start_ms, double* end_ms);
 
 /* Number of kernels this library has launched in this process so far. */
 uint64_t ks_kernel_launches(void);

@@ -169,9 +169,11 @@ ks_status ks_td_step(ks_grid g, double dt, int nsteps, int propagator, int hartr
 
 ks_status ks_profile(ks_grid g, int mode) {
   return guarded([&] {
-    need(g != nullptr && mode >= 0 && mode <= 2, "grid is NULL or mode not in {0,1,2}");
+    need(g != nullptr && mode >= 0 && mode <= 4, "grid is NULL or mode not in 0..4");
     if (mode == 2)
       g->eng->prof.reset();
+    else if (mode >= 3)
+      g->eng->prof.timeline(mode == 3);
     else
       g->eng->prof.enable(mode == 1);
   });
@@ -186,6 +188,18 @@ ks_status ks_profile_read(ks_grid g, int idx, char* name, int name_len, double* 
     std::snprintf(name, name_len, "%s", e[idx].name.c_str());
     *ms = e[idx].ms;
     *count = e[idx].count;
+  });
+}
+
+ks_status ks_profile_span(ks_grid g, int idx, char* name, int name_len, double* start_ms, double* end_ms) {
+  return guarded([&] {
+    need(g && name && name_len > 0 && start_ms && end_ms, "bad profile_span arguments");
+    g->eng->prof.collect();
+    const auto& sp = g->eng->prof.spans();
+    if (idx < 0 || idx >= (int)sp.size()) ks::fail(KS_ERR_ARG, "profile span %d of %d", idx, (int)sp.size());
+    std::snprintf(name, name_len, "%s", g->eng->prof.entries()[sp[idx].entry].name.c_str());
+    *start_ms = sp[idx].start;
+    *end_ms = sp[idx].end;
   });
 }
 

@@ -258,9 +258,11 @@ __global__ void __launch_bounds__(C32_THREADS, 1)
 //           C_ij = conj(B_ij - sum_{j <= k <= i} Phi_ik B_kj), Phi_ik = A_ik for k < i and
 //           (A_ii - 1)/2 for k = i; i >= j, 0 above; C = I once *status is set.  Phi is
 //           O(eps_32 kappa), so FP32 products keep the 24-bit accuracy of the rotation.
+// MODE 2 also writes an FP32 copy of C to C32 when it is given.
 template <int MODE>
 __global__ void __launch_bounds__(64) k_tri_product(const double2* __restrict__ A, const double2* __restrict__ B,
-                                                    int n, const int* __restrict__ status, double2* __restrict__ C) {
+                                                    int n, const int* __restrict__ status, double2* __restrict__ C,
+                                                    float2* __restrict__ C32) {
   constexpr int KC = 32;
   __shared__ double2 As[8][KC + 1];
   __shared__ double2 Bs[8][KC + 1];                                  // Bs[j][k]
@@ -268,11 +270,17 @@ __global__ void __launch_bounds__(64) k_tri_product(const double2* __restrict__ 
   const int I = blockIdx.y * 8, J = blockIdx.x * 8;
   const int i = I + ty, j = J + tx;
   if (MODE == 2 && *status != 0) {
-    if (i < n && j < n) C[(size_t)i * n + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    if (i < n && j < n) {
+      C[(size_t)i * n + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      if (C32) C32[(size_t)i * n + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+    }
     return;
   }
   if (MODE != 0 && J > I) {                                          // strictly upper tile
-    if (MODE == 2 && i < n && j < n) C[(size_t)i * n + j] = make_double2(0.0, 0.0);
+    if (MODE == 2 && i < n && j < n) {
+      C[(size_t)i * n + j] = make_double2(0.0, 0.0);
+      if (C32) C32[(size_t)i * n + j] = make_float2(0.f, 0.f);
+    }
     return;
   }
   // k range of the tile
@@ -326,11 +334,14 @@ __global__ void __launch_bounds__(64) k_tri_product(const double2* __restrict__ 
     C[(size_t)i * n + j] = make_double2((double)re, (double)im);
   } else if (MODE == 1) {
     if (j <= i) C[(size_t)i * n + j] = make_double2((double)re, (double)im);
-  } else if (j <= i) {
-    const double2 bij = B[(size_t)i * n + j];
-    C[(size_t)i * n + j] = make_double2(bij.x - (double)re, -(bij.y - (double)im));
   } else {
-    C[(size_t)i * n + j] = make_double2(0.0, 0.0);
+    double2 c = make_double2(0.0, 0.0);
+    if (j <= i) {
+      const double2 bij = B[(size_t)i * n + j];
+      c = make_double2(bij.x - (double)re, -(bij.y - (double)im));
+    }
+    C[(size_t)i * n + j] = c;
+    if (C32) C32[(size_t)i * n + j] = make_float2((float)c.x, (float)c.y);
   }
 }
 
@@ -339,7 +350,7 @@ __global__ void __launch_bounds__(64) k_tri_product(const double2* __restrict__ 
 size_t cholesky_mixed_workspace(int n) { return (size_t)3 * n * n; }
 
 void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, double2* work, int* status,
-                            cudaStream_t s) {
+                            cudaStream_t s, float2* M32) {
   if (n > C32_MAXN) fail(KS_ERR_ARG, "cholesky_inverse_mixed: n=%d > %d", n, C32_MAXN);
   const size_t smem = (size_t)n * (n + 1) * sizeof(float2);           // square [n][n+1]
   static bool attr_set = false;
@@ -355,11 +366,11 @@ void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, dou
   const dim3 grid(nt, nt);
   k_chol32_inverse<<<1, C32_THREADS, smem, s>>>(S, n, tol, 0, status, M1);
   KS_CHECK_LAUNCH();
-  k_tri_product<0><<<grid, 64, 0, s>>>(S, M1, n, status, T);
+  k_tri_product<0><<<grid, 64, 0, s>>>(S, M1, n, status, T, nullptr);
   KS_CHECK_LAUNCH();
-  k_tri_product<1><<<grid, 64, 0, s>>>(M1, T, n, status, S2);      // S2 = M1 S M1^H (lower)
+  k_tri_product<1><<<grid, 64, 0, s>>>(M1, T, n, status, S2, nullptr);   // S2 = M1 S M1^H (lower)
   KS_CHECK_LAUNCH();
-  k_tri_product<2><<<grid, 64, 0, s>>>(S2, M1, n, status, M);
+  k_tri_product<2><<<grid, 64, 0, s>>>(S2, M1, n, status, M, M32);
   KS_CHECK_LAUNCH();
 }
 

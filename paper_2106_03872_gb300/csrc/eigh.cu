@@ -22,6 +22,18 @@
 //
 // The FP32 vectors are written as complex128 columns; the caller takes the eigenvalues as
 // FP64 Rayleigh quotients of these vectors on the FP64 matrix, then sorts and fixes phases.
+//
+// The block-iteration variant (rr_step_mixed) runs the whole Rayleigh-Ritz step of one
+// iteration in the same CTA, all in FP32 with FP32 inputs and outputs (FP64 conversions run
+// at the FP64 rate, which one SM cannot afford):
+//   0. H_sub = conj(M) H_raw M^T from the raw projection H_raw = Psi^H (H Psi) and the
+//      lower-triangular orthonormaliser M (T = H_raw M^T, then conj(M) T in place, row blocks
+//      from the bottom up, since row block b of the result needs T rows <= b only);
+//   1-4 as above;
+//   5. C = Vt M and the steepest-descent step matrix Mcat = [(I + alpha Lambda) C | -alpha C]
+//      with rows in ascending order of the FP32 eigenvalues.
+// H_sub and the eigenvectors are exported so that ritz_values can form the reported FP64
+// Rayleigh quotients off the iteration's critical path.
 #include "kernels.h"
 
 namespace ks {
@@ -32,12 +44,31 @@ constexpr int EH_MAXN = 128;
 constexpr int EH_THREADS = 1024;
 constexpr int EH_WARPS = EH_THREADS / 32;
 constexpr unsigned FULL = 0xffffffffu;
+// shared memory: the matrix [EH_MAXN][EH_MAXN + 1], then a region for the packed reflectors
+// (n(n-1)/2) that also stages operand rows in the Rayleigh-Ritz phases (64 x EH_MAXN)
+constexpr int EH_AREG = EH_MAXN * (EH_MAXN + 1);
+constexpr int EH_RREG = EH_MAXN * (EH_MAXN - 1) / 2 > 64 * EH_MAXN ? EH_MAXN * (EH_MAXN - 1) / 2 : 64 * EH_MAXN;
+constexpr size_t EH_SMEM = (size_t)(EH_AREG + EH_RREG) * sizeof(float2);
 
 __device__ __forceinline__ float2 cm(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ float2 cmc(float2 a, float2 b) {   // conj(a) * b
   return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cfma(float2 acc, float2 a, float2 b) {   // acc + a b
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ float2 cfmac(float2 acc, float2 a, float2 b) {  // acc + conj(a) b
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+  return acc;
+}
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 warp_sum(float2 v) {
   for (int o = 16; o > 0; o >>= 1) {
@@ -61,22 +92,200 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
   return c;
 }
 
+// Phase 0 of the Rayleigh-Ritz variant: A = conj(M) H_raw M^T (FP32), Hermitian part, in the
+// [n][ld] matrix region; R (EH_RREG float2) stages operand rows.  M is lower triangular.
+__device__ __forceinline__ void subspace_matrix(const float2* __restrict__ Hraw, const float2* __restrict__ M, int n,
+                                                float2* A, float2* R, float2* __restrict__ Aout) {
+  const int ld = n + 1;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const float2 zero = make_float2(0.f, 0.f);
+  // T = H_raw M^T: T_ij = sum_{k <= j} H_ik M_jk, in two halves of 64 rows.  Thread: rows
+  // r0 + warp + 32u (u < 2), columns lane + 32v (v < 4); K staged 32 at a time.
+  constexpr int KC = 32, MLD = EH_MAXN + 1;
+  float2* Hs = R;                                                    // [64][KC]
+  float2* Mt = R + 64 * KC;                                          // [KC][MLD]: Mt[kk][j] = M_j,k0+kk
+  for (int r0 = 0; r0 < n; r0 += 64) {
+    float2 acc[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = zero;
+    for (int k0 = 0; k0 < n; k0 += KC) {
+      const int c = k0 / KC;
+      __syncthreads();
+      for (int e = t; e < 64 * KC; e += EH_THREADS) {
+        const int i = r0 + (e >> 5), k = k0 + (e & 31);
+        Hs[e] = (i < n && k < n) ? Hraw[i * n + k] : zero;
+      }
+      for (int e = t; e < EH_MAXN * KC; e += EH_THREADS) {
+        const int j = e >> 5, kk = e & 31, k = k0 + kk;
+        Mt[kk * MLD + j] = (j < n && k < n) ? M[j * n + k] : zero;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < KC; ++kk) {
+        float2 hv[2], mv[4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) hv[u] = Hs[(warp + 32 * u) * KC + kk];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) mv[v] = Mt[kk * MLD + lane + 32 * v];
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (v >= c)                                                // M_jk = 0 for j < k0
+#pragma unroll
+            for (int u = 0; u < 2; ++u) acc[u][v] = cfma(acc[u][v], hv[u], mv[v]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int i = r0 + warp + 32 * u, j = lane + 32 * v;
+        if (i < n && j < n) A[i * ld + j] = acc[u][v];
+      }
+  }
+  // A = conj(M) T in place: A_ij = sum_{k <= i} conj(M_ik) T_kj.  Row blocks of 64 from the
+  // bottom up: block b reads T rows < its end only, so it may overwrite its own rows.
+  float2* Ms = R;                                                    // [64][EH_MAXN]
+  for (int i0 = ((n - 1) / 64) * 64; i0 >= 0; i0 -= 64) {
+    const int kend = min(n, i0 + 64);
+    __syncthreads();
+    for (int e = t; e < 64 * EH_MAXN; e += EH_THREADS) {
+      const int i = i0 + (e >> 7), k = e & (EH_MAXN - 1);
+      Ms[e] = (i < n && k < kend) ? M[i * n + k] : zero;
+    }
+    __syncthreads();
+    float2 acc[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = zero;
+    const int ia = i0 + warp, ib = i0 + 32 + warp;
+    for (int k = 0; k < kend; ++k) {
+      float2 tv[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int j = lane + 32 * v;
+        tv[v] = j < n ? A[k * ld + j] : zero;
+      }
+      const float2 ma = Ms[warp * EH_MAXN + k], mb = Ms[(32 + warp) * EH_MAXN + k];
+      if (k <= ia)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[0][v] = cfmac(acc[0][v], ma, tv[v]);
+      if (k <= ib)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[1][v] = cfmac(acc[1][v], mb, tv[v]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int i = i0 + warp + 32 * u, j = lane + 32 * v;
+        if (i < n && j < n) A[i * ld + j] = acc[u][v];
+      }
+  }
+  __syncthreads();
+  // Hermitian part (one thread per pair), real diagonal
+  for (int i = warp; i < n; i += EH_WARPS)
+    for (int j = lane; j <= i; j += 32) {
+      const float2 a = A[i * ld + j], b = A[j * ld + i];
+      const float2 h = make_float2(0.5f * (a.x + b.x), i == j ? 0.f : 0.5f * (a.y - b.y));
+      A[i * ld + j] = h;
+      A[j * ld + i] = make_float2(h.x, -h.y);
+    }
+  __syncthreads();
+  for (int i = warp; i < n; i += EH_WARPS)
+    for (int j = lane; j < n; j += 32) Aout[i * n + j] = A[i * ld + j];
+}
+
+// Phase 5 of the Rayleigh-Ritz variant: with V staged in the matrix region (V_kr at k ld + r),
+// C = Vt M (C_rj = sum_{k >= j} V_kr M_kj) and Mcat row rank(r) = [(1 + alpha lam_r) C_r | -alpha C_r].
+__device__ __forceinline__ void step_matrix(const float2* Vs, const float2* __restrict__ M, int n, const float* lam,
+                                            const int* rank, float alpha, float2* R, float2* __restrict__ Mcat) {
+  const int ld = n + 1;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const float2 zero = make_float2(0.f, 0.f);
+  float2* Ms = R;                                                    // [64][EH_MAXN]: M rows k0..
+  for (int pass = 0; pass < 2; ++pass) {
+    float2 acc[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = zero;
+    for (int k0 = 0; k0 < n; k0 += 64) {
+      __syncthreads();
+      for (int e = t; e < 64 * EH_MAXN; e += EH_THREADS) {
+        const int k = k0 + (e >> 7), j = e & (EH_MAXN - 1);
+        Ms[e] = (k < n && j < n) ? M[k * n + j] : zero;
+      }
+      __syncthreads();
+      const int kend = min(64, n - k0);
+      for (int kr = 0; kr < kend; ++kr) {
+        const int k = k0 + kr;
+        float2 vr[2], mv[4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) vr[u] = Vs[k * ld + warp + 32 * (2 * pass + u)];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) mv[v] = Ms[kr * EH_MAXN + lane + 32 * v];
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (32 * v <= k)                                           // M_kj = 0 for j > k
+#pragma unroll
+            for (int u = 0; u < 2; ++u) acc[u][v] = cfma(acc[u][v], vr[u], mv[v]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int r = warp + 32 * (2 * pass + u);
+      if (r < n) {
+        const float f = 1.f + alpha * lam[r];
+        float2* row = Mcat + (size_t)rank[r] * 2 * n;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int j = lane + 32 * v;
+          if (j < n) {
+            row[j] = make_float2(f * acc[u][v].x, f * acc[u][v].y);
+            row[n + j] = make_float2(-alpha * acc[u][v].x, -alpha * acc[u][v].y);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Inputs and outputs of the Rayleigh-Ritz variant (all device pointers, row-major, FP32).
+struct RRStep {
+  const float2* Hraw;   // [n][n] Psi^H (H Psi)
+  const float2* M;      // [n][n] lower-triangular orthonormaliser
+  float alpha;          // steepest-descent step
+  float2* Mcat;         // [n][2n] step matrix
+  float2* Aout;         // [n][n] Hermitian subspace matrix
+  float2* Vout;         // [n][n] eigenvectors, column j for lam_j (unsorted)
+  int* perm;            // [n] rank of lam_j
+};
+
+template <bool RR>
 __global__ void __launch_bounds__(EH_THREADS, 1)
-    k_eigh_householder(const double2* __restrict__ H, int n, double2* __restrict__ Vout) {
+    k_eigh_householder(const double2* __restrict__ H, int n, double2* __restrict__ Vout, RRStep rr) {
   extern __shared__ __align__(16) unsigned char esm[];
   const int ld = n + 1;
   float2* A = reinterpret_cast<float2*>(esm);                       // [n][ld]
-  float2* R = A + (size_t)EH_MAXN * (EH_MAXN + 1);                  // packed reflectors
+  float2* R = A + EH_AREG;                                          // packed reflectors
   __shared__ float d[EH_MAXN], e[EH_MAXN], e2[EH_MAXN], lam[EH_MAXN];
   __shared__ float2 tau[EH_MAXN], wvp[2][EH_MAXN], red[2][EH_WARPS];
   __shared__ int blk_lo[EH_MAXN], blk_hi[EH_MAXN];
   __shared__ float s_err[EH_WARPS];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
 
-  for (int idx = t; idx < n * n; idx += EH_THREADS) {
-    const int i = idx / n, j = idx - (idx / n) * n;
-    const double2 h = H[idx];
-    A[i * ld + j] = make_float2((float)h.x, i == j ? 0.f : (float)h.y);
+  if constexpr (RR) {
+    subspace_matrix(rr.Hraw, rr.M, n, A, R, rr.Aout);
+  } else {
+    for (int idx = t; idx < n * n; idx += EH_THREADS) {
+      const int i = idx / n, j = idx - (idx / n) * n;
+      const double2 h = H[idx];
+      A[i * ld + j] = make_float2((float)h.x, i == j ? 0.f : (float)h.y);
+    }
   }
   __syncthreads();
 
@@ -521,10 +730,70 @@ __global__ void __launch_bounds__(EH_THREADS, 1)
     }
   }
   __syncthreads();
-  for (int idx = t; idx < n * n; idx += EH_THREADS) {
-    const int i = idx / n, j = idx - (idx / n) * n;
-    const float2 v = A[i * ld + j];
-    Vout[idx] = make_double2((double)v.x, (double)v.y);
+  if constexpr (RR) {
+    // ranks of the eigenvalues (ties by index) and the exported vectors
+    int* rank = blk_lo;
+    if (t < n) {
+      const float li = lam[t];
+      int r = 0;
+      for (int j = 0; j < n; ++j) r += (lam[j] < li) || (lam[j] == li && j < t);
+      rank[t] = r;
+      rr.perm[t] = r;
+    }
+    for (int i = warp; i < n; i += EH_WARPS)
+      for (int j = lane; j < n; j += 32) rr.Vout[i * n + j] = A[i * ld + j];
+    __syncthreads();
+    step_matrix(A, rr.M, n, lam, rank, rr.alpha, R, rr.Mcat);
+  } else {
+    for (int idx = t; idx < n * n; idx += EH_THREADS) {
+      const int i = idx / n, j = idx - (idx / n) * n;
+      const float2 v = A[i * ld + j];
+      Vout[idx] = make_double2((double)v.x, (double)v.y);
+    }
+  }
+}
+
+// Reported eigenvalues of the Rayleigh-Ritz variant: FP64 Rayleigh quotients of the FP32
+// eigenvectors on the FP32 subspace matrix, eig[perm[j]] = Re(v_j^H A v_j) / (v_j^H v_j).
+__global__ void k_ritz_values(const float2* __restrict__ A, const float2* __restrict__ V, const int* __restrict__ perm,
+                              int n, double* __restrict__ eig) {
+  const int j = blockIdx.x;
+  __shared__ double2 v[EH_MAXN];
+  __shared__ double red[2][8];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const float2 x = V[k * n + j];
+    v[k] = make_double2((double)x.x, (double)x.y);
+  }
+  __syncthreads();
+  double num = 0.0, den = 0.0;
+  for (int a = threadIdx.x >> 5; a < n; a += blockDim.x >> 5) {
+    const double2 va = v[a];
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = threadIdx.x & 31; b < n; b += 32) {
+      const float2 h = A[a * n + b];
+      const double2 vb = v[b];
+      s.x += (double)h.x * vb.x - (double)h.y * vb.y;
+      s.y += (double)h.x * vb.y + (double)h.y * vb.x;
+    }
+    num += va.x * s.x + va.y * s.y;                                  // Re(conj(v_a) s)
+    if ((threadIdx.x & 31) == 0) den += va.x * va.x + va.y * va.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(FULL, num, o);
+    den += __shfl_xor_sync(FULL, den, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = num;
+    red[1][threadIdx.x >> 5] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    eig[perm[j]] = a / b;
   }
 }
 
@@ -532,13 +801,31 @@ __global__ void __launch_bounds__(EH_THREADS, 1)
 
 void eigh_householder_f32(const double2* A, double2* V, int n, cudaStream_t s) {
   if (n > EH_MAXN || n < 1) fail(KS_ERR_ARG, "eigh_householder_f32: n=%d not in [1, %d]", n, EH_MAXN);
-  const size_t smem = ((size_t)EH_MAXN * (EH_MAXN + 1) + (size_t)EH_MAXN * (EH_MAXN - 1) / 2) * sizeof(float2);
   static bool attr = false;
   if (!attr) {
-    KS_CUDA(cudaFuncSetAttribute(k_eigh_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KS_CUDA(cudaFuncSetAttribute(k_eigh_householder<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EH_SMEM));
     attr = true;
   }
-  k_eigh_householder<<<1, EH_THREADS, smem, s>>>(A, n, V);
+  k_eigh_householder<false><<<1, EH_THREADS, EH_SMEM, s>>>(A, n, V, RRStep{});
+  KS_CHECK_LAUNCH();
+}
+
+void rr_step_mixed(const float2* Hraw, const float2* M, double alpha, int n, float2* Mcat, float2* Aout,
+                   float2* Vout, int* perm, cudaStream_t s) {
+  if (n > EH_MAXN || n < 1) fail(KS_ERR_ARG, "rr_step_mixed: n=%d not in [1, %d]", n, EH_MAXN);
+  static bool attr = false;
+  if (!attr) {
+    KS_CUDA(cudaFuncSetAttribute(k_eigh_householder<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EH_SMEM));
+    attr = true;
+  }
+  const RRStep rr{Hraw, M, (float)alpha, Mcat, Aout, Vout, perm};
+  k_eigh_householder<true><<<1, EH_THREADS, EH_SMEM, s>>>(nullptr, n, nullptr, rr);
+  KS_CHECK_LAUNCH();
+}
+
+void ritz_values(const float2* A, const float2* V, const int* perm, int n, double* eig, cudaStream_t s) {
+  if (n > EH_MAXN || n < 1) fail(KS_ERR_ARG, "ritz_values: n=%d not in [1, %d]", n, EH_MAXN);
+  k_ritz_values<<<n, 256, 0, s>>>(A, V, perm, n, eig);
   KS_CHECK_LAUNCH();
 }
 

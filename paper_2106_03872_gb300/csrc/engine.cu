@@ -32,11 +32,20 @@ StageProfiler::~StageProfiler() {
     cudaEventDestroy(p.b);
   }
   for (auto e : free_) cudaEventDestroy(e);
+  if (base_) cudaEventDestroy(base_);
 }
 
 void StageProfiler::enable(bool on) {
   if (!on) collect();
   on_ = on;
+}
+
+void StageProfiler::timeline(bool on) {
+  collect();
+  timeline_ = on;
+  base_set_ = false;
+  spans_.clear();
+  if (on && !base_) KS_CUDA(cudaEventCreate(&base_));
 }
 
 cudaEvent_t StageProfiler::get_event() {
@@ -59,6 +68,10 @@ int StageProfiler::begin(const char* name, cudaStream_t s) {
     idx = (int)entries_.size() - 1;
   }
   Pending p{idx, get_event(), get_event()};
+  if (timeline_ && !base_set_) {
+    KS_CUDA(cudaEventRecord(base_, s));
+    base_set_ = true;
+  }
   KS_CUDA(cudaEventRecord(p.a, s));
   pending_.push_back(p);
   return (int)pending_.size() - 1;
@@ -73,6 +86,12 @@ void StageProfiler::collect() {
     KS_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
     entries_[p.entry].ms += ms;
     entries_[p.entry].count += 1;
+    if (timeline_ && base_set_) {
+      float t0 = 0, t1 = 0;
+      KS_CUDA(cudaEventElapsedTime(&t0, base_, p.a));
+      KS_CUDA(cudaEventElapsedTime(&t1, base_, p.b));
+      spans_.push_back(Span{p.entry, t0, t1});
+    }
     free_.push_back(p.a);
     free_.push_back(p.b);
   }
@@ -167,6 +186,14 @@ template <typename T> class Engine final : public EngineBase {
     eig_ = alloc<double>(ns_);
     lam_ = alloc<double>(ns_);
     if (mixed_cholesky()) chw_ = alloc<double2>(cholesky_mixed_workspace(ns_));
+    if (fused_rr()) {
+      hraw32_ = alloc<float2>(nn);
+      m32_ = alloc<float2>(nn);
+      mcat32_ = alloc<float2>(2 * nn);
+      aexp_ = alloc<float2>(nn);
+      vexp_ = alloc<float2>(nn);
+      perm_ = alloc<int>(ns_);
+    }
     // ---- potentials / real-time
     dens_ = alloc<T>(N3);
     pwork_ = alloc<C>(N3);
@@ -182,6 +209,7 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaEventCreateWithFlags(&ev_gram_, cudaEventDisableTiming));
     KS_CUDA(cudaEventCreateWithFlags(&ev_hraw_, cudaEventDisableTiming));
     KS_CUDA(cudaEventCreateWithFlags(&ev_chol_, cudaEventDisableTiming));
+    KS_CUDA(cudaEventCreateWithFlags(&ev_ritz_, cudaEventDisableTiming));
     KS_CUDA(cudaStreamSynchronize(nullptr));
   }
 
@@ -193,6 +221,7 @@ template <typename T> class Engine final : public EngineBase {
     if (ev_gram_) cudaEventDestroy(ev_gram_);
     if (ev_hraw_) cudaEventDestroy(ev_hraw_);
     if (ev_chol_) cudaEventDestroy(ev_chol_);
+    if (ev_ritz_) cudaEventDestroy(ev_ritz_);
   }
 
   const HostGeometry& geo() const override { return g_; }
@@ -320,11 +349,11 @@ template <typename T> class Engine final : public EngineBase {
   // CholQR: S = Psi^H Psi, S = L L^H, Psi <- Psi L^{-H}  (rows: psi <- conj(L^{-1}) psi)
   // ------------------------------------------------------------------------------------------
   // M = conj(L^{-1}) for S = L L^H (mS_ -> mM_), on stream st
-  void factor(cudaStream_t st) {
+  void factor(cudaStream_t st, float2* m32 = nullptr) {
     const int n = ns_;
     ProfScope p(prof, "cholesky", st);
     if (mixed_cholesky()) {
-      cholesky_inverse_mixed(mS_, mM_, n, 1e-6, chw_, status_, st);
+      cholesky_inverse_mixed(mS_, mM_, n, 1e-6, chw_, status_, st, m32);
     } else {
       KS_CUDA(cudaMemcpyAsync(mF_, mS_, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
       cholesky_inverse_tol(mF_, mM_, n, sizeof(T) == 8 ? 1e-12 : 1e-6, status_, st);
@@ -409,10 +438,16 @@ template <typename T> class Engine final : public EngineBase {
     //    Mcat = [(I + alpha Lambda) C | -alpha C] run on the side stream (one SM), while
     //  - the main stream applies H to H psi (H^2 psi);
     //  - then psi <- Mcat [psi; H psi] and H psi <- Mcat [H psi; H^2 psi].
+    // On the bf16x3 path with n <= 128 the side stream's Rayleigh-Ritz step is one CTA
+    // (rr_step_mixed: subspace matrix, eigenpairs, C and Mcat in FP32, rows in ascending order
+    // of the FP32 eigenvalues); the reported FP64 Rayleigh quotients follow on the side
+    // stream while the main stream rotates.
     // H psi enters the next iteration without a new application of H to psi; it is recomputed
     // directly on entry to a call whose block changed and every HPSI_REFRESH iterations.
     const int n = ns_;
     const bool mixed = sizeof(T) == 4;
+    const bool frr = fused_rr();
+    bool ritz_pending = false;
     for (int it = 0; it < niter; ++it) {
       if (!hpsi_valid_ || hpsi_age_ >= HPSI_REFRESH) {
         apply_h(psi_, hpsi_, n, s);
@@ -426,32 +461,51 @@ template <typename T> class Engine final : public EngineBase {
       KS_CUDA(cudaEventRecord(ev_gram_, s));
       {
         ProfScope p(prof, "gram", s);
-        overlap(psi_, hpsi_, n, mA_, s);
+        overlap(psi_, hpsi_, n, mA_, s, frr ? hraw32_ : nullptr);
       }
       KS_CUDA(cudaEventRecord(ev_hraw_, s));
       // side stream: factor, subspace matrix, eigenpairs, step matrix
       KS_CUDA(cudaStreamWaitEvent(aux_, ev_gram_, 0));
-      factor(aux_);
+      factor(aux_, frr ? m32_ : nullptr);
       KS_CUDA(cudaStreamWaitEvent(aux_, ev_hraw_, 0));
-      {
-        ProfScope p(prof, "subspace", aux_);
-        small_product(mA_, mM_, n, SP_TRANS_B, mixed, mT_, aux_);   // H_raw M^T
-        small_product(mM_, mT_, n, SP_CONJ_A, mixed, mA_, aux_);    // conj(M) H_raw M^T
-        hermitize(mA_, n, aux_);
+      if (frr) {
+        {
+          ProfScope p(prof, "rr_step", aux_);
+          rr_step_mixed(hraw32_, m32_, alpha, n, mcat32_, aexp_, vexp_, perm_, aux_);
+        }
+        {
+          ProfScope p(prof, "rot_prep", aux_);
+          tc_rotate_prepare(mcat32_, n, 2 * n, rotws_, rotws_bytes_, aux_);
+        }
+        KS_CUDA(cudaEventRecord(ev_chol_, aux_));
+        // the reported eigenvalues, while the main stream rotates
+        {
+          ProfScope p(prof, "ritz_values", aux_);
+          ritz_values(aexp_, vexp_, perm_, n, eig_, aux_);
+        }
+        KS_CUDA(cudaEventRecord(ev_ritz_, aux_));
+        ritz_pending = true;
+      } else {
+        {
+          ProfScope p(prof, "subspace", aux_);
+          small_product(mA_, mM_, n, SP_TRANS_B, mixed, mT_, aux_);   // H_raw M^T
+          small_product(mM_, mT_, n, SP_CONJ_A, mixed, mA_, aux_);    // conj(M) H_raw M^T
+          hermitize(mA_, n, aux_);
+        }
+        {
+          ProfScope p(prof, "eigh", aux_);
+          if (mixed && n <= 128)
+            eigh_mixed(mA_, mV_, lam_, eig_, mT_, n, aux_);
+          else
+            jacobi_eigh(mA_, mV_, eig_, mT_, n, aux_);
+        }
+        {
+          ProfScope p(prof, "subspace", aux_);
+          small_product(mT_, mM_, n, 0, mixed, mC_, aux_);            // C = Vt M
+          sd_matrix(mC_, eig_, alpha, n, mCat_, aux_);
+        }
+        KS_CUDA(cudaEventRecord(ev_chol_, aux_));
       }
-      {
-        ProfScope p(prof, "eigh", aux_);
-        if (mixed && n <= 128)
-          eigh_mixed(mA_, mV_, lam_, eig_, mT_, n, aux_);
-        else
-          jacobi_eigh(mA_, mV_, eig_, mT_, n, aux_);
-      }
-      {
-        ProfScope p(prof, "subspace", aux_);
-        small_product(mT_, mM_, n, 0, mixed, mC_, aux_);            // C = Vt M
-        sd_matrix(mC_, eig_, alpha, n, mCat_, aux_);
-      }
-      KS_CUDA(cudaEventRecord(ev_chol_, aux_));
       // main stream: H^2 psi meanwhile
       C* h2 = spare(psi_, hpsi_);
       apply_h(hpsi_, h2, n, s);
@@ -459,15 +513,21 @@ template <typename T> class Engine final : public EngineBase {
       {
         ProfScope p(prof, "rotate", s);
         C* o1 = spare3(psi_, hpsi_, h2);
-        rot(mCat_, psi_, o1, s, hpsi_);
         C* o2 = spare4(psi_, hpsi_, h2, o1);
-        rot(mCat_, hpsi_, o2, s, h2);
+        if (frr) {
+          rot_prepared(psi_, hpsi_, o1, s);
+          rot_prepared(hpsi_, h2, o2, s);
+        } else {
+          rot(mCat_, psi_, o1, s, hpsi_);
+          rot(mCat_, hpsi_, o2, s, h2);
+        }
         psi_ = o1;
         hpsi_ = o2;
       }
       hpsi_valid_ = true;
       ++hpsi_age_;
     }
+    if (ritz_pending) KS_CUDA(cudaStreamWaitEvent(s, ev_ritz_, 0));
     int st = 0;
     KS_CUDA(cudaMemcpyAsync(&st, status_, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (eig_host) KS_CUDA(cudaMemcpyAsync(eig_host, eig_, ns_ * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -574,12 +634,14 @@ template <typename T> class Engine final : public EngineBase {
   }
   bool use_tc() const { return sizeof(T) == 4 && prec_ == KS_MIXED_BF16X3; }
   bool mixed_cholesky() const { return sizeof(T) == 4 && ns_ <= 160; }
+  // the block iteration's Rayleigh-Ritz step runs in one CTA (rr_step_mixed)
+  bool fused_rr() const { return use_tc() && ns_ <= 128; }
 
   // out = A^H B over the sphere (n x n), tensor cores on the bf16x3 mixed path
-  void overlap(const C* A, const C* B, int n, double2* out, cudaStream_t s) {
+  void overlap(const C* A, const C* B, int n, double2* out, cudaStream_t s, float2* out32 = nullptr) {
     if constexpr (std::is_same<T, float>::value) {
       if (use_tc()) {
-        tc_overlap(A, g_.nG, B, g_.nG, n, n, g_.nG, part_, part_elems_, out, status_ + 1, s);
+        tc_overlap(A, g_.nG, B, g_.nG, n, n, g_.nG, part_, part_elems_, out, status_ + 1, s, out32);
         return;
       }
     }
@@ -596,6 +658,14 @@ template <typename T> class Engine final : public EngineBase {
       }
     }
     rotate<T>(M, nin, X, X2, ns_, g_.nG, Y, g_.nG, ns_, g_.nG, s);
+  }
+
+  // Y = Mcat [X; X2] from the split image of mcat32_ that tc_rotate_prepare left in rotws_
+  void rot_prepared(const C* X, const C* X2, C* Y, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value)
+      tc_rotate_prepared(rotws_, 2 * ns_, X, X2, ns_, g_.nG, Y, g_.nG, ns_, g_.nG, status_ + 1, s);
+    else
+      fail(KS_ERR_STATE, "internal: prepared rotation on the FP64 path");
   }
 
   void check_tc_status(cudaStream_t s) {
@@ -655,13 +725,16 @@ template <typename T> class Engine final : public EngineBase {
   double2* chw_ = nullptr;   // two-pass FP32 Cholesky workspace (mixed path)
   double2 *mT_ = nullptr, *mC_ = nullptr, *mF_ = nullptr;   // subspace products, FP64 factor scratch
   double2* mCat_ = nullptr;                                   // [n][2n] steepest-descent step matrix
+  // one-CTA Rayleigh-Ritz step of the block iteration (FP32 operands and results)
+  float2 *hraw32_ = nullptr, *m32_ = nullptr, *mcat32_ = nullptr, *aexp_ = nullptr, *vexp_ = nullptr;
+  int* perm_ = nullptr;
   // hpsi_ = H psi_ for the resident block (kept by the block iteration between calls); after
   // HPSI_REFRESH iterations that derived it by recurrence, H is applied to psi_ afresh.
   static constexpr int HPSI_REFRESH = 16;
   bool hpsi_valid_ = false;
   int hpsi_age_ = 0;
   cudaStream_t aux_ = nullptr;
-  cudaEvent_t ev_gram_ = nullptr, ev_hraw_ = nullptr, ev_chol_ = nullptr;
+  cudaEvent_t ev_gram_ = nullptr, ev_hraw_ = nullptr, ev_chol_ = nullptr, ev_ritz_ = nullptr;
   void* rotws_ = nullptr;
   size_t rotws_bytes_ = 0;
   int* status_ = nullptr;

@@ -22,7 +22,9 @@ class DeviceArena {
 
 // Per-stage CUDA-event timing of an engine's kernels (off by default).  Each stage scope
 // records an event pair on the launching stream; collect() waits for them and accumulates
-// milliseconds and launch counts per stage name.
+// milliseconds and launch counts per stage name.  With the timeline on, every scope is also
+// kept as a span (start and end in milliseconds after the first scope recorded since the
+// timeline was started), which shows how stages on different streams overlap.
 class StageProfiler {
  public:
   struct Entry {
@@ -30,16 +32,23 @@ class StageProfiler {
     double ms = 0;
     long count = 0;
   };
+  struct Span {
+    int entry;
+    double start, end;
+  };
   ~StageProfiler();
   void enable(bool on);
+  void timeline(bool on);
   bool on() const { return on_; }
   int begin(const char* name, cudaStream_t s);
   void end(int slot, cudaStream_t s);
   void collect();
   const std::vector<Entry>& entries() const { return entries_; }
+  const std::vector<Span>& spans() const { return spans_; }
   void reset() {
     collect();
     entries_.clear();
+    spans_.clear();
   }
 
  private:
@@ -49,8 +58,12 @@ class StageProfiler {
   };
   cudaEvent_t get_event();
   bool on_ = false;
+  bool timeline_ = false;
+  cudaEvent_t base_ = nullptr;
+  bool base_set_ = false;
   std::vector<Entry> entries_;
   std::vector<Pending> pending_;
+  std::vector<Span> spans_;
   std::vector<cudaEvent_t> free_;
 };
 

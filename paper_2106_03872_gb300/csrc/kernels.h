@@ -98,7 +98,7 @@ void cholesky_inverse_tol(double2* A, double2* M, int n, double tol, int* status
 // cholesky_mixed_workspace(n) complex128.  Same status convention as cholesky_inverse.
 size_t cholesky_mixed_workspace(int n);
 void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, double2* work, int* status,
-                            cudaStream_t s);
+                            cudaStream_t s, float2* M32 = nullptr);
 // Hermitian eigen-decomposition of A (destroyed) by cyclic Jacobi; eig ascending, rows of
 // Vt = eigenvectors (largest-magnitude component real positive).  `V` is n*n workspace.
 void jacobi_eigh(double2* A, double2* V, double* eig, double2* Vt, int n, cudaStream_t s);
@@ -109,15 +109,29 @@ void eigh_householder_f32(const double2* A, double2* V, int n, cudaStream_t s);
 // FP64 Rayleigh quotients of the FP32 vectors on A; same outputs as jacobi_eigh.
 // V is n*n workspace, lam n doubles of workspace.
 void eigh_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, int n, cudaStream_t s);
+// Rayleigh-Ritz step of the mixed block iteration in one CTA (n <= 128), FP32 in and out:
+// H_sub = conj(M) Hraw M^T (Hermitian part, exported to Aout), its eigenpairs, C = Vt M and
+// Mcat = [(I + alpha Lambda) C | -alpha C] (n x 2n) with rows in ascending eigenvalue order;
+// Vout holds the eigenvectors as columns in solver order and perm their ranks.
+void rr_step_mixed(const float2* Hraw, const float2* M, double alpha, int n, float2* Mcat, float2* Aout,
+                   float2* Vout, int* perm, cudaStream_t s);
+// eig[perm[j]] = FP64 Rayleigh quotient of column j of V on A (outputs of rr_step_mixed).
+void ritz_values(const float2* A, const float2* V, const int* perm, int n, double* eig, cudaStream_t s);
 
 // ---- tensor-core GEMMs (tc_gemm.cu), split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulation ---------
 // Same contract as gemm_cn<float> / rotate<float>; err receives 1 if a bounded wait expired.
+// out32, when given, receives an FP32 copy of out.
 void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n, int K, double2* part,
-                size_t part_elems, double2* out, int* err, cudaStream_t s);
+                size_t part_elems, double2* out, int* err, cudaStream_t s, float2* out32 = nullptr);
 // Partial-buffer elements tc_overlap wants for an m x n output (one wave of CTAs).
 size_t tc_overlap_part_elems(int m, int n);
 void tc_rotate(const double2* M, int nin, const float2* X, const float2* X2, int nin1, int ldx, float2* Y, int ldy,
                int m, int K, void* work, size_t work_bytes, int* err, cudaStream_t s);
 size_t tc_rotation_workspace_bytes(int m, int nin);
+// tc_rotate in two steps, for one FP32 M applied to several blocks: split M (m x nin) into the
+// workspace once, then run rotations from it.
+void tc_rotate_prepare(const float2* M, int m, int nin, void* work, size_t work_bytes, cudaStream_t s);
+void tc_rotate_prepared(const void* work, int nin, const float2* X, const float2* X2, int nin1, int ldx, float2* Y,
+                        int ldy, int m, int K, int* err, cudaStream_t s);
 
 }  // namespace ks

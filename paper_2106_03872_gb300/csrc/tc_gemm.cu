@@ -468,8 +468,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // Mb images: B row 2i (output Re Y_i) = [Re M_ij | -Im M_ij], row 2i+1 (Im Y_i) = [Im M_ij | Re M_ij]
 // over the 16 states of chunk jc (K index kk: kk < 16 -> X_re of state jc*16+kk, else X_im);
 // value x = t1 + t2 + t3 with t1 = bf16(x), t2 = bf16(x - t1), t3 = bf16(x - t1 - t2).
-__global__ void k_tc_prep_rotation(const double2* __restrict__ M, int m, int nin, int nit, int njc,
+// One bf16 term of the three-way split: the nearest bf16 of x, and what it leaves.
+__device__ __forceinline__ __nv_bfloat16 split_term(double& x) {
+  const __nv_bfloat16 b = __double2bfloat16(x);
+  x -= (double)__bfloat162float(b);
+  return b;
+}
+__device__ __forceinline__ __nv_bfloat16 split_term(float& x) {
+  const __nv_bfloat16 b = __float2bfloat16_rn(x);
+  x -= __bfloat162float(b);                                          // exact in FP32
+  return b;
+}
+
+template <typename CM>
+__global__ void k_tc_prep_rotation(const CM* __restrict__ M, int m, int nin, int nit, int njc,
                                    unsigned char* __restrict__ Mb) {
+  using R = decltype(M->x);
   const size_t total = (size_t)nit * njc * TC_N * R_KR;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int kk = (int)(e % R_KR);
@@ -479,19 +493,17 @@ __global__ void k_tc_prep_rotation(const double2* __restrict__ M, int m, int nin
     const int i = it_i * (TC_N / 2) + row / 2;
     const int j = jc * R_KC + (kk & (R_KC - 1));
     const int part = kk / R_KC;          // 0: multiplies Re X, 1: Im X
-    double x = 0.0;
+    R x = 0;
     if (i < m && j < nin) {
-      const double2 v = M[(size_t)i * nin + j];
+      const CM v = M[(size_t)i * nin + j];
       if ((row & 1) == 0)
         x = (part == 0 ? v.x : -v.y);
       else
         x = (part == 0 ? v.y : v.x);
     }
-    const __nv_bfloat16 t1 = __double2bfloat16(x);
-    const double r1 = x - (double)__bfloat162float(t1);
-    const __nv_bfloat16 t2 = __double2bfloat16(r1);
-    const double r2 = r1 - (double)__bfloat162float(t2);
-    const __nv_bfloat16 t3 = __double2bfloat16(r2);
+    const __nv_bfloat16 t1 = split_term(x);
+    const __nv_bfloat16 t2 = split_term(x);
+    const __nv_bfloat16 t3 = split_term(x);
     unsigned char* img = Mb + tile * (3 * RB_BYTES);
     const uint32_t o = tile_off(TC_N, row, kk);
     *reinterpret_cast<__nv_bfloat16*>(img + o) = t1;
@@ -500,7 +512,8 @@ __global__ void k_tc_prep_rotation(const double2* __restrict__ M, int m, int nin
   }
 }
 
-__global__ void k_reduce_parts_tc(const double2* __restrict__ part, int nks, size_t mn, double2* __restrict__ out) {
+__global__ void k_reduce_parts_tc(const double2* __restrict__ part, int nks, size_t mn, double2* __restrict__ out,
+                                  float2* __restrict__ out32) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < mn; e += (size_t)gridDim.x * blockDim.x) {
     double2 s = make_double2(0.0, 0.0);
     for (int k = 0; k < nks; ++k) {
@@ -509,6 +522,7 @@ __global__ void k_reduce_parts_tc(const double2* __restrict__ part, int nks, siz
       s.y += p.y;
     }
     out[e] = s;
+    if (out32) out32[e] = make_float2((float)s.x, (float)s.y);
   }
 }
 
@@ -533,7 +547,7 @@ size_t tc_rotation_workspace_bytes(int m, int nin) {
 }
 
 void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n, int K, double2* part,
-                size_t part_elems, double2* out, int* err, cudaStream_t s) {
+                size_t part_elems, double2* out, int* err, cudaStream_t s, float2* out32) {
   set_attrs();
   const int tm = (m + TC_M - 1) / TC_M, tn = (n + TC_N / 2 - 1) / (TC_N / 2);
   int ks = std::max(1, 148 / (tm * tn));
@@ -547,24 +561,43 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
   k_tc_overlap<<<g, O_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, part, err);
   KS_CHECK_LAUNCH();
   const size_t mn = (size_t)m * n;
-  k_reduce_parts_tc<<<(unsigned)std::min<size_t>((mn + 255) / 256, 1024), 256, 0, s>>>(part, ks, mn, out);
+  k_reduce_parts_tc<<<(unsigned)std::min<size_t>((mn + 255) / 256, 1024), 256, 0, s>>>(part, ks, mn, out, out32);
   KS_CHECK_LAUNCH();
 }
 
-void tc_rotate(const double2* M, int nin, const float2* X, const float2* X2, int nin1, int ldx, float2* Y, int ldy,
-               int m, int K, void* work, size_t work_bytes, int* err, cudaStream_t s) {
-  if (!X2) nin1 = nin;
-  set_attrs();
+namespace {
+
+template <typename CM>
+void prepare_rotation(const CM* M, int m, int nin, void* work, size_t work_bytes, cudaStream_t s) {
   const int nit = (m + TC_N / 2 - 1) / (TC_N / 2), njc = (nin + R_KC - 1) / R_KC;
   if (tc_rotation_workspace_bytes(m, nin) > work_bytes) fail(KS_ERR_ARG, "tc_rotate: workspace too small");
   const size_t total = (size_t)nit * njc * TC_N * R_KR;
-  k_tc_prep_rotation<<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0, s>>>(
+  k_tc_prep_rotation<CM><<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0, s>>>(
       M, m, nin, nit, njc, static_cast<unsigned char*>(work));
   KS_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+void tc_rotate_prepared(const void* work, int nin, const float2* X, const float2* X2, int nin1, int ldx, float2* Y,
+                        int ldy, int m, int K, int* err, cudaStream_t s) {
+  if (!X2) nin1 = nin;
+  set_attrs();
+  const int nit = (m + TC_N / 2 - 1) / (TC_N / 2), njc = (nin + R_KC - 1) / R_KC;
   dim3 g((K + TC_M - 1) / TC_M, nit);
   k_tc_rotate<<<g, TC_THREADS, R_SMEM, s>>>(static_cast<const uint4*>(work), njc, X, X2, nin1, ldx, Y, ldy, m, nin, K,
                                             err);
   KS_CHECK_LAUNCH();
+}
+
+void tc_rotate_prepare(const float2* M, int m, int nin, void* work, size_t work_bytes, cudaStream_t s) {
+  prepare_rotation(M, m, nin, work, work_bytes, s);
+}
+
+void tc_rotate(const double2* M, int nin, const float2* X, const float2* X2, int nin1, int ldx, float2* Y, int ldy,
+               int m, int K, void* work, size_t work_bytes, int* err, cudaStream_t s) {
+  prepare_rotation(M, m, nin, work, work_bytes, s);
+  tc_rotate_prepared(work, nin, X, X2, nin1, ldx, Y, ldy, m, K, err, s);
 }
 
 }  // namespace ks

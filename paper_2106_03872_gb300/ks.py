@@ -25,7 +25,7 @@ EXPORTS = ["ks_count_gvectors", "ks_grid_create", "ks_grid_destroy", "ks_grid_gv
            "ks_get_vloc", "ks_set_states", "ks_get_states", "ks_states_device", "ks_apply_h", "ks_apply_h_host",
            "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_td_step",
            "ks_serve_create", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info",
-           "ks_profile", "ks_profile_read", "ks_kernel_launches", "ks_overlap_noalloc", "ks_last_error"]
+           "ks_profile", "ks_profile_read", "ks_profile_span", "ks_kernel_launches", "ks_overlap_noalloc", "ks_last_error"]
 
 
 class KsError(RuntimeError):
@@ -89,6 +89,8 @@ def load():
     lib.ks_profile.restype = ct.c_int
     lib.ks_profile_read.argtypes = [P, ct.c_int, ct.c_char_p, ct.c_int, dp, ct.POINTER(ct.c_long)]
     lib.ks_profile_read.restype = ct.c_int
+    lib.ks_profile_span.argtypes = [P, ct.c_int, ct.c_char_p, ct.c_int, dp, dp]
+    lib.ks_profile_span.restype = ct.c_int
     lib.ks_kernel_launches.argtypes = []
     lib.ks_kernel_launches.restype = ct.c_uint64
     lib.ks_last_error.argtypes = []
@@ -249,6 +251,18 @@ class Grid:
         i = 0
         while load().ks_profile_read(self.h, i, buf, 128, ct.byref(ms), ct.byref(cnt)) == KS_OK:
             out[buf.value.decode()] = (ms.value, cnt.value)
+            i += 1
+        return out
+
+    def profile_spans(self):
+        """[(stage name, start ms, end ms)] of the timeline started by profile(3)."""
+        out = []
+        buf = ct.create_string_buffer(128)
+        t0 = ct.c_double()
+        t1 = ct.c_double()
+        i = 0
+        while load().ks_profile_span(self.h, i, buf, 128, ct.byref(t0), ct.byref(t1)) == KS_OK:
+            out.append((buf.value.decode(), t0.value, t1.value))
             i += 1
         return out
 

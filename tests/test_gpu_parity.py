@@ -414,6 +414,45 @@ def test_block_iteration_split_calls_bit_identical(ks):
     b.close()
 
 
+def test_block_iteration_mixed_128_states(ks):
+    """128 states, the largest block whose Rayleigh-Ritz step runs in one CTA on the mixed
+    path: eigenvalues against the oracle's, and the returned states in ascending order."""
+    cell = inputs.small_cell(16.0, 48, 3, 128, 47, depth=-3.0)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec="bf16x3")
+    c = inputs.random_coeffs(47, 128, ref.nG)
+    g.set_states(c)
+    eps = g.block_iteration(2)
+    eps_ref, c_ref = ko.block_iteration(ref, c, 2)
+    assert np.max(np.abs(eps - eps_ref)) <= 1e-4 * max(1.0, np.max(np.abs(eps_ref)))
+    # rows in ascending order of the (FP32) eigenvalues; the reported FP64 Rayleigh quotients
+    # may swap only within the FP32 error
+    assert np.all(np.diff(eps) >= -1e-5)
+    g.close()
+
+
+def test_block_iteration_degenerate_shells(ks):
+    """Free electrons, a block spanning the 19 plane waves with |m|^2 <= 2 mixed by a random
+    unitary: one block iteration's Ritz values are the exact shell energies (1, 6 and 12-fold
+    degenerate), and the states stay in the span (the SD step vanishes on exact eigenvectors)."""
+    cell = inputs.small_cell(8.0, 24, 0, 19, 19)
+    ref = ko.Cell(cell)
+    m2 = np.sum(ref.m ** 2, axis=1)
+    picks = np.flatnonzero(m2 <= 2)
+    c = np.zeros((19, ref.nG), complex)
+    c[np.arange(19), picks] = 1.0
+    rng = np.random.default_rng(5)
+    Q, _ = np.linalg.qr(rng.normal(size=(19, 19)) + 1j * rng.normal(size=(19, 19)))
+    g = ks.Grid(cell, prec="bf16x3")
+    g.set_states(Q @ c)
+    eps = g.block_iteration(1)
+    assert np.allclose(eps, np.sort(0.5 * ref.g2[picks]), atol=2e-5)
+    out = g.get_states()
+    outside = np.delete(out, picks, axis=1)
+    assert np.max(np.abs(outside)) <= 1e-5 * np.max(np.abs(out))
+    g.close()
+
+
 def test_block_iteration_mixed_beyond_128_states(ks):
     """150 states on the mixed path: the factor keeps the two-pass FP32 scheme (n <= 160) and
     the eigensolver falls back to FP64 Jacobi (n > 128)."""
