@@ -29,7 +29,7 @@
 //   0. H_sub = conj(M) H_raw M^T from the raw projection H_raw = Psi^H (H Psi) and the
 //      lower-triangular orthonormaliser M (T = H_raw M^T, then conj(M) T in place, row blocks
 //      from the bottom up, since row block b of the result needs T rows <= b only);
-//   1-4 as above;
+//   1-4 as above, without the Newton-Schulz steps (the next CholQR orthonormalises);
 //   5. C = Vt M and the steepest-descent step matrix Mcat = [(I + alpha Lambda) C | -alpha C]
 //      with rows in ascending order of the FP32 eigenvalues.
 // H_sub and the eigenvectors are exported so that ritz_values can form the reported FP64
@@ -614,8 +614,11 @@ __global__ void __launch_bounds__(EH_THREADS, 1)
   }
   __syncthreads();
   // Newton-Schulz: G = Z^T Z; while max |G - I| > 2e-6: Z <- 1.5 Z - 0.5 Z G.
-  // Thread tiles: rows warp + 32u, columns lane + 32v (u, v < 4).
-  {
+  // Thread tiles: rows warp + 32u, columns lane + 32v (u, v < 4).  The Rayleigh-Ritz variant
+  // skips it: its vectors only span the next iterate, whose CholQR orthonormalises the block,
+  // and outside degenerate clusters (handled above) they are orthogonal to eps |T| / gap
+  // <= 6e-3, a condition number of the step matrix within 1.01.
+  if constexpr (!RR) {
     float* G = low;                                                  // [n][n]
     for (int it = 0; it < 4; ++it) {
       float g[4][4] = {};

@@ -14,9 +14,11 @@
 // the MMA rows are grid coefficients k, the reduction runs over (j, re|im) and B holds the
 // four real blocks of M, so column 2i is Re Y[i][k] and 2i+1 is Im Y[i][k].
 //
-// One CTA computes a 128 x 256 real tile (M = 128 rows, N = 256 columns) with shared-memory
-// rings: all 256 threads load and split the next K-chunk while one thread issues the MMAs
-// of the current one; tcgen05.commit arrives on a per-stage mbarrier.
+// MMA tiles are 128 x 256 real (M = 128 rows, N = 256 columns), accumulated in TMEM.  Both
+// kernels are warp-specialised: sixteen warps load and split operand chunks into a ring of
+// shared-memory stages, one warp issues the MMAs, and stages are handed over with mbarriers
+// (the splitters arrive on `full`; tcgen05.commit arrives on `empty` once the MMAs that read
+// the stage have completed).  The rotation's M images arrive by bulk copy (TMA).
 // Operand tiles use the K-major no-swizzle canonical layout (8-row x 16-byte core
 // matrices; LBO = distance between core matrices along K, SBO = along rows).
 // Every mbarrier wait is bounded; on expiry the kernel records an error code and returns.
@@ -30,7 +32,6 @@ namespace ks {
 
 namespace {
 
-constexpr int TC_THREADS = 256;
 constexpr int TC_M = 128;           // MMA rows
 constexpr int TC_N = 256;           // MMA columns
 constexpr uint32_t TMEM_COLS = 256;
@@ -39,10 +40,19 @@ constexpr int R_KR = 32;
 constexpr int R_KC = R_KR / 2;
 constexpr int RA_BYTES = TC_M * R_KR * 2;                 // 8 KB
 constexpr int RB_BYTES = TC_N * R_KR * 2;                 // 16 KB
-constexpr int R_STAGE_BYTES = 2 * RA_BYTES + 3 * RB_BYTES; // 64 KB
-constexpr int R_NSTAGE = 3;
-constexpr int R_SMEM = R_NSTAGE * R_STAGE_BYTES + 1024;
-constexpr long WAIT_LIMIT = 1L << 28;                    // spin bound of every mbarrier wait
+// one CTA: two 128-row tiles of grid coefficients (two TMEM accumulators of 256 columns), so
+// each chunk of M images serves 256 rows; A (states, hi/lo per tile) in a 2-deep ring, the
+// three M images in a 3-deep ring prefetched two chunks ahead
+constexpr int R_TILES = 2;
+constexpr int R_SPLIT_WARPS = 16;                            // split X into the A stages
+constexpr int R_THREADS = 32 * (R_SPLIT_WARPS + 2);          // + MMA warp + image-copy warp
+constexpr int R_A_STAGE = R_TILES * 2 * RA_BYTES;           // 32 KB
+constexpr int R_B_STAGE = 3 * RB_BYTES;                      // 48 KB
+constexpr int R_NA = 2, R_NB = 3;
+constexpr int R_RING = R_NA * R_A_STAGE + R_NB * R_B_STAGE;  // 208 KB
+constexpr int R_SMEM = R_RING + 1024;
+constexpr uint32_t R_TMEM_COLS = 512;
+constexpr long long WAIT_CYCLES = 4000000000LL;          // bound of every mbarrier wait (~2 s)
 
 // ---- PTX wrappers -----------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -63,14 +73,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return done != 0;
 }
 
-// Bounded wait; false if the limit expired.
+// Bounded wait (by elapsed SM clocks, since a failed try_wait may itself suspend the thread
+// for a while); false if the limit expired.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (long it = 0; it < WAIT_LIMIT; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  return true;
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bulk (TMA) copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from global to
+// this CTA's shared memory; completion is counted on mbarrier `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -147,182 +174,155 @@ __device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo
   lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
 }
 
+// x = hi + lo + O(2^-17 |x|) with hi = bf16(x), lo = bf16(x - hi) (as floats).
+__device__ __forceinline__ void split1(float x, float& hi, float& lo) {
+  hi = __bfloat162float(__float2bfloat16_rn(x));
+  lo = x - hi;
+}
+
+__device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                : "memory");
 }
 
-// Common prologue: barriers and TMEM.  Returns the TMEM base address.
-__device__ __forceinline__ uint32_t tc_setup(unsigned char* smem, uint32_t& bar0, int ring_bytes, int nstage) {
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + ring_bytes);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + ring_bytes + 64);
-  bar0 = smem_u32(bars);
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < nstage; ++i) mbar_init(bar0 + 8 * i, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if ((threadIdx.x >> 5) == 0) tmem_alloc(smem_u32(slot), TMEM_COLS);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  return *slot;
-}
 
 // ------------------------------------------------------------------------------------------------
-// Overlap: part[ks][i][j] = sum_{k in chunk ks} conj(A[i][k]) B[j][k], tile 128 (i) x 128 (j).
-// Pipeline per K-chunk of 16 complex: cp.async copies raw FP32 rows into a 3-deep ring two
-// chunks ahead; all threads split the current chunk into the bf16 operand ring (2 deep);
-// one thread issues the MMAs.  Raw rows are padded to 18 complex (144 bytes) so that the
-// split pass's 16-byte reads from consecutive rows hit distinct bank groups.
+// Overlap: part[ks][i][j] = sum_{k in chunk ks} conj(A[i][k]) B[j][k] (FP32), tile 128 (i) x 128 (j).
+// Warp roles: warps 0-15 load the FP32 rows of a K-chunk of 16 complex into registers (two
+// chunks ahead; rows are only 8-byte aligned when the row length is odd), split them into the
+// bf16 hi/lo operand stages and arrive on the stage's `full` barrier; warp 16 issues the MMAs
+// and releases the stage through tcgen05.commit on its `empty` barrier.
 // ------------------------------------------------------------------------------------------------
 constexpr int O_KC = 16;
 constexpr int O_KR = 2 * O_KC;
-constexpr int O_PITCH = 18;                                  // complex per raw row (144 B)
-constexpr int O_THREADS = 512;
-constexpr int O_RAW_A = TC_M * O_PITCH * 8;                  // 20 KB
-constexpr int O_RAW_B = (TC_N / 2) * O_PITCH * 8;            // 20 KB
-constexpr int O_RAW_STAGE = O_RAW_A + O_RAW_B;
-constexpr int O_NRAW = 3;
+constexpr int O_SPLIT_WARPS = 16;
+constexpr int O_THREADS = 32 * (O_SPLIT_WARPS + 1);
 constexpr int O_A_BYTES = TC_M * O_KR * 2;                   // 8 KB (hi or lo)
 constexpr int O_B_BYTES = TC_N * O_KR * 2;                   // 16 KB
 constexpr int O_OP_STAGE = 2 * O_A_BYTES + 2 * O_B_BYTES;    // 48 KB
-constexpr int O_NOP = 2;
-constexpr int O_RING = O_NRAW * O_RAW_STAGE + O_NOP * O_OP_STAGE;
+constexpr int O_NOP = 4;
+constexpr int O_RING = O_NOP * O_OP_STAGE;                   // 192 KB
 constexpr int O_SMEM = O_RING + 1024;
 
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int NPEND> __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
-}
 
 __global__ void __launch_bounds__(O_THREADS, 1)
     k_tc_overlap(const float2* __restrict__ A, int lda, const float2* __restrict__ B, int ldb, int m, int n, int K,
-                 int kchunk, double2* __restrict__ part, int* __restrict__ err) {
+                 int kchunk, float2* __restrict__ part, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
-  const uint32_t raw0 = smem_u32(tsm);
-  const uint32_t op0 = raw0 + O_NRAW * O_RAW_STAGE;
-  const float2* rawp = reinterpret_cast<const float2*>(tsm);
-  uint32_t bar0;
-  const uint32_t tmem = tc_setup(tsm, bar0, O_RING, O_NOP);
+  const uint32_t op0 = smem_u32(tsm);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + O_RING);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(tsm + O_RING + 128);
+  const uint32_t full = smem_u32(bars), empty = full + 8 * O_NOP, done = empty + 8 * O_NOP;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  if (t == 0) {
+    for (int i = 0; i < O_NOP; ++i) {
+      mbar_init(full + 8 * i, 32 * O_SPLIT_WARPS);
+      mbar_init(empty + 8 * i, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (w == 0) tmem_alloc(smem_u32(slot), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
   const int i0 = blockIdx.y * TC_M, j0 = blockIdx.x * (TC_N / 2);
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
   const int nk = (kend - kbeg + O_KC - 1) / O_KC;
-  const int t = threadIdx.x;
-
-  // raw copies of chunk c: 128 rows of A and 128 rows of B, 16 complex each (8-byte copies)
-  auto issue_raw = [&](int c) {
-    const uint32_t rs = raw0 + (c % O_NRAW) * O_RAW_STAGE;
-    const int k0 = kbeg + c * O_KC;
-#pragma unroll
-    for (int p = 0; p < (TC_M * O_KC) / O_THREADS; ++p) {
-      const int idx = p * O_THREADS + t;
-      const int r = idx / O_KC, kk = idx - r * O_KC;
-      const int k = k0 + kk;
-      const bool va = (i0 + r < m) && (k < kend);
-      cp_async8(rs + (uint32_t)(r * O_PITCH + kk) * 8, va ? (const void*)(A + (size_t)(i0 + r) * lda + k) : (const void*)A,
-                va ? 8u : 0u);
-      const bool vb = (j0 + r < n) && (k < kend);
-      cp_async8(rs + O_RAW_A + (uint32_t)(r * O_PITCH + kk) * 8,
-                vb ? (const void*)(B + (size_t)(j0 + r) * ldb + k) : (const void*)B, vb ? 8u : 0u);
-    }
-  };
-
-  if (nk > 0) issue_raw(0);
-  cp_async_commit();
-  if (nk > 1) issue_raw(1);
-  cp_async_commit();
   bool ok = true;
-  for (int it = 0; it < nk; ++it) {
-    if (it + 2 < nk) issue_raw(it + 2);
-    cp_async_commit();
-    cp_async_wait<2>();            // chunk `it` has landed (this thread's copies)
-    __syncthreads();               // ... and every thread's
-    const int ost = it % O_NOP;
-    if (it >= O_NOP) {
-      ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ost, ((it - O_NOP) / O_NOP) & 1)) != 0;
-      if (!ok) break;
-    }
-    const float2* ra = rawp + (size_t)(it % O_NRAW) * (O_RAW_STAGE / 8);
-    const float2* rb = ra + O_RAW_A / 8;
-    const uint32_t oa_hi = op0 + ost * O_OP_STAGE, oa_lo = oa_hi + O_A_BYTES;
-    const uint32_t ob_hi = oa_hi + 2 * O_A_BYTES, ob_lo = ob_hi + O_B_BYTES;
-    // A: item (kq, r), 4 complex per item
+
+  if (w < O_SPLIT_WARPS) {
+    // thread (row r, lane-in-row l): complex l, l + 4, l + 8, l + 12 of the chunk for row r
+    // of A and complex row r of B, so four lanes read 32 contiguous bytes of a row; each
+    // complex becomes one 4-byte (re, im) bf16 pair in K-group u of the tile, and a warp's
+    // eight rows fill one core matrix per store
+    const int r = t >> 2, l = t & 3;
+    const bool ra = i0 + r < m, rb = j0 + r < n;
+    const float2* pa = A + (size_t)(ra ? i0 + r : 0) * lda;
+    const float2* pb = B + (size_t)(rb ? j0 + r : 0) * ldb;
+    float2 xa[8], xb[8];                     // [0, 4): A, [4, 8): B
+    auto load = [&](int c, float2 (&x)[8]) {
+      const int k = kbeg + c * O_KC + l;
 #pragma unroll
-    for (int p = 0; p < (TC_M * (O_KC / 4)) / O_THREADS; ++p) {
-      const int item = p * O_THREADS + t;
-      const int kq = item / TC_M, r = item - kq * TC_M;
-      float x[8];
-      const float4* src = reinterpret_cast<const float4*>(ra + r * O_PITCH + 4 * kq);
-      const float4 v0 = src[0], v1 = src[1];
-      x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
-      x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
-      uint4 hi, lo;
-      split8(x, hi, lo);
-      const uint32_t o = tile_off(TC_M, r, 8 * kq);
-      sts128(oa_hi + o, hi);
-      sts128(oa_lo + o, lo);
-    }
-    // B: item (kq, real row e); row 2j <- (re, im), row 2j+1 <- (im, -re)
-#pragma unroll
-    for (int p = 0; p < (TC_N * (O_KC / 4)) / O_THREADS; ++p) {
-      const int item = p * O_THREADS + t;
-      const int kq = item / TC_N, e = item - kq * TC_N;
-      float x[8];
-      const float4* src = reinterpret_cast<const float4*>(rb + (e >> 1) * O_PITCH + 4 * kq);
-      const float4 v0 = src[0], v1 = src[1];
-      const float y[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (e & 1) {
-          x[2 * q] = y[2 * q + 1];
-          x[2 * q + 1] = -y[2 * q];
-        } else {
-          x[2 * q] = y[2 * q];
-          x[2 * q + 1] = y[2 * q + 1];
-        }
+      for (int u = 0; u < 4; ++u) {
+        x[u] = (ra && k + 4 * u < kend) ? pa[k + 4 * u] : make_float2(0.f, 0.f);
+        x[4 + u] = (rb && k + 4 * u < kend) ? pb[k + 4 * u] : make_float2(0.f, 0.f);
       }
-      uint4 hi, lo;
-      split8(x, hi, lo);
-      const uint32_t o = tile_off(TC_N, e, 8 * kq);
-      sts128(ob_hi + o, hi);
-      sts128(ob_lo + o, lo);
-    }
-    fence_proxy_async();
-    __syncthreads();
-    if (t == 0) {
-      tc_fence_after();
-      constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
-      constexpr uint32_t a_lbo = TC_M * 16, b_lbo = TC_N * 16;
+    };
+    auto chunk = [&](int c, float2 (&x)[8]) {
+      const int st = c % O_NOP;
+      if (c >= O_NOP) {
+        ok = mbar_wait_bounded(empty + 8 * st, ((c / O_NOP) - 1) & 1);
+        if (!ok) return;
+      }
+      const uint32_t oa_hi = op0 + st * O_OP_STAGE, oa_lo = oa_hi + O_A_BYTES;
+      const uint32_t ob_hi = oa_hi + 2 * O_A_BYTES, ob_lo = ob_hi + O_B_BYTES;
 #pragma unroll
-      for (int s = 0; s < O_KR / 16; ++s) {
-        const uint32_t ao = 2 * s * a_lbo, bo = 2 * s * b_lbo;
+      for (int u = 0; u < 4; ++u) {
+        const int kr = 8 * u + 2 * l;        // real K index of the pair
+        float h0, l0, h1, l1;
+        split1(x[u].x, h0, l0);
+        split1(x[u].y, h1, l1);
+        uint32_t o = tile_off(TC_M, r, kr);
+        sts32(oa_hi + o, pack_bf16(h0, h1));
+        sts32(oa_lo + o, pack_bf16(l0, l1));
+        // B real row 2j <- (re, im), row 2j+1 <- (im, -re)
+        split1(x[4 + u].x, h0, l0);
+        split1(x[4 + u].y, h1, l1);
+        o = tile_off(TC_N, 2 * r, kr);
+        sts32(ob_hi + o, pack_bf16(h0, h1));
+        sts32(ob_lo + o, pack_bf16(l0, l1));
+        o = tile_off(TC_N, 2 * r + 1, kr);
+        sts32(ob_hi + o, pack_bf16(h1, -h0));
+        sts32(ob_lo + o, pack_bf16(l1, -l0));
+      }
+      fence_proxy_async();
+      mbar_arrive(full + 8 * st);
+      if (c + 2 < nk) load(c + 2, x);
+    };
+    if (nk > 0) load(0, xa);
+    if (nk > 1) load(1, xb);
+    for (int c = 0; c < nk && ok; c += 2) {
+      chunk(c, xa);
+      if (ok && c + 1 < nk) chunk(c + 1, xb);
+    }
+  } else if (lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+    constexpr uint32_t a_lbo = TC_M * 16, b_lbo = TC_N * 16;
+    for (int c = 0; c < nk; ++c) {
+      const int st = c % O_NOP;
+      ok = mbar_wait_bounded(full + 8 * st, (c / O_NOP) & 1);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t oa_hi = op0 + st * O_OP_STAGE, oa_lo = oa_hi + O_A_BYTES;
+      const uint32_t ob_hi = oa_hi + 2 * O_A_BYTES, ob_lo = ob_hi + O_B_BYTES;
+#pragma unroll
+      for (int q = 0; q < O_KR / 16; ++q) {
+        const uint32_t ao = 2 * q * a_lbo, bo = 2 * q * b_lbo;
         const uint64_t ahi = smem_desc(oa_hi + ao, a_lbo, 128), alo = smem_desc(oa_lo + ao, a_lbo, 128);
         const uint64_t bhi = smem_desc(ob_hi + bo, b_lbo, 128), blo = smem_desc(ob_lo + bo, b_lbo, 128);
-        mma_bf16(tmem, ahi, bhi, idesc, (it == 0 && s == 0) ? 0u : 1u);
+        mma_bf16(tmem, ahi, bhi, idesc, (c == 0 && q == 0) ? 0u : 1u);
         mma_bf16(tmem, ahi, blo, idesc, 1u);
         mma_bf16(tmem, alo, bhi, idesc, 1u);
       }
-      mma_commit(bar0 + 8 * ost);
+      mma_commit(empty + 8 * st);
     }
+    mma_commit(done);                        // also when nothing was issued
   }
-  cp_async_wait<0>();
-  __syncthreads();
-  if (ok && nk > 0)
-    ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ((nk - 1) % O_NOP), ((nk - 1) / O_NOP) & 1)) != 0;
+  ok = mbar_wait_bounded(done, 0) && ok;
+  ok = __syncthreads_and(ok) != 0;
   if (!ok && t == 0) atomicExch(err, 1);
   tc_fence_after();
-  // epilogue: warp w reads TMEM lanes 32*(w%4).., columns [128*(w/4), +128)
-  const int w = t >> 5, lane = t & 31;
-  const int row = 32 * (w & 3) + lane;
-  const int i = i0 + row;
-  if (ok) {
+  // epilogue (split warps): warp w reads TMEM lanes 32 (w % 4).., columns [64 (w / 4), +64)
+  if (ok && w < O_SPLIT_WARPS) {
+    const int row = 32 * (w & 3) + lane;
+    const int i = i0 + row;
     for (int c0 = 64 * (w >> 2); c0 < 64 * (w >> 2) + 64; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + c0, v);
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(O_THREADS, 1)
           const int j = j0 + c0 / 2 + q;
           if (j < n)
             part[((size_t)blockIdx.z * m + i) * n + j] =
-                nk > 0 ? make_double2((double)v[2 * q], (double)v[2 * q + 1]) : make_double2(0.0, 0.0);
+                nk > 0 ? make_float2(v[2 * q], v[2 * q + 1]) : make_float2(0.f, 0.f);
         }
       }
     }
@@ -343,15 +343,15 @@ __global__ void __launch_bounds__(O_THREADS, 1)
 }
 
 // ------------------------------------------------------------------------------------------------
-// Rotation: Y[i][k] = sum_j M[i][j] X[j][k].  CTA tile: 128 grid columns k x 128 outputs i.
-// Mb holds M pre-split into the B-tile images, per (i-tile, j-chunk of 16 states): the
-// three bf16 terms one after the other.  Per stage (two K16 steps) the MMAs are
-// X_hi M_1 + X_hi M_2 + X_lo M_1 + X_hi M_3.
+// Rotation: Y[i][k] = sum_j M[i][j] X[j][k].  CTA: 256 grid columns k (two MMA tiles of 128)
+// x 128 outputs i.  Mb holds M pre-split into the B-tile images, per (i-tile, j-chunk of 16
+// states): the three bf16 terms one after the other.  Per chunk and tile (two K16 steps) the
+// MMAs are X_hi M_1 + X_hi M_2 + X_lo M_1 + X_hi M_3.
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ void issue_rotation_stage(uint32_t s, uint32_t tmem_d, bool first) {
+__device__ __forceinline__ void issue_rotation_tile(uint32_t a, uint32_t b, uint32_t tmem_d, bool first) {
   constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
   constexpr uint32_t a_lbo = TC_M * 16, b_lbo = TC_N * 16;
-  const uint32_t a_hi = s, a_lo = s + RA_BYTES, b1 = s + 2 * RA_BYTES, b2 = b1 + RB_BYTES, b3 = b2 + RB_BYTES;
+  const uint32_t a_hi = a, a_lo = a + RA_BYTES, b1 = b, b2 = b1 + RB_BYTES, b3 = b2 + RB_BYTES;
 #pragma unroll
   for (int k = 0; k < R_KR / 16; ++k) {
     const uint32_t ao = 2 * k * a_lbo, bo = 2 * k * b_lbo;
@@ -363,55 +363,67 @@ __device__ __forceinline__ void issue_rotation_stage(uint32_t s, uint32_t tmem_d
   }
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// Warp roles: warps 0-15 split X (one grid row, 8 states each) into the A stages, warp 16
+// issues the MMAs, warp 17 copies each chunk's M images with one bulk copy.  Stage hand-offs
+// are mbarriers: a_full (512 arrivals), b_full (transaction bytes), and a_empty / b_empty,
+// on which tcgen05.commit arrives when the MMAs that read the stage have completed.
+__global__ void __launch_bounds__(R_THREADS, 1)
     k_tc_rotate(const uint4* __restrict__ Mb, int njc, const float2* __restrict__ X, const float2* __restrict__ X2,
                 int nin1, int ldx, float2* __restrict__ Y, int ldy, int m, int nin, int K, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   const uint32_t base = smem_u32(tsm);
-  uint32_t bar0;
-  const uint32_t tmem = tc_setup(tsm, bar0, R_NSTAGE * R_STAGE_BYTES, R_NSTAGE);
-  const int k0 = blockIdx.x * TC_M;
+  const uint32_t abase = base, bbase = base + R_NA * R_A_STAGE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + R_RING);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(tsm + R_RING + 128);
+  const uint32_t bar_base = smem_u32(bars);
+  const uint32_t a_full = bar_base, a_empty = bar_base + 8 * R_NA, b_full = bar_base + 16 * R_NA,
+                 b_empty = b_full + 8 * R_NB, done = b_empty + 8 * R_NB;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  if (t == 0) {
+    for (int i = 0; i < R_NA; ++i) {
+      mbar_init(a_full + 8 * i, 32 * R_SPLIT_WARPS);
+      mbar_init(a_empty + 8 * i, 1);
+    }
+    for (int i = 0; i < R_NB; ++i) {
+      mbar_init(b_full + 8 * i, 1);
+      mbar_init(b_empty + 8 * i, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (w == 0) tmem_alloc(smem_u32(slot), R_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const int k0 = blockIdx.x * (R_TILES * TC_M);
   const int it_i = blockIdx.y;
   const int i0 = it_i * (TC_N / 2);
-  const int t = threadIdx.x;
-  const int r = t & (TC_M - 1);          // grid coefficient row of the A tile
-  const int jb = t >> 7;                 // which 8 of the 16 states of a chunk
-  const int kk = k0 + r;
-  // pipeline: the three M images of chunk c+1 are copied with cp.async into their stage and
-  // the X rows of chunk c+1 are loaded into registers while the MMAs of chunk c run
-  float2 xr[8];
-  auto load_x = [&](int c) {
-    const int jc0 = c * R_KC;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int j = jc0 + 8 * jb + q;
-      xr[q] = (j < nin && kk < K) ? (j < nin1 ? X[(size_t)j * ldx + kk] : X2[(size_t)(j - nin1) * ldx + kk])
-                                  : make_float2(0.f, 0.f);
-    }
-  };
-  auto issue_b = [&](int c) {
-    const uint32_t sb = base + (c % R_NSTAGE) * R_STAGE_BYTES + 2 * RA_BYTES;
-    const uint4* src = Mb + ((size_t)it_i * njc + c) * (3 * RB_BYTES / 16);
-    for (int v = t; v < 3 * RB_BYTES / 16; v += TC_THREADS) cp_async16(sb + 16 * v, src + v);
-  };
-  if (njc > 0) {
-    issue_b(0);
-    load_x(0);
-  }
-  cp_async_commit();
   bool ok = true;
-  for (int it = 0; it < njc; ++it) {
-    const int st = it % R_NSTAGE;
-    // chunk it+1's stage was last read by the MMAs of chunk it-2
-    if (it + 1 < njc && it >= 2) {
-      ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ((it + 1) % R_NSTAGE), ((it - 2) / R_NSTAGE) & 1)) != 0;
-      if (!ok) break;
-    }
-    if (it + 1 < njc) issue_b(it + 1);
-    cp_async_commit();
-    const uint32_t sb = base + st * R_STAGE_BYTES;
-    // A: row r = grid coefficient kk; real K: [0,16) re of states jc0.., [16,32) im
-    {
+
+  if (w < R_SPLIT_WARPS) {
+    const int r = t & (R_TILES * TC_M - 1);  // grid coefficient row of the CTA block
+    const int tile = r >> 7, tr = r & (TC_M - 1);
+    const int jb = t >> 8;                   // which 8 of the 16 states of a chunk
+    const int kk = k0 + r;
+    // X rows are prefetched into registers two chunks ahead (two register sets, alternating)
+    float2 xa[8], xb[8];
+    auto load_x = [&](int c, float2 (&xr)[8]) {
+      const int jc0 = c * R_KC;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = jc0 + 8 * jb + q;
+        xr[q] = (j < nin && kk < K) ? (j < nin1 ? X[(size_t)j * ldx + kk] : X2[(size_t)(j - nin1) * ldx + kk])
+                                    : make_float2(0.f, 0.f);
+      }
+    };
+    auto chunk = [&](int c, float2 (&xr)[8]) {
+      const int st = c % R_NA;
+      if (c >= R_NA) {
+        ok = mbar_wait_bounded(a_empty + 8 * st, ((c / R_NA) - 1) & 1);
+        if (!ok) return;
+      }
+      const uint32_t sa = abase + st * R_A_STAGE + tile * (2 * RA_BYTES);
       float re[8], im[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -420,49 +432,72 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       uint4 hi, lo;
       split8(re, hi, lo);
-      uint32_t o = tile_off(TC_M, r, 8 * jb);
-      sts128(sb + o, hi);
-      sts128(sb + RA_BYTES + o, lo);
+      uint32_t o = tile_off(TC_M, tr, 8 * jb);
+      sts128(sa + o, hi);
+      sts128(sa + RA_BYTES + o, lo);
       split8(im, hi, lo);
-      o = tile_off(TC_M, r, 16 + 8 * jb);
-      sts128(sb + o, hi);
-      sts128(sb + RA_BYTES + o, lo);
+      o = tile_off(TC_M, tr, 16 + 8 * jb);
+      sts128(sa + o, hi);
+      sts128(sa + RA_BYTES + o, lo);
+      fence_proxy_async();
+      mbar_arrive(a_full + 8 * st);
+      if (c + 2 < njc) load_x(c + 2, xr);
+    };
+    if (njc > 0) load_x(0, xa);
+    if (njc > 1) load_x(1, xb);
+    for (int c = 0; c < njc && ok; c += 2) {
+      chunk(c, xa);
+      if (ok && c + 1 < njc) chunk(c + 1, xb);
     }
-    if (it + 1 < njc) load_x(it + 1);
-    cp_async_wait<1>();              // chunk it's images have landed (this thread's copies)
-    fence_proxy_async();
-    __syncthreads();                 // ... and every thread's, with the A tile stored
-    if (t == 0) {
-      tc_fence_after();
-      issue_rotation_stage(sb, tmem, it == 0);
-      mma_commit(bar0 + 8 * st);
+  } else if (w == R_SPLIT_WARPS) {
+    if (lane == 0) {
+      for (int c = 0; c < njc; ++c) {
+        ok = mbar_wait_bounded(a_full + 8 * (c % R_NA), (c / R_NA) & 1) &&
+             mbar_wait_bounded(b_full + 8 * (c % R_NB), (c / R_NB) & 1);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t a = abase + (c % R_NA) * R_A_STAGE, b = bbase + (c % R_NB) * R_B_STAGE;
+#pragma unroll
+        for (int q = 0; q < R_TILES; ++q) issue_rotation_tile(a + q * (2 * RA_BYTES), b, tmem + 256 * q, c == 0);
+        mma_commit(a_empty + 8 * (c % R_NA));
+        mma_commit(b_empty + 8 * (c % R_NB));
+      }
+      mma_commit(done);                      // also when nothing was issued
+    }
+  } else if (lane == 0) {
+    for (int c = 0; c < njc; ++c) {
+      const int st = c % R_NB;
+      if (c >= R_NB) {
+        ok = mbar_wait_bounded(b_empty + 8 * st, ((c / R_NB) - 1) & 1);
+        if (!ok) break;
+      }
+      mbar_expect_tx(b_full + 8 * st, R_B_STAGE);
+      bulk_g2s(bbase + st * R_B_STAGE, Mb + ((size_t)it_i * njc + c) * (R_B_STAGE / 16), R_B_STAGE, b_full + 8 * st);
     }
   }
-  cp_async_wait<0>();
-  __syncthreads();
-  if (ok && njc > 0)
-    ok = __syncthreads_and(mbar_wait_bounded(bar0 + 8 * ((njc - 1) % R_NSTAGE), ((njc - 1) / R_NSTAGE) & 1)) != 0;
+  ok = mbar_wait_bounded(done, 0) && ok;
+  ok = __syncthreads_and(ok) != 0;
   if (!ok && t == 0) atomicExch(err, 1);
   tc_fence_after();
-  const int w = t >> 5, lane = t & 31;
-  const int row = 32 * (w & 3) + lane;
-  const int k = k0 + row;
-  if (ok) {
-    for (int c0 = 128 * (w >> 2); c0 < 128 * (w >> 2) + 128; c0 += 16) {
+  // epilogue (split warps): warp w reads TMEM lanes 32 (w % 4).., columns [128 (w / 4), +128)
+  if (ok && w < R_SPLIT_WARPS) {
+    const int q4 = w >> 2;                   // 0..3: tile q4 / 2, half q4 % 2
+    const int k = k0 + (q4 >> 1) * TC_M + 32 * (w & 3) + lane;
+    for (int c0 = 128 * q4; c0 < 128 * q4 + 128; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + c0, v);
       if (k < K) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const int i = i0 + c0 / 2 + q;
-          if (i < m) Y[(size_t)i * ldy + k] = make_float2(v[2 * q], v[2 * q + 1]);
+          const int i = i0 + (c0 & 255) / 2 + q;
+          if (i < m) Y[(size_t)i * ldy + k] = njc > 0 ? make_float2(v[2 * q], v[2 * q + 1]) : make_float2(0.f, 0.f);
         }
       }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (w == 0) tmem_dealloc(tmem, TMEM_COLS);
+  if (w == 0) tmem_dealloc(tmem, R_TMEM_COLS);
 }
 
 // Mb images: B row 2i (output Re Y_i) = [Re M_ij | -Im M_ij], row 2i+1 (Im Y_i) = [Im M_ij | Re M_ij]
@@ -512,17 +547,45 @@ __global__ void k_tc_prep_rotation(const CM* __restrict__ M, int m, int nin, int
   }
 }
 
-__global__ void k_reduce_parts_tc(const double2* __restrict__ part, int nks, size_t mn, double2* __restrict__ out,
-                                  float2* __restrict__ out32) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < mn; e += (size_t)gridDim.x * blockDim.x) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int k = 0; k < nks; ++k) {
-      const double2 p = part[(size_t)k * mn + e];
-      s.x += p.x;
-      s.y += p.y;
+// s + x = hi + err exactly (Knuth's TwoSum); the error terms are summed separately.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  c += (s - (t - bp)) + (x - bp);
+  s = t;
+}
+
+// out[e] = sum_k part[k][e]: FP32 partials (exact copies of the TMEM accumulators) summed
+// with compensated FP32 arithmetic, so the sum carries about twice FP32's precision without
+// the FP64 pipe.  A CTA covers 32 elements; warp w takes partials w, w + 8, ...; the eight
+// (sum, error) pairs are combined in a fixed order, so the result is deterministic.
+__global__ void __launch_bounds__(256) k_reduce_parts_tc(const float2* __restrict__ part, int nks, size_t mn,
+                                                         double2* __restrict__ out, float2* __restrict__ out32) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t e = (size_t)blockIdx.x * 32 + lane;
+  __shared__ float4 red[8][32];
+  float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+  if (e < mn)
+    for (int k = w; k < nks; k += 8) {
+      const float2 p = part[(size_t)k * mn + e];
+      two_sum_acc(sx, cx, p.x);
+      two_sum_acc(sy, cy, p.y);
     }
-    out[e] = s;
-    if (out32) out32[e] = make_float2((float)s.x, (float)s.y);
+  red[w][lane] = make_float4(sx, cx, sy, cy);
+  __syncthreads();
+  if (w == 0 && e < mn) {
+    float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 r = red[q][lane];
+      two_sum_acc(hx, lx, r.x);
+      lx += r.y;
+      two_sum_acc(hy, ly, r.z);
+      ly += r.w;
+    }
+    const double x = (double)hx + (double)lx, y = (double)hy + (double)ly;
+    out[e] = make_double2(x, y);
+    if (out32) out32[e] = make_float2((float)x, (float)y);
   }
 }
 
@@ -558,10 +621,11 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
   kchunk = (kchunk + O_KC - 1) / O_KC * O_KC;
   ks = (K + kchunk - 1) / kchunk;
   dim3 g(tn, tm, ks);
-  k_tc_overlap<<<g, O_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, part, err);
+  float2* p32 = reinterpret_cast<float2*>(part);                      // FP32 partials
+  k_tc_overlap<<<g, O_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err);
   KS_CHECK_LAUNCH();
   const size_t mn = (size_t)m * n;
-  k_reduce_parts_tc<<<(unsigned)std::min<size_t>((mn + 255) / 256, 1024), 256, 0, s>>>(part, ks, mn, out, out32);
+  k_reduce_parts_tc<<<(unsigned)((mn + 31) / 32), 256, 0, s>>>(p32, ks, mn, out, out32);
   KS_CHECK_LAUNCH();
 }
 
@@ -584,8 +648,8 @@ void tc_rotate_prepared(const void* work, int nin, const float2* X, const float2
   if (!X2) nin1 = nin;
   set_attrs();
   const int nit = (m + TC_N / 2 - 1) / (TC_N / 2), njc = (nin + R_KC - 1) / R_KC;
-  dim3 g((K + TC_M - 1) / TC_M, nit);
-  k_tc_rotate<<<g, TC_THREADS, R_SMEM, s>>>(static_cast<const uint4*>(work), njc, X, X2, nin1, ldx, Y, ldy, m, nin, K,
+  dim3 g((K + R_TILES * TC_M - 1) / (R_TILES * TC_M), nit);
+  k_tc_rotate<<<g, R_THREADS, R_SMEM, s>>>(static_cast<const uint4*>(work), njc, X, X2, nin1, ldx, Y, ldy, m, nin, K,
                                             err);
   KS_CHECK_LAUNCH();
 }
