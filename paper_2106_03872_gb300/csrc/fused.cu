@@ -96,15 +96,19 @@ __global__ void __launch_bounds__(FCfg<N>::ZT) k_zinv(const float2* __restrict__
   }
   __syncthreads();
   cfft_lines<N, ZT, CT, true, +1>(s, nl, ld, 1, tw);
+  // transpose out: element e = z * CT + l (a compile-time split; columns l >= nl are absent
+  // in the last block)
   float2* out = colbuf + (size_t)b * N * ncols + c0;
-  for (int e = threadIdx.x; e < N * nl; e += ZT) {
-    const int z = e / nl, l = e - z * nl;
-    out[(size_t)z * ncols + l] = s[l * ld + z];
+#pragma unroll
+  for (int q = 0; q < (N * CT + ZT - 1) / ZT; ++q) {
+    const int e = threadIdx.x + q * ZT;
+    const int z = e / CT, l = e % CT;
+    if (z < N && l < nl) out[(size_t)z * ncols + l] = s[l * ld + z];
   }
 }
 
 template <int N>
-__global__ void __launch_bounds__(FCfg<N>::ZT) k_zfwd(const float2* __restrict__ colbuf, const float2* __restrict__ psi,
+__global__ void __launch_bounds__(FCfg<N>::ZT, 3) k_zfwd(const float2* __restrict__ colbuf, const float2* __restrict__ psi,
                                                       float2* __restrict__ hpsi, int nG, const int* __restrict__ col_off,
                                                       const int* __restrict__ col_half, const float* __restrict__ g2half,
                                                       int ncols, float scale, const float2* __restrict__ twg) {
@@ -120,26 +124,42 @@ __global__ void __launch_bounds__(FCfg<N>::ZT) k_zfwd(const float2* __restrict__
     coff[t] = col_off[c0 + t];
     chalf[t] = col_half[c0 + t];
   }
-  const float2* in = colbuf + (size_t)b * N * ncols + c0;
-  for (int e = threadIdx.x; e < N * nl; e += ZT) {
-    const int z = e / nl, l = e - z * nl;
-    s[l * ld + z] = in[(size_t)z * ncols + l];
-  }
   __syncthreads();
-  cfft_lines<N, ZT, CT, true, -1>(s, nl, ld, 1, tw);
-  // a group of TPC threads per column gathers the column's coefficients
-  constexpr int TPC = ZT / CT;
+  // the coefficients this thread finally writes: psi and |G|^2/2 are loaded now, so that their
+  // latency hides behind the column loads and the FFT (a group of TPC threads per column)
+  constexpr int TPC = ZT / CT, GS = (N + TPC - 1) / TPC, LOADS = (N * CT + ZT - 1) / ZT;
   const size_t off = (size_t)b * nG;
   const int l = threadIdx.x / TPC, sub = threadIdx.x - (threadIdx.x / TPC) * TPC;
-  if (l < nl) {
-    const int h = chalf[l], g0 = coff[l];
-    for (int k = sub; k <= 2 * h; k += TPC) {
+  const int h = l < nl ? chalf[l] : -1, g0 = l < nl ? coff[l] : 0;
+  float2 pv[GS];
+  float kv[GS];
+#pragma unroll
+  for (int q = 0; q < GS; ++q) {
+    const int k = sub + q * TPC;
+    if (k <= 2 * h) {
+      pv[q] = psi[off + g0 + k];
+      kv[q] = g2half[g0 + k];
+    }
+  }
+  // the column block, transposed into the line layout by 8-byte asynchronous copies
+  const float2* in = colbuf + (size_t)b * N * ncols + c0;
+#pragma unroll
+  for (int q = 0; q < LOADS; ++q) {
+    const int e = threadIdx.x + q * ZT;
+    const int z = e / CT, lc = e % CT;
+    if (z < N && lc < nl) cp_async8(&s[lc * ld + z], &in[(size_t)z * ncols + lc]);
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  cfft_lines<N, ZT, CT, true, -1>(s, nl, ld, 1, tw);
+#pragma unroll
+  for (int q = 0; q < GS; ++q) {
+    const int k = sub + q * TPC;
+    if (k <= 2 * h) {
       const int z = k <= h ? k : k + N - 2 * h - 1;
       const float2 u = s[l * ld + z];
-      const int g = g0 + k;
-      const float2 p = psi[off + g];
-      const float kf = g2half[g];
-      hpsi[off + g] = make_float2(u.x * scale + kf * p.x, u.y * scale + kf * p.y);
+      hpsi[off + g0 + k] = make_float2(u.x * scale + kv[q] * pv[q].x, u.y * scale + kv[q] * pv[q].y);
     }
   }
 }
