@@ -21,7 +21,7 @@ What it computes, each function citing the paper passage it follows:
 * the ETRS propagator with the 4th-order Taylor exponential and shared powers
   (Eqs. 6-8, Sec. "Real-time propagation").
 
-Conventions where the paper is silent (each one a reading, listed in the design doc):
+Conventions where the paper is silent (each one a reading of it):
 cubic cell of side L, grid N^3, r_j = h j, h = L/N; G = (2 pi / L) m with
 m = j for j < N/2 else j - N; S = {G : |G|^2/2 <= E_cut} in grid-index order
 (j_x, j_y, j_z) row-major, z fastest; psi(r_j) = Omega^{-1/2} sum_{G in S} c_G e^{i G.r_j};
