@@ -209,6 +209,7 @@ constexpr int O_RING = O_NOP * O_OP_STAGE;                   // 192 KB
 constexpr int O_SMEM = O_RING + 1024;
 
 
+template <bool SAME>
 __global__ void __launch_bounds__(O_THREADS, 1)
     k_tc_overlap(const float2* __restrict__ A, int lda, const float2* __restrict__ B, int ldb, int m, int n, int K,
                  int kchunk, float2* __restrict__ part, int* __restrict__ err) {
@@ -252,7 +253,8 @@ __global__ void __launch_bounds__(O_THREADS, 1)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         x[u] = (ra && k + 4 * u < kend) ? pa[k + 4 * u] : make_float2(0.f, 0.f);
-        x[4 + u] = (rb && k + 4 * u < kend) ? pb[k + 4 * u] : make_float2(0.f, 0.f);
+        // SAME: one diagonal tile of A^H A, so B's rows are A's and are loaded once
+        x[4 + u] = SAME ? x[u] : ((rb && k + 4 * u < kend) ? pb[k + 4 * u] : make_float2(0.f, 0.f));
       }
     };
     auto chunk = [&](int c, float2 (&x)[8]) {
@@ -592,7 +594,8 @@ __global__ void __launch_bounds__(256) k_reduce_parts_tc(const float2* __restric
 bool g_attr_done = false;
 void set_attrs() {
   if (g_attr_done) return;
-  KS_CUDA(cudaFuncSetAttribute(k_tc_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
+  KS_CUDA(cudaFuncSetAttribute(k_tc_overlap<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
+  KS_CUDA(cudaFuncSetAttribute(k_tc_overlap<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
   KS_CUDA(cudaFuncSetAttribute(k_tc_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, R_SMEM));
   g_attr_done = true;
 }
@@ -622,7 +625,11 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
   ks = (K + kchunk - 1) / kchunk;
   dim3 g(tn, tm, ks);
   float2* p32 = reinterpret_cast<float2*>(part);                      // FP32 partials
-  k_tc_overlap<<<g, O_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err);
+  // one output tile of A^H A: both operands are the same rows
+  if (A == B && lda == ldb && m == n && tm == 1 && tn == 1)
+    k_tc_overlap<true><<<g, O_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err);
+  else
+    k_tc_overlap<false><<<g, O_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err);
   KS_CHECK_LAUNCH();
   const size_t mn = (size_t)m * n;
   k_reduce_parts_tc<<<(unsigned)((mn + 31) / 32), 256, 0, s>>>(p32, ks, mn, out, out32);
