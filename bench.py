@@ -372,6 +372,22 @@ def main_gpu(args):
               "stages_ms_per_step": {k: v[0] / len(tt) for k, v in te.items() if v[0] > 0}}
         gt.close()
 
+    # ---- self-consistent field on the gs96 cell: 4 SCF iterations per call, each with
+    # V[n_in], 2 block iterations, CholQR, the output density and linear mixing
+    scf = None
+    if not args.no_scf:
+        gs = ks.Grid(cell, prec="bf16x3")
+        gs.set_states(c0)
+        SCF_IT, SCF_EIG = 4, 2
+        ts, _, se = timed_steps(gs, 2, 1, lambda: gs.scf(SCF_IT, eig_iters=SCF_EIG, mix=0.3, stream=stream),
+                                profile=True)
+        sms = statistics.mean(ts)
+        scf = {"workload": "gs96, %d SCF iterations per call, %d block iterations each, linear mixing 0.3 "
+                           "(the call's initial CholQR and density included)" % (SCF_IT, SCF_EIG),
+               "ms_per_scf_iteration": sms / SCF_IT, "ms_per_call": sms,
+               "stages_ms_per_call": {k: v[0] / len(ts) for k, v in se.items() if v[0] > 0}}
+        gs.close()
+
     serve = None if args.no_serve else serve_bench(ks, inputs, args.serve_requests)
 
     if rank != 0:
@@ -388,7 +404,7 @@ def main_gpu(args):
         "roofline": rl, "side_stream_roofline": rl_side,
         "cpu_baseline": cpu_baseline_obj(cpu) if cpu else None, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk.summary(), "hpsi_only": hpsi_only, "fp64_gpu": fp64, "td": td,
-        "serve": serve,
+        "scf": scf, "serve": serve,
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in entries.items() if v[0] > 0},
     }
     print(json.dumps(line), flush=True)
@@ -472,6 +488,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-td", action="store_true")
+    ap.add_argument("--no-scf", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
     args = ap.parse_args()

@@ -108,8 +108,9 @@ ks_status ks_states_device(ks_grid g, void** psi_dev);
 
 /* H psi for nstates <= desc->nstates states (Eq. 2): hpsi = P_S (T + V + V_NL) psi.
  * psi_dev, hpsi_dev: device [nstates][nG] complex of the handle's precision; must not
- * overlap.  V is the handle's current potential (V_loc, or V_loc + v_H + v_x after a
- * real-time step with hartree_xc).  Asynchronous on stream. */
+ * overlap.  V is the handle's current potential: V_loc at creation; V_loc + v_H + v_x of
+ * the last density used by ks_scf or by a real-time step with hartree_xc (a real-time step
+ * without it resets V to V_loc).  Asynchronous on stream. */
 ks_status ks_apply_h(ks_grid g, const void* psi_dev, void* hpsi_dev, int nstates, void* stream);
 
 /* Same operation end to end from host memory: psi_host / hpsi_host are
@@ -124,7 +125,8 @@ ks_status ks_density(ks_grid g, void* n_dev, void* stream);
 
 /* CholQR of the resident states (Sec. "Ground-state solution", orthogonalisation):
  * S = Psi^H Psi, S = L L^H, Psi <- Psi L^{-H}.  KS_FP64 factors S in FP64; the mixed
- * paths (nstates <= 160) take two FP32 Cholesky passes refined by FP64 triangular products.
+ * paths (nstates <= 160) take one FP32 Cholesky factor and inverse, refined to first order
+ * with the FP64 triangular product L1^{-1} S L1^{-H}.
  * S_host_opt (may be NULL) receives S, [nstates][nstates] complex128 row-major,
  * S_ij = sum_G conj(c_iG) c_jG.  KS_ERR_NOT_POSDEF if S is not positive definite
  * (states unchanged then).  Synchronous (reads a status word). */
@@ -141,6 +143,21 @@ ks_status ks_rayleigh_ritz(ks_grid g, double* eig_host, void* stream);
  * alpha = 1/(ecut + max V_loc - min V_loc + proj_D).  eig_host [nstates] receives the
  * Ritz values of the last iteration.  Synchronous. */
 ks_status ks_block_iteration(ks_grid g, int niter, double* eig_host, void* stream);
+
+/* Self-consistent field (Sec. "Ground-state solution"), static linear mixing.  The
+ * resident states are orthonormalised (CholQR) and their density is the first input
+ * density n_in.  Each SCF iteration:
+ *   V = V_loc + v_H[n_in] + v_x[n_in];  eig_iters block iterations with this V;
+ *   CholQR;  n_out = density of the states;  r = dV sum_j |n_out - n_in|;
+ *   n_in <- n_in + mix (n_out - n_in).
+ * Stops after max_iter iterations or once r < tol.  eig_out [max_iter][nstates] (may be
+ * NULL) receives each iteration's Ritz values, resid_out [max_iter] (may be NULL) its r,
+ * iters_done (may be NULL) the number of iterations run.  Afterwards the states are
+ * orthonormal and V is the potential of the last iteration's n_in.  KS_ERR_ARG unless
+ * max_iter >= 0, eig_iters >= 1, 0 < mix <= 1 and tol >= 0; KS_ERR_DIVERGED if r is not
+ * finite.  Synchronous. */
+ks_status ks_scf(ks_grid g, int max_iter, int eig_iters, double mix, double tol, double* eig_out,
+                 double* resid_out, int* iters_done, void* stream);
 
 /* nsteps real-time steps of dt (Sec. "Real-time propagation").
  *   propagator 0: ETRS (Eq. 6) with H(t+dt) from the density of the full step (Eq. 7);

@@ -323,6 +323,33 @@ def hxc_potential(cell, n):
     return cell.vloc + vh + vx, parts
 
 
+def scf(cell, c, max_iter, eig_iters, mix, tol=0.0):
+    """Self-consistent field (Sec. "Ground-state solution"): each iteration solves the
+    linear problem for the current input density with a few eigensolver iterations, forms
+    the output density and mixes it into the input (static linear mixing).
+
+    The initial input density is that of the orthonormalised initial states (the paper
+    starts from atomic densities of pseudopotential files, which this setting has none of).
+    Per iteration: V = V_loc + v_H[n_in] + v_x[n_in]; eig_iters block iterations; CholQR;
+    n_out = density; r = dV sum |n_out - n_in|; n_in <- n_in + mix (n_out - n_in); stop
+    once r < tol.  Returns (Ritz values per iteration, residuals, states, final n_in)."""
+    c, _ = cholqr(c)
+    n_in = density(cell, c)
+    eps_hist, res_hist = [], []
+    for _ in range(max_iter):
+        v, _ = hxc_potential(cell, n_in)
+        eps, c = block_iteration(cell, c, eig_iters, v)
+        c, _ = cholqr(c)
+        n_out = density(cell, c)
+        r = cell.dV * float(np.sum(np.abs(n_out - n_in)))
+        eps_hist.append(eps)
+        res_hist.append(r)
+        n_in = n_in + mix * (n_out - n_in)
+        if r < tol:
+            break
+    return np.array(eps_hist), np.array(res_hist), c, n_in
+
+
 def total_energy(cell, c, hc, parts=None):
     """E = sum_k f_k <psi_k|H|psi_k> - 1/2 int n v_H + E_x - int n v_x (Eq. 5, eigenvalues
     replaced by expectation values).  Without Hartree/exchange only the first term remains."""

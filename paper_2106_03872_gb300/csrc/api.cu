@@ -167,6 +167,16 @@ ks_status ks_td_step(ks_grid g, double dt, int nsteps, int propagator, int hartr
   });
 }
 
+ks_status ks_scf(ks_grid g, int max_iter, int eig_iters, double mix, double tol, double* eig_out,
+                 double* resid_out, int* iters_done, void* stream) {
+  return guarded([&] {
+    need(g != nullptr, "grid is NULL");
+    need(max_iter >= 0 && eig_iters >= 1 && mix > 0.0 && mix <= 1.0 && tol >= 0.0,
+         "scf: need max_iter >= 0, eig_iters >= 1, 0 < mix <= 1, tol >= 0");
+    g->eng->scf(max_iter, eig_iters, mix, tol, eig_out, resid_out, iters_done, as_stream(stream));
+  });
+}
+
 ks_status ks_profile(ks_grid g, int mode) {
   return guarded([&] {
     need(g != nullptr && mode >= 0 && mode <= 4, "grid is NULL or mode not in 0..4");

@@ -198,6 +198,8 @@ template <typename T> class Engine final : public EngineBase {
     dens_ = alloc<T>(N3);
     pwork_ = alloc<C>(N3);
     hxc_partials_ = alloc<double>(HXC_BLOCKS * 3);
+    nin_ = alloc<T>(N3);
+    resid_dev_ = alloc<double>(1);
     parts_ = alloc<double>(4);
     dots_ = alloc<double2>(ns_);
     norms_dev_ = alloc<double>(MAX_STEPS_CHUNK);
@@ -537,6 +539,43 @@ template <typename T> class Engine final : public EngineBase {
   }
 
   // ------------------------------------------------------------------------------------------
+  // Self-consistent field (Sec. Ground-state solution) with static linear mixing.
+  // ------------------------------------------------------------------------------------------
+  void scf(int max_iter, int eig_iters, double mix, double tol, double* eig_out, double* resid_out, int* iters_done,
+           cudaStream_t s) override {
+    if (max_iter < 0 || eig_iters < 1 || !(mix > 0.0 && mix <= 1.0) || !(tol >= 0.0))
+      fail(KS_ERR_ARG, "scf: max_iter=%d eig_iters=%d mix=%g tol=%g", max_iter, eig_iters, mix, tol);
+    const int N3 = g_.N * g_.N * g_.N;
+    std::vector<double> eig(ns_);
+    orthonormalize(nullptr, s);
+    density_of(psi_, ns_, nin_, s);
+    int it = 0;
+    for (; it < max_iter; ++it) {
+      update_potential(nin_, s);
+      hpsi_valid_ = false;
+      block_iteration(eig_iters, eig.data(), s);
+      orthonormalize(nullptr, s);
+      density_of(psi_, ns_, dens_, s);
+      double r = 0.0;
+      {
+        ProfScope p(prof, "density_mix", s);
+        density_mix<T>(dens_, nin_, N3, mix, hxc_partials_, HXC_BLOCKS, s);
+        sum_partials(hxc_partials_, HXC_BLOCKS, g_.dV, resid_dev_, s);
+      }
+      KS_CUDA(cudaMemcpyAsync(&r, resid_dev_, sizeof(double), cudaMemcpyDeviceToHost, s));
+      KS_CUDA(cudaStreamSynchronize(s));
+      if (eig_out) std::memcpy(eig_out + (size_t)it * ns_, eig.data(), ns_ * sizeof(double));
+      if (resid_out) resid_out[it] = r;
+      if (!std::isfinite(r)) fail(KS_ERR_DIVERGED, "scf iteration %d: density residual %g", it, r);
+      if (r < tol) {
+        ++it;
+        break;
+      }
+    }
+    if (iters_done) *iters_done = it;
+  }
+
+  // ------------------------------------------------------------------------------------------
   // Real-time steps: ETRS + Taylor 4 with shared powers (Eqs. 6-8), or plain Taylor 4.
   // ------------------------------------------------------------------------------------------
   void td_steps(double dt, int nsteps, int propagator, int hartree_xc, double* norm_out, double* energy_out,
@@ -741,6 +780,8 @@ template <typename T> class Engine final : public EngineBase {
   T* dens_ = nullptr;
   C* pwork_ = nullptr;
   double* hxc_partials_ = nullptr;
+  T* nin_ = nullptr;                // SCF input density
+  double* resid_dev_ = nullptr;     // SCF residual
   double* parts_ = nullptr;
   double2* dots_ = nullptr;
   double* norms_dev_ = nullptr;

@@ -233,6 +233,29 @@ __global__ void k_hxc_finish(const double* __restrict__ partials, int nblocks, d
   }
 }
 
+// Linear density mixing (Sec. Ground-state solution): nin <- nin + mix (nout - nin); the
+// block partials of sum |nout - nin| (before the update) give the self-consistency residual.
+template <typename T>
+__global__ void k_density_mix(const T* __restrict__ nout, T* __restrict__ nin, size_t N3, T mix,
+                              double* __restrict__ partials) {
+  double acc[1] = {0.0};
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
+    const T a = nin[j], b = nout[j];
+    acc[0] += fabs((double)b - (double)a);
+    nin[j] = a + mix * (b - a);
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partials, int nblocks, double scale, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partials[b];
+    *out = scale * s;
+  }
+}
+
 template <typename T>
 __global__ void k_state_dots(const cplx<T>* __restrict__ a, const cplx<T>* __restrict__ bb, int nG,
                              double2* __restrict__ dots) {
@@ -426,6 +449,17 @@ void hxc_finish(const double* partials, int nblocks, double dV, double* parts, c
 }
 
 template <typename T>
+void density_mix(const T* nout, T* nin, int N3, double mix, double* partials, int nblocks, cudaStream_t s) {
+  k_density_mix<T><<<nblocks, RED_THREADS, 0, s>>>(nout, nin, (size_t)N3, (T)mix, partials);
+  KS_CHECK_LAUNCH();
+}
+
+void sum_partials(const double* partials, int nblocks, double scale, double* out, cudaStream_t s) {
+  k_sum_partials<<<1, 32, 0, s>>>(partials, nblocks, scale, out);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
 void state_dots(const cplx<T>* a, const cplx<T>* b, int nG, int nb, double2* dots, cudaStream_t s) {
   k_state_dots<T><<<nb, RED_THREADS, 0, s>>>(a, b, nG, dots);
   KS_CHECK_LAUNCH();
@@ -478,6 +512,7 @@ void real_to_double(const T* in, double* out, size_t n, cudaStream_t s) {
   template void real_to_complex<T>(const T*, cplx<T>*, int, cudaStream_t);                                      \
   template void poisson_multiply<T>(cplx<T>*, int, double, T, cudaStream_t);                                    \
   template void hxc_combine<T>(const T*, const cplx<T>*, const T*, T*, double*, int, int, cudaStream_t);        \
+  template void density_mix<T>(const T*, T*, int, double, double*, int, cudaStream_t);                          \
   template void state_dots<T>(const cplx<T>*, const cplx<T>*, int, int, double2*, cudaStream_t);                \
   template void axpy2<T>(cplx<T>*, double2, cplx<T>*, double2, const cplx<T>*, const cplx<T>*, size_t, cudaStream_t);           \
   template void random_states<T>(cplx<T>*, size_t, uint64_t, cudaStream_t);                                     \

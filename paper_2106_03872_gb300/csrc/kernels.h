@@ -53,6 +53,11 @@ template <typename T> void hxc_combine(const T* n, const cplx<T>* work, const T*
                                        int N3, int nblocks, cudaStream_t s);
 // parts[0..2] = dV * (0.5 sum n vH, sum n eps_x, sum n v_x) from the partials
 void hxc_finish(const double* partials, int nblocks, double dV, double* parts, cudaStream_t s);
+// nin <- nin + mix (nout - nin) over N3 points; partials[b] (nblocks) = sum of |nout - nin| before
+// the update in block b.  sum_partials: *out = scale * sum_b partials[b] (fixed order).
+template <typename T> void density_mix(const T* nout, T* nin, int N3, double mix, double* partials, int nblocks,
+                                       cudaStream_t s);
+void sum_partials(const double* partials, int nblocks, double scale, double* out, cudaStream_t s);
 constexpr int HXC_BLOCKS = 296;
 
 // dots[b] = sum_g conj(a[b][g]) b[b][g] (FP64 accumulation, fixed order)

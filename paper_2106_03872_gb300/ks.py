@@ -23,7 +23,7 @@ PRECISIONS = {"fp64": KS_FP64, "bf16x3": KS_MIXED_BF16X3, "tf32": KS_MIXED_TF32}
 # Every symbol declared in include/ks.h.
 EXPORTS = ["ks_count_gvectors", "ks_grid_create", "ks_grid_destroy", "ks_grid_gvectors", "ks_grid_device_bytes",
            "ks_get_vloc", "ks_set_states", "ks_get_states", "ks_states_device", "ks_apply_h", "ks_apply_h_host",
-           "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_td_step",
+           "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_scf", "ks_td_step",
            "ks_serve_create", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info",
            "ks_profile", "ks_profile_read", "ks_profile_span", "ks_kernel_launches", "ks_overlap_noalloc", "ks_last_error"]
 
@@ -72,6 +72,7 @@ def load():
         "ks_orthonormalize": [P, dp, P],
         "ks_rayleigh_ritz": [P, dp, P],
         "ks_block_iteration": [P, ct.c_int, dp, P],
+        "ks_scf": [P, ct.c_int, ct.c_int, ct.c_double, ct.c_double, dp, dp, ip, P],
         "ks_td_step": [P, ct.c_double, ct.c_int, ct.c_int, ct.c_int, dp, dp, P],
         "ks_serve_create": [ct.c_size_t, ct.POINTER(P)],
         "ks_serve_destroy": [P],
@@ -238,6 +239,16 @@ class Grid:
         e = np.zeros(self.nstates)
         check(load().ks_block_iteration(self.h, int(niter), _dptr(e), _stream_ptr(stream)))
         return e
+
+    def scf(self, max_iter, eig_iters=2, mix=0.3, tol=0.0, stream=None):
+        """Self-consistent field with linear mixing: returns (Ritz values [iters][nstates],
+        density residuals [iters]) of the iterations run."""
+        eig = np.zeros((max(max_iter, 1), self.nstates))
+        res = np.zeros(max(max_iter, 1))
+        done = ct.c_int(0)
+        check(load().ks_scf(self.h, int(max_iter), int(eig_iters), float(mix), float(tol), _dptr(eig), _dptr(res),
+                            ct.byref(done), _stream_ptr(stream)))
+        return eig[:done.value], res[:done.value]
 
     def profile(self, mode):
         check(load().ks_profile(self.h, int(mode)))

@@ -469,3 +469,65 @@ def test_block_iteration_mixed_beyond_128_states(ks):
     # not orthonormal (the SD step follows the rotation), but Hermitian positive definite
     assert np.all(np.linalg.eigvalsh(0.5 * (s + s.conj().T)) > 0)
     g.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# Self-consistent field (Sec. "Ground-state solution"), linear mixing
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_scf_parity(ks, prec):
+    cell = inputs.small_cell(10.0, 24, 4, 8, 51, depth=-3.0)
+    ref = ko.Cell(cell)
+    c = inputs.random_coeffs(51, 8, ref.nG)
+    eps_ref, res_ref, c_ref, _ = ko.scf(ref, c, 4, 2, 0.4)
+    g = ks.Grid(cell, prec=prec)
+    g.set_states(c)
+    eps, res = g.scf(4, eig_iters=2, mix=0.4)
+    assert eps.shape == eps_ref.shape and res.shape == res_ref.shape
+    if prec == "fp64":
+        assert np.max(np.abs(eps - eps_ref)) <= 1e-10
+        assert np.max(np.abs(res - res_ref)) <= 1e-10 * np.max(res_ref)
+        assert rel(g.get_states(), c_ref) <= 1e-9
+    else:
+        assert np.max(np.abs(eps - eps_ref)) <= 1e-4 * max(1.0, np.max(np.abs(eps_ref)))
+        assert np.max(np.abs(res - res_ref)) <= 1e-3 * np.max(res_ref)
+    # the states are orthonormal afterwards
+    q = g.get_states()
+    assert np.max(np.abs(ko.gram(q) - np.eye(8))) <= (1e-12 if prec == "fp64" else 1e-5)
+    g.close()
+
+
+def test_scf_free_electron_fixed_point(ks):
+    """Closed shells of free electrons: uniform density, so the SCF sits at its fixed point
+    with Ritz values 1/2 |G|^2 + v_x(n0) (uniform-gas LDA exchange) and zero residual."""
+    cell = inputs.small_cell(10.0, 24, 0, 7, 52)
+    ref = ko.Cell(cell)
+    picks = np.argsort(ref.g2)[:7]
+    c = np.zeros((7, ref.nG), complex)
+    c[np.arange(7), picks] = 1.0
+    rng = np.random.default_rng(9)
+    Q, _ = np.linalg.qr(rng.normal(size=(7, 7)) + 1j * rng.normal(size=(7, 7)))
+    rs = (3.0 / (4.0 * np.pi * 7.0 / ref.omega)) ** (1.0 / 3.0)
+    vx = -0.610887 / rs
+    for prec, tol in (("fp64", 1e-5), ("bf16x3", 3e-5)):
+        g = ks.Grid(cell, prec=prec)
+        g.set_states(Q @ c)
+        eps, res = g.scf(2, eig_iters=1, mix=0.5)
+        assert np.allclose(eps[-1], np.sort(0.5 * ref.g2[picks]) + vx, atol=tol)
+        assert np.max(res) < (1e-11 if prec == "fp64" else 1e-5)
+        g.close()
+
+
+def test_scf_arguments_and_tolerance(ks):
+    cell = inputs.small_cell(10.0, 24, 2, 4, 53)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec="bf16x3")
+    g.set_states(inputs.random_coeffs(53, 4, ref.nG))
+    for bad in (dict(eig_iters=0), dict(mix=0.0), dict(mix=1.5), dict(tol=-1.0)):
+        with pytest.raises(ks.KsError):
+            g.scf(2, **bad)
+    eps, res = g.scf(0)
+    assert eps.shape == (0, 4) and res.shape == (0,)
+    eps, res = g.scf(5, eig_iters=1, mix=0.5, tol=1e9)
+    assert len(res) == 1
+    g.close()

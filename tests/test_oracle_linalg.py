@@ -74,3 +74,38 @@ def test_block_iteration_lowers_ritz_values():
     e1, c1 = ko.block_iteration(cell, c, 2)
     e2, _ = ko.block_iteration(cell, c1, 10)
     assert np.all(e2 <= e1 + 1e-12)
+
+
+def test_scf_free_electron_closed_shell_is_a_fixed_point():
+    """V_loc = 0, no projectors, the 7 plane waves of the G = 0 and |m| = 1 shells mixed by a
+    random unitary: the density is uniform, n0 = 7 / Omega, so v_H = 0 and v_x is the
+    uniform-gas value -0.610887 / r_s (textbook LDA exchange, r_s = (3 / (4 pi n0))^(1/3)).
+    The SCF is at its fixed point: Ritz values 1/2 |G|^2 + v_x, density residual 0."""
+    cell = make_cell(natoms=0)
+    picks = np.argsort(cell.g2)[:7]
+    assert np.allclose(np.sort(cell.g2[picks])[1:], cell.g2[picks].max())
+    c = np.zeros((7, cell.nG), complex)
+    c[np.arange(7), picks] = 1.0
+    rng = np.random.default_rng(8)
+    Q, _ = np.linalg.qr(rng.normal(size=(7, 7)) + 1j * rng.normal(size=(7, 7)))
+    eps, res, _, n_in = ko.scf(cell, Q @ c, 2, 1, 0.5)
+    rs = (3.0 / (4.0 * np.pi * 7.0 / cell.omega)) ** (1.0 / 3.0)
+    vx = -0.610887 / rs
+    assert np.allclose(eps[-1], np.sort(0.5 * cell.g2[picks]) + vx, atol=1e-5)
+    assert np.max(res) < 1e-12
+    assert np.allclose(n_in, 7.0 / cell.omega, atol=1e-13)
+
+
+def test_scf_residual_contracts_and_tolerance_stops():
+    """From random states the residual is dominated by the unconverged eigenvectors at
+    first; after a few iterations each SCF step shrinks it.  The tolerance stops the loop
+    at the first iteration whose residual is below it, with the same history."""
+    cell = make_cell(natoms=4, depth=-3.0)
+    c = inputs.random_coeffs(9, 6, cell.nG)
+    eps, res, c_out, _ = ko.scf(cell, c, 12, 5, 0.3)
+    assert len(res) == 12
+    assert np.all(np.diff(res[4:]) < 0)
+    assert res[-1] < 0.6 * res[0]
+    assert np.max(np.abs(ko.gram(c_out) - np.eye(6))) <= 1e-12
+    eps2, res2, _, _ = ko.scf(cell, c, 12, 5, 0.3, tol=res[6] * 1.0000001)
+    assert len(res2) == 7 and np.allclose(res2, res[:7]) and np.allclose(eps2, eps[:7])
