@@ -14,6 +14,8 @@
 // conj(b_Il(G)) c_G with b_Il the sphere coefficients of the grid function beta_Il (built
 // once at setup with the FP64 FFT).  That is one overlap GEMM of the projector block with
 // the state block; the add stays in real space, fused into the plane kernel.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -204,14 +206,6 @@ __device__ __forceinline__ void plane_load_y(float2* P, const float2* __restrict
   if (xr > 0) cfft_lines<N, PT, LPC, true, +1>(P + (N - xr) * ld, xr, ld, 1, tw);
 }
 
-// ... then the inverse x transforms: every column jy, element jx at P[jx*ld + jy].
-template <int N>
-__device__ __forceinline__ void plane_load_inverse(float2* P, const float2* __restrict__ colrow, int ncols,
-                                                   const int* __restrict__ col_xy, int xr, const float2* tw) {
-  plane_load_y<N>(P, colrow, ncols, col_xy, xr, tw);
-  cfft_lines<N, FCfg<N>::PT, FCfg<N>::LPC, true, +1>(P, N, 1, N + 1, tw);
-}
-
 // u = V psi as the last stage of the inverse x transform stores it (x = jx, line = jy).
 template <int N> struct VMul {
   const float* V;
@@ -285,15 +279,77 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
   }
 }
 
-// Density partial sums: one (z-plane, chunk of states) per CTA, states in order.  The
-// accumulator plane lives in shared memory after the transform plane (each thread owns the
-// same elements for every state, so the sums are race-free and in a fixed order).
+// Density partial sums: one (z-plane, state) per CTA; a cluster holds DCL consecutive states
+// of one plane.  Each CTA transforms its state and writes f |u|^2 into its own shared-memory
+// plane (fused into the last stage of the inverse x transform).  The cluster then sums its
+// DCL planes through distributed shared memory, rank by rank in a fixed order, each CTA a
+// slice of the plane.  One state per CTA keeps the transforms free of a loop over states,
+// which would hold their index arithmetic live and spill.
+constexpr int DCL = 8;
+
+template <int N> struct DensSet {
+  float* acc;
+  float f;
+  __device__ __forceinline__ float2 operator()(float2 v, int x, int l) const {
+    acc[x * N + l] = f * (v.x * v.x + v.y * v.y);
+    return v;
+  }
+};
+
 template <int N>
-__global__ void __launch_bounds__(FCfg<N>::PT, 1)
+__global__ void __cluster_dims__(1, DCL, 1) __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
     k_plane_density(const float2* __restrict__ colbuf1, int ncols, const int* __restrict__ col_xy, int xr,
-                    int nstates, int chunk, const double* __restrict__ occ, float scale, float* __restrict__ partial,
+                    int nstates, const double* __restrict__ occ, float scale, float* __restrict__ partial,
                     const float2* __restrict__ twg) {
-  constexpr int ld = N + 1, PT = FCfg<N>::PT;
+  namespace cg = cooperative_groups;
+  constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC;
+  extern __shared__ __align__(16) float2 psm[];
+  float2* tw = psm;
+  float2* P = psm + N;
+  float* acc = reinterpret_cast<float*>(P + N * ld);
+  const int z = blockIdx.x, b = blockIdx.y;
+  for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
+  if (b < nstates) {
+    // the y transforms (their first barrier also publishes tw), then the x transforms
+    plane_load_y<N>(P, colbuf1 + ((size_t)b * N + z) * ncols, ncols, col_xy, xr, tw);
+    cfft_lines<N, PT, LPC, true, +1>(P, N, 1, ld, tw, DensSet<N>{acc, (float)occ[b]});
+  } else {
+    for (int e = threadIdx.x; e < N * N; e += PT) acc[e] = 0.f;   // padding state of the cluster
+  }
+  cg::cluster_group cl = cg::this_cluster();
+  cl.sync();
+  const int r = (int)cl.block_rank();
+  constexpr int E = (N * N + DCL - 1) / DCL;
+  float* out = partial + ((size_t)(b / DCL) * N + z) * N * N;
+  const int e1 = min(N * N, (r + 1) * E);
+  for (int e = r * E + threadIdx.x; e < e1; e += PT) {
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < DCL; ++q) sum += cl.map_shared_rank(acc, q)[e];
+    out[e] = sum * scale;
+  }
+  cl.sync();                                                         // keep the planes until read
+}
+
+// The same partial sums with one (z-plane, chunk of states) per CTA, states in order, for
+// the grids whose plane CTA fills an SM alone (N = 128: 1024 threads), where a cluster's
+// synchronisation and reduction per state would be exposed.  f |u|^2 is accumulated in the
+// last stage of the inverse x transform (each point by one thread, in state order).
+template <int N> struct DensAcc {
+  float* acc;
+  float f;
+  __device__ __forceinline__ float2 operator()(float2 v, int x, int l) const {
+    acc[x * N + l] += f * (v.x * v.x + v.y * v.y);
+    return v;
+  }
+};
+
+template <int N>
+__global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
+    k_plane_density_chunk(const float2* __restrict__ colbuf1, int ncols, const int* __restrict__ col_xy, int xr,
+                          int nstates, int chunk, const double* __restrict__ occ, float scale,
+                          float* __restrict__ partial, const float2* __restrict__ twg) {
+  constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC;
   extern __shared__ __align__(16) float2 psm[];
   float2* tw = psm;
   float2* P = psm + N;
@@ -302,15 +358,10 @@ __global__ void __launch_bounds__(FCfg<N>::PT, 1)
   for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
   for (int e = threadIdx.x; e < N * N; e += PT) acc[e] = 0.f;
   const int b0 = ch * chunk, b1 = min(nstates, b0 + chunk);
+#pragma unroll 1
   for (int b = b0; b < b1; ++b) {
-    plane_load_inverse<N>(P, colbuf1 + ((size_t)b * N + z) * ncols, ncols, col_xy, xr, tw);
-    const float f = (float)occ[b];
-    for (int e = threadIdx.x; e < N * N; e += PT) {
-      const int jx = e / N, jy = e - jx * N;
-      const float2 u = P[jx * ld + jy];
-      acc[e] += f * (u.x * u.x + u.y * u.y);
-    }
-    __syncthreads();
+    plane_load_y<N>(P, colbuf1 + ((size_t)b * N + z) * ncols, ncols, col_xy, xr, tw);
+    cfft_lines<N, PT, LPC, true, +1>(P, N, 1, ld, tw, DensAcc<N>{acc, (float)occ[b]});
   }
   float* out = partial + ((size_t)ch * N + z) * N * N;
   for (int e = threadIdx.x; e < N * N; e += PT) out[e] = acc[e] * scale;
@@ -427,8 +478,7 @@ class FusedImpl final : public FusedOps {
       part_ = alloc<double2>(part_elems_);
       build_projector_block();
     }
-    dchunk_ = std::max(1, std::min(32, (ns_ + 7) / 8));
-    nch_max_ = (ns_ + dchunk_ - 1) / dchunk_;
+    nch_max_ = (ns_ + density_chunk() - 1) / density_chunk();
     dpartial_ = alloc<float>((size_t)nch_max_ * N3);
   }
 
@@ -457,7 +507,7 @@ class FusedImpl final : public FusedOps {
   void density(const float2* psi, int n, const double* occ, float* nout, cudaStream_t s) override {
     zinv(psi, n, s);
     ProfScope ps(prof_, "plane_density", s);
-    const int nch = (n + dchunk_ - 1) / dchunk_;
+    const int nch = (n + density_chunk() - 1) / density_chunk();
     dispatch([&](auto tag) { launch_density<decltype(tag)::value>(n, nch, occ, s); });
     k_density_reduce<<<nblk((size_t)N_ * N_ * N_, 256), 256, 0, s>>>(dpartial_, nch, N_, nout);
     KS_CHECK_LAUNCH();
@@ -514,15 +564,29 @@ class FusedImpl final : public FusedOps {
                                                                    vplane_, nl_, pf_, nprojtot_, pf_smem, t_.tw);
     KS_CHECK_LAUNCH();
   }
+  // states per density partial: a cluster of DCL states, or a chunk per CTA at N = 128
+  int density_chunk() const { return N_ >= 128 ? std::max(1, std::min(32, (ns_ + 7) / 8)) : DCL; }
+
   template <int N> void launch_density(int n, int nch, const double* occ, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-      KS_CUDA(cudaFuncSetAttribute(k_plane_density<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX));
-      attr = true;
+    const size_t smem = plane_smem<N>() + (size_t)N * N * sizeof(float);
+    if constexpr (N >= 128) {
+      static bool attr = false;
+      if (!attr) {
+        KS_CUDA(cudaFuncSetAttribute(k_plane_density_chunk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM_MAX));
+        attr = true;
+      }
+      k_plane_density_chunk<N><<<dim3(N, nch), FCfg<N>::PT, smem, s>>>(
+          colbuf1_, ncols_, t_.col_xy, g_.xr, n, density_chunk(), occ, (float)(1.0 / g_.omega), dpartial_, t_.tw);
+    } else {
+      static bool attr = false;
+      if (!attr) {
+        KS_CUDA(cudaFuncSetAttribute(k_plane_density<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX));
+        attr = true;
+      }
+      k_plane_density<N><<<dim3(N, nch * DCL), FCfg<N>::PT, smem, s>>>(   // whole clusters of DCL states
+          colbuf1_, ncols_, t_.col_xy, g_.xr, n, occ, (float)(1.0 / g_.omega), dpartial_, t_.tw);
     }
-    dim3 grid(N, nch);
-    k_plane_density<N><<<grid, FCfg<N>::PT, plane_smem<N>() + (size_t)N * N * sizeof(float), s>>>(colbuf1_, ncols_, t_.col_xy, g_.xr, n, dchunk_, occ,
-                                                                   (float)(1.0 / g_.omega), dpartial_, t_.tw);
     KS_CHECK_LAUNCH();
   }
 
@@ -587,7 +651,7 @@ class FusedImpl final : public FusedOps {
   float2* pf_ = nullptr;
   double2* part_ = nullptr;
   size_t part_elems_ = 0;
-  int dchunk_ = 1, nch_max_ = 1;
+  int nch_max_ = 1;
   float* dpartial_ = nullptr;
 };
 

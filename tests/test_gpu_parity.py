@@ -127,6 +127,36 @@ def test_density_parity(ks, prec):
     g.close()
 
 
+def test_density_clusters_and_ragged_tail(ks):
+    """19 states: two full clusters of 8 states and a ragged third (3 states, 5 padding
+    slots), with unequal occupations, on the mixed path."""
+    cell = inputs.small_cell(10.0, 24, 2, 19, 54)
+    occ = np.linspace(0.0, 2.0, 19)
+    ref = ko.Cell(dict(cell, occ=occ))
+    g = ks.Grid(cell, prec="bf16x3", occ=occ)
+    c = inputs.random_coeffs(54, 19, ref.nG)
+    g.set_states(c)
+    n = torch.empty(24 ** 3, dtype=torch.float32, device="cuda")
+    g.density(n.data_ptr())
+    torch.cuda.synchronize()
+    assert rel(n.cpu().numpy().astype(float), ko.density(ref, c, occ).reshape(-1)) <= 1e-5
+    g.close()
+
+
+def test_density_128_grid(ks):
+    """128^3 grid (the real-time workload's size): the chunked density kernel."""
+    cell = inputs.small_cell(40.0, 128, 4, 5, 55)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec="bf16x3")
+    c = inputs.random_coeffs(55, 5, ref.nG)
+    g.set_states(c)
+    n = torch.empty(128 ** 3, dtype=torch.float32, device="cuda")
+    g.density(n.data_ptr())
+    torch.cuda.synchronize()
+    assert rel(n.cpu().numpy().astype(float), ko.density(ref, c).reshape(-1)) <= 1e-5
+    g.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_orthonormalize_parity(ks, prec):
     cell = inputs.small_cell(10.0, 24, 4, 9, 8)
