@@ -365,9 +365,12 @@ def main_gpu(args):
         ntg = gt.nG
         gt.set_states(inputs.random_coeffs(tcell["seed"], tcell["nstates"], ntg))
         gt.orthonormalize()
-        tt, _, te = timed_steps(gt, 2, 1, lambda: gt.td_step(0.05, 1, "etrs", True, stream), profile=True)
+        gt.kick((0.01, 0.0, 0.0))
+        tt, _, te = timed_steps(gt, 2, 1, lambda: gt.td_step(0.05, 1, "etrs", True, stream, dipoles=True),
+                                profile=True)
         tms = statistics.mean(tt)
-        td = {"workload": "td128: L=40, N=128, 512 states, 128 atoms, ETRS + Taylor 4, Hartree + Slater, dt=0.05",
+        td = {"workload": "td128: L=40, N=128, 512 states, 128 atoms, kick 0.01 bohr^-1 along x at t=0, then "
+                          "ETRS + Taylor 4 with Hartree + Slater and the dipole recorded each step, dt=0.05",
               "steps_per_s": 1e3 / tms, "ms_per_step": tms,
               "stages_ms_per_step": {k: v[0] / len(tt) for k, v in te.items() if v[0] > 0}}
         gt.close()

@@ -174,6 +174,25 @@ ks_status ks_scf(ks_grid g, int max_iter, int eig_iters, double mix, double tol,
 ks_status ks_td_step(ks_grid g, double dt, int nsteps, int propagator, int hartree_xc,
                      double* norm_out, double* energy_out, void* stream);
 
+/* ks_td_step that also records the dipole at the start of every step: dipole_out
+ * [nsteps][3] (may be NULL) receives d(t_s) = dV sum_j (r_j - L/2) n(r_j, t_s), the first
+ * moment of the density (Sec. "Validation with other codes": the observable of the kicked
+ * response), r_j = (L/N) (jx, jy, jz).  With hartree_xc the density is the one the step
+ * computes anyway; without it one density per step is added. */
+ks_status ks_td_step_dipole(ks_grid g, double dt, int nsteps, int propagator, int hartree_xc,
+                            double* norm_out, double* energy_out, double* dipole_out, void* stream);
+
+/* Delta kick (Sec. "Validation with other codes": a time-localised field at t = 0): every
+ * resident state psi_k(r) <- exp(i kappa . (r - L/2)) psi_k(r), projected back onto the
+ * sphere S.  kappa[3] (host, bohr^-1, finite).  The phase is periodic only when kappa is a
+ * reciprocal-lattice vector; otherwise the kick assumes states that vanish near the cell
+ * boundary (a molecule in a box).  Asynchronous on stream. */
+ks_status ks_kick(ks_grid g, const double* kappa, void* stream);
+
+/* Dipole of the resident states' density, d_out[3] (host) = dV sum_j (r_j - L/2) n(r_j).
+ * Synchronous. */
+ks_status ks_dipole(ks_grid g, double* d_out, void* stream);
+
 /* ---------------------------------------------------------------------------------- */
 /* Serving: continuous batching of independent calculations on one GPU.               */
 /* ---------------------------------------------------------------------------------- */

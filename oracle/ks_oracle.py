@@ -413,6 +413,31 @@ def td_step(cell, c, dt, propagator="etrs", hartree_xc=True):
     return out, norm_t, energy_t
 
 
+def kick(cell, c, kappa):
+    """Delta kick (Sec. "Validation with other codes", a time-localised field at t = 0):
+    psi(r) <- exp(i kappa . (r - L/2)) psi(r) on the grid, then back to the sphere S."""
+    r = cell.grid_points()
+    phase = np.exp(1j * np.tensordot(r - 0.5 * cell.L, np.asarray(kappa, float), axes=([3], [0])))
+    return to_coeff(cell, phase[None] * to_real(cell, c))
+
+
+def dipole(cell, n):
+    """First moment of the density, d = dV sum_j (r_j - L/2) n(r_j)."""
+    r = cell.grid_points()
+    return cell.dV * np.tensordot(r - 0.5 * cell.L, n, axes=([0, 1, 2], [0, 1, 2]))
+
+
+def td_run_dipole(cell, c, dt, nsteps, propagator="etrs", hartree_xc=True):
+    """td_run that also returns the dipole of the density at the start of every step."""
+    norms, energies, dips = [], [], []
+    for _ in range(nsteps):
+        dips.append(dipole(cell, density(cell, c)))
+        c, nrm, e = td_step(cell, c, dt, propagator, hartree_xc)
+        norms.append(nrm)
+        energies.append(e)
+    return c, np.array(norms), np.array(energies), np.array(dips)
+
+
 def td_run(cell, c, dt, nsteps, propagator="etrs", hartree_xc=True):
     norms, energies = [], []
     for _ in range(nsteps):

@@ -1,5 +1,6 @@
 // The C ABI (include/ks.h): argument checks, handle lifetime, and translation of internal
 // errors into ks_status.  No exception crosses this boundary.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -163,7 +164,31 @@ ks_status ks_td_step(ks_grid g, double dt, int nsteps, int propagator, int hartr
   return guarded([&] {
     need(g != nullptr, "grid is NULL");
     need(dt > 0 && dt < 10, "dt must be in (0, 10)");
-    g->eng->td_steps(dt, nsteps, propagator, hartree_xc, norm_out, energy_out, as_stream(stream));
+    g->eng->td_steps(dt, nsteps, propagator, hartree_xc, norm_out, energy_out, nullptr, as_stream(stream));
+  });
+}
+
+ks_status ks_td_step_dipole(ks_grid g, double dt, int nsteps, int propagator, int hartree_xc, double* norm_out,
+                            double* energy_out, double* dipole_out, void* stream) {
+  return guarded([&] {
+    need(g != nullptr, "grid is NULL");
+    need(dt > 0 && dt < 10, "dt must be in (0, 10)");
+    g->eng->td_steps(dt, nsteps, propagator, hartree_xc, norm_out, energy_out, dipole_out, as_stream(stream));
+  });
+}
+
+ks_status ks_kick(ks_grid g, const double* kappa, void* stream) {
+  return guarded([&] {
+    need(g != nullptr && kappa != nullptr, "grid or kappa is NULL");
+    for (int i = 0; i < 3; ++i) need(std::isfinite(kappa[i]), "kappa must be finite");
+    g->eng->kick(kappa, as_stream(stream));
+  });
+}
+
+ks_status ks_dipole(ks_grid g, double* d_out, void* stream) {
+  return guarded([&] {
+    need(g != nullptr && d_out != nullptr, "grid or d_out is NULL");
+    g->eng->dipole(d_out, as_stream(stream));
   });
 }
 

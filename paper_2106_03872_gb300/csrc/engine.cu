@@ -200,6 +200,8 @@ template <typename T> class Engine final : public EngineBase {
     hxc_partials_ = alloc<double>(HXC_BLOCKS * 3);
     nin_ = alloc<T>(N3);
     resid_dev_ = alloc<double>(1);
+    dip_partials_ = alloc<double>(HXC_BLOCKS * 3);
+    dipoles_dev_ = alloc<double>(3 * MAX_STEPS_CHUNK);
     parts_ = alloc<double>(4);
     dots_ = alloc<double2>(ns_);
     norms_dev_ = alloc<double>(MAX_STEPS_CHUNK);
@@ -576,10 +578,40 @@ template <typename T> class Engine final : public EngineBase {
   }
 
   // ------------------------------------------------------------------------------------------
+  // Delta kick and dipole (Sec. Validation with other codes: a time-localised field at t = 0
+  // and the first moment of the density as the observable)
+  // ------------------------------------------------------------------------------------------
+  // psi_k <- P_S exp(i kappa . (r - L/2)) psi_k, one state at a time through the full-grid
+  // work buffer (a once-per-run operation)
+  void kick(const double kappa[3], cudaStream_t s) override {
+    hpsi_valid_ = false;
+    const int N = g_.N;
+    const size_t N3 = (size_t)N * N * N;
+    ProfScope p(prof, "kick", s);
+    for (int b = 0; b < ns_; ++b) {
+      C* st = psi_ + (size_t)b * g_.nG;
+      KS_CUDA(cudaMemsetAsync(pwork_, 0, N3 * sizeof(C), s));
+      scatter_sphere<T>(st, pwork_, t_, 1, s);
+      for (int ax = 2; ax >= 0; --ax) fft_axis<T>(pwork_, 1, N, ax, +1, t_.tw, s);
+      multiply_phase<T>(pwork_, N, g_.L, kappa, s);
+      for (int ax = 0; ax < 3; ++ax) fft_axis<T>(pwork_, 1, N, ax, -1, t_.tw, s);
+      gather_kinetic<T>(pwork_, nullptr, st, t_, 1, T(1.0 / double(N3)), s);
+    }
+  }
+
+  // d = dV sum_j (r_j - L/2) n(r_j) of the resident states' density
+  void dipole(double* d_host, cudaStream_t s) override {
+    density_of(psi_, ns_, dens_, s);
+    ks::dipole<T>(dens_, g_.N, g_.L, dip_partials_, HXC_BLOCKS, dipoles_dev_, s);
+    KS_CUDA(cudaMemcpyAsync(d_host, dipoles_dev_, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // ------------------------------------------------------------------------------------------
   // Real-time steps: ETRS + Taylor 4 with shared powers (Eqs. 6-8), or plain Taylor 4.
   // ------------------------------------------------------------------------------------------
   void td_steps(double dt, int nsteps, int propagator, int hartree_xc, double* norm_out, double* energy_out,
-                cudaStream_t s) override {
+                double* dipole_out, cudaStream_t s) override {
     hpsi_valid_ = false;
     if (nsteps < 0 || (propagator != 0 && propagator != 1)) fail(KS_ERR_ARG, "td: nsteps=%d propagator=%d", nsteps, propagator);
     const int n = ns_, nG = g_.nG;
@@ -599,10 +631,9 @@ template <typename T> class Engine final : public EngineBase {
         C* wb = others[1];
         C* acc_full = others[2];
         C* acc_half = others[3];
-        if (hartree_xc) {
-          density_of(psi_, n, dens_, s);
-          update_potential(dens_, s);
-        }
+        if (hartree_xc || dipole_out) density_of(psi_, n, dens_, s);
+        if (dipole_out) ks::dipole<T>(dens_, g_.N, g_.L, dip_partials_, HXC_BLOCKS, dipoles_dev_ + 3 * st, s);
+        if (hartree_xc) update_potential(dens_, s);
         state_dots<T>(psi_, psi_, nG, n, dots_, s);
         weighted_energy(dots_, occ_, n, nullptr, norms_dev_ + st, s);
         // the accumulators start from psi in the first power's update (no copies)
@@ -640,13 +671,16 @@ template <typename T> class Engine final : public EngineBase {
         }
         psi_ = acc_full;
       }
-      std::vector<double> nh(cn), eh(cn);
+      std::vector<double> nh(cn), eh(cn), dh(dipole_out ? 3 * cn : 0);
       KS_CUDA(cudaMemcpyAsync(nh.data(), norms_dev_, cn * sizeof(double), cudaMemcpyDeviceToHost, s));
       KS_CUDA(cudaMemcpyAsync(eh.data(), energies_dev_, cn * sizeof(double), cudaMemcpyDeviceToHost, s));
+      if (dipole_out)
+        KS_CUDA(cudaMemcpyAsync(dh.data(), dipoles_dev_, 3 * cn * sizeof(double), cudaMemcpyDeviceToHost, s));
       KS_CUDA(cudaStreamSynchronize(s));
       check_tc_status(s);
       if (norm_out) std::memcpy(norm_out + c0, nh.data(), cn * sizeof(double));
       if (energy_out) std::memcpy(energy_out + c0, eh.data(), cn * sizeof(double));
+      if (dipole_out) std::memcpy(dipole_out + 3 * (size_t)c0, dh.data(), 3 * cn * sizeof(double));
       for (int i = 0; i < cn; ++i) {
         if (!have_first) {
           first_norm = nh[i];
@@ -782,6 +816,8 @@ template <typename T> class Engine final : public EngineBase {
   double* hxc_partials_ = nullptr;
   T* nin_ = nullptr;                // SCF input density
   double* resid_dev_ = nullptr;     // SCF residual
+  double* dip_partials_ = nullptr;  // dipole block partials
+  double* dipoles_dev_ = nullptr;   // [MAX_STEPS_CHUNK][3] dipoles of a chunk of real-time steps
   double* parts_ = nullptr;
   double2* dots_ = nullptr;
   double* norms_dev_ = nullptr;

@@ -100,7 +100,9 @@ class EngineBase {
   virtual void scf(int max_iter, int eig_iters, double mix, double tol, double* eig_out, double* resid_out,
                    int* iters_done, cudaStream_t s) = 0;
   virtual void td_steps(double dt, int nsteps, int propagator, int hartree_xc, double* norm_out,
-                        double* energy_out, cudaStream_t s) = 0;
+                        double* energy_out, double* dipole_out, cudaStream_t s) = 0;
+  virtual void kick(const double kappa[3], cudaStream_t s) = 0;
+  virtual void dipole(double* d_host, cudaStream_t s) = 0;
   virtual void randomize_states(uint64_t seed, cudaStream_t s) = 0;
 };
 

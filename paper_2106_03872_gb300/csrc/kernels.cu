@@ -1,6 +1,8 @@
 // Full-grid ("plain") path kernels: batched line FFTs, sphere scatter/gather with the
 // kinetic term, potential multiply, real-space KB projectors (Eq. 9), density (Eq. 1),
 // periodic Poisson + Slater exchange, and the FP64 reductions for norms and energies.
+#include <type_traits>
+
 #include "fft_device.cuh"
 #include "kernels.h"
 
@@ -101,9 +103,13 @@ __global__ void k_gather_kinetic(const cplx<T>* __restrict__ grid, const cplx<T>
   const int b = blockIdx.y;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nG; g += gridDim.x * blockDim.x) {
     const cplx<T> u = grid[b * N3 + gidx[g]];
-    const cplx<T> p = psi[(size_t)b * nG + g];
-    const T k = g2h[g];
-    hpsi[(size_t)b * nG + g] = mk<cplx<T>>(u.x * scale + k * p.x, u.y * scale + k * p.y);
+    if (psi) {
+      const cplx<T> p = psi[(size_t)b * nG + g];
+      const T k = g2h[g];
+      hpsi[(size_t)b * nG + g] = mk<cplx<T>>(u.x * scale + k * p.x, u.y * scale + k * p.y);
+    } else {
+      hpsi[(size_t)b * nG + g] = mk<cplx<T>>(u.x * scale, u.y * scale);
+    }
   }
 }
 
@@ -114,6 +120,49 @@ __global__ void k_multiply_potential(cplx<T>* __restrict__ grid, const T* __rest
     const T vj = v[j];
     cplx<T> u = grid[b * N3 + j];
     grid[b * N3 + j] = mk<cplx<T>>(u.x * vj, u.y * vj);
+  }
+}
+
+// grid[j] *= exp(i kappa . (r_j - L/2)), r_j = h (jx, jy, jz), row-major z fastest
+template <typename T>
+__global__ void k_multiply_phase(cplx<T>* __restrict__ grid, int N, T h, T L, T kx, T ky, T kz) {
+  const size_t N3 = (size_t)N * N * N;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
+    const int jz = (int)(j % N), jy = (int)((j / N) % N), jx = (int)(j / ((size_t)N * N));
+    const T ph = kx * (h * jx - T(0.5) * L) + ky * (h * jy - T(0.5) * L) + kz * (h * jz - T(0.5) * L);
+    T sn, cs;
+    if constexpr (std::is_same<T, float>::value)
+      sincosf(ph, &sn, &cs);
+    else
+      sincos(ph, &sn, &cs);
+    const cplx<T> u = grid[j];
+    grid[j] = mk<cplx<T>>(u.x * cs - u.y * sn, u.x * sn + u.y * cs);
+  }
+}
+
+// Block partials of sum_j n_j (r_j - L/2) (three components), r_j = h (jx, jy, jz)
+template <typename T>
+__global__ void k_dipole_partials(const T* __restrict__ n, int N, double h, double L, double* __restrict__ partials) {
+  const size_t N3 = (size_t)N * N * N;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
+    const int jz = (int)(j % N), jy = (int)((j / N) % N), jx = (int)(j / ((size_t)N * N));
+    const double nj = (double)n[j];
+    acc[0] += nj * (h * jx - 0.5 * L);
+    acc[1] += nj * (h * jy - 0.5 * L);
+    acc[2] += nj * (h * jz - 0.5 * L);
+  }
+  block_sum<3>(acc);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 3; ++i) partials[blockIdx.x * 3 + i] = acc[i];
+}
+
+__global__ void k_dipole_finish(const double* __restrict__ partials, int nblocks, double dV, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s[3] = {0, 0, 0};
+    for (int b = 0; b < nblocks; ++b)
+      for (int i = 0; i < 3; ++i) s[i] += partials[b * 3 + i];
+    for (int i = 0; i < 3; ++i) out[i] = dV * s[i];
   }
 }
 
@@ -391,6 +440,22 @@ void multiply_potential(cplx<T>* grid, const T* v, int N3, int nb, cudaStream_t 
 }
 
 template <typename T>
+void multiply_phase(cplx<T>* grid, int N, double L, const double kappa[3], cudaStream_t s) {
+  const size_t N3 = (size_t)N * N * N;
+  k_multiply_phase<T><<<blocks_for(N3, 256, 2048), 256, 0, s>>>(grid, N, (T)(L / N), (T)L, (T)kappa[0], (T)kappa[1],
+                                                                 (T)kappa[2]);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void dipole(const T* n, int N, double L, double* partials, int nblocks, double* out, cudaStream_t s) {
+  k_dipole_partials<T><<<nblocks, RED_THREADS, 0, s>>>(n, N, L / N, L, partials);
+  KS_CHECK_LAUNCH();
+  k_dipole_finish<<<1, 32, 0, s>>>(partials, nblocks, (L / N) * (L / N) * (L / N), out);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
 void nl_project(const cplx<T>* grid, const DevTables<T>& t, cplx<T>* proj, int nb, T scale, cudaStream_t s) {
   if (t.natoms == 0) return;
   dim3 g(t.natoms, nb);
@@ -513,6 +578,8 @@ void real_to_double(const T* in, double* out, size_t n, cudaStream_t s) {
   template void poisson_multiply<T>(cplx<T>*, int, double, T, cudaStream_t);                                    \
   template void hxc_combine<T>(const T*, const cplx<T>*, const T*, T*, double*, int, int, cudaStream_t);        \
   template void density_mix<T>(const T*, T*, int, double, double*, int, cudaStream_t);                          \
+  template void multiply_phase<T>(cplx<T>*, int, double, const double*, cudaStream_t);                          \
+  template void dipole<T>(const T*, int, double, double*, int, double*, cudaStream_t);                          \
   template void state_dots<T>(const cplx<T>*, const cplx<T>*, int, int, double2*, cudaStream_t);                \
   template void axpy2<T>(cplx<T>*, double2, cplx<T>*, double2, const cplx<T>*, const cplx<T>*, size_t, cudaStream_t);           \
   template void random_states<T>(cplx<T>*, size_t, uint64_t, cudaStream_t);                                     \

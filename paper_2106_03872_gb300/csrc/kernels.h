@@ -30,11 +30,16 @@ template <typename T> struct DevTables {
 template <typename T> void fft_axis(cplx<T>* grid, int nb, int N, int axis, int sign, const cplx<T>* tw, cudaStream_t s);
 // grid[b][gidx[g]] = psi[b][g] (grid must be zeroed before).
 template <typename T> void scatter_sphere(const cplx<T>* psi, cplx<T>* grid, const DevTables<T>& t, int nb, cudaStream_t s);
-// hpsi[b][g] = scale * grid[b][gidx[g]] + g2half[g] * psi[b][g]
+// hpsi[b][g] = scale * grid[b][gidx[g]] + g2half[g] * psi[b][g] (no kinetic term if psi is null)
 template <typename T> void gather_kinetic(const cplx<T>* grid, const cplx<T>* psi, cplx<T>* hpsi, const DevTables<T>& t,
                                           int nb, T scale, cudaStream_t s);
 // grid[b][j] *= v[j]
 template <typename T> void multiply_potential(cplx<T>* grid, const T* v, int N3, int nb, cudaStream_t s);
+// one grid [N][N][N]: grid[j] *= exp(i kappa . (r_j - L/2)), r_j = (L/N) (jx, jy, jz)
+template <typename T> void multiply_phase(cplx<T>* grid, int N, double L, const double kappa[3], cudaStream_t s);
+// out[3] (device) = dV sum_j n_j (r_j - L/2); partials holds nblocks * 3 doubles
+template <typename T> void dipole(const T* n, int N, double L, double* partials, int nblocks, double* out,
+                                  cudaStream_t s);
 // proj[b][I][l] = scale * sum_{j in sphere I} beta_Il(j) grid[b][j]
 template <typename T> void nl_project(const cplx<T>* grid, const DevTables<T>& t, cplx<T>* proj, int nb, T scale, cudaStream_t s);
 // grid[b][j] += scale * sum_{(I,l) covering j} beta_Il(j) proj[b][I][l]

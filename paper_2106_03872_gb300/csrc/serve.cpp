@@ -148,7 +148,7 @@ bool quantum(Request* r) {
     r->eng->block_iteration(1, r->result.data(), r->stream);
   } else {
     double nrm = 0, e = 0;
-    r->eng->td_steps(r->dt, 1, 0, 1, &nrm, &e, r->stream);
+    r->eng->td_steps(r->dt, 1, 0, 1, &nrm, &e, nullptr, r->stream);
     r->result.push_back(e);
   }
   return ++r->done >= r->count;

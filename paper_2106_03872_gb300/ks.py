@@ -23,7 +23,7 @@ PRECISIONS = {"fp64": KS_FP64, "bf16x3": KS_MIXED_BF16X3, "tf32": KS_MIXED_TF32}
 # Every symbol declared in include/ks.h.
 EXPORTS = ["ks_count_gvectors", "ks_grid_create", "ks_grid_destroy", "ks_grid_gvectors", "ks_grid_device_bytes",
            "ks_get_vloc", "ks_set_states", "ks_get_states", "ks_states_device", "ks_apply_h", "ks_apply_h_host",
-           "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_scf", "ks_td_step",
+           "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_scf", "ks_td_step", "ks_td_step_dipole", "ks_kick", "ks_dipole",
            "ks_serve_create", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info",
            "ks_profile", "ks_profile_read", "ks_profile_span", "ks_kernel_launches", "ks_overlap_noalloc", "ks_last_error"]
 
@@ -74,6 +74,9 @@ def load():
         "ks_block_iteration": [P, ct.c_int, dp, P],
         "ks_scf": [P, ct.c_int, ct.c_int, ct.c_double, ct.c_double, dp, dp, ip, P],
         "ks_td_step": [P, ct.c_double, ct.c_int, ct.c_int, ct.c_int, dp, dp, P],
+        "ks_td_step_dipole": [P, ct.c_double, ct.c_int, ct.c_int, ct.c_int, dp, dp, dp, P],
+        "ks_kick": [P, dp, P],
+        "ks_dipole": [P, dp, P],
         "ks_serve_create": [ct.c_size_t, ct.POINTER(P)],
         "ks_serve_destroy": [P],
         "ks_serve_submit": [P, ct.POINTER(CellDesc), dp, ct.c_int, ct.c_int, ct.c_double,
@@ -277,13 +280,31 @@ class Grid:
             i += 1
         return out
 
-    def td_step(self, dt, nsteps, propagator="etrs", hartree_xc=True, stream=None):
+    def td_step(self, dt, nsteps, propagator="etrs", hartree_xc=True, stream=None, dipoles=False):
+        """nsteps real-time steps; returns (norms, energies), plus the dipoles [nsteps][3] at
+        the start of each step when dipoles is set."""
         norms = np.zeros(nsteps)
         energies = np.zeros(nsteps)
         prop = {"etrs": 0, "taylor": 1}[propagator] if isinstance(propagator, str) else int(propagator)
+        if dipoles:
+            d = np.zeros((max(nsteps, 1), 3))
+            check(load().ks_td_step_dipole(self.h, float(dt), int(nsteps), prop, 1 if hartree_xc else 0,
+                                           _dptr(norms), _dptr(energies), _dptr(d), _stream_ptr(stream)))
+            return norms, energies, d[:nsteps]
         check(load().ks_td_step(self.h, float(dt), int(nsteps), prop, 1 if hartree_xc else 0, _dptr(norms),
                                 _dptr(energies), _stream_ptr(stream)))
         return norms, energies
+
+    def kick(self, kappa, stream=None):
+        """Delta kick psi <- P_S exp(i kappa . (r - L/2)) psi of every resident state."""
+        k = np.ascontiguousarray(kappa, dtype=np.float64).reshape(3)
+        check(load().ks_kick(self.h, _dptr(k), _stream_ptr(stream)))
+
+    def dipole(self, stream=None):
+        """dV sum_j (r_j - L/2) n(r_j) of the resident states."""
+        d = np.zeros(3)
+        check(load().ks_dipole(self.h, _dptr(d), _stream_ptr(stream)))
+        return d
 
 
 class Server:

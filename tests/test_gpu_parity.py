@@ -561,3 +561,57 @@ def test_scf_arguments_and_tolerance(ks):
     eps, res = g.scf(5, eig_iters=1, mix=0.5, tol=1e9)
     assert len(res) == 1
     g.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# Delta kick and dipole (Sec. "Validation with other codes")
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_kick_and_dipole_parity(ks, prec):
+    cell = inputs.small_cell(10.0, 24, 3, 6, 56)
+    ref = ko.Cell(cell)
+    q, _ = ko.cholqr(inputs.random_coeffs(56, 6, ref.nG))
+    kappa = (0.05, -0.03, 0.02)
+    g = ks.Grid(cell, prec=prec)
+    g.set_states(q)
+    d0 = g.dipole()
+    d0_ref = ko.dipole(ref, ko.density(ref, q))
+    g.kick(kappa)
+    got = g.get_states()
+    kq = ko.kick(ref, q, kappa)
+    if prec == "fp64":
+        assert rel(got, kq) <= 1e-12
+        assert np.max(np.abs(d0 - d0_ref)) <= 1e-11 * np.max(np.abs(d0_ref))
+    else:
+        assert rel(got, kq) <= 2e-5
+        assert np.max(np.abs(d0 - d0_ref)) <= 1e-5 * np.max(np.abs(d0_ref))
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_td_dipole_after_kick_parity(ks, prec):
+    """Kick at t = 0, then ETRS steps with Hartree + exchange: the dipole at the start of
+    every step against the oracle's."""
+    cell = inputs.small_cell(10.0, 24, 3, 6, 57)
+    ref = ko.Cell(cell)
+    q, _ = ko.cholqr(inputs.random_coeffs(57, 6, ref.nG))
+    kappa = (0.1, 0.0, 0.0)
+    g = ks.Grid(cell, prec=prec)
+    g.set_states(q)
+    g.kick(kappa)
+    norms, energies, dips = g.td_step(0.05, 4, "etrs", True, dipoles=True)
+    _, n_ref, e_ref, d_ref = ko.td_run_dipole(ref, ko.kick(ref, q, kappa), 0.05, 4, "etrs", True)
+    scale = np.max(np.abs(d_ref))
+    if prec == "fp64":
+        assert np.max(np.abs(dips - d_ref)) <= 1e-10 * scale
+        assert np.max(np.abs(norms - n_ref)) <= 1e-11 * n_ref[0]
+    else:
+        assert np.max(np.abs(dips - d_ref)) <= 1e-5 * scale
+    # the dipole path adds no change to norms and energies
+    g2 = ks.Grid(cell, prec=prec)
+    g2.set_states(q)
+    g2.kick(kappa)
+    n2, e2 = g2.td_step(0.05, 4, "etrs", True)
+    assert np.array_equal(n2, norms) and np.array_equal(e2, energies)
+    g.close()
+    g2.close()

@@ -117,3 +117,31 @@ def test_energy_conserved_and_converges_with_dt():
         assert abs(norms[-1] - norms[0]) < 1e-5
     assert drifts[0] < 1e-4
     assert drifts[1] < drifts[0] / 10.0         # observed ~dt^4 (ratio 16-28); demand > 3rd order
+
+
+def test_kick_by_reciprocal_lattice_vector_shifts_plane_wave():
+    """kappa = 2 pi m0 / L with m0 = (1, 0, 0): exp(i kappa (x - L/2)) maps the plane wave G to
+    G + kappa with the phase exp(-i pi) = -1 (and keeps its norm)."""
+    cell = make_cell(natoms=0)
+    m = cell.m
+    g0 = int(np.flatnonzero((m[:, 0] == 2) & (m[:, 1] == -1) & (m[:, 2] == 3))[0])
+    g1 = int(np.flatnonzero((m[:, 0] == 3) & (m[:, 1] == -1) & (m[:, 2] == 3))[0])
+    c = np.zeros((1, cell.nG), complex)
+    c[0, g0] = 1.0
+    kc = ko.kick(cell, c, (2 * np.pi / cell.L, 0.0, 0.0))
+    expect = np.zeros_like(c)
+    expect[0, g1] = -1.0
+    assert np.max(np.abs(kc - expect)) < 1e-12
+
+
+def test_dipole_closed_forms():
+    """A Gaussian density well inside the cell has first moment (R - L/2) times its charge;
+    a uniform density has -(h/2) times its charge on the grid r_j = h j."""
+    cell = make_cell(natoms=0)
+    r = cell.grid_points()
+    R = np.array([3.1, 6.2, 4.4])
+    n = np.exp(-np.sum((r - R) ** 2, axis=-1) / (2 * 0.6 ** 2))
+    q = cell.dV * n.sum()
+    assert np.allclose(ko.dipole(cell, n) / q, R - 0.5 * cell.L, atol=1e-9)
+    n0 = np.full((cell.N,) * 3, 0.37)
+    assert np.allclose(ko.dipole(cell, n0), -0.5 * cell.h * cell.dV * n0.sum(), atol=1e-12)
