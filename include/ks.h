@@ -144,20 +144,23 @@ ks_status ks_rayleigh_ritz(ks_grid g, double* eig_host, void* stream);
  * Ritz values of the last iteration.  Synchronous. */
 ks_status ks_block_iteration(ks_grid g, int niter, double* eig_host, void* stream);
 
-/* Self-consistent field (Sec. "Ground-state solution"), static linear mixing.  The
- * resident states are orthonormalised (CholQR) and their density is the first input
- * density n_in.  Each SCF iteration:
+/* Self-consistent field (Sec. "Ground-state solution").  The resident states are
+ * orthonormalised (CholQR) and their density is the first input density n_in.  Each SCF
+ * iteration:
  *   V = V_loc + v_H[n_in] + v_x[n_in];  eig_iters block iterations with this V;
- *   CholQR;  n_out = density of the states;  r = dV sum_j |n_out - n_in|;
- *   n_in <- n_in + mix (n_out - n_in).
+ *   CholQR;  n_out = density of the states;  R = n_out - n_in;  r = dV sum_j |R_j|;
+ *   mixer 0 (static linear): n_in <- n_in + mix R;
+ *   mixer 1 (Pulay / DIIS):  with the last `history` (1..8) pairs (n_in_i, R_i) and
+ *     alpha minimising |sum_i alpha_i R_i| (dV-weighted L2) subject to sum_i alpha_i = 1,
+ *     n_in <- sum_i alpha_i (n_in_i + mix R_i).
  * Stops after max_iter iterations or once r < tol.  eig_out [max_iter][nstates] (may be
  * NULL) receives each iteration's Ritz values, resid_out [max_iter] (may be NULL) its r,
  * iters_done (may be NULL) the number of iterations run.  Afterwards the states are
  * orthonormal and V is the potential of the last iteration's n_in.  KS_ERR_ARG unless
- * max_iter >= 0, eig_iters >= 1, 0 < mix <= 1 and tol >= 0; KS_ERR_DIVERGED if r is not
- * finite.  Synchronous. */
-ks_status ks_scf(ks_grid g, int max_iter, int eig_iters, double mix, double tol, double* eig_out,
-                 double* resid_out, int* iters_done, void* stream);
+ * max_iter >= 0, eig_iters >= 1, mixer in {0, 1}, 0 < mix <= 1, 1 <= history <= 8 and
+ * tol >= 0; KS_ERR_DIVERGED if r is not finite.  Synchronous. */
+ks_status ks_scf(ks_grid g, int max_iter, int eig_iters, int mixer, double mix, int history, double tol,
+                 double* eig_out, double* resid_out, int* iters_done, void* stream);
 
 /* nsteps real-time steps of dt (Sec. "Real-time propagation").
  *   propagator 0: ETRS (Eq. 6) with H(t+dt) from the density of the full step (Eq. 7);

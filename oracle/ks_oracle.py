@@ -323,28 +323,57 @@ def hxc_potential(cell, n):
     return cell.vloc + vh + vx, parts
 
 
-def scf(cell, c, max_iter, eig_iters, mix, tol=0.0):
+def pulay_coefficients(A):
+    """alpha minimising || sum_i alpha_i R_i ||^2 subject to sum_i alpha_i = 1, from the Gram
+    matrix A_ij = <R_i|R_j> (Pulay / DIIS): the bordered system [A 1; 1^T 0] [alpha; mu] =
+    [0; 1], with A regularised by 1e-12 of its mean diagonal."""
+    m = A.shape[0]
+    reg = 1e-12 * max(np.trace(A) / m, 1e-300)
+    B = np.zeros((m + 1, m + 1))
+    B[:m, :m] = A + reg * np.eye(m)
+    B[:m, m] = 1.0
+    B[m, :m] = 1.0
+    rhs = np.zeros(m + 1)
+    rhs[m] = 1.0
+    return np.linalg.solve(B, rhs)[:m]
+
+
+def scf(cell, c, max_iter, eig_iters, mix, tol=0.0, mixer="linear", history=4):
     """Self-consistent field (Sec. "Ground-state solution"): each iteration solves the
     linear problem for the current input density with a few eigensolver iterations, forms
-    the output density and mixes it into the input (static linear mixing).
+    the output density and mixes it into the input.
 
     The initial input density is that of the orthonormalised initial states (the paper
     starts from atomic densities of pseudopotential files, which this setting has none of).
     Per iteration: V = V_loc + v_H[n_in] + v_x[n_in]; eig_iters block iterations; CholQR;
-    n_out = density; r = dV sum |n_out - n_in|; n_in <- n_in + mix (n_out - n_in); stop
-    once r < tol.  Returns (Ritz values per iteration, residuals, states, final n_in)."""
+    n_out = density; R = n_out - n_in, r = dV sum |R|; then
+      linear: n_in <- n_in + mix R;
+      pulay:  with the last `history` pairs (n_in_i, R_i) and alpha from pulay_coefficients
+              of A_ij = dV sum R_i R_j, n_in <- sum_i alpha_i (n_in_i + mix R_i).
+    Stops once r < tol.  Returns (Ritz values per iteration, residuals, states, final n_in)."""
     c, _ = cholqr(c)
     n_in = density(cell, c)
     eps_hist, res_hist = [], []
+    hist_n, hist_r = [], []
     for _ in range(max_iter):
         v, _ = hxc_potential(cell, n_in)
         eps, c = block_iteration(cell, c, eig_iters, v)
         c, _ = cholqr(c)
         n_out = density(cell, c)
-        r = cell.dV * float(np.sum(np.abs(n_out - n_in)))
+        R = n_out - n_in
+        r = cell.dV * float(np.sum(np.abs(R)))
         eps_hist.append(eps)
         res_hist.append(r)
-        n_in = n_in + mix * (n_out - n_in)
+        if mixer == "linear":
+            n_next = n_in + mix * R
+        else:
+            hist_n.append(n_in)
+            hist_r.append(R)
+            hist_n, hist_r = hist_n[-history:], hist_r[-history:]
+            A = np.array([[cell.dV * float(np.sum(a * b)) for b in hist_r] for a in hist_r])
+            alpha = pulay_coefficients(A)
+            n_next = sum(a * (n + mix * rr) for a, n, rr in zip(alpha, hist_n, hist_r))
+        n_in = n_next
         if r < tol:
             break
     return np.array(eps_hist), np.array(res_hist), c, n_in

@@ -192,13 +192,14 @@ ks_status ks_dipole(ks_grid g, double* d_out, void* stream) {
   });
 }
 
-ks_status ks_scf(ks_grid g, int max_iter, int eig_iters, double mix, double tol, double* eig_out,
-                 double* resid_out, int* iters_done, void* stream) {
+ks_status ks_scf(ks_grid g, int max_iter, int eig_iters, int mixer, double mix, int history, double tol,
+                 double* eig_out, double* resid_out, int* iters_done, void* stream) {
   return guarded([&] {
     need(g != nullptr, "grid is NULL");
-    need(max_iter >= 0 && eig_iters >= 1 && mix > 0.0 && mix <= 1.0 && tol >= 0.0,
-         "scf: need max_iter >= 0, eig_iters >= 1, 0 < mix <= 1, tol >= 0");
-    g->eng->scf(max_iter, eig_iters, mix, tol, eig_out, resid_out, iters_done, as_stream(stream));
+    need(max_iter >= 0 && eig_iters >= 1 && (mixer == 0 || mixer == 1) && mix > 0.0 && mix <= 1.0 &&
+             history >= 1 && history <= 8 && tol >= 0.0,
+         "scf: need max_iter >= 0, eig_iters >= 1, mixer 0 or 1, 0 < mix <= 1, 1 <= history <= 8, tol >= 0");
+    g->eng->scf(max_iter, eig_iters, mixer, mix, history, tol, eig_out, resid_out, iters_done, as_stream(stream));
   });
 }
 

@@ -543,12 +543,24 @@ template <typename T> class Engine final : public EngineBase {
   // ------------------------------------------------------------------------------------------
   // Self-consistent field (Sec. Ground-state solution) with static linear mixing.
   // ------------------------------------------------------------------------------------------
-  void scf(int max_iter, int eig_iters, double mix, double tol, double* eig_out, double* resid_out, int* iters_done,
-           cudaStream_t s) override {
-    if (max_iter < 0 || eig_iters < 1 || !(mix > 0.0 && mix <= 1.0) || !(tol >= 0.0))
-      fail(KS_ERR_ARG, "scf: max_iter=%d eig_iters=%d mix=%g tol=%g", max_iter, eig_iters, mix, tol);
+  void scf(int max_iter, int eig_iters, int mixer, double mix, int history, double tol, double* eig_out,
+           double* resid_out, int* iters_done, cudaStream_t s) override {
+    if (max_iter < 0 || eig_iters < 1 || (mixer != 0 && mixer != 1) || !(mix > 0.0 && mix <= 1.0) || history < 1 ||
+        history > PULAY_MAX || !(tol >= 0.0))
+      fail(KS_ERR_ARG, "scf: max_iter=%d eig_iters=%d mixer=%d mix=%g history=%d tol=%g", max_iter, eig_iters, mixer,
+           mix, history, tol);
     const int N3 = g_.N * g_.N * g_.N;
+    if (mixer == 1 && !hist_n_[0]) {
+      for (int i = 0; i < PULAY_MAX; ++i) {
+        hist_n_[i] = alloc<T>(N3);
+        hist_r_[i] = alloc<T>(N3);
+      }
+      pulay_partials_ = alloc<double>((size_t)HXC_BLOCKS * (2 + PULAY_MAX));
+      pulay_out_ = alloc<double>(2 + PULAY_MAX);
+    }
     std::vector<double> eig(ns_);
+    std::vector<double> A((size_t)PULAY_MAX * PULAY_MAX, 0.0);   // <R_i|R_j> of the history slots
+    std::vector<int> order;                                       // slots, oldest first
     orthonormalize(nullptr, s);
     density_of(psi_, ns_, nin_, s);
     int it = 0;
@@ -559,13 +571,44 @@ template <typename T> class Engine final : public EngineBase {
       orthonormalize(nullptr, s);
       density_of(psi_, ns_, dens_, s);
       double r = 0.0;
-      {
+      if (mixer == 0) {
         ProfScope p(prof, "density_mix", s);
         density_mix<T>(dens_, nin_, N3, mix, hxc_partials_, HXC_BLOCKS, s);
         sum_partials(hxc_partials_, HXC_BLOCKS, g_.dV, resid_dev_, s);
+        KS_CUDA(cudaMemcpyAsync(&r, resid_dev_, sizeof(double), cudaMemcpyDeviceToHost, s));
+        KS_CUDA(cudaStreamSynchronize(s));
+      } else {
+        ProfScope p(prof, "density_mix", s);
+        // the new pair goes to the oldest slot once the history is full
+        if ((int)order.size() == history) order.erase(order.begin());
+        int slot = 0;
+        while (std::find(order.begin(), order.end(), slot) != order.end()) ++slot;
+        PulayRefs<T> refs{};
+        refs.m = (int)order.size();
+        for (int q = 0; q < refs.m; ++q) refs.r[q] = hist_r_[order[q]];
+        double out[2 + PULAY_MAX];
+        pulay_store<T>(dens_, nin_, hist_n_[slot], hist_r_[slot], N3, refs, pulay_partials_, HXC_BLOCKS, g_.dV,
+                       pulay_out_, s);
+        KS_CUDA(cudaMemcpyAsync(out, pulay_out_, sizeof(out), cudaMemcpyDeviceToHost, s));
+        KS_CUDA(cudaStreamSynchronize(s));
+        r = out[0];
+        A[slot * PULAY_MAX + slot] = out[1];
+        for (int q = 0; q < refs.m; ++q) {
+          A[slot * PULAY_MAX + order[q]] = out[2 + q];
+          A[order[q] * PULAY_MAX + slot] = out[2 + q];
+        }
+        order.push_back(slot);
+        const std::vector<double> alpha = pulay_coefficients(A, order);
+        PulayMix<T> pm{};
+        pm.m = (int)order.size();
+        pm.mix = mix;
+        for (int q = 0; q < pm.m; ++q) {
+          pm.n[q] = hist_n_[order[q]];
+          pm.r[q] = hist_r_[order[q]];
+          pm.a[q] = alpha[q];
+        }
+        pulay_mix<T>(nin_, N3, pm, s);
       }
-      KS_CUDA(cudaMemcpyAsync(&r, resid_dev_, sizeof(double), cudaMemcpyDeviceToHost, s));
-      KS_CUDA(cudaStreamSynchronize(s));
       if (eig_out) std::memcpy(eig_out + (size_t)it * ns_, eig.data(), ns_ * sizeof(double));
       if (resid_out) resid_out[it] = r;
       if (!std::isfinite(r)) fail(KS_ERR_DIVERGED, "scf iteration %d: density residual %g", it, r);
@@ -575,6 +618,41 @@ template <typename T> class Engine final : public EngineBase {
       }
     }
     if (iters_done) *iters_done = it;
+  }
+
+  // alpha minimising |sum_i alpha_i R_i|^2 with sum_i alpha_i = 1 over the slots in `order`:
+  // the bordered system [A 1; 1^T 0] [alpha; mu] = [0; 1], A regularised by 1e-12 of its mean
+  // diagonal, solved by Gaussian elimination with partial pivoting (m <= 8).
+  static std::vector<double> pulay_coefficients(const std::vector<double>& A, const std::vector<int>& order) {
+    const int m = (int)order.size();
+    double tr = 0.0;
+    for (int i = 0; i < m; ++i) tr += A[order[i] * PULAY_MAX + order[i]];
+    const double reg = 1e-12 * std::max(tr / m, 1e-300);
+    const int n = m + 1;
+    std::vector<double> B((size_t)n * (n + 1), 0.0);
+    for (int i = 0; i < m; ++i) {
+      for (int j = 0; j < m; ++j) B[i * (n + 1) + j] = A[order[i] * PULAY_MAX + order[j]] + (i == j ? reg : 0.0);
+      B[i * (n + 1) + m] = 1.0;
+      B[m * (n + 1) + i] = 1.0;
+    }
+    B[m * (n + 1) + n] = 1.0;                                         // right-hand side (0, ..., 0, 1)
+    for (int c = 0; c < n; ++c) {
+      int piv = c;
+      for (int i = c + 1; i < n; ++i)
+        if (std::fabs(B[i * (n + 1) + c]) > std::fabs(B[piv * (n + 1) + c])) piv = i;
+      if (piv != c)
+        for (int j = 0; j <= n; ++j) std::swap(B[c * (n + 1) + j], B[piv * (n + 1) + j]);
+      const double d = B[c * (n + 1) + c];
+      if (d == 0.0) fail(KS_ERR_DIVERGED, "scf: singular Pulay system");
+      for (int i = 0; i < n; ++i) {
+        if (i == c) continue;
+        const double f = B[i * (n + 1) + c] / d;
+        for (int j = c; j <= n; ++j) B[i * (n + 1) + j] -= f * B[c * (n + 1) + j];
+      }
+    }
+    std::vector<double> alpha(m);
+    for (int i = 0; i < m; ++i) alpha[i] = B[i * (n + 1) + n] / B[i * (n + 1) + i];
+    return alpha;
   }
 
   // ------------------------------------------------------------------------------------------
@@ -817,6 +895,10 @@ template <typename T> class Engine final : public EngineBase {
   T* nin_ = nullptr;                // SCF input density
   double* resid_dev_ = nullptr;     // SCF residual
   double* dip_partials_ = nullptr;  // dipole block partials
+  T* hist_n_[PULAY_MAX] = {};       // Pulay history: input densities and residuals (allocated on first use)
+  T* hist_r_[PULAY_MAX] = {};
+  double* pulay_partials_ = nullptr;
+  double* pulay_out_ = nullptr;
   double* dipoles_dev_ = nullptr;   // [MAX_STEPS_CHUNK][3] dipoles of a chunk of real-time steps
   double* parts_ = nullptr;
   double2* dots_ = nullptr;

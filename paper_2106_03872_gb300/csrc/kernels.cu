@@ -297,6 +297,52 @@ __global__ void k_density_mix(const T* __restrict__ nout, T* __restrict__ nin, s
   if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
 }
 
+// Pulay mixing, store step: R = nout - nin into hr, nin into hn (the history slot), and the
+// block partials of sum |R|, sum R^2 and sum R r_q for the other history residuals r_q.
+template <typename T>
+__global__ void k_pulay_store(const T* __restrict__ nout, const T* __restrict__ nin, T* __restrict__ hn,
+                              T* __restrict__ hr, size_t N3, PulayRefs<T> refs, double* __restrict__ partials) {
+  double acc[2 + PULAY_MAX];
+#pragma unroll
+  for (int i = 0; i < 2 + PULAY_MAX; ++i) acc[i] = 0.0;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
+    const T a = nin[j];
+    const T rr = nout[j] - a;
+    hn[j] = a;
+    hr[j] = rr;
+    const double rd = (double)rr;
+    acc[0] += fabs(rd);
+    acc[1] += rd * rd;
+#pragma unroll
+    for (int q = 0; q < PULAY_MAX; ++q)
+      if (q < refs.m) acc[2 + q] += rd * (double)refs.r[q][j];
+  }
+  block_sum<2 + PULAY_MAX>(acc);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 2 + PULAY_MAX; ++i) partials[blockIdx.x * (2 + PULAY_MAX) + i] = acc[i];
+}
+
+__global__ void k_pulay_finish(const double* __restrict__ partials, int nblocks, double dV, double* __restrict__ out) {
+  const int i = threadIdx.x;
+  if (blockIdx.x == 0 && i < 2 + PULAY_MAX) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partials[b * (2 + PULAY_MAX) + i];
+    out[i] = dV * s;
+  }
+}
+
+// nin = sum_i a_i (n_i + mix r_i) over the history pairs
+template <typename T>
+__global__ void k_pulay_mix(T* __restrict__ nin, size_t N3, PulayMix<T> p) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < PULAY_MAX; ++q)
+      if (q < p.m) v += p.a[q] * ((double)p.n[q][j] + p.mix * (double)p.r[q][j]);
+    nin[j] = (T)v;
+  }
+}
+
 __global__ void k_sum_partials(const double* __restrict__ partials, int nblocks, double scale, double* __restrict__ out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double s = 0.0;
@@ -519,6 +565,21 @@ void density_mix(const T* nout, T* nin, int N3, double mix, double* partials, in
   KS_CHECK_LAUNCH();
 }
 
+template <typename T>
+void pulay_store(const T* nout, const T* nin, T* hn, T* hr, int N3, const PulayRefs<T>& refs, double* partials,
+                 int nblocks, double dV, double* out, cudaStream_t s) {
+  k_pulay_store<T><<<nblocks, RED_THREADS, 0, s>>>(nout, nin, hn, hr, (size_t)N3, refs, partials);
+  KS_CHECK_LAUNCH();
+  k_pulay_finish<<<1, 32, 0, s>>>(partials, nblocks, dV, out);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void pulay_mix(T* nin, int N3, const PulayMix<T>& p, cudaStream_t s) {
+  k_pulay_mix<T><<<blocks_for((size_t)N3, 256, 2048), 256, 0, s>>>(nin, (size_t)N3, p);
+  KS_CHECK_LAUNCH();
+}
+
 void sum_partials(const double* partials, int nblocks, double scale, double* out, cudaStream_t s) {
   k_sum_partials<<<1, 32, 0, s>>>(partials, nblocks, scale, out);
   KS_CHECK_LAUNCH();
@@ -578,6 +639,9 @@ void real_to_double(const T* in, double* out, size_t n, cudaStream_t s) {
   template void poisson_multiply<T>(cplx<T>*, int, double, T, cudaStream_t);                                    \
   template void hxc_combine<T>(const T*, const cplx<T>*, const T*, T*, double*, int, int, cudaStream_t);        \
   template void density_mix<T>(const T*, T*, int, double, double*, int, cudaStream_t);                          \
+  template void pulay_store<T>(const T*, const T*, T*, T*, int, const PulayRefs<T>&, double*, int, double, double*, \
+                               cudaStream_t);                                                                   \
+  template void pulay_mix<T>(T*, int, const PulayMix<T>&, cudaStream_t);                                        \
   template void multiply_phase<T>(cplx<T>*, int, double, const double*, cudaStream_t);                          \
   template void dipole<T>(const T*, int, double, double*, int, double*, cudaStream_t);                          \
   template void state_dots<T>(const cplx<T>*, const cplx<T>*, int, int, double2*, cudaStream_t);                \

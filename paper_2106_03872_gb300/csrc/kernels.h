@@ -63,6 +63,25 @@ void hxc_finish(const double* partials, int nblocks, double dV, double* parts, c
 template <typename T> void density_mix(const T* nout, T* nin, int N3, double mix, double* partials, int nblocks,
                                        cudaStream_t s);
 void sum_partials(const double* partials, int nblocks, double scale, double* out, cudaStream_t s);
+// Pulay (DIIS) density mixing.  History of at most PULAY_MAX (n_in, R) pairs.
+constexpr int PULAY_MAX = 8;
+template <typename T> struct PulayRefs {
+  const T* r[PULAY_MAX];   // the other history residuals
+  int m;
+};
+template <typename T> struct PulayMix {
+  const T* n[PULAY_MAX];
+  const T* r[PULAY_MAX];
+  double a[PULAY_MAX];
+  double mix;
+  int m;
+};
+// hr = nout - nin, hn = nin; out (device, 2 + PULAY_MAX) = dV * {sum |R|, sum R^2, sum R r_q};
+// partials holds nblocks * (2 + PULAY_MAX) doubles
+template <typename T> void pulay_store(const T* nout, const T* nin, T* hn, T* hr, int N3, const PulayRefs<T>& refs,
+                                       double* partials, int nblocks, double dV, double* out, cudaStream_t s);
+// nin = sum_i a_i (n_i + mix r_i)
+template <typename T> void pulay_mix(T* nin, int N3, const PulayMix<T>& p, cudaStream_t s);
 constexpr int HXC_BLOCKS = 296;
 
 // dots[b] = sum_g conj(a[b][g]) b[b][g] (FP64 accumulation, fixed order)

@@ -72,7 +72,7 @@ def load():
         "ks_orthonormalize": [P, dp, P],
         "ks_rayleigh_ritz": [P, dp, P],
         "ks_block_iteration": [P, ct.c_int, dp, P],
-        "ks_scf": [P, ct.c_int, ct.c_int, ct.c_double, ct.c_double, dp, dp, ip, P],
+        "ks_scf": [P, ct.c_int, ct.c_int, ct.c_int, ct.c_double, ct.c_int, ct.c_double, dp, dp, ip, P],
         "ks_td_step": [P, ct.c_double, ct.c_int, ct.c_int, ct.c_int, dp, dp, P],
         "ks_td_step_dipole": [P, ct.c_double, ct.c_int, ct.c_int, ct.c_int, dp, dp, dp, P],
         "ks_kick": [P, dp, P],
@@ -243,14 +243,15 @@ class Grid:
         check(load().ks_block_iteration(self.h, int(niter), _dptr(e), _stream_ptr(stream)))
         return e
 
-    def scf(self, max_iter, eig_iters=2, mix=0.3, tol=0.0, stream=None):
-        """Self-consistent field with linear mixing: returns (Ritz values [iters][nstates],
-        density residuals [iters]) of the iterations run."""
+    def scf(self, max_iter, eig_iters=2, mix=0.3, tol=0.0, stream=None, mixer="linear", history=4):
+        """Self-consistent field with linear or Pulay mixing: returns (Ritz values
+        [iters][nstates], density residuals [iters]) of the iterations run."""
         eig = np.zeros((max(max_iter, 1), self.nstates))
         res = np.zeros(max(max_iter, 1))
         done = ct.c_int(0)
-        check(load().ks_scf(self.h, int(max_iter), int(eig_iters), float(mix), float(tol), _dptr(eig), _dptr(res),
-                            ct.byref(done), _stream_ptr(stream)))
+        mode = {"linear": 0, "pulay": 1}[mixer] if isinstance(mixer, str) else int(mixer)
+        check(load().ks_scf(self.h, int(max_iter), int(eig_iters), mode, float(mix), int(history), float(tol),
+                            _dptr(eig), _dptr(res), ct.byref(done), _stream_ptr(stream)))
         return eig[:done.value], res[:done.value]
 
     def profile(self, mode):

@@ -109,3 +109,26 @@ def test_scf_residual_contracts_and_tolerance_stops():
     assert np.max(np.abs(ko.gram(c_out) - np.eye(6))) <= 1e-12
     eps2, res2, _, _ = ko.scf(cell, c, 12, 5, 0.3, tol=res[6] * 1.0000001)
     assert len(res2) == 7 and np.allclose(res2, res[:7]) and np.allclose(eps2, eps[:7])
+
+
+def test_pulay_coefficients_closed_forms():
+    """Two residuals R and -R: the combination 1/2 R + 1/2 (-R) = 0 is the minimiser.  Two
+    orthogonal residuals of squared norms a and b: alpha = (b, a) / (a + b) (the weighted
+    minimum of alpha_1^2 a + alpha_2^2 b on alpha_1 + alpha_2 = 1)."""
+    A = np.array([[2.0, -2.0], [-2.0, 2.0]])
+    assert np.allclose(ko.pulay_coefficients(A), [0.5, 0.5], atol=1e-6)
+    a, b = 3.0, 0.5
+    assert np.allclose(ko.pulay_coefficients(np.diag([a, b])), [b / (a + b), a / (a + b)], atol=1e-10)
+
+
+def test_scf_pulay_with_one_pair_is_linear_and_converges_faster():
+    """History 1 reduces Pulay mixing to linear mixing (alpha = 1); with history 4 the
+    residual falls below linear mixing's after the same number of iterations."""
+    cell = make_cell(natoms=4, depth=-3.0)
+    c = inputs.random_coeffs(9, 6, cell.nG)
+    e_lin, r_lin, _, _ = ko.scf(cell, c, 5, 5, 0.3)
+    e_p1, r_p1, _, _ = ko.scf(cell, c, 5, 5, 0.3, mixer="pulay", history=1)
+    assert np.allclose(r_p1, r_lin, rtol=1e-10) and np.allclose(e_p1, e_lin, atol=1e-10)
+    _, r_lin12, _, _ = ko.scf(cell, c, 12, 5, 0.3)
+    _, r_p4, _, _ = ko.scf(cell, c, 12, 5, 0.3, mixer="pulay", history=4)
+    assert r_p4[-1] < r_lin12[-1]
