@@ -144,6 +144,16 @@ ks_status ks_rayleigh_ritz(ks_grid g, double* eig_host, void* stream);
  * Ritz values of the last iteration.  Synchronous. */
 ks_status ks_block_iteration(ks_grid g, int niter, double* eig_host, void* stream);
 
+/* Block iterations with a choice of preconditioner: precond 0 is ks_block_iteration; precond 1
+ * is the Teter-preconditioned steepest descent (Sec. "Ground-state solution", applied in
+ * Fourier space), per iteration CholQR -> H Psi -> Rayleigh-Ritz -> for each state i with
+ * residual R_i = H psi_i - eps_i psi_i and T_i = sum_G |G|^2/2 |R_iG|^2 / sum_G |R_iG|^2
+ * (floored at (2 pi / L)^2 / 2, the smallest nonzero plane-wave kinetic energy):
+ *   psi_iG <- psi_iG - K(|G|^2 / (2 T_i)) R_iG / (T_i + max V_loc - min V_loc + proj_D),
+ *   K(x) = (27 + 18x + 12x^2 + 8x^3) / (27 + 18x + 12x^2 + 8x^3 + 16x^4)
+ * (states with R_i = 0 unchanged).  eig_host as for ks_block_iteration.  Synchronous. */
+ks_status ks_block_iteration_pc(ks_grid g, int niter, int precond, double* eig_host, void* stream);
+
 /* Self-consistent field (Sec. "Ground-state solution").  The resident states are
  * orthonormalised (CholQR) and their density is the first input density n_in.  Each SCF
  * iteration:

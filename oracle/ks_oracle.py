@@ -293,6 +293,40 @@ def block_iteration(cell, c, niter, v=None):
     return eps, c
 
 
+def teter_factor(x):
+    """Teter-Payne-Allan preconditioner (the paper's SD preconditioner, applied in Fourier
+    space): K(x) = (27 + 18x + 12x^2 + 8x^3) / (27 + 18x + 12x^2 + 8x^3 + 16x^4), with x the
+    plane wave's kinetic energy over that of the residual vector it multiplies."""
+    p = 27.0 + 18.0 * x + 12.0 * x ** 2 + 8.0 * x ** 3
+    return p / (p + 16.0 * x ** 4)
+
+
+def block_iteration_teter(cell, c, niter, v=None):
+    """Preconditioned steepest descent (Sec. "Ground-state solution"), per iteration:
+    CholQR -> H Psi -> Rayleigh-Ritz -> R = H Psi - Psi diag(eps) -> for each state i, with
+    T_i = sum_G |G|^2/2 |R_iG|^2 / sum_G |R_iG|^2 the kinetic energy of its residual vector,
+    floored at that of the smallest nonzero plane wave, (2 pi / L)^2 / 2 (a residual with
+    weight at G = 0 only would give T_i = 0),
+    c_iG <- c_iG - alpha_i K(|G|^2 / (2 T_i)) R_iG, alpha_i = 1 / (T_i + max V_loc - min V_loc + D)
+    (a state with R_i = 0 is left as it is).  Returns (eps of the last Rayleigh-Ritz, final c)."""
+    dv = float(cell.vloc.max() - cell.vloc.min())
+    eps = None
+    for _ in range(niter):
+        c, _ = cholqr(c)
+        hc = apply_h(cell, c, v)
+        eps, _, c, hc = rayleigh_ritz(c, hc)
+        R = hc - eps[:, None] * c
+        r2 = np.real(np.sum(np.abs(R) ** 2, axis=1))
+        tr = np.real(np.sum(0.5 * cell.g2[None, :] * np.abs(R) ** 2, axis=1))
+        live = r2 > 0
+        tmin = 0.5 * (2.0 * np.pi / cell.L) ** 2
+        t = np.maximum(np.where(live, tr / np.where(live, r2, 1.0), tmin), tmin)
+        alpha = np.where(live, 1.0 / (t + dv + cell.D), 0.0)
+        K = teter_factor(0.5 * cell.g2[None, :] / t[:, None])
+        c = c - alpha[:, None] * K * R
+    return eps, c
+
+
 # ----------------------------------------------------------------------------------------------
 # Hartree (Sec. "Poisson solver", periodic) and LDA Slater exchange
 # ----------------------------------------------------------------------------------------------

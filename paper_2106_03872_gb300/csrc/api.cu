@@ -192,6 +192,17 @@ ks_status ks_dipole(ks_grid g, double* d_out, void* stream) {
   });
 }
 
+ks_status ks_block_iteration_pc(ks_grid g, int niter, int precond, double* eig_host, void* stream) {
+  return guarded([&] {
+    need(g != nullptr, "grid is NULL");
+    need(niter >= 0 && (precond == 0 || precond == 1), "block_iteration_pc: niter >= 0, precond 0 or 1");
+    if (precond == 0)
+      g->eng->block_iteration(niter, eig_host, as_stream(stream));
+    else
+      g->eng->block_iteration_teter(niter, eig_host, as_stream(stream));
+  });
+}
+
 ks_status ks_scf(ks_grid g, int max_iter, int eig_iters, int mixer, double mix, int history, double tol,
                  double* eig_out, double* resid_out, int* iters_done, void* stream) {
   return guarded([&] {

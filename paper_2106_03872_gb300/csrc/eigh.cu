@@ -335,9 +335,16 @@ __global__ void __launch_bounds__(EH_THREADS, 1)
     const float2 al = make_float2(__shfl_sync(FULL, x[0].x, 0), __shfl_sync(FULL, x[0].y, 0));
     float2 tk, sc = make_float2(0.f, 0.f);
     float ek;
+    const float s2 = al.x * al.x + al.y * al.y + xn2;
     if (xn2 == 0.f && al.y == 0.f) {
       tk = make_float2(0.f, 0.f);
       ek = al.x;
+    } else if (s2 < 1e-30f) {
+      // a column already reduced up to rounding noise (|x| < 1e-15): no reflection and a zero
+      // off-diagonal element, which moves eigenvalues by < 1e-15; forming the reflector from
+      // such a column would underflow its squares and divide by zero
+      tk = make_float2(0.f, 0.f);
+      ek = 0.f;
     } else {
       const float beta = -copysignf(sqrtf(al.x * al.x + al.y * al.y + xn2), al.x);
       const float rb = __frcp_rn(beta);

@@ -201,6 +201,7 @@ template <typename T> class Engine final : public EngineBase {
     nin_ = alloc<T>(N3);
     resid_dev_ = alloc<double>(1);
     dip_partials_ = alloc<double>(HXC_BLOCKS * 3);
+    trr_ = alloc<double2>(ns_);
     dipoles_dev_ = alloc<double>(3 * MAX_STEPS_CHUNK);
     parts_ = alloc<double>(4);
     dots_ = alloc<double2>(ns_);
@@ -538,6 +539,34 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaStreamSynchronize(s));
     check_tc_status(s);
     if (st) fail(KS_ERR_NOT_POSDEF, "block iteration: Gram matrix not positive definite at column %d", st - 1);
+  }
+
+  // ------------------------------------------------------------------------------------------
+  // Teter-preconditioned steepest descent (Sec. Ground-state solution).  The preconditioner
+  // scales every state per G, so H psi of the update is no rotation of [H psi; H^2 psi]: each
+  // iteration runs CholQR, H psi, Rayleigh-Ritz and the update in order.
+  // ------------------------------------------------------------------------------------------
+  void block_iteration_teter(int niter, double* eig_host, cudaStream_t s) override {
+    if (niter < 0) fail(KS_ERR_ARG, "niter=%d", niter);
+    hpsi_valid_ = false;
+    const double shift = (g_.vmax - g_.vmin) + g_.D;
+    const double tmin = 0.5 * (2.0 * M_PI / g_.L) * (2.0 * M_PI / g_.L);   // smallest nonzero |G|^2 / 2
+    KS_CUDA(cudaMemsetAsync(status_, 0, sizeof(int), s));
+    for (int it = 0; it < niter; ++it) {
+      cholqr_factor(s);
+      cholqr_rotate(s);
+      apply_h(psi_, hpsi_, ns_, s);
+      rr_core(s);
+      ProfScope p(prof, "teter_update", s);
+      teter_update<T>(psi_, hpsi_, t_.g2half, eig_, trr_, shift, tmin, g_.nG, ns_, s);
+    }
+    int st = 0;
+    KS_CUDA(cudaMemcpyAsync(&st, status_, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (eig_host) KS_CUDA(cudaMemcpyAsync(eig_host, eig_, ns_ * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    check_tc_status(s);
+    if (st) fail(KS_ERR_NOT_POSDEF, "preconditioned block iteration: Gram matrix not positive definite at column %d",
+                 st - 1);
   }
 
   // ------------------------------------------------------------------------------------------
@@ -895,6 +924,7 @@ template <typename T> class Engine final : public EngineBase {
   T* nin_ = nullptr;                // SCF input density
   double* resid_dev_ = nullptr;     // SCF residual
   double* dip_partials_ = nullptr;  // dipole block partials
+  double2* trr_ = nullptr;          // per-state residual kinetic sums of the preconditioned update
   T* hist_n_[PULAY_MAX] = {};       // Pulay history: input densities and residuals (allocated on first use)
   T* hist_r_[PULAY_MAX] = {};
   double* pulay_partials_ = nullptr;

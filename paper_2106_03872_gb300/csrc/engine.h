@@ -97,6 +97,7 @@ class EngineBase {
   virtual void orthonormalize(double* S_host, cudaStream_t s) = 0;
   virtual void rayleigh_ritz(double* eig_host, cudaStream_t s) = 0;
   virtual void block_iteration(int niter, double* eig_host, cudaStream_t s) = 0;
+  virtual void block_iteration_teter(int niter, double* eig_host, cudaStream_t s) = 0;
   virtual void scf(int max_iter, int eig_iters, int mixer, double mix, int history, double tol, double* eig_out,
                    double* resid_out, int* iters_done, cudaStream_t s) = 0;
   virtual void td_steps(double dt, int nsteps, int propagator, int hartree_xc, double* norm_out,

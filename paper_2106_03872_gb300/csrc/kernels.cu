@@ -343,6 +343,49 @@ __global__ void k_pulay_mix(T* __restrict__ nin, size_t N3, PulayMix<T> p) {
   }
 }
 
+// Teter-preconditioned SD, step 1 (one block per state): tr[b] = sum_g g2half |R|^2 and
+// r2[b] = sum_g |R|^2 of the residual R = hpsi - eig[b] psi.
+template <typename T>
+__global__ void k_residual_kinetic(const cplx<T>* __restrict__ psi, const cplx<T>* __restrict__ hpsi,
+                                   const T* __restrict__ g2h, const double* __restrict__ eig, int nG,
+                                   double2* __restrict__ out) {
+  const int b = blockIdx.x;
+  const double e = eig[b];
+  double acc[2] = {0.0, 0.0};
+  for (int g = threadIdx.x; g < nG; g += blockDim.x) {
+    const cplx<T> p = psi[(size_t)b * nG + g], h = hpsi[(size_t)b * nG + g];
+    const double rx = (double)h.x - e * (double)p.x, ry = (double)h.y - e * (double)p.y;
+    const double r2 = rx * rx + ry * ry;
+    acc[0] += (double)g2h[g] * r2;
+    acc[1] += r2;
+  }
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) out[b] = make_double2(acc[0], acc[1]);
+}
+
+// Step 2: psi -= alpha_b K(g2half / T_b) R with T_b = max(tr / r2, tmin), alpha_b = 1 / (T_b + shift);
+// K(x) = (27 + 18x + 12x^2 + 8x^3) / (27 + 18x + 12x^2 + 8x^3 + 16x^4).  States with R = 0 stay.
+template <typename T>
+__global__ void k_teter_update(cplx<T>* __restrict__ psi, const cplx<T>* __restrict__ hpsi, const T* __restrict__ g2h,
+                               const double* __restrict__ eig, const double2* __restrict__ trr, double shift,
+                               double tmin, int nG) {
+  const int b = blockIdx.y;
+  const double2 q = trr[b];
+  if (!(q.y > 0.0)) return;                                          // uniform per block
+  const double t = fmax(q.x / q.y, tmin);
+  const T inv_t = (T)(1.0 / t), alpha = (T)(1.0 / (t + shift)), e = (T)eig[b];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nG; g += gridDim.x * blockDim.x) {
+    const T x = g2h[g] * inv_t;
+    const T p = T(27) + x * (T(18) + x * (T(12) + x * T(8)));
+    const T k = alpha * p / (p + T(16) * x * x * x * x);
+    cplx<T> c = psi[(size_t)b * nG + g];
+    const cplx<T> h = hpsi[(size_t)b * nG + g];
+    c.x -= k * (h.x - e * c.x);
+    c.y -= k * (h.y - e * c.y);
+    psi[(size_t)b * nG + g] = c;
+  }
+}
+
 __global__ void k_sum_partials(const double* __restrict__ partials, int nblocks, double scale, double* __restrict__ out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double s = 0.0;
@@ -580,6 +623,16 @@ void pulay_mix(T* nin, int N3, const PulayMix<T>& p, cudaStream_t s) {
   KS_CHECK_LAUNCH();
 }
 
+template <typename T>
+void teter_update(cplx<T>* psi, const cplx<T>* hpsi, const T* g2half, const double* eig, double2* trr, double shift,
+                  double tmin, int nG, int n, cudaStream_t s) {
+  k_residual_kinetic<T><<<n, RED_THREADS, 0, s>>>(psi, hpsi, g2half, eig, nG, trr);
+  KS_CHECK_LAUNCH();
+  k_teter_update<T><<<dim3(blocks_for((size_t)nG, 256, 64), n), 256, 0, s>>>(psi, hpsi, g2half, eig, trr, shift,
+                                                                            tmin, nG);
+  KS_CHECK_LAUNCH();
+}
+
 void sum_partials(const double* partials, int nblocks, double scale, double* out, cudaStream_t s) {
   k_sum_partials<<<1, 32, 0, s>>>(partials, nblocks, scale, out);
   KS_CHECK_LAUNCH();
@@ -642,6 +695,9 @@ void real_to_double(const T* in, double* out, size_t n, cudaStream_t s) {
   template void pulay_store<T>(const T*, const T*, T*, T*, int, const PulayRefs<T>&, double*, int, double, double*, \
                                cudaStream_t);                                                                   \
   template void pulay_mix<T>(T*, int, const PulayMix<T>&, cudaStream_t);                                        \
+  template void teter_update<T>(cplx<T>*, const cplx<T>*, const T*, const double*, double2*, double, double, int, \
+                                int,                                                                            \
+                                cudaStream_t);                                                                  \
   template void multiply_phase<T>(cplx<T>*, int, double, const double*, cudaStream_t);                          \
   template void dipole<T>(const T*, int, double, double*, int, double*, cudaStream_t);                          \
   template void state_dots<T>(const cplx<T>*, const cplx<T>*, int, int, double2*, cudaStream_t);                \

@@ -82,6 +82,11 @@ template <typename T> void pulay_store(const T* nout, const T* nin, T* hn, T* hr
                                        double* partials, int nblocks, double dV, double* out, cudaStream_t s);
 // nin = sum_i a_i (n_i + mix r_i)
 template <typename T> void pulay_mix(T* nin, int N3, const PulayMix<T>& p, cudaStream_t s);
+// Teter-preconditioned SD update of n states [n][nG]: R = hpsi - eig psi, T_b = kinetic energy
+// of R_b (sum g2half |R|^2 / sum |R|^2) floored at tmin, psi_b -= K(g2half / T_b) R_b / (T_b + shift).
+// trr (device, n double2) receives (sum g2half |R|^2, sum |R|^2) per state.
+template <typename T> void teter_update(cplx<T>* psi, const cplx<T>* hpsi, const T* g2half, const double* eig,
+                                        double2* trr, double shift, double tmin, int nG, int n, cudaStream_t s);
 constexpr int HXC_BLOCKS = 296;
 
 // dots[b] = sum_g conj(a[b][g]) b[b][g] (FP64 accumulation, fixed order)

@@ -23,7 +23,7 @@ PRECISIONS = {"fp64": KS_FP64, "bf16x3": KS_MIXED_BF16X3, "tf32": KS_MIXED_TF32}
 # Every symbol declared in include/ks.h.
 EXPORTS = ["ks_count_gvectors", "ks_grid_create", "ks_grid_destroy", "ks_grid_gvectors", "ks_grid_device_bytes",
            "ks_get_vloc", "ks_set_states", "ks_get_states", "ks_states_device", "ks_apply_h", "ks_apply_h_host",
-           "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_scf", "ks_td_step", "ks_td_step_dipole", "ks_kick", "ks_dipole",
+           "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_block_iteration_pc", "ks_scf", "ks_td_step", "ks_td_step_dipole", "ks_kick", "ks_dipole",
            "ks_serve_create", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info",
            "ks_profile", "ks_profile_read", "ks_profile_span", "ks_kernel_launches", "ks_overlap_noalloc", "ks_last_error"]
 
@@ -72,6 +72,7 @@ def load():
         "ks_orthonormalize": [P, dp, P],
         "ks_rayleigh_ritz": [P, dp, P],
         "ks_block_iteration": [P, ct.c_int, dp, P],
+        "ks_block_iteration_pc": [P, ct.c_int, ct.c_int, dp, P],
         "ks_scf": [P, ct.c_int, ct.c_int, ct.c_int, ct.c_double, ct.c_int, ct.c_double, dp, dp, ip, P],
         "ks_td_step": [P, ct.c_double, ct.c_int, ct.c_int, ct.c_int, dp, dp, P],
         "ks_td_step_dipole": [P, ct.c_double, ct.c_int, ct.c_int, ct.c_int, dp, dp, dp, P],
@@ -238,9 +239,15 @@ class Grid:
         check(load().ks_rayleigh_ritz(self.h, _dptr(e), _stream_ptr(stream)))
         return e
 
-    def block_iteration(self, niter, stream=None):
+    def block_iteration(self, niter, stream=None, precond=None):
+        """niter block iterations; precond "teter" selects the Teter-preconditioned steepest
+        descent.  Returns the Ritz values of the last iteration."""
         e = np.zeros(self.nstates)
-        check(load().ks_block_iteration(self.h, int(niter), _dptr(e), _stream_ptr(stream)))
+        if precond is None:
+            check(load().ks_block_iteration(self.h, int(niter), _dptr(e), _stream_ptr(stream)))
+        else:
+            mode = {"none": 0, "teter": 1}[precond]
+            check(load().ks_block_iteration_pc(self.h, int(niter), mode, _dptr(e), _stream_ptr(stream)))
         return e
 
     def scf(self, max_iter, eig_iters=2, mix=0.3, tol=0.0, stream=None, mixer="linear", history=4):

@@ -637,3 +637,36 @@ def test_td_dipole_after_kick_parity(ks, prec):
     assert np.array_equal(n2, norms) and np.array_equal(e2, energies)
     g.close()
     g2.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# Teter-preconditioned steepest descent (Sec. "Ground-state solution")
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_block_iteration_teter_parity(ks, prec):
+    cell = inputs.small_cell(12.0, 32, 4, 10, 59, depth=-3.0)
+    ref = ko.Cell(cell)
+    c = inputs.random_coeffs(59, 10, ref.nG)
+    g = ks.Grid(cell, prec=prec)
+    g.set_states(c)
+    eps = g.block_iteration(6, precond="teter")
+    eps_ref, c_ref = ko.block_iteration_teter(ref, c, 6)
+    if prec == "fp64":
+        assert np.max(np.abs(eps - eps_ref)) <= 1e-10
+        assert rel(g.get_states(), c_ref) <= 1e-9
+    else:
+        assert np.max(np.abs(eps - eps_ref)) <= 1e-4 * max(1.0, np.max(np.abs(eps_ref)))
+    g.close()
+
+
+def test_block_iteration_teter_free_electron_limit(ks):
+    """No atoms: the preconditioned iteration reaches the G = 0 and |m| = 1 shells."""
+    cell = inputs.small_cell(4.0, 12, 0, 7, 60)
+    ref = ko.Cell(cell)
+    c = inputs.random_coeffs(60, 7, ref.nG)
+    for prec, tol in (("fp64", 1e-10), ("bf16x3", 2e-5)):
+        g = ks.Grid(cell, prec=prec)
+        g.set_states(c)
+        eps = g.block_iteration(80, precond="teter")
+        assert np.allclose(eps, np.sort(0.5 * ref.g2)[:7], atol=tol)
+        g.close()

@@ -132,3 +132,24 @@ def test_scf_pulay_with_one_pair_is_linear_and_converges_faster():
     _, r_lin12, _, _ = ko.scf(cell, c, 12, 5, 0.3)
     _, r_p4, _, _ = ko.scf(cell, c, 12, 5, 0.3, mixer="pulay", history=4)
     assert r_p4[-1] < r_lin12[-1]
+
+
+def test_teter_block_iteration_free_electron_fixed_points_and_limit():
+    """The preconditioner changes no fixed point: the free-electron limit still converges to
+    the G = 0 and |m| = 1 shells."""
+    cell = make_cell(L=4.0, N=12, natoms=0, ecut=20.0)
+    c = inputs.random_coeffs(3, 7, cell.nG)
+    eps, _ = ko.block_iteration_teter(cell, c, 80)
+    assert np.allclose(eps, np.sort(0.5 * cell.g2)[:7], atol=1e-12)
+
+
+def test_teter_preconditioning_converges_faster():
+    """With atoms: after the same number of iterations the preconditioned Ritz values lie
+    below the plain steepest-descent ones (Ritz values bound the eigenvalues from above)."""
+    cell = make_cell(natoms=4, depth=-3.0)
+    c = inputs.random_coeffs(5, 6, cell.nG)
+    e_sd, _ = ko.block_iteration(cell, c, 15)
+    e_pc, _ = ko.block_iteration_teter(cell, c, 15)
+    assert np.sum(e_pc) < np.sum(e_sd) - 1e-3
+    e_pc2, _ = ko.block_iteration_teter(cell, c, 30)
+    assert np.all(e_pc2 <= e_pc + 1e-9)
