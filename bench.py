@@ -394,10 +394,15 @@ def main_gpu(args):
     # ---- Teter-preconditioned steepest descent on the gs96 cell (non-pipelined: CholQR, H psi,
     # Rayleigh-Ritz and the preconditioned update in order)
     teter = None
+    forces = None
     if not args.no_scf:
         gp = ks.Grid(cell, prec="bf16x3")
         gp.set_states(c0)
         tp, _, pe = timed_steps(gp, 3, 1, lambda: gp.block_iteration(1, stream, precond="teter"), profile=True)
+        tf, _, fe = timed_steps(gp, 2, 1, lambda: gp.forces(stream), profile=False)
+        forces = {"workload": "gs96, forces on the 64 atoms from the 128 states (Eq. 11): 4 full-grid transforms "
+                              "per state, real-space projections, separable local term",
+                  "ms_per_call": statistics.mean(tf)}
         teter = {"workload": "gs96, one Teter-preconditioned block iteration per call",
                  "ms_per_iteration": statistics.mean(tp),
                  "stages_ms_per_iteration": {k: v[0] / len(tp) for k, v in pe.items() if v[0] > 0}}
@@ -419,7 +424,7 @@ def main_gpu(args):
         "roofline": rl, "side_stream_roofline": rl_side,
         "cpu_baseline": cpu_baseline_obj(cpu) if cpu else None, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk.summary(), "hpsi_only": hpsi_only, "fp64_gpu": fp64, "td": td,
-        "scf": scf, "teter": teter, "serve": serve,
+        "scf": scf, "teter": teter, "forces": forces, "serve": serve,
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in entries.items() if v[0] > 0},
     }
     print(json.dumps(line), flush=True)

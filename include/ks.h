@@ -202,6 +202,16 @@ ks_status ks_td_step_dipole(ks_grid g, double dt, int nsteps, int propagator, in
  * boundary (a molecule in a box).  Asynchronous on stream. */
 ks_status ks_kick(ks_grid g, const double* kappa, void* stream);
 
+/* Forces on the atoms from the orbital gradients (Sec. "Forces", Eq. 11), for the resident
+ * states with their occupations:
+ *   F_I = -sum_k f_k [<grad psi_k| v_I |psi_k> + c.c.],
+ * v_I the atom's local Gaussian (27 periodic images) and KB projectors; the overall sign is
+ * that of -dE/dR_I (the paper prints the opposite).  The gradient is i G c in Fourier space;
+ * local part dV sum_j v_I(r_j) sum_k f_k 2 Re(conj(grad psi_k) psi_k)(r_j), nonlocal part
+ * sum_k f_k sum_l 2 D Re(conj(<beta_Il|grad psi_k>) <beta_Il|psi_k>) on the grid.  f_out
+ * [natoms][3] (host, Ha/bohr); nothing is written when natoms = 0.  Synchronous. */
+ks_status ks_forces(ks_grid g, double* f_out, void* stream);
+
 /* Dipole of the resident states' density, d_out[3] (host) = dV sum_j (r_j - L/2) n(r_j).
  * Synchronous. */
 ks_status ks_dipole(ks_grid g, double* d_out, void* stream);

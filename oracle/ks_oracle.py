@@ -476,6 +476,43 @@ def td_step(cell, c, dt, propagator="etrs", hartree_xc=True):
     return out, norm_t, energy_t
 
 
+def atom_potential(cell, R):
+    """The local potential of one atom at R: A sum_{27 images} exp(-|r - R - L n|^2 / (2 w^2))."""
+    x = np.arange(cell.N) * cell.h
+    v = np.zeros((cell.N,) * 3)
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            for cc in (-1, 0, 1):
+                C = R + cell.L * np.array([a, b, cc], float)
+                gx, gy, gz = (np.exp(-(x - C[k]) ** 2 / (2.0 * cell.width ** 2)) for k in range(3))
+                v += cell.depth * gx[:, None, None] * gy[None, :, None] * gz[None, None, :]
+    return v
+
+
+def forces(cell, c):
+    """Forces on the atoms from the orbital gradients (Eq. 11), F_I = -sum_k f_k
+    [<grad phi_k| v_I |phi_k> + c.c.], v_I the local and KB nonlocal potential of atom I; the
+    overall sign is that of -dE/dR_I (the printed Eqs. 10-11 carry the opposite one).
+    Local part: -dV sum_j v_I(r_j) g(r_j), g = sum_k f_k 2 Re(conj(grad phi_k) phi_k) on the grid.
+    Nonlocal part: -sum_k f_k sum_l 2 D Re(conj(q_Il) p_Il), p_Il = <beta_Il|phi_k> and
+    q_Il = <beta_Il|grad phi_k> on the grid; grad phi from i G c_G.  Returns [natoms, 3]."""
+    c = np.atleast_2d(c)
+    f = cell.occupations(c.shape[0])
+    psi = to_real(cell, c)
+    G = 2.0 * np.pi / cell.L * cell.m
+    grads = [to_real(cell, 1j * G[None, :, a] * c) for a in range(3)]
+    p = nonlocal_projections(cell, psi)
+    F = np.zeros((cell.natoms, 3))
+    for a in range(3):
+        g = np.einsum("k,kxyz->xyz", f, 2.0 * np.real(np.conj(grads[a]) * psi))
+        for I, R in enumerate(cell.pos):
+            F[I, a] -= cell.dV * np.sum(atom_potential(cell, R) * g)
+        if cell.natoms:
+            q = nonlocal_projections(cell, grads[a])
+            F[:, a] -= np.einsum("k,kil->i", f, 2.0 * cell.D * np.real(np.conj(q) * p))
+    return F
+
+
 def kick(cell, c, kappa):
     """Delta kick (Sec. "Validation with other codes", a time-localised field at t = 0):
     psi(r) <- exp(i kappa . (r - L/2)) psi(r) on the grid, then back to the sphere S."""

@@ -185,6 +185,13 @@ ks_status ks_kick(ks_grid g, const double* kappa, void* stream) {
   });
 }
 
+ks_status ks_forces(ks_grid g, double* f_out, void* stream) {
+  return guarded([&] {
+    need(g != nullptr && f_out != nullptr, "grid or f_out is NULL");
+    g->eng->forces(f_out, as_stream(stream));
+  });
+}
+
 ks_status ks_dipole(ks_grid g, double* d_out, void* stream) {
   return guarded([&] {
     need(g != nullptr && d_out != nullptr, "grid or d_out is NULL");

@@ -86,6 +86,8 @@ struct HostGeometry {
   int xr = 0;                   // columns exist only for |m_x| <= xr (and |m_y| <= xr)
   std::vector<double> vloc;     // [N^3] grid order
   double vmin = 0, vmax = 0;
+  std::vector<double> pos;      // [natoms][3] atom positions (bohr)
+  double vloc_depth = 0, vloc_width = 0;
   // projectors: sphere point lists per atom (grid order within an atom)
   int natoms = 0, nproj = 0;
   double D = 0;

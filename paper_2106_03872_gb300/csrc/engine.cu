@@ -715,6 +715,68 @@ template <typename T> class Engine final : public EngineBase {
   }
 
   // ------------------------------------------------------------------------------------------
+  // Forces from the orbital gradients (Eq. 11, with the sign of -dE/dR_I), one state at a time
+  // through two full-grid buffers: psi(r) and d_alpha psi(r) from i G_alpha c.
+  //   local:    F_Ia -= dV sum_j v_I(r_j) g_a(r_j),  g_a = sum_k f_k 2 Re(conj(d_a psi_k) psi_k)
+  //   nonlocal: F_Ia -= sum_k f_k sum_l 2 D Re(conj(q_Il,a) p_Il)
+  // v_I is the atom's 27-image Gaussian, separable per axis.
+  // ------------------------------------------------------------------------------------------
+  void forces(double* f_host, cudaStream_t s) override {
+    const int N = g_.N, na = g_.natoms, np = g_.nproj;
+    if (na == 0) return;
+    const size_t N3 = (size_t)N * N * N;
+    if (!fw_) {
+      fw_ = alloc<C>(N3);
+      fg_ = alloc<T>(3 * N3);
+      fp_ = alloc<C>((size_t)na * np);
+      fq_ = alloc<C>((size_t)na * np);
+      fnl_ = alloc<double>(3 * (size_t)na);
+      floc_ = alloc<double>(3 * (size_t)na);
+      // per atom and axis: X_a(x) = sum_{s = -1, 0, 1} exp(-(x - R_a - L s)^2 / (2 w^2)) on the grid
+      std::vector<double> xyz(3 * (size_t)na * N);
+      const double w2 = 2.0 * g_.vloc_width * g_.vloc_width;
+      for (int I = 0; I < na; ++I)
+        for (int a = 0; a < 3; ++a)
+          for (int j = 0; j < N; ++j) {
+            double v = 0.0;
+            for (int sh = -1; sh <= 1; ++sh) {
+              const double dx = g_.h * j - g_.pos[3 * I + a] - g_.L * sh;
+              v += std::exp(-dx * dx / w2);
+            }
+            xyz[((size_t)I * 3 + a) * N + j] = v;
+          }
+      fxyz_ = alloc<double>(xyz.size());
+      KS_CUDA(cudaMemcpy(fxyz_, xyz.data(), xyz.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    ProfScope p(prof, "forces", s);
+    KS_CUDA(cudaMemsetAsync(fg_, 0, 3 * N3 * sizeof(T), s));
+    KS_CUDA(cudaMemsetAsync(fnl_, 0, 3 * (size_t)na * sizeof(double), s));
+    const T pscale = T(g_.dV / std::sqrt(g_.omega));   // grids hold Omega^{1/2} psi
+    for (int b = 0; b < ns_; ++b) {
+      const C* st = psi_ + (size_t)b * g_.nG;
+      const double f = g_.occ[b];
+      KS_CUDA(cudaMemsetAsync(pwork_, 0, N3 * sizeof(C), s));
+      scatter_sphere<T>(st, pwork_, t_, 1, s);
+      for (int ax = 2; ax >= 0; --ax) fft_axis<T>(pwork_, 1, N, ax, +1, t_.tw, s);
+      nl_project<T>(pwork_, t_, fp_, 1, pscale, s);
+      for (int a = 0; a < 3; ++a) {
+        KS_CUDA(cudaMemsetAsync(fw_, 0, N3 * sizeof(C), s));
+        scatter_grad<T>(st, fw_, t_, a, s);
+        for (int ax = 2; ax >= 0; --ax) fft_axis<T>(fw_, 1, N, ax, +1, t_.tw, s);
+        nl_project<T>(fw_, t_, fq_, 1, pscale, s);
+        grad_accumulate<T>(fw_, pwork_, fg_ + a * N3, (int)N3, T(f), s);
+        nl_force<T>(fp_, fq_, na, np, 2.0 * g_.D * f, fnl_, a, s);
+      }
+    }
+    local_force<T>(fg_, fxyz_, N, na, -g_.dV * g_.vloc_depth / g_.omega, floc_, s);
+    std::vector<double> fl(3 * (size_t)na), fn(3 * (size_t)na);
+    KS_CUDA(cudaMemcpyAsync(fl.data(), floc_, fl.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaMemcpyAsync(fn.data(), fnl_, fn.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < fl.size(); ++i) f_host[i] = fl[i] + fn[i];
+  }
+
+  // ------------------------------------------------------------------------------------------
   // Real-time steps: ETRS + Taylor 4 with shared powers (Eqs. 6-8), or plain Taylor 4.
   // ------------------------------------------------------------------------------------------
   void td_steps(double dt, int nsteps, int propagator, int hartree_xc, double* norm_out, double* energy_out,
@@ -925,6 +987,10 @@ template <typename T> class Engine final : public EngineBase {
   double* resid_dev_ = nullptr;     // SCF residual
   double* dip_partials_ = nullptr;  // dipole block partials
   double2* trr_ = nullptr;          // per-state residual kinetic sums of the preconditioned update
+  C* fw_ = nullptr;                 // forces: gradient grid, accumulators, projections (on first use)
+  T* fg_ = nullptr;
+  C *fp_ = nullptr, *fq_ = nullptr;
+  double *fnl_ = nullptr, *floc_ = nullptr, *fxyz_ = nullptr;
   T* hist_n_[PULAY_MAX] = {};       // Pulay history: input densities and residuals (allocated on first use)
   T* hist_r_[PULAY_MAX] = {};
   double* pulay_partials_ = nullptr;

@@ -104,6 +104,7 @@ class EngineBase {
                         double* energy_out, double* dipole_out, cudaStream_t s) = 0;
   virtual void kick(const double kappa[3], cudaStream_t s) = 0;
   virtual void dipole(double* d_host, cudaStream_t s) = 0;
+  virtual void forces(double* f_host, cudaStream_t s) = 0;
   virtual void randomize_states(uint64_t seed, cudaStream_t s) = 0;
 };
 

@@ -133,6 +133,9 @@ void build_geometry(const ks_cell_desc& d, HostGeometry& g) {
   // ---- V_loc(r) = sum_a A exp(-|r - R_a - L n|^2 / (2 w^2)) over the 27 image shifts -------
   // Terms with |r - R_a - L n| > 10 w are below 2e-22 |A| and are skipped.
   g.vloc.assign((size_t)N * N * N, 0.0);
+  g.pos.assign(d.pos ? d.pos : nullptr, d.pos ? d.pos + 3 * (size_t)d.natoms : nullptr);
+  g.vloc_depth = d.vloc_depth;
+  g.vloc_width = d.vloc_width;
   const double w2 = 2.0 * d.vloc_width * d.vloc_width;
   const double rcut = 10.0 * d.vloc_width;
   for (int a = 0; a < d.natoms; ++a) {

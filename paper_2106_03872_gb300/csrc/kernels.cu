@@ -140,6 +140,67 @@ __global__ void k_multiply_phase(cplx<T>* __restrict__ grid, int N, T h, T L, T 
   }
 }
 
+// Forces (Eq. 11).  grid[gidx[g]] = i G_alpha c_g for one state, G = g0 m, m from the grid
+// index (j < N/2: j, else j - N); the grid must be zeroed before.
+template <typename T>
+__global__ void k_scatter_grad(const cplx<T>* __restrict__ psi, cplx<T>* __restrict__ grid, const int* __restrict__ gidx,
+                               int nG, int N, T g0, int alpha) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nG; g += gridDim.x * blockDim.x) {
+    const int idx = gidx[g];
+    const int j = alpha == 0 ? idx / (N * N) : (alpha == 1 ? (idx / N) % N : idx % N);
+    const T G = g0 * (T)(j < N / 2 ? j : j - N);
+    const cplx<T> c = psi[g];
+    grid[idx] = mk<cplx<T>>(-G * c.y, G * c.x);
+  }
+}
+
+// gacc[j] += w 2 Re(conj(dpsi[j]) psi[j])
+template <typename T>
+__global__ void k_grad_accumulate(const cplx<T>* __restrict__ dpsi, const cplx<T>* __restrict__ psi, T* __restrict__ gacc,
+                                  size_t N3, T w) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
+    const cplx<T> d = dpsi[j], p = psi[j];
+    gacc[j] += w * T(2) * (d.x * p.x + d.y * p.y);
+  }
+}
+
+// fnl[3 I + alpha] -= w sum_l Re(conj(q_Il) p_Il), one thread per atom (states in order)
+template <typename T>
+__global__ void k_nl_force(const cplx<T>* __restrict__ p, const cplx<T>* __restrict__ q, int natoms, int nproj,
+                           double w, double* __restrict__ fnl, int alpha) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= natoms) return;
+  double s = 0.0;
+  for (int l = 0; l < nproj; ++l) {
+    const cplx<T> a = p[I * nproj + l], b = q[I * nproj + l];
+    s += (double)b.x * (double)a.x + (double)b.y * (double)a.y;
+  }
+  fnl[3 * I + alpha] -= w * s;
+}
+
+// floc[3 I + a] = coef sum_j X_I[jx] Y_I[jy] Z_I[jz] g_a[j], one block per atom; xyz holds per
+// atom the three per-axis image sums [natoms][3][N] of the separable Gaussian
+template <typename T>
+__global__ void k_local_force(const T* __restrict__ g, const double* __restrict__ xyz, int N, double coef,
+                              double* __restrict__ floc) {
+  const int I = blockIdx.x;
+  const size_t N3 = (size_t)N * N * N;
+  const double* X = xyz + (size_t)I * 3 * N;
+  const double* Y = X + N;
+  const double* Z = Y + N;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (size_t j = threadIdx.x; j < N3; j += blockDim.x) {
+    const int jz = (int)(j % N), jy = (int)((j / N) % N), jx = (int)(j / ((size_t)N * N));
+    const double v = X[jx] * Y[jy] * Z[jz];
+    acc[0] += v * (double)g[j];
+    acc[1] += v * (double)g[N3 + j];
+    acc[2] += v * (double)g[2 * N3 + j];
+  }
+  block_sum<3>(acc);
+  if (threadIdx.x == 0)
+    for (int a = 0; a < 3; ++a) floc[3 * I + a] = coef * acc[a];
+}
+
 // Block partials of sum_j n_j (r_j - L/2) (three components), r_j = h (jx, jy, jz)
 template <typename T>
 __global__ void k_dipole_partials(const T* __restrict__ n, int N, double h, double L, double* __restrict__ partials) {
@@ -537,6 +598,32 @@ void multiply_phase(cplx<T>* grid, int N, double L, const double kappa[3], cudaS
 }
 
 template <typename T>
+void scatter_grad(const cplx<T>* psi, cplx<T>* grid, const DevTables<T>& t, int alpha, cudaStream_t s) {
+  k_scatter_grad<T><<<blocks_for((size_t)t.nG, 256, 1024), 256, 0, s>>>(psi, grid, t.gidx, t.nG, t.N,
+                                                                         (T)(2.0 * M_PI / t.L), alpha);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void grad_accumulate(const cplx<T>* dpsi, const cplx<T>* psi, T* gacc, int N3, T w, cudaStream_t s) {
+  k_grad_accumulate<T><<<blocks_for((size_t)N3, 256, 2048), 256, 0, s>>>(dpsi, psi, gacc, (size_t)N3, w);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void nl_force(const cplx<T>* p, const cplx<T>* q, int natoms, int nproj, double w, double* fnl, int alpha,
+              cudaStream_t s) {
+  k_nl_force<T><<<(natoms + 127) / 128, 128, 0, s>>>(p, q, natoms, nproj, w, fnl, alpha);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+void local_force(const T* g, const double* xyz, int N, int natoms, double coef, double* floc, cudaStream_t s) {
+  k_local_force<T><<<natoms, RED_THREADS, 0, s>>>(g, xyz, N, coef, floc);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
 void dipole(const T* n, int N, double L, double* partials, int nblocks, double* out, cudaStream_t s) {
   k_dipole_partials<T><<<nblocks, RED_THREADS, 0, s>>>(n, N, L / N, L, partials);
   KS_CHECK_LAUNCH();
@@ -700,6 +787,10 @@ void real_to_double(const T* in, double* out, size_t n, cudaStream_t s) {
                                 cudaStream_t);                                                                  \
   template void multiply_phase<T>(cplx<T>*, int, double, const double*, cudaStream_t);                          \
   template void dipole<T>(const T*, int, double, double*, int, double*, cudaStream_t);                          \
+  template void scatter_grad<T>(const cplx<T>*, cplx<T>*, const DevTables<T>&, int, cudaStream_t);              \
+  template void grad_accumulate<T>(const cplx<T>*, const cplx<T>*, T*, int, T, cudaStream_t);                   \
+  template void nl_force<T>(const cplx<T>*, const cplx<T>*, int, int, double, double*, int, cudaStream_t);       \
+  template void local_force<T>(const T*, const double*, int, int, double, double*, cudaStream_t);               \
   template void state_dots<T>(const cplx<T>*, const cplx<T>*, int, int, double2*, cudaStream_t);                \
   template void axpy2<T>(cplx<T>*, double2, cplx<T>*, double2, const cplx<T>*, const cplx<T>*, size_t, cudaStream_t);           \
   template void random_states<T>(cplx<T>*, size_t, uint64_t, cudaStream_t);                                     \

@@ -37,6 +37,18 @@ template <typename T> void gather_kinetic(const cplx<T>* grid, const cplx<T>* ps
 template <typename T> void multiply_potential(cplx<T>* grid, const T* v, int N3, int nb, cudaStream_t s);
 // one grid [N][N][N]: grid[j] *= exp(i kappa . (r_j - L/2)), r_j = (L/N) (jx, jy, jz)
 template <typename T> void multiply_phase(cplx<T>* grid, int N, double L, const double kappa[3], cudaStream_t s);
+// Forces (Eq. 11): grid[gidx[g]] = i G_alpha c_g of one state (grid zeroed before)
+template <typename T> void scatter_grad(const cplx<T>* psi, cplx<T>* grid, const DevTables<T>& t, int alpha,
+                                        cudaStream_t s);
+// gacc[j] += w 2 Re(conj(dpsi[j]) psi[j])
+template <typename T> void grad_accumulate(const cplx<T>* dpsi, const cplx<T>* psi, T* gacc, int N3, T w,
+                                           cudaStream_t s);
+// fnl[3 I + alpha] -= w sum_l Re(conj(q_Il) p_Il) (one state's projections p, q [natoms][nproj])
+template <typename T> void nl_force(const cplx<T>* p, const cplx<T>* q, int natoms, int nproj, double w, double* fnl,
+                                    int alpha, cudaStream_t s);
+// floc[3 I + a] = coef sum_j X_I[jx] Y_I[jy] Z_I[jz] g_a[j], g [3][N^3], xyz [natoms][3][N]
+template <typename T> void local_force(const T* g, const double* xyz, int N, int natoms, double coef, double* floc,
+                                       cudaStream_t s);
 // out[3] (device) = dV sum_j n_j (r_j - L/2); partials holds nblocks * 3 doubles
 template <typename T> void dipole(const T* n, int N, double L, double* partials, int nblocks, double* out,
                                   cudaStream_t s);

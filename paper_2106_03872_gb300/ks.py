@@ -23,7 +23,7 @@ PRECISIONS = {"fp64": KS_FP64, "bf16x3": KS_MIXED_BF16X3, "tf32": KS_MIXED_TF32}
 # Every symbol declared in include/ks.h.
 EXPORTS = ["ks_count_gvectors", "ks_grid_create", "ks_grid_destroy", "ks_grid_gvectors", "ks_grid_device_bytes",
            "ks_get_vloc", "ks_set_states", "ks_get_states", "ks_states_device", "ks_apply_h", "ks_apply_h_host",
-           "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_block_iteration_pc", "ks_scf", "ks_td_step", "ks_td_step_dipole", "ks_kick", "ks_dipole",
+           "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_block_iteration_pc", "ks_scf", "ks_td_step", "ks_td_step_dipole", "ks_kick", "ks_dipole", "ks_forces",
            "ks_serve_create", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info",
            "ks_profile", "ks_profile_read", "ks_profile_span", "ks_kernel_launches", "ks_overlap_noalloc", "ks_last_error"]
 
@@ -78,6 +78,7 @@ def load():
         "ks_td_step_dipole": [P, ct.c_double, ct.c_int, ct.c_int, ct.c_int, dp, dp, dp, P],
         "ks_kick": [P, dp, P],
         "ks_dipole": [P, dp, P],
+        "ks_forces": [P, dp, P],
         "ks_serve_create": [ct.c_size_t, ct.POINTER(P)],
         "ks_serve_destroy": [P],
         "ks_serve_submit": [P, ct.POINTER(CellDesc), dp, ct.c_int, ct.c_int, ct.c_double,
@@ -307,6 +308,13 @@ class Grid:
         """Delta kick psi <- P_S exp(i kappa . (r - L/2)) psi of every resident state."""
         k = np.ascontiguousarray(kappa, dtype=np.float64).reshape(3)
         check(load().ks_kick(self.h, _dptr(k), _stream_ptr(stream)))
+
+    def forces(self, stream=None):
+        """Forces on the atoms (Eq. 11) from the resident states, [natoms][3] Ha/bohr."""
+        natoms = self.desc.natoms
+        f = np.zeros((max(natoms, 1), 3))
+        check(load().ks_forces(self.h, _dptr(f), _stream_ptr(stream)))
+        return f[:natoms]
 
     def dipole(self, stream=None):
         """dV sum_j (r_j - L/2) n(r_j) of the resident states."""

@@ -670,3 +670,32 @@ def test_block_iteration_teter_free_electron_limit(ks):
         eps = g.block_iteration(80, precond="teter")
         assert np.allclose(eps, np.sort(0.5 * ref.g2)[:7], atol=tol)
         g.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# Forces from the orbital gradients (Sec. "Forces", Eq. 11)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_forces_parity(ks, prec):
+    cell = inputs.small_cell(10.0, 24, 3, 5, 63, depth=-3.0)
+    occ = np.array([2.0, 2.0, 1.5, 1.0, 0.5])
+    ref = ko.Cell(dict(cell, occ=occ))
+    q, _ = ko.cholqr(inputs.random_coeffs(63, 5, ref.nG))
+    q = ko.block_iteration(ref, q, 6)[1]
+    g = ks.Grid(cell, prec=prec, occ=occ)
+    g.set_states(q)
+    F = g.forces()
+    F_ref = ko.forces(ref, q)
+    assert F.shape == (3, 3)
+    scale = np.max(np.abs(F_ref))
+    assert np.max(np.abs(F - F_ref)) <= (1e-10 if prec == "fp64" else 1e-4) * scale
+    g.close()
+
+
+def test_forces_no_atoms(ks):
+    cell = inputs.small_cell(10.0, 24, 0, 3, 64)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec="bf16x3")
+    g.set_states(inputs.random_coeffs(64, 3, ref.nG))
+    assert g.forces().shape == (0, 3)
+    g.close()
