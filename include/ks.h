@@ -162,12 +162,17 @@ ks_status ks_block_iteration_pc(ks_grid g, int niter, int precond, double* eig_h
  *   mixer 0 (static linear): n_in <- n_in + mix R;
  *   mixer 1 (Pulay / DIIS):  with the last `history` (1..8) pairs (n_in_i, R_i) and
  *     alpha minimising |sum_i alpha_i R_i| (dV-weighted L2) subject to sum_i alpha_i = 1,
- *     n_in <- sum_i alpha_i (n_in_i + mix R_i).
+ *     n_in <- sum_i alpha_i (n_in_i + mix R_i);
+ *   mixer 2 (Broyden, the paper's default; Broyden's second method, which updates an
+ *     approximate inverse Jacobian G of R(n_in)): over the last `history` pairs, oldest
+ *     first, G starts at -mix I and takes each secant pair (dn, dR) of consecutive pairs as
+ *     G <- G + (dn - G dR) dR^T / (dR^T dR) (dV-weighted inner products; a pair with dR = 0
+ *     is skipped); n_in <- n_in - G R.  History 1 is linear mixing.
  * Stops after max_iter iterations or once r < tol.  eig_out [max_iter][nstates] (may be
  * NULL) receives each iteration's Ritz values, resid_out [max_iter] (may be NULL) its r,
  * iters_done (may be NULL) the number of iterations run.  Afterwards the states are
  * orthonormal and V is the potential of the last iteration's n_in.  KS_ERR_ARG unless
- * max_iter >= 0, eig_iters >= 1, mixer in {0, 1}, 0 < mix <= 1, 1 <= history <= 8 and
+ * max_iter >= 0, eig_iters >= 1, mixer in {0, 1, 2}, 0 < mix <= 1, 1 <= history <= 8 and
  * tol >= 0; KS_ERR_DIVERGED if r is not finite.  Synchronous. */
 ks_status ks_scf(ks_grid g, int max_iter, int eig_iters, int mixer, double mix, int history, double tol,
                  double* eig_out, double* resid_out, int* iters_done, void* stream);

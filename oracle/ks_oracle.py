@@ -372,6 +372,29 @@ def pulay_coefficients(A):
     return np.linalg.solve(B, rhs)[:m]
 
 
+def broyden_apply(dx, dF, beta, v):
+    """G v for the approximate inverse Jacobian G of Broyden's second method (Broyden 1965,
+    the method that updates the inverse directly; the paper names Broyden mixing as its
+    default in Sec. "Ground-state solution").  G starts from -beta I and takes the secant
+    pairs (dx_j, dF_j) in order, each a rank-one update
+        G_{j+1} = G_j + (dx_j - G_j dF_j) dF_j^T / (dF_j^T dF_j),
+    which makes G_{j+1} dF_j = dx_j and leaves G unchanged on vectors orthogonal to dF_j.
+    Dot products are dV sums over the grid.  A pair with dF_j = 0 carries no information and
+    is skipped."""
+    us, ds = [], []
+    for j in range(len(dF)):
+        g = -beta * dF[j]                                 # G_j dF_j from the updates before j
+        for u, d, f in zip(us, ds, dF[:j]):
+            g = g + u * (float(np.sum(f * dF[j])) / d)
+        dd = float(np.sum(dF[j] * dF[j]))
+        us.append(dx[j] - g)
+        ds.append(dd if dd > 0.0 else np.inf)
+    out = -beta * v
+    for u, d, f in zip(us, ds, dF):
+        out = out + u * (float(np.sum(f * v)) / d)
+    return out
+
+
 def scf(cell, c, max_iter, eig_iters, mix, tol=0.0, mixer="linear", history=4):
     """Self-consistent field (Sec. "Ground-state solution"): each iteration solves the
     linear problem for the current input density with a few eigensolver iterations, forms
@@ -383,7 +406,11 @@ def scf(cell, c, max_iter, eig_iters, mix, tol=0.0, mixer="linear", history=4):
     n_out = density; R = n_out - n_in, r = dV sum |R|; then
       linear: n_in <- n_in + mix R;
       pulay:  with the last `history` pairs (n_in_i, R_i) and alpha from pulay_coefficients
-              of A_ij = dV sum R_i R_j, n_in <- sum_i alpha_i (n_in_i + mix R_i).
+              of A_ij = dV sum R_i R_j, n_in <- sum_i alpha_i (n_in_i + mix R_i);
+      broyden: the root of R(n_in) by Broyden's second method over the last `history` pairs:
+              n_in <- n_in - G R with G from broyden_apply, started at -mix I and updated by
+              the secant pairs (n_in_{i+1} - n_in_i, R_{i+1} - R_i) of the window in order
+              (history 1 is linear mixing).
     Stops once r < tol.  Returns (Ritz values per iteration, residuals, states, final n_in)."""
     c, _ = cholqr(c)
     n_in = density(cell, c)
@@ -400,6 +427,13 @@ def scf(cell, c, max_iter, eig_iters, mix, tol=0.0, mixer="linear", history=4):
         res_hist.append(r)
         if mixer == "linear":
             n_next = n_in + mix * R
+        elif mixer == "broyden":
+            hist_n.append(n_in)
+            hist_r.append(R)
+            hist_n, hist_r = hist_n[-history:], hist_r[-history:]
+            dx = [b - a for a, b in zip(hist_n[:-1], hist_n[1:])]
+            dF = [b - a for a, b in zip(hist_r[:-1], hist_r[1:])]
+            n_next = n_in - broyden_apply(dx, dF, mix, R)
         else:
             hist_n.append(n_in)
             hist_r.append(R)

@@ -214,9 +214,9 @@ ks_status ks_scf(ks_grid g, int max_iter, int eig_iters, int mixer, double mix, 
                  double* eig_out, double* resid_out, int* iters_done, void* stream) {
   return guarded([&] {
     need(g != nullptr, "grid is NULL");
-    need(max_iter >= 0 && eig_iters >= 1 && (mixer == 0 || mixer == 1) && mix > 0.0 && mix <= 1.0 &&
+    need(max_iter >= 0 && eig_iters >= 1 && mixer >= 0 && mixer <= 2 && mix > 0.0 && mix <= 1.0 &&
              history >= 1 && history <= 8 && tol >= 0.0,
-         "scf: need max_iter >= 0, eig_iters >= 1, mixer 0 or 1, 0 < mix <= 1, 1 <= history <= 8, tol >= 0");
+         "scf: need max_iter >= 0, eig_iters >= 1, mixer 0, 1 or 2, 0 < mix <= 1, 1 <= history <= 8, tol >= 0");
     g->eng->scf(max_iter, eig_iters, mixer, mix, history, tol, eig_out, resid_out, iters_done, as_stream(stream));
   });
 }

@@ -12,6 +12,11 @@
 // inverse Cholesky factor of S up to O(E^2) ~ (eps_32 kappa(S))^2 -- below the 24-bit
 // precision of the states for kappa(S) up to ~1e4.  A pivot <= tol * S_jj sets status = j + 1
 // and M = I.
+//
+// Without refinement the result is M1 itself (conjugated), accurate to ~eps_32 kappa(S)
+// sqrt(n).  The pipelined block iteration takes that form: it uses only the FP32 copy of M,
+// whose rounding is of the order of the refinement's correction for the well-conditioned S of
+// an iterate, and the next iteration's CholQR starts again from the S of the new block.
 #include <type_traits>
 
 #include "kernels.h"
@@ -24,7 +29,7 @@ constexpr int C32_MAXN = 160;
 constexpr int C32_THREADS = 1024;
 
 // One CTA.  Reads the lower triangle of S (n x n, row-major), writes X = L^{-1} (lower,
-// zeros above; conj(X) when conj_out) to Out.
+// zeros above; conj(X) when conj_out) to Out, and an FP32 copy to Out32 when it is given.
 //
 // Shared memory holds one square [n][ld] array: L_rc (r >= c) at [c][r] (column-major, so
 // lanes running along a column touch consecutive words) and X_rc (r > c) at [r][c], i.e. in
@@ -49,7 +54,7 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
 
 __global__ void __launch_bounds__(C32_THREADS, 1)
     k_chol32_inverse(const double2* __restrict__ S, int n, double tol, int conj_out, int* __restrict__ status,
-                     double2* __restrict__ Out) {
+                     double2* __restrict__ Out, float2* __restrict__ Out32) {
   extern __shared__ float2 c32[];
   const int ld = n + 1;
   float2* U = c32;
@@ -193,7 +198,11 @@ __global__ void __launch_bounds__(C32_THREADS, 1)
     __syncthreads();
   }
   if (s_bad) {
-    for (int e = t; e < n * n; e += C32_THREADS) Out[e] = make_double2((e / n == e % n) ? 1.0 : 0.0, 0.0);
+    for (int e = t; e < n * n; e += C32_THREADS) {
+      const bool diag = e / n == e % n;
+      Out[e] = make_double2(diag ? 1.0 : 0.0, 0.0);
+      if (Out32) Out32[e] = make_float2(diag ? 1.f : 0.f, 0.f);
+    }
     if (t == 0) atomicCAS(status, 0, s_bad);
     return;
   }
@@ -238,12 +247,9 @@ __global__ void __launch_bounds__(C32_THREADS, 1)
   const float sgn = conj_out ? -1.f : 1.f;
   for (int e = t; e < n * n; e += C32_THREADS) {
     const int r = e / n, c = e - (e / n) * n;
-    if (c <= r) {
-      const float2 x = XL(r, c);
-      Out[e] = make_double2((double)x.x, (double)(sgn * x.y));
-    } else {
-      Out[e] = make_double2(0.0, 0.0);
-    }
+    const float2 x = c <= r ? XL(r, c) : make_float2(0.f, 0.f);
+    Out[e] = make_double2((double)x.x, (double)(sgn * x.y));
+    if (Out32) Out32[e] = make_float2(x.x, sgn * x.y);
   }
 #undef UL
 #undef XU
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(64) k_tri_product(const double2* __restrict__ 
 size_t cholesky_mixed_workspace(int n) { return (size_t)3 * n * n; }
 
 void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, double2* work, int* status,
-                            cudaStream_t s, float2* M32) {
+                            cudaStream_t s, float2* M32, bool refine) {
   if (n > C32_MAXN) fail(KS_ERR_ARG, "cholesky_inverse_mixed: n=%d > %d", n, C32_MAXN);
   const size_t smem = (size_t)n * (n + 1) * sizeof(float2);           // square [n][n+1]
   static bool attr_set = false;
@@ -362,9 +368,14 @@ void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, dou
   double2* M1 = work;
   double2* T = work + (size_t)n * n;
   double2* S2 = work + (size_t)2 * n * n;
+  if (!refine) {                                                     // the FP32 factor itself
+    k_chol32_inverse<<<1, C32_THREADS, smem, s>>>(S, n, tol, 1, status, M, M32);
+    KS_CHECK_LAUNCH();
+    return;
+  }
   const int nt = (n + 7) / 8;
   const dim3 grid(nt, nt);
-  k_chol32_inverse<<<1, C32_THREADS, smem, s>>>(S, n, tol, 0, status, M1);
+  k_chol32_inverse<<<1, C32_THREADS, smem, s>>>(S, n, tol, 0, status, M1, nullptr);
   KS_CHECK_LAUNCH();
   k_tri_product<0><<<grid, 64, 0, s>>>(S, M1, n, status, T, nullptr);
   KS_CHECK_LAUNCH();

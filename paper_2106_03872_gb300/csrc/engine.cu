@@ -354,11 +354,13 @@ template <typename T> class Engine final : public EngineBase {
   // CholQR: S = Psi^H Psi, S = L L^H, Psi <- Psi L^{-H}  (rows: psi <- conj(L^{-1}) psi)
   // ------------------------------------------------------------------------------------------
   // M = conj(L^{-1}) for S = L L^H (mS_ -> mM_), on stream st
+  // With m32 (the fused block iteration, which reads only the FP32 copy), the single FP32
+  // pass of the mixed path without its FP64 refinement.
   void factor(cudaStream_t st, float2* m32 = nullptr) {
     const int n = ns_;
     ProfScope p(prof, "cholesky", st);
     if (mixed_cholesky()) {
-      cholesky_inverse_mixed(mS_, mM_, n, 1e-6, chw_, status_, st, m32);
+      cholesky_inverse_mixed(mS_, mM_, n, 1e-6, chw_, status_, st, m32, m32 == nullptr);
     } else {
       KS_CUDA(cudaMemcpyAsync(mF_, mS_, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
       cholesky_inverse_tol(mF_, mM_, n, sizeof(T) == 8 ? 1e-12 : 1e-6, status_, st);
@@ -574,12 +576,12 @@ template <typename T> class Engine final : public EngineBase {
   // ------------------------------------------------------------------------------------------
   void scf(int max_iter, int eig_iters, int mixer, double mix, int history, double tol, double* eig_out,
            double* resid_out, int* iters_done, cudaStream_t s) override {
-    if (max_iter < 0 || eig_iters < 1 || (mixer != 0 && mixer != 1) || !(mix > 0.0 && mix <= 1.0) || history < 1 ||
+    if (max_iter < 0 || eig_iters < 1 || mixer < 0 || mixer > 2 || !(mix > 0.0 && mix <= 1.0) || history < 1 ||
         history > PULAY_MAX || !(tol >= 0.0))
       fail(KS_ERR_ARG, "scf: max_iter=%d eig_iters=%d mixer=%d mix=%g history=%d tol=%g", max_iter, eig_iters, mixer,
            mix, history, tol);
     const int N3 = g_.N * g_.N * g_.N;
-    if (mixer == 1 && !hist_n_[0]) {
+    if (mixer != 0 && !hist_n_[0]) {
       for (int i = 0; i < PULAY_MAX; ++i) {
         hist_n_[i] = alloc<T>(N3);
         hist_r_[i] = alloc<T>(N3);
@@ -627,14 +629,20 @@ template <typename T> class Engine final : public EngineBase {
           A[order[q] * PULAY_MAX + slot] = out[2 + q];
         }
         order.push_back(slot);
-        const std::vector<double> alpha = pulay_coefficients(A, order);
         PulayMix<T> pm{};
         pm.m = (int)order.size();
-        pm.mix = mix;
+        std::vector<double> a, b;
+        if (mixer == 1) {
+          a = pulay_coefficients(A, order);
+          for (double x : a) b.push_back(mix * x);
+        } else {
+          broyden_coefficients(A, order, mix, a, b);
+        }
         for (int q = 0; q < pm.m; ++q) {
           pm.n[q] = hist_n_[order[q]];
           pm.r[q] = hist_r_[order[q]];
-          pm.a[q] = alpha[q];
+          pm.a[q] = a[q];
+          pm.b[q] = b[q];
         }
         pulay_mix<T>(nin_, N3, pm, s);
       }
@@ -682,6 +690,68 @@ template <typename T> class Engine final : public EngineBase {
     std::vector<double> alpha(m);
     for (int i = 0; i < m; ++i) alpha[i] = B[i * (n + 1) + n] / B[i * (n + 1) + i];
     return alpha;
+  }
+
+  // Broyden's second method (Broyden 1965: the update of the approximate inverse Jacobian)
+  // over the window of pairs (x_i, F_i) = (n_in_i, R_i) in `order`, oldest first:
+  //   G_0 = -beta I,  G_{j+1} = G_j + u_j dF_j^T / <dF_j|dF_j>,  u_j = dx_j - G_j dF_j,
+  //   dx_j = x_{j+1} - x_j, dF_j = F_{j+1} - F_j, and x_next = x_last - G F_last.
+  // Every vector involved is a combination of the window's x_i and F_i, so each is carried as
+  // its coefficients (over x, over F), and every inner product needed is one of F-combinations,
+  // read from the Gram matrix A of the residuals.  Out: x_next = sum_q a_q x_q + b_q F_q.  A
+  // pair with <dF_j|dF_j> = 0 carries no update.
+  static void broyden_coefficients(const std::vector<double>& A, const std::vector<int>& order, double beta,
+                                   std::vector<double>& a, std::vector<double>& b) {
+    const int m = (int)order.size();
+    auto dot = [&](const std::vector<double>& c1, const std::vector<double>& c2) {   // <sum c1 F|sum c2 F>
+      double acc = 0.0;
+      for (int i = 0; i < m; ++i)
+        for (int k = 0; k < m; ++k) acc += c1[i] * A[order[i] * PULAY_MAX + order[k]] * c2[k];
+      return acc;
+    };
+    auto diff = [&](int j) {                                          // e_{j+1} - e_j
+      std::vector<double> e(m, 0.0);
+      e[j + 1] = 1.0;
+      e[j] = -1.0;
+      return e;
+    };
+    std::vector<std::vector<double>> ux, uF;
+    std::vector<double> dd;
+    for (int j = 0; j + 1 < m; ++j) {
+      const std::vector<double> df = diff(j);
+      std::vector<double> gx(m, 0.0), gF(m, 0.0);                     // G_j dF_j
+      for (int k = 0; k < m; ++k) gF[k] = -beta * df[k];
+      for (int i = 0; i < j; ++i) {
+        if (!(dd[i] > 0.0)) continue;
+        const double c = dot(diff(i), df) / dd[i];
+        for (int k = 0; k < m; ++k) {
+          gx[k] += c * ux[i][k];
+          gF[k] += c * uF[i][k];
+        }
+      }
+      std::vector<double> uxj(m), uFj(m);
+      for (int k = 0; k < m; ++k) {
+        uxj[k] = df[k] - gx[k];                                       // dx_j has the coefficients of dF_j
+        uFj[k] = -gF[k];
+      }
+      ux.push_back(uxj);
+      uF.push_back(uFj);
+      dd.push_back(dot(df, df));
+    }
+    a.assign(m, 0.0);
+    b.assign(m, 0.0);
+    a[m - 1] = 1.0;
+    b[m - 1] = beta;
+    std::vector<double> last(m, 0.0);
+    last[m - 1] = 1.0;
+    for (int i = 0; i + 1 < m; ++i) {
+      if (!(dd[i] > 0.0)) continue;
+      const double c = dot(diff(i), last) / dd[i];
+      for (int k = 0; k < m; ++k) {
+        a[k] -= c * ux[i][k];
+        b[k] -= c * uF[i][k];
+      }
+    }
   }
 
   // ------------------------------------------------------------------------------------------

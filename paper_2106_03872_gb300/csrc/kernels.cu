@@ -399,7 +399,7 @@ __global__ void k_pulay_mix(T* __restrict__ nin, size_t N3, PulayMix<T> p) {
     double v = 0.0;
 #pragma unroll
     for (int q = 0; q < PULAY_MAX; ++q)
-      if (q < p.m) v += p.a[q] * ((double)p.n[q][j] + p.mix * (double)p.r[q][j]);
+      if (q < p.m) v += p.a[q] * (double)p.n[q][j] + p.b[q] * (double)p.r[q][j];
     nin[j] = (T)v;
   }
 }

@@ -75,7 +75,7 @@ void hxc_finish(const double* partials, int nblocks, double dV, double* parts, c
 template <typename T> void density_mix(const T* nout, T* nin, int N3, double mix, double* partials, int nblocks,
                                        cudaStream_t s);
 void sum_partials(const double* partials, int nblocks, double scale, double* out, cudaStream_t s);
-// Pulay (DIIS) density mixing.  History of at most PULAY_MAX (n_in, R) pairs.
+// History mixing of the density (Pulay / DIIS and Broyden): at most PULAY_MAX (n_in, R) pairs.
 constexpr int PULAY_MAX = 8;
 template <typename T> struct PulayRefs {
   const T* r[PULAY_MAX];   // the other history residuals
@@ -84,15 +84,15 @@ template <typename T> struct PulayRefs {
 template <typename T> struct PulayMix {
   const T* n[PULAY_MAX];
   const T* r[PULAY_MAX];
-  double a[PULAY_MAX];
-  double mix;
+  double a[PULAY_MAX];     // coefficients of n_q
+  double b[PULAY_MAX];     // coefficients of r_q
   int m;
 };
 // hr = nout - nin, hn = nin; out (device, 2 + PULAY_MAX) = dV * {sum |R|, sum R^2, sum R r_q};
 // partials holds nblocks * (2 + PULAY_MAX) doubles
 template <typename T> void pulay_store(const T* nout, const T* nin, T* hn, T* hr, int N3, const PulayRefs<T>& refs,
                                        double* partials, int nblocks, double dV, double* out, cudaStream_t s);
-// nin = sum_i a_i (n_i + mix r_i)
+// nin = sum_i a_i n_i + b_i r_i
 template <typename T> void pulay_mix(T* nin, int N3, const PulayMix<T>& p, cudaStream_t s);
 // Teter-preconditioned SD update of n states [n][nG]: R = hpsi - eig psi, T_b = kinetic energy
 // of R_b (sum g2half |R|^2 / sum |R|^2) floored at tmin, psi_b -= K(g2half / T_b) R_b / (T_b + shift).
@@ -139,12 +139,13 @@ void sd_matrix(const double2* C, const double* eig, double alpha, int n, double2
 void cholesky_inverse(double2* A, double2* M, int n, int* status, cudaStream_t s);
 // Same with an explicit relative pivot tolerance (pivot <= tol * S_jj fails).
 void cholesky_inverse_tol(double2* A, double2* M, int n, double tol, int* status, cudaStream_t s);
-// Mixed path (n <= 160): M = conj(L^{-1}) for S = L L^H from two FP32 Cholesky passes
-// refined by FP64 triangular products (cholqr_mixed.cu); work holds
-// cholesky_mixed_workspace(n) complex128.  Same status convention as cholesky_inverse.
+// Mixed path (n <= 160): M = conj(L^{-1}) for S = L L^H from an FP32 Cholesky pass, refined
+// by FP64 triangular products when `refine` (cholqr_mixed.cu); work holds
+// cholesky_mixed_workspace(n) complex128.  M32, when given, receives an FP32 copy of M.
+// Same status convention as cholesky_inverse.
 size_t cholesky_mixed_workspace(int n);
 void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, double2* work, int* status,
-                            cudaStream_t s, float2* M32 = nullptr);
+                            cudaStream_t s, float2* M32 = nullptr, bool refine = true);
 // Hermitian eigen-decomposition of A (destroyed) by cyclic Jacobi; eig ascending, rows of
 // Vt = eigenvectors (largest-magnitude component real positive).  `V` is n*n workspace.
 void jacobi_eigh(double2* A, double2* V, double* eig, double2* Vt, int n, cudaStream_t s);

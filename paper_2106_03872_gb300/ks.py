@@ -252,12 +252,12 @@ class Grid:
         return e
 
     def scf(self, max_iter, eig_iters=2, mix=0.3, tol=0.0, stream=None, mixer="linear", history=4):
-        """Self-consistent field with linear or Pulay mixing: returns (Ritz values
+        """Self-consistent field with linear, Pulay or Broyden mixing: returns (Ritz values
         [iters][nstates], density residuals [iters]) of the iterations run."""
         eig = np.zeros((max(max_iter, 1), self.nstates))
         res = np.zeros(max(max_iter, 1))
         done = ct.c_int(0)
-        mode = {"linear": 0, "pulay": 1}[mixer] if isinstance(mixer, str) else int(mixer)
+        mode = {"linear": 0, "pulay": 1, "broyden": 2}[mixer] if isinstance(mixer, str) else int(mixer)
         check(load().ks_scf(self.h, int(max_iter), int(eig_iters), mode, float(mix), int(history), float(tol),
                             _dptr(eig), _dptr(res), ct.byref(done), _stream_ptr(stream)))
         return eig[:done.value], res[:done.value]

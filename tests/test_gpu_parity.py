@@ -548,6 +548,28 @@ def test_scf_pulay_parity(ks, prec):
     g.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_scf_broyden_parity(ks, prec):
+    """Broyden mixing with a window of 3 pairs (the ring of history slots wraps), against the
+    oracle's direct rank-one updates of the inverse Jacobian."""
+    cell = inputs.small_cell(10.0, 24, 4, 8, 59, depth=-3.0)
+    ref = ko.Cell(cell)
+    c = inputs.random_coeffs(59, 8, ref.nG)
+    eps_ref, res_ref, _, _ = ko.scf(ref, c, 6, 2, 0.4, mixer="broyden", history=3)
+    g = ks.Grid(cell, prec=prec)
+    g.set_states(c)
+    eps, res = g.scf(6, eig_iters=2, mix=0.4, mixer="broyden", history=3)
+    if prec == "fp64":
+        assert np.max(np.abs(eps - eps_ref)) <= 1e-9
+        assert np.max(np.abs(res - res_ref)) <= 1e-9 * np.max(res_ref)
+    else:
+        # secant pairs are differences of densities and residuals, which amplifies the
+        # single-precision error of the densities (as for Pulay mixing)
+        assert np.max(np.abs(eps - eps_ref)) <= 1e-3 * max(1.0, np.max(np.abs(eps_ref)))
+        assert np.max(np.abs(res - res_ref)) <= 1e-2 * np.max(res_ref)
+    g.close()
+
+
 def test_scf_free_electron_fixed_point(ks):
     """Closed shells of free electrons: uniform density, so the SCF sits at its fixed point
     with Ritz values 1/2 |G|^2 + v_x(n0) (uniform-gas LDA exchange) and zero residual."""
@@ -574,7 +596,7 @@ def test_scf_arguments_and_tolerance(ks):
     ref = ko.Cell(cell)
     g = ks.Grid(cell, prec="bf16x3")
     g.set_states(inputs.random_coeffs(53, 4, ref.nG))
-    for bad in (dict(eig_iters=0), dict(mix=0.0), dict(mix=1.5), dict(tol=-1.0), dict(mixer=2),
+    for bad in (dict(eig_iters=0), dict(mix=0.0), dict(mix=1.5), dict(tol=-1.0), dict(mixer=3),
                 dict(mixer="pulay", history=0), dict(mixer="pulay", history=9)):
         with pytest.raises(ks.KsError):
             g.scf(2, **bad)

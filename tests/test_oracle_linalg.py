@@ -134,6 +134,64 @@ def test_scf_pulay_with_one_pair_is_linear_and_converges_faster():
     assert r_p4[-1] < r_lin12[-1]
 
 
+def _secant_pairs(rng, d, m):
+    return ([rng.standard_normal(d) for _ in range(m)], [rng.standard_normal(d) for _ in range(m)])
+
+
+def test_broyden_update_secant_condition_and_invariance():
+    """Broyden's second method: after the update with the pair (dx, dF), G dF = dx (the
+    secant condition), and on every vector orthogonal to dF the new G acts as the previous
+    one.  The two properties fix a rank-one update uniquely."""
+    rng = np.random.default_rng(5)
+    d, beta = 7, 0.3
+    dx, dF = _secant_pairs(rng, d, 3)
+    for m in (1, 2, 3):
+        g = ko.broyden_apply(dx[:m], dF[:m], beta, dF[m - 1])
+        assert np.allclose(g, dx[m - 1], rtol=0, atol=1e-12)
+        v = rng.standard_normal(d)
+        v -= dF[m - 1] * (np.dot(dF[m - 1], v) / np.dot(dF[m - 1], dF[m - 1]))
+        prev = ko.broyden_apply(dx[:m - 1], dF[:m - 1], beta, v)
+        assert np.allclose(ko.broyden_apply(dx[:m], dF[:m], beta, v), prev, rtol=0, atol=1e-12)
+    # no pairs: linear mixing; a zero dF carries no update
+    v = rng.standard_normal(d)
+    assert np.array_equal(ko.broyden_apply([], [], beta, v), -beta * v)
+    assert np.allclose(ko.broyden_apply([dx[0]], [np.zeros(d)], beta, v), -beta * v, atol=0)
+
+
+def test_broyden_in_one_dimension_is_the_secant_method():
+    """For a scalar equation f(x) = 0 the window of the last two pairs turns the Broyden step
+    into the secant method x+ = x - f(x) (x - x_prev) / (f(x) - f(x_prev)); on 2 - x^3 (a
+    decreasing residual, like a density residual) it converges superlinearly to 2^(1/3)."""
+    f = lambda x: 2.0 - x ** 3
+    beta = 0.1
+    xs = [np.array([1.0])]
+    xs.append(xs[0] - ko.broyden_apply([], [], beta, f(xs[0])))     # first step: linear
+    assert np.isclose(xs[1][0], 1.1, rtol=0, atol=1e-15)
+    for _ in range(8):
+        x0, x1 = xs[-2], xs[-1]
+        step = ko.broyden_apply([x1 - x0], [f(x1) - f(x0)], beta, f(x1))
+        secant = f(x1) * (x1 - x0) / (f(x1) - f(x0))
+        assert np.allclose(step, secant, rtol=1e-12, atol=0)
+        xs.append(x1 - step)
+        if abs(f(xs[-1])[0]) < 1e-14:
+            break
+    assert abs(xs[-1][0] - 2.0 ** (1.0 / 3.0)) < 1e-12
+    assert len(xs) <= 10
+
+
+def test_scf_broyden_with_one_pair_is_linear_and_converges_faster():
+    """History 1 leaves no secant pair, so Broyden mixing is linear mixing; with history 4 the
+    residual falls below linear mixing's after the same number of iterations."""
+    cell = make_cell(natoms=4, depth=-3.0)
+    c = inputs.random_coeffs(9, 6, cell.nG)
+    e_lin, r_lin, _, _ = ko.scf(cell, c, 5, 5, 0.3)
+    e_b1, r_b1, _, _ = ko.scf(cell, c, 5, 5, 0.3, mixer="broyden", history=1)
+    assert np.allclose(r_b1, r_lin, rtol=1e-10) and np.allclose(e_b1, e_lin, atol=1e-10)
+    _, r_lin12, _, _ = ko.scf(cell, c, 12, 5, 0.3)
+    _, r_b4, _, _ = ko.scf(cell, c, 12, 5, 0.3, mixer="broyden", history=4)
+    assert r_b4[-1] < r_lin12[-1]
+
+
 def test_teter_block_iteration_free_electron_fixed_points_and_limit():
     """The preconditioner changes no fixed point: the free-electron limit still converges to
     the G = 0 and |m| = 1 shells."""
