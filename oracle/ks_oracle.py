@@ -19,7 +19,10 @@ What it computes, each function citing the paper passage it follows:
 * periodic Poisson solve in Fourier space (Sec. "Poisson solver") and LDA Slater exchange;
 * the total energy with eigenvalues replaced by expectation values (Eq. 5);
 * the ETRS propagator with the 4th-order Taylor exponential and shared powers
-  (Eqs. 6-8, Sec. "Real-time propagation").
+  (Eqs. 6-8, Sec. "Real-time propagation");
+* SCF density mixing (linear, Pulay, Broyden), Teter-preconditioned steepest descent, the
+  delta kick and dipole, forces from the orbital gradients (Eq. 11) and Ehrenfest dynamics
+  with velocity-Verlet ions.
 
 Conventions where the paper is silent (each one a reading of it):
 cubic cell of side L, grid N^3, r_j = h j, h = L/N; G = (2 pi / L) m with
@@ -483,7 +486,7 @@ def potential_for(cell, c, hartree_xc):
     return hxc_potential(cell, density(cell, c))
 
 
-def td_step(cell, c, dt, propagator="etrs", hartree_xc=True):
+def td_step(cell, c, dt, propagator="etrs", hartree_xc=True, next_cell=None):
     """One real-time step from t to t + dt; returns (c(t+dt), norm(t), energy(t)).
 
     ETRS (Eq. 6): phi(t+dt) = exp(-i dt/2 H(t+dt)) exp(-i dt/2 H(t)) phi(t), with
@@ -491,6 +494,8 @@ def td_step(cell, c, dt, propagator="etrs", hartree_xc=True):
     The powers H(t)^k phi are computed once and combined with both coefficient sets
     lam = -i dt and lam = -i dt/2 (the shared-power saving).  'taylor' is the plain
     4th-order step phi <- sum_k (-i dt H(t))^k / k! phi.
+    With moving ions, next_cell holds the ions at t + dt: H(t+dt) takes its local potential
+    and projectors (the ionic potential evaluated at the time of the half step it acts in).
     """
     v_t, parts = potential_for(cell, c, hartree_xc)
     powers = [c]
@@ -502,10 +507,11 @@ def td_step(cell, c, dt, propagator="etrs", hartree_xc=True):
     if propagator == "taylor":
         return full, norm_t, energy_t
     half = sum(a * w for a, w in zip(taylor_coefficients(-0.5j * dt), powers))
-    v_next, _ = potential_for(cell, full, hartree_xc)
+    cell2 = cell if next_cell is None else next_cell
+    v_next, _ = potential_for(cell2, full, hartree_xc)
     out, w = half.copy(), half
     for a in taylor_coefficients(-0.5j * dt)[1:]:
-        w = apply_h(cell, w, v_next)
+        w = apply_h(cell2, w, v_next)
         out = out + a * w
     return out, norm_t, energy_t
 
@@ -570,6 +576,39 @@ def td_run_dipole(cell, c, dt, nsteps, propagator="etrs", hartree_xc=True):
         norms.append(nrm)
         energies.append(e)
     return c, np.array(norms), np.array(energies), np.array(dips)
+
+
+def ehrenfest_run(desc, c, dt, nsteps, mass, vel, hartree_xc=True):
+    """Ehrenfest dynamics (Sec. "Real-time propagation"): the electrons follow the ETRS step
+    and the ions classical equations of motion under the forces of Eq. 11, integrated by
+    velocity Verlet, with the ionic potential of H(t+dt) taken at the new positions:
+      R(t+dt) = R(t) + v(t) dt + F(t) dt^2 / (2M);
+      phi(t+dt) = ETRS step with H(t) at R(t) and H(t+dt) at R(t+dt);
+      F(t+dt) = forces of phi(t+dt) at R(t+dt);  v(t+dt) = v(t) + (F(t) + F(t+dt)) dt / (2M).
+    desc is the cell dict at the initial positions, mass [natoms] (electron masses), vel
+    [natoms, 3] the initial velocities (bohr per atomic time unit).  Returns (c, positions
+    [nsteps, natoms, 3] after each step, velocities [nsteps, natoms, 3] after each step,
+    energies [nsteps]: electronic energy of Eq. 5 (as in td_step) plus the ionic kinetic energy
+    sum 1/2 M v^2, both at the start of each step)."""
+    M = np.asarray(mass, float)[:, None]
+    v = np.array(vel, float).reshape(-1, 3)
+    d = dict(desc)
+    cell = Cell(d)
+    F = forces(cell, c)
+    pos_h, vel_h, e_h = [], [], []
+    for _ in range(nsteps):
+        kin = float(np.sum(0.5 * M * v * v))
+        R1 = cell.pos + v * dt + F * dt * dt / (2.0 * M)
+        d = dict(d, pos=R1)
+        cell1 = Cell(d)
+        c, _, e_el = td_step(cell, c, dt, "etrs", hartree_xc, next_cell=cell1)
+        F1 = forces(cell1, c)
+        v = v + (F + F1) * dt / (2.0 * M)
+        cell, F = cell1, F1
+        pos_h.append(cell.pos.copy())
+        vel_h.append(v.copy())
+        e_h.append(e_el + kin)
+    return c, np.array(pos_h), np.array(vel_h), np.array(e_h)
 
 
 def td_run(cell, c, dt, nsteps, propagator="etrs", hartree_xc=True):

@@ -145,3 +145,59 @@ def test_dipole_closed_forms():
     assert np.allclose(ko.dipole(cell, n) / q, R - 0.5 * cell.L, atol=1e-9)
     n0 = np.full((cell.N,) * 3, 0.37)
     assert np.allclose(ko.dipole(cell, n0), -0.5 * cell.h * cell.dV * n0.sum(), atol=1e-12)
+
+
+# ------------------------------------------------------------------------------------------------
+# Ehrenfest dynamics (Sec. "Real-time propagation": velocity-Verlet ions under the forces of
+# Eq. 11, the ionic potential of each ETRS half step taken at its own time)
+# ------------------------------------------------------------------------------------------------
+def _two_atom_desc(D):
+    return dict(L=8.0, N=24, ecut=20.0, pos=np.array([[2.0, 2.5, 3.0], [5.5, 4.0, 4.5]]), vloc_depth=-3.0,
+                vloc_width=0.8, nproj=4, proj_sigma=0.5, proj_rc=2.0, proj_D=D)
+
+
+def _relaxed_states(desc, nstates=4, iters=30):
+    cell = ko.Cell(desc)
+    _, c = ko.block_iteration(cell, inputs.random_coeffs(3, nstates, cell.nG), iters)
+    return ko.cholqr(c)[0]
+
+
+def test_ehrenfest_with_immobile_ions_is_the_real_time_run():
+    """Infinite masses at rest: the ions never move and the electrons follow td_run exactly."""
+    desc = _two_atom_desc(0.5)
+    cell = ko.Cell(desc)
+    c = _relaxed_states(desc, iters=5)
+    c1, P, V, E = ko.ehrenfest_run(desc, c, 0.1, 3, [1e300, 1e300], np.zeros((2, 3)))
+    c2, _, e2 = ko.td_run(cell, c, 0.1, 3)
+    assert np.array_equal(P[-1], cell.pos) and np.max(np.abs(V)) < 1e-250
+    assert np.max(np.abs(c1 - c2)) <= 1e-13
+    assert np.allclose(E, e2, rtol=0, atol=1e-13)
+
+
+def test_ehrenfest_free_flight_without_potential():
+    """Atoms with no potential and no projector coupling feel no force: R(t) = R(0) + v t."""
+    desc = dict(_two_atom_desc(0.0), vloc_depth=0.0)
+    c = ko.cholqr(inputs.random_coeffs(4, 3, ko.Cell(desc).nG))[0]
+    v0 = np.array([[0.03, -0.01, 0.02], [0.0, 0.05, -0.04]])
+    _, P, V, _ = ko.ehrenfest_run(desc, c, 0.05, 4, [7.0, 3.0], v0)
+    t = 0.05 * np.arange(1, 5)
+    assert np.allclose(P, desc["pos"][None] + t[:, None, None] * v0[None], rtol=0, atol=1e-14)
+    assert np.allclose(V[-1], v0, rtol=0, atol=1e-15)
+
+
+def test_ehrenfest_energy_conserved_to_second_order():
+    """Local pseudopotential only (D = 0, where Eq. 11 is -dE/dR of the grid energy up to
+    the grid's aliasing): the total energy (electrons + ionic kinetic energy) deviates by at
+    most O(dt^2) over a fixed time, each halving of dt dividing the deviation by >= 3.  Taking
+    H(t+dt) at the old positions instead makes the drift first order and ~10x larger."""
+    desc = _two_atom_desc(0.0)
+    c = _relaxed_states(desc)
+    mass = [20.0, 20.0]
+    v0 = np.array([[0.05, 0.0, -0.03], [-0.03, 0.04, 0.0]])
+    dev = []
+    for dt in (0.2, 0.1):
+        _, P, _, E = ko.ehrenfest_run(desc, c, dt, int(round(1.6 / dt)), mass, v0)
+        dev.append(np.max(np.abs(E - E[0])))
+        assert np.max(np.abs(P[-1] - desc["pos"])) > 0.05              # the ions did move
+    assert dev[1] < 5e-5
+    assert dev[0] / dev[1] >= 3.0
