@@ -217,6 +217,36 @@ ks_status ks_kick(ks_grid g, const double* kappa, void* stream);
  * [natoms][3] (host, Ha/bohr); nothing is written when natoms = 0.  Synchronous. */
 ks_status ks_forces(ks_grid g, double* f_out, void* stream);
 
+/* Moves the atoms (Sec. "Real-time propagation": the ionic potential is recomputed for each
+ * ionic configuration).  pos [natoms][3] (host, bohr, finite; positions outside [0, L) are
+ * periodic images).  Rebuilds, for the same atoms and parameters as at creation: the
+ * projector spheres |r_j - R_I| < proj_rc (minimum image) with their normalised beta values,
+ * the projector block of the mixed path (FP64 FFT), and V_loc from the separable 27-image
+ * Gaussians (in FP64 on the device).  The potential V becomes the new V_loc (a following
+ * SCF or real-time step recomputes Hartree and exchange).  The states are kept.  No-op when
+ * natoms = 0.  KS_ERR_ARG on a non-finite position.  Synchronous. */
+ks_status ks_set_positions(ks_grid g, const double* pos, void* stream);
+
+/* The current positions pos [natoms][3] (host, bohr). */
+ks_status ks_get_positions(ks_grid g, double* pos);
+
+/* nsteps steps of Ehrenfest dynamics (Sec. "Real-time propagation"): the resident states
+ * follow the ETRS step of ks_td_step (propagator 0, Hartree and exchange when hartree_xc)
+ * and the atoms classical equations of motion under the forces of ks_forces (Eq. 11), by
+ * velocity Verlet:
+ *   R(t+dt) = R(t) + v(t) dt + F(t) dt^2 / (2 M);
+ *   the ETRS step with H(t) at R(t) and H(t+dt) at R(t+dt) (the ions move between the two
+ *   half steps, so that each half step sees the ionic potential of its own time);
+ *   F(t+dt) from the new states at R(t+dt);  v(t+dt) = v(t) + (F(t) + F(t+dt)) dt / (2 M).
+ * mass [natoms] (host, electron masses, > 0); vel [natoms][3] (host, bohr per atomic time
+ * unit): v(0) in, v(t_nsteps) out.  pos_out [nsteps][natoms][3] (may be NULL) receives the
+ * positions after each step; energy_out [nsteps] (may be NULL) the total energy at the start
+ * of each step: the energy of ks_td_step plus sum_I M_I |v_I|^2 / 2.  The handle's positions
+ * end at R(t_nsteps).  KS_ERR_ARG unless nsteps >= 0, dt > 0 and masses and velocities are
+ * valid; KS_ERR_DIVERGED as for ks_td_step.  Synchronous. */
+ks_status ks_ehrenfest(ks_grid g, double dt, int nsteps, int hartree_xc, const double* mass, double* vel,
+                       double* pos_out, double* energy_out, void* stream);
+
 /* Dipole of the resident states' density, d_out[3] (host) = dV sum_j (r_j - L/2) n(r_j).
  * Synchronous. */
 ks_status ks_dipole(ks_grid g, double* d_out, void* stream);

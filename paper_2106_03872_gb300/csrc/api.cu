@@ -192,6 +192,30 @@ ks_status ks_forces(ks_grid g, double* f_out, void* stream) {
   });
 }
 
+ks_status ks_set_positions(ks_grid g, const double* pos, void* stream) {
+  return guarded([&] {
+    need(g != nullptr && (pos != nullptr || g->eng->geo().natoms == 0), "grid or pos is NULL");
+    g->eng->set_positions(pos, as_stream(stream));
+  });
+}
+
+ks_status ks_get_positions(ks_grid g, double* pos) {
+  return guarded([&] {
+    need(g != nullptr && (pos != nullptr || g->eng->geo().natoms == 0), "grid or pos is NULL");
+    const auto& geo = g->eng->geo();
+    if (geo.natoms) std::memcpy(pos, geo.pos.data(), 3 * (size_t)geo.natoms * sizeof(double));
+  });
+}
+
+ks_status ks_ehrenfest(ks_grid g, double dt, int nsteps, int hartree_xc, const double* mass, double* vel,
+                       double* pos_out, double* energy_out, void* stream) {
+  return guarded([&] {
+    need(g != nullptr, "grid is NULL");
+    need(g->eng->geo().natoms == 0 || (mass != nullptr && vel != nullptr), "mass or vel is NULL");
+    g->eng->ehrenfest(dt, nsteps, hartree_xc, mass, vel, pos_out, energy_out, as_stream(stream));
+  });
+}
+
 ks_status ks_dipole(ks_grid g, double* d_out, void* stream) {
   return guarded([&] {
     need(g != nullptr && d_out != nullptr, "grid or d_out is NULL");

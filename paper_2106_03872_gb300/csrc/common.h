@@ -90,7 +90,7 @@ struct HostGeometry {
   double vloc_depth = 0, vloc_width = 0;
   // projectors: sphere point lists per atom (grid order within an atom)
   int natoms = 0, nproj = 0;
-  double D = 0;
+  double D = 0, proj_sigma = 0, proj_rc = 0;
   std::vector<int> sph_off;     // [natoms+1]
   std::vector<int> sph_idx;     // flat grid index of each sphere point
   std::vector<int> sph_atom;    // atom of each sphere point
@@ -106,5 +106,8 @@ struct HostGeometry {
 bool valid_fft_length(int N);
 void count_sphere(double L, int N, double ecut, int* nG);
 void build_geometry(const ks_cell_desc& d, HostGeometry& g);
+// Rebuilds the atom-dependent parts (pos, the projector sphere lists and their inverse lists;
+// V_loc on the host when with_vloc) for new positions pos [natoms][3] of the same atoms.
+void build_atoms(const double* pos, HostGeometry& g, bool with_vloc);
 
 }  // namespace ks

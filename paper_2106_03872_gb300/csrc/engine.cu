@@ -3,6 +3,7 @@
 // (its fused Hamiltonian lives in fused.cu and plugs in through FusedOps).
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <cstring>
 #include <type_traits>
 
@@ -22,8 +23,22 @@ void* DeviceArena::alloc(size_t bytes) {
   bytes = (bytes + 255) / 256 * 256;
   KS_CUDA(cudaMalloc(&p, bytes));
   ptrs_.push_back(p);
+  sizes_.push_back(bytes);
   total_ += bytes;
   return p;
+}
+
+void DeviceArena::release(const void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < ptrs_.size(); ++i)
+    if (ptrs_[i] == p) {
+      KS_CUDA(cudaFree(ptrs_[i]));
+      total_ -= sizes_[i];
+      ptrs_.erase(ptrs_.begin() + i);
+      sizes_.erase(sizes_.begin() + i);
+      return;
+    }
+  fail(KS_ERR_STATE, "internal: release of a pointer the arena does not own");
 }
 
 StageProfiler::~StageProfiler() {
@@ -795,29 +810,7 @@ template <typename T> class Engine final : public EngineBase {
     const int N = g_.N, na = g_.natoms, np = g_.nproj;
     if (na == 0) return;
     const size_t N3 = (size_t)N * N * N;
-    if (!fw_) {
-      fw_ = alloc<C>(N3);
-      fg_ = alloc<T>(3 * N3);
-      fp_ = alloc<C>((size_t)na * np);
-      fq_ = alloc<C>((size_t)na * np);
-      fnl_ = alloc<double>(3 * (size_t)na);
-      floc_ = alloc<double>(3 * (size_t)na);
-      // per atom and axis: X_a(x) = sum_{s = -1, 0, 1} exp(-(x - R_a - L s)^2 / (2 w^2)) on the grid
-      std::vector<double> xyz(3 * (size_t)na * N);
-      const double w2 = 2.0 * g_.vloc_width * g_.vloc_width;
-      for (int I = 0; I < na; ++I)
-        for (int a = 0; a < 3; ++a)
-          for (int j = 0; j < N; ++j) {
-            double v = 0.0;
-            for (int sh = -1; sh <= 1; ++sh) {
-              const double dx = g_.h * j - g_.pos[3 * I + a] - g_.L * sh;
-              v += std::exp(-dx * dx / w2);
-            }
-            xyz[((size_t)I * 3 + a) * N + j] = v;
-          }
-      fxyz_ = alloc<double>(xyz.size());
-      KS_CUDA(cudaMemcpy(fxyz_, xyz.data(), xyz.size() * sizeof(double), cudaMemcpyHostToDevice));
-    }
+    force_buffers();
     ProfScope p(prof, "forces", s);
     KS_CUDA(cudaMemsetAsync(fg_, 0, 3 * N3 * sizeof(T), s));
     KS_CUDA(cudaMemsetAsync(fnl_, 0, 3 * (size_t)na * sizeof(double), s));
@@ -853,63 +846,12 @@ template <typename T> class Engine final : public EngineBase {
                 double* dipole_out, cudaStream_t s) override {
     hpsi_valid_ = false;
     if (nsteps < 0 || (propagator != 0 && propagator != 1)) fail(KS_ERR_ARG, "td: nsteps=%d propagator=%d", nsteps, propagator);
-    const int n = ns_, nG = g_.nG;
-    const size_t sn = (size_t)n * nG;
     if (!hartree_xc) KS_CUDA(cudaMemcpyAsync(vtot_, vloc_, (size_t)g_.N * g_.N * g_.N * sizeof(T), cudaMemcpyDeviceToDevice, s));
     double first_norm = 0;
     bool have_first = false;
     for (int c0 = 0; c0 < nsteps; c0 += MAX_STEPS_CHUNK) {
       const int cn = std::min(MAX_STEPS_CHUNK, nsteps - c0);
-      for (int st = 0; st < cn; ++st) {
-        // roles: psi, two power buffers, acc_full, acc_half
-        C* others[5];
-        int k = 0;
-        for (int i = 0; i < 6; ++i)
-          if (buf_[i] != psi_) others[k++] = buf_[i];
-        C* wa = others[0];
-        C* wb = others[1];
-        C* acc_full = others[2];
-        C* acc_half = others[3];
-        if (hartree_xc || dipole_out) density_of(psi_, n, dens_, s);
-        if (dipole_out) ks::dipole<T>(dens_, g_.N, g_.L, dip_partials_, HXC_BLOCKS, dipoles_dev_ + 3 * st, s);
-        if (hartree_xc) update_potential(dens_, s);
-        state_dots<T>(psi_, psi_, nG, n, dots_, s);
-        weighted_energy(dots_, occ_, n, nullptr, norms_dev_ + st, s);
-        // the accumulators start from psi in the first power's update (no copies)
-        const C* w = psi_;
-        double2 af = make_double2(1, 0), ah = make_double2(1, 0);
-        for (int kk = 1; kk <= 4; ++kk) {
-          C* wn = (w == wa) ? wb : wa;
-          apply_h(w, wn, n, s);
-          if (kk == 1) {
-            state_dots<T>(psi_, wn, nG, n, dots_, s);
-            weighted_energy(dots_, occ_, n, hartree_xc ? parts_ : nullptr, energies_dev_ + st, s);
-          }
-          af = cmul_scalar(af, make_double2(0, -dt / kk));
-          ah = cmul_scalar(ah, make_double2(0, -0.5 * dt / kk));
-          axpy2<T>(acc_full, af, propagator == 0 ? acc_half : nullptr, ah, wn, kk == 1 ? psi_ : nullptr, sn, s);
-          w = wn;
-        }
-        if (propagator == 1) {
-          psi_ = acc_full;
-          continue;
-        }
-        if (hartree_xc) {
-          density_of(acc_full, n, dens_, s);
-          update_potential(dens_, s);
-        }
-        // second half: out = acc_half + sum_k (-i dt/2)^k/k! H(t+dt)^k acc_half
-        w = acc_half;
-        ah = make_double2(1, 0);
-        for (int kk = 1; kk <= 4; ++kk) {
-          C* wn = (w == wa) ? wb : wa;
-          apply_h(w, wn, n, s);
-          ah = cmul_scalar(ah, make_double2(0, -0.5 * dt / kk));
-          axpy2<T>(acc_full, ah, nullptr, ah, wn, kk == 1 ? acc_half : nullptr, sn, s);
-          w = wn;
-        }
-        psi_ = acc_full;
-      }
+      for (int st = 0; st < cn; ++st) td_step_body(dt, propagator, hartree_xc, st, dipole_out != nullptr, nullptr, s);
       std::vector<double> nh(cn), eh(cn), dh(dipole_out ? 3 * cn : 0);
       KS_CUDA(cudaMemcpyAsync(nh.data(), norms_dev_, cn * sizeof(double), cudaMemcpyDeviceToHost, s));
       KS_CUDA(cudaMemcpyAsync(eh.data(), energies_dev_, cn * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -933,7 +875,186 @@ template <typename T> class Engine final : public EngineBase {
     if (hpsi_ == psi_) hpsi_ = spare(psi_, nullptr);
   }
 
+  // ------------------------------------------------------------------------------------------
+  // Moving atoms: the ionic potential and the projectors at new positions, and Ehrenfest
+  // dynamics (Sec. "Real-time propagation": velocity-Verlet ions under the forces of Eq. 11,
+  // with H(t+dt) of the ETRS step taken at the ions' positions at t + dt).
+  // ------------------------------------------------------------------------------------------
+  void set_positions(const double* pos, cudaStream_t s) override {
+    const int na = g_.natoms, N = g_.N;
+    if (na == 0) return;
+    for (int i = 0; i < 3 * na; ++i)
+      if (!std::isfinite(pos[i])) fail(KS_ERR_ARG, "set_positions: position %d is not finite", i);
+    const size_t N3 = (size_t)N * N * N;
+    KS_CUDA(cudaStreamSynchronize(s));
+    KS_CUDA(cudaDeviceSynchronize());
+    ProfScope p(prof, "set_positions", s);
+    build_atoms(pos, g_, false);
+    // projector sphere lists (their sizes change as grid points enter and leave the spheres)
+    for (const void* q : {(const void*)t_.sph_off, (const void*)t_.sph_idx, (const void*)t_.sph_atom,
+                          (const void*)t_.sph_beta, (const void*)t_.cov_idx, (const void*)t_.cov_off,
+                          (const void*)t_.cov_ent})
+      arena_.release(q);
+    t_.sph_off = upload(g_.sph_off);
+    t_.sph_idx = upload(g_.sph_idx);
+    t_.sph_atom = upload(g_.sph_atom);
+    t_.sph_beta = upload_real(g_.sph_beta);
+    t_.cov_idx = upload(g_.cov_idx);
+    t_.cov_off = upload(g_.cov_off);
+    t_.cov_ent = upload(g_.cov_ent);
+    t_.ncov = (int)g_.cov_idx.size();
+    // V_loc from the separable 27-image Gaussians, in FP64 on the device, with a host copy
+    force_buffers();
+    build_axis_tables();
+    double* v64 = reinterpret_cast<double*>(pwork_);                  // N^3 doubles fit the work grid
+    vloc_from_axes<T>(fxyz_, na, N, g_.vloc_depth, vloc_, v64, s);
+    g_.vloc.resize(N3);
+    KS_CUDA(cudaMemcpyAsync(g_.vloc.data(), v64, N3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaMemcpyAsync(vtot_, vloc_, N3 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    g_.vmin = *std::min_element(g_.vloc.begin(), g_.vloc.end());
+    g_.vmax = *std::max_element(g_.vloc.begin(), g_.vloc.end());
+    if constexpr (sizeof(T) == 4) {
+      if (fused_) fused_->set_atoms(t_);
+    }
+    hpsi_valid_ = false;
+  }
+
+  void ehrenfest(double dt, int nsteps, int hartree_xc, const double* mass, double* vel, double* pos_out,
+                 double* energy_out, cudaStream_t s) override {
+    const int na = g_.natoms;
+    if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) fail(KS_ERR_ARG, "ehrenfest: nsteps=%d dt=%g", nsteps, dt);
+    for (int I = 0; I < na; ++I)
+      if (!(mass[I] > 0.0) || !std::isfinite(mass[I])) fail(KS_ERR_ARG, "ehrenfest: mass[%d] = %g", I, mass[I]);
+    for (int i = 0; i < 3 * na; ++i)
+      if (!std::isfinite(vel[i])) fail(KS_ERR_ARG, "ehrenfest: velocity %d is not finite", i);
+    hpsi_valid_ = false;
+    const size_t N3 = (size_t)g_.N * g_.N * g_.N;
+    if (!hartree_xc) KS_CUDA(cudaMemcpyAsync(vtot_, vloc_, N3 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    std::vector<double> F(3 * (size_t)na), F1(3 * (size_t)na), R1(3 * (size_t)na);
+    if (na) forces(F.data(), s);
+    double first_norm = 0.0;
+    for (int st = 0; st < nsteps; ++st) {
+      double kin = 0.0;
+      for (int i = 0; i < 3 * na; ++i) {
+        const double M = mass[i / 3];
+        kin += 0.5 * M * vel[i] * vel[i];
+        R1[i] = g_.pos[i] + vel[i] * dt + F[i] * dt * dt / (2.0 * M);
+      }
+      const std::function<void()> move = [&]() { set_positions(R1.data(), s); };
+      td_step_body(dt, 0, hartree_xc, 0, false, na ? &move : nullptr, s);
+      double nrm = 0.0, e = 0.0;
+      KS_CUDA(cudaMemcpyAsync(&nrm, norms_dev_, sizeof(double), cudaMemcpyDeviceToHost, s));
+      KS_CUDA(cudaMemcpyAsync(&e, energies_dev_, sizeof(double), cudaMemcpyDeviceToHost, s));
+      KS_CUDA(cudaStreamSynchronize(s));
+      check_tc_status(s);
+      if (st == 0) first_norm = nrm;
+      if (!std::isfinite(nrm) || !std::isfinite(e) || std::fabs(nrm / first_norm - 1.0) > 0.05)
+        fail(KS_ERR_DIVERGED, "Ehrenfest step %d: norm %g vs initial %g", st, nrm, first_norm);
+      if (na) forces(F1.data(), s);
+      for (int i = 0; i < 3 * na; ++i) {
+        vel[i] += (F[i] + F1[i]) * dt / (2.0 * mass[i / 3]);
+        F[i] = F1[i];
+      }
+      if (pos_out) std::memcpy(pos_out + 3 * (size_t)na * st, g_.pos.data(), 3 * (size_t)na * sizeof(double));
+      if (energy_out) energy_out[st] = e + kin;
+    }
+    if (hpsi_ == psi_) hpsi_ = spare(psi_, nullptr);
+  }
+
  private:
+  // One real-time step of the resident states from t to t + dt (ETRS with shared powers, or
+  // plain Taylor 4).  norms_dev_[slot] and energies_dev_[slot] receive the norm and energy at
+  // t, dipoles_dev_[3 slot] the dipole when `dipole`; `mid` (may be null) runs after the
+  // first half and before H(t+dt) is formed (the ions move there).
+  void td_step_body(double dt, int propagator, int hartree_xc, int slot, bool dipole, const std::function<void()>* mid,
+                    cudaStream_t s) {
+    const int n = ns_, nG = g_.nG;
+    const size_t sn = (size_t)n * nG;
+    // roles: psi, two power buffers, acc_full, acc_half
+    C* others[5];
+    int k = 0;
+    for (int i = 0; i < 6; ++i)
+      if (buf_[i] != psi_) others[k++] = buf_[i];
+    C* wa = others[0];
+    C* wb = others[1];
+    C* acc_full = others[2];
+    C* acc_half = others[3];
+    if (hartree_xc || dipole) density_of(psi_, n, dens_, s);
+    if (dipole) ks::dipole<T>(dens_, g_.N, g_.L, dip_partials_, HXC_BLOCKS, dipoles_dev_ + 3 * slot, s);
+    if (hartree_xc) update_potential(dens_, s);
+    state_dots<T>(psi_, psi_, nG, n, dots_, s);
+    weighted_energy(dots_, occ_, n, nullptr, norms_dev_ + slot, s);
+    // the accumulators start from psi in the first power's update (no copies)
+    const C* w = psi_;
+    double2 af = make_double2(1, 0), ah = make_double2(1, 0);
+    for (int kk = 1; kk <= 4; ++kk) {
+      C* wn = (w == wa) ? wb : wa;
+      apply_h(w, wn, n, s);
+      if (kk == 1) {
+        state_dots<T>(psi_, wn, nG, n, dots_, s);
+        weighted_energy(dots_, occ_, n, hartree_xc ? parts_ : nullptr, energies_dev_ + slot, s);
+      }
+      af = cmul_scalar(af, make_double2(0, -dt / kk));
+      ah = cmul_scalar(ah, make_double2(0, -0.5 * dt / kk));
+      axpy2<T>(acc_full, af, propagator == 0 ? acc_half : nullptr, ah, wn, kk == 1 ? psi_ : nullptr, sn, s);
+      w = wn;
+    }
+    if (propagator == 1) {
+      psi_ = acc_full;
+      return;
+    }
+    if (mid) (*mid)();
+    if (hartree_xc) {
+      density_of(acc_full, n, dens_, s);
+      update_potential(dens_, s);
+    }
+    // second half: out = acc_half + sum_k (-i dt/2)^k/k! H(t+dt)^k acc_half
+    w = acc_half;
+    ah = make_double2(1, 0);
+    for (int kk = 1; kk <= 4; ++kk) {
+      C* wn = (w == wa) ? wb : wa;
+      apply_h(w, wn, n, s);
+      ah = cmul_scalar(ah, make_double2(0, -0.5 * dt / kk));
+      axpy2<T>(acc_full, ah, nullptr, ah, wn, kk == 1 ? acc_half : nullptr, sn, s);
+      w = wn;
+    }
+    psi_ = acc_full;
+  }
+
+  // Work buffers of the force evaluation (allocated on first use).
+  void force_buffers() {
+    if (fw_) return;
+    const int N = g_.N, na = g_.natoms, np = g_.nproj;
+    const size_t N3 = (size_t)N * N * N;
+    fw_ = alloc<C>(N3);
+    fg_ = alloc<T>(3 * N3);
+    fp_ = alloc<C>((size_t)na * np);
+    fq_ = alloc<C>((size_t)na * np);
+    fnl_ = alloc<double>(3 * (size_t)na);
+    floc_ = alloc<double>(3 * (size_t)na);
+    fxyz_ = alloc<double>(3 * (size_t)na * N);
+    build_axis_tables();
+  }
+
+  // Per atom and axis: X_a(x) = sum_{s = -1, 0, 1} exp(-(x - R_a - L s)^2 / (2 w^2)) on the
+  // grid; V_loc = A sum_a X_a(x) Y_a(y) Z_a(z) and the local force both use them.
+  void build_axis_tables() {
+    const int N = g_.N, na = g_.natoms;
+    std::vector<double> xyz(3 * (size_t)na * N);
+    const double w2 = 2.0 * g_.vloc_width * g_.vloc_width;
+    for (int I = 0; I < na; ++I)
+      for (int a = 0; a < 3; ++a)
+        for (int j = 0; j < N; ++j) {
+          double v = 0.0;
+          for (int sh = -1; sh <= 1; ++sh) {
+            const double dx = g_.h * j - g_.pos[3 * I + a] - g_.L * sh;
+            v += std::exp(-dx * dx / w2);
+          }
+          xyz[((size_t)I * 3 + a) * N + j] = v;
+        }
+    KS_CUDA(cudaMemcpy(fxyz_, xyz.data(), xyz.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
   static double2 cmul_scalar(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
   }

@@ -13,10 +13,13 @@ class DeviceArena {
  public:
   ~DeviceArena();
   void* alloc(size_t bytes);
+  // Frees one allocation of this arena (the device is synchronised by cudaFree); null is a no-op.
+  void release(const void* p);
   size_t bytes() const { return total_; }
 
  private:
   std::vector<void*> ptrs_;
+  std::vector<size_t> sizes_;
   size_t total_ = 0;
 };
 
@@ -105,6 +108,9 @@ class EngineBase {
   virtual void kick(const double kappa[3], cudaStream_t s) = 0;
   virtual void dipole(double* d_host, cudaStream_t s) = 0;
   virtual void forces(double* f_host, cudaStream_t s) = 0;
+  virtual void set_positions(const double* pos, cudaStream_t s) = 0;
+  virtual void ehrenfest(double dt, int nsteps, int hartree_xc, const double* mass, double* vel, double* pos_out,
+                         double* energy_out, cudaStream_t s) = 0;
   virtual void randomize_states(uint64_t seed, cudaStream_t s) = 0;
 };
 

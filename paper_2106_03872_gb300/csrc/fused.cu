@@ -441,31 +441,7 @@ class FusedImpl final : public FusedOps {
     ncols_ = g.ncols;
     nprojtot_ = g.natoms * g.nproj;
     const size_t N3 = (size_t)N_ * N_ * N_;
-    // per-plane projector lists
-    std::vector<int> pt_off(N_ + 1, 0), pt_xy, ent_off(1, 0), ent_proj;
-    std::vector<float> ent_beta;
-    {
-      std::vector<std::vector<int>> byz(N_);
-      for (size_t c = 0; c < g.cov_idx.size(); ++c) byz[g.cov_idx[c] % N_].push_back((int)c);
-      for (int z = 0; z < N_; ++z) {
-        for (int c : byz[z]) {
-          pt_xy.push_back(g.cov_idx[c] / N_);
-          for (int e = g.cov_off[c]; e < g.cov_off[c + 1]; ++e) {
-            const int p = g.cov_ent[e];
-            ent_proj.push_back(g.sph_atom[p] * g.nproj);
-            for (int l = 0; l < g.nproj; ++l) ent_beta.push_back((float)g.sph_beta[(size_t)p * g.nproj + l]);
-          }
-          ent_off.push_back((int)ent_proj.size());
-        }
-        pt_off[z + 1] = (int)pt_xy.size();
-      }
-    }
-    nl_.pt_off = upload(pt_off);
-    nl_.pt_xy = upload(pt_xy);
-    nl_.ent_off = upload(ent_off);
-    nl_.ent_proj = upload(ent_proj);
-    nl_.ent_beta = upload(ent_beta);
-    nl_.nproj = g.nproj;
+    build_plane_lists();
     // buffers
     colbuf1_ = alloc<float2>((size_t)ns_ * N_ * ncols_);
     colbuf2_ = alloc<float2>((size_t)ns_ * N_ * ncols_);
@@ -502,6 +478,18 @@ class FusedImpl final : public FusedOps {
       ProfScope ps(prof_, "zfwd", s);
       dispatch([&](auto tag) { launch_zfwd<decltype(tag)::value>(psi, hpsi, n, s); });
     }
+  }
+
+  void set_atoms(const DevTables<float>& t) override {
+    KS_CUDA(cudaDeviceSynchronize());
+    t_ = t;
+    arena_.release(nl_.pt_off);
+    arena_.release(nl_.pt_xy);
+    arena_.release(nl_.ent_off);
+    arena_.release(nl_.ent_proj);
+    arena_.release(nl_.ent_beta);
+    build_plane_lists();
+    if (nprojtot_ > 0) build_projector_block();
   }
 
   void density(const float2* psi, int n, const double* occ, float* nout, cudaStream_t s) override {
@@ -588,6 +576,34 @@ class FusedImpl final : public FusedOps {
           colbuf1_, ncols_, t_.col_xy, g_.xr, n, occ, (float)(1.0 / g_.omega), dpartial_, t_.tw);
     }
     KS_CHECK_LAUNCH();
+  }
+
+  // Per-plane projector lists from the geometry's inverse lists: the covered points of each
+  // z-plane, each with its sphere entries (first projector row and the nproj beta values).
+  void build_plane_lists() {
+    const HostGeometry& g = g_;
+    std::vector<int> pt_off(N_ + 1, 0), pt_xy, ent_off(1, 0), ent_proj;
+    std::vector<float> ent_beta;
+    std::vector<std::vector<int>> byz(N_);
+    for (size_t c = 0; c < g.cov_idx.size(); ++c) byz[g.cov_idx[c] % N_].push_back((int)c);
+    for (int z = 0; z < N_; ++z) {
+      for (int c : byz[z]) {
+        pt_xy.push_back(g.cov_idx[c] / N_);
+        for (int e = g.cov_off[c]; e < g.cov_off[c + 1]; ++e) {
+          const int p = g.cov_ent[e];
+          ent_proj.push_back(g.sph_atom[p] * g.nproj);
+          for (int l = 0; l < g.nproj; ++l) ent_beta.push_back((float)g.sph_beta[(size_t)p * g.nproj + l]);
+        }
+        ent_off.push_back((int)ent_proj.size());
+      }
+      pt_off[z + 1] = (int)pt_xy.size();
+    }
+    nl_.pt_off = upload(pt_off);
+    nl_.pt_xy = upload(pt_xy);
+    nl_.ent_off = upload(ent_off);
+    nl_.ent_proj = upload(ent_proj);
+    nl_.ent_beta = upload(ent_beta);
+    nl_.nproj = g.nproj;
   }
 
   // B[atom*nproj + l][G] = c_G[beta_Il] = Omega^{1/2} N^-3 sum_j exp(-iG.r_j) beta_Il(r_j), FP64 FFT.

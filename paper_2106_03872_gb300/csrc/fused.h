@@ -18,6 +18,9 @@ class FusedOps {
   virtual void apply_h(const float2* psi, float2* hpsi, int n, const float* v, cudaStream_t s) = 0;
   // nout = sum_k occ[k] |psi_k(r)|^2 (grid order).
   virtual void density(const float2* psi, int n, const double* occ, float* nout, cudaStream_t s) = 0;
+  // The atoms moved: rebuild the per-plane projector lists and the projector block from the
+  // geometry's new sphere lists (t: the engine's re-uploaded tables).  Synchronous.
+  virtual void set_atoms(const DevTables<float>& t) = 0;
 };
 
 std::unique_ptr<FusedOps> make_fused_ops(const HostGeometry& g, const DevTables<float>& t, int nstates,

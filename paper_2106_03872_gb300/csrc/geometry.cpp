@@ -69,6 +69,119 @@ void count_sphere(double L, int N, double ecut, int* nG) {
   *nG = (int)count;
 }
 
+void build_atoms(const double* pos, HostGeometry& g, bool with_vloc) {
+  const int N = g.N;
+  const double L = g.L;
+  // ---- V_loc(r) = sum_a A exp(-|r - R_a - L n|^2 / (2 w^2)) over the 27 image shifts -------
+  // Terms with |r - R_a - L n| > 10 w are below 2e-22 |A| and are skipped.
+  g.pos.assign(pos ? pos : nullptr, pos ? pos + 3 * (size_t)g.natoms : nullptr);
+  const double w2 = 2.0 * g.vloc_width * g.vloc_width;
+  const double rcut = 10.0 * g.vloc_width;
+  if (with_vloc) g.vloc.assign((size_t)N * N * N, 0.0);
+  for (int a = 0; a < g.natoms && with_vloc; ++a) {
+    const double R[3] = {pos[3 * a], pos[3 * a + 1], pos[3 * a + 2]};
+    for (int sx = -1; sx <= 1; ++sx)
+      for (int sy = -1; sy <= 1; ++sy)
+        for (int sz = -1; sz <= 1; ++sz) {
+          const double C[3] = {R[0] + L * sx, R[1] + L * sy, R[2] + L * sz};
+          int lo[3], hi[3];
+          for (int k = 0; k < 3; ++k) {
+            lo[k] = std::max(0, (int)std::floor((C[k] - rcut) / g.h));
+            hi[k] = std::min(N - 1, (int)std::ceil((C[k] + rcut) / g.h));
+          }
+          for (int jx = lo[0]; jx <= hi[0]; ++jx)
+            for (int jy = lo[1]; jy <= hi[1]; ++jy)
+              for (int jz = lo[2]; jz <= hi[2]; ++jz) {
+                const double dx = jx * g.h - C[0], dy = jy * g.h - C[1], dz = jz * g.h - C[2];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 > rcut * rcut) continue;
+                g.vloc[((size_t)jx * N + jy) * N + jz] += g.vloc_depth * std::exp(-r2 / w2);
+              }
+        }
+  }
+  if (with_vloc) {
+    g.vmin = *std::min_element(g.vloc.begin(), g.vloc.end());
+    g.vmax = *std::max_element(g.vloc.begin(), g.vloc.end());
+  }
+
+  // ---- projector spheres |d| < R_c around each atom (minimum image), grid order ----------
+  g.sph_off.assign(1, 0);
+  g.sph_idx.clear();
+  g.sph_atom.clear();
+  g.sph_beta.clear();
+  const double s2 = 2.0 * g.proj_sigma * g.proj_sigma;
+  const double rc2 = g.proj_rc * g.proj_rc;
+  for (int a = 0; a < g.natoms; ++a) {
+    const double R[3] = {pos[3 * a], pos[3 * a + 1], pos[3 * a + 2]};
+    std::vector<int> pts;
+    int lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = (int)std::floor((R[k] - g.proj_rc) / g.h) - 1;
+      hi[k] = (int)std::ceil((R[k] + g.proj_rc) / g.h) + 1;
+    }
+    for (int ix = lo[0]; ix <= hi[0]; ++ix)
+      for (int iy = lo[1]; iy <= hi[1]; ++iy)
+        for (int iz = lo[2]; iz <= hi[2]; ++iz) {
+          const int jx = ((ix % N) + N) % N, jy = ((iy % N) + N) % N, jz = ((iz % N) + N) % N;
+          pts.push_back((jx * N + jy) * N + jz);
+        }
+    std::sort(pts.begin(), pts.end());
+    pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
+    std::vector<int> inside;
+    std::vector<double> dd;
+    for (int p : pts) {
+      const int jx = p / (N * N), jy = (p / N) % N, jz = p % N;
+      const int j3[3] = {jx, jy, jz};
+      double dv[3], r2 = 0;
+      for (int k = 0; k < 3; ++k) {
+        double t = j3[k] * g.h - R[k];
+        t -= L * std::nearbyint(t / L);
+        dv[k] = t;
+        r2 += t * t;
+      }
+      if (r2 < rc2) {
+        inside.push_back(p);
+        dd.push_back(dv[0]);
+        dd.push_back(dv[1]);
+        dd.push_back(dv[2]);
+        dd.push_back(r2);
+      }
+    }
+    const size_t np = inside.size();
+    std::vector<double> beta(np * g.nproj);
+    std::vector<double> norm(g.nproj, 0.0);
+    for (size_t i = 0; i < np; ++i) {
+      const double gs = std::exp(-dd[4 * i + 3] / s2);
+      beta[i * g.nproj] = gs;
+      if (g.nproj == 4)
+        for (int k = 0; k < 3; ++k) beta[i * 4 + 1 + k] = dd[4 * i + k] * gs;
+      for (int l = 0; l < g.nproj; ++l) norm[l] += beta[i * g.nproj + l] * beta[i * g.nproj + l];
+    }
+    for (int l = 0; l < g.nproj; ++l) {
+      const double s = (norm[l] > 0) ? 1.0 / std::sqrt(g.dV * norm[l]) : 0.0;
+      for (size_t i = 0; i < np; ++i) beta[i * g.nproj + l] *= s;
+    }
+    for (size_t i = 0; i < np; ++i) {
+      g.sph_idx.push_back(inside[i]);
+      g.sph_atom.push_back(a);
+      for (int l = 0; l < g.nproj; ++l) g.sph_beta.push_back(beta[i * g.nproj + l]);
+    }
+    g.sph_off.push_back((int)g.sph_idx.size());
+  }
+  // inverse lists (grid point -> its sphere points, atoms in index order)
+  std::map<int, std::vector<int>> cover;
+  for (size_t i = 0; i < g.sph_idx.size(); ++i) cover[g.sph_idx[i]].push_back((int)i);
+  g.cov_idx.clear();
+  g.cov_off.assign(1, 0);
+  g.cov_ent.clear();
+  for (auto& kv : cover) {
+    g.cov_idx.push_back(kv.first);
+    for (int e : kv.second) g.cov_ent.push_back(e);
+    g.cov_off.push_back((int)g.cov_ent.size());
+  }
+
+}
+
 void build_geometry(const ks_cell_desc& d, HostGeometry& g) {
   if (d.natoms < 0 || (d.natoms > 0 && !d.pos)) fail(KS_ERR_ARG, "natoms=%d with pos=%p", d.natoms, (const void*)d.pos);
   if (d.nproj != 1 && d.nproj != 4) fail(KS_ERR_ARG, "nproj must be 1 or 4, got %d", d.nproj);
@@ -130,116 +243,14 @@ void build_geometry(const ks_cell_desc& d, HostGeometry& g) {
   g.ncols = (int)g.col_xy.size();
   if (g.nG != nG) fail(KS_ERR_ARG, "internal: sphere count mismatch");
 
-  // ---- V_loc(r) = sum_a A exp(-|r - R_a - L n|^2 / (2 w^2)) over the 27 image shifts -------
-  // Terms with |r - R_a - L n| > 10 w are below 2e-22 |A| and are skipped.
-  g.vloc.assign((size_t)N * N * N, 0.0);
-  g.pos.assign(d.pos ? d.pos : nullptr, d.pos ? d.pos + 3 * (size_t)d.natoms : nullptr);
   g.vloc_depth = d.vloc_depth;
   g.vloc_width = d.vloc_width;
-  const double w2 = 2.0 * d.vloc_width * d.vloc_width;
-  const double rcut = 10.0 * d.vloc_width;
-  for (int a = 0; a < d.natoms; ++a) {
-    const double R[3] = {d.pos[3 * a], d.pos[3 * a + 1], d.pos[3 * a + 2]};
-    for (int sx = -1; sx <= 1; ++sx)
-      for (int sy = -1; sy <= 1; ++sy)
-        for (int sz = -1; sz <= 1; ++sz) {
-          const double C[3] = {R[0] + L * sx, R[1] + L * sy, R[2] + L * sz};
-          int lo[3], hi[3];
-          for (int k = 0; k < 3; ++k) {
-            lo[k] = std::max(0, (int)std::floor((C[k] - rcut) / g.h));
-            hi[k] = std::min(N - 1, (int)std::ceil((C[k] + rcut) / g.h));
-          }
-          for (int jx = lo[0]; jx <= hi[0]; ++jx)
-            for (int jy = lo[1]; jy <= hi[1]; ++jy)
-              for (int jz = lo[2]; jz <= hi[2]; ++jz) {
-                const double dx = jx * g.h - C[0], dy = jy * g.h - C[1], dz = jz * g.h - C[2];
-                const double r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 > rcut * rcut) continue;
-                g.vloc[((size_t)jx * N + jy) * N + jz] += d.vloc_depth * std::exp(-r2 / w2);
-              }
-        }
-  }
-  g.vmin = *std::min_element(g.vloc.begin(), g.vloc.end());
-  g.vmax = *std::max_element(g.vloc.begin(), g.vloc.end());
-
-  // ---- projector spheres |d| < R_c around each atom (minimum image), grid order ----------
   g.natoms = d.natoms;
   g.nproj = d.nproj;
   g.D = d.proj_D;
-  g.sph_off.assign(1, 0);
-  g.sph_idx.clear();
-  g.sph_atom.clear();
-  g.sph_beta.clear();
-  const double s2 = 2.0 * d.proj_sigma * d.proj_sigma;
-  const double rc2 = d.proj_rc * d.proj_rc;
-  for (int a = 0; a < d.natoms; ++a) {
-    const double R[3] = {d.pos[3 * a], d.pos[3 * a + 1], d.pos[3 * a + 2]};
-    std::vector<int> pts;
-    int lo[3], hi[3];
-    for (int k = 0; k < 3; ++k) {
-      lo[k] = (int)std::floor((R[k] - d.proj_rc) / g.h) - 1;
-      hi[k] = (int)std::ceil((R[k] + d.proj_rc) / g.h) + 1;
-    }
-    for (int ix = lo[0]; ix <= hi[0]; ++ix)
-      for (int iy = lo[1]; iy <= hi[1]; ++iy)
-        for (int iz = lo[2]; iz <= hi[2]; ++iz) {
-          const int jx = ((ix % N) + N) % N, jy = ((iy % N) + N) % N, jz = ((iz % N) + N) % N;
-          pts.push_back((jx * N + jy) * N + jz);
-        }
-    std::sort(pts.begin(), pts.end());
-    pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
-    std::vector<int> inside;
-    std::vector<double> dd;
-    for (int p : pts) {
-      const int jx = p / (N * N), jy = (p / N) % N, jz = p % N;
-      const int j3[3] = {jx, jy, jz};
-      double dv[3], r2 = 0;
-      for (int k = 0; k < 3; ++k) {
-        double t = j3[k] * g.h - R[k];
-        t -= L * std::nearbyint(t / L);
-        dv[k] = t;
-        r2 += t * t;
-      }
-      if (r2 < rc2) {
-        inside.push_back(p);
-        dd.push_back(dv[0]);
-        dd.push_back(dv[1]);
-        dd.push_back(dv[2]);
-        dd.push_back(r2);
-      }
-    }
-    const size_t np = inside.size();
-    std::vector<double> beta(np * d.nproj);
-    std::vector<double> norm(d.nproj, 0.0);
-    for (size_t i = 0; i < np; ++i) {
-      const double gs = std::exp(-dd[4 * i + 3] / s2);
-      beta[i * d.nproj] = gs;
-      if (d.nproj == 4)
-        for (int k = 0; k < 3; ++k) beta[i * 4 + 1 + k] = dd[4 * i + k] * gs;
-      for (int l = 0; l < d.nproj; ++l) norm[l] += beta[i * d.nproj + l] * beta[i * d.nproj + l];
-    }
-    for (int l = 0; l < d.nproj; ++l) {
-      const double s = (norm[l] > 0) ? 1.0 / std::sqrt(g.dV * norm[l]) : 0.0;
-      for (size_t i = 0; i < np; ++i) beta[i * d.nproj + l] *= s;
-    }
-    for (size_t i = 0; i < np; ++i) {
-      g.sph_idx.push_back(inside[i]);
-      g.sph_atom.push_back(a);
-      for (int l = 0; l < d.nproj; ++l) g.sph_beta.push_back(beta[i * d.nproj + l]);
-    }
-    g.sph_off.push_back((int)g.sph_idx.size());
-  }
-  // inverse lists (grid point -> its sphere points, atoms in index order)
-  std::map<int, std::vector<int>> cover;
-  for (size_t i = 0; i < g.sph_idx.size(); ++i) cover[g.sph_idx[i]].push_back((int)i);
-  g.cov_idx.clear();
-  g.cov_off.assign(1, 0);
-  g.cov_ent.clear();
-  for (auto& kv : cover) {
-    g.cov_idx.push_back(kv.first);
-    for (int e : kv.second) g.cov_ent.push_back(e);
-    g.cov_off.push_back((int)g.cov_ent.size());
-  }
+  g.proj_sigma = d.proj_sigma;
+  g.proj_rc = d.proj_rc;
+  build_atoms(d.pos, g, true);
 
   g.occ.assign(d.nstates, 1.0);
   if (d.occ)

@@ -201,6 +201,24 @@ __global__ void k_local_force(const T* __restrict__ g, const double* __restrict_
     for (int a = 0; a < 3; ++a) floc[3 * I + a] = coef * acc[a];
 }
 
+// The local potential of Gaussian atoms from their separable 27-image axis factors.
+template <typename T>
+__global__ void k_vloc_from_axes(const double* __restrict__ xyz, int natoms, int N, double depth, T* __restrict__ v,
+                                 double* __restrict__ v64) {
+  const size_t N3 = (size_t)N * N * N;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
+    const int jz = (int)(j % N), jy = (int)((j / N) % N), jx = (int)(j / ((size_t)N * N));
+    double acc = 0.0;
+    for (int I = 0; I < natoms; ++I) {
+      const double* X = xyz + (size_t)I * 3 * N;
+      acc += X[jx] * X[N + jy] * X[2 * N + jz];
+    }
+    acc *= depth;
+    v[j] = (T)acc;
+    if (v64) v64[j] = acc;
+  }
+}
+
 // Block partials of sum_j n_j (r_j - L/2) (three components), r_j = h (jx, jy, jz)
 template <typename T>
 __global__ void k_dipole_partials(const T* __restrict__ n, int N, double h, double L, double* __restrict__ partials) {
@@ -624,6 +642,13 @@ void local_force(const T* g, const double* xyz, int N, int natoms, double coef, 
 }
 
 template <typename T>
+void vloc_from_axes(const double* xyz, int natoms, int N, double depth, T* v, double* v64, cudaStream_t s) {
+  const size_t N3 = (size_t)N * N * N;
+  k_vloc_from_axes<T><<<blocks_for(N3, 256, 4096), 256, 0, s>>>(xyz, natoms, N, depth, v, v64);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
 void dipole(const T* n, int N, double L, double* partials, int nblocks, double* out, cudaStream_t s) {
   k_dipole_partials<T><<<nblocks, RED_THREADS, 0, s>>>(n, N, L / N, L, partials);
   KS_CHECK_LAUNCH();
@@ -791,6 +816,7 @@ void real_to_double(const T* in, double* out, size_t n, cudaStream_t s) {
   template void grad_accumulate<T>(const cplx<T>*, const cplx<T>*, T*, int, T, cudaStream_t);                   \
   template void nl_force<T>(const cplx<T>*, const cplx<T>*, int, int, double, double*, int, cudaStream_t);       \
   template void local_force<T>(const T*, const double*, int, int, double, double*, cudaStream_t);               \
+  template void vloc_from_axes<T>(const double*, int, int, double, T*, double*, cudaStream_t);                  \
   template void state_dots<T>(const cplx<T>*, const cplx<T>*, int, int, double2*, cudaStream_t);                \
   template void axpy2<T>(cplx<T>*, double2, cplx<T>*, double2, const cplx<T>*, const cplx<T>*, size_t, cudaStream_t);           \
   template void random_states<T>(cplx<T>*, size_t, uint64_t, cudaStream_t);                                     \

@@ -49,6 +49,10 @@ template <typename T> void nl_force(const cplx<T>* p, const cplx<T>* q, int nato
 // floc[3 I + a] = coef sum_j X_I[jx] Y_I[jy] Z_I[jz] g_a[j], g [3][N^3], xyz [natoms][3][N]
 template <typename T> void local_force(const T* g, const double* xyz, int N, int natoms, double coef, double* floc,
                                        cudaStream_t s);
+// v[j] = depth sum_I X_I[jx] Y_I[jy] Z_I[jz] (xyz as for local_force), in FP64; v64 (may be
+// NULL) receives the FP64 values
+template <typename T> void vloc_from_axes(const double* xyz, int natoms, int N, double depth, T* v, double* v64,
+                                          cudaStream_t s);
 // out[3] (device) = dV sum_j n_j (r_j - L/2); partials holds nblocks * 3 doubles
 template <typename T> void dipole(const T* n, int N, double L, double* partials, int nblocks, double* out,
                                   cudaStream_t s);

@@ -75,6 +75,14 @@ def cell(name, nstates=None, natoms=None, seed_offset=0):
                 seed=seed)
 
 
+def thermal_velocities(seed, mass, kT=9.5e-4):
+    """Seeded Maxwell-Boltzmann velocities [natoms, 3] (bohr per atomic time unit) for masses
+    [natoms] (electron masses) at temperature kT (Ha; the default is 300 K)."""
+    m = np.asarray(mass, float)
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(len(m), 3)) * np.sqrt(kT / m)[:, None]
+
+
 def small_cell(L, N, natoms, nstates, seed, depth=-2.0, nproj=4, ecut=20.0):
     """Arbitrary small cell with uniformly placed atoms, for parity sweeps."""
     return dict(L=float(L), N=int(N), ecut=float(ecut), pos=uniform_positions(seed, natoms, L),

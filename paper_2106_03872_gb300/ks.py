@@ -24,6 +24,7 @@ PRECISIONS = {"fp64": KS_FP64, "bf16x3": KS_MIXED_BF16X3, "tf32": KS_MIXED_TF32}
 EXPORTS = ["ks_count_gvectors", "ks_grid_create", "ks_grid_destroy", "ks_grid_gvectors", "ks_grid_device_bytes",
            "ks_get_vloc", "ks_set_states", "ks_get_states", "ks_states_device", "ks_apply_h", "ks_apply_h_host",
            "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_block_iteration_pc", "ks_scf", "ks_td_step", "ks_td_step_dipole", "ks_kick", "ks_dipole", "ks_forces",
+           "ks_set_positions", "ks_get_positions", "ks_ehrenfest",
            "ks_serve_create", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info",
            "ks_profile", "ks_profile_read", "ks_profile_span", "ks_kernel_launches", "ks_overlap_noalloc", "ks_last_error"]
 
@@ -79,6 +80,9 @@ def load():
         "ks_kick": [P, dp, P],
         "ks_dipole": [P, dp, P],
         "ks_forces": [P, dp, P],
+        "ks_set_positions": [P, dp, P],
+        "ks_get_positions": [P, dp],
+        "ks_ehrenfest": [P, ct.c_double, ct.c_int, ct.c_int, dp, dp, dp, dp, P],
         "ks_serve_create": [ct.c_size_t, ct.POINTER(P)],
         "ks_serve_destroy": [P],
         "ks_serve_submit": [P, ct.POINTER(CellDesc), dp, ct.c_int, ct.c_int, ct.c_double,
@@ -315,6 +319,32 @@ class Grid:
         f = np.zeros((max(natoms, 1), 3))
         check(load().ks_forces(self.h, _dptr(f), _stream_ptr(stream)))
         return f[:natoms]
+
+    def set_positions(self, pos, stream=None):
+        """Moves the atoms to pos [natoms][3] (bohr): V_loc and the projectors are rebuilt."""
+        p = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1)
+        if p.size != 3 * self.desc.natoms:
+            raise ValueError("pos must hold natoms x 3 values")
+        check(load().ks_set_positions(self.h, _dptr(p) if p.size else None, _stream_ptr(stream)))
+
+    def positions(self):
+        natoms = self.desc.natoms
+        p = np.zeros((max(natoms, 1), 3))
+        check(load().ks_get_positions(self.h, _dptr(p)))
+        return p[:natoms]
+
+    def ehrenfest(self, dt, nsteps, mass, vel, hartree_xc=True, stream=None):
+        """Ehrenfest dynamics (ETRS electrons, velocity-Verlet ions): returns (positions
+        [nsteps][natoms][3], final velocities [natoms][3], total energies [nsteps])."""
+        natoms = self.desc.natoms
+        m = np.ascontiguousarray(np.broadcast_to(np.asarray(mass, np.float64), (natoms,)))
+        v = np.ascontiguousarray(vel, dtype=np.float64).reshape(natoms, 3).copy()
+        pos = np.zeros((max(nsteps, 1), max(natoms, 1), 3))
+        e = np.zeros(max(nsteps, 1))
+        check(load().ks_ehrenfest(self.h, float(dt), int(nsteps), 1 if hartree_xc else 0,
+                                  _dptr(m) if natoms else None, _dptr(v) if natoms else None,
+                                  _dptr(pos), _dptr(e), _stream_ptr(stream)))
+        return pos[:nsteps, :natoms], v, e[:nsteps]
 
     def dipole(self, stream=None):
         """dV sum_j (r_j - L/2) n(r_j) of the resident states."""

@@ -721,3 +721,81 @@ def test_forces_no_atoms(ks):
     g.set_states(inputs.random_coeffs(64, 3, ref.nG))
     assert g.forces().shape == (0, 3)
     g.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# Moving atoms and Ehrenfest dynamics (Sec. "Real-time propagation")
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_set_positions_rebuilds_potential_and_projectors(ks, prec):
+    """After moving the atoms (one across the cell boundary, so that its projector sphere
+    wraps), V_loc, H psi and the forces match an oracle cell built at the new positions."""
+    cell = inputs.small_cell(10.0, 24, 3, 5, 65, depth=-3.0)
+    moved = np.array(cell["pos"]) + np.array([[0.7, -0.4, 0.25], [-0.3, 0.9, -1.1], [0.05, 0.1, 0.2]])
+    moved[0, 0] = 9.8                                                # next to the x = L face
+    ref = ko.Cell(dict(cell, pos=moved))
+    g = ks.Grid(cell, prec=prec)
+    c = inputs.random_coeffs(65, 5, ref.nG)
+    g.set_states(c)
+    g.set_positions(moved)
+    assert np.array_equal(g.positions(), moved)
+    assert np.max(np.abs(g.vloc() - ref.vloc)) <= 1e-13 * np.max(np.abs(ref.vloc))
+    got = apply_dev(ks, g, c, prec)
+    expect = ko.apply_h(ref, c)
+    for k in range(5):
+        assert rel(got[k], expect[k]) <= TOL_H[prec]
+    q = ko.block_iteration(ref, ko.cholqr(c)[0], 4)[1]
+    g.set_states(q)
+    F_ref = ko.forces(ref, q)
+    assert np.max(np.abs(g.forces() - F_ref)) <= (1e-10 if prec == "fp64" else 1e-4) * np.max(np.abs(F_ref))
+    with pytest.raises(ks.KsError):
+        g.set_positions(np.full((3, 3), np.nan))
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_ehrenfest_parity(ks, prec):
+    """Three Ehrenfest steps with Hartree and exchange against the oracle: positions,
+    velocities, total energies and states."""
+    desc = dict(L=8.0, N=24, ecut=20.0, pos=np.array([[2.0, 2.5, 3.0], [5.5, 4.0, 4.5]]), vloc_depth=-3.0,
+                vloc_width=0.8, nproj=4, proj_sigma=0.5, proj_rc=2.0, proj_D=0.5, nstates=4)
+    ref = ko.Cell(desc)
+    c = ko.cholqr(ko.block_iteration(ref, inputs.random_coeffs(66, 4, ref.nG), 10)[1])[0]
+    mass = np.array([20.0, 30.0])
+    v0 = np.array([[0.05, 0.0, -0.03], [-0.03, 0.04, 0.0]])
+    c_ref, P_ref, V_ref, E_ref = ko.ehrenfest_run(desc, c, 0.1, 3, mass, v0)
+    g = ks.Grid(desc, prec=prec)
+    g.set_states(c)
+    P, V, E = g.ehrenfest(0.1, 3, mass, v0)
+    dtol = 1e-10 if prec == "fp64" else 1e-5
+    assert np.max(np.abs(P - P_ref)) <= dtol * np.max(np.abs(P_ref - desc["pos"]))
+    assert np.max(np.abs(V - V_ref[-1])) <= (1e-10 if prec == "fp64" else 1e-4) * np.max(np.abs(V_ref[-1]))
+    assert np.max(np.abs(E - E_ref)) <= (1e-10 if prec == "fp64" else 1e-4) * np.max(np.abs(E_ref))
+    assert rel(g.get_states(), c_ref) <= (1e-10 if prec == "fp64" else 1e-4)
+    assert np.array_equal(g.positions(), P[-1])
+    g.close()
+
+
+def test_ehrenfest_immobile_ions_match_td_step(ks):
+    """Masses so large that the ions stay put: the same norms, energies and states as the
+    plain real-time steps (V_loc is recomputed on the device each step: equal to rounding)."""
+    desc = dict(L=8.0, N=24, ecut=20.0, pos=np.array([[2.0, 2.5, 3.0], [5.5, 4.0, 4.5]]), vloc_depth=-3.0,
+                vloc_width=0.8, nproj=4, proj_sigma=0.5, proj_rc=2.0, proj_D=0.5, nstates=4)
+    ref = ko.Cell(desc)
+    c = ko.cholqr(inputs.random_coeffs(67, 4, ref.nG))[0]
+    a = ks.Grid(desc, prec="fp64")
+    b = ks.Grid(desc, prec="fp64")
+    a.set_states(c)
+    b.set_states(c)
+    P, V, E = a.ehrenfest(0.05, 3, [1e300, 1e300], np.zeros((2, 3)))
+    _, e = b.td_step(0.05, 3)
+    assert np.array_equal(P[-1], desc["pos"]) and np.max(np.abs(V)) < 1e-250
+    assert np.max(np.abs(E - e)) <= 1e-12 * np.max(np.abs(e))
+    assert rel(a.get_states(), b.get_states()) <= 1e-12
+    for bad in (dict(dt=0.0), dict(nsteps=-1), dict(mass=[1.0, -1.0]), dict(mass=[1.0, np.inf])):
+        kw = dict(dt=0.05, nsteps=1, mass=[1.0, 1.0], vel=np.zeros((2, 3)))
+        kw.update(bad)
+        with pytest.raises(ks.KsError):
+            a.ehrenfest(**kw)
+    a.close()
+    b.close()
