@@ -221,10 +221,11 @@ ks_status ks_forces(ks_grid g, double* f_out, void* stream);
  * ionic configuration).  pos [natoms][3] (host, bohr, finite; positions outside [0, L) are
  * periodic images).  Rebuilds, for the same atoms and parameters as at creation: the
  * projector spheres |r_j - R_I| < proj_rc (minimum image) with their normalised beta values,
- * the projector block of the mixed path (FP64 FFT), and V_loc from the separable 27-image
- * Gaussians (in FP64 on the device).  The potential V becomes the new V_loc (a following
- * SCF or real-time step recomputes Hartree and exchange).  The states are kept.  No-op when
- * natoms = 0.  KS_ERR_ARG on a non-finite position.  Synchronous. */
+ * the projector block of the mixed path (FP64 DFT over each atom's box of grid points), and
+ * V_loc from the separable 27-image Gaussians (in FP64 on the device).  The potential V
+ * becomes the new V_loc (a following SCF or real-time step recomputes Hartree and exchange).
+ * The states are kept.  No-op when natoms = 0.  KS_ERR_ARG on a non-finite position.
+ * Synchronous. */
 ks_status ks_set_positions(ks_grid g, const double* pos, void* stream);
 
 /* The current positions pos [natoms][3] (host, bohr). */

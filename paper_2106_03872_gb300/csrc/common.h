@@ -84,7 +84,7 @@ struct HostGeometry {
   std::vector<int> col_off;     // first packed index of the column
   std::vector<int> col_half;    // hz
   int xr = 0;                   // columns exist only for |m_x| <= xr (and |m_y| <= xr)
-  std::vector<double> vloc;     // [N^3] grid order
+  std::vector<double> vloc;     // [N^3] grid order (host copy of the device-formed V_loc)
   double vmin = 0, vmax = 0;
   std::vector<double> pos;      // [natoms][3] atom positions (bohr)
   double vloc_depth = 0, vloc_width = 0;
@@ -106,8 +106,9 @@ struct HostGeometry {
 bool valid_fft_length(int N);
 void count_sphere(double L, int N, double ecut, int* nG);
 void build_geometry(const ks_cell_desc& d, HostGeometry& g);
-// Rebuilds the atom-dependent parts (pos, the projector sphere lists and their inverse lists;
-// V_loc on the host when with_vloc) for new positions pos [natoms][3] of the same atoms.
-void build_atoms(const double* pos, HostGeometry& g, bool with_vloc);
+// Rebuilds the atom-dependent parts (pos, the projector sphere lists and their inverse lists)
+// for new positions pos [natoms][3] of the same atoms.  V_loc, vmin and vmax are the
+// engine's to fill (on the device).
+void build_atoms(const double* pos, HostGeometry& g);
 
 }  // namespace ks

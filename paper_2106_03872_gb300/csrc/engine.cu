@@ -160,9 +160,8 @@ template <typename T> class Engine final : public EngineBase {
     t_.cov_idx = upload(g_.cov_idx);
     t_.cov_off = upload(g_.cov_off);
     t_.cov_ent = upload(g_.cov_ent);
-    vloc_ = const_cast<T*>(upload_real(g_.vloc));
+    vloc_ = alloc<T>(N3);
     vtot_ = alloc<T>(N3);
-    KS_CUDA(cudaMemcpy(vtot_, vloc_, N3 * sizeof(T), cudaMemcpyDeviceToDevice));
     occ_ = const_cast<double*>(upload(g_.occ));
     // ---- states: 6 buffers (resident psi, H psi, and 4 work buffers for the real-time step)
     for (int i = 0; i < 6; ++i) {
@@ -230,7 +229,7 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaEventCreateWithFlags(&ev_hraw_, cudaEventDisableTiming));
     KS_CUDA(cudaEventCreateWithFlags(&ev_chol_, cudaEventDisableTiming));
     KS_CUDA(cudaEventCreateWithFlags(&ev_ritz_, cudaEventDisableTiming));
-    KS_CUDA(cudaStreamSynchronize(nullptr));
+    update_vloc(nullptr);
   }
 
   ~Engine() override {
@@ -815,23 +814,40 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaMemsetAsync(fg_, 0, 3 * N3 * sizeof(T), s));
     KS_CUDA(cudaMemsetAsync(fnl_, 0, 3 * (size_t)na * sizeof(double), s));
     const T pscale = T(g_.dV / std::sqrt(g_.omega));   // grids hold Omega^{1/2} psi
-    for (int b = 0; b < ns_; ++b) {
-      const C* st = psi_ + (size_t)b * g_.nG;
-      const double f = g_.occ[b];
-      KS_CUDA(cudaMemsetAsync(pwork_, 0, N3 * sizeof(C), s));
-      scatter_sphere<T>(st, pwork_, t_, 1, s);
-      for (int ax = 2; ax >= 0; --ax) fft_axis<T>(pwork_, 1, N, ax, +1, t_.tw, s);
-      nl_project<T>(pwork_, t_, fp_, 1, pscale, s);
+    // chunks of fb_ states: psi and one gradient component of every state of the chunk on the
+    // full grid, transformed together.  The mixed path transforms with its pruned z-columns
+    // and in-SMEM plane passes (planes stored [z][x][y]); the FP64 path with full-grid FFTs.
+    bool zmajor = false;
+    C* gpack = spare(psi_, hpsi_);                                    // i G_a c of a chunk (packed)
+    for (int b0 = 0; b0 < ns_; b0 += fb_) {
+      const int nb = std::min(fb_, ns_ - b0);
+      const C* st = psi_ + (size_t)b0 * g_.nG;
+      auto to_grid = [&](const C* packed, C* grid, int a) {
+        if constexpr (sizeof(T) == 4) {
+          if (fused_) {
+            if (a >= 0) grad_packed<T>(packed, gpack, t_, a, nb, s);
+            fused_->real_space(a >= 0 ? gpack : packed, nb, grid, s);
+            zmajor = true;
+            return;
+          }
+        }
+        KS_CUDA(cudaMemsetAsync(grid, 0, nb * N3 * sizeof(C), s));
+        if (a >= 0)
+          scatter_grad<T>(packed, grid, t_, a, nb, s);
+        else
+          scatter_sphere<T>(packed, grid, t_, nb, s);
+        for (int ax = 2; ax >= 0; --ax) fft_axis<T>(grid, nb, N, ax, +1, t_.tw, s);
+      };
+      to_grid(st, fpsi_, -1);
+      nl_project<T>(fpsi_, t_, fp_, nb, pscale, s, zmajor);
       for (int a = 0; a < 3; ++a) {
-        KS_CUDA(cudaMemsetAsync(fw_, 0, N3 * sizeof(C), s));
-        scatter_grad<T>(st, fw_, t_, a, s);
-        for (int ax = 2; ax >= 0; --ax) fft_axis<T>(fw_, 1, N, ax, +1, t_.tw, s);
-        nl_project<T>(fw_, t_, fq_, 1, pscale, s);
-        grad_accumulate<T>(fw_, pwork_, fg_ + a * N3, (int)N3, T(f), s);
-        nl_force<T>(fp_, fq_, na, np, 2.0 * g_.D * f, fnl_, a, s);
+        to_grid(st, fw_, a);
+        nl_project<T>(fw_, t_, fq_, nb, pscale, s, zmajor);
+        grad_accumulate<T>(fw_, fpsi_, fg_ + a * N3, (int)N3, nb, occ_ + b0, s);
+        nl_force<T>(fp_, fq_, na, np, nb, 2.0 * g_.D, occ_ + b0, fnl_, a, s);
       }
     }
-    local_force<T>(fg_, fxyz_, N, na, -g_.dV * g_.vloc_depth / g_.omega, floc_, s);
+    local_force<T>(fg_, fxyz_, N, na, -g_.dV * g_.vloc_depth / g_.omega, floc_, s, zmajor);
     std::vector<double> fl(3 * (size_t)na), fn(3 * (size_t)na);
     KS_CUDA(cudaMemcpyAsync(fl.data(), floc_, fl.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     KS_CUDA(cudaMemcpyAsync(fn.data(), fnl_, fn.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -889,7 +905,7 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaStreamSynchronize(s));
     KS_CUDA(cudaDeviceSynchronize());
     ProfScope p(prof, "set_positions", s);
-    build_atoms(pos, g_, false);
+    build_atoms(pos, g_);
     // projector sphere lists (their sizes change as grid points enter and leave the spheres)
     for (const void* q : {(const void*)t_.sph_off, (const void*)t_.sph_idx, (const void*)t_.sph_atom,
                           (const void*)t_.sph_beta, (const void*)t_.cov_idx, (const void*)t_.cov_off,
@@ -903,17 +919,7 @@ template <typename T> class Engine final : public EngineBase {
     t_.cov_off = upload(g_.cov_off);
     t_.cov_ent = upload(g_.cov_ent);
     t_.ncov = (int)g_.cov_idx.size();
-    // V_loc from the separable 27-image Gaussians, in FP64 on the device, with a host copy
-    force_buffers();
-    build_axis_tables();
-    double* v64 = reinterpret_cast<double*>(pwork_);                  // N^3 doubles fit the work grid
-    vloc_from_axes<T>(fxyz_, na, N, g_.vloc_depth, vloc_, v64, s);
-    g_.vloc.resize(N3);
-    KS_CUDA(cudaMemcpyAsync(g_.vloc.data(), v64, N3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    KS_CUDA(cudaMemcpyAsync(vtot_, vloc_, N3 * sizeof(T), cudaMemcpyDeviceToDevice, s));
-    KS_CUDA(cudaStreamSynchronize(s));
-    g_.vmin = *std::min_element(g_.vloc.begin(), g_.vloc.end());
-    g_.vmax = *std::max_element(g_.vloc.begin(), g_.vloc.end());
+    update_vloc(s);
     if constexpr (sizeof(T) == 4) {
       if (fused_) fused_->set_atoms(t_);
     }
@@ -1022,25 +1028,43 @@ template <typename T> class Engine final : public EngineBase {
     psi_ = acc_full;
   }
 
-  // Work buffers of the force evaluation (allocated on first use).
+  // V = V_loc from the separable 27-image Gaussians of the current positions, in FP64 on the
+  // device, with the host copy g_.vloc and its extremes (the steepest-descent step uses them).
+  void update_vloc(cudaStream_t s) {
+    const int N = g_.N;
+    const size_t N3 = (size_t)N * N * N;
+    build_axis_tables();
+    double* v64 = reinterpret_cast<double*>(pwork_);                  // N^3 doubles fit the work grid
+    vloc_from_axes<T>(fxyz_, g_.natoms, N, g_.vloc_depth, vloc_, v64, s);
+    g_.vloc.resize(N3);
+    KS_CUDA(cudaMemcpyAsync(g_.vloc.data(), v64, N3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaMemcpyAsync(vtot_, vloc_, N3 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    KS_CUDA(cudaStreamSynchronize(s));
+    g_.vmin = *std::min_element(g_.vloc.begin(), g_.vloc.end());
+    g_.vmax = *std::max_element(g_.vloc.begin(), g_.vloc.end());
+  }
+
+  // Work buffers of the force evaluation (allocated on first use): full grids for a chunk of
+  // fb_ states (at most 512 MB for the two), their projections, the gradient densities.
   void force_buffers() {
     if (fw_) return;
     const int N = g_.N, na = g_.natoms, np = g_.nproj;
     const size_t N3 = (size_t)N * N * N;
-    fw_ = alloc<C>(N3);
+    fb_ = (int)std::max<size_t>(1, std::min<size_t>((size_t)ns_, (size_t(512) << 20) / (2 * N3 * sizeof(C))));
+    fpsi_ = alloc<C>((size_t)fb_ * N3);
+    fw_ = alloc<C>((size_t)fb_ * N3);
     fg_ = alloc<T>(3 * N3);
-    fp_ = alloc<C>((size_t)na * np);
-    fq_ = alloc<C>((size_t)na * np);
+    fp_ = alloc<C>((size_t)fb_ * na * np);
+    fq_ = alloc<C>((size_t)fb_ * na * np);
     fnl_ = alloc<double>(3 * (size_t)na);
     floc_ = alloc<double>(3 * (size_t)na);
-    fxyz_ = alloc<double>(3 * (size_t)na * N);
-    build_axis_tables();
   }
 
   // Per atom and axis: X_a(x) = sum_{s = -1, 0, 1} exp(-(x - R_a - L s)^2 / (2 w^2)) on the
   // grid; V_loc = A sum_a X_a(x) Y_a(y) Z_a(z) and the local force both use them.
   void build_axis_tables() {
     const int N = g_.N, na = g_.natoms;
+    if (!fxyz_) fxyz_ = alloc<double>(std::max<size_t>(1, 3 * (size_t)na * N));
     std::vector<double> xyz(3 * (size_t)na * N);
     const double w2 = 2.0 * g_.vloc_width * g_.vloc_width;
     for (int I = 0; I < na; ++I)
@@ -1178,7 +1202,9 @@ template <typename T> class Engine final : public EngineBase {
   double* resid_dev_ = nullptr;     // SCF residual
   double* dip_partials_ = nullptr;  // dipole block partials
   double2* trr_ = nullptr;          // per-state residual kinetic sums of the preconditioned update
-  C* fw_ = nullptr;                 // forces: gradient grid, accumulators, projections (on first use)
+  C* fw_ = nullptr;                 // forces: state and gradient grids of a chunk, accumulators,
+  C* fpsi_ = nullptr;               // projections (on first use)
+  int fb_ = 1;
   T* fg_ = nullptr;
   C *fp_ = nullptr, *fq_ = nullptr;
   double *fnl_ = nullptr, *floc_ = nullptr, *fxyz_ = nullptr;

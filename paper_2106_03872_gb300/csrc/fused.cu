@@ -12,7 +12,8 @@
 // The projections p_Il = dV sum_j beta_Il(r_j) psi(r_j) (Eq. 9) are computed before the
 // plane pass, in Fourier space: on the grid, by Parseval, p_Il = sum_{G in S}
 // conj(b_Il(G)) c_G with b_Il the sphere coefficients of the grid function beta_Il (built
-// once at setup with the FP64 FFT).  That is one overlap GEMM of the projector block with
+// at setup, and again when the atoms move, by a separable FP64 DFT over each atom's box).
+// That is one overlap GEMM of the projector block with
 // the state block; the add stays in real space, fused into the plane kernel.
 #include <cooperative_groups.h>
 
@@ -279,6 +280,26 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
   }
 }
 
+// Real-space planes of the states (forces, Eq. 11, need psi and its gradient on the grid):
+// one (state, z-plane) per CTA, the inverse y and x passes of k_plane, then the plane is
+// stored contiguously at out[b][z] ([x][y], row pitch N).
+template <int N>
+__global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
+    k_plane_inverse(const float2* __restrict__ colbuf1, int ncols, const int* __restrict__ col_xy, int xr,
+                    const float2* __restrict__ twg, float2* __restrict__ out) {
+  constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC;
+  extern __shared__ __align__(16) float2 psm[];
+  float2* tw = psm;
+  float2* P = psm + N;
+  const int z = blockIdx.x, b = blockIdx.y;
+  for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
+  const size_t row = ((size_t)b * N + z) * ncols;
+  plane_load_y<N>(P, colbuf1 + row, ncols, col_xy, xr, tw);
+  cfft_lines<N, PT, LPC, true, +1>(P, N, 1, ld, tw);
+  float2* o = out + ((size_t)b * N + z) * N * N;
+  for (int e = threadIdx.x; e < N * N; e += PT) o[e] = P[(e / N) * ld + (e - (e / N) * N)];
+}
+
 // Density partial sums: one (z-plane, state) per CTA; a cluster holds DCL consecutive states
 // of one plane.  Each CTA transforms its state and writes f |u|^2 into its own shared-memory
 // plane (fused into the last stage of the inverse x transform).  The cluster then sums its
@@ -399,24 +420,92 @@ __global__ void k_proj_to_states(const double2* __restrict__ pout, int nprojtot,
 }
 
 // Setup: projector grid functions -> sphere coefficients (FP64), then rounded to complex64.
-__global__ void k_scatter_projectors(const int* __restrict__ sph_off, const int* __restrict__ sph_idx,
-                                     const double* __restrict__ beta, int nproj, int p0, int np, size_t N3,
-                                     double2* __restrict__ grid) {
-  const int k = blockIdx.y;            // projector row p0 + k = atom * nproj + l
-  const int row = p0 + k;
-  const int atom = row / nproj, l = row % nproj;
-  for (int p = sph_off[atom] + blockIdx.x * blockDim.x + threadIdx.x; p < sph_off[atom + 1];
-       p += gridDim.x * blockDim.x)
-    grid[k * N3 + sph_idx[p]] = make_double2(beta[(size_t)p * nproj + l], 0.0);
-  (void)np;
+// The projector block by a separable DFT over each atom's box of grid points (Sec.
+// "Pseudopotentials": beta_Il lives on the sphere |r - R_I| < R_c, so its sphere coefficients
+// are a DFT of a function supported on a small box).  Box coordinates b = 0..B-1 stand for the
+// unwrapped grid index lo + b of the atom's minimum-image sphere; exp(-2 pi i m j / N) is
+// periodic in j, so the unwrapped index gives the phase directly.  FP64 throughout.
+//   T1[p][bx][by][mz] = sum_bz beta[p][bx][by][bz] e(mz (lo_z + bz))
+//   T2[p][bx][my][mz] = sum_by T1[p][bx][by][mz] e(my (lo_y + by))
+//   B[p][G]          = scale sum_bx T2[p][bx][my][mz] e(mx (lo_x + bx)),  e(t) = exp(-2 pi i t / N)
+// with m_y, m_z in [-xr, xr] stored at index m + xr.
+__device__ __forceinline__ int mod_n(long v, int N) {
+  const int r = (int)(v % N);
+  return r < 0 ? r + N : r;
 }
 
-__global__ void k_gather_projectors(const double2* __restrict__ grid, const int* __restrict__ gidx, int nG, size_t N3,
-                                    double scale, float2* __restrict__ B) {
-  const int k = blockIdx.y;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nG; g += gridDim.x * blockDim.x) {
-    const double2 v = grid[k * N3 + gidx[g]];
-    B[(size_t)k * nG + g] = make_float2((float)(v.x * scale), (float)(v.y * scale));
+__global__ void k_box_dft_z(const double* __restrict__ box, const int* __restrict__ lo, int nproj, int nrows, int B,
+                            int xr, int N, const double2* __restrict__ tw, double2* __restrict__ T1) {
+  const int M = 2 * xr + 1;
+  const size_t total = (size_t)nrows * B * B * M;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int mi = (int)(e % M);
+    const size_t pb = e / M;                                          // (p, bx, by)
+    const int p = (int)(pb / ((size_t)B * B));
+    const int m = mi - xr;
+    const int step = mod_n(m, N);
+    int t = mod_n((long)m * lo[3 * (p / nproj) + 2], N);
+    const double* v = box + pb * B;
+    double ax = 0.0, ay = 0.0;
+    for (int bz = 0; bz < B; ++bz) {
+      const double2 w = tw[t];                                        // (cos, sin)(2 pi t / N)
+      ax += v[bz] * w.x;
+      ay -= v[bz] * w.y;
+      t += step;
+      if (t >= N) t -= N;
+    }
+    T1[e] = make_double2(ax, ay);
+  }
+}
+
+__global__ void k_box_dft_y(const double2* __restrict__ T1, const int* __restrict__ lo, int nproj, int nrows, int B,
+                            int xr, int N, const double2* __restrict__ tw, double2* __restrict__ T2) {
+  const int M = 2 * xr + 1;
+  const size_t total = (size_t)nrows * B * M * M;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int mz = (int)(e % M);
+    const int my = (int)((e / M) % M);
+    const size_t pbx = e / ((size_t)M * M);                           // (p, bx)
+    const int p = (int)(pbx / B);
+    const int m = my - xr;
+    const int step = mod_n(m, N);
+    int t = mod_n((long)m * lo[3 * (p / nproj) + 1], N);
+    const double2* v = T1 + pbx * B * M + mz;                         // v[by * M]
+    double ax = 0.0, ay = 0.0;
+    for (int by = 0; by < B; ++by) {
+      const double2 w = tw[t], x = v[(size_t)by * M];
+      ax += x.x * w.x + x.y * w.y;                                    // x * conj(w)
+      ay += x.y * w.x - x.x * w.y;
+      t += step;
+      if (t >= N) t -= N;
+    }
+    T2[e] = make_double2(ax, ay);
+  }
+}
+
+__global__ void k_box_dft_x(const double2* __restrict__ T2, const int* __restrict__ lo, const int* __restrict__ gidx,
+                            int nproj, int nrows, int B, int xr, int N, int nG, double scale,
+                            const double2* __restrict__ tw, float2* __restrict__ out) {
+  const int M = 2 * xr + 1;
+  const size_t total = (size_t)nrows * nG;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int g = (int)(e % nG);
+    const int p = (int)(e / nG);
+    const int idx = gidx[g];
+    const int jx = idx / (N * N), jy = (idx / N) % N, jz = idx % N;
+    const int mx = 2 * jx < N ? jx : jx - N, my = 2 * jy < N ? jy : jy - N, mz = 2 * jz < N ? jz : jz - N;
+    const int step = mod_n(mx, N);
+    int t = mod_n((long)mx * lo[3 * (p / nproj)], N);
+    const double2* v = T2 + (size_t)p * B * M * M + (size_t)(my + xr) * M + (mz + xr);   // v[bx * M * M]
+    double ax = 0.0, ay = 0.0;
+    for (int bx = 0; bx < B; ++bx) {
+      const double2 w = tw[t], x = v[(size_t)bx * M * M];
+      ax += x.x * w.x + x.y * w.y;
+      ay += x.y * w.x - x.x * w.y;
+      t += step;
+      if (t >= N) t -= N;
+    }
+    out[e] = make_float2((float)(ax * scale), (float)(ay * scale));
   }
 }
 
@@ -478,6 +567,12 @@ class FusedImpl final : public FusedOps {
       ProfScope ps(prof_, "zfwd", s);
       dispatch([&](auto tag) { launch_zfwd<decltype(tag)::value>(psi, hpsi, n, s); });
     }
+  }
+
+  void real_space(const float2* psi, int n, float2* out, cudaStream_t s) override {
+    zinv(psi, n, s);
+    ProfScope ps(prof_, "plane_inverse", s);
+    dispatch([&](auto tag) { launch_plane_inverse<decltype(tag)::value>(n, out, s); });
   }
 
   void set_atoms(const DevTables<float>& t) override {
@@ -552,6 +647,16 @@ class FusedImpl final : public FusedOps {
                                                                    vplane_, nl_, pf_, nprojtot_, pf_smem, t_.tw);
     KS_CHECK_LAUNCH();
   }
+  template <int N> void launch_plane_inverse(int n, float2* out, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+      KS_CUDA(cudaFuncSetAttribute(k_plane_inverse<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX));
+      attr = true;
+    }
+    k_plane_inverse<N><<<dim3(N, n), FCfg<N>::PT, plane_smem<N>(), s>>>(colbuf1_, ncols_, t_.col_xy, g_.xr, t_.tw,
+                                                                         out);
+    KS_CHECK_LAUNCH();
+  }
   // states per density partial: a cluster of DCL states, or a chunk per CTA at N = 128
   int density_chunk() const { return N_ >= 128 ? std::max(1, std::min(32, (ns_ + 7) / 8)) : DCL; }
 
@@ -606,42 +711,74 @@ class FusedImpl final : public FusedOps {
     nl_.nproj = g.nproj;
   }
 
-  // B[atom*nproj + l][G] = c_G[beta_Il] = Omega^{1/2} N^-3 sum_j exp(-iG.r_j) beta_Il(r_j), FP64 FFT.
+  // B[atom*nproj + l][G] = c_G[beta_Il] = Omega^{1/2} N^-3 sum_j exp(-iG.r_j) beta_Il(r_j), by the
+  // separable DFT over each atom's box (k_box_dft_*), FP64.
   void build_projector_block() {
-    const int N = N_;
-    const size_t N3 = (size_t)N * N * N;
-    const int batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)nprojtot_, (size_t(512) << 20) / (N3 * 16)));
-    double2* grid = nullptr;
-    int* sph_off = nullptr;
-    int* sph_idx = nullptr;
-    double* beta = nullptr;
-    double2* tw = nullptr;
-    KS_CUDA(cudaMalloc(&grid, (size_t)batch * N3 * sizeof(double2)));
-    KS_CUDA(cudaMalloc(&sph_off, g_.sph_off.size() * sizeof(int)));
-    KS_CUDA(cudaMalloc(&sph_idx, std::max<size_t>(1, g_.sph_idx.size()) * sizeof(int)));
-    KS_CUDA(cudaMalloc(&beta, std::max<size_t>(1, g_.sph_beta.size()) * sizeof(double)));
+    const HostGeometry& g = g_;
+    const int N = N_, na = g.natoms, np = g.nproj;
+    int xr = 0;                                                       // max |m| over S, every axis
+    for (int v : g.mvec) xr = std::max(xr, std::abs(v));
+    const int M = 2 * xr + 1;
+    // unwrapped grid coordinates of the sphere points (the minimum image of build_atoms) and
+    // the box that holds each atom's sphere
+    std::vector<int> lo(3 * (size_t)na, 0), hi(3 * (size_t)na, 0), ju(3 * g.sph_idx.size());
+    int B = 1;
+    for (int a = 0; a < na; ++a) {
+      for (int p = g.sph_off[a]; p < g.sph_off[a + 1]; ++p) {
+        const int idx = g.sph_idx[p];
+        const int j3[3] = {idx / (N * N), (idx / N) % N, idx % N};
+        for (int k = 0; k < 3; ++k) {
+          const double t = j3[k] * g.h - g.pos[3 * a + k];
+          const int u = j3[k] - N * (int)std::nearbyint(t / g.L);
+          ju[3 * (size_t)p + k] = u;
+          if (p == g.sph_off[a] || u < lo[3 * a + k]) lo[3 * a + k] = u;
+          if (p == g.sph_off[a] || u > hi[3 * a + k]) hi[3 * a + k] = u;
+        }
+      }
+      if (g.sph_off[a + 1] > g.sph_off[a])
+        for (int k = 0; k < 3; ++k) B = std::max(B, hi[3 * a + k] - lo[3 * a + k] + 1);
+    }
+    std::vector<double> box((size_t)nprojtot_ * B * B * B, 0.0);
+    for (int a = 0; a < na; ++a)
+      for (int p = g.sph_off[a]; p < g.sph_off[a + 1]; ++p) {
+        const size_t bx = ju[3 * (size_t)p] - lo[3 * a], by = ju[3 * (size_t)p + 1] - lo[3 * a + 1],
+                     bz = ju[3 * (size_t)p + 2] - lo[3 * a + 2];
+        for (int l = 0; l < np; ++l)
+          box[(((size_t)(a * np + l) * B + bx) * B + by) * B + bz] = g.sph_beta[(size_t)p * np + l];
+      }
+    // rows in chunks of whole atoms (the intermediate sums of a chunk stay below ~64 MB)
+    const size_t per_row = (size_t)B * M * (B + M) * sizeof(double2);
+    const int chunk = np * std::max(1, (int)std::min<size_t>(na, (size_t(64) << 20) / (per_row * np)));
+    double* dbox = nullptr;
+    int* dlo = nullptr;
+    double2 *tw = nullptr, *T1 = nullptr, *T2 = nullptr;
+    KS_CUDA(cudaMalloc(&dbox, box.size() * sizeof(double)));
+    KS_CUDA(cudaMalloc(&dlo, std::max<size_t>(1, lo.size()) * sizeof(int)));
     KS_CUDA(cudaMalloc(&tw, N * sizeof(double2)));
-    KS_CUDA(cudaMemcpy(sph_off, g_.sph_off.data(), g_.sph_off.size() * sizeof(int), cudaMemcpyHostToDevice));
-    KS_CUDA(cudaMemcpy(sph_idx, g_.sph_idx.data(), g_.sph_idx.size() * sizeof(int), cudaMemcpyHostToDevice));
-    KS_CUDA(cudaMemcpy(beta, g_.sph_beta.data(), g_.sph_beta.size() * sizeof(double), cudaMemcpyHostToDevice));
-    KS_CUDA(cudaMemcpy(tw, g_.tw.data(), N * sizeof(double2), cudaMemcpyHostToDevice));
-    const double scale = std::sqrt(g_.omega) / double(N3);
-    for (int p0 = 0; p0 < nprojtot_; p0 += batch) {
-      const int nb = std::min(batch, nprojtot_ - p0);
-      KS_CUDA(cudaMemset(grid, 0, (size_t)nb * N3 * sizeof(double2)));
-      k_scatter_projectors<<<dim3(8, nb), 256>>>(sph_off, sph_idx, beta, g_.nproj, p0, nb, N3, grid);
+    KS_CUDA(cudaMalloc(&T1, (size_t)chunk * B * B * M * sizeof(double2)));
+    KS_CUDA(cudaMalloc(&T2, (size_t)chunk * B * M * M * sizeof(double2)));
+    KS_CUDA(cudaMemcpy(dbox, box.data(), box.size() * sizeof(double), cudaMemcpyHostToDevice));
+    KS_CUDA(cudaMemcpy(dlo, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice));
+    KS_CUDA(cudaMemcpy(tw, g.tw.data(), N * sizeof(double2), cudaMemcpyHostToDevice));
+    const double scale = std::sqrt(g.omega) / ((double)N * N * N);
+    for (int r0 = 0; r0 < nprojtot_; r0 += chunk) {                   // r0: a multiple of np
+      const int nr = std::min(chunk, nprojtot_ - r0);
+      const int* clo = dlo + 3 * (r0 / np);
+      k_box_dft_z<<<nblk((size_t)nr * B * B * M, 256), 256>>>(dbox + (size_t)r0 * B * B * B, clo, np, nr, B, xr, N,
+                                                               tw, T1);
       KS_CHECK_LAUNCH();
-      for (int ax = 2; ax >= 0; --ax) fft_axis<double>(grid, nb, N, ax, -1, tw, 0);
-      k_gather_projectors<<<dim3(nblk(g_.nG, 256, 1024), nb), 256>>>(grid, t_.gidx, g_.nG, N3, scale,
-                                                                    B_ + (size_t)p0 * g_.nG);
+      k_box_dft_y<<<nblk((size_t)nr * B * M * M, 256), 256>>>(T1, clo, np, nr, B, xr, N, tw, T2);
+      KS_CHECK_LAUNCH();
+      k_box_dft_x<<<nblk((size_t)nr * g.nG, 256), 256>>>(T2, clo, t_.gidx, np, nr, B, xr, N, g.nG, scale, tw,
+                                                         B_ + (size_t)r0 * g.nG);
       KS_CHECK_LAUNCH();
     }
     KS_CUDA(cudaStreamSynchronize(nullptr));
-    cudaFree(grid);
-    cudaFree(sph_off);
-    cudaFree(sph_idx);
-    cudaFree(beta);
+    cudaFree(dbox);
+    cudaFree(dlo);
     cudaFree(tw);
+    cudaFree(T1);
+    cudaFree(T2);
   }
 
   template <typename U> U* alloc(size_t n) { return static_cast<U*>(arena_.alloc(n * sizeof(U))); }

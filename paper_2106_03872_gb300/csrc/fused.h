@@ -18,6 +18,9 @@ class FusedOps {
   virtual void apply_h(const float2* psi, float2* hpsi, int n, const float* v, cudaStream_t s) = 0;
   // nout = sum_k occ[k] |psi_k(r)|^2 (grid order).
   virtual void density(const float2* psi, int n, const double* occ, float* nout, cudaStream_t s) = 0;
+  // out[b][z][x][y] = Omega^{1/2} psi_b(r) on the grid (plane-major: z slowest), the unscaled
+  // inverse transform of n packed states, by the pruned z-columns and the in-SMEM y, x passes.
+  virtual void real_space(const float2* psi, int n, float2* out, cudaStream_t s) = 0;
   // The atoms moved: rebuild the per-plane projector lists and the projector block from the
   // geometry's new sphere lists (t: the engine's re-uploaded tables).  Synchronous.
   virtual void set_atoms(const DevTables<float>& t) = 0;

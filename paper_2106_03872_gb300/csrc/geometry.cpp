@@ -69,40 +69,12 @@ void count_sphere(double L, int N, double ecut, int* nG) {
   *nG = (int)count;
 }
 
-void build_atoms(const double* pos, HostGeometry& g, bool with_vloc) {
+void build_atoms(const double* pos, HostGeometry& g) {
   const int N = g.N;
   const double L = g.L;
-  // ---- V_loc(r) = sum_a A exp(-|r - R_a - L n|^2 / (2 w^2)) over the 27 image shifts -------
-  // Terms with |r - R_a - L n| > 10 w are below 2e-22 |A| and are skipped.
+  // V_loc (the 27-image Gaussians of Sec. "Pseudopotentials") is formed on the device from
+  // separable per-axis factors; the engine keeps a host copy in g.vloc.
   g.pos.assign(pos ? pos : nullptr, pos ? pos + 3 * (size_t)g.natoms : nullptr);
-  const double w2 = 2.0 * g.vloc_width * g.vloc_width;
-  const double rcut = 10.0 * g.vloc_width;
-  if (with_vloc) g.vloc.assign((size_t)N * N * N, 0.0);
-  for (int a = 0; a < g.natoms && with_vloc; ++a) {
-    const double R[3] = {pos[3 * a], pos[3 * a + 1], pos[3 * a + 2]};
-    for (int sx = -1; sx <= 1; ++sx)
-      for (int sy = -1; sy <= 1; ++sy)
-        for (int sz = -1; sz <= 1; ++sz) {
-          const double C[3] = {R[0] + L * sx, R[1] + L * sy, R[2] + L * sz};
-          int lo[3], hi[3];
-          for (int k = 0; k < 3; ++k) {
-            lo[k] = std::max(0, (int)std::floor((C[k] - rcut) / g.h));
-            hi[k] = std::min(N - 1, (int)std::ceil((C[k] + rcut) / g.h));
-          }
-          for (int jx = lo[0]; jx <= hi[0]; ++jx)
-            for (int jy = lo[1]; jy <= hi[1]; ++jy)
-              for (int jz = lo[2]; jz <= hi[2]; ++jz) {
-                const double dx = jx * g.h - C[0], dy = jy * g.h - C[1], dz = jz * g.h - C[2];
-                const double r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 > rcut * rcut) continue;
-                g.vloc[((size_t)jx * N + jy) * N + jz] += g.vloc_depth * std::exp(-r2 / w2);
-              }
-        }
-  }
-  if (with_vloc) {
-    g.vmin = *std::min_element(g.vloc.begin(), g.vloc.end());
-    g.vmax = *std::max_element(g.vloc.begin(), g.vloc.end());
-  }
 
   // ---- projector spheres |d| < R_c around each atom (minimum image), grid order ----------
   g.sph_off.assign(1, 0);
@@ -113,39 +85,41 @@ void build_atoms(const double* pos, HostGeometry& g, bool with_vloc) {
   const double rc2 = g.proj_rc * g.proj_rc;
   for (int a = 0; a < g.natoms; ++a) {
     const double R[3] = {pos[3 * a], pos[3 * a + 1], pos[3 * a + 2]};
-    std::vector<int> pts;
     int lo[3], hi[3];
+    // per axis: wrapped grid index and minimum-image displacement of each box coordinate
+    std::vector<int> jw[3];
+    std::vector<double> dw[3];
     for (int k = 0; k < 3; ++k) {
       lo[k] = (int)std::floor((R[k] - g.proj_rc) / g.h) - 1;
       hi[k] = (int)std::ceil((R[k] + g.proj_rc) / g.h) + 1;
+      for (int i = lo[k]; i <= hi[k]; ++i) {
+        const int j = ((i % N) + N) % N;
+        double t = j * g.h - R[k];
+        t -= L * std::nearbyint(t / L);
+        jw[k].push_back(j);
+        dw[k].push_back(t);
+      }
     }
-    for (int ix = lo[0]; ix <= hi[0]; ++ix)
-      for (int iy = lo[1]; iy <= hi[1]; ++iy)
-        for (int iz = lo[2]; iz <= hi[2]; ++iz) {
-          const int jx = ((ix % N) + N) % N, jy = ((iy % N) + N) % N, jz = ((iz % N) + N) % N;
-          pts.push_back((jx * N + jy) * N + jz);
+    // box points inside the sphere, then in grid order (a box wider than the grid would
+    // repeat an index: the repeats are dropped)
+    std::vector<std::pair<int, int>> hit;                            // (grid index, slot in dd)
+    std::vector<double> cand;                                         // dx, dy, dz, r2 per hit
+    for (size_t ix = 0; ix < jw[0].size(); ++ix)
+      for (size_t iy = 0; iy < jw[1].size(); ++iy)
+        for (size_t iz = 0; iz < jw[2].size(); ++iz) {
+          const double dx = dw[0][ix], dy = dw[1][iy], dz = dw[2][iz];
+          const double r2 = dx * dx + dy * dy + dz * dz;
+          if (!(r2 < rc2)) continue;
+          hit.push_back({(jw[0][ix] * N + jw[1][iy]) * N + jw[2][iz], (int)(cand.size() / 4)});
+          cand.insert(cand.end(), {dx, dy, dz, r2});
         }
-    std::sort(pts.begin(), pts.end());
-    pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
+    std::sort(hit.begin(), hit.end());
     std::vector<int> inside;
     std::vector<double> dd;
-    for (int p : pts) {
-      const int jx = p / (N * N), jy = (p / N) % N, jz = p % N;
-      const int j3[3] = {jx, jy, jz};
-      double dv[3], r2 = 0;
-      for (int k = 0; k < 3; ++k) {
-        double t = j3[k] * g.h - R[k];
-        t -= L * std::nearbyint(t / L);
-        dv[k] = t;
-        r2 += t * t;
-      }
-      if (r2 < rc2) {
-        inside.push_back(p);
-        dd.push_back(dv[0]);
-        dd.push_back(dv[1]);
-        dd.push_back(dv[2]);
-        dd.push_back(r2);
-      }
+    for (size_t i = 0; i < hit.size(); ++i) {
+      if (i > 0 && hit[i].first == hit[i - 1].first) continue;
+      inside.push_back(hit[i].first);
+      dd.insert(dd.end(), cand.begin() + 4 * hit[i].second, cand.begin() + 4 * hit[i].second + 4);
     }
     const size_t np = inside.size();
     std::vector<double> beta(np * g.nproj);
@@ -168,17 +142,22 @@ void build_atoms(const double* pos, HostGeometry& g, bool with_vloc) {
     }
     g.sph_off.push_back((int)g.sph_idx.size());
   }
-  // inverse lists (grid point -> its sphere points, atoms in index order)
-  std::map<int, std::vector<int>> cover;
-  for (size_t i = 0; i < g.sph_idx.size(); ++i) cover[g.sph_idx[i]].push_back((int)i);
+  // inverse lists (grid point -> its sphere points, atoms in index order): sort the
+  // (grid index, sphere point) pairs and group them
+  std::vector<std::pair<int, int>> cover(g.sph_idx.size());
+  for (size_t i = 0; i < g.sph_idx.size(); ++i) cover[i] = {g.sph_idx[i], (int)i};
+  std::sort(cover.begin(), cover.end());
   g.cov_idx.clear();
   g.cov_off.assign(1, 0);
   g.cov_ent.clear();
-  for (auto& kv : cover) {
-    g.cov_idx.push_back(kv.first);
-    for (int e : kv.second) g.cov_ent.push_back(e);
-    g.cov_off.push_back((int)g.cov_ent.size());
+  for (size_t i = 0; i < cover.size(); ++i) {
+    if (i == 0 || cover[i].first != cover[i - 1].first) {
+      if (i > 0) g.cov_off.push_back((int)g.cov_ent.size());
+      g.cov_idx.push_back(cover[i].first);
+    }
+    g.cov_ent.push_back(cover[i].second);
   }
+  if (!cover.empty()) g.cov_off.push_back((int)g.cov_ent.size());
 
 }
 
@@ -250,7 +229,7 @@ void build_geometry(const ks_cell_desc& d, HostGeometry& g) {
   g.D = d.proj_D;
   g.proj_sigma = d.proj_sigma;
   g.proj_rc = d.proj_rc;
-  build_atoms(d.pos, g, true);
+  build_atoms(d.pos, g);
 
   g.occ.assign(d.nstates, 1.0);
   if (d.occ)

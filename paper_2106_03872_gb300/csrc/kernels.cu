@@ -145,35 +145,46 @@ __global__ void k_multiply_phase(cplx<T>* __restrict__ grid, int N, T h, T L, T 
 template <typename T>
 __global__ void k_scatter_grad(const cplx<T>* __restrict__ psi, cplx<T>* __restrict__ grid, const int* __restrict__ gidx,
                                int nG, int N, T g0, int alpha) {
+  const int b = blockIdx.y;
+  const size_t N3 = (size_t)N * N * N;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nG; g += gridDim.x * blockDim.x) {
     const int idx = gidx[g];
     const int j = alpha == 0 ? idx / (N * N) : (alpha == 1 ? (idx / N) % N : idx % N);
     const T G = g0 * (T)(j < N / 2 ? j : j - N);
-    const cplx<T> c = psi[g];
-    grid[idx] = mk<cplx<T>>(-G * c.y, G * c.x);
+    const cplx<T> c = psi[(size_t)b * nG + g];
+    grid[b * N3 + idx] = mk<cplx<T>>(-G * c.y, G * c.x);
   }
 }
 
-// gacc[j] += w 2 Re(conj(dpsi[j]) psi[j])
+// gacc[j] += sum_b occ[b] 2 Re(conj(dpsi[b][j]) psi[b][j]), states in order, FP64 sum
 template <typename T>
 __global__ void k_grad_accumulate(const cplx<T>* __restrict__ dpsi, const cplx<T>* __restrict__ psi, T* __restrict__ gacc,
-                                  size_t N3, T w) {
+                                  size_t N3, int nb, const double* __restrict__ occ) {
   for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
-    const cplx<T> d = dpsi[j], p = psi[j];
-    gacc[j] += w * T(2) * (d.x * p.x + d.y * p.y);
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      const cplx<T> d = dpsi[b * N3 + j], p = psi[b * N3 + j];
+      acc += occ[b] * 2.0 * ((double)d.x * (double)p.x + (double)d.y * (double)p.y);
+    }
+    gacc[j] += (T)acc;
   }
 }
 
-// fnl[3 I + alpha] -= w sum_l Re(conj(q_Il) p_Il), one thread per atom (states in order)
+// fnl[3 I + alpha] -= w sum_b occ[b] sum_l Re(conj(q_bIl) p_bIl), one thread per atom (states in order)
 template <typename T>
-__global__ void k_nl_force(const cplx<T>* __restrict__ p, const cplx<T>* __restrict__ q, int natoms, int nproj,
-                           double w, double* __restrict__ fnl, int alpha) {
+__global__ void k_nl_force(const cplx<T>* __restrict__ p, const cplx<T>* __restrict__ q, int natoms, int nproj, int nb,
+                           double w, const double* __restrict__ occ, double* __restrict__ fnl, int alpha) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= natoms) return;
   double s = 0.0;
-  for (int l = 0; l < nproj; ++l) {
-    const cplx<T> a = p[I * nproj + l], b = q[I * nproj + l];
-    s += (double)b.x * (double)a.x + (double)b.y * (double)a.y;
+  for (int b = 0; b < nb; ++b) {
+    double sb = 0.0;
+    for (int l = 0; l < nproj; ++l) {
+      const size_t e = ((size_t)b * natoms + I) * nproj + l;
+      const cplx<T> a = p[e], c = q[e];
+      sb += (double)c.x * (double)a.x + (double)c.y * (double)a.y;
+    }
+    s += occ[b] * sb;
   }
   fnl[3 * I + alpha] -= w * s;
 }
@@ -182,7 +193,7 @@ __global__ void k_nl_force(const cplx<T>* __restrict__ p, const cplx<T>* __restr
 // atom the three per-axis image sums [natoms][3][N] of the separable Gaussian
 template <typename T>
 __global__ void k_local_force(const T* __restrict__ g, const double* __restrict__ xyz, int N, double coef,
-                              double* __restrict__ floc) {
+                              double* __restrict__ floc, int zmajor) {
   const int I = blockIdx.x;
   const size_t N3 = (size_t)N * N * N;
   const double* X = xyz + (size_t)I * 3 * N;
@@ -190,7 +201,8 @@ __global__ void k_local_force(const T* __restrict__ g, const double* __restrict_
   const double* Z = Y + N;
   double acc[3] = {0.0, 0.0, 0.0};
   for (size_t j = threadIdx.x; j < N3; j += blockDim.x) {
-    const int jz = (int)(j % N), jy = (int)((j / N) % N), jx = (int)(j / ((size_t)N * N));
+    const int a0 = (int)(j % N), a1 = (int)((j / N) % N), a2 = (int)(j / ((size_t)N * N));
+    const int jz = zmajor ? a2 : a0, jy = zmajor ? a0 : a1, jx = zmajor ? a1 : a2;
     const double v = X[jx] * Y[jy] * Z[jz];
     acc[0] += v * (double)g[j];
     acc[1] += v * (double)g[N3 + j];
@@ -248,13 +260,18 @@ __global__ void k_dipole_finish(const double* __restrict__ partials, int nblocks
 template <typename T, int NP>
 __global__ void k_nl_project(const cplx<T>* __restrict__ grid, size_t N3, const int* __restrict__ sph_off,
                              const int* __restrict__ sph_idx, const T* __restrict__ beta, int natoms,
-                             cplx<T>* __restrict__ proj, T scale) {
+                             cplx<T>* __restrict__ proj, T scale, int zmajor_n) {
   const int I = blockIdx.x, b = blockIdx.y;
   double acc[2 * NP];
 #pragma unroll
   for (int i = 0; i < 2 * NP; ++i) acc[i] = 0.0;
   for (int p = sph_off[I] + threadIdx.x; p < sph_off[I + 1]; p += blockDim.x) {
-    const cplx<T> v = grid[b * N3 + sph_idx[p]];
+    int idx = sph_idx[p];
+    if (zmajor_n) {                                                   // (x, y, z) -> [z][x][y]
+      const int n = zmajor_n, jz = idx % n, jxy = idx / n;
+      idx = jz * n * n + jxy;
+    }
+    const cplx<T> v = grid[b * N3 + idx];
 #pragma unroll
     for (int l = 0; l < NP; ++l) {
       const double w = (double)beta[(size_t)p * NP + l];
@@ -616,28 +633,50 @@ void multiply_phase(cplx<T>* grid, int N, double L, const double kappa[3], cudaS
 }
 
 template <typename T>
-void scatter_grad(const cplx<T>* psi, cplx<T>* grid, const DevTables<T>& t, int alpha, cudaStream_t s) {
-  k_scatter_grad<T><<<blocks_for((size_t)t.nG, 256, 1024), 256, 0, s>>>(psi, grid, t.gidx, t.nG, t.N,
-                                                                         (T)(2.0 * M_PI / t.L), alpha);
+void scatter_grad(const cplx<T>* psi, cplx<T>* grid, const DevTables<T>& t, int alpha, int nb, cudaStream_t s) {
+  k_scatter_grad<T><<<dim3(blocks_for((size_t)t.nG, 256, 1024), nb), 256, 0, s>>>(psi, grid, t.gidx, t.nG, t.N,
+                                                                                   (T)(2.0 * M_PI / t.L), alpha);
   KS_CHECK_LAUNCH();
 }
 
 template <typename T>
-void grad_accumulate(const cplx<T>* dpsi, const cplx<T>* psi, T* gacc, int N3, T w, cudaStream_t s) {
-  k_grad_accumulate<T><<<blocks_for((size_t)N3, 256, 2048), 256, 0, s>>>(dpsi, psi, gacc, (size_t)N3, w);
+void grad_accumulate(const cplx<T>* dpsi, const cplx<T>* psi, T* gacc, int N3, int nb, const double* occ,
+                     cudaStream_t s) {
+  k_grad_accumulate<T><<<blocks_for((size_t)N3, 256, 2048), 256, 0, s>>>(dpsi, psi, gacc, (size_t)N3, nb, occ);
   KS_CHECK_LAUNCH();
 }
 
 template <typename T>
-void nl_force(const cplx<T>* p, const cplx<T>* q, int natoms, int nproj, double w, double* fnl, int alpha,
-              cudaStream_t s) {
-  k_nl_force<T><<<(natoms + 127) / 128, 128, 0, s>>>(p, q, natoms, nproj, w, fnl, alpha);
+void nl_force(const cplx<T>* p, const cplx<T>* q, int natoms, int nproj, int nb, double w, const double* occ,
+              double* fnl, int alpha, cudaStream_t s) {
+  k_nl_force<T><<<(natoms + 127) / 128, 128, 0, s>>>(p, q, natoms, nproj, nb, w, occ, fnl, alpha);
   KS_CHECK_LAUNCH();
 }
 
 template <typename T>
-void local_force(const T* g, const double* xyz, int N, int natoms, double coef, double* floc, cudaStream_t s) {
-  k_local_force<T><<<natoms, RED_THREADS, 0, s>>>(g, xyz, N, coef, floc);
+void local_force(const T* g, const double* xyz, int N, int natoms, double coef, double* floc, cudaStream_t s,
+                 bool zmajor) {
+  k_local_force<T><<<natoms, RED_THREADS, 0, s>>>(g, xyz, N, coef, floc, zmajor ? 1 : 0);
+  KS_CHECK_LAUNCH();
+}
+
+template <typename T>
+__global__ void k_grad_packed(const cplx<T>* __restrict__ psi, cplx<T>* __restrict__ out, const int* __restrict__ gidx,
+                              int nG, int N, T g0, int alpha) {
+  const int b = blockIdx.y;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nG; g += gridDim.x * blockDim.x) {
+    const int idx = gidx[g];
+    const int j = alpha == 0 ? idx / (N * N) : (alpha == 1 ? (idx / N) % N : idx % N);
+    const T G = g0 * (T)(j < N / 2 ? j : j - N);
+    const cplx<T> c = psi[(size_t)b * nG + g];
+    out[(size_t)b * nG + g] = mk<cplx<T>>(-G * c.y, G * c.x);
+  }
+}
+
+template <typename T>
+void grad_packed(const cplx<T>* psi, cplx<T>* out, const DevTables<T>& t, int alpha, int nb, cudaStream_t s) {
+  k_grad_packed<T><<<dim3(blocks_for((size_t)t.nG, 256, 1024), nb), 256, 0, s>>>(psi, out, t.gidx, t.nG, t.N,
+                                                                                  (T)(2.0 * M_PI / t.L), alpha);
   KS_CHECK_LAUNCH();
 }
 
@@ -657,14 +696,16 @@ void dipole(const T* n, int N, double L, double* partials, int nblocks, double* 
 }
 
 template <typename T>
-void nl_project(const cplx<T>* grid, const DevTables<T>& t, cplx<T>* proj, int nb, T scale, cudaStream_t s) {
+void nl_project(const cplx<T>* grid, const DevTables<T>& t, cplx<T>* proj, int nb, T scale, cudaStream_t s,
+                bool zmajor) {
   if (t.natoms == 0) return;
   dim3 g(t.natoms, nb);
   const size_t N3 = (size_t)t.N * t.N * t.N;
+  const int zn = zmajor ? t.N : 0;
   if (t.nproj == 4)
-    k_nl_project<T, 4><<<g, RED_THREADS, 0, s>>>(grid, N3, t.sph_off, t.sph_idx, t.sph_beta, t.natoms, proj, scale);
+    k_nl_project<T, 4><<<g, RED_THREADS, 0, s>>>(grid, N3, t.sph_off, t.sph_idx, t.sph_beta, t.natoms, proj, scale, zn);
   else
-    k_nl_project<T, 1><<<g, RED_THREADS, 0, s>>>(grid, N3, t.sph_off, t.sph_idx, t.sph_beta, t.natoms, proj, scale);
+    k_nl_project<T, 1><<<g, RED_THREADS, 0, s>>>(grid, N3, t.sph_off, t.sph_idx, t.sph_beta, t.natoms, proj, scale, zn);
   KS_CHECK_LAUNCH();
 }
 
@@ -797,7 +838,7 @@ void real_to_double(const T* in, double* out, size_t n, cudaStream_t s) {
   template void gather_kinetic<T>(const cplx<T>*, const cplx<T>*, cplx<T>*, const DevTables<T>&, int, T,        \
                                   cudaStream_t);                                                                \
   template void multiply_potential<T>(cplx<T>*, const T*, int, int, cudaStream_t);                              \
-  template void nl_project<T>(const cplx<T>*, const DevTables<T>&, cplx<T>*, int, T, cudaStream_t);             \
+  template void nl_project<T>(const cplx<T>*, const DevTables<T>&, cplx<T>*, int, T, cudaStream_t, bool);       \
   template void nl_add<T>(cplx<T>*, const DevTables<T>&, const cplx<T>*, int, T, cudaStream_t);                 \
   template void density_accumulate<T>(const cplx<T>*, const double*, T*, int, int, T, bool, cudaStream_t);      \
   template void real_to_complex<T>(const T*, cplx<T>*, int, cudaStream_t);                                      \
@@ -812,10 +853,12 @@ void real_to_double(const T* in, double* out, size_t n, cudaStream_t s) {
                                 cudaStream_t);                                                                  \
   template void multiply_phase<T>(cplx<T>*, int, double, const double*, cudaStream_t);                          \
   template void dipole<T>(const T*, int, double, double*, int, double*, cudaStream_t);                          \
-  template void scatter_grad<T>(const cplx<T>*, cplx<T>*, const DevTables<T>&, int, cudaStream_t);              \
-  template void grad_accumulate<T>(const cplx<T>*, const cplx<T>*, T*, int, T, cudaStream_t);                   \
-  template void nl_force<T>(const cplx<T>*, const cplx<T>*, int, int, double, double*, int, cudaStream_t);       \
-  template void local_force<T>(const T*, const double*, int, int, double, double*, cudaStream_t);               \
+  template void scatter_grad<T>(const cplx<T>*, cplx<T>*, const DevTables<T>&, int, int, cudaStream_t);         \
+  template void grad_accumulate<T>(const cplx<T>*, const cplx<T>*, T*, int, int, const double*, cudaStream_t);  \
+  template void nl_force<T>(const cplx<T>*, const cplx<T>*, int, int, int, double, const double*, double*, int,  \
+                            cudaStream_t);                                                                      \
+  template void local_force<T>(const T*, const double*, int, int, double, double*, cudaStream_t, bool);         \
+  template void grad_packed<T>(const cplx<T>*, cplx<T>*, const DevTables<T>&, int, int, cudaStream_t);          \
   template void vloc_from_axes<T>(const double*, int, int, double, T*, double*, cudaStream_t);                  \
   template void state_dots<T>(const cplx<T>*, const cplx<T>*, int, int, double2*, cudaStream_t);                \
   template void axpy2<T>(cplx<T>*, double2, cplx<T>*, double2, const cplx<T>*, const cplx<T>*, size_t, cudaStream_t);           \

@@ -37,17 +37,21 @@ template <typename T> void gather_kinetic(const cplx<T>* grid, const cplx<T>* ps
 template <typename T> void multiply_potential(cplx<T>* grid, const T* v, int N3, int nb, cudaStream_t s);
 // one grid [N][N][N]: grid[j] *= exp(i kappa . (r_j - L/2)), r_j = (L/N) (jx, jy, jz)
 template <typename T> void multiply_phase(cplx<T>* grid, int N, double L, const double kappa[3], cudaStream_t s);
-// Forces (Eq. 11): grid[gidx[g]] = i G_alpha c_g of one state (grid zeroed before)
-template <typename T> void scatter_grad(const cplx<T>* psi, cplx<T>* grid, const DevTables<T>& t, int alpha,
+// Forces (Eq. 11): grid[b][gidx[g]] = i G_alpha c_bg for nb states (grids zeroed before)
+template <typename T> void scatter_grad(const cplx<T>* psi, cplx<T>* grid, const DevTables<T>& t, int alpha, int nb,
                                         cudaStream_t s);
-// gacc[j] += w 2 Re(conj(dpsi[j]) psi[j])
-template <typename T> void grad_accumulate(const cplx<T>* dpsi, const cplx<T>* psi, T* gacc, int N3, T w,
-                                           cudaStream_t s);
-// fnl[3 I + alpha] -= w sum_l Re(conj(q_Il) p_Il) (one state's projections p, q [natoms][nproj])
-template <typename T> void nl_force(const cplx<T>* p, const cplx<T>* q, int natoms, int nproj, double w, double* fnl,
-                                    int alpha, cudaStream_t s);
-// floc[3 I + a] = coef sum_j X_I[jx] Y_I[jy] Z_I[jz] g_a[j], g [3][N^3], xyz [natoms][3][N]
+// gacc[j] += sum_{b < nb} occ[b] 2 Re(conj(dpsi[b][j]) psi[b][j])  (states in order, FP64 sum)
+template <typename T> void grad_accumulate(const cplx<T>* dpsi, const cplx<T>* psi, T* gacc, int N3, int nb,
+                                           const double* occ, cudaStream_t s);
+// fnl[3 I + alpha] -= w sum_{b < nb} occ[b] sum_l Re(conj(q_bIl) p_bIl) (projections [nb][natoms][nproj])
+template <typename T> void nl_force(const cplx<T>* p, const cplx<T>* q, int natoms, int nproj, int nb, double w,
+                                    const double* occ, double* fnl, int alpha, cudaStream_t s);
+// floc[3 I + a] = coef sum_j X_I[jx] Y_I[jy] Z_I[jz] g_a[j], g [3][N^3], xyz [natoms][3][N];
+// zmajor: g laid out [z][x][y]
 template <typename T> void local_force(const T* g, const double* xyz, int N, int natoms, double coef, double* floc,
+                                       cudaStream_t s, bool zmajor = false);
+// out[b][g] = i G_alpha c_bg (packed, nb states)
+template <typename T> void grad_packed(const cplx<T>* psi, cplx<T>* out, const DevTables<T>& t, int alpha, int nb,
                                        cudaStream_t s);
 // v[j] = depth sum_I X_I[jx] Y_I[jy] Z_I[jz] (xyz as for local_force), in FP64; v64 (may be
 // NULL) receives the FP64 values
@@ -57,7 +61,9 @@ template <typename T> void vloc_from_axes(const double* xyz, int natoms, int N, 
 template <typename T> void dipole(const T* n, int N, double L, double* partials, int nblocks, double* out,
                                   cudaStream_t s);
 // proj[b][I][l] = scale * sum_{j in sphere I} beta_Il(j) grid[b][j]
-template <typename T> void nl_project(const cplx<T>* grid, const DevTables<T>& t, cplx<T>* proj, int nb, T scale, cudaStream_t s);
+// zmajor: the grids are laid out [b][z][x][y] (the fused path's real-space planes)
+template <typename T> void nl_project(const cplx<T>* grid, const DevTables<T>& t, cplx<T>* proj, int nb, T scale, cudaStream_t s,
+                                      bool zmajor = false);
 // grid[b][j] += scale * sum_{(I,l) covering j} beta_Il(j) proj[b][I][l]
 template <typename T> void nl_add(cplx<T>* grid, const DevTables<T>& t, const cplx<T>* proj, int nb, T scale, cudaStream_t s);
 // n[j] (+)= scale * sum_b occ[b] |grid[b][j]|^2 (states in order; first batch overwrites)
