@@ -90,8 +90,7 @@ ks_status ks_grid_device_bytes(ks_grid g, size_t* bytes) {
 ks_status ks_get_vloc(ks_grid g, double* v_host) {
   return guarded([&] {
     need(g && v_host, "grid/v is NULL");
-    const auto& geo = g->eng->geo();
-    std::memcpy(v_host, geo.vloc.data(), geo.vloc.size() * sizeof(double));
+    g->eng->get_vloc(v_host);
   });
 }
 

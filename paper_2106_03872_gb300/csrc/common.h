@@ -84,8 +84,7 @@ struct HostGeometry {
   std::vector<int> col_off;     // first packed index of the column
   std::vector<int> col_half;    // hz
   int xr = 0;                   // columns exist only for |m_x| <= xr (and |m_y| <= xr)
-  std::vector<double> vloc;     // [N^3] grid order (host copy of the device-formed V_loc)
-  double vmin = 0, vmax = 0;
+  double vmin = 0, vmax = 0;     // extremes of V_loc (formed on the device)
   std::vector<double> pos;      // [natoms][3] atom positions (bohr)
   double vloc_depth = 0, vloc_width = 0;
   // projectors: sphere point lists per atom (grid order within an atom)

@@ -161,6 +161,8 @@ template <typename T> class Engine final : public EngineBase {
     t_.cov_off = upload(g_.cov_off);
     t_.cov_ent = upload(g_.cov_ent);
     vloc_ = alloc<T>(N3);
+    vloc64_ = alloc<double>(N3);
+    vmm_ = alloc<double>(2);
     vtot_ = alloc<T>(N3);
     occ_ = const_cast<double*>(upload(g_.occ));
     // ---- states: 6 buffers (resident psi, H psi, and 4 work buffers for the real-time step)
@@ -1029,19 +1031,24 @@ template <typename T> class Engine final : public EngineBase {
   }
 
   // V = V_loc from the separable 27-image Gaussians of the current positions, in FP64 on the
-  // device, with the host copy g_.vloc and its extremes (the steepest-descent step uses them).
+  // device, kept in FP64 (vloc64_) beside the working precision, with its extremes on the host
+  // (the steepest-descent step uses them).
   void update_vloc(cudaStream_t s) {
     const int N = g_.N;
     const size_t N3 = (size_t)N * N * N;
     build_axis_tables();
-    double* v64 = reinterpret_cast<double*>(pwork_);                  // N^3 doubles fit the work grid
-    vloc_from_axes<T>(fxyz_, g_.natoms, N, g_.vloc_depth, vloc_, v64, s);
-    g_.vloc.resize(N3);
-    KS_CUDA(cudaMemcpyAsync(g_.vloc.data(), v64, N3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    vloc_from_axes<T>(fxyz_, g_.natoms, N, g_.vloc_depth, vloc_, vloc64_, s);
     KS_CUDA(cudaMemcpyAsync(vtot_, vloc_, N3 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    minmax(vloc64_, N3, hxc_partials_, HXC_BLOCKS, vmm_, s);
+    double mm[2];
+    KS_CUDA(cudaMemcpyAsync(mm, vmm_, sizeof(mm), cudaMemcpyDeviceToHost, s));
     KS_CUDA(cudaStreamSynchronize(s));
-    g_.vmin = *std::min_element(g_.vloc.begin(), g_.vloc.end());
-    g_.vmax = *std::max_element(g_.vloc.begin(), g_.vloc.end());
+    g_.vmin = mm[0];
+    g_.vmax = mm[1];
+  }
+
+  void get_vloc(double* v_host) override {
+    KS_CUDA(cudaMemcpy(v_host, vloc64_, (size_t)g_.N * g_.N * g_.N * sizeof(double), cudaMemcpyDeviceToHost));
   }
 
   // Work buffers of the force evaluation (allocated on first use): full grids for a chunk of
@@ -1165,6 +1172,8 @@ template <typename T> class Engine final : public EngineBase {
   DevTables<T> t_;
   std::unique_ptr<FusedOps> fused_;
   T* vloc_ = nullptr;
+  double* vloc64_ = nullptr;        // V_loc in FP64 (the ABI's copy), and its min and max
+  double* vmm_ = nullptr;
   T* vtot_ = nullptr;
   double* occ_ = nullptr;
   C* buf_[6] = {};

@@ -91,6 +91,7 @@ class EngineBase {
   virtual int nstates() const = 0;
   virtual ks_precision precision() const = 0;
   virtual size_t device_bytes() const = 0;
+  virtual void get_vloc(double* v_host) = 0;
   virtual void* states_device() = 0;
   virtual void set_states(const double* c_host, cudaStream_t s) = 0;
   virtual void get_states(double* c_host, cudaStream_t s) = 0;

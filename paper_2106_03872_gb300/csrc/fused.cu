@@ -424,7 +424,8 @@ __global__ void k_proj_to_states(const double2* __restrict__ pout, int nprojtot,
 // "Pseudopotentials": beta_Il lives on the sphere |r - R_I| < R_c, so its sphere coefficients
 // are a DFT of a function supported on a small box).  Box coordinates b = 0..B-1 stand for the
 // unwrapped grid index lo + b of the atom's minimum-image sphere; exp(-2 pi i m j / N) is
-// periodic in j, so the unwrapped index gives the phase directly.  FP64 throughout.
+// periodic in j, so the unwrapped index gives the phase directly.  FP32, like the block it
+// fills (the sums run over at most B ~ 2 R_c / h + 2 terms per axis).
 //   T1[p][bx][by][mz] = sum_bz beta[p][bx][by][bz] e(mz (lo_z + bz))
 //   T2[p][bx][my][mz] = sum_by T1[p][bx][by][mz] e(my (lo_y + by))
 //   B[p][G]          = scale sum_bx T2[p][bx][my][mz] e(mx (lo_x + bx)),  e(t) = exp(-2 pi i t / N)
@@ -434,8 +435,8 @@ __device__ __forceinline__ int mod_n(long v, int N) {
   return r < 0 ? r + N : r;
 }
 
-__global__ void k_box_dft_z(const double* __restrict__ box, const int* __restrict__ lo, int nproj, int nrows, int B,
-                            int xr, int N, const double2* __restrict__ tw, double2* __restrict__ T1) {
+__global__ void k_box_dft_z(const float* __restrict__ box, const int* __restrict__ lo, int nproj, int nrows, int B,
+                            int xr, int N, const float2* __restrict__ tw, float2* __restrict__ T1) {
   const int M = 2 * xr + 1;
   const size_t total = (size_t)nrows * B * B * M;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -445,21 +446,21 @@ __global__ void k_box_dft_z(const double* __restrict__ box, const int* __restric
     const int m = mi - xr;
     const int step = mod_n(m, N);
     int t = mod_n((long)m * lo[3 * (p / nproj) + 2], N);
-    const double* v = box + pb * B;
-    double ax = 0.0, ay = 0.0;
+    const float* v = box + pb * B;
+    float ax = 0.f, ay = 0.f;
     for (int bz = 0; bz < B; ++bz) {
-      const double2 w = tw[t];                                        // (cos, sin)(2 pi t / N)
+      const float2 w = tw[t];                                         // (cos, sin)(2 pi t / N)
       ax += v[bz] * w.x;
       ay -= v[bz] * w.y;
       t += step;
       if (t >= N) t -= N;
     }
-    T1[e] = make_double2(ax, ay);
+    T1[e] = make_float2(ax, ay);
   }
 }
 
-__global__ void k_box_dft_y(const double2* __restrict__ T1, const int* __restrict__ lo, int nproj, int nrows, int B,
-                            int xr, int N, const double2* __restrict__ tw, double2* __restrict__ T2) {
+__global__ void k_box_dft_y(const float2* __restrict__ T1, const int* __restrict__ lo, int nproj, int nrows, int B,
+                            int xr, int N, const float2* __restrict__ tw, float2* __restrict__ T2) {
   const int M = 2 * xr + 1;
   const size_t total = (size_t)nrows * B * M * M;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -470,22 +471,22 @@ __global__ void k_box_dft_y(const double2* __restrict__ T1, const int* __restric
     const int m = my - xr;
     const int step = mod_n(m, N);
     int t = mod_n((long)m * lo[3 * (p / nproj) + 1], N);
-    const double2* v = T1 + pbx * B * M + mz;                         // v[by * M]
-    double ax = 0.0, ay = 0.0;
+    const float2* v = T1 + pbx * B * M + mz;                         // v[by * M]
+    float ax = 0.f, ay = 0.f;
     for (int by = 0; by < B; ++by) {
-      const double2 w = tw[t], x = v[(size_t)by * M];
+      const float2 w = tw[t], x = v[(size_t)by * M];
       ax += x.x * w.x + x.y * w.y;                                    // x * conj(w)
       ay += x.y * w.x - x.x * w.y;
       t += step;
       if (t >= N) t -= N;
     }
-    T2[e] = make_double2(ax, ay);
+    T2[e] = make_float2(ax, ay);
   }
 }
 
-__global__ void k_box_dft_x(const double2* __restrict__ T2, const int* __restrict__ lo, const int* __restrict__ gidx,
-                            int nproj, int nrows, int B, int xr, int N, int nG, double scale,
-                            const double2* __restrict__ tw, float2* __restrict__ out) {
+__global__ void k_box_dft_x(const float2* __restrict__ T2, const int* __restrict__ lo, const int* __restrict__ gidx,
+                            int nproj, int nrows, int B, int xr, int N, int nG, float scale,
+                            const float2* __restrict__ tw, float2* __restrict__ out) {
   const int M = 2 * xr + 1;
   const size_t total = (size_t)nrows * nG;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -496,16 +497,16 @@ __global__ void k_box_dft_x(const double2* __restrict__ T2, const int* __restric
     const int mx = 2 * jx < N ? jx : jx - N, my = 2 * jy < N ? jy : jy - N, mz = 2 * jz < N ? jz : jz - N;
     const int step = mod_n(mx, N);
     int t = mod_n((long)mx * lo[3 * (p / nproj)], N);
-    const double2* v = T2 + (size_t)p * B * M * M + (size_t)(my + xr) * M + (mz + xr);   // v[bx * M * M]
-    double ax = 0.0, ay = 0.0;
+    const float2* v = T2 + (size_t)p * B * M * M + (size_t)(my + xr) * M + (mz + xr);   // v[bx * M * M]
+    float ax = 0.f, ay = 0.f;
     for (int bx = 0; bx < B; ++bx) {
-      const double2 w = tw[t], x = v[(size_t)bx * M * M];
+      const float2 w = tw[t], x = v[(size_t)bx * M * M];
       ax += x.x * w.x + x.y * w.y;
       ay += x.y * w.x - x.x * w.y;
       t += step;
       if (t >= N) t -= N;
     }
-    out[e] = make_float2((float)(ax * scale), (float)(ay * scale));
+    out[e] = make_float2(ax * scale, ay * scale);
   }
 }
 
@@ -712,7 +713,7 @@ class FusedImpl final : public FusedOps {
   }
 
   // B[atom*nproj + l][G] = c_G[beta_Il] = Omega^{1/2} N^-3 sum_j exp(-iG.r_j) beta_Il(r_j), by the
-  // separable DFT over each atom's box (k_box_dft_*), FP64.
+  // separable DFT over each atom's box (k_box_dft_*), FP32.
   void build_projector_block() {
     const HostGeometry& g = g_;
     const int N = N_, na = g.natoms, np = g.nproj;
@@ -738,29 +739,28 @@ class FusedImpl final : public FusedOps {
       if (g.sph_off[a + 1] > g.sph_off[a])
         for (int k = 0; k < 3; ++k) B = std::max(B, hi[3 * a + k] - lo[3 * a + k] + 1);
     }
-    std::vector<double> box((size_t)nprojtot_ * B * B * B, 0.0);
+    std::vector<float> box((size_t)nprojtot_ * B * B * B, 0.f);
     for (int a = 0; a < na; ++a)
       for (int p = g.sph_off[a]; p < g.sph_off[a + 1]; ++p) {
         const size_t bx = ju[3 * (size_t)p] - lo[3 * a], by = ju[3 * (size_t)p + 1] - lo[3 * a + 1],
                      bz = ju[3 * (size_t)p + 2] - lo[3 * a + 2];
         for (int l = 0; l < np; ++l)
-          box[(((size_t)(a * np + l) * B + bx) * B + by) * B + bz] = g.sph_beta[(size_t)p * np + l];
+          box[(((size_t)(a * np + l) * B + bx) * B + by) * B + bz] = (float)g.sph_beta[(size_t)p * np + l];
       }
     // rows in chunks of whole atoms (the intermediate sums of a chunk stay below ~64 MB)
-    const size_t per_row = (size_t)B * M * (B + M) * sizeof(double2);
+    const size_t per_row = (size_t)B * M * (B + M) * sizeof(float2);
     const int chunk = np * std::max(1, (int)std::min<size_t>(na, (size_t(64) << 20) / (per_row * np)));
-    double* dbox = nullptr;
+    float* dbox = nullptr;
     int* dlo = nullptr;
-    double2 *tw = nullptr, *T1 = nullptr, *T2 = nullptr;
-    KS_CUDA(cudaMalloc(&dbox, box.size() * sizeof(double)));
+    float2 *T1 = nullptr, *T2 = nullptr;
+    const float2* tw = t_.tw;                                         // (cos, sin)(2 pi t / N), FP32
+    KS_CUDA(cudaMalloc(&dbox, box.size() * sizeof(float)));
     KS_CUDA(cudaMalloc(&dlo, std::max<size_t>(1, lo.size()) * sizeof(int)));
-    KS_CUDA(cudaMalloc(&tw, N * sizeof(double2)));
-    KS_CUDA(cudaMalloc(&T1, (size_t)chunk * B * B * M * sizeof(double2)));
-    KS_CUDA(cudaMalloc(&T2, (size_t)chunk * B * M * M * sizeof(double2)));
-    KS_CUDA(cudaMemcpy(dbox, box.data(), box.size() * sizeof(double), cudaMemcpyHostToDevice));
+    KS_CUDA(cudaMalloc(&T1, (size_t)chunk * B * B * M * sizeof(float2)));
+    KS_CUDA(cudaMalloc(&T2, (size_t)chunk * B * M * M * sizeof(float2)));
+    KS_CUDA(cudaMemcpy(dbox, box.data(), box.size() * sizeof(float), cudaMemcpyHostToDevice));
     KS_CUDA(cudaMemcpy(dlo, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice));
-    KS_CUDA(cudaMemcpy(tw, g.tw.data(), N * sizeof(double2), cudaMemcpyHostToDevice));
-    const double scale = std::sqrt(g.omega) / ((double)N * N * N);
+    const float scale = (float)(std::sqrt(g.omega) / ((double)N * N * N));
     for (int r0 = 0; r0 < nprojtot_; r0 += chunk) {                   // r0: a multiple of np
       const int nr = std::min(chunk, nprojtot_ - r0);
       const int* clo = dlo + 3 * (r0 / np);
@@ -776,7 +776,6 @@ class FusedImpl final : public FusedOps {
     KS_CUDA(cudaStreamSynchronize(nullptr));
     cudaFree(dbox);
     cudaFree(dlo);
-    cudaFree(tw);
     cudaFree(T1);
     cudaFree(T2);
   }

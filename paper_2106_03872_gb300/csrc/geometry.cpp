@@ -5,7 +5,6 @@
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
-#include <map>
 
 #include "common.h"
 
@@ -73,7 +72,7 @@ void build_atoms(const double* pos, HostGeometry& g) {
   const int N = g.N;
   const double L = g.L;
   // V_loc (the 27-image Gaussians of Sec. "Pseudopotentials") is formed on the device from
-  // separable per-axis factors; the engine keeps a host copy in g.vloc.
+  // separable per-axis factors; only its extremes are kept on the host.
   g.pos.assign(pos ? pos : nullptr, pos ? pos + 3 * (size_t)g.natoms : nullptr);
 
   // ---- projector spheres |d| < R_c around each atom (minimum image), grid order ----------
@@ -113,7 +112,10 @@ void build_atoms(const double* pos, HostGeometry& g) {
           hit.push_back({(jw[0][ix] * N + jw[1][iy]) * N + jw[2][iz], (int)(cand.size() / 4)});
           cand.insert(cand.end(), {dx, dy, dz, r2});
         }
-    std::sort(hit.begin(), hit.end());
+    // a box inside [0, N) on every axis enumerates in grid order already
+    bool wraps = false;
+    for (int k = 0; k < 3; ++k) wraps = wraps || lo[k] < 0 || hi[k] >= N;
+    if (wraps) std::sort(hit.begin(), hit.end());
     std::vector<int> inside;
     std::vector<double> dd;
     for (size_t i = 0; i < hit.size(); ++i) {
@@ -142,22 +144,22 @@ void build_atoms(const double* pos, HostGeometry& g) {
     }
     g.sph_off.push_back((int)g.sph_idx.size());
   }
-  // inverse lists (grid point -> its sphere points, atoms in index order): sort the
-  // (grid index, sphere point) pairs and group them
-  std::vector<std::pair<int, int>> cover(g.sph_idx.size());
-  for (size_t i = 0; i < g.sph_idx.size(); ++i) cover[i] = {g.sph_idx[i], (int)i};
-  std::sort(cover.begin(), cover.end());
+  // inverse lists (grid point -> its sphere points, atoms in index order): count the sphere
+  // points of every grid point, then place the points in increasing order
+  const size_t N3 = (size_t)N * N * N;
+  std::vector<int> first(N3 + 1, 0);
+  for (int idx : g.sph_idx) ++first[idx + 1];
   g.cov_idx.clear();
   g.cov_off.assign(1, 0);
-  g.cov_ent.clear();
-  for (size_t i = 0; i < cover.size(); ++i) {
-    if (i == 0 || cover[i].first != cover[i - 1].first) {
-      if (i > 0) g.cov_off.push_back((int)g.cov_ent.size());
-      g.cov_idx.push_back(cover[i].first);
+  for (size_t j = 0; j < N3; ++j) {
+    if (first[j + 1] > 0) {
+      g.cov_idx.push_back((int)j);
+      g.cov_off.push_back(g.cov_off.back() + first[j + 1]);
     }
-    g.cov_ent.push_back(cover[i].second);
+    first[j + 1] += first[j];                                         // first[j]: start of point j's entries
   }
-  if (!cover.empty()) g.cov_off.push_back((int)g.cov_ent.size());
+  g.cov_ent.assign(g.sph_idx.size(), 0);
+  for (size_t i = 0; i < g.sph_idx.size(); ++i) g.cov_ent[first[g.sph_idx[i]]++] = (int)i;
 
 }
 

@@ -786,6 +786,47 @@ void teter_update(cplx<T>* psi, const cplx<T>* hpsi, const T* g2half, const doub
   KS_CHECK_LAUNCH();
 }
 
+__global__ void k_minmax_partials(const double* __restrict__ v, size_t n, double* __restrict__ partials) {
+  __shared__ double smin[RED_THREADS], smax[RED_THREADS];
+  double lo = INFINITY, hi = -INFINITY;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n; j += (size_t)gridDim.x * blockDim.x) {
+    lo = fmin(lo, v[j]);
+    hi = fmax(hi, v[j]);
+  }
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w /= 2) {
+    if ((int)threadIdx.x < w) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + w]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = smin[0];
+    partials[2 * blockIdx.x + 1] = smax[0];
+  }
+}
+
+__global__ void k_minmax_finish(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double lo = INFINITY, hi = -INFINITY;
+  for (int b = 0; b < nblocks; ++b) {
+    lo = fmin(lo, partials[2 * b]);
+    hi = fmax(hi, partials[2 * b + 1]);
+  }
+  out[0] = lo;
+  out[1] = hi;
+}
+
+void minmax(const double* v, size_t n, double* partials, int nblocks, double* out, cudaStream_t s) {
+  k_minmax_partials<<<nblocks, RED_THREADS, 0, s>>>(v, n, partials);
+  KS_CHECK_LAUNCH();
+  k_minmax_finish<<<1, 32, 0, s>>>(partials, nblocks, out);
+  KS_CHECK_LAUNCH();
+}
+
 void sum_partials(const double* partials, int nblocks, double scale, double* out, cudaStream_t s) {
   k_sum_partials<<<1, 32, 0, s>>>(partials, nblocks, scale, out);
   KS_CHECK_LAUNCH();

@@ -53,6 +53,8 @@ template <typename T> void local_force(const T* g, const double* xyz, int N, int
 // out[b][g] = i G_alpha c_bg (packed, nb states)
 template <typename T> void grad_packed(const cplx<T>* psi, cplx<T>* out, const DevTables<T>& t, int alpha, int nb,
                                        cudaStream_t s);
+// out[0] = min_j v[j], out[1] = max_j v[j] (device); partials holds 2 * nblocks doubles
+void minmax(const double* v, size_t n, double* partials, int nblocks, double* out, cudaStream_t s);
 // v[j] = depth sum_I X_I[jx] Y_I[jy] Z_I[jz] (xyz as for local_force), in FP64; v64 (may be
 // NULL) receives the FP64 values
 template <typename T> void vloc_from_axes(const double* xyz, int natoms, int N, double depth, T* v, double* v64,

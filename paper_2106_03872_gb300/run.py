@@ -2,6 +2,7 @@
 
     python -m paper_2106_03872_gb300.run --cell gs96 --iterations 1
     python -m paper_2106_03872_gb300.run --cell td128 --td-steps 2
+    python -m paper_2106_03872_gb300.run --cell gs96 --iterations 3 --timeline
 
 It builds the grid of a named synthetic cell (plane-wave sphere, local potential, KB
 projectors), loads seeded random coefficients, and runs block iterations (Sec. 3: H psi,
@@ -24,11 +25,19 @@ def main(argv=None):
     ap.add_argument("--iterations", type=int, default=1, help="block iterations (ground state)")
     ap.add_argument("--td-steps", type=int, default=0, help="ETRS time steps after the iterations")
     ap.add_argument("--dt", type=float, default=0.05)
+    ap.add_argument("--timeline", action="store_true",
+                    help="after one warm-up iteration, print the stage spans of the block iterations "
+                         "(main and side stream, ms on a common clock)")
     args = ap.parse_args(argv)
 
     cell = inputs.cell(args.cell)
     g = ks.Grid(cell, prec=args.prec)
     g.set_states(inputs.random_coeffs(cell["seed"], cell["nstates"], g.nG))
+    if args.timeline:
+        g.block_iteration(1)
+        torch.cuda.synchronize()
+        g.profile(1)
+        g.profile(3)
     t0 = time.perf_counter()
     eps = g.block_iteration(args.iterations) if args.iterations > 0 else None
     if args.td_steps > 0:
@@ -40,6 +49,11 @@ def main(argv=None):
     if eps is not None:
         line += " eps0=%.6f" % float(eps[0])
     print(line)
+    if args.timeline:
+        for name, a, b in sorted(g.profile_spans(), key=lambda x: x[1]):
+            print("%-14s %8.3f %8.3f" % (name, a, b))
+        g.profile(4)
+        g.profile(0)
     g.close()
 
 
