@@ -799,3 +799,29 @@ def test_ehrenfest_immobile_ions_match_td_step(ks):
             a.ehrenfest(**kw)
     a.close()
     b.close()
+
+
+def test_moved_atoms_and_forces_full_size_sampled(ks):
+    """The gs96 cell (96^3, 128 states, 64 atoms) with every atom displaced: H psi of sampled
+    states after ks_set_positions, and the forces of one occupied state (occupations pick the
+    state whose forces the oracle computes), against an oracle cell built at the new
+    positions."""
+    cell, _ = oracle_cell("gs96")
+    rng = np.random.default_rng(cell["seed"] + 7)
+    moved = np.asarray(cell["pos"]) + rng.normal(scale=0.3, size=np.shape(cell["pos"]))
+    ref = ko.Cell(dict(cell, pos=moved))
+    occ = np.zeros(cell["nstates"])
+    occ[5] = 1.0
+    g = ks.Grid(cell, prec="bf16x3", occ=occ)
+    c = inputs.random_coeffs(cell["seed"], cell["nstates"], ref.nG)
+    g.set_states(c)
+    g.set_positions(moved)
+    got = apply_dev(ks, g, c, "bf16x3")
+    for k in (5, 127):
+        e = ko.apply_h(ref, c[k:k + 1])[0]
+        assert rel(got[k], e) <= TOL_H["bf16x3"], (k, rel(got[k], e))
+    g.set_states(c)
+    F = g.forces()
+    F_ref = ko.forces(ref, c[5:6])
+    assert np.max(np.abs(F - F_ref)) <= 1e-4 * np.max(np.abs(F_ref))
+    g.close()
