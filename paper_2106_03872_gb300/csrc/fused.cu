@@ -61,15 +61,25 @@ template <int N> struct FCfg {
 // Column c of the sphere holds 2h+1 consecutive coefficients (h = col_half[c]) starting at
 // col_off[c], z-indices 0..h then N-h..N-1: coefficient k has z = k for k <= h, else
 // k + N - 2h - 1.  The z-kernels derive a coefficient's (column, z) from these two numbers.
+// k_zinv takes ZSB consecutive states per CTA for one block of CT columns and keeps two
+// column blocks in shared memory: while one state's block is transformed, the next state's
+// coefficients arrive by asynchronous copies (software pipelining hides the load latency that
+// one block per CTA left exposed).  Dynamic shared memory: twiddles [N], then the two blocks
+// [CT][N + 1].
+constexpr int ZSB = 4;
+template <int N> constexpr size_t zsmem() { return (size_t)(N + 2 * FCfg<N>::CT * (N + 1)) * sizeof(float2); }
+
 template <int N>
-__global__ void __launch_bounds__(FCfg<N>::ZT) k_zinv(const float2* __restrict__ psi, int nG, const int* __restrict__ col_off,
-                                                      const int* __restrict__ col_half, int ncols,
+__global__ void __launch_bounds__(FCfg<N>::ZT, 2) k_zinv(const float2* __restrict__ psi, int nG, const int* __restrict__ col_off,
+                                                      const int* __restrict__ col_half, int ncols, int nstates,
                                                       float2* __restrict__ colbuf, const float2* __restrict__ twg) {
   constexpr int CT = FCfg<N>::CT, ld = N + 1, ZT = FCfg<N>::ZT;
-  __shared__ float2 tw[N];
-  __shared__ float2 s[CT * ld];
+  extern __shared__ __align__(16) float2 zsm[];
+  float2* tw = zsm;
+  float2* sb[2] = {zsm + N, zsm + N + CT * ld};
   __shared__ int coff[CT], chalf[CT];
-  const int b = blockIdx.y;
+  const int b0 = blockIdx.y * ZSB;
+  const int nb = min(ZSB, nstates - b0);
   const int c0 = blockIdx.x * CT;
   const int nl = min(CT, ncols - c0);
   for (int t = threadIdx.x; t < N; t += ZT) tw[t] = twg[t];
@@ -78,38 +88,67 @@ __global__ void __launch_bounds__(FCfg<N>::ZT) k_zinv(const float2* __restrict__
     chalf[t] = col_half[c0 + t];
   }
   __syncthreads();
-  // a group of TPC threads per column fills the column's N slots: the coefficient where z is in
-  // the column's range, else zero (all loads of a thread are independent and issued together)
+  // slot z of column l holds coefficient k = z (z <= h) or z - (N - 2h - 1) (z >= N - h); the
+  // other slots are zero in both blocks (set here, and again after each block is stored)
   constexpr int TPC = ZT / CT, SLOTS = (N + TPC - 1) / TPC;
-  const float2* in = psi + (size_t)b * nG;
-  {
-    const int l = threadIdx.x / TPC, sub = threadIdx.x - (threadIdx.x / TPC) * TPC;
-    if (l < nl) {
-      const int h = chalf[l];
-      const float2* col = in + coff[l];
+  const int l = threadIdx.x / TPC, sub = threadIdx.x - (threadIdx.x / TPC) * TPC;
+  const int h = l < nl ? chalf[l] : -1, g0 = l < nl ? coff[l] : 0;
+  if (l < nl) {
 #pragma unroll
-      for (int q = 0; q < SLOTS; ++q) {
-        const int z = sub + q * TPC;
-        if (z < N) {
-          const int k = z <= h ? z : (z >= N - h ? z - (N - 2 * h - 1) : -1);
-          s[l * ld + z] = k >= 0 ? col[k] : make_float2(0.f, 0.f);
-        }
+    for (int q = 0; q < SLOTS; ++q) {
+      const int z = sub + q * TPC;
+      if (z < N && z > h && z < N - h) {
+        sb[0][l * ld + z] = make_float2(0.f, 0.f);
+        sb[1][l * ld + z] = make_float2(0.f, 0.f);
       }
     }
   }
-  __syncthreads();
-  cfft_lines<N, ZT, CT, true, +1>(s, nl, ld, 1, tw);
-  // transpose out: element e = z * CT + l (a compile-time split; columns l >= nl are absent
-  // in the last block)
-  float2* out = colbuf + (size_t)b * N * ncols + c0;
+  auto issue = [&](int i) {                                          // state b0 + i -> block i & 1
+    if (l >= nl) return;
+    const float2* col = psi + (size_t)(b0 + i) * nG + g0;
+    float2* dst = sb[i & 1] + l * ld;
 #pragma unroll
-  for (int q = 0; q < (N * CT + ZT - 1) / ZT; ++q) {
-    const int e = threadIdx.x + q * ZT;
-    const int z = e / CT, l = e % CT;
-    if (z < N && l < nl) out[(size_t)z * ncols + l] = s[l * ld + z];
+    for (int q = 0; q < SLOTS; ++q) {
+      const int z = sub + q * TPC;
+      if (z < N) {
+        const int k = z <= h ? z : (z >= N - h ? z - (N - 2 * h - 1) : -1);
+        if (k >= 0) cp_async8(dst + z, col + k);
+      }
+    }
+  };
+  issue(0);
+  cp_async_commit();
+  for (int i = 0; i < nb; ++i) {
+    if (i + 1 < nb) {
+      issue(i + 1);
+      cp_async_commit();
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();
+    float2* s = sb[i & 1];
+    cfft_lines<N, ZT, CT, true, +1>(s, nl, ld, 1, tw);
+    // transpose out: element e = z * CT + lc; slots outside the column's range go back to zero
+    float2* out = colbuf + (size_t)(b0 + i) * N * ncols + c0;
+#pragma unroll
+    for (int q = 0; q < (N * CT + ZT - 1) / ZT; ++q) {
+      const int e = threadIdx.x + q * ZT;
+      const int z = e / CT, lc = e % CT;
+      if (z < N && lc < nl) {
+        out[(size_t)z * ncols + lc] = s[lc * ld + z];
+        const int hc = chalf[lc];
+        if (z > hc && z < N - hc) s[lc * ld + z] = make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();                                                  // block i & 1 free for state i + 2
   }
 }
 
+// k_zfwd: one state per CTA (blockIdx.y); the column block arrives by asynchronous copies
+// while the state's psi and |G|^2/2 load into registers.  (A ZSB-state pipelined form like
+// k_zinv's spilled: the next block's copy addresses and the write-back indices stayed live
+// across the transform.)
 template <int N>
 __global__ void __launch_bounds__(FCfg<N>::ZT, 3) k_zfwd(const float2* __restrict__ colbuf, const float2* __restrict__ psi,
                                                       float2* __restrict__ hpsi, int nG, const int* __restrict__ col_off,
@@ -621,8 +660,13 @@ class FusedImpl final : public FusedOps {
   }
 
   template <int N> void launch_zinv(const float2* psi, int n, cudaStream_t s) {
-    dim3 grid((ncols_ + FCfg<N>::CT - 1) / FCfg<N>::CT, n);
-    k_zinv<N><<<grid, FCfg<N>::ZT, 0, s>>>(psi, g_.nG, t_.col_off, t_.col_half, ncols_, colbuf1_, t_.tw);
+    static bool attr = false;
+    if (!attr) {
+      KS_CUDA(cudaFuncSetAttribute(k_zinv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem<N>()));
+      attr = true;
+    }
+    dim3 grid((ncols_ + FCfg<N>::CT - 1) / FCfg<N>::CT, (n + ZSB - 1) / ZSB);
+    k_zinv<N><<<grid, FCfg<N>::ZT, zsmem<N>(), s>>>(psi, g_.nG, t_.col_off, t_.col_half, ncols_, n, colbuf1_, t_.tw);
     KS_CHECK_LAUNCH();
   }
   template <int N> void launch_zfwd(const float2* psi, float2* hpsi, int n, cudaStream_t s) {
