@@ -65,9 +65,9 @@ size_t estimate_bytes(const ks_cell_desc& d) {
   const bool fp64 = d.prec == KS_FP64;
   const size_t cb = fp64 ? 16 : 8;
   size_t b = 7 * ns * nG * cb + ns * nG * 16;         // six state buffers + complex128 staging
-  b += N3 * (fp64 ? 8 : 4) * 4 + N3 * cb;             // V_loc, V, density, Poisson work
+  b += N3 * (fp64 ? 8 : 4) * 4 + N3 * cb + N3 * 8;   // V_loc, V, density, Poisson work, FP64 V_loc
   const size_t nn = ns * ns;
-  b += nn * 16 * 8 + nn * 16 * 148 / 4;               // dense matrices and split-K partials
+  b += nn * 16 * 8 + nn * 16 * 152 / 4;               // dense matrices and split-K partials (152 SMs)
   if (fp64) {
     b += std::min<size_t>(ns, std::max<size_t>(1, (size_t(1) << 30) / (N3 * 16))) * N3 * 16;
   } else {

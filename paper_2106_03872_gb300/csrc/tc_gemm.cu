@@ -602,9 +602,20 @@ void set_attrs() {
 
 }  // namespace
 
+// SMs of the current device (the overlap kernel splits K into about one CTA per SM)
+static int sm_count() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    KS_CUDA(cudaGetDevice(&dev));
+    KS_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    return v;
+  }();
+  return n;
+}
+
 size_t tc_overlap_part_elems(int m, int n) {
   const int tm = (m + TC_M - 1) / TC_M, tn = (n + TC_N / 2 - 1) / (TC_N / 2);
-  return (size_t)m * n * (size_t)std::max(1, 148 / (tm * tn));
+  return (size_t)m * n * (size_t)std::max(1, sm_count() / (tm * tn));
 }
 
 size_t tc_rotation_workspace_bytes(int m, int nin) {
@@ -616,7 +627,7 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
                 size_t part_elems, double2* out, int* err, cudaStream_t s, float2* out32) {
   set_attrs();
   const int tm = (m + TC_M - 1) / TC_M, tn = (n + TC_N / 2 - 1) / (TC_N / 2);
-  int ks = std::max(1, 148 / (tm * tn));
+  int ks = std::max(1, sm_count() / (tm * tn));
   ks = std::min(ks, std::max(1, K / (4 * O_KC)));
   ks = (int)std::min<long>(ks, (long)(part_elems / ((size_t)m * n)));
   if (ks < 1) fail(KS_ERR_ARG, "tc_overlap: partial buffer too small");
