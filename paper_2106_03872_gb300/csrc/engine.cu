@@ -228,6 +228,7 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     KS_CUDA(cudaStreamCreateWithPriority(&aux_, cudaStreamNonBlocking, hi));
     KS_CUDA(cudaEventCreateWithFlags(&ev_gram_, cudaEventDisableTiming));
+    KS_CUDA(cudaEventCreateWithFlags(&ev_hraw_, cudaEventDisableTiming));
     KS_CUDA(cudaEventCreateWithFlags(&ev_chol_, cudaEventDisableTiming));
     KS_CUDA(cudaEventCreateWithFlags(&ev_ritz_, cudaEventDisableTiming));
     update_vloc(nullptr);
@@ -239,6 +240,7 @@ template <typename T> class Engine final : public EngineBase {
       cudaStreamDestroy(aux_);
     }
     if (ev_gram_) cudaEventDestroy(ev_gram_);
+    if (ev_hraw_) cudaEventDestroy(ev_hraw_);
     if (ev_chol_) cudaEventDestroy(ev_chol_);
     if (ev_ritz_) cudaEventDestroy(ev_ritz_);
   }
@@ -455,8 +457,8 @@ template <typename T> class Engine final : public EngineBase {
     // Per iteration (Sec. Ground-state solution): CholQR, H psi, Rayleigh-Ritz, SD update,
     // reorganised around the linearity of H:
     //  - S = psi^H psi and H_raw = psi^H (H psi) are formed on the raw block; the factor M of S,
-    //    H_raw, H_sub = conj(M) H_raw M^T, its eigenvectors Vt, C = Vt M and the step matrix
-    //    Mcat = [(I + alpha Lambda) C | -alpha C] run on the side stream, while
+    //    H_sub = conj(M) H_raw M^T, its eigenvectors Vt, C = Vt M and the step matrix
+    //    Mcat = [(I + alpha Lambda) C | -alpha C] run on the side stream (one SM), while
     //  - the main stream applies H to H psi (H^2 psi);
     //  - then psi <- Mcat [psi; H psi] and H psi <- Mcat [H psi; H^2 psi].
     // On the bf16x3 path with n <= 128 the side stream's Rayleigh-Ritz step is one CTA
@@ -480,14 +482,15 @@ template <typename T> class Engine final : public EngineBase {
         hermitize(mS_, n, s);
       }
       KS_CUDA(cudaEventRecord(ev_gram_, s));
-      // side stream: factor, H_raw = Psi^H (H Psi) (off the main stream, which goes on to
-      // H^2 psi; neither writes psi or H psi), subspace matrix, eigenpairs, step matrix
+      {
+        ProfScope p(prof, "gram", s);
+        overlap(psi_, hpsi_, n, mA_, s, frr ? hraw32_ : nullptr);
+      }
+      KS_CUDA(cudaEventRecord(ev_hraw_, s));
+      // side stream: factor, subspace matrix, eigenpairs, step matrix
       KS_CUDA(cudaStreamWaitEvent(aux_, ev_gram_, 0));
       factor(aux_, frr ? m32_ : nullptr);
-      {
-        ProfScope p(prof, "gram", aux_);
-        overlap(psi_, hpsi_, n, mA_, aux_, frr ? hraw32_ : nullptr);
-      }
+      KS_CUDA(cudaStreamWaitEvent(aux_, ev_hraw_, 0));
       if (frr) {
         {
           ProfScope p(prof, "rr_step", aux_);
@@ -1197,7 +1200,7 @@ template <typename T> class Engine final : public EngineBase {
   bool hpsi_valid_ = false;
   int hpsi_age_ = 0;
   cudaStream_t aux_ = nullptr;
-  cudaEvent_t ev_gram_ = nullptr, ev_chol_ = nullptr, ev_ritz_ = nullptr;
+  cudaEvent_t ev_gram_ = nullptr, ev_hraw_ = nullptr, ev_chol_ = nullptr, ev_ritz_ = nullptr;
   void* rotws_ = nullptr;
   size_t rotws_bytes_ = 0;
   int* status_ = nullptr;
