@@ -577,6 +577,7 @@ class FusedImpl final : public FusedOps {
     vplane_ = alloc<float>(N3);
     if (nprojtot_ > 0) {
       B_ = alloc<float2>((size_t)nprojtot_ * g.nG);
+      Bimg_ = arena_.alloc(tc_overlap_image_bytes(nprojtot_, g.nG));
       pout_ = alloc<double2>((size_t)nprojtot_ * ns_);
       pf_ = alloc<float2>((size_t)nprojtot_ * ns_);
       part_elems_ = std::max<size_t>(tc_overlap_part_elems(nprojtot_, ns_), 4096);
@@ -593,7 +594,7 @@ class FusedImpl final : public FusedOps {
     KS_CHECK_LAUNCH();
     if (nprojtot_ > 0) {
       ProfScope ps(prof_, "proj_gemm", s);
-      tc_overlap(B_, g_.nG, psi, g_.nG, nprojtot_, n, g_.nG, part_, part_elems_, pout_, err_, s);
+      tc_overlap(B_, g_.nG, psi, g_.nG, nprojtot_, n, g_.nG, part_, part_elems_, pout_, err_, s, nullptr, Bimg_);
       const float scale = (float)(g_.D * std::sqrt(g_.omega));
       k_proj_to_states<<<nblk((size_t)nprojtot_ * n, 256), 256, 0, s>>>(pout_, nprojtot_, n, scale, pf_);
       KS_CHECK_LAUNCH();
@@ -817,6 +818,7 @@ class FusedImpl final : public FusedOps {
                                                          B_ + (size_t)r0 * g.nG);
       KS_CHECK_LAUNCH();
     }
+    tc_overlap_prepare_a(B_, g.nG, nprojtot_, g.nG, Bimg_, nullptr);   // the operand split once
     KS_CUDA(cudaStreamSynchronize(nullptr));
     cudaFree(dbox);
     cudaFree(dlo);
@@ -843,6 +845,7 @@ class FusedImpl final : public FusedOps {
   float2* colbuf2_ = nullptr;
   float* vplane_ = nullptr;
   float2* B_ = nullptr;
+  void* Bimg_ = nullptr;             // B_ split into bf16 hi/lo operand tiles
   double2* pout_ = nullptr;
   float2* pf_ = nullptr;
   double2* part_ = nullptr;

@@ -179,9 +179,15 @@ void ritz_values(const float2* A, const float2* V, const int* perm, int n, doubl
 
 // ---- tensor-core GEMMs (tc_gemm.cu), split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulation ---------
 // Same contract as gemm_cn<float> / rotate<float>; err receives 1 if a bounded wait expired.
-// out32, when given, receives an FP32 copy of out.
+// out32, when given, receives an FP32 copy of out.  Aimg, when given, is A's pre-split image
+// (tc_overlap_prepare_a of the same A, m and K): A's operand tiles then arrive by bulk copy.
 void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n, int K, double2* part,
-                size_t part_elems, double2* out, int* err, cudaStream_t s, float2* out32 = nullptr);
+                size_t part_elems, double2* out, int* err, cudaStream_t s, float2* out32 = nullptr,
+                const void* Aimg = nullptr);
+// Bytes of the pre-split image of an m x K operand, and the image itself (bf16 hi and lo
+// operand tiles per 128-row tile and chunk of 16 complex; a constant operand is split once).
+size_t tc_overlap_image_bytes(int m, int K);
+void tc_overlap_prepare_a(const float2* A, int lda, int m, int K, void* img, cudaStream_t s);
 // Partial-buffer elements tc_overlap wants for an m x n output (one wave of CTAs).
 size_t tc_overlap_part_elems(int m, int n);
 void tc_rotate(const double2* M, int nin, const float2* X, const float2* X2, int nin1, int ldx, float2* Y, int ldy,

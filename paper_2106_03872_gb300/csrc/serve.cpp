@@ -73,7 +73,7 @@ size_t estimate_bytes(const ks_cell_desc& d) {
   } else {
     b += 2 * ns * d.N * ncols * 8 + N3 * 4 * 2;       // column buffers, planes, density partials
     const size_t np = (size_t)d.natoms * d.nproj;
-    b += np * nG * 8 + np * ns * 32 + np * ns * 16 * 40;
+    b += 2 * np * nG * 8 + np * ns * 32 + np * ns * 16 * 40;   // projector block and its split image
   }
   b += (size_t)d.natoms * 1400 * (d.nproj + 4) * 8;   // projector tables
   return b + (size_t(64) << 20);

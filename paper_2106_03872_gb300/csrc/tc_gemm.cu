@@ -209,10 +209,15 @@ constexpr int O_RING = O_NOP * O_OP_STAGE;                   // 192 KB
 constexpr int O_SMEM = O_RING + 1024;
 
 
-template <bool SAME>
-__global__ void __launch_bounds__(O_THREADS, 1)
+// PREP: A comes as a pre-split image (k_tc_prep_overlap_a: per 128-row tile and global chunk
+// of 16 complex, the hi and lo operand tiles as the split warps would write them) and one
+// extra warp copies each chunk's 16 KB with a bulk copy; the split warps handle B alone.
+constexpr int O_THREADS_PREP = O_THREADS + 32;
+template <bool SAME, bool PREP = false>
+__global__ void __launch_bounds__(PREP ? O_THREADS_PREP : O_THREADS, 1)
     k_tc_overlap(const float2* __restrict__ A, int lda, const float2* __restrict__ B, int ldb, int m, int n, int K,
-                 int kchunk, float2* __restrict__ part, int* __restrict__ err) {
+                 int kchunk, float2* __restrict__ part, int* __restrict__ err, const uint4* __restrict__ Aimg = nullptr,
+                 int nchunks = 0) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   const uint32_t op0 = smem_u32(tsm);
   uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + O_RING);
@@ -221,7 +226,7 @@ __global__ void __launch_bounds__(O_THREADS, 1)
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   if (t == 0) {
     for (int i = 0; i < O_NOP; ++i) {
-      mbar_init(full + 8 * i, 32 * O_SPLIT_WARPS);
+      mbar_init(full + 8 * i, 32 * O_SPLIT_WARPS + (PREP ? 1 : 0));
       mbar_init(empty + 8 * i, 1);
     }
     mbar_init(done, 1);
@@ -252,7 +257,7 @@ __global__ void __launch_bounds__(O_THREADS, 1)
       const int k = kbeg + c * O_KC + l;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        x[u] = (ra && k + 4 * u < kend) ? pa[k + 4 * u] : make_float2(0.f, 0.f);
+        if (!PREP) x[u] = (ra && k + 4 * u < kend) ? pa[k + 4 * u] : make_float2(0.f, 0.f);
         // SAME: one diagonal tile of A^H A, so B's rows are A's and are loaded once
         x[4 + u] = SAME ? x[u] : ((rb && k + 4 * u < kend) ? pb[k + 4 * u] : make_float2(0.f, 0.f));
       }
@@ -269,11 +274,14 @@ __global__ void __launch_bounds__(O_THREADS, 1)
       for (int u = 0; u < 4; ++u) {
         const int kr = 8 * u + 2 * l;        // real K index of the pair
         float h0, l0, h1, l1;
-        split1(x[u].x, h0, l0);
-        split1(x[u].y, h1, l1);
-        uint32_t o = tile_off(TC_M, r, kr);
-        sts32(oa_hi + o, pack_bf16(h0, h1));
-        sts32(oa_lo + o, pack_bf16(l0, l1));
+        uint32_t o;
+        if (!PREP) {
+          split1(x[u].x, h0, l0);
+          split1(x[u].y, h1, l1);
+          o = tile_off(TC_M, r, kr);
+          sts32(oa_hi + o, pack_bf16(h0, h1));
+          sts32(oa_lo + o, pack_bf16(l0, l1));
+        }
         // B real row 2j <- (re, im), row 2j+1 <- (im, -re)
         split1(x[4 + u].x, h0, l0);
         split1(x[4 + u].y, h1, l1);
@@ -294,7 +302,21 @@ __global__ void __launch_bounds__(O_THREADS, 1)
       chunk(c, xa);
       if (ok && c + 1 < nk) chunk(c + 1, xb);
     }
-  } else if (lane == 0) {
+  } else if (PREP && w == O_SPLIT_WARPS + 1) {
+    // A chunks of this CTA's tile: global chunk kbeg / O_KC + c of the image
+    if (lane == 0) {
+      const uint4* src = Aimg + ((size_t)blockIdx.y * nchunks + kbeg / O_KC) * (2 * O_A_BYTES / 16);
+      for (int c = 0; c < nk; ++c) {
+        const int st = c % O_NOP;
+        if (c >= O_NOP) {
+          ok = mbar_wait_bounded(empty + 8 * st, ((c / O_NOP) - 1) & 1);
+          if (!ok) break;
+        }
+        mbar_expect_tx(full + 8 * st, 2 * O_A_BYTES);
+        bulk_g2s(op0 + st * O_OP_STAGE, src + (size_t)c * (2 * O_A_BYTES / 16), 2 * O_A_BYTES, full + 8 * st);
+      }
+    }
+  } else if (w == O_SPLIT_WARPS && lane == 0) {
     constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
     constexpr uint32_t a_lbo = TC_M * 16, b_lbo = TC_N * 16;
     for (int c = 0; c < nk; ++c) {
@@ -596,11 +618,51 @@ void set_attrs() {
   if (g_attr_done) return;
   KS_CUDA(cudaFuncSetAttribute(k_tc_overlap<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
   KS_CUDA(cudaFuncSetAttribute(k_tc_overlap<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
+  KS_CUDA(cudaFuncSetAttribute(k_tc_overlap<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
   KS_CUDA(cudaFuncSetAttribute(k_tc_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, R_SMEM));
   g_attr_done = true;
 }
 
+// The pre-split image of A for the PREP overlap: thread (tile, chunk, row r, lane l) splits
+// the complexes l + 4u (u < 4) of the chunk of row r exactly as the split warps do, into the
+// hi and lo tiles of image block (tile, chunk); rows >= m and K >= K are zero.
+__global__ void k_tc_prep_overlap_a(const float2* __restrict__ A, int lda, int m, int K, int tiles, int nchunks,
+                                    uint32_t* __restrict__ img) {
+  const size_t total = (size_t)tiles * nchunks * TC_M * 4;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(e & 3), r = (int)((e >> 2) % TC_M);
+    const size_t tc = e / (TC_M * 4);                                 // tile * nchunks + chunk
+    const int chunk = (int)(tc % nchunks), tile = (int)(tc / nchunks);
+    const int row = tile * TC_M + r;
+    uint32_t* blk = img + tc * (2 * O_A_BYTES / 4);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = chunk * O_KC + l + 4 * u;
+      const float2 x = (row < m && k < K) ? A[(size_t)row * lda + k] : make_float2(0.f, 0.f);
+      float h0, l0, h1, l1;
+      split1(x.x, h0, l0);
+      split1(x.y, h1, l1);
+      const uint32_t o = tile_off(TC_M, r, 8 * u + 2 * l) / 4;
+      blk[o] = pack_bf16(h0, h1);
+      blk[O_A_BYTES / 4 + o] = pack_bf16(l0, l1);
+    }
+  }
+}
+
 }  // namespace
+
+size_t tc_overlap_image_bytes(int m, int K) {
+  const int tiles = (m + TC_M - 1) / TC_M, nchunks = (K + O_KC - 1) / O_KC;
+  return (size_t)tiles * nchunks * 2 * O_A_BYTES;
+}
+
+void tc_overlap_prepare_a(const float2* A, int lda, int m, int K, void* img, cudaStream_t s) {
+  const int tiles = (m + TC_M - 1) / TC_M, nchunks = (K + O_KC - 1) / O_KC;
+  const size_t total = (size_t)tiles * nchunks * TC_M * 4;
+  k_tc_prep_overlap_a<<<(unsigned)std::min<size_t>((total + 255) / 256, 8192), 256, 0, s>>>(
+      A, lda, m, K, tiles, nchunks, static_cast<uint32_t*>(img));
+  KS_CHECK_LAUNCH();
+}
 
 // SMs the overlap kernel spreads its K range over: the device's SMs less four, which the
 // block iteration's one-CTA side-stream kernels (factor, Rayleigh-Ritz step) hold while the
@@ -627,7 +689,7 @@ size_t tc_rotation_workspace_bytes(int m, int nin) {
 }
 
 void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n, int K, double2* part,
-                size_t part_elems, double2* out, int* err, cudaStream_t s, float2* out32) {
+                size_t part_elems, double2* out, int* err, cudaStream_t s, float2* out32, const void* Aimg) {
   set_attrs();
   const int tm = (m + TC_M - 1) / TC_M, tn = (n + TC_N / 2 - 1) / (TC_N / 2);
   int ks = std::max(1, sm_count() / (tm * tn));
@@ -640,7 +702,11 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
   dim3 g(tn, tm, ks);
   float2* p32 = reinterpret_cast<float2*>(part);                      // FP32 partials
   // one output tile of A^H A: both operands are the same rows
-  if (A == B && lda == ldb && m == n && tm == 1 && tn == 1)
+  if (Aimg)
+    k_tc_overlap<false, true><<<g, O_THREADS_PREP, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err,
+                                                                static_cast<const uint4*>(Aimg),
+                                                                (K + O_KC - 1) / O_KC);
+  else if (A == B && lda == ldb && m == n && tm == 1 && tn == 1)
     k_tc_overlap<true><<<g, O_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err);
   else
     k_tc_overlap<false><<<g, O_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err);
