@@ -98,6 +98,7 @@ struct HostGeometry {
   std::vector<int> cov_idx;     // flat grid index, increasing
   std::vector<int> cov_off;     // [ncov+1]
   std::vector<int> cov_ent;     // sphere point indices
+  std::vector<int> cov_scratch; // [N^3 + 1] counts, kept between rebuilds (no page faults per move)
   std::vector<double> occ;      // [nstates]
   std::vector<double> tw;       // [N][2] cos, sin of 2 pi t / N
 };

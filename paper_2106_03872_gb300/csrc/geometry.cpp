@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <thread>
 
 #include "common.h"
 
@@ -76,13 +77,16 @@ void build_atoms(const double* pos, HostGeometry& g) {
   g.pos.assign(pos ? pos : nullptr, pos ? pos + 3 * (size_t)g.natoms : nullptr);
 
   // ---- projector spheres |d| < R_c around each atom (minimum image), grid order ----------
-  g.sph_off.assign(1, 0);
-  g.sph_idx.clear();
-  g.sph_atom.clear();
-  g.sph_beta.clear();
+  // Atoms are independent: threads take contiguous ranges of atoms and the per-atom lists are
+  // joined in atom order, so the result does not depend on the thread count.
   const double s2 = 2.0 * g.proj_sigma * g.proj_sigma;
   const double rc2 = g.proj_rc * g.proj_rc;
-  for (int a = 0; a < g.natoms; ++a) {
+  struct AtomPts {
+    std::vector<int> idx;
+    std::vector<double> beta;
+  };
+  std::vector<AtomPts> per(g.natoms);
+  auto one_atom = [&](int a) {
     const double R[3] = {pos[3 * a], pos[3 * a + 1], pos[3 * a + 2]};
     int lo[3], hi[3];
     // per axis: wrapped grid index and minimum-image displacement of each box coordinate
@@ -101,7 +105,7 @@ void build_atoms(const double* pos, HostGeometry& g) {
     }
     // box points inside the sphere, then in grid order (a box wider than the grid would
     // repeat an index: the repeats are dropped)
-    std::vector<std::pair<int, int>> hit;                            // (grid index, slot in dd)
+    std::vector<std::pair<int, int>> hit;                            // (grid index, slot in cand)
     std::vector<double> cand;                                         // dx, dy, dz, r2 per hit
     for (size_t ix = 0; ix < jw[0].size(); ++ix)
       for (size_t iy = 0; iy < jw[1].size(); ++iy)
@@ -116,15 +120,16 @@ void build_atoms(const double* pos, HostGeometry& g) {
     bool wraps = false;
     for (int k = 0; k < 3; ++k) wraps = wraps || lo[k] < 0 || hi[k] >= N;
     if (wraps) std::sort(hit.begin(), hit.end());
-    std::vector<int> inside;
+    AtomPts& out = per[a];
     std::vector<double> dd;
     for (size_t i = 0; i < hit.size(); ++i) {
       if (i > 0 && hit[i].first == hit[i - 1].first) continue;
-      inside.push_back(hit[i].first);
+      out.idx.push_back(hit[i].first);
       dd.insert(dd.end(), cand.begin() + 4 * hit[i].second, cand.begin() + 4 * hit[i].second + 4);
     }
-    const size_t np = inside.size();
-    std::vector<double> beta(np * g.nproj);
+    const size_t np = out.idx.size();
+    std::vector<double>& beta = out.beta;
+    beta.assign(np * g.nproj, 0.0);
     std::vector<double> norm(g.nproj, 0.0);
     for (size_t i = 0; i < np; ++i) {
       const double gs = std::exp(-dd[4 * i + 3] / s2);
@@ -134,20 +139,37 @@ void build_atoms(const double* pos, HostGeometry& g) {
       for (int l = 0; l < g.nproj; ++l) norm[l] += beta[i * g.nproj + l] * beta[i * g.nproj + l];
     }
     for (int l = 0; l < g.nproj; ++l) {
-      const double s = (norm[l] > 0) ? 1.0 / std::sqrt(g.dV * norm[l]) : 0.0;
-      for (size_t i = 0; i < np; ++i) beta[i * g.nproj + l] *= s;
+      const double sc = (norm[l] > 0) ? 1.0 / std::sqrt(g.dV * norm[l]) : 0.0;
+      for (size_t i = 0; i < np; ++i) beta[i * g.nproj + l] *= sc;
     }
-    for (size_t i = 0; i < np; ++i) {
-      g.sph_idx.push_back(inside[i]);
-      g.sph_atom.push_back(a);
-      for (int l = 0; l < g.nproj; ++l) g.sph_beta.push_back(beta[i * g.nproj + l]);
-    }
+  };
+  const int nthr = (int)std::max(1, std::min<int>({8, g.natoms / 8, (int)std::thread::hardware_concurrency()}));
+  if (nthr > 1) {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthr; ++t)
+      pool.emplace_back([&, t] {
+        for (int a = (int)((long)g.natoms * t / nthr); a < (int)((long)g.natoms * (t + 1) / nthr); ++a) one_atom(a);
+      });
+    for (auto& th : pool) th.join();
+  } else {
+    for (int a = 0; a < g.natoms; ++a) one_atom(a);
+  }
+  g.sph_off.assign(1, 0);
+  g.sph_idx.clear();
+  g.sph_atom.clear();
+  g.sph_beta.clear();
+  for (int a = 0; a < g.natoms; ++a) {
+    g.sph_idx.insert(g.sph_idx.end(), per[a].idx.begin(), per[a].idx.end());
+    g.sph_atom.insert(g.sph_atom.end(), per[a].idx.size(), a);
+    g.sph_beta.insert(g.sph_beta.end(), per[a].beta.begin(), per[a].beta.end());
     g.sph_off.push_back((int)g.sph_idx.size());
   }
   // inverse lists (grid point -> its sphere points, atoms in index order): count the sphere
   // points of every grid point, then place the points in increasing order
   const size_t N3 = (size_t)N * N * N;
-  std::vector<int> first(N3 + 1, 0);
+  std::vector<int>& first = g.cov_scratch;
+  first.resize(N3 + 1);
+  std::fill(first.begin(), first.end(), 0);
   for (int idx : g.sph_idx) ++first[idx + 1];
   g.cov_idx.clear();
   g.cov_off.assign(1, 0);
