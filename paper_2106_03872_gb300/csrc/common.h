@@ -94,6 +94,7 @@ struct HostGeometry {
   std::vector<int> sph_idx;     // flat grid index of each sphere point
   std::vector<int> sph_atom;    // atom of each sphere point
   std::vector<double> sph_beta; // [npts][nproj]
+  std::vector<int> sph_zorder;  // [npts] the atom's sphere points visited plane by plane (z, then x, y)
   // inverse lists: every grid point covered by >= 1 sphere, with its sphere points in atom order
   std::vector<int> cov_idx;     // flat grid index, increasing
   std::vector<int> cov_off;     // [ncov+1]

@@ -157,6 +157,7 @@ template <typename T> class Engine final : public EngineBase {
     t_.sph_idx = upload(g_.sph_idx);
     t_.sph_atom = upload(g_.sph_atom);
     t_.sph_beta = upload_real(g_.sph_beta);
+    t_.sph_zorder = upload(g_.sph_zorder);
     t_.cov_idx = upload(g_.cov_idx);
     t_.cov_off = upload(g_.cov_off);
     t_.cov_ent = upload(g_.cov_ent);
@@ -849,7 +850,7 @@ template <typename T> class Engine final : public EngineBase {
         nl_force<T>(fp_, fq_, na, np, nb, 2.0 * g_.D, occ_ + b0, fnl_, a, s);
       }
     }
-    local_force<T>(fg_, fxyz_, N, na, -g_.dV * g_.vloc_depth / g_.omega, floc_, s, zmajor);
+    local_force<T>(fg_, fxyz_, N, na, -g_.dV * g_.vloc_depth / g_.omega, flocp_, floc_, s, zmajor);
     std::vector<double> fl(3 * (size_t)na), fn(3 * (size_t)na);
     KS_CUDA(cudaMemcpyAsync(fl.data(), floc_, fl.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     KS_CUDA(cudaMemcpyAsync(fn.data(), fnl_, fn.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -910,13 +911,14 @@ template <typename T> class Engine final : public EngineBase {
     build_atoms(pos, g_);
     // projector sphere lists (their sizes change as grid points enter and leave the spheres)
     for (const void* q : {(const void*)t_.sph_off, (const void*)t_.sph_idx, (const void*)t_.sph_atom,
-                          (const void*)t_.sph_beta, (const void*)t_.cov_idx, (const void*)t_.cov_off,
-                          (const void*)t_.cov_ent})
+                          (const void*)t_.sph_beta, (const void*)t_.sph_zorder, (const void*)t_.cov_idx,
+                          (const void*)t_.cov_off, (const void*)t_.cov_ent})
       arena_.release(q);
     t_.sph_off = upload(g_.sph_off);
     t_.sph_idx = upload(g_.sph_idx);
     t_.sph_atom = upload(g_.sph_atom);
     t_.sph_beta = upload_real(g_.sph_beta);
+    t_.sph_zorder = upload(g_.sph_zorder);
     t_.cov_idx = upload(g_.cov_idx);
     t_.cov_off = upload(g_.cov_off);
     t_.cov_ent = upload(g_.cov_ent);
@@ -1052,12 +1054,12 @@ template <typename T> class Engine final : public EngineBase {
   }
 
   // Work buffers of the force evaluation (allocated on first use): full grids for a chunk of
-  // fb_ states (at most 512 MB for the two), their projections, the gradient densities.
+  // fb_ states (at most 2 GB for the two), their projections, the gradient densities.
   void force_buffers() {
     if (fw_) return;
     const int N = g_.N, na = g_.natoms, np = g_.nproj;
     const size_t N3 = (size_t)N * N * N;
-    fb_ = (int)std::max<size_t>(1, std::min<size_t>((size_t)ns_, (size_t(512) << 20) / (2 * N3 * sizeof(C))));
+    fb_ = (int)std::max<size_t>(1, std::min<size_t>((size_t)ns_, (size_t(2048) << 20) / (2 * N3 * sizeof(C))));
     fpsi_ = alloc<C>((size_t)fb_ * N3);
     fw_ = alloc<C>((size_t)fb_ * N3);
     fg_ = alloc<T>(3 * N3);
@@ -1065,6 +1067,7 @@ template <typename T> class Engine final : public EngineBase {
     fq_ = alloc<C>((size_t)fb_ * na * np);
     fnl_ = alloc<double>(3 * (size_t)na);
     floc_ = alloc<double>(3 * (size_t)na);
+    flocp_ = alloc<double>(3 * (size_t)na * LOCAL_FORCE_SPLIT);
   }
 
   // Per atom and axis: X_a(x) = sum_{s = -1, 0, 1} exp(-(x - R_a - L s)^2 / (2 w^2)) on the
@@ -1216,7 +1219,7 @@ template <typename T> class Engine final : public EngineBase {
   int fb_ = 1;
   T* fg_ = nullptr;
   C *fp_ = nullptr, *fq_ = nullptr;
-  double *fnl_ = nullptr, *floc_ = nullptr, *fxyz_ = nullptr;
+  double *fnl_ = nullptr, *floc_ = nullptr, *flocp_ = nullptr, *fxyz_ = nullptr;
   T* hist_n_[PULAY_MAX] = {};       // Pulay history: input densities and residuals (allocated on first use)
   T* hist_r_[PULAY_MAX] = {};
   double* pulay_partials_ = nullptr;

@@ -84,6 +84,7 @@ void build_atoms(const double* pos, HostGeometry& g) {
   struct AtomPts {
     std::vector<int> idx;
     std::vector<double> beta;
+    std::vector<int> zorder;                                          // positions in idx
   };
   std::vector<AtomPts> per(g.natoms);
   auto one_atom = [&](int a) {
@@ -142,6 +143,23 @@ void build_atoms(const double* pos, HostGeometry& g) {
       const double sc = (norm[l] > 0) ? 1.0 / std::sqrt(g.dV * norm[l]) : 0.0;
       for (size_t i = 0; i < np; ++i) beta[i * g.nproj + l] *= sc;
     }
+    // plane-major visiting order (box z outermost, then x, then y): a pass over a grid laid
+    // out [z][x][y] then reads runs of consecutive y (a grid index met twice, in a box wider
+    // than the grid, is visited once)
+    std::vector<char> seen(np, 0);
+    for (size_t iz = 0; iz < jw[2].size(); ++iz)
+      for (size_t ix = 0; ix < jw[0].size(); ++ix)
+        for (size_t iy = 0; iy < jw[1].size(); ++iy) {
+          const double dx = dw[0][ix], dy = dw[1][iy], dz = dw[2][iz];
+          if (!(dx * dx + dy * dy + dz * dz < rc2)) continue;
+          const int gi = (jw[0][ix] * N + jw[1][iy]) * N + jw[2][iz];
+          const auto it = std::lower_bound(out.idx.begin(), out.idx.end(), gi);
+          const int q = (int)(it - out.idx.begin());
+          if (!seen[q]) {
+            seen[q] = 1;
+            out.zorder.push_back(q);
+          }
+        }
   };
   const int nthr = (int)std::max(1, std::min<int>({8, g.natoms / 8, (int)std::thread::hardware_concurrency()}));
   if (nthr > 1) {
@@ -158,7 +176,10 @@ void build_atoms(const double* pos, HostGeometry& g) {
   g.sph_idx.clear();
   g.sph_atom.clear();
   g.sph_beta.clear();
+  g.sph_zorder.clear();
   for (int a = 0; a < g.natoms; ++a) {
+    const int base = (int)g.sph_idx.size();
+    for (int q : per[a].zorder) g.sph_zorder.push_back(base + q);
     g.sph_idx.insert(g.sph_idx.end(), per[a].idx.begin(), per[a].idx.end());
     g.sph_atom.insert(g.sph_atom.end(), per[a].idx.size(), a);
     g.sph_beta.insert(g.sph_beta.end(), per[a].beta.begin(), per[a].beta.end());

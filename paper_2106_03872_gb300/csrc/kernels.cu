@@ -156,17 +156,18 @@ __global__ void k_scatter_grad(const cplx<T>* __restrict__ psi, cplx<T>* __restr
   }
 }
 
-// gacc[j] += sum_b occ[b] 2 Re(conj(dpsi[b][j]) psi[b][j]), states in order, FP64 sum
+// gacc[j] += sum_b occ[b] 2 Re(conj(dpsi[b][j]) psi[b][j]), states in order, summed in T (the
+// precision of gacc; FP64 arithmetic would run at 1/64 of the FP32 rate on the mixed path)
 template <typename T>
 __global__ void k_grad_accumulate(const cplx<T>* __restrict__ dpsi, const cplx<T>* __restrict__ psi, T* __restrict__ gacc,
                                   size_t N3, int nb, const double* __restrict__ occ) {
   for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < N3; j += (size_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
+    T acc = 0;
     for (int b = 0; b < nb; ++b) {
       const cplx<T> d = dpsi[b * N3 + j], p = psi[b * N3 + j];
-      acc += occ[b] * 2.0 * ((double)d.x * (double)p.x + (double)d.y * (double)p.y);
+      acc += (T)(2.0 * occ[b]) * (d.x * p.x + d.y * p.y);
     }
-    gacc[j] += (T)acc;
+    gacc[j] += acc;
   }
 }
 
@@ -193,14 +194,15 @@ __global__ void k_nl_force(const cplx<T>* __restrict__ p, const cplx<T>* __restr
 // atom the three per-axis image sums [natoms][3][N] of the separable Gaussian
 template <typename T>
 __global__ void k_local_force(const T* __restrict__ g, const double* __restrict__ xyz, int N, double coef,
-                              double* __restrict__ floc, int zmajor) {
-  const int I = blockIdx.x;
+                              double* __restrict__ partials, int zmajor) {
+  const int I = blockIdx.x, sl = blockIdx.y;
   const size_t N3 = (size_t)N * N * N;
+  const size_t j0 = N3 * sl / LOCAL_FORCE_SPLIT, j1 = N3 * (sl + 1) / LOCAL_FORCE_SPLIT;
   const double* X = xyz + (size_t)I * 3 * N;
   const double* Y = X + N;
   const double* Z = Y + N;
   double acc[3] = {0.0, 0.0, 0.0};
-  for (size_t j = threadIdx.x; j < N3; j += blockDim.x) {
+  for (size_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     const int a0 = (int)(j % N), a1 = (int)((j / N) % N), a2 = (int)(j / ((size_t)N * N));
     const int jz = zmajor ? a2 : a0, jy = zmajor ? a0 : a1, jx = zmajor ? a1 : a2;
     const double v = X[jx] * Y[jy] * Z[jz];
@@ -210,7 +212,16 @@ __global__ void k_local_force(const T* __restrict__ g, const double* __restrict_
   }
   block_sum<3>(acc);
   if (threadIdx.x == 0)
-    for (int a = 0; a < 3; ++a) floc[3 * I + a] = coef * acc[a];
+    for (int a = 0; a < 3; ++a) partials[((size_t)I * LOCAL_FORCE_SPLIT + sl) * 3 + a] = coef * acc[a];
+}
+
+__global__ void k_local_force_finish(const double* __restrict__ partials, int natoms, double* __restrict__ floc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;                // 3 I + a
+  if (e >= 3 * natoms) return;
+  const int I = e / 3, a = e % 3;
+  double s = 0.0;
+  for (int sl = 0; sl < LOCAL_FORCE_SPLIT; ++sl) s += partials[((size_t)I * LOCAL_FORCE_SPLIT + sl) * 3 + a];
+  floc[e] = s;
 }
 
 // The local potential of Gaussian atoms from their separable 27-image axis factors.
@@ -260,12 +271,14 @@ __global__ void k_dipole_finish(const double* __restrict__ partials, int nblocks
 template <typename T, int NP>
 __global__ void k_nl_project(const cplx<T>* __restrict__ grid, size_t N3, const int* __restrict__ sph_off,
                              const int* __restrict__ sph_idx, const T* __restrict__ beta, int natoms,
-                             cplx<T>* __restrict__ proj, T scale, int zmajor_n) {
+                             cplx<T>* __restrict__ proj, T scale, int zmajor_n, const int* __restrict__ zorder) {
   const int I = blockIdx.x, b = blockIdx.y;
   double acc[2 * NP];
 #pragma unroll
   for (int i = 0; i < 2 * NP; ++i) acc[i] = 0.0;
-  for (int p = sph_off[I] + threadIdx.x; p < sph_off[I + 1]; p += blockDim.x) {
+  for (int q = sph_off[I] + threadIdx.x; q < sph_off[I + 1]; q += blockDim.x) {
+    // on [z][x][y] grids the points go plane by plane, so that a warp reads runs of y
+    const int p = zmajor_n ? zorder[q] : q;
     int idx = sph_idx[p];
     if (zmajor_n) {                                                   // (x, y, z) -> [z][x][y]
       const int n = zmajor_n, jz = idx % n, jxy = idx / n;
@@ -654,9 +667,11 @@ void nl_force(const cplx<T>* p, const cplx<T>* q, int natoms, int nproj, int nb,
 }
 
 template <typename T>
-void local_force(const T* g, const double* xyz, int N, int natoms, double coef, double* floc, cudaStream_t s,
-                 bool zmajor) {
-  k_local_force<T><<<natoms, RED_THREADS, 0, s>>>(g, xyz, N, coef, floc, zmajor ? 1 : 0);
+void local_force(const T* g, const double* xyz, int N, int natoms, double coef, double* partials, double* floc,
+                 cudaStream_t s, bool zmajor) {
+  k_local_force<T><<<dim3(natoms, LOCAL_FORCE_SPLIT), RED_THREADS, 0, s>>>(g, xyz, N, coef, partials, zmajor ? 1 : 0);
+  KS_CHECK_LAUNCH();
+  k_local_force_finish<<<(3 * natoms + 127) / 128, 128, 0, s>>>(partials, natoms, floc);
   KS_CHECK_LAUNCH();
 }
 
@@ -703,9 +718,11 @@ void nl_project(const cplx<T>* grid, const DevTables<T>& t, cplx<T>* proj, int n
   const size_t N3 = (size_t)t.N * t.N * t.N;
   const int zn = zmajor ? t.N : 0;
   if (t.nproj == 4)
-    k_nl_project<T, 4><<<g, RED_THREADS, 0, s>>>(grid, N3, t.sph_off, t.sph_idx, t.sph_beta, t.natoms, proj, scale, zn);
+    k_nl_project<T, 4><<<g, RED_THREADS, 0, s>>>(grid, N3, t.sph_off, t.sph_idx, t.sph_beta, t.natoms, proj, scale, zn,
+                                                 t.sph_zorder);
   else
-    k_nl_project<T, 1><<<g, RED_THREADS, 0, s>>>(grid, N3, t.sph_off, t.sph_idx, t.sph_beta, t.natoms, proj, scale, zn);
+    k_nl_project<T, 1><<<g, RED_THREADS, 0, s>>>(grid, N3, t.sph_off, t.sph_idx, t.sph_beta, t.natoms, proj, scale, zn,
+                                                 t.sph_zorder);
   KS_CHECK_LAUNCH();
 }
 
@@ -898,7 +915,7 @@ void real_to_double(const T* in, double* out, size_t n, cudaStream_t s) {
   template void grad_accumulate<T>(const cplx<T>*, const cplx<T>*, T*, int, int, const double*, cudaStream_t);  \
   template void nl_force<T>(const cplx<T>*, const cplx<T>*, int, int, int, double, const double*, double*, int,  \
                             cudaStream_t);                                                                      \
-  template void local_force<T>(const T*, const double*, int, int, double, double*, cudaStream_t, bool);         \
+  template void local_force<T>(const T*, const double*, int, int, double, double*, double*, cudaStream_t, bool); \
   template void grad_packed<T>(const cplx<T>*, cplx<T>*, const DevTables<T>&, int, int, cudaStream_t);          \
   template void vloc_from_axes<T>(const double*, int, int, double, T*, double*, cudaStream_t);                  \
   template void state_dots<T>(const cplx<T>*, const cplx<T>*, int, int, double2*, cudaStream_t);                \

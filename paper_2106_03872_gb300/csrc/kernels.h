@@ -20,6 +20,7 @@ template <typename T> struct DevTables {
   const int* sph_idx = nullptr;       // [npts]
   const int* sph_atom = nullptr;      // [npts]
   const T* sph_beta = nullptr;        // [npts][nproj]
+  const int* sph_zorder = nullptr;    // [npts] plane-major visiting order of each atom's points
   const int* cov_idx = nullptr;       // [ncov]
   const int* cov_off = nullptr;       // [ncov+1]
   const int* cov_ent = nullptr;       // [nent]
@@ -40,16 +41,18 @@ template <typename T> void multiply_phase(cplx<T>* grid, int N, double L, const 
 // Forces (Eq. 11): grid[b][gidx[g]] = i G_alpha c_bg for nb states (grids zeroed before)
 template <typename T> void scatter_grad(const cplx<T>* psi, cplx<T>* grid, const DevTables<T>& t, int alpha, int nb,
                                         cudaStream_t s);
-// gacc[j] += sum_{b < nb} occ[b] 2 Re(conj(dpsi[b][j]) psi[b][j])  (states in order, FP64 sum)
+// gacc[j] += sum_{b < nb} occ[b] 2 Re(conj(dpsi[b][j]) psi[b][j])  (states in order, summed in T)
 template <typename T> void grad_accumulate(const cplx<T>* dpsi, const cplx<T>* psi, T* gacc, int N3, int nb,
                                            const double* occ, cudaStream_t s);
 // fnl[3 I + alpha] -= w sum_{b < nb} occ[b] sum_l Re(conj(q_bIl) p_bIl) (projections [nb][natoms][nproj])
 template <typename T> void nl_force(const cplx<T>* p, const cplx<T>* q, int natoms, int nproj, int nb, double w,
                                     const double* occ, double* fnl, int alpha, cudaStream_t s);
 // floc[3 I + a] = coef sum_j X_I[jx] Y_I[jy] Z_I[jz] g_a[j], g [3][N^3], xyz [natoms][3][N];
-// zmajor: g laid out [z][x][y]
-template <typename T> void local_force(const T* g, const double* xyz, int N, int natoms, double coef, double* floc,
-                                       cudaStream_t s, bool zmajor = false);
+// zmajor: g laid out [z][x][y].  Each atom's sum runs over LOCAL_FORCE_SPLIT slices of the
+// grid (partials [natoms][LOCAL_FORCE_SPLIT][3]), then the slices are added in order.
+constexpr int LOCAL_FORCE_SPLIT = 8;
+template <typename T> void local_force(const T* g, const double* xyz, int N, int natoms, double coef, double* partials,
+                                       double* floc, cudaStream_t s, bool zmajor = false);
 // out[b][g] = i G_alpha c_bg (packed, nb states)
 template <typename T> void grad_packed(const cplx<T>* psi, cplx<T>* out, const DevTables<T>& t, int alpha, int nb,
                                        cudaStream_t s);
