@@ -421,7 +421,7 @@ template <typename T> class Engine final : public EngineBase {
 
   // Rayleigh-Ritz on (psi_, hpsi_): H_sub = Psi^H H Psi, eigh, rotate both.
   void rr_core(cudaStream_t s) {
-    const int n = ns_, nG = g_.nG;
+    const int n = ns_;
     {
       ProfScope p(prof, "gram", s);
       overlap(psi_, hpsi_, n, mA_, s);
@@ -900,15 +900,19 @@ template <typename T> class Engine final : public EngineBase {
   // with H(t+dt) of the ETRS step taken at the ions' positions at t + dt).
   // ------------------------------------------------------------------------------------------
   void set_positions(const double* pos, cudaStream_t s) override {
-    const int na = g_.natoms, N = g_.N;
+    const int na = g_.natoms;
     if (na == 0) return;
     for (int i = 0; i < 3 * na; ++i)
       if (!std::isfinite(pos[i])) fail(KS_ERR_ARG, "set_positions: position %d is not finite", i);
-    const size_t N3 = (size_t)N * N * N;
+    // the host lists first: they touch no device memory, so they overlap the kernels still in
+    // flight (in Ehrenfest dynamics, the first half of the real-time step)
+    build_atoms(pos, g_);
+    if constexpr (sizeof(T) == 4) {
+      if (fused_) fused_->prepare_atoms();
+    }
     KS_CUDA(cudaStreamSynchronize(s));
     KS_CUDA(cudaDeviceSynchronize());
     ProfScope p(prof, "set_positions", s);
-    build_atoms(pos, g_);
     // projector sphere lists (their sizes change as grid points enter and leave the spheres)
     for (const void* q : {(const void*)t_.sph_off, (const void*)t_.sph_idx, (const void*)t_.sph_atom,
                           (const void*)t_.sph_beta, (const void*)t_.sph_zorder, (const void*)t_.cov_idx,

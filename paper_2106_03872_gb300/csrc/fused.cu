@@ -616,7 +616,14 @@ class FusedImpl final : public FusedOps {
     dispatch([&](auto tag) { launch_plane_inverse<decltype(tag)::value>(n, out, s); });
   }
 
+  void prepare_atoms() override {
+    plane_lists_host();
+    lists_ready_ = true;
+  }
+
   void set_atoms(const DevTables<float>& t) override {
+    if (!lists_ready_) plane_lists_host();
+    lists_ready_ = false;
     KS_CUDA(cudaDeviceSynchronize());
     t_ = t;
     arena_.release(nl_.pt_off);
@@ -624,7 +631,7 @@ class FusedImpl final : public FusedOps {
     arena_.release(nl_.ent_off);
     arena_.release(nl_.ent_proj);
     arena_.release(nl_.ent_beta);
-    build_plane_lists();
+    upload_plane_lists();
     if (nprojtot_ > 0) build_projector_block();
   }
 
@@ -732,9 +739,21 @@ class FusedImpl final : public FusedOps {
   // Per-plane projector lists from the geometry's inverse lists: the covered points of each
   // z-plane, each with its sphere entries (first projector row and the nproj beta values).
   void build_plane_lists() {
+    plane_lists_host();
+    upload_plane_lists();
+  }
+  void plane_lists_host() {
     const HostGeometry& g = g_;
-    std::vector<int> pt_off(N_ + 1, 0), pt_xy, ent_off(1, 0), ent_proj;
-    std::vector<float> ent_beta;
+    std::vector<int>& pt_off = h_pt_off_;
+    std::vector<int>& pt_xy = h_pt_xy_;
+    std::vector<int>& ent_off = h_ent_off_;
+    std::vector<int>& ent_proj = h_ent_proj_;
+    std::vector<float>& ent_beta = h_ent_beta_;
+    pt_off.assign(N_ + 1, 0);
+    pt_xy.clear();
+    ent_off.assign(1, 0);
+    ent_proj.clear();
+    ent_beta.clear();
     std::vector<std::vector<int>> byz(N_);
     for (size_t c = 0; c < g.cov_idx.size(); ++c) byz[g.cov_idx[c] % N_].push_back((int)c);
     for (int z = 0; z < N_; ++z) {
@@ -749,12 +768,14 @@ class FusedImpl final : public FusedOps {
       }
       pt_off[z + 1] = (int)pt_xy.size();
     }
-    nl_.pt_off = upload(pt_off);
-    nl_.pt_xy = upload(pt_xy);
-    nl_.ent_off = upload(ent_off);
-    nl_.ent_proj = upload(ent_proj);
-    nl_.ent_beta = upload(ent_beta);
-    nl_.nproj = g.nproj;
+  }
+  void upload_plane_lists() {
+    nl_.pt_off = upload(h_pt_off_);
+    nl_.pt_xy = upload(h_pt_xy_);
+    nl_.ent_off = upload(h_ent_off_);
+    nl_.ent_proj = upload(h_ent_proj_);
+    nl_.ent_beta = upload(h_ent_beta_);
+    nl_.nproj = g_.nproj;
   }
 
   // B[atom*nproj + l][G] = c_G[beta_Il] = Omega^{1/2} N^-3 sum_j exp(-iG.r_j) beta_Il(r_j), by the
@@ -841,6 +862,9 @@ class FusedImpl final : public FusedOps {
   int* err_;
   int N_ = 0, ncols_ = 0, nprojtot_ = 0;
   PlaneNL nl_{};
+  std::vector<int> h_pt_off_, h_pt_xy_, h_ent_off_, h_ent_proj_;   // host copies of the plane lists
+  std::vector<float> h_ent_beta_;
+  bool lists_ready_ = false;
   float2* colbuf1_ = nullptr;
   float2* colbuf2_ = nullptr;
   float* vplane_ = nullptr;

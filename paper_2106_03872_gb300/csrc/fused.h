@@ -21,8 +21,11 @@ class FusedOps {
   // out[b][z][x][y] = Omega^{1/2} psi_b(r) on the grid (plane-major: z slowest), the unscaled
   // inverse transform of n packed states, by the pruned z-columns and the in-SMEM y, x passes.
   virtual void real_space(const float2* psi, int n, float2* out, cudaStream_t s) = 0;
-  // The atoms moved: rebuild the per-plane projector lists and the projector block from the
-  // geometry's new sphere lists (t: the engine's re-uploaded tables).  Synchronous.
+  // The atoms moved.  prepare_atoms forms the per-plane projector lists on the host from the
+  // geometry's new sphere lists (no device work, so it may overlap kernels in flight);
+  // set_atoms uploads them and rebuilds the projector block (t: the engine's re-uploaded
+  // tables).  Synchronous.
+  virtual void prepare_atoms() = 0;
   virtual void set_atoms(const DevTables<float>& t) = 0;
 };
 
