@@ -580,7 +580,7 @@ class FusedImpl final : public FusedOps {
       Bimg_ = arena_.alloc(tc_overlap_image_bytes(nprojtot_, g.nG));
       pout_ = alloc<double2>((size_t)nprojtot_ * ns_);
       pf_ = alloc<float2>((size_t)nprojtot_ * ns_);
-      part_elems_ = std::max<size_t>(tc_overlap_part_elems(nprojtot_, ns_), 4096);
+      part_elems_ = std::max<size_t>(tc_overlap_part_elems(nprojtot_, ns_, true), 4096);
       part_ = alloc<double2>(part_elems_);
       build_projector_block();
     }

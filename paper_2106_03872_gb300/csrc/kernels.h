@@ -192,7 +192,7 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
 size_t tc_overlap_image_bytes(int m, int K);
 void tc_overlap_prepare_a(const float2* A, int lda, int m, int K, void* img, cudaStream_t s);
 // Partial-buffer elements tc_overlap wants for an m x n output (one wave of CTAs).
-size_t tc_overlap_part_elems(int m, int n);
+size_t tc_overlap_part_elems(int m, int n, bool prepared = false);
 void tc_rotate(const double2* M, int nin, const float2* X, const float2* X2, int nin1, int ldx, float2* Y, int ldy,
                int m, int K, void* work, size_t work_bytes, int* err, cudaStream_t s);
 size_t tc_rotation_workspace_bytes(int m, int nin);

@@ -213,19 +213,24 @@ constexpr int O_SMEM = O_RING + 1024;
 // of 16 complex, the hi and lo operand tiles as the split warps would write them) and one
 // extra warp copies each chunk's 16 KB with a bulk copy; the split warps handle B alone.
 constexpr int O_THREADS_PREP = O_THREADS + 32;
+// The PREP form needs fewer registers (54 x 576 threads), so two CTAs share an SM, each with a
+// ring of two stages (97 KB): twice the loading warps per SM for the same operand bytes.
+constexpr int O_NOP_PREP = 2;
+constexpr int O_SMEM_PREP = O_NOP_PREP * O_OP_STAGE + 1024;
 template <bool SAME, bool PREP = false>
-__global__ void __launch_bounds__(PREP ? O_THREADS_PREP : O_THREADS, 1)
+__global__ void __launch_bounds__(PREP ? O_THREADS_PREP : O_THREADS, PREP ? 2 : 1)
     k_tc_overlap(const float2* __restrict__ A, int lda, const float2* __restrict__ B, int ldb, int m, int n, int K,
                  int kchunk, float2* __restrict__ part, int* __restrict__ err, const uint4* __restrict__ Aimg = nullptr,
                  int nchunks = 0) {
+  constexpr int NOP = PREP ? O_NOP_PREP : O_NOP, RING = NOP * O_OP_STAGE;
   extern __shared__ __align__(1024) unsigned char tsm[];
   const uint32_t op0 = smem_u32(tsm);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + O_RING);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(tsm + O_RING + 128);
-  const uint32_t full = smem_u32(bars), empty = full + 8 * O_NOP, done = empty + 8 * O_NOP;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + RING);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(tsm + RING + 128);
+  const uint32_t full = smem_u32(bars), empty = full + 8 * NOP, done = empty + 8 * NOP;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   if (t == 0) {
-    for (int i = 0; i < O_NOP; ++i) {
+    for (int i = 0; i < NOP; ++i) {
       mbar_init(full + 8 * i, 32 * O_SPLIT_WARPS + (PREP ? 1 : 0));
       mbar_init(empty + 8 * i, 1);
     }
@@ -263,9 +268,9 @@ __global__ void __launch_bounds__(PREP ? O_THREADS_PREP : O_THREADS, 1)
       }
     };
     auto chunk = [&](int c, float2 (&x)[8]) {
-      const int st = c % O_NOP;
-      if (c >= O_NOP) {
-        ok = mbar_wait_bounded(empty + 8 * st, ((c / O_NOP) - 1) & 1);
+      const int st = c % NOP;
+      if (c >= NOP) {
+        ok = mbar_wait_bounded(empty + 8 * st, ((c / NOP) - 1) & 1);
         if (!ok) return;
       }
       const uint32_t oa_hi = op0 + st * O_OP_STAGE, oa_lo = oa_hi + O_A_BYTES;
@@ -307,9 +312,9 @@ __global__ void __launch_bounds__(PREP ? O_THREADS_PREP : O_THREADS, 1)
     if (lane == 0) {
       const uint4* src = Aimg + ((size_t)blockIdx.y * nchunks + kbeg / O_KC) * (2 * O_A_BYTES / 16);
       for (int c = 0; c < nk; ++c) {
-        const int st = c % O_NOP;
-        if (c >= O_NOP) {
-          ok = mbar_wait_bounded(empty + 8 * st, ((c / O_NOP) - 1) & 1);
+        const int st = c % NOP;
+        if (c >= NOP) {
+          ok = mbar_wait_bounded(empty + 8 * st, ((c / NOP) - 1) & 1);
           if (!ok) break;
         }
         mbar_expect_tx(full + 8 * st, 2 * O_A_BYTES);
@@ -320,8 +325,8 @@ __global__ void __launch_bounds__(PREP ? O_THREADS_PREP : O_THREADS, 1)
     constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
     constexpr uint32_t a_lbo = TC_M * 16, b_lbo = TC_N * 16;
     for (int c = 0; c < nk; ++c) {
-      const int st = c % O_NOP;
-      ok = mbar_wait_bounded(full + 8 * st, (c / O_NOP) & 1);
+      const int st = c % NOP;
+      ok = mbar_wait_bounded(full + 8 * st, (c / NOP) & 1);
       if (!ok) break;
       tc_fence_after();
       const uint32_t oa_hi = op0 + st * O_OP_STAGE, oa_lo = oa_hi + O_A_BYTES;
@@ -618,7 +623,7 @@ void set_attrs() {
   if (g_attr_done) return;
   KS_CUDA(cudaFuncSetAttribute(k_tc_overlap<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
   KS_CUDA(cudaFuncSetAttribute(k_tc_overlap<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
-  KS_CUDA(cudaFuncSetAttribute(k_tc_overlap<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
+  KS_CUDA(cudaFuncSetAttribute(k_tc_overlap<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM_PREP));
   KS_CUDA(cudaFuncSetAttribute(k_tc_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, R_SMEM));
   g_attr_done = true;
 }
@@ -678,9 +683,9 @@ static int sm_count() {
   return n;
 }
 
-size_t tc_overlap_part_elems(int m, int n) {
+size_t tc_overlap_part_elems(int m, int n, bool prepared) {
   const int tm = (m + TC_M - 1) / TC_M, tn = (n + TC_N / 2 - 1) / (TC_N / 2);
-  return (size_t)m * n * (size_t)std::max(1, sm_count() / (tm * tn));
+  return (size_t)m * n * (size_t)std::max(1, (prepared ? 2 : 1) * sm_count() / (tm * tn));
 }
 
 size_t tc_rotation_workspace_bytes(int m, int nin) {
@@ -692,7 +697,7 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
                 size_t part_elems, double2* out, int* err, cudaStream_t s, float2* out32, const void* Aimg) {
   set_attrs();
   const int tm = (m + TC_M - 1) / TC_M, tn = (n + TC_N / 2 - 1) / (TC_N / 2);
-  int ks = std::max(1, sm_count() / (tm * tn));
+  int ks = std::max(1, (Aimg ? 2 : 1) * sm_count() / (tm * tn));   // the prepared form runs two CTAs per SM
   ks = std::min(ks, std::max(1, K / (4 * O_KC)));
   ks = (int)std::min<long>(ks, (long)(part_elems / ((size_t)m * n)));
   if (ks < 1) fail(KS_ERR_ARG, "tc_overlap: partial buffer too small");
@@ -703,7 +708,7 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
   float2* p32 = reinterpret_cast<float2*>(part);                      // FP32 partials
   // one output tile of A^H A: both operands are the same rows
   if (Aimg)
-    k_tc_overlap<false, true><<<g, O_THREADS_PREP, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err,
+    k_tc_overlap<false, true><<<g, O_THREADS_PREP, O_SMEM_PREP, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err,
                                                                 static_cast<const uint4*>(Aimg),
                                                                 (K + O_KC - 1) / O_KC);
   else if (A == B && lda == ldb && m == n && tm == 1 && tn == 1)
