@@ -211,3 +211,63 @@ def test_teter_preconditioning_converges_faster():
     assert np.sum(e_pc) < np.sum(e_sd) - 1e-3
     e_pc2, _ = ko.block_iteration_teter(cell, c, 30)
     assert np.all(e_pc2 <= e_pc + 1e-9)
+
+
+def test_teter_factor_series_limits_and_exact_values():
+    """K(x) of Teter, Payne and Allan, pinned by what its rational form fixes independently of
+    the code: K(x) = 1 - (16/27) x^4 + O(x^5) near 0 (so its first three derivatives vanish
+    there); x K(x) -> 1/2 as x -> infinity; and the exact values K(1/2) = 40/41, K(1) = 65/81,
+    K(2) = 175/431 worked out by hand from 27 + 18x + 12x^2 + 8x^3 over the same plus 16x^4.
+    A wrong coefficient anywhere fails one of them: the series fixes 27 and 16, the limit 8/16,
+    the three exact values the x and x^2 terms."""
+    for x in (1e-2, 2e-2):
+        q = (ko.teter_factor(x) - 1.0) / x ** 4
+        assert abs(q + 16.0 / 27.0) <= (16.0 / 27.0) * 1.0 * x          # next term is O(x)
+    # finite differences at 0: K'(0) = K''(0) = K'''(0) = 0 (each estimate is O(h) from x^4)
+    h = 1e-2
+    k = [ko.teter_factor(j * h) for j in range(-2, 3)]
+    d1 = (k[3] - k[1]) / (2 * h)
+    d2 = (k[3] - 2 * k[2] + k[1]) / h ** 2
+    d3 = (k[4] - 2 * k[3] + 2 * k[1] - k[0]) / (2 * h ** 3)
+    assert abs(d1) < 1e-5 and abs(d2) < 1e-3 and abs(d3) < 0.1
+    for x in (1e3, 1e5):
+        assert abs(x * ko.teter_factor(x) - 0.5) <= 1.0 / x
+    assert abs(ko.teter_factor(0.5) - 40.0 / 41.0) <= 1e-15
+    assert abs(ko.teter_factor(1.0) - 65.0 / 81.0) <= 1e-15
+    assert abs(ko.teter_factor(2.0) - 175.0 / 431.0) <= 1e-15
+    assert ko.teter_factor(0.0) == 1.0
+    xs = np.linspace(0.0, 50.0, 2001)
+    ks = ko.teter_factor(xs)
+    assert np.all(np.diff(ks) < 0) and np.all(ks > 0)
+
+
+def _two_wave_state(cell, m1, m2):
+    i1 = int(np.flatnonzero(np.all(cell.m == m1, axis=1))[0])
+    i2 = int(np.flatnonzero(np.all(cell.m == m2, axis=1))[0])
+    c = np.zeros((1, cell.nG), complex)
+    c[0, i1] = c[0, i2] = 1.0 / np.sqrt(2.0)
+    return c, i1, i2
+
+
+def test_teter_step_hand_computed():
+    """One preconditioned step of one free-electron state made of two plane waves (L = 2 pi, so
+    |G|^2/2 = |m|^2/2; V_loc = 0; D = 0.5), worked out by hand:
+    - waves m = 0 and (1,0,0): eps = 1/4, R = (-1/4, +1/4)/sqrt2, T = 1/4 is floored at
+      (2 pi / L)^2 / 2 = 1/2, alpha = 1/(1/2 + 1/2) = 1, K(0) = 1 and K(1) = 65/81, so the new
+      coefficients are (1 + 1/4)/sqrt2 and (1 - (65/81)/4)/sqrt2 = (259/324)/sqrt2;
+    - waves (1,0,0) and (2,0,0): eps = 5/4, R = (-3/4, +3/4)/sqrt2, T = (1/2 + 2)/2 = 5/4,
+      alpha = 1/(5/4 + 1/2) = 4/7, x = 2/5 and 8/5 with K = 22895/23151 and 74555/140091."""
+    cell = make_cell(L=2.0 * np.pi, N=8, natoms=0, ecut=2.5)
+    c, i1, i2 = _two_wave_state(cell, (0, 0, 0), (1, 0, 0))
+    eps, out = ko.block_iteration_teter(cell, c, 1)
+    assert abs(eps[0] - 0.25) <= 1e-14
+    s = 1.0 / np.sqrt(2.0)
+    assert abs(out[0, i1] - 1.25 * s) <= 1e-14
+    assert abs(out[0, i2] - (259.0 / 324.0) * s) <= 1e-14
+    assert np.max(np.abs(np.delete(out[0], [i1, i2]))) <= 1e-14
+    c, i1, i2 = _two_wave_state(cell, (1, 0, 0), (2, 0, 0))
+    eps, out = ko.block_iteration_teter(cell, c, 1)
+    assert abs(eps[0] - 1.25) <= 1e-14
+    a = 4.0 / 7.0
+    assert abs(out[0, i1] - (1.0 + a * (22895.0 / 23151.0) * 0.75) * s) <= 1e-14
+    assert abs(out[0, i2] - (1.0 - a * (74555.0 / 140091.0) * 0.75) * s) <= 1e-14
