@@ -73,12 +73,40 @@ def run_cpu_leg(nsteps, warmup, nsample):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline_obj(leg):
+def run_cpu_leg_all(nsteps, warmup, nsample, nproc=None):
+    """The same bounded sample on every host core: nproc independent 1-thread oracle processes
+    at once (the block iterations of different samples are independent problems); returns the
+    legs of all of them."""
+    nproc = nproc or os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", "--steps", str(nsteps), "--warmup", str(warmup),
+           "--sample", str(nsample)]
+    procs = [subprocess.Popen(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+             for _ in range(nproc)]
+    legs = []
+    for p in procs:
+        out, err = p.communicate(timeout=1800)
+        if p.returncode != 0:
+            raise RuntimeError("cpu leg failed: " + err[-2000:])
+        legs.append(json.loads(out.strip().splitlines()[-1]))
+    return legs
+
+
+def cpu_baseline_obj(leg, legs_all=None):
     t = sum(leg["times"]) / len(leg["times"])
-    return {"value": leg["nsample"] * leg["N"] ** 3 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one block iteration (CholQR, H psi, Rayleigh-Ritz, SD update) of %d of the 128 states of "
-                      "the %s cell, FP64 numpy oracle, 1 thread; mean of %d steps" % (
-                          leg["nsample"], WORKLOAD, len(leg["times"]))}
+    one = {"value": leg["nsample"] * leg["N"] ** 3 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "one block iteration (CholQR, H psi, Rayleigh-Ritz, SD update) of %d of the 128 states of "
+                     "the %s cell, FP64 numpy oracle, 1 thread; mean of %d steps" % (
+                         leg["nsample"], WORKLOAD, len(leg["times"]))}
+    if not legs_all:
+        return one
+    value = sum(l["nsample"] * l["N"] ** 3 / (sum(l["times"]) / len(l["times"])) for l in legs_all)
+    return {"value": value, "unit": UNIT, "cores": len(legs_all), "kind": "oracle",
+            "sample": "%d concurrent 1-thread oracle processes (one per host core, nproc = %d), each one block "
+                      "iteration of %d of the 128 states of the %s cell per step; throughputs summed" % (
+                          len(legs_all), os.cpu_count() or 1, leg["nsample"], WORKLOAD),
+            "one_core": one}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -198,9 +226,26 @@ def stage_model(name, geo, pk, fp32_tflops):
     return None
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from one ncu capture
-# of the current kernels on the gs96 cell
-NCU_TRAFFIC_GS96 = {"plane": 287898368 + 236069376, "zinv": 118125312 + 221490432, "zfwd": 400642304 + 96463616}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch on the gs96 cell, from
+# one ncu capture, with the hash of the kernel sources it was taken on: the bench reports the
+# figure only while the sources are unchanged (otherwise traffic is null until re-captured).
+NCU_TRAFFIC_GS96 = {"sources": "", "bytes": {}}
+KERNEL_SOURCES = ("paper_2106_03872_gb300/csrc/fused.cu", "paper_2106_03872_gb300/csrc/fft_device.cuh")
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(name):
+    if NCU_TRAFFIC_GS96["sources"] != kernel_sources_hash():
+        return None
+    return NCU_TRAFFIC_GS96["bytes"].get(name)
 
 
 # Stages that run as single-CTA kernels on the side stream, concurrently with the main stream's
@@ -226,15 +271,60 @@ def _rate(name, ms, count, geo, pk, peak_scale=1.0):
     return out
 
 
+# FP32 CUDA-core rate measured by an FMA-chain probe over all 152 SMs (the derived 80.5 TFLOP/s
+# assumes every lane issues an FMA every cycle at the maximum clock)
+FP32_PROBE_TFLOPS = 69.5
+HPSI_STAGES = ("plane", "zinv", "zfwd", "proj_gemm")
+
+
+def hpsi_algorithmic_bytes(geo):
+    """Algorithmic bytes of one H psi of the block: packed psi in and packed H psi out (complex64,
+    2 |S| 8 B per state) plus the potential (N^3 4 B per call)."""
+    return 2 * geo["nG"] * 8 * geo["nstates"] + geo["N"] ** 3 * 4
+
+
+def hpsi_fft_flops(geo):
+    """Nominal FFT flops of one H psi of the block: two full 3D FFTs per state at 5 n log2 n per
+    length-n transform (5 N^3 log2(N^3) each), however much of the grid the pruned kernels skip."""
+    import math
+    N = geo["N"]
+    return geo["nstates"] * 2 * 5.0 * N ** 3 * math.log2(N ** 3)
+
+
 def roofline(entries, geo, pk, steps):
-    """The dominant kernel: the main-stream stage with the most device time.  Returns it with
-    its roofline, plus the side-stream single-SM stages rated against one SM's peak."""
+    """The dominant kernel: the main-stream stage with the most device time.  A stage of the H psi
+    pipeline is rated against HBM on the algorithmic bytes of the whole H psi it serves (one launch
+    processes the block's states), with its share of the nominal FFT flops against the measured
+    FP32 rate beside it; other stages by their own model.  Returns it, its name, and the
+    side-stream single-SM stages rated against one SM's share of the peak."""
     leaf = {k: v for k, v in entries.items() if k != "apply_h" and k not in SIDE_STREAM}
     if not leaf:
         return None, None, []
     name = max(leaf, key=lambda k: leaf[k][0])
-    out = _rate(name, leaf[name][0], leaf[name][1], geo, pk)
-    out["traffic"] = NCU_TRAFFIC_GS96.get(name) if geo.get("N") == 96 else None
+    ms, count = leaf[name]
+    launch_s = ms / max(count, 1) * 1e-3
+    if name in HPSI_STAGES:
+        nbytes = hpsi_algorithmic_bytes(geo)
+        achieved = nbytes / launch_s / 1e9
+        # x and y passes of both 3D FFTs for the plane kernel (2/3 of the FFT flops), z passes
+        # (1/3) for zinv + zfwd together (1/6 each); the projections carry none
+        share = {"plane": 2.0 / 3.0, "zinv": 1.0 / 6.0, "zfwd": 1.0 / 6.0}.get(name, 0.0)
+        flops = share * hpsi_fft_flops(geo)
+        out = {"kernel": name, "launch_ms": launch_s * 1e3, "launches": count, "bound": "hbm",
+               "achieved": achieved, "peak": pk["hbm"], "unit": "GB/s", "frac": achieved / pk["hbm"],
+               "peak_src": pk["src"], "algorithmic_bytes_per_launch": nbytes,
+               "basis": "algorithmic bytes of one H psi of the %d-state block (packed psi in, packed H psi "
+                        "out, complex64, plus V) / this kernel's launch time" % geo["nstates"],
+               "traffic": measured_traffic(name),
+               "alu": {"flops_per_launch": flops, "achieved": flops / launch_s / 1e12 if flops else None,
+                       "peak": FP32_PROBE_TFLOPS, "unit": "TFLOP/s",
+                       "frac": flops / launch_s / 1e12 / FP32_PROBE_TFLOPS if flops else None,
+                       "peak_src": "measured FP32 FMA probe",
+                       "basis": "this kernel's share of the nominal FFT flops of H psi "
+                                "(2 x 5 N^3 log2 N^3 per state)"}}
+    else:
+        out = _rate(name, ms, count, geo, pk)
+        out["traffic"] = None
     side = [dict(_rate(k, entries[k][0], entries[k][1], geo, pk, 1.0 / 152), peak_note="one SM of 152")
             for k in SIDE_STREAM if k in entries and stage_model(k, geo, pk, None) is not None]
     return out, name, side
@@ -255,9 +345,10 @@ def main_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and not args.no_cpu:
         cpu = run_cpu_leg(args.cpu_steps, 1, CPU_SAMPLE_STATES)     # before any CUDA work
+        cpu_all = run_cpu_leg_all(args.cpu_steps, 1, CPU_SAMPLE_STATES)
 
     torch.cuda.set_device(local)
     from paper_2106_03872_gb300 import inputs, ks
@@ -343,25 +434,34 @@ def main_gpu(args):
                  "hbm_frac_algorithmic": h_bytes / (h_ms * 1e-3) / 1e9 / pk["hbm"],
                  "stages_ms_per_call": {k: v[0] / args.steps for k, v in h_entries.items() if v[0] > 0}}
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step copies the states in
+    # from pinned host memory, runs one block iteration and copies the updated states (the
+    # iteration's result) and the Ritz values back
     pinned = torch.empty((ns, g.nG), dtype=torch.complex128, pin_memory=True)
     pinned.numpy()[:] = c0
     pin_np = pinned.numpy()
+    pinned_out = torch.empty((ns, g.nG), dtype=torch.complex128, pin_memory=True)
+    out_np = pinned_out.numpy()
     e2e_times = []
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g.set_states(pin_np)
         eig = g.block_iteration(1, stream)
+        g.get_states(out=out_np)
         t1 = time.perf_counter()
         if i >= args.warmup:
             e2e_times.append(t1 - t0)
     e2e_ms = max_over_ranks(1e3 * statistics.mean(e2e_times), dist, "cuda")
-    e2e = {"value": replica_throughput(world, ns * N ** 3, e2e_ms), "unit": UNIT,
-           "h2d_bytes_per_step": ns * g.nG * 16, "d2h_bytes_per_step": ns * 8,
-           "note": "set_states (pinned complex128 host -> device) + one block iteration + Ritz values to host"}
-    assert np.all(np.isfinite(eig))
-    g.close()
+    e2e = {"value": replica_throughput(world, ns * N ** 3, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": ns * g.nG * 16, "d2h_bytes_per_step": ns * g.nG * 16 + ns * 8,
+           "note": "ks_set_states (pinned complex128 host -> device) + one block iteration + ks_get_states "
+                   "(updated states, device -> pinned complex128 host) + Ritz values to host"}
+    assert np.all(np.isfinite(eig)) and np.all(np.isfinite(out_np[0]))
+
+    # ---- the 24^3 parity cell (8 states, FP64 and mixed): microseconds per H psi call through the
+    # C ABI, device buffers (stream-ordered, timed on the device) and host buffers (wall clock)
+    small = small_cell_timing(ks, inputs, stream, args.steps)
 
     # ---- all-FP64 GPU path, same workload
     fp64 = None
@@ -465,12 +565,44 @@ def main_gpu(args):
                    "l2": "flushed (256 MB device write) before the timed call of K steps; one step's working set "
                          "(psi, H psi, H^2 psi: 354 MB) exceeds the 126 MB L2"},
         "roofline": rl, "side_stream_roofline": rl_side,
-        "cpu_baseline": cpu_baseline_obj(cpu) if cpu else None, "e2e": e2e,
+        "cpu_baseline": cpu_baseline_obj(cpu, cpu_all) if cpu else None, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk.summary(), "hpsi_only": hpsi_only, "fp64_gpu": fp64, "td": td,
+        "small_cell": small,
         "scf": scf, "teter": teter, "forces": forces, "ehrenfest": ehrenfest, "serve": serve,
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in entries.items() if v[0] > 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def small_cell_timing(ks, inputs, stream, nsteps):
+    import numpy as np
+    import torch
+    cell = inputs.cell("small")
+    out = {"workload": "small: L=10, N=24, |S|=4,337, 8 states, 4 atoms, FP64 and mixed H psi"}
+    for prec, cdt in (("fp64", torch.complex128), ("bf16x3", torch.complex64)):
+        g = ks.Grid(cell, prec=prec)
+        c = inputs.random_coeffs(cell["seed"], cell["nstates"], g.nG)
+        psi = torch.from_numpy(c).to("cuda", cdt)
+        h = torch.empty_like(psi)
+        reps = 200
+        for _ in range(10):
+            g.apply_h(psi.data_ptr(), h.data_ptr(), cell["nstates"], stream)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            g.apply_h(psi.data_ptr(), h.data_ptr(), cell["nstates"], stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        dev_us = 1e3 * ev0.elapsed_time(ev1) / reps
+        t = []
+        for _ in range(max(5, nsteps)):
+            t0 = time.perf_counter()
+            g.apply_h_host(c)
+            t.append(time.perf_counter() - t0)
+        out[prec] = {"us_per_call_device": dev_us, "us_per_call_host_buffers": 1e6 * statistics.median(t)}
+        g.close()
+    return out
 
 
 def serve_bench(ks, inputs, nreq):

@@ -312,22 +312,29 @@ uint64_t ks_kernel_launches(void);
 /* ---------------------------------------------------------------------------------- */
 
 /* out[i][j] = sum_g conj(a[i][g]) b[j][g] for i < m, j < n: the overlap (Gram) matrix of two
- * device blocks, computed with the same split-K kernel as ks_orthonormalize, for callers that
- * cannot allocate device memory: code whose device memory is all handed to its own pool
- * allocator, or latency-critical loops that cannot take the device synchronisation a
- * cudaMalloc/cudaFree may imply.  It needs no ks_grid and calls no cudaMalloc, cudaFree or
- * allocating library routine.
+ * device blocks, for callers that cannot allocate device memory: code whose device memory is
+ * all handed to its own pool allocator, or latency-critical loops that cannot take the device
+ * synchronisation a cudaMalloc/cudaFree may imply.  It needs no ks_grid and calls no cudaMalloc,
+ * cudaFree or allocating library routine.
  *   a_dev [m][nG], b_dev [n][nG]: complex device arrays, double2 if fp64 != 0, else float2.
  *   out_dev [m][n]: complex128 device array written by the call (row-major).
+ * Arithmetic: a split-K CUDA-core GEMM (the FP64 path's Gram kernel).  fp64 != 0: FP64
+ * throughout, as ks_orthonormalize on a KS_FP64 handle.  fp64 == 0: FP32 products accumulated
+ * in FP32 within each K range, the ranges summed in FP64; this is not the split-BF16
+ * tensor-core kernel a mixed-precision handle's ks_orthonormalize uses, so the two agree to
+ * FP32 rounding, not bit for bit.
  * The split-K partial sums live in a fixed 4 MiB device array inside the library (262,144
  * complex128 values), which every GPU that loads the library keeps until the process exits;
- * m * n above 262,144 is rejected with KS_ERR_ARG before any device work.  The first call on a
- * device looks the array's device address up (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the array and it keeps
- * the last call's contents; nothing in it has to start at zero (every partial is written
- * before it is read), but calls that overlap on the GPU (different streams, or different host
- * threads on one device) race on it and must be serialised by the caller.  Asynchronous on
- * stream. */
+ * m * n above 262,144 is rejected with KS_ERR_ARG before any device work.  The array's device
+ * address is looked up (cudaGetSymbolAddress) on the first call in each CUDA context, with
+ * that context's device current; with lazy module loading that first call (or the library's
+ * first kernel launch on the device) may also load the module and reserve the 4 MiB, with the
+ * synchronisation that implies.  So make one call per device during set-up, outside
+ * latency-critical regions and before any stream capture (and again after the context is
+ * reset).  All calls share the array and it keeps the last call's contents; nothing in it has
+ * to start at zero (every partial is written before it is read), but calls that overlap on the
+ * GPU (different streams, or different host threads on one device) race on it and must be
+ * serialised by the caller.  Asynchronous on stream. */
 ks_status ks_overlap_noalloc(const void* a_dev, const void* b_dev, int m, int n, int nG, int fp64, void* out_dev,
                              void* stream);
 

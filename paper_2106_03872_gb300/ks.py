@@ -208,8 +208,12 @@ class Grid:
         c = np.ascontiguousarray(np.asarray(c, np.complex128).reshape(self.nstates, self.nG))
         check(load().ks_set_states(self.h, c.ctypes.data_as(ct.POINTER(ct.c_double))))
 
-    def get_states(self):
-        c = np.zeros((self.nstates, self.nG), np.complex128)
+    def get_states(self, out=None):
+        """The resident states as [nstates][nG] complex128; out (optional, e.g. a pinned
+        buffer) receives them in place."""
+        c = np.zeros((self.nstates, self.nG), np.complex128) if out is None else out
+        if c.dtype != np.complex128 or c.shape != (self.nstates, self.nG) or not c.flags.c_contiguous:
+            raise ValueError("out must be a contiguous [nstates][nG] complex128 array")
         check(load().ks_get_states(self.h, c.ctypes.data_as(ct.POINTER(ct.c_double))))
         return c
 
