@@ -32,6 +32,7 @@ UNIT = "state·gridpts/s"
 WORKLOAD = "gs96"
 CPU_SAMPLE_STATES = 4
 BASE_SERVE_SEED = 20210612
+SERVE_WORKERS = 8
 
 
 def peaks():
@@ -304,21 +305,27 @@ def roofline(entries, geo, pk, steps):
     ms, count = leaf[name]
     launch_s = ms / max(count, 1) * 1e-3
     if name in HPSI_STAGES:
+        # the H application runs its kernels over batches of states (column buffers resident in
+        # L2): rate the kernel's time per H psi call, its launches of all batches together
+        calls = entries.get("apply_h", (0.0, count))[1]
+        call_s = ms / max(calls, 1) * 1e-3
         nbytes = hpsi_algorithmic_bytes(geo)
-        achieved = nbytes / launch_s / 1e9
+        achieved = nbytes / call_s / 1e9
         # x and y passes of both 3D FFTs for the plane kernel (2/3 of the FFT flops), z passes
         # (1/3) for zinv + zfwd together (1/6 each); the projections carry none
         share = {"plane": 2.0 / 3.0, "zinv": 1.0 / 6.0, "zfwd": 1.0 / 6.0}.get(name, 0.0)
         flops = share * hpsi_fft_flops(geo)
-        out = {"kernel": name, "launch_ms": launch_s * 1e3, "launches": count, "bound": "hbm",
+        out = {"kernel": name, "launch_ms": launch_s * 1e3, "launches": count, "ms_per_hpsi": call_s * 1e3,
+               "hpsi_calls": calls, "bound": "hbm",
                "achieved": achieved, "peak": pk["hbm"], "unit": "GB/s", "frac": achieved / pk["hbm"],
-               "peak_src": pk["src"], "algorithmic_bytes_per_launch": nbytes,
+               "peak_src": pk["src"], "algorithmic_bytes_per_hpsi": nbytes,
                "basis": "algorithmic bytes of one H psi of the %d-state block (packed psi in, packed H psi "
-                        "out, complex64, plus V) / this kernel's launch time" % geo["nstates"],
+                        "out, complex64, plus V) / this kernel's device time per H psi (its launches over "
+                        "the L2-sized state batches together)" % geo["nstates"],
                "traffic": measured_traffic(name),
-               "alu": {"flops_per_launch": flops, "achieved": flops / launch_s / 1e12 if flops else None,
+               "alu": {"flops_per_hpsi": flops, "achieved": flops / call_s / 1e12 if flops else None,
                        "peak": FP32_PROBE_TFLOPS, "unit": "TFLOP/s",
-                       "frac": flops / launch_s / 1e12 / FP32_PROBE_TFLOPS if flops else None,
+                       "frac": flops / call_s / 1e12 / FP32_PROBE_TFLOPS if flops else None,
                        "peak_src": "measured FP32 FMA probe",
                        "basis": "this kernel's share of the nominal FFT flops of H psi "
                                 "(2 x 5 N^3 log2 N^3 per state)"}}
@@ -463,6 +470,22 @@ def main_gpu(args):
     # C ABI, device buffers (stream-ordered, timed on the device) and host buffers (wall clock)
     small = small_cell_timing(ks, inputs, stream, args.steps)
 
+    # ---- the precision plan with FP64 Cholesky and FP64 Rayleigh-Ritz inside the timed iteration
+    # (KS_OPT_FP64_SUBSPACE): same workload, the states and their GEMMs mixed
+    fp64_sub = None
+    if not args.no_fp64:
+        gf = ks.Grid(cell, prec="bf16x3")
+        gf.set_option(ks.KS_OPT_FP64_SUBSPACE, 1)
+        gf.set_states(c0)
+        gf.orthonormalize()
+        tf_, _, ef_ = timed_steps(gf, 3, 1, lambda: gf.block_iteration(1, stream), profile=True)
+        msf = statistics.mean(tf_)
+        fp64_sub = {"workload": "gs96 block iteration, mixed states and GEMMs with the Cholesky factor, subspace "
+                                "products and Rayleigh-Ritz eigensolver in FP64 (one-CTA FP64 kernels)",
+                    "value": ns * N ** 3 / (msf * 1e-3), "ms_per_step": msf,
+                    "stages_ms_per_step": {k: v[0] / len(tf_) for k, v in ef_.items() if v[0] > 0}}
+        gf.close()
+
     # ---- all-FP64 GPU path, same workload
     fp64 = None
     if not args.no_fp64:
@@ -550,7 +573,7 @@ def main_gpu(args):
                      "stages_ms_per_call": {k: v[0] / len(tE) for k, v in eE.items() if v[0] > 0}}
         ge.close()
 
-    serve = None if args.no_serve else serve_bench(ks, inputs, args.serve_requests)
+    serve = None if args.no_serve else serve_bench(ks, inputs, args.serve_requests, args.serve_load_requests)
 
     if rank != 0:
         return
@@ -566,8 +589,8 @@ def main_gpu(args):
                          "(psi, H psi, H^2 psi: 354 MB) exceeds the 126 MB L2"},
         "roofline": rl, "side_stream_roofline": rl_side,
         "cpu_baseline": cpu_baseline_obj(cpu, cpu_all) if cpu else None, "e2e": e2e,
-        "gpu_launches": launches, "clocks": clk.summary(), "hpsi_only": hpsi_only, "fp64_gpu": fp64, "td": td,
-        "small_cell": small,
+        "gpu_launches": launches, "clocks": clk.summary(), "hpsi_only": hpsi_only, "fp64_gpu": fp64, "fp64_subspace": fp64_sub, "td": td,
+        "small_cell": small, "autotune": ks.autotune_report(),
         "scf": scf, "teter": teter, "forces": forces, "ehrenfest": ehrenfest, "serve": serve,
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in entries.items() if v[0] > 0},
     }
@@ -605,22 +628,23 @@ def small_cell_timing(ks, inputs, stream, nsteps):
     return out
 
 
-def serve_bench(ks, inputs, nreq):
-    """Continuous-batching server: saturated throughput, then Poisson arrivals at 50/80/95 %
-    of it with p50/p99 latency (submit to finish)."""
+def serve_bench(ks, inputs, nreq, nreq_load):
+    """Continuous-batching server on the serving workload's shape (grids {32,48,64,96}^3 at
+    h = 0.3125 bohr, 8-256 states, 4-64 atoms, half 10 block iterations and half 50 ETRS steps with
+    Hartree + Slater): saturated throughput over nreq requests submitted at once, then Poisson
+    arrivals at 50/80/95 % of that rate over the first nreq_load of them, with p50/p99 latency
+    (submit to finish)."""
     import numpy as np
 
-    reqs = inputs.serve_requests(BASE_SERVE_SEED, nreq, state_range=(8, 64))
-    for r in reqs:
-        r["count"] = 10 if r["kind"] == 0 else 20
+    reqs = inputs.serve_requests(BASE_SERVE_SEED, nreq)
 
-    def run(rate):
-        srv = ks.Server(0)
+    def run(rate, sub):
+        srv = ks.Server(0, workers=SERVE_WORKERS)
         t0 = time.perf_counter()
         tickets = []
         arrival = 0.0
         rng = np.random.default_rng(BASE_SERVE_SEED + 1)
-        for r in reqs:
+        for r in sub:
             if rate:
                 arrival += rng.exponential(1.0 / rate)
                 delay = t0 + arrival - time.perf_counter()
@@ -640,19 +664,24 @@ def serve_bench(ks, inputs, nreq):
         srv.close()
         return span, np.array(lat)
 
-    span, lat = run(None)
+    span, lat = run(None, reqs)
     sat = nreq / span
     loads = []
+    sub = reqs[:nreq_load]
     for frac in (0.5, 0.8, 0.95):
-        sp, la = run(frac * sat)
-        loads.append({"load": frac, "rate_req_per_s": frac * sat, "p50_s": float(np.percentile(la, 50)),
-                      "p99_s": float(np.percentile(la, 99)), "throughput_req_per_s": nreq / sp})
+        sp, la = run(frac * sat, sub)
+        loads.append({"load": frac, "rate_req_per_s": frac * sat, "requests": len(sub),
+                      "p50_s": float(np.percentile(la, 50)), "p99_s": float(np.percentile(la, 99)),
+                      "throughput_req_per_s": len(sub) / sp})
     gp = sum(r["nstates"] * r["N"] ** 3 * r["count"] for r in reqs)
-    return {"requests": nreq, "saturated_req_per_s": sat, "saturated_state_gridpts_steps_per_s": gp / span,
+    return {"requests": nreq, "workers": SERVE_WORKERS, "saturated_req_per_s": sat,
+            "saturated_state_gridpts_steps_per_s": gp / span, "saturated_s": span,
             "saturated_p50_s": float(np.percentile(lat, 50)), "saturated_p99_s": float(np.percentile(lat, 99)),
             "loads": loads,
-            "workload": "seeded requests: N in {32,48,64,96} (L = 0.3125 N), 8-64 states, 4-64 atoms, "
-                        "half 10 block iterations, half 20 ETRS steps (dt 0.05, Hartree + Slater), mixed precision"}
+            "workload": "seeded requests of the serving workload: N in {32,48,64,96} (L = 0.3125 N), 8-256 "
+                        "states, 4-64 atoms at uniform positions, half 10 block iterations and half 50 ETRS "
+                        "steps (dt 0.05, Hartree + Slater), mixed precision; %d requests at saturation, the "
+                        "first %d at each Poisson load" % (nreq, nreq_load)}
 
 
 def main_reference(args):
@@ -685,7 +714,8 @@ def main():
     ap.add_argument("--no-td", action="store_true")
     ap.add_argument("--no-scf", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-load-requests", type=int, default=120)
     args = ap.parse_args()
     if args.cpu_leg:
         print(json.dumps(cpu_leg(args.steps, args.warmup, args.sample)))

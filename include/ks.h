@@ -45,14 +45,15 @@ typedef enum {
   KS_ERR_STATE = 8        /* call not valid in the handle's current state              */
 } ks_status;
 
-/* Internal arithmetic of a handle.
+/* Internal arithmetic of a handle (any other value: KS_ERR_ARG).
  *   KS_FP64          complex128 states, FP64 FFTs, FP64 everything (correctness anchor).
- *   KS_MIXED_BF16X3  complex64 states and FFTs; projector and Gram/rotation GEMMs with
- *                    each FP32 operand split into two bf16 terms (3 products), FP32
- *                    accumulation; Cholesky, Rayleigh-Ritz eigenvalues, norms and
- *                    energies in FP64.
- *   KS_MIXED_TF32    as above with the GEMM operands split into two tf32 terms. */
-typedef enum { KS_FP64 = 0, KS_MIXED_BF16X3 = 1, KS_MIXED_TF32 = 2 } ks_precision;
+ *   KS_MIXED_BF16X3  complex64 states and FFTs; projector and Gram/rotation GEMMs on the
+ *                    tensor cores with each FP32 operand split into two bf16 terms (3
+ *                    products), FP32 accumulation; the Cholesky factor and the subspace
+ *                    eigensolver in FP32 with FP64 refinement (FP64 Rayleigh quotients for the
+ *                    reported eigenvalues; FP64 throughout with KS_OPT_FP64_SUBSPACE); norms
+ *                    and energies in FP64. */
+typedef enum { KS_FP64 = 0, KS_MIXED_BF16X3 = 1 } ks_precision;
 
 /* Cell description (all host memory, copied by ks_grid_create).
  *   pos      [natoms][3] atom positions (bohr), any real values (wrapped periodically).
@@ -77,6 +78,15 @@ typedef struct {
   ks_precision prec;
 } ks_cell_desc;
 
+/* Options of a handle, set with ks_set_option.
+ *   KS_OPT_FP64_SUBSPACE (value 0 or 1, default 0): on a mixed-precision handle, 1 factors the
+ *     Gram matrix (Cholesky of S in ks_orthonormalize, ks_block_iteration, ks_scf) and
+ *     diagonalises the subspace matrix (Rayleigh-Ritz in ks_rayleigh_ritz, ks_block_iteration)
+ *     in FP64 on the GPU, with FP64 subspace products, as the FP64 path does; the states, their
+ *     FFTs and GEMMs stay in the handle's precision.  0 takes an FP32 factor and eigensolver
+ *     (with FP64 Rayleigh quotients for the reported eigenvalues).  No effect on KS_FP64. */
+enum { KS_OPT_FP64_SUBSPACE = 1 };
+
 /* Number of plane waves in the cutoff sphere for (L, N, ecut).  Host only: needs no GPU.
  * KS_ERR_ARG if N is not an even 2^a 3^b in [8, 128] or the sphere leaves the grid's
  * Nyquist box. */
@@ -96,6 +106,11 @@ ks_status ks_grid_device_bytes(ks_grid g, size_t* bytes);
 
 /* V_loc on the grid, [N^3] doubles in grid order (host). */
 ks_status ks_get_vloc(ks_grid g, double* v_host);
+
+/* Sets a handle option (the KS_OPT_* values above; the paper has no counterpart: its code runs
+ * in FP64 throughout).  KS_ERR_ARG for an unknown option or value.  Takes effect with the next
+ * call on the handle. */
+ks_status ks_set_option(ks_grid g, int option, int value);
 
 /* Copy host states in ([nstates][nG] complex128, converted to the handle's precision)
  * or out (converted back to complex128).  Synchronous. */
@@ -256,9 +271,16 @@ ks_status ks_dipole(ks_grid g, double* d_out, void* stream);
 /* Serving: continuous batching of independent calculations on one GPU.               */
 /* ---------------------------------------------------------------------------------- */
 
-/* A server owns a scheduler thread and admits requests while the device memory they
- * need fits in mem_budget_bytes (0: 80% of the free device memory at creation). */
+/* A server owns worker threads and admits requests while the device memory they need fits in
+ * mem_budget_bytes (0: 80% of the free device memory at creation).  The requests' device memory
+ * comes from a slab pool the server keeps until ks_serve_destroy, so admitting and retiring
+ * requests does not synchronise the device.  Real-time requests (kind 1) of mixed precision on
+ * one grid geometry (same L, N, ecut) are stepped together, up to eight at a time, each H
+ * application of their ETRS step one packed launch over all their states; a request's results
+ * are the same alone and in such a group.  ks_serve_create starts 4 workers. */
 ks_status ks_serve_create(size_t mem_budget_bytes, ks_server* out);
+/* Same with `workers` worker threads (1..64; 0: the default of 4). */
+ks_status ks_serve_create_ex(size_t mem_budget_bytes, int workers, ks_server* out);
 /* Stops the scheduler after the running requests finish; pending ones are dropped. */
 ks_status ks_serve_destroy(ks_server s);
 
@@ -303,6 +325,21 @@ ks_status ks_profile_read(ks_grid g, int idx, char* name, int name_len, double* 
  * iteration appear beside the main stream's, so their overlap can be read off.  Waits for
  * pending events.  KS_ERR_ARG once idx passes the last span. */
 ks_status ks_profile_span(ks_grid g, int idx, char* name, int name_len, double* start_ms, double* end_ms);
+
+/* The status a call returns for the error word of the tensor-core GEMM kernels, which every
+ * handle reads after its calls: flag 0 gives KS_OK; a nonzero flag (a bounded mbarrier wait in a
+ * kernel expired after about 2 s; the kernel recorded it and returned) gives KS_ERR_CUDA with a
+ * message in ks_last_error.  Host only: lets the expiry path be checked without a GPU. */
+ks_status ks_tc_status_check(int flag);
+
+/* The launch-shape autotuner's decisions so far, as JSON: the first H application or density of
+ * each (grid, bucket of state counts) times the candidate plane kernels (team-owned line
+ * transforms and CTA-wide Stockham stages) on the live data and keeps the faster one for the
+ * process; the report lists, per decision, each candidate's best time in ms and the choice:
+ *   [{"key": "plane N=96 states<=128", "ms": {"team": 0.69, "cta": 0.72}, "choice": "team"}, ...]
+ * buf (may be NULL) receives at most cap bytes including the terminating NUL; len (may be NULL)
+ * the size the whole report needs.  (The paper has no counterpart.) */
+ks_status ks_autotune_report(char* buf, size_t cap, size_t* len);
 
 /* Number of kernels this library has launched in this process so far. */
 uint64_t ks_kernel_launches(void);

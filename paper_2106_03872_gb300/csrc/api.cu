@@ -1,11 +1,13 @@
 // The C ABI (include/ks.h): argument checks, handle lifetime, and translation of internal
 // errors into ks_status.  No exception crosses this boundary.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <memory>
 
 #include "engine.h"
+#include "tuner.h"
 
 namespace ks {
 const char* last_error_cstr();
@@ -219,6 +221,29 @@ ks_status ks_dipole(ks_grid g, double* d_out, void* stream) {
   return guarded([&] {
     need(g != nullptr && d_out != nullptr, "grid or d_out is NULL");
     g->eng->dipole(d_out, as_stream(stream));
+  });
+}
+
+ks_status ks_autotune_report(char* buf, size_t cap, size_t* len) {
+  return guarded([&] {
+    const std::string j = ks::tune_log_json();
+    if (len) *len = j.size() + 1;
+    if (buf && cap > 0) {
+      const size_t k = std::min(cap - 1, j.size());
+      std::memcpy(buf, j.data(), k);
+      buf[k] = 0;
+    }
+  });
+}
+
+ks_status ks_tc_status_check(int flag) {
+  return guarded([&] { ks::raise_tc_status(flag); });
+}
+
+ks_status ks_set_option(ks_grid g, int option, int value) {
+  return guarded([&] {
+    need(g != nullptr, "grid is NULL");
+    g->eng->set_option(option, value);
   });
 }
 

@@ -13,15 +13,97 @@
 
 namespace ks {
 
+DevicePool::~DevicePool() {
+  for (auto& sl : slabs_) cudaFree(sl.base);
+}
+
+void* DevicePool::alloc(size_t bytes) {
+  bytes = std::max<size_t>(256, (bytes + 255) / 256 * 256);
+  std::lock_guard<std::mutex> lk(mu_);
+  for (int si = 0; si < (int)slabs_.size(); ++si) {
+    Slab& sl = slabs_[si];
+    for (auto it = sl.free_blocks.begin(); it != sl.free_blocks.end(); ++it) {
+      if (it->second < bytes) continue;
+      const size_t off = it->first, size = it->second;
+      sl.free_blocks.erase(it);
+      if (size > bytes) sl.free_blocks[off + bytes] = size - bytes;
+      char* p = sl.base + off;
+      used_[p] = {si, bytes};
+      in_use_ += bytes;
+      return p;
+    }
+  }
+  // grow: a new slab of at least slab_bytes_
+  Slab sl;
+  sl.size = std::max(slab_bytes_, bytes);
+  void* base = nullptr;
+  const cudaError_t e = cudaMalloc(&base, sl.size);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(KS_ERR_NOMEM, "device pool: cudaMalloc of a %zu-byte slab failed (%s)", sl.size, cudaGetErrorString(e));
+  }
+  sl.base = static_cast<char*>(base);
+  if (sl.size > bytes) sl.free_blocks[bytes] = sl.size - bytes;
+  slabs_.push_back(std::move(sl));
+  reserved_ += slabs_.back().size;
+  char* p = slabs_.back().base;
+  used_[p] = {(int)slabs_.size() - 1, bytes};
+  in_use_ += bytes;
+  return p;
+}
+
+void DevicePool::free(void* vp) {
+  if (!vp) return;
+  std::lock_guard<std::mutex> lk(mu_);
+  auto it = used_.find(static_cast<char*>(vp));
+  if (it == used_.end()) fail(KS_ERR_STATE, "internal: device pool release of an unknown block");
+  Slab& sl = slabs_[it->second.first];
+  size_t off = static_cast<size_t>(it->first - sl.base), size = it->second.second;
+  in_use_ -= size;
+  used_.erase(it);
+  // coalesce with the free neighbours inside the slab
+  auto next = sl.free_blocks.lower_bound(off);
+  if (next != sl.free_blocks.end() && next->first == off + size) {
+    size += next->second;
+    next = sl.free_blocks.erase(next);
+  }
+  if (next != sl.free_blocks.begin()) {
+    auto prev = std::prev(next);
+    if (prev->first + prev->second == off) {
+      prev->second += size;
+      return;
+    }
+  }
+  sl.free_blocks[off] = size;
+}
+
+size_t DevicePool::reserved() const {
+  std::lock_guard<std::mutex> lk(mu_);
+  return reserved_;
+}
+
+size_t DevicePool::in_use() const {
+  std::lock_guard<std::mutex> lk(mu_);
+  return in_use_;
+}
+
 DeviceArena::~DeviceArena() {
-  for (void* p : ptrs_) cudaFree(p);
+  for (void* p : ptrs_) {
+    if (pool_)
+      pool_->free(p);
+    else
+      cudaFree(p);
+  }
 }
 
 void* DeviceArena::alloc(size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) / 256 * 256;
-  KS_CUDA(cudaMalloc(&p, bytes));
+  if (pool_)
+    p = pool_->alloc(bytes);
+  else
+    KS_CUDA(cudaMalloc(&p, bytes));
   ptrs_.push_back(p);
   sizes_.push_back(bytes);
   total_ += bytes;
@@ -32,7 +114,10 @@ void DeviceArena::release(const void* p) {
   if (!p) return;
   for (size_t i = 0; i < ptrs_.size(); ++i)
     if (ptrs_[i] == p) {
-      KS_CUDA(cudaFree(ptrs_[i]));
+      if (pool_)
+        pool_->free(ptrs_[i]);
+      else
+        KS_CUDA(cudaFree(ptrs_[i]));
       total_ -= sizes_[i];
       ptrs_.erase(ptrs_.begin() + i);
       sizes_.erase(sizes_.begin() + i);
@@ -128,7 +213,8 @@ template <typename T> class Engine final : public EngineBase {
  public:
   using C = cplx<T>;
 
-  explicit Engine(const ks_cell_desc& d) : prec_(d.prec), ns_(d.nstates) {
+  explicit Engine(const ks_cell_desc& d, DevicePool* pool = nullptr) : prec_(d.prec), ns_(d.nstates) {
+    arena_.set_pool(pool);
     build_geometry(d, g_);
     const int N = g_.N, nG = g_.nG;
     const size_t N3 = (size_t)N * N * N;
@@ -270,6 +356,36 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaStreamSynchronize(s));
   }
 
+  // Pieces of td_steps for a lockstep group (td_step_engines): the potential reset before the
+  // step, the asynchronous read of slot 0's norm and energy, and the buffer roles after it.
+  bool groupable_with(const Engine& o) const {
+    return fused_ && o.fused_ && fused_same_geometry(fused_.get(), o.fused_.get());
+  }
+  void td_prepare(int hartree_xc, cudaStream_t s) {
+    hpsi_valid_ = false;
+    if (!hartree_xc)
+      KS_CUDA(cudaMemcpyAsync(vtot_, vloc_, (size_t)g_.N * g_.N * g_.N * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  }
+  void td_read_slot0(double* nrm, double* e, cudaStream_t s) {
+    KS_CUDA(cudaMemcpyAsync(nrm, norms_dev_, sizeof(double), cudaMemcpyDeviceToHost, s));
+    KS_CUDA(cudaMemcpyAsync(e, energies_dev_, sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  void td_finish(cudaStream_t s) {
+    check_tc_status(s);
+    if (hpsi_ == psi_) hpsi_ = spare(psi_, nullptr);
+  }
+
+  void set_option(int option, int value) override {
+    if (option == KS_OPT_FP64_SUBSPACE) {
+      if (value != 0 && value != 1) fail(KS_ERR_ARG, "KS_OPT_FP64_SUBSPACE takes 0 or 1, got %d", value);
+      if (sizeof(T) == 8) return;                                     // the FP64 path has it always
+      fp64_subspace_ = value != 0;
+      hpsi_valid_ = false;
+      return;
+    }
+    fail(KS_ERR_ARG, "unknown option %d", option);
+  }
+
   void randomize_states(uint64_t seed, cudaStream_t s) override {
     random_states<T>(psi_, (size_t)ns_ * g_.nG, seed, s);
     hpsi_valid_ = false;
@@ -376,7 +492,7 @@ template <typename T> class Engine final : public EngineBase {
   void factor(cudaStream_t st, float2* m32 = nullptr) {
     const int n = ns_;
     ProfScope p(prof, "cholesky", st);
-    if (mixed_cholesky()) {
+    if (mixed_cholesky() && !fp64_subspace_) {
       cholesky_inverse_mixed(mS_, mM_, n, 1e-6, chw_, status_, st, m32, m32 == nullptr);
     } else {
       KS_CUDA(cudaMemcpyAsync(mF_, mS_, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
@@ -429,7 +545,7 @@ template <typename T> class Engine final : public EngineBase {
     }
     {
       ProfScope p(prof, "eigh", s);
-      if (sizeof(T) == 4 && n <= 128)
+      if (sizeof(T) == 4 && n <= 128 && !fp64_subspace_)
         eigh_mixed(mA_, mV_, lam_, eig_, mM_, n, s);
       else
         jacobi_eigh(mA_, mV_, eig_, mM_, n, s);
@@ -470,7 +586,8 @@ template <typename T> class Engine final : public EngineBase {
     // directly on entry to a call whose block changed and every HPSI_REFRESH iterations.
     const int n = ns_;
     const bool mixed = sizeof(T) == 4;
-    const bool frr = fused_rr();
+    const bool frr = fused_rr() && !fp64_subspace_;
+    const bool mixed_sub = mixed && !fp64_subspace_;     // FP32 subspace products and eigensolver
     bool ritz_pending = false;
     for (int it = 0; it < niter; ++it) {
       if (!hpsi_valid_ || hpsi_age_ >= HPSI_REFRESH) {
@@ -512,20 +629,20 @@ template <typename T> class Engine final : public EngineBase {
       } else {
         {
           ProfScope p(prof, "subspace", aux_);
-          small_product(mA_, mM_, n, SP_TRANS_B, mixed, mT_, aux_);   // H_raw M^T
-          small_product(mM_, mT_, n, SP_CONJ_A, mixed, mA_, aux_);    // conj(M) H_raw M^T
+          small_product(mA_, mM_, n, SP_TRANS_B, mixed_sub, mT_, aux_);   // H_raw M^T
+          small_product(mM_, mT_, n, SP_CONJ_A, mixed_sub, mA_, aux_);    // conj(M) H_raw M^T
           hermitize(mA_, n, aux_);
         }
         {
           ProfScope p(prof, "eigh", aux_);
-          if (mixed && n <= 128)
+          if (mixed_sub && n <= 128)
             eigh_mixed(mA_, mV_, lam_, eig_, mT_, n, aux_);
           else
             jacobi_eigh(mA_, mV_, eig_, mT_, n, aux_);
         }
         {
           ProfScope p(prof, "subspace", aux_);
-          small_product(mT_, mM_, n, 0, mixed, mC_, aux_);            // C = Vt M
+          small_product(mT_, mM_, n, 0, mixed_sub, mC_, aux_);        // C = Vt M
           sd_matrix(mC_, eig_, alpha, n, mCat_, aux_);
         }
         KS_CUDA(cudaEventRecord(ev_chol_, aux_));
@@ -910,8 +1027,11 @@ template <typename T> class Engine final : public EngineBase {
     if constexpr (sizeof(T) == 4) {
       if (fused_) fused_->prepare_atoms();
     }
+    // the old lists are released below: wait for this engine's streams (not the whole device, whose
+    // other engines keep running)
     KS_CUDA(cudaStreamSynchronize(s));
-    KS_CUDA(cudaDeviceSynchronize());
+    KS_CUDA(cudaStreamSynchronize(aux_));
+    KS_CUDA(cudaStreamSynchronize(nullptr));
     ProfScope p(prof, "set_positions", s);
     // projector sphere lists (their sizes change as grid points enter and leave the spheres)
     for (const void* q : {(const void*)t_.sph_off, (const void*)t_.sph_idx, (const void*)t_.sph_atom,
@@ -977,63 +1097,127 @@ template <typename T> class Engine final : public EngineBase {
   }
 
  private:
-  // One real-time step of the resident states from t to t + dt (ETRS with shared powers, or
-  // plain Taylor 4).  norms_dev_[slot] and energies_dev_[slot] receive the norm and energy at
-  // t, dipoles_dev_[3 slot] the dipole when `dipole`; `mid` (may be null) runs after the
-  // first half and before H(t+dt) is formed (the ions move there).
-  void td_step_body(double dt, int propagator, int hartree_xc, int slot, bool dipole, const std::function<void()>* mid,
-                    cudaStream_t s) {
-    const int n = ns_, nG = g_.nG;
-    const size_t sn = (size_t)n * nG;
-    // roles: psi, two power buffers, acc_full, acc_half
-    C* others[5];
-    int k = 0;
-    for (int i = 0; i < 6; ++i)
-      if (buf_[i] != psi_) others[k++] = buf_[i];
-    C* wa = others[0];
-    C* wb = others[1];
-    C* acc_full = others[2];
-    C* acc_half = others[3];
-    if (hartree_xc || dipole) density_of(psi_, n, dens_, s);
-    if (dipole) ks::dipole<T>(dens_, g_.N, g_.L, dip_partials_, HXC_BLOCKS, dipoles_dev_ + 3 * slot, s);
-    if (hartree_xc) update_potential(dens_, s);
-    state_dots<T>(psi_, psi_, nG, n, dots_, s);
-    weighted_energy(dots_, occ_, n, nullptr, norms_dev_ + slot, s);
-    // the accumulators start from psi in the first power's update (no copies)
-    const C* w = psi_;
+  // One real-time step from t to t + dt (ETRS with shared powers, or plain Taylor 4) of the
+  // resident states of several engines of one precision in lockstep.  norms_dev_[slot] and
+  // energies_dev_[slot] of each engine receive its norm and energy at t, dipoles_dev_[3 slot] the
+  // dipole when `dipole`; `mid` (one engine only; may be null) runs after the first half and
+  // before H(t+dt) is formed (the ions move there).  Every H application of the step runs as one
+  // packed launch over the engines where the fused path allows it (fused_apply_h_group), so an
+  // engine's results are the same alone and in a group; otherwise engine by engine.
+ public:
+  static void td_step_group(const std::vector<Engine*>& es, double dt, int propagator, int hartree_xc, int slot,
+                            bool dipole, const std::function<void()>* mid, cudaStream_t s) {
+    const size_t ne = es.size();
+    std::vector<C*> wa(ne), wb(ne), acc_full(ne), acc_half(ne), wn(ne);
+    std::vector<const C*> w(ne), base(ne);
+    for (size_t i = 0; i < ne; ++i) {
+      Engine* e = es[i];
+      const int n = e->ns_, nG = e->g_.nG;
+      // roles: psi, two power buffers, acc_full, acc_half
+      C* others[5];
+      int k = 0;
+      for (int q = 0; q < 6; ++q)
+        if (e->buf_[q] != e->psi_) others[k++] = e->buf_[q];
+      wa[i] = others[0];
+      wb[i] = others[1];
+      acc_full[i] = others[2];
+      acc_half[i] = others[3];
+      if (hartree_xc || dipole) e->density_of(e->psi_, n, e->dens_, s);
+      if (dipole) ks::dipole<T>(e->dens_, e->g_.N, e->g_.L, e->dip_partials_, HXC_BLOCKS, e->dipoles_dev_ + 3 * slot, s);
+      if (hartree_xc) e->update_potential(e->dens_, s);
+      state_dots<T>(e->psi_, e->psi_, nG, n, e->dots_, s);
+      weighted_energy(e->dots_, e->occ_, n, nullptr, e->norms_dev_ + slot, s);
+      w[i] = e->psi_;                 // the accumulators start from psi in the first power's update
+    }
     double2 af = make_double2(1, 0), ah = make_double2(1, 0);
     for (int kk = 1; kk <= 4; ++kk) {
-      C* wn = (w == wa) ? wb : wa;
-      apply_h(w, wn, n, s);
-      if (kk == 1) {
-        state_dots<T>(psi_, wn, nG, n, dots_, s);
-        weighted_energy(dots_, occ_, n, hartree_xc ? parts_ : nullptr, energies_dev_ + slot, s);
-      }
       af = cmul_scalar(af, make_double2(0, -dt / kk));
       ah = cmul_scalar(ah, make_double2(0, -0.5 * dt / kk));
-      axpy2<T>(acc_full, af, propagator == 0 ? acc_half : nullptr, ah, wn, kk == 1 ? psi_ : nullptr, sn, s);
-      w = wn;
+      for (size_t i = 0; i < ne; ++i) {
+        wn[i] = (w[i] == wa[i]) ? wb[i] : wa[i];
+        base[i] = kk == 1 ? es[i]->psi_ : nullptr;
+      }
+      // H w and both accumulators in one pass; the last power is not stored (nothing reads it)
+      group_h(es, w, wn, acc_full, af, propagator == 0 ? acc_half : std::vector<C*>(ne, nullptr), ah, base, kk == 4,
+              s);
+      for (size_t i = 0; i < ne; ++i) {
+        Engine* e = es[i];
+        if (kk == 1) {
+          state_dots<T>(e->psi_, wn[i], e->g_.nG, e->ns_, e->dots_, s);
+          weighted_energy(e->dots_, e->occ_, e->ns_, hartree_xc ? e->parts_ : nullptr, e->energies_dev_ + slot, s);
+        }
+        w[i] = wn[i];
+      }
     }
     if (propagator == 1) {
-      psi_ = acc_full;
+      for (size_t i = 0; i < ne; ++i) es[i]->psi_ = acc_full[i];
       return;
     }
     if (mid) (*mid)();
-    if (hartree_xc) {
-      density_of(acc_full, n, dens_, s);
-      update_potential(dens_, s);
+    for (size_t i = 0; i < ne; ++i) {
+      Engine* e = es[i];
+      if (hartree_xc) {
+        e->density_of(acc_full[i], e->ns_, e->dens_, s);
+        e->update_potential(e->dens_, s);
+      }
+      w[i] = acc_half[i];
     }
     // second half: out = acc_half + sum_k (-i dt/2)^k/k! H(t+dt)^k acc_half
-    w = acc_half;
     ah = make_double2(1, 0);
     for (int kk = 1; kk <= 4; ++kk) {
-      C* wn = (w == wa) ? wb : wa;
-      apply_h(w, wn, n, s);
       ah = cmul_scalar(ah, make_double2(0, -0.5 * dt / kk));
-      axpy2<T>(acc_full, ah, nullptr, ah, wn, kk == 1 ? acc_half : nullptr, sn, s);
-      w = wn;
+      for (size_t i = 0; i < ne; ++i) {
+        wn[i] = (w[i] == wa[i]) ? wb[i] : wa[i];
+        base[i] = kk == 1 ? acc_half[i] : nullptr;
+      }
+      group_h(es, w, wn, acc_full, ah, std::vector<C*>(ne, nullptr), ah, base, kk == 4, s);
+      for (size_t i = 0; i < ne; ++i) w[i] = wn[i];
     }
-    psi_ = acc_full;
+    for (size_t i = 0; i < ne; ++i) es[i]->psi_ = acc_full[i];
+  }
+
+ private:
+  // wn_i = H w_i for every engine, with acc1_i <- base_i + a1 wn_i and acc2_i <- base_i + a2 wn_i
+  // (base null: each accumulator's own value): one packed fused launch per kernel when every
+  // engine has the fused path, else engine by engine (H application, then one accumulation pass).
+  static void group_h(const std::vector<Engine*>& es, const std::vector<const C*>& w, const std::vector<C*>& wn,
+                      const std::vector<C*>& acc1, double2 a1, const std::vector<C*>& acc2, double2 a2,
+                      const std::vector<const C*>& base, bool skip_h, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+      bool fused = true;
+      for (Engine* e : es) fused = fused && e->fused_ != nullptr;
+      if (fused) {
+        ProfScope scope(es[0]->prof, "apply_h", s);
+        std::vector<FusedGroupItem> items(es.size());
+        for (size_t i = 0; i < es.size(); ++i) {
+          FusedGroupItem& it = items[i];
+          it.ops = es[i]->fused_.get();
+          it.psi = w[i];
+          it.hpsi = wn[i];
+          it.n = es[i]->ns_;
+          it.v = es[i]->vtot_;
+          it.te.acc1 = acc1[i];
+          it.te.a1 = make_float2((float)a1.x, (float)a1.y);
+          it.te.acc2 = acc2[i];
+          it.te.a2 = make_float2((float)a2.x, (float)a2.y);
+          it.te.base = base[i];
+          it.te.base_is_psi = base[i] != nullptr && base[i] == w[i];
+          it.te.skip_h = skip_h ? 1 : 0;
+        }
+        fused_apply_h_group(items, s);
+        return;
+      }
+    }
+    for (size_t i = 0; i < es.size(); ++i) {
+      Engine* e = es[i];
+      e->apply_h(w[i], wn[i], e->ns_, s);
+      axpy2<T>(acc1[i], a1, acc2[i], a2, wn[i], base[i], (size_t)e->ns_ * e->g_.nG, s);
+    }
+  }
+
+  void td_step_body(double dt, int propagator, int hartree_xc, int slot, bool dipole, const std::function<void()>* mid,
+                    cudaStream_t s) {
+    td_step_group(std::vector<Engine*>{this}, dt, propagator, hartree_xc, slot, dipole, mid, s);
   }
 
   // V = V_loc from the separable 27-image Gaussians of the current positions, in FP64 on the
@@ -1105,6 +1289,9 @@ template <typename T> class Engine final : public EngineBase {
   }
   bool use_tc() const { return sizeof(T) == 4 && prec_ == KS_MIXED_BF16X3; }
   bool mixed_cholesky() const { return sizeof(T) == 4 && ns_ <= 160; }
+  // KS_OPT_FP64_SUBSPACE on a mixed handle: the Cholesky factor of S, the subspace products and
+  // the Rayleigh-Ritz eigensolver in FP64 (as on the FP64 path), the states and their GEMMs mixed
+  bool fp64_subspace_ = false;
   // the block iteration's Rayleigh-Ritz step runs in one CTA (rr_step_mixed)
   bool fused_rr() const { return use_tc() && ns_ <= 128; }
 
@@ -1143,10 +1330,8 @@ template <typename T> class Engine final : public EngineBase {
     int e = 0;
     KS_CUDA(cudaMemcpyAsync(&e, status_ + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     KS_CUDA(cudaStreamSynchronize(s));
-    if (e) {
-      KS_CUDA(cudaMemsetAsync(status_ + 1, 0, sizeof(int), s));
-      fail(KS_ERR_CUDA, "tensor-core GEMM: a bounded wait expired (error flag %d)", e);
-    }
+    if (e) KS_CUDA(cudaMemsetAsync(status_ + 1, 0, sizeof(int), s));
+    raise_tc_status(e);
   }
 
   C* spare3(const C* a, const C* b, const C* c) {
@@ -1237,9 +1422,40 @@ template <typename T> class Engine final : public EngineBase {
 
 }  // namespace
 
-std::unique_ptr<EngineBase> make_engine(const ks_cell_desc& d) {
-  if (d.prec == KS_FP64) return std::unique_ptr<EngineBase>(new Engine<double>(d));
-  if (d.prec == KS_MIXED_BF16X3 || d.prec == KS_MIXED_TF32) return std::unique_ptr<EngineBase>(new Engine<float>(d));
+void raise_tc_status(int flag) {
+  if (flag) fail(KS_ERR_CUDA, "tensor-core GEMM: a bounded wait expired (error flag %d)", flag);
+}
+
+bool td_groupable(const EngineBase* a, const EngineBase* b) {
+  if (a->precision() != KS_MIXED_BF16X3 || b->precision() != KS_MIXED_BF16X3) return false;
+  const auto* ea = dynamic_cast<const Engine<float>*>(a);
+  const auto* eb = dynamic_cast<const Engine<float>*>(b);
+  return ea && eb && ea->groupable_with(*eb);
+}
+
+void td_step_engines(const std::vector<EngineBase*>& es, double dt, int hartree_xc, double* norms, double* energies,
+                     cudaStream_t s) {
+  if (es.empty()) return;
+  std::vector<Engine<float>*> ef;
+  for (EngineBase* e : es) {
+    auto* p = dynamic_cast<Engine<float>*>(e);
+    if (!p || !td_groupable(es[0], e)) fail(KS_ERR_ARG, "td_step_engines: engines that cannot share launches");
+    ef.push_back(p);
+  }
+  for (auto* e : ef) e->td_prepare(hartree_xc, s);
+  Engine<float>::td_step_group(ef, dt, 0, hartree_xc, 0, false, nullptr, s);
+  for (size_t i = 0; i < ef.size(); ++i) ef[i]->td_read_slot0(norms + i, energies + i, s);
+  KS_CUDA(cudaStreamSynchronize(s));
+  for (size_t i = 0; i < ef.size(); ++i) {
+    ef[i]->td_finish(s);
+    if (!std::isfinite(norms[i]) || !std::isfinite(energies[i]))
+      fail(KS_ERR_DIVERGED, "real-time step: norm %g, energy %g", norms[i], energies[i]);
+  }
+}
+
+std::unique_ptr<EngineBase> make_engine(const ks_cell_desc& d, DevicePool* pool) {
+  if (d.prec == KS_FP64) return std::unique_ptr<EngineBase>(new Engine<double>(d, pool));
+  if (d.prec == KS_MIXED_BF16X3) return std::unique_ptr<EngineBase>(new Engine<float>(d, pool));
   fail(KS_ERR_ARG, "unknown precision %d", (int)d.prec);
 }
 

@@ -2,22 +2,56 @@
 // operations of the C ABI built from the kernels.  One instance per ks_grid.
 #pragma once
 
+#include <map>
 #include <memory>
+#include <mutex>
 
 #include "common.h"
 
 namespace ks {
 
-// Device allocation owned by an engine; every allocation is counted for admission.
+// Device memory shared by the engines of a server: slabs obtained with cudaMalloc as the pool
+// grows and kept until the pool is destroyed; blocks of 256-byte granularity handed out first
+// fit from per-slab free lists and returned without cudaFree.  cudaFree synchronises the whole
+// device, so engines that allocate from a pool are created and destroyed without stalling the
+// kernels of other engines in flight.  The caller returns a block only once the work that uses
+// it has completed (a server synchronises a request's stream before retiring it).  Thread-safe.
+class DevicePool {
+ public:
+  explicit DevicePool(size_t slab_bytes) : slab_bytes_(slab_bytes) {}
+  ~DevicePool();
+  void* alloc(size_t bytes);
+  void free(void* p);
+  size_t reserved() const;   // bytes obtained from the device
+  size_t in_use() const;     // bytes handed out
+
+ private:
+  struct Slab {
+    char* base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_blocks;   // offset -> size, coalesced
+  };
+  size_t slab_bytes_;
+  mutable std::mutex mu_;
+  std::vector<Slab> slabs_;
+  std::map<char*, std::pair<int, size_t>> used_;   // address -> (slab, size)
+  size_t reserved_ = 0, in_use_ = 0;
+};
+
+// Device allocation owned by an engine; every allocation is counted for admission.  With a pool,
+// allocations come from it and go back to it (no cudaMalloc or cudaFree of their own).
 class DeviceArena {
  public:
   ~DeviceArena();
+  void set_pool(DevicePool* pool) { pool_ = pool; }
   void* alloc(size_t bytes);
-  // Frees one allocation of this arena (the device is synchronised by cudaFree); null is a no-op.
+  // Frees one allocation of this arena (without a pool the device is synchronised by cudaFree);
+  // null is a no-op.
   void release(const void* p);
   size_t bytes() const { return total_; }
 
  private:
+  DevicePool* pool_ = nullptr;
   std::vector<void*> ptrs_;
   std::vector<size_t> sizes_;
   size_t total_ = 0;
@@ -113,8 +147,26 @@ class EngineBase {
   virtual void ehrenfest(double dt, int nsteps, int hartree_xc, const double* mass, double* vel, double* pos_out,
                          double* energy_out, cudaStream_t s) = 0;
   virtual void randomize_states(uint64_t seed, cudaStream_t s) = 0;
+  virtual void set_option(int option, int value) = 0;
 };
 
-std::unique_ptr<EngineBase> make_engine(const ks_cell_desc& d);
+// pool (may be null): the engine's device memory comes from it.
+std::unique_ptr<EngineBase> make_engine(const ks_cell_desc& d, DevicePool* pool = nullptr);
+
+// The status a call returns for the tensor-core kernels' error word, read after the call: 0 is
+// success; nonzero means a bounded mbarrier wait expired (the kernel recorded it and returned),
+// raised as KS_ERR_CUDA with a message.
+void raise_tc_status(int flag);
+
+// True when two engines may take their real-time steps together (mixed precision, fused path,
+// one grid geometry).
+bool td_groupable(const EngineBase* a, const EngineBase* b);
+// One ETRS step (Sec. "Real-time propagation"; Hartree and exchange when hartree_xc) of every
+// engine in es, in lockstep on stream s: each H application of the step is one packed launch
+// over all of them.  norms[i] and energies[i] receive engine i's norm and energy at the start of
+// the step.  KS_ERR_ARG unless td_groupable holds for every pair; KS_ERR_DIVERGED on a non-finite
+// norm or energy.  Synchronous.
+void td_step_engines(const std::vector<EngineBase*>& es, double dt, int hartree_xc, double* norms, double* energies,
+                     cudaStream_t s);
 
 }  // namespace ks

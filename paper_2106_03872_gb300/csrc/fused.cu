@@ -22,6 +22,7 @@
 
 #include "fft_device.cuh"
 #include "fused.h"
+#include "tuner.h"
 
 namespace ks {
 
@@ -29,12 +30,14 @@ namespace {
 
 
 struct PlaneNL {
-  const int* pt_off;     // [N+1] covered points of plane z
+  const int* pt_off;     // [N+1] covered points of plane z, sorted by (jy, jx) within the plane
   const int* pt_xy;      // jx*N + jy
   const int* ent_off;    // [npts+1]
   const int* ent_proj;   // first projector row (atom * nproj)
   const float* ent_beta; // [nent][nproj]
+  const int* line_off;   // [N][N+1]: points of plane z with y < jy start at pt_off[z] + line_off[z][jy]
   int nproj;
+  int cap;               // most covered points of any plane
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -45,6 +48,7 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Per-size launch shapes: plane kernel threads (and CTAs per SM), lines per FFT call
 // (at most 8 complex values per thread per stage), z-kernel columns per CTA.
@@ -70,15 +74,15 @@ constexpr int ZSB = 4;
 template <int N> constexpr size_t zsmem() { return (size_t)(N + 2 * FCfg<N>::CT * (N + 1)) * sizeof(float2); }
 
 template <int N>
-__global__ void __launch_bounds__(FCfg<N>::ZT, 2) k_zinv(const float2* __restrict__ psi, int nG, const int* __restrict__ col_off,
-                                                      const int* __restrict__ col_half, int ncols, int nstates,
-                                                      float2* __restrict__ colbuf, const float2* __restrict__ twg) {
+__device__ __forceinline__ void zinv_body(const float2* __restrict__ psi, int nG, const int* __restrict__ col_off,
+                                          const int* __restrict__ col_half, int ncols, int nstates,
+                                          float2* __restrict__ colbuf, const float2* __restrict__ twg, int yblk) {
   constexpr int CT = FCfg<N>::CT, ld = N + 1, ZT = FCfg<N>::ZT;
   extern __shared__ __align__(16) float2 zsm[];
   float2* tw = zsm;
   float2* sb[2] = {zsm + N, zsm + N + CT * ld};
   __shared__ int coff[CT], chalf[CT];
-  const int b0 = blockIdx.y * ZSB;
+  const int b0 = yblk * ZSB;
   const int nb = min(ZSB, nstates - b0);
   const int c0 = blockIdx.x * CT;
   const int nl = min(CT, ncols - c0);
@@ -145,20 +149,27 @@ __global__ void __launch_bounds__(FCfg<N>::ZT, 2) k_zinv(const float2* __restric
   }
 }
 
+template <int N>
+__global__ void __launch_bounds__(FCfg<N>::ZT, 2) k_zinv(const float2* __restrict__ psi, int nG, const int* __restrict__ col_off,
+                                                      const int* __restrict__ col_half, int ncols, int nstates,
+                                                      float2* __restrict__ colbuf, const float2* __restrict__ twg) {
+  zinv_body<N>(psi, nG, col_off, col_half, ncols, nstates, colbuf, twg, blockIdx.y);
+}
+
 // k_zfwd: one state per CTA (blockIdx.y); the column block arrives by asynchronous copies
 // while the state's psi and |G|^2/2 load into registers.  (A ZSB-state pipelined form like
 // k_zinv's spilled: the next block's copy addresses and the write-back indices stayed live
 // across the transform.)
 template <int N>
-__global__ void __launch_bounds__(FCfg<N>::ZT, 3) k_zfwd(const float2* __restrict__ colbuf, const float2* __restrict__ psi,
-                                                      float2* __restrict__ hpsi, int nG, const int* __restrict__ col_off,
-                                                      const int* __restrict__ col_half, const float* __restrict__ g2half,
-                                                      int ncols, float scale, const float2* __restrict__ twg) {
+__device__ __forceinline__ void zfwd_body(const float2* __restrict__ colbuf, const float2* __restrict__ psi,
+                                          float2* __restrict__ hpsi, int nG, const int* __restrict__ col_off,
+                                          const int* __restrict__ col_half, const float* __restrict__ g2half,
+                                          int ncols, float scale, const float2* __restrict__ twg, const TaylorEpi& te,
+                                          int b) {
   constexpr int CT = FCfg<N>::CT, ld = N + 1, ZT = FCfg<N>::ZT;
   __shared__ float2 tw[N];
   __shared__ float2 s[CT * ld];
   __shared__ int coff[CT], chalf[CT];
-  const int b = blockIdx.y;
   const int c0 = blockIdx.x * CT;
   const int nl = min(CT, ncols - c0);
   for (int t = threadIdx.x; t < N; t += ZT) tw[t] = twg[t];
@@ -201,9 +212,49 @@ __global__ void __launch_bounds__(FCfg<N>::ZT, 3) k_zfwd(const float2* __restric
     if (k <= 2 * h) {
       const int z = k <= h ? k : k + N - 2 * h - 1;
       const float2 u = s[l * ld + z];
-      hpsi[off + g0 + k] = make_float2(u.x * scale + kv[q] * pv[q].x, u.y * scale + kv[q] * pv[q].y);
+      const float2 h = make_float2(u.x * scale + kv[q] * pv[q].x, u.y * scale + kv[q] * pv[q].y);
+      const size_t i = off + g0 + k;
+      if (!te.skip_h) hpsi[i] = h;
+      if (te.acc1) {
+        // the accumulators of the Taylor series (Eq. 8): acc <- base + a h
+        float2 b = te.base_is_psi ? pv[q] : (te.base ? te.base[i] : te.acc1[i]);
+        b.x += te.a1.x * h.x - te.a1.y * h.y;
+        b.y += te.a1.x * h.y + te.a1.y * h.x;
+        te.acc1[i] = b;
+        if (te.acc2) {
+          float2 c = te.base_is_psi ? pv[q] : (te.base ? te.base[i] : te.acc2[i]);
+          c.x += te.a2.x * h.x - te.a2.y * h.y;
+          c.y += te.a2.x * h.y + te.a2.y * h.x;
+          te.acc2[i] = c;
+        }
+      }
     }
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(FCfg<N>::ZT, 2) k_zfwd(const float2* __restrict__ colbuf, const float2* __restrict__ psi,
+                                                      float2* __restrict__ hpsi, int nG, const int* __restrict__ col_off,
+                                                      const int* __restrict__ col_half, const float* __restrict__ g2half,
+                                                      int ncols, float scale, const float2* __restrict__ twg,
+                                                      TaylorEpi te) {
+  zfwd_body<N>(colbuf, psi, hpsi, nG, col_off, col_half, g2half, ncols, scale, twg, te, blockIdx.y);
+}
+
+// The x-lines (all N) and the y-lines of the rows that hold columns (x in [0, xr] and
+// [N - xr, N - 1]) of a plane [x][y] with row pitch N + 1, by the CTA-wide stages of cfft_lines
+// (consecutive threads on consecutive lines; with the odd row pitch a warp's 8-byte accesses fall
+// on distinct bank pairs in either direction).  Both end with a CTA barrier.
+template <int N, int SIGN, class Epi = NoEpi>
+__device__ __forceinline__ void x_pass(float2* P, const float2* tw, const Epi& epi = Epi()) {
+  cfft_lines<N, FCfg<N>::PT, FCfg<N>::LPC, true, SIGN>(P, N, 1, N + 1, tw, epi);
+}
+
+template <int N, int SIGN>
+__device__ __forceinline__ void y_pass(float2* P, int xr, const float2* tw) {
+  constexpr int ld = N + 1;
+  cfft_lines<N, FCfg<N>::PT, FCfg<N>::LPC, true, SIGN>(P, xr + 1, ld, 1, tw);
+  if (xr > 0) cfft_lines<N, FCfg<N>::PT, FCfg<N>::LPC, true, SIGN>(P + (N - xr) * ld, xr, ld, 1, tw);
 }
 
 // Zero the plane, scatter the columns of one (state, z-plane), inverse y transforms of the
@@ -212,7 +263,7 @@ __global__ void __launch_bounds__(FCfg<N>::ZT, 3) k_zfwd(const float2* __restric
 template <int N>
 __device__ __forceinline__ void plane_load_y(float2* P, const float2* __restrict__ colrow, int ncols,
                                              const int* __restrict__ col_xy, int xr, const float2* tw) {
-  constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC, EARLY = 4;
+  constexpr int ld = N + 1, PT = FCfg<N>::PT, EARLY = 4;
   float2 cv[EARLY];
   int cxy[EARLY];
 #pragma unroll
@@ -239,11 +290,9 @@ __device__ __forceinline__ void plane_load_y(float2* P, const float2* __restrict
     P[jx * ld + jy] = colrow[c];
   }
   __syncthreads();
-  // y-lines of the rows that hold columns: jx in [0, xr] and [N - xr, N - 1].  Every line pass
-  // puts consecutive threads on consecutive lines: with the odd row pitch N + 1 a warp's
-  // 8-byte accesses then fall on distinct bank pairs.
-  cfft_lines<N, PT, LPC, true, +1>(P, xr + 1, ld, 1, tw);
-  if (xr > 0) cfft_lines<N, PT, LPC, true, +1>(P + (N - xr) * ld, xr, ld, 1, tw);
+  // y-lines of the rows that hold columns: jx in [0, xr] and [N - xr, N - 1].  With the odd row
+  // pitch N + 1 a warp's 8-byte accesses along either direction fall on distinct bank pairs.
+  y_pass<N, +1>(P, xr, tw);
 }
 
 // u = V psi as the last stage of the inverse x transform stores it (x = jx, line = jy).
@@ -263,7 +312,7 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
     k_plane(const float2* __restrict__ colbuf1, float2* __restrict__ colbuf2, int ncols, const int* __restrict__ col_xy,
             int xr, const float* __restrict__ vplane, PlaneNL nl, const float2* __restrict__ pf, int nprojtot,
             int pf_smem, const float2* __restrict__ twg) {
-  constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC;
+  constexpr int ld = N + 1, PT = FCfg<N>::PT;
   extern __shared__ __align__(16) float2 psm[];
   float2* tw = psm;
   float2* P = psm + N;
@@ -286,7 +335,7 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
   cp_async_wait_all();
   __syncthreads();
   // inverse x transforms; the last stage stores u = V psi
-  cfft_lines<N, PT, LPC, true, +1>(P, N, 1, ld, tw, VMul<N>{Vs});
+  x_pass<N, +1>(P, tw, VMul<N>{Vs});
   // + sum_{I,l} D Omega^{1/2} beta_Il p_Il  (pf already carries D Omega^{1/2})
   if (nprojtot > 0) {
     const float2* pb = pf_smem ? pfs : pf + (size_t)b * nprojtot;
@@ -309,13 +358,550 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
   }
   __syncthreads();
   // forward x-lines (all), then y-lines of the rows that hold columns
-  cfft_lines<N, PT, LPC, true, -1>(P, N, 1, ld, tw);
-  cfft_lines<N, PT, LPC, true, -1>(P, xr + 1, ld, 1, tw);
-  if (xr > 0) cfft_lines<N, PT, LPC, true, -1>(P + (N - xr) * ld, xr, ld, 1, tw);
+  x_pass<N, -1>(P, tw);
+  y_pass<N, -1>(P, xr, tw);
   for (int c = threadIdx.x; c < ncols; c += PT) {
     const int xy = col_xy[c];
     const int jx = xy / N, jy = xy - jx * N;
     colbuf2[row + c] = P[jx * ld + jy];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Team plane kernel (N = 32, 48, 64, 96, 128): the same H application per (state, z-plane) as k_plane,
+// with the line transforms owned by teams of W warps.  A team owns 32 lines, one per lane, so
+// a warp's 32 lanes always touch 32 consecutive lines at one element: with the odd row pitch
+// N + 1 every shared-memory access is free of bank conflicts along x and along y.  A team's
+// stages synchronise on a named barrier of its 32 W threads; the CTA barrier is needed only
+// where the transposition between the y and x passes crosses teams.
+//
+// N = R1 R2.  Inverse transforms: stage A radix R1 over stride-R2 elements (no twiddles), stage B
+// radix R2 over stride-R1 elements with twiddles w^(j r), natural order out (Stockham).  Forward
+// transforms take the mirrored plan: stage A' radix R2 over stride-R1 elements, stage B' radix R1
+// with twiddles.  After the inverse x stage B a thread holds, in registers, exactly the elements
+// j + r R1 that the forward x stage A' transforms, so u = V psi + V_NL psi (Eq. 9 add) is formed
+// in registers between the two and the x transforms make one shared-memory round trip fewer.
+// Rows with |m_x| > x_r hold zeros before the inverse x transform (not loaded) and are not
+// needed after the forward one (not stored).  The projector add reads the values of the plane's
+// covered points from a list sorted by (y, x) through a per-line bitmap.
+// ---------------------------------------------------------------------------------------------
+template <int N> struct TPlan {
+  static constexpr bool ok = false;
+};
+template <> struct TPlan<32> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 4, W = 4; };
+template <> struct TPlan<48> { static constexpr bool ok = true; static constexpr int R1 = 4, R2 = 12, W = 4; };
+template <> struct TPlan<64> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 8, W = 4; };
+template <> struct TPlan<96> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 12, W = 4; };
+template <> struct TPlan<128> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 16, W = 8; };
+
+template <int N> struct TCfg {
+  static constexpr int TEAMS = (N + 31) / 32;
+  static constexpr int PT = 32 * TPlan<N>::W * TEAMS;
+  static constexpr int PMIN = N >= 128 ? 1 : 2;
+  static constexpr int NW = (N + 31) / 32;                // bitmap words per line
+};
+
+__device__ __forceinline__ void team_bar(int team, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(nthreads) : "memory");
+}
+
+template <int SIGN> __device__ __forceinline__ float2 twiddle(const float2* tw, int t) {
+  float2 w = tw[t];
+  if (SIGN < 0) w.y = -w.y;
+  return w;
+}
+
+// A two-stage transform (R1 then R2, the inverse plan; SIGN selects the exponent) of the lines
+// of one team.  Line l at P + off(l), element e at e * KS.  Ends without a barrier: stage B
+// writes back only the elements the same thread read.
+template <int N, int SIGN, int KS, class Off>
+__device__ __forceinline__ void team_lines(float2* P, int nlines, const Off& off, const float2* tw) {
+  using TP = TPlan<N>;
+  constexpr int R1 = TP::R1, R2 = TP::R2, W = TP::W, QA = R2 / W, QB = R1 / W;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int team = warp / W, wi = warp - team * W;
+  if (team * 32 >= nlines) return;                               // whole team idle (uniform)
+  const int l = team * 32 + lane;
+  const bool act = l < nlines;
+  float2* p = P + off(act ? l : 0);
+  {
+    float2 v[QA][R1];
+#pragma unroll
+    for (int q = 0; q < QA; ++q) {
+      const int j = wi + W * q;
+#pragma unroll
+      for (int r = 0; r < R1; ++r) v[q][r] = act ? p[(j + r * R2) * KS] : make_float2(0.f, 0.f);
+      SmallDft<R1, float2>::run(v[q], SIGN);
+    }
+    team_bar(team, 32 * W);
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < QA; ++q) {
+        const int j = wi + W * q;
+#pragma unroll
+        for (int r = 0; r < R1; ++r) p[(j * R1 + r) * KS] = v[q][r];
+      }
+    }
+    team_bar(team, 32 * W);
+  }
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      const int j = wi + W * q;
+      float2 v[R2];
+#pragma unroll
+      for (int r = 0; r < R2; ++r) v[r] = p[(j + r * R1) * KS];
+#pragma unroll
+      for (int r = 1; r < R2; ++r) v[r] = cmul(v[r], twiddle<SIGN>(tw, j * r));
+      SmallDft<R2, float2>::run(v, SIGN);
+#pragma unroll
+      for (int r = 0; r < R2; ++r) p[(j + r * R1) * KS] = v[r];
+    }
+  }
+}
+
+// Forward y transform (mirrored plan: R2 then R1) of the band rows of a team.
+template <int N, class Off>
+__device__ __forceinline__ void team_lines_fwd(float2* P, int nlines, const Off& off, const float2* tw) {
+  using TP = TPlan<N>;
+  constexpr int R1 = TP::R1, R2 = TP::R2, W = TP::W, QA = R1 / W, QB = R2 / W;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int team = warp / W, wi = warp - team * W;
+  if (team * 32 >= nlines) return;
+  const int l = team * 32 + lane;
+  const bool act = l < nlines;
+  float2* p = P + off(act ? l : 0);
+  {
+    float2 v[QA][R2];
+#pragma unroll
+    for (int q = 0; q < QA; ++q) {
+      const int j = wi + W * q;
+#pragma unroll
+      for (int r = 0; r < R2; ++r) v[q][r] = act ? p[j + r * R1] : make_float2(0.f, 0.f);
+      SmallDft<R2, float2>::run(v[q], -1);
+    }
+    team_bar(team, 32 * W);
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < QA; ++q) {
+        const int j = wi + W * q;
+#pragma unroll
+        for (int r = 0; r < R2; ++r) p[j * R2 + r] = v[q][r];
+      }
+    }
+    team_bar(team, 32 * W);
+  }
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      const int j = wi + W * q;
+      float2 v[R1];
+#pragma unroll
+      for (int r = 0; r < R1; ++r) v[r] = p[j + r * R2];
+#pragma unroll
+      for (int r = 1; r < R1; ++r) v[r] = cmul(v[r], twiddle<-1>(tw, j * r));
+      SmallDft<R1, float2>::run(v, -1);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) p[j + r * R2] = v[r];
+    }
+  }
+}
+
+template <int N> struct RowOff {   // band row g -> row x (g <= xr) or g + N - 2 xr - 1, pitch N + 1
+  int xr;
+  __device__ __forceinline__ int operator()(int g) const { return (g <= xr ? g : g + N - 2 * xr - 1) * (N + 1); }
+};
+template <int N> struct ColOff {   // x-line = column y of the plane
+  __device__ __forceinline__ int operator()(int l) const { return l; }
+};
+
+// The x round trip of a team: inverse x transform, u = V psi + the projector add in registers,
+// forward x transform.  x-line l (= y) of the plane, element e = x at P[e (N + 1) + l].
+template <int N>
+__device__ __forceinline__ void team_x_roundtrip(float2* P, int xr, const float* __restrict__ V, const float2* nlv,
+                                                 const uint32_t* bits, const int* loff, const float2* tw) {
+  using TP = TPlan<N>;
+  constexpr int R1 = TP::R1, R2 = TP::R2, W = TP::W, KS = N + 1, NW = TCfg<N>::NW;
+  constexpr int QA = R2 / W, QB = R1 / W;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int team = warp / W, wi = warp - team * W;
+  const int l = team * 32 + lane;
+  const bool act = l < N;
+  float2* p = P + (act ? l : 0);
+  auto band = [&](int e) { return e <= xr || e >= N - xr; };
+  // inverse stage A: radix R1 over e = j + r R2; rows outside the band are zero
+  {
+    float2 v[QA][R1];
+#pragma unroll
+    for (int q = 0; q < QA; ++q) {
+      const int j = wi + W * q;
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        const int e = j + r * R2;
+        v[q][r] = (act && band(e)) ? p[e * KS] : make_float2(0.f, 0.f);
+      }
+      SmallDft<R1, float2>::run(v[q], +1);
+    }
+    team_bar(team, 32 * W);
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < QA; ++q) {
+        const int j = wi + W * q;
+#pragma unroll
+        for (int r = 0; r < R1; ++r) p[(j * R1 + r) * KS] = v[q][r];
+      }
+    }
+    team_bar(team, 32 * W);
+  }
+  // inverse stage B (radix R2, natural order out), pointwise u, forward stage A' (radix R2 on the
+  // same elements e = j + r R1)
+  {
+    // element e = j + R1 r (j < R1, R1 dividing 32) lies in bitmap word (R1 r) / 32 at bit
+    // (R1 r mod 32) + j: the word index is a compile-time constant; pre[k] counts the line's points
+    // in words < k
+    static_assert(32 % R1 == 0, "bitmap word of e = j + R1 r");
+    uint32_t wbits[NW];
+    int pre[NW];
+    if (act) {
+      int acc = loff[l];
+#pragma unroll
+      for (int k = 0; k < NW; ++k) {
+        wbits[k] = bits[l * NW + k];
+        pre[k] = acc;
+        acc += __popc(wbits[k]);
+      }
+    }
+    float2 v[QB][R2];
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      const int j = wi + W * q;
+      // the potential at this job's elements, requested before the transform so that its L2
+      // latency overlaps the arithmetic (all states of a plane read the same V plane)
+      float vv[R2];
+#pragma unroll
+      for (int r = 0; r < R2; ++r) vv[r] = act ? __ldg(V + (j + r * R1) * N + l) : 0.f;
+      if (act) {
+#pragma unroll
+        for (int r = 0; r < R2; ++r) v[q][r] = p[(j + r * R1) * KS];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R2; ++r) v[q][r] = make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int r = 1; r < R2; ++r) v[q][r] = cmul(v[q][r], twiddle<+1>(tw, j * r));
+      SmallDft<R2, float2>::run(v[q], +1);
+      if (act) {
+#pragma unroll
+        for (int r = 0; r < R2; ++r) {
+          float2 u = make_float2(v[q][r].x * vv[r], v[q][r].y * vv[r]);
+          const uint32_t word = wbits[(R1 * r) >> 5];
+          const int bit = ((R1 * r) & 31) + j;
+          if ((word >> bit) & 1u) {
+            const float2 a = nlv[pre[(R1 * r) >> 5] + __popc(word & ((1u << bit) - 1u))];
+            u.x += a.x;
+            u.y += a.y;
+          }
+          v[q][r] = u;
+        }
+      }
+      SmallDft<R2, float2>::run(v[q], -1);
+    }
+    team_bar(team, 32 * W);
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < QB; ++q) {
+        const int j = wi + W * q;
+#pragma unroll
+        for (int r = 0; r < R2; ++r) p[(j * R2 + r) * KS] = v[q][r];
+      }
+    }
+    team_bar(team, 32 * W);
+  }
+  // forward stage B' (radix R1 with twiddles), in place; only the band rows are stored
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < QA; ++q) {
+      const int j = wi + W * q;
+      float2 v[R1];
+#pragma unroll
+      for (int r = 0; r < R1; ++r) v[r] = p[(j + r * R2) * KS];
+#pragma unroll
+      for (int r = 1; r < R1; ++r) v[r] = cmul(v[r], twiddle<-1>(tw, j * r));
+      SmallDft<R1, float2>::run(v, -1);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        const int e = j + r * R2;
+        if (band(e)) p[e * KS] = v[r];
+      }
+    }
+  }
+}
+
+// Dynamic shared memory: twiddles [N], plane [N][N+1], projections [nprojtot] (this state),
+// covered-point values [cap], bitmap [N][NW], line offsets [N].
+template <int N> size_t team_smem(int nprojtot, int cap) {
+  return (size_t)(N + N * (N + 1) + nprojtot + cap) * sizeof(float2) +
+         (size_t)N * TCfg<N>::NW * sizeof(uint32_t) + (size_t)N * sizeof(int);
+}
+
+template <int N>
+__device__ __forceinline__ void plane_team_body(const float2* __restrict__ colbuf1, float2* __restrict__ colbuf2,
+                                                int ncols, const int* __restrict__ col_xy, int xr,
+                                                const float* __restrict__ vplane, const PlaneNL& nl,
+                                                const float2* __restrict__ pf, int nprojtot, int cap_layout,
+                                                const float2* __restrict__ twg, int z, int b) {
+  constexpr int ld = N + 1, PT = TCfg<N>::PT, NW = TCfg<N>::NW;
+  extern __shared__ __align__(16) float2 psm[];
+  float2* tw = psm;
+  float2* P = tw + N;
+  float2* pfs = P + N * ld;
+  float2* nlv = pfs + nprojtot;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(nlv + cap_layout);
+  int* loff = reinterpret_cast<int*>(bits + N * NW);
+  for (int q = threadIdx.x; q < nprojtot; q += PT) cp_async8(pfs + q, pf + (size_t)b * nprojtot + q);
+  cp_async_commit();
+  for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
+  int pt0 = 0, pt1 = 0;
+  if (nprojtot > 0) {
+    pt0 = nl.pt_off[z];
+    pt1 = nl.pt_off[z + 1];
+  }
+  for (int e = threadIdx.x; e < N * NW; e += PT) bits[e] = 0u;
+  for (int e = threadIdx.x; e < N; e += PT) loff[e] = nprojtot > 0 ? nl.line_off[(size_t)z * (N + 1) + e] : 0;
+  // zero the band rows (the only rows the inverse transforms read before writing them)
+  const int nband = 2 * xr + 1;
+  for (int e = threadIdx.x; e < nband * N; e += PT) {
+    const int g = e / N, y = e - g * N;
+    P[(g <= xr ? g : g + N - 2 * xr - 1) * ld + y] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  // the columns land in the zeroed band rows by asynchronous copies while the projector values
+  // are formed
+  const size_t row = ((size_t)b * N + z) * ncols;
+  for (int c = threadIdx.x; c < ncols; c += PT) {
+    const int xy = col_xy[c];
+    const int jx = xy / N, jy = xy - jx * N;
+    cp_async8(P + jx * ld + jy, colbuf1 + row + c);
+  }
+  cp_async_commit();
+  cp_async_wait_group1();                                              // the projections (first group)
+  __syncthreads();
+  // values of the projector add at the plane's covered points: sum_{I,l} D Omega^{1/2} beta_Il p_Il
+  for (int pt = pt0 + threadIdx.x; pt < pt1; pt += PT) {
+    const int e0 = nl.ent_off[pt], e1 = nl.ent_off[pt + 1];
+    float ax = 0.f, ay = 0.f;
+    for (int e = e0; e < e1; ++e) {
+      const float2* pp = pfs + nl.ent_proj[e];
+      const float* bt = nl.ent_beta + (size_t)e * nl.nproj;
+      for (int q = 0; q < nl.nproj; ++q) {
+        ax += bt[q] * pp[q].x;
+        ay += bt[q] * pp[q].y;
+      }
+    }
+    nlv[pt - pt0] = make_float2(ax, ay);
+    const int xy = nl.pt_xy[pt];
+    const int jx = xy / N, jy = xy - jx * N;
+    atomicOr(&bits[jy * NW + (jx >> 5)], 1u << (jx & 31));
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // inverse y transforms of the band rows
+  team_lines<N, +1, 1>(P, nband, RowOff<N>{xr}, tw);
+  __syncthreads();
+  team_x_roundtrip<N>(P, xr, vplane + (size_t)z * N * N, nlv, bits, loff, tw);
+  __syncthreads();
+  team_lines_fwd<N>(P, nband, RowOff<N>{xr}, tw);
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncols; c += PT) {
+    const int xy = col_xy[c];
+    const int jx = xy / N, jy = xy - jx * N;
+    colbuf2[row + c] = P[jx * ld + jy];
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(TCfg<N>::PT, TCfg<N>::PMIN)
+    k_plane_team(const float2* __restrict__ colbuf1, float2* __restrict__ colbuf2, int ncols,
+                 const int* __restrict__ col_xy, int xr, const float* __restrict__ vplane, PlaneNL nl,
+                 const float2* __restrict__ pf, int nprojtot, const float2* __restrict__ twg) {
+  plane_team_body<N>(colbuf1, colbuf2, ncols, col_xy, xr, vplane, nl, pf, nprojtot, nl.cap, twg, blockIdx.x,
+                     blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Packed H application of several cells with one grid geometry (fused_apply_h_group): the same
+// kernel bodies, launched once over all members' states.  Member m's states are packed rows
+// [s0, s0 + n) of the plane and zfwd grids and z-blocks [z0, z0 + ceil(n / ZSB)) of the zinv grid;
+// each CTA finds its member by a scan of the descriptor (a kernel parameter, at most GMAX members).
+// ---------------------------------------------------------------------------------------------
+struct GMember {
+  const float2* psi;
+  float2* hpsi;
+  float2* cb1;
+  float2* cb2;
+  const float* vplane;
+  PlaneNL nl;
+  const float2* pf;
+  TaylorEpi te;
+  int nprojtot, n, s0, z0;
+};
+constexpr int GMAX = 8;
+struct GDesc {
+  int nm;
+  GMember m[GMAX];
+};
+
+__device__ __forceinline__ int member_by_state(const GDesc& g, int row) {
+  int m = 0;
+  while (m + 1 < g.nm && row >= g.m[m + 1].s0) ++m;
+  return m;
+}
+__device__ __forceinline__ int member_by_zblock(const GDesc& g, int row) {
+  int m = 0;
+  while (m + 1 < g.nm && row >= g.m[m + 1].z0) ++m;
+  return m;
+}
+
+template <int N>
+__global__ void __launch_bounds__(FCfg<N>::ZT, 2) k_zinv_group(const __grid_constant__ GDesc gd, int nG,
+                                                            const int* __restrict__ col_off,
+                                                            const int* __restrict__ col_half, int ncols,
+                                                            const float2* __restrict__ twg) {
+  const GMember& M = gd.m[member_by_zblock(gd, blockIdx.y)];
+  zinv_body<N>(M.psi, nG, col_off, col_half, ncols, M.n, M.cb1, twg, blockIdx.y - M.z0);
+}
+
+template <int N>
+__global__ void __launch_bounds__(TCfg<N>::PT, TCfg<N>::PMIN)
+    k_plane_team_group(const __grid_constant__ GDesc gd, int ncols, const int* __restrict__ col_xy, int xr,
+                       const float2* __restrict__ twg) {
+  const GMember& M = gd.m[member_by_state(gd, blockIdx.y)];
+  plane_team_body<N>(M.cb1, M.cb2, ncols, col_xy, xr, M.vplane, M.nl, M.pf, M.nprojtot, M.nl.cap, twg, blockIdx.x,
+                     blockIdx.y - M.s0);
+}
+
+template <int N>
+__global__ void __launch_bounds__(FCfg<N>::ZT, 2) k_zfwd_group(const __grid_constant__ GDesc gd, int nG,
+                                                            const int* __restrict__ col_off,
+                                                            const int* __restrict__ col_half,
+                                                            const float* __restrict__ g2half, int ncols, float scale,
+                                                            const float2* __restrict__ twg) {
+  const GMember& M = gd.m[member_by_state(gd, blockIdx.y)];
+  zfwd_body<N>(M.cb2, M.psi, M.hpsi, nG, col_off, col_half, g2half, ncols, scale, twg, M.te, blockIdx.y - M.s0);
+}
+
+// Density partial sums with the team transforms (N = 32, 48, 64, 96, 128): one (z-plane, chunk of
+// states) per CTA, states in order.  Per state: the band rows are zeroed, the columns scattered,
+// the inverse y transform of the band rows, then the inverse x transform whose stage B leaves
+// each thread the elements e = j + r R1 of its x-line in registers; f |u|^2 is added to
+// per-thread accumulators (every grid point of the plane belongs to one thread, so each point's
+// sum runs over the states in order and needs no atomics).
+template <int N>
+__global__ void __launch_bounds__(TCfg<N>::PT, TCfg<N>::PMIN)
+    k_plane_density_team(const float2* __restrict__ colbuf1, int ncols, const int* __restrict__ col_xy, int xr,
+                         int nstates, int chunk, const double* __restrict__ occ, float scale,
+                         float* __restrict__ partial, const float2* __restrict__ twg) {
+  using TP = TPlan<N>;
+  constexpr int R1 = TP::R1, R2 = TP::R2, W = TP::W, QA = R2 / W, QB = R1 / W;
+  constexpr int ld = N + 1, KS = N + 1, PT = TCfg<N>::PT;
+  // N = 96 keeps the accumulators in shared memory ([x][y], each point owned by one thread): 24
+  // more registers per thread would spill at two CTAs per SM
+  constexpr bool ACC_SMEM = N == 96;
+  extern __shared__ __align__(16) float2 psm[];
+  float2* tw = psm;
+  float2* P = tw + N;
+  float* accs = reinterpret_cast<float*>(P + N * ld);
+  const int z = blockIdx.x, ch = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int team = warp / W, wi = warp - team * W;
+  const int l = team * 32 + lane;
+  const bool act = l < N;
+  for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
+  const int nband = 2 * xr + 1;
+  auto band = [&](int e) { return e <= xr || e >= N - xr; };
+  float acc[ACC_SMEM ? 1 : QB][ACC_SMEM ? 1 : R2];
+  if constexpr (ACC_SMEM) {
+    for (int e = threadIdx.x; e < N * N; e += PT) accs[e] = 0.f;
+  } else {
+#pragma unroll
+    for (int q = 0; q < QB; ++q)
+#pragma unroll
+      for (int r = 0; r < R2; ++r) acc[q][r] = 0.f;
+  }
+  const int b0 = ch * chunk, b1 = min(nstates, b0 + chunk);
+#pragma unroll 1
+  for (int b = b0; b < b1; ++b) {
+    for (int e = threadIdx.x; e < nband * N; e += PT) {
+      const int g = e / N, y = e - g * N;
+      P[(g <= xr ? g : g + N - 2 * xr - 1) * ld + y] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float2* src = colbuf1 + ((size_t)b * N + z) * ncols;
+    for (int c = threadIdx.x; c < ncols; c += PT) {
+      const int xy = col_xy[c];
+      const int jx = xy / N, jy = xy - jx * N;
+      P[jx * ld + jy] = src[c];
+    }
+    __syncthreads();
+    team_lines<N, +1, 1>(P, nband, RowOff<N>{xr}, tw);
+    __syncthreads();
+    float2* p = P + (act ? l : 0);
+    {
+      float2 v[QA][R1];
+#pragma unroll
+      for (int q = 0; q < QA; ++q) {
+        const int j = wi + W * q;
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+          const int e = j + r * R2;
+          v[q][r] = (act && band(e)) ? p[e * KS] : make_float2(0.f, 0.f);
+        }
+        SmallDft<R1, float2>::run(v[q], +1);
+      }
+      team_bar(team, 32 * W);
+      if (act) {
+#pragma unroll
+        for (int q = 0; q < QA; ++q) {
+          const int j = wi + W * q;
+#pragma unroll
+          for (int r = 0; r < R1; ++r) p[(j * R1 + r) * KS] = v[q][r];
+        }
+      }
+      team_bar(team, 32 * W);
+    }
+    const float f = (float)occ[b];
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < QB; ++q) {
+        const int j = wi + W * q;
+        float2 v[R2];
+#pragma unroll
+        for (int r = 0; r < R2; ++r) v[r] = p[(j + r * R1) * KS];
+#pragma unroll
+        for (int r = 1; r < R2; ++r) v[r] = cmul(v[r], twiddle<+1>(tw, j * r));
+        SmallDft<R2, float2>::run(v, +1);
+#pragma unroll
+        for (int r = 0; r < R2; ++r) {
+          const float d = f * (v[r].x * v[r].x + v[r].y * v[r].y);
+          if constexpr (ACC_SMEM)
+            accs[(j + r * R1) * N + l] += d;
+          else
+            acc[q][r] += d;
+        }
+      }
+    }
+    __syncthreads();                                                  // the plane is reused
+  }
+  float* out = partial + ((size_t)ch * N + z) * N * N;
+  if constexpr (ACC_SMEM) {
+    for (int e = threadIdx.x; e < N * N; e += PT) out[e] = accs[e] * scale;
+  } else if (act) {
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      const int j = wi + W * q;
+#pragma unroll
+      for (int r = 0; r < R2; ++r) out[(j + r * R1) * N + l] = acc[q][r] * scale;
+    }
   }
 }
 
@@ -326,7 +912,7 @@ template <int N>
 __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
     k_plane_inverse(const float2* __restrict__ colbuf1, int ncols, const int* __restrict__ col_xy, int xr,
                     const float2* __restrict__ twg, float2* __restrict__ out) {
-  constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC;
+  constexpr int ld = N + 1, PT = FCfg<N>::PT;
   extern __shared__ __align__(16) float2 psm[];
   float2* tw = psm;
   float2* P = psm + N;
@@ -334,7 +920,7 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
   for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
   const size_t row = ((size_t)b * N + z) * ncols;
   plane_load_y<N>(P, colbuf1 + row, ncols, col_xy, xr, tw);
-  cfft_lines<N, PT, LPC, true, +1>(P, N, 1, ld, tw);
+  x_pass<N, +1>(P, tw);
   float2* o = out + ((size_t)b * N + z) * N * N;
   for (int e = threadIdx.x; e < N * N; e += PT) o[e] = P[(e / N) * ld + (e - (e / N) * N)];
 }
@@ -362,7 +948,7 @@ __global__ void __cluster_dims__(1, DCL, 1) __launch_bounds__(FCfg<N>::PT, FCfg<
                     int nstates, const double* __restrict__ occ, float scale, float* __restrict__ partial,
                     const float2* __restrict__ twg) {
   namespace cg = cooperative_groups;
-  constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC;
+  constexpr int ld = N + 1, PT = FCfg<N>::PT;
   extern __shared__ __align__(16) float2 psm[];
   float2* tw = psm;
   float2* P = psm + N;
@@ -372,7 +958,7 @@ __global__ void __cluster_dims__(1, DCL, 1) __launch_bounds__(FCfg<N>::PT, FCfg<
   if (b < nstates) {
     // the y transforms (their first barrier also publishes tw), then the x transforms
     plane_load_y<N>(P, colbuf1 + ((size_t)b * N + z) * ncols, ncols, col_xy, xr, tw);
-    cfft_lines<N, PT, LPC, true, +1>(P, N, 1, ld, tw, DensSet<N>{acc, (float)occ[b]});
+    x_pass<N, +1>(P, tw, DensSet<N>{acc, (float)occ[b]});
   } else {
     for (int e = threadIdx.x; e < N * N; e += PT) acc[e] = 0.f;   // padding state of the cluster
   }
@@ -409,7 +995,7 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
     k_plane_density_chunk(const float2* __restrict__ colbuf1, int ncols, const int* __restrict__ col_xy, int xr,
                           int nstates, int chunk, const double* __restrict__ occ, float scale,
                           float* __restrict__ partial, const float2* __restrict__ twg) {
-  constexpr int ld = N + 1, PT = FCfg<N>::PT, LPC = FCfg<N>::LPC;
+  constexpr int ld = N + 1, PT = FCfg<N>::PT;
   extern __shared__ __align__(16) float2 psm[];
   float2* tw = psm;
   float2* P = psm + N;
@@ -421,7 +1007,7 @@ __global__ void __launch_bounds__(FCfg<N>::PT, FCfg<N>::PMIN)
 #pragma unroll 1
   for (int b = b0; b < b1; ++b) {
     plane_load_y<N>(P, colbuf1 + ((size_t)b * N + z) * ncols, ncols, col_xy, xr, tw);
-    cfft_lines<N, PT, LPC, true, +1>(P, N, 1, ld, tw, DensAcc<N>{acc, (float)occ[b]});
+    x_pass<N, +1>(P, tw, DensAcc<N>{acc, (float)occ[b]});
   }
   float* out = partial + ((size_t)ch * N + z) * N * N;
   for (int e = threadIdx.x; e < N * N; e += PT) out[e] = acc[e] * scale;
@@ -584,11 +1170,13 @@ class FusedImpl final : public FusedOps {
       part_ = alloc<double2>(part_elems_);
       build_projector_block();
     }
-    nch_max_ = (ns_ + density_chunk() - 1) / density_chunk();
+    nch_max_ = std::max((ns_ + density_chunk(0) - 1) / density_chunk(0), (ns_ + density_chunk(1) - 1) / density_chunk(1));
     dpartial_ = alloc<float>((size_t)nch_max_ * N3);
   }
 
-  void apply_h(const float2* psi, float2* hpsi, int n, const float* v, cudaStream_t s) override {
+  // The per-cell part of an H application: V re-laid per z-plane and the projections
+  // p_Il = sum_G conj(b_Il(G)) c_G of the block (tensor cores), scaled for the plane kernel.
+  void pre_h(const float2* psi, int n, const float* v, cudaStream_t s) {
     const size_t N3 = (size_t)N_ * N_ * N_;
     k_to_planes<<<nblk(N3, 256), 256, 0, s>>>(v, N_, vplane_);
     KS_CHECK_LAUNCH();
@@ -599,16 +1187,112 @@ class FusedImpl final : public FusedOps {
       k_proj_to_states<<<nblk((size_t)nprojtot_ * n, 256), 256, 0, s>>>(pout_, nprojtot_, n, scale, pf_);
       KS_CHECK_LAUNCH();
     }
+  }
+
+  static bool same_geometry(const FusedImpl* a, const FusedImpl* b) {
+    return a->N_ == b->N_ && a->g_.nG == b->g_.nG && a->ncols_ == b->ncols_ && a->g_.xr == b->g_.xr &&
+           a->g_.L == b->g_.L && a->g_.ecut == b->g_.ecut;
+  }
+
+  // fused_apply_h_group: the members' per-cell parts, then one launch of each kernel per chunk of
+  // GMAX members (grids without a team plan: each member alone).
+  static void group_apply(const std::vector<FusedGroupItem>& items, cudaStream_t s) {
+    if (items.empty()) return;
+    FusedImpl* f0 = static_cast<FusedImpl*>(items[0].ops);
+    for (const auto& it : items) {
+      FusedImpl* f = static_cast<FusedImpl*>(it.ops);
+      if (!same_geometry(f0, f)) fail(KS_ERR_ARG, "packed H application: the members' grids differ");
+      if (it.n < 1 || it.n > f->ns_) fail(KS_ERR_ARG, "packed H application: member with %d states", it.n);
+      f->pre_h(it.psi, it.n, it.v, s);
+    }
+    f0->dispatch([&](auto tag) { group_launch<decltype(tag)::value>(items, s); });
+  }
+
+  template <int N> static void group_launch(const std::vector<FusedGroupItem>& items, cudaStream_t s) {
+    FusedImpl* f0 = static_cast<FusedImpl*>(items[0].ops);
+    if constexpr (!TPlan<N>::ok) {
+      for (const auto& it : items) {
+        FusedImpl* f = static_cast<FusedImpl*>(it.ops);
+        f->zinv(it.psi, it.n, s);
+        f->template launch_plane<N>(it.n, f->colbuf1_, f->pf_, s);
+        f->template launch_zfwd<N>(it.psi, it.hpsi, it.n, it.te, s);
+      }
+    } else {
+      static bool attr = false;
+      if (!attr) {
+        KS_CUDA(cudaFuncSetAttribute(k_zinv_group<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem<N>()));
+        KS_CUDA(cudaFuncSetAttribute(k_plane_team_group<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM_MAX));
+        attr = true;
+      }
+      const int ncb = (f0->ncols_ + FCfg<N>::CT - 1) / FCfg<N>::CT;
+      for (size_t a = 0; a < items.size(); a += GMAX) {
+        GDesc gd{};
+        int s0 = 0, z0 = 0;
+        size_t smem = 0;
+        for (size_t k = a; k < std::min(items.size(), a + GMAX); ++k) {
+          const FusedGroupItem& it = items[k];
+          FusedImpl* f = static_cast<FusedImpl*>(it.ops);
+          GMember& m = gd.m[gd.nm++];
+          m.psi = it.psi;
+          m.hpsi = it.hpsi;
+          m.cb1 = f->colbuf1_;
+          m.cb2 = f->colbuf2_;
+          m.vplane = f->vplane_;
+          m.nl = f->nl_;
+          if (f->nprojtot_ == 0) m.nl.cap = 0;
+          m.pf = f->pf_;
+          m.te = it.te;
+          m.nprojtot = f->nprojtot_;
+          m.n = it.n;
+          m.s0 = s0;
+          m.z0 = z0;
+          s0 += it.n;
+          z0 += (it.n + ZSB - 1) / ZSB;
+          smem = std::max(smem, team_smem<N>(m.nprojtot, m.nl.cap));
+        }
+        if (smem > SMEM_MAX) fail(KS_ERR_ARG, "packed H application: %zu bytes of shared memory", smem);
+        {
+          ProfScope ps(f0->prof_, "zinv", s);
+          k_zinv_group<N><<<dim3(ncb, z0), FCfg<N>::ZT, zsmem<N>(), s>>>(gd, f0->g_.nG, f0->t_.col_off,
+                                                                         f0->t_.col_half, f0->ncols_, f0->t_.tw);
+          KS_CHECK_LAUNCH();
+        }
+        {
+          ProfScope ps(f0->prof_, "plane", s);
+          k_plane_team_group<N><<<dim3(N, s0), TCfg<N>::PT, smem, s>>>(gd, f0->ncols_, f0->t_.col_xy, f0->g_.xr,
+                                                                       f0->t_.tw);
+          KS_CHECK_LAUNCH();
+        }
+        {
+          ProfScope ps(f0->prof_, "zfwd", s);
+          k_zfwd_group<N><<<dim3(ncb, s0), FCfg<N>::ZT, 0, s>>>(gd, f0->g_.nG, f0->t_.col_off, f0->t_.col_half,
+                                                                f0->t_.g2half, f0->ncols_,
+                                                                (float)(1.0 / ((double)N * N * N)), f0->t_.tw);
+          KS_CHECK_LAUNCH();
+        }
+      }
+    }
+  }
+
+  void apply_h(const float2* psi, float2* hpsi, int n, const float* v, cudaStream_t s,
+               const TaylorEpi* te) override {
+    pre_h(psi, n, v, s);
     zinv(psi, n, s);
     {
       ProfScope ps(prof_, "plane", s);
-      dispatch([&](auto tag) { launch_plane<decltype(tag)::value>(n, s); });
+      dispatch([&](auto tag) {
+        constexpr int N = decltype(tag)::value;
+        launch_plane<N>(n, colbuf1_, pf_, s, plane_variant<N>(n, s));
+      });
     }
     {
       ProfScope ps(prof_, "zfwd", s);
-      dispatch([&](auto tag) { launch_zfwd<decltype(tag)::value>(psi, hpsi, n, s); });
+      const TaylorEpi none{};
+      dispatch([&](auto tag) { launch_zfwd<decltype(tag)::value>(psi, hpsi, n, te ? *te : none, s); });
     }
   }
+
 
   void real_space(const float2* psi, int n, float2* out, cudaStream_t s) override {
     zinv(psi, n, s);
@@ -624,13 +1308,13 @@ class FusedImpl final : public FusedOps {
   void set_atoms(const DevTables<float>& t) override {
     if (!lists_ready_) plane_lists_host();
     lists_ready_ = false;
-    KS_CUDA(cudaDeviceSynchronize());
-    t_ = t;
+    t_ = t;                                 // the caller has synchronised the engine's streams
     arena_.release(nl_.pt_off);
     arena_.release(nl_.pt_xy);
     arena_.release(nl_.ent_off);
     arena_.release(nl_.ent_proj);
     arena_.release(nl_.ent_beta);
+    arena_.release(nl_.line_off);
     upload_plane_lists();
     if (nprojtot_ > 0) build_projector_block();
   }
@@ -638,8 +1322,15 @@ class FusedImpl final : public FusedOps {
   void density(const float2* psi, int n, const double* occ, float* nout, cudaStream_t s) override {
     zinv(psi, n, s);
     ProfScope ps(prof_, "plane_density", s);
-    const int nch = (n + density_chunk() - 1) / density_chunk();
-    dispatch([&](auto tag) { launch_density<decltype(tag)::value>(n, nch, occ, s); });
+    int variant = 1;
+    if (team_density()) {
+      static const char* names[2] = {"team", "cta"};
+      variant = tune_choice(tune_key("density", n), 2, [&](int c) {
+        dispatch([&](auto tag) { launch_density<decltype(tag)::value>(n, occ, s, c); });
+      }, s, names);
+    }
+    dispatch([&](auto tag) { launch_density<decltype(tag)::value>(n, occ, s, variant); });
+    const int nch = (n + density_chunk(variant) - 1) / density_chunk(variant);
     k_density_reduce<<<nblk((size_t)N_ * N_ * N_, 256), 256, 0, s>>>(dpartial_, nch, N_, nout);
     KS_CHECK_LAUNCH();
   }
@@ -677,15 +1368,50 @@ class FusedImpl final : public FusedOps {
     k_zinv<N><<<grid, FCfg<N>::ZT, zsmem<N>(), s>>>(psi, g_.nG, t_.col_off, t_.col_half, ncols_, n, colbuf1_, t_.tw);
     KS_CHECK_LAUNCH();
   }
-  template <int N> void launch_zfwd(const float2* psi, float2* hpsi, int n, cudaStream_t s) {
+  template <int N> void launch_zfwd(const float2* psi, float2* hpsi, int n, const TaylorEpi& te, cudaStream_t s) {
     dim3 grid((ncols_ + FCfg<N>::CT - 1) / FCfg<N>::CT, n);
     k_zfwd<N><<<grid, FCfg<N>::ZT, 0, s>>>(colbuf2_, psi, hpsi, g_.nG, t_.col_off, t_.col_half, t_.g2half, ncols_,
-                                           (float)(1.0 / ((double)N * N * N)), t_.tw);
+                                           (float)(1.0 / ((double)N * N * N)), t_.tw, te);
     KS_CHECK_LAUNCH();
   }
   template <int N> static size_t plane_smem() { return (size_t)(N + N * (N + 1)) * sizeof(float2); }
   static constexpr size_t SMEM_MAX = 227 * 1024;
-  template <int N> void launch_plane(int n, cudaStream_t s) {
+  // Tuned choice of the plane kernel for n states (0: team transforms, 1: CTA-wide stages),
+  // where both exist.
+  template <int N> int plane_variant(int n, cudaStream_t s) {
+    if constexpr (TPlan<N>::ok) {
+      if (team_smem<N>(nprojtot_, nprojtot_ > 0 ? nl_.cap : 0) > SMEM_MAX) return 1;
+      static const char* names[2] = {"team", "cta"};
+      return tune_choice(tune_key("plane", n), 2, [&](int c) { launch_plane<N>(n, colbuf1_, pf_, s, c); }, s,
+                         names);
+    }
+    return 1;
+  }
+  std::string tune_key(const char* what, int n) const {
+    int b = 1;
+    while (b < n) b *= 2;
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), "%s N=%d states<=%d", what, N_, b);
+    return buf;
+  }
+
+  template <int N> void launch_plane(int n, const float2* cb1, const float2* pf, cudaStream_t s, int variant = 0) {
+    if constexpr (TPlan<N>::ok) {
+      const size_t smem = team_smem<N>(nprojtot_, nprojtot_ > 0 ? nl_.cap : 0);
+      if (smem <= SMEM_MAX && variant == 0) {
+        static bool tattr = false;
+        if (!tattr) {
+          KS_CUDA(cudaFuncSetAttribute(k_plane_team<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX));
+          tattr = true;
+        }
+        PlaneNL nl = nl_;
+        if (nprojtot_ == 0) nl.cap = 0;
+        k_plane_team<N><<<dim3(N, n), TCfg<N>::PT, smem, s>>>(cb1, colbuf2_, ncols_, t_.col_xy, g_.xr, vplane_, nl,
+                                                              pf, nprojtot_, t_.tw);
+        KS_CHECK_LAUNCH();
+        return;
+      }
+    }
     static bool attr = false;
     if (!attr) {
       KS_CUDA(cudaFuncSetAttribute(k_plane<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX));
@@ -696,8 +1422,8 @@ class FusedImpl final : public FusedOps {
     const int pf_smem = with_pf <= SMEM_MAX;
     if (base > SMEM_MAX) fail(KS_ERR_ARG, "plane kernel: %zu bytes of shared memory for N=%d", base, N);
     dim3 grid(N, n);
-    k_plane<N><<<grid, FCfg<N>::PT, pf_smem ? with_pf : base, s>>>(colbuf1_, colbuf2_, ncols_, t_.col_xy, g_.xr,
-                                                                   vplane_, nl_, pf_, nprojtot_, pf_smem, t_.tw);
+    k_plane<N><<<grid, FCfg<N>::PT, pf_smem ? with_pf : base, s>>>(cb1, colbuf2_, ncols_, t_.col_xy, g_.xr,
+                                                                   vplane_, nl_, pf, nprojtot_, pf_smem, t_.tw);
     KS_CHECK_LAUNCH();
   }
   template <int N> void launch_plane_inverse(int n, float2* out, cudaStream_t s) {
@@ -710,11 +1436,40 @@ class FusedImpl final : public FusedOps {
                                                                          out);
     KS_CHECK_LAUNCH();
   }
-  // states per density partial: a cluster of DCL states, or a chunk per CTA at N = 128
-  int density_chunk() const { return N_ >= 128 ? std::max(1, std::min(32, (ns_ + 7) / 8)) : DCL; }
+  // states per density partial: a chunk of states per CTA with the team transforms (about 16
+  // chunks, each CTA's partial an N^3 / N plane), else a cluster of DCL states, or a chunk per CTA
+  // at N = 128
+  bool team_density() const {
+    switch (N_) {
+      case 32: case 48: case 64: case 96: case 128: return true;
+      default: return false;
+    }
+  }
+  // variant 0: the team kernel (about 16 chunks); 1: a cluster of DCL states, or a chunk per CTA
+  // at N = 128
+  int density_chunk(int variant) const {
+    if (variant == 0 && team_density()) return std::max(1, (ns_ + 15) / 16);
+    return N_ >= 128 ? std::max(1, std::min(32, (ns_ + 7) / 8)) : DCL;
+  }
 
-  template <int N> void launch_density(int n, int nch, const double* occ, cudaStream_t s) {
+  template <int N> void launch_density(int n, const double* occ, cudaStream_t s, int variant) {
     const size_t smem = plane_smem<N>() + (size_t)N * N * sizeof(float);
+    const int nch = (n + density_chunk(variant) - 1) / density_chunk(variant);
+    if constexpr (TPlan<N>::ok) {
+      if (variant == 0) {
+        static bool attr = false;
+        if (!attr) {
+          KS_CUDA(cudaFuncSetAttribute(k_plane_density_team<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SMEM_MAX));
+          attr = true;
+        }
+        const size_t tsmem = plane_smem<N>() + (N == 96 ? (size_t)N * N * sizeof(float) : 0);
+        k_plane_density_team<N><<<dim3(N, nch), TCfg<N>::PT, tsmem, s>>>(
+            colbuf1_, ncols_, t_.col_xy, g_.xr, n, density_chunk(0), occ, (float)(1.0 / g_.omega), dpartial_, t_.tw);
+        KS_CHECK_LAUNCH();
+        return;
+      }
+    }
     if constexpr (N >= 128) {
       static bool attr = false;
       if (!attr) {
@@ -723,7 +1478,7 @@ class FusedImpl final : public FusedOps {
         attr = true;
       }
       k_plane_density_chunk<N><<<dim3(N, nch), FCfg<N>::PT, smem, s>>>(
-          colbuf1_, ncols_, t_.col_xy, g_.xr, n, density_chunk(), occ, (float)(1.0 / g_.omega), dpartial_, t_.tw);
+          colbuf1_, ncols_, t_.col_xy, g_.xr, n, density_chunk(1), occ, (float)(1.0 / g_.omega), dpartial_, t_.tw);
     } else {
       static bool attr = false;
       if (!attr) {
@@ -756,8 +1511,22 @@ class FusedImpl final : public FusedOps {
     ent_beta.clear();
     std::vector<std::vector<int>> byz(N_);
     for (size_t c = 0; c < g.cov_idx.size(); ++c) byz[g.cov_idx[c] % N_].push_back((int)c);
+    // within a plane, points in (y, x) order, with the offset of each y-line (the team plane
+    // kernel finds a point's value by its line's offset and a bitmap of x)
+    std::vector<int>& line_off = h_line_off_;
+    line_off.assign((size_t)N_ * (N_ + 1), 0);
+    nl_cap_ = 0;
     for (int z = 0; z < N_; ++z) {
-      for (int c : byz[z]) {
+      std::vector<int>& v = byz[z];
+      std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+        const int xa = g.cov_idx[a] / N_, xb = g.cov_idx[b] / N_;       // jx*N + jy
+        return (xa % N_) != (xb % N_) ? (xa % N_) < (xb % N_) : (xa / N_) < (xb / N_);
+      });
+      int* lo = line_off.data() + (size_t)z * (N_ + 1);
+      for (int c : v) lo[(g.cov_idx[c] / N_) % N_ + 1]++;
+      for (int y = 0; y < N_; ++y) lo[y + 1] += lo[y];
+      nl_cap_ = std::max(nl_cap_, (int)v.size());
+      for (int c : v) {
         pt_xy.push_back(g.cov_idx[c] / N_);
         for (int e = g.cov_off[c]; e < g.cov_off[c + 1]; ++e) {
           const int p = g.cov_ent[e];
@@ -775,7 +1544,9 @@ class FusedImpl final : public FusedOps {
     nl_.ent_off = upload(h_ent_off_);
     nl_.ent_proj = upload(h_ent_proj_);
     nl_.ent_beta = upload(h_ent_beta_);
+    nl_.line_off = upload(h_line_off_);
     nl_.nproj = g_.nproj;
+    nl_.cap = nl_cap_;
   }
 
   // B[atom*nproj + l][G] = c_G[beta_Il] = Omega^{1/2} N^-3 sum_j exp(-iG.r_j) beta_Il(r_j), by the
@@ -816,14 +1587,12 @@ class FusedImpl final : public FusedOps {
     // rows in chunks of whole atoms (the intermediate sums of a chunk stay below ~64 MB)
     const size_t per_row = (size_t)B * M * (B + M) * sizeof(float2);
     const int chunk = np * std::max(1, (int)std::min<size_t>(na, (size_t(64) << 20) / (per_row * np)));
-    float* dbox = nullptr;
-    int* dlo = nullptr;
-    float2 *T1 = nullptr, *T2 = nullptr;
+    // temporaries from the engine's arena (a server's pool when there is one), returned below
     const float2* tw = t_.tw;                                         // (cos, sin)(2 pi t / N), FP32
-    KS_CUDA(cudaMalloc(&dbox, box.size() * sizeof(float)));
-    KS_CUDA(cudaMalloc(&dlo, std::max<size_t>(1, lo.size()) * sizeof(int)));
-    KS_CUDA(cudaMalloc(&T1, (size_t)chunk * B * B * M * sizeof(float2)));
-    KS_CUDA(cudaMalloc(&T2, (size_t)chunk * B * M * M * sizeof(float2)));
+    float* dbox = alloc<float>(box.size());
+    int* dlo = alloc<int>(std::max<size_t>(1, lo.size()));
+    float2* T1 = alloc<float2>((size_t)chunk * B * B * M);
+    float2* T2 = alloc<float2>((size_t)chunk * B * M * M);
     KS_CUDA(cudaMemcpy(dbox, box.data(), box.size() * sizeof(float), cudaMemcpyHostToDevice));
     KS_CUDA(cudaMemcpy(dlo, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice));
     const float scale = (float)(std::sqrt(g.omega) / ((double)N * N * N));
@@ -840,11 +1609,11 @@ class FusedImpl final : public FusedOps {
       KS_CHECK_LAUNCH();
     }
     tc_overlap_prepare_a(B_, g.nG, nprojtot_, g.nG, Bimg_, nullptr);   // the operand split once
-    KS_CUDA(cudaStreamSynchronize(nullptr));
-    cudaFree(dbox);
-    cudaFree(dlo);
-    cudaFree(T1);
-    cudaFree(T2);
+    KS_CUDA(cudaStreamSynchronize(nullptr));                           // the temporaries are idle
+    arena_.release(dbox);
+    arena_.release(dlo);
+    arena_.release(T1);
+    arena_.release(T2);
   }
 
   template <typename U> U* alloc(size_t n) { return static_cast<U*>(arena_.alloc(n * sizeof(U))); }
@@ -864,6 +1633,8 @@ class FusedImpl final : public FusedOps {
   PlaneNL nl_{};
   std::vector<int> h_pt_off_, h_pt_xy_, h_ent_off_, h_ent_proj_;   // host copies of the plane lists
   std::vector<float> h_ent_beta_;
+  std::vector<int> h_line_off_;       // [N][N+1] per-plane y-line offsets of the covered points
+  int nl_cap_ = 0;                    // most covered points of any plane
   bool lists_ready_ = false;
   float2* colbuf1_ = nullptr;
   float2* colbuf2_ = nullptr;
@@ -879,6 +1650,14 @@ class FusedImpl final : public FusedOps {
 };
 
 }  // namespace
+
+void fused_apply_h_group(const std::vector<FusedGroupItem>& items, cudaStream_t s) {
+  FusedImpl::group_apply(items, s);
+}
+
+bool fused_same_geometry(const FusedOps* a, const FusedOps* b) {
+  return FusedImpl::same_geometry(static_cast<const FusedImpl*>(a), static_cast<const FusedImpl*>(b));
+}
 
 std::unique_ptr<FusedOps> make_fused_ops(const HostGeometry& g, const DevTables<float>& t, int nstates,
                                          DeviceArena& arena, StageProfiler& prof, int* err) {

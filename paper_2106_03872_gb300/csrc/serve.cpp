@@ -2,12 +2,16 @@
 //
 // Requests are queued by ks_serve_submit and admitted in arrival order while the device
 // memory they need fits the server's budget.  Every admitted request owns an engine (its
-// states, potentials and tables stay resident on the device) and a CUDA stream.  A pool of
-// worker threads runs the admitted requests in quanta -- one steepest-descent block
-// iteration or one ETRS step -- and puts each request back in the ready queue after its
-// quantum, so requests that arrive while others run are admitted as memory frees up and
-// their kernels overlap on the device with the running ones.  A finished request releases
-// its device memory; its results wait on the host until polled.
+// states, potentials and tables stay resident on the device) and a CUDA stream; the engines'
+// memory comes from the server's slab pool, so admitting and retiring a request neither
+// allocates nor frees device memory once the pool has grown (cudaFree would synchronise the
+// whole device).  A pool of worker threads runs the admitted requests in quanta -- one
+// steepest-descent block iteration or one ETRS step -- and puts each request back in the ready
+// queue after its quantum, so requests that arrive while others run are admitted as memory frees
+// up and their kernels overlap on the device with the running ones.  Real-time requests on one
+// grid geometry are batched: a worker takes up to eight of them that are ready and runs their
+// step in lockstep, each H application one packed launch over all their states.  A finished
+// request releases its device memory; its results wait on the host until polled.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -29,6 +33,7 @@ const char* last_error_cstr();
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr size_t kMaxGroup = 8;                  // real-time requests per lockstep group
 
 struct Request {
   uint64_t id = 0;
@@ -85,6 +90,7 @@ size_t estimate_bytes(const ks_cell_desc& d) {
 
 struct ks_server_s {
   size_t budget = 0, in_use = 0;
+  std::unique_ptr<ks::DevicePool> pool;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<ks::Request*> pending;   // waiting for admission
@@ -112,6 +118,7 @@ void finish(ks_server_s* s, Request* r, ks_status st, const std::string& err) {
       st = e.st;
     }
   }
+  if (r->stream) cudaStreamSynchronize(r->stream);   // the engine's blocks go back to the pool idle
   r->eng.reset();
   if (r->stream) {
     cudaStreamDestroy(r->stream);
@@ -128,9 +135,9 @@ void finish(ks_server_s* s, Request* r, ks_status st, const std::string& err) {
 }
 
 // Create the engine and initial states of an admitted request (worker thread, no lock).
-void start(Request* r) {
+void start(ks_server_s* s, Request* r) {
   KS_CUDA(cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking));
-  r->eng = make_engine(r->desc);
+  r->eng = make_engine(r->desc, s->pool.get());
   if (!r->c0.empty()) {
     r->eng->set_states(r->c0.data(), r->stream);
     r->c0.clear();
@@ -142,10 +149,30 @@ void start(Request* r) {
   if (r->kind == 0) r->result.assign(r->desc.nstates, 0.0);
 }
 
+// One ETRS step of a group of started real-time requests in lockstep (td_step_engines) on the
+// first one's stream, after the work already queued on the others' streams.
+void td_group_quantum(const std::vector<Request*>& g) {
+  std::vector<EngineBase*> es;
+  for (Request* r : g) es.push_back(r->eng.get());
+  cudaStream_t s0 = g[0]->stream;
+  for (size_t i = 1; i < g.size(); ++i) {
+    cudaEvent_t ev;
+    KS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    KS_CUDA(cudaEventRecord(ev, g[i]->stream));
+    KS_CUDA(cudaStreamWaitEvent(s0, ev, 0));
+    KS_CUDA(cudaEventDestroy(ev));
+  }
+  std::vector<double> nrm(g.size()), e(g.size());
+  td_step_engines(es, g[0]->dt, 1, nrm.data(), e.data(), s0);      // synchronous on s0
+  for (size_t i = 0; i < g.size(); ++i) g[i]->result.push_back(e[i]);
+}
+
 // One quantum; returns true when the request has done all its work.
 bool quantum(Request* r) {
   if (r->kind == 0) {
     r->eng->block_iteration(1, r->result.data(), r->stream);
+  } else if (r->eng->precision() == KS_MIXED_BF16X3) {
+    td_group_quantum(std::vector<Request*>{r});      // the same kernels as in a group
   } else {
     double nrm = 0, e = 0;
     r->eng->td_steps(r->dt, 1, 0, 1, &nrm, &e, nullptr, r->stream);
@@ -174,32 +201,50 @@ void worker_loop(ks_server_s* s) {
     }
     Request* r = s->ready.front();
     s->ready.pop_front();
-    ++s->running;
+    // a started real-time request takes along the ready ones it can share launches with
+    std::vector<Request*> group{r};
+    if (r->kind == 1 && r->done >= 0 && r->eng) {
+      for (auto it = s->ready.begin(); it != s->ready.end() && group.size() < kMaxGroup;) {
+        Request* q = *it;
+        if (q->kind == 1 && q->done >= 0 && q->eng && q->dt == r->dt && td_groupable(r->eng.get(), q->eng.get())) {
+          group.push_back(q);
+          it = s->ready.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    s->running += (int)group.size();
     lk.unlock();
     ks_status st = KS_OK;
     std::string err;
-    bool complete = false;
+    std::vector<bool> complete(group.size(), false);
     try {
-      if (r->done < 0) {
+      if (group.size() > 1) {
+        td_group_quantum(group);
+        for (size_t i = 0; i < group.size(); ++i) complete[i] = ++group[i]->done >= group[i]->count;
+      } else if (r->done < 0) {
         r->done = 0;
-        start(r);
-        complete = r->count <= 0;
+        start(s, r);
+        complete[0] = r->count <= 0;
       } else {
-        complete = quantum(r);
+        complete[0] = quantum(r);
       }
     } catch (const Error& e) {
       st = e.st;
       err = std::string("request failed: ") + last_error_cstr();
-      complete = true;
+      complete.assign(group.size(), true);
     } catch (...) {
       st = KS_ERR_CUDA;
       err = "request failed";
-      complete = true;
+      complete.assign(group.size(), true);
     }
-    if (complete) finish(s, r, st, err);
+    for (size_t i = 0; i < group.size(); ++i)
+      if (complete[i]) finish(s, group[i], st, err);
     lk.lock();
-    --s->running;
-    if (!complete) s->ready.push_back(r);
+    s->running -= (int)group.size();
+    for (size_t i = 0; i < group.size(); ++i)
+      if (!complete[i]) s->ready.push_back(group[i]);
     s->cv_work.notify_all();
   }
 }
@@ -211,9 +256,14 @@ void worker_loop(ks_server_s* s) {
 extern "C" {
 
 ks_status ks_serve_create(size_t mem_budget_bytes, ks_server* out) {
+  return ks_serve_create_ex(mem_budget_bytes, 0, out);
+}
+
+ks_status ks_serve_create_ex(size_t mem_budget_bytes, int workers, ks_server* out) {
   if (out) *out = nullptr;
   try {
     if (!out) ks::fail(KS_ERR_ARG, "out is NULL");
+    if (workers < 0 || workers > 64) ks::fail(KS_ERR_ARG, "workers=%d outside [0, 64]", workers);
     std::unique_ptr<ks_server_s> s(new ks_server_s);
     if (cudaGetDevice(&s->device) != cudaSuccess) {   // no device: requests fail when started
       cudaGetLastError();
@@ -225,7 +275,8 @@ ks_status ks_serve_create(size_t mem_budget_bytes, ks_server* out) {
       mem_budget_bytes = (size_t)(0.8 * (double)fr);
     }
     s->budget = mem_budget_bytes;
-    const int nworkers = 4;
+    s->pool.reset(new ks::DevicePool(size_t(1) << 30));
+    const int nworkers = workers > 0 ? workers : 4;
     for (int i = 0; i < nworkers; ++i) s->workers.emplace_back(ks::worker_loop, s.get());
     *out = s.release();
     return KS_OK;

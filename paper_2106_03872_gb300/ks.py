@@ -17,16 +17,19 @@ KS_OK, KS_ERR_ARG, KS_ERR_NOMEM, KS_ERR_NOT_POSDEF, KS_ERR_DIVERGED, KS_ERR_TIME
     KS_ERR_STATE = range(9)
 STATUS_NAMES = ["KS_OK", "KS_ERR_ARG", "KS_ERR_NOMEM", "KS_ERR_NOT_POSDEF", "KS_ERR_DIVERGED", "KS_ERR_TIMEOUT",
                 "KS_ERR_CUDA", "KS_PENDING", "KS_ERR_STATE"]
-KS_FP64, KS_MIXED_BF16X3, KS_MIXED_TF32 = 0, 1, 2
-PRECISIONS = {"fp64": KS_FP64, "bf16x3": KS_MIXED_BF16X3, "tf32": KS_MIXED_TF32}
+KS_FP64, KS_MIXED_BF16X3 = 0, 1
+PRECISIONS = {"fp64": KS_FP64, "bf16x3": KS_MIXED_BF16X3}
 
 # Every symbol declared in include/ks.h.
 EXPORTS = ["ks_count_gvectors", "ks_grid_create", "ks_grid_destroy", "ks_grid_gvectors", "ks_grid_device_bytes",
            "ks_get_vloc", "ks_set_states", "ks_get_states", "ks_states_device", "ks_apply_h", "ks_apply_h_host",
-           "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_block_iteration_pc", "ks_scf", "ks_td_step", "ks_td_step_dipole", "ks_kick", "ks_dipole", "ks_forces",
+           "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_block_iteration_pc", "ks_set_option", "ks_scf", "ks_td_step", "ks_td_step_dipole", "ks_kick", "ks_dipole", "ks_forces",
            "ks_set_positions", "ks_get_positions", "ks_ehrenfest",
-           "ks_serve_create", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info",
-           "ks_profile", "ks_profile_read", "ks_profile_span", "ks_kernel_launches", "ks_overlap_noalloc", "ks_last_error"]
+           "ks_serve_create", "ks_serve_create_ex", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info",
+           "ks_profile", "ks_profile_read", "ks_profile_span", "ks_kernel_launches", "ks_tc_status_check", "ks_autotune_report", "ks_overlap_noalloc", "ks_last_error"]
+
+
+KS_OPT_FP64_SUBSPACE = 1
 
 
 class KsError(RuntimeError):
@@ -90,6 +93,10 @@ def load():
         "ks_serve_poll": [P, ct.c_uint64, ct.c_int, dp, dp, dp],
         "ks_serve_result_info": [P, ct.c_uint64, ip, ip, ip],
         "ks_overlap_noalloc": [P, P, ct.c_int, ct.c_int, ct.c_int, ct.c_int, P, P],
+        "ks_set_option": [P, ct.c_int, ct.c_int],
+        "ks_tc_status_check": [ct.c_int],
+        "ks_autotune_report": [ct.c_char_p, ct.c_size_t, ct.POINTER(ct.c_size_t)],
+        "ks_serve_create_ex": [ct.c_size_t, ct.c_int, ct.POINTER(P)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -142,6 +149,16 @@ def overlap_noalloc(a_ptr, b_ptr, m, n, nG, fp64, out_ptr, stream=None):
     """out = A^H B ([m][n] complex128, device) without any device allocation (see ks.h)."""
     check(load().ks_overlap_noalloc(ct.c_void_p(a_ptr), ct.c_void_p(b_ptr), int(m), int(n), int(nG),
                                     1 if fp64 else 0, ct.c_void_p(out_ptr), _stream_ptr(stream)))
+
+
+def autotune_report():
+    """The autotuner's decisions so far (list of dicts: key, per-candidate ms, choice)."""
+    import json
+    n = ct.c_size_t(0)
+    check(load().ks_autotune_report(None, 0, ct.byref(n)))
+    buf = ct.create_string_buffer(max(1, n.value))
+    check(load().ks_autotune_report(buf, n.value, ct.byref(n)))
+    return json.loads(buf.value.decode() or "[]")
 
 
 def kernel_launches():
@@ -202,6 +219,10 @@ class Grid:
         v = np.zeros(self.N ** 3)
         check(load().ks_get_vloc(self.h, _dptr(v)))
         return v.reshape(self.N, self.N, self.N)
+
+    def set_option(self, option, value):
+        """KS_OPT_FP64_SUBSPACE (1): FP64 Cholesky and Rayleigh-Ritz on a mixed handle."""
+        check(load().ks_set_option(self.h, int(option), int(value)))
 
     # --- states
     def set_states(self, c):
@@ -360,9 +381,9 @@ class Grid:
 class Server:
     """Owns a ks_server (continuous batching of independent calculations)."""
 
-    def __init__(self, budget_bytes=0):
+    def __init__(self, budget_bytes=0, workers=0):
         self.h = ct.c_void_p()
-        check(load().ks_serve_create(ct.c_size_t(int(budget_bytes)), ct.byref(self.h)))
+        check(load().ks_serve_create_ex(ct.c_size_t(int(budget_bytes)), int(workers), ct.byref(self.h)))
         self._descs = {}
 
     def close(self):

@@ -65,3 +65,13 @@ def test_make_desc_marshals_cell(ks):
     d = ks.make_desc(cell, "fp64")
     assert d.N == 24 and d.natoms == 4 and d.nstates == 8 and d.prec == ks.KS_FP64
     assert abs(d.pos[5] - cell["pos"][1, 2]) == 0.0
+
+
+def test_tensor_core_wait_expiry_reports_cuda_error(ks):
+    """The host side of the bounded mbarrier waits: a nonzero error word becomes KS_ERR_CUDA with
+    a message; zero is success.  (No kernel is made to time out: the word is what a kernel whose
+    wait expired leaves behind.)"""
+    lib = ks.load()
+    assert lib.ks_tc_status_check(0) == ks.KS_OK
+    assert lib.ks_tc_status_check(1) == ks.KS_ERR_CUDA
+    assert b"bounded wait expired" in lib.ks_last_error()

@@ -108,6 +108,22 @@ def test_gs96_block_iteration_mixed_and_refined(ks, meas):
     dump("gs96_mixed_eps.json", {"eps": eps.tolist(), "eps_refined": e_sub.tolist()})
 
 
+def test_gs96_block_iteration_mixed_fp64_subspace(ks, meas):
+    """The precision plan that keeps FP64 for the Cholesky of S and the Rayleigh-Ritz
+    diagonalisation (KS_OPT_FP64_SUBSPACE) on the mixed path: 20 iterations against the golden,
+    at the mixed path's bound (the states are complex64 either way)."""
+    gd = golden("gs96_block_iteration.json")
+    cell = inputs.cell("gs96")
+    g = ks.Grid(cell, prec="bf16x3")
+    g.set_option(ks.KS_OPT_FP64_SUBSPACE, 1)
+    g.set_states(inputs.random_coeffs(cell["seed"], cell["nstates"], g.nG))
+    eps = g.block_iteration(20)
+    ref = np.asarray(gd["eps"][19])
+    meas("gs96 mixed + FP64 subspace, Ritz values after 20 iterations, max |d| / max |eps|",
+         np.max(np.abs(eps - ref)) / np.max(np.abs(ref)), 1e-4)
+    g.close()
+
+
 # ------------------------------------------------------------------------------------------------
 # td64: 200 ETRS steps with Hartree + Slater, the reduced real-time workload
 # ------------------------------------------------------------------------------------------------

@@ -104,3 +104,36 @@ def test_poll_reports_pending_then_result(ks):
     assert np.all(np.diff(res) < 0)
     assert abs(res[-1] - res[0]) <= 1e-2 * abs(res[0])
     srv.close()
+
+
+def test_grouped_realtime_requests_same_as_alone(ks):
+    """Real-time requests on one grid geometry (32^3 and 64^3, different state and atom counts)
+    are stepped in lockstep groups with packed launches; each result equals the request run alone
+    through ks_td_step to 1e-12 (the same kernels act on the same data)."""
+    rng = np.random.default_rng(91)
+    reqs = []
+    for k, (L, N) in enumerate([(12.0, 32)] * 5 + [(20.0, 64)] * 3):
+        ns = int(rng.integers(3, 11))
+        na = int(rng.integers(1, 5))
+        cell = inputs.small_cell(L, N, na, ns, 300 + k, depth=-3.0)
+        reqs.append(dict(cell=cell, kind=1, count=3, seed=300 + k))
+    srv = ks.Server(0, workers=2)
+    tickets = []
+    for r in reqs:
+        nG = ks.count_gvectors(r["cell"]["L"], r["cell"]["N"], 20.0)
+        c0 = inputs.random_coeffs(r["seed"], r["cell"]["nstates"], nG)
+        tickets.append(srv.submit(r["cell"], 1, r["count"], 0.05, c0=c0, prec="bf16x3"))
+    got = [wait(srv, ks, t) for t in tickets]
+    srv.close()
+    for r, (st, res, states, lat) in zip(reqs, got):
+        assert st == ks.KS_OK, ks.load().ks_last_error()
+        ref_res, ref_states = run_alone(ks, r, "bf16x3")
+        assert np.max(np.abs(res - ref_res)) <= 1e-12 * max(1.0, np.max(np.abs(ref_res)))
+        assert np.max(np.abs(states - ref_states)) <= 1e-12 * np.max(np.abs(ref_states))
+
+
+def test_server_worker_count_validated(ks):
+    for bad in (-1, 65):
+        with pytest.raises(ks.KsError) as e:
+            ks.Server(0, workers=bad)
+        assert e.value.status == ks.KS_ERR_ARG
