@@ -25,12 +25,13 @@ def main(argv=None):
     ap.add_argument("--iterations", type=int, default=1, help="block iterations (ground state)")
     ap.add_argument("--td-steps", type=int, default=0, help="ETRS time steps after the iterations")
     ap.add_argument("--dt", type=float, default=0.05)
+    ap.add_argument("--states", type=int, default=0, help="states of the cell (0: the cell's own count)")
     ap.add_argument("--timeline", action="store_true",
                     help="after one warm-up iteration, print the stage spans of the block iterations "
                          "(main and side stream, ms on a common clock)")
     args = ap.parse_args(argv)
 
-    cell = inputs.cell(args.cell)
+    cell = inputs.cell(args.cell, nstates=args.states or None)
     g = ks.Grid(cell, prec=args.prec)
     g.set_states(inputs.random_coeffs(cell["seed"], cell["nstates"], g.nG))
     if args.timeline:
