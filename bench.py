@@ -32,7 +32,7 @@ UNIT = "state·gridpts/s"
 WORKLOAD = "gs96"
 CPU_SAMPLE_STATES = 4
 BASE_SERVE_SEED = 20210612
-SERVE_WORKERS = 8
+SERVE_WORKERS = 32
 
 
 def peaks():
@@ -661,15 +661,16 @@ def serve_bench(ks, inputs, nreq, nreq_load):
                 if st not in (ks.KS_PENDING, ks.KS_ERR_TIMEOUT):
                     raise RuntimeError("serving request failed: %s" % ks.load().ks_last_error())
         span = time.perf_counter() - t0
+        stats = srv.stats()
         srv.close()
-        return span, np.array(lat)
+        return span, np.array(lat), stats
 
-    span, lat = run(None, reqs)
+    span, lat, stats = run(None, reqs)
     sat = nreq / span
     loads = []
     sub = reqs[:nreq_load]
     for frac in (0.5, 0.8, 0.95):
-        sp, la = run(frac * sat, sub)
+        sp, la, _ = run(frac * sat, sub)
         loads.append({"load": frac, "rate_req_per_s": frac * sat, "requests": len(sub),
                       "p50_s": float(np.percentile(la, 50)), "p99_s": float(np.percentile(la, 99)),
                       "throughput_req_per_s": len(sub) / sp})
@@ -677,7 +678,7 @@ def serve_bench(ks, inputs, nreq, nreq_load):
     return {"requests": nreq, "workers": SERVE_WORKERS, "saturated_req_per_s": sat,
             "saturated_state_gridpts_steps_per_s": gp / span, "saturated_s": span,
             "saturated_p50_s": float(np.percentile(lat, 50)), "saturated_p99_s": float(np.percentile(lat, 99)),
-            "loads": loads,
+            "saturated_worker_stats": stats, "loads": loads,
             "workload": "seeded requests of the serving workload: N in {32,48,64,96} (L = 0.3125 N), 8-256 "
                         "states, 4-64 atoms at uniform positions, half 10 block iterations and half 50 ETRS "
                         "steps (dt 0.05, Hartree + Slater), mixed precision; %d requests at saturation, the "

@@ -277,9 +277,10 @@ ks_status ks_dipole(ks_grid g, double* d_out, void* stream);
  * requests does not synchronise the device.  Real-time requests (kind 1) of mixed precision on
  * one grid geometry (same L, N, ecut) are stepped together, up to eight at a time, each H
  * application of their ETRS step one packed launch over all their states; a request's results
- * are the same alone and in such a group.  ks_serve_create starts 4 workers. */
+ * are the same alone and in such a group.  ks_serve_create starts 16 workers (each runs one
+ * request's or group's quantum at a time, so long single-SM quanta do not hold the others). */
 ks_status ks_serve_create(size_t mem_budget_bytes, ks_server* out);
-/* Same with `workers` worker threads (1..64; 0: the default of 4). */
+/* Same with `workers` worker threads (1..64; 0: the default of 16). */
 ks_status ks_serve_create_ex(size_t mem_budget_bytes, int workers, ks_server* out);
 /* Stops the scheduler after the running requests finish; pending ones are dropped. */
 ks_status ks_serve_destroy(ks_server s);
@@ -299,6 +300,14 @@ ks_status ks_serve_submit(ks_server s, const ks_cell_desc* desc, const double* c
  * the ticket is then released. */
 ks_status ks_serve_poll(ks_server s, uint64_t ticket, int timeout_ms, double* result_out,
                         double* c_out_opt, double* latency_s_opt);
+
+/* Counters of a server since its creation (no counterpart in the paper), out[0..nout-1] of:
+ * worker seconds spent creating requests' engines and initial states, in ground-state quanta
+ * (block iterations), in real-time steps (each group step counted once), in retiring requests;
+ * then the number of request starts, ground-state quanta, real-time group steps, request-steps
+ * in those groups (their ratio is the mean group size), and the bytes the server's device pool
+ * holds.  nout <= 9. */
+ks_status ks_serve_stats(ks_server s, double* out, int nout);
 
 /* Result sizes for a ticket: number of doubles in result_out, nstates, nG. */
 ks_status ks_serve_result_info(ks_server s, uint64_t ticket, int* nresult, int* nstates, int* nG);

@@ -25,7 +25,8 @@ namespace ks {
 
 namespace {
 
-constexpr int C32_MAXN = 160;
+constexpr int C32_MAXN = 160;          // square array in shared memory
+constexpr int C32_MAXN_GLOBAL = 256;   // square array in global memory
 constexpr int C32_THREADS = 1024;
 
 // One CTA.  Reads the lower triangle of S (n x n, row-major), writes X = L^{-1} (lower,
@@ -52,14 +53,17 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
   return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
+// MAXN: the largest n; GLB: the square array lives in global memory (gU, n (n + 1) values,
+// L2-resident) instead of shared memory, for n beyond what shared memory holds (160 < n <= 256).
+template <int MAXN, bool GLB>
 __global__ void __launch_bounds__(C32_THREADS, 1)
     k_chol32_inverse(const double2* __restrict__ S, int n, double tol, int conj_out, int* __restrict__ status,
-                     double2* __restrict__ Out, float2* __restrict__ Out32) {
+                     double2* __restrict__ Out, float2* __restrict__ Out32, float2* __restrict__ gU) {
   extern __shared__ float2 c32[];
   const int ld = n + 1;
-  float2* U = c32;
-  __shared__ float sjj[C32_MAXN];
-  __shared__ float2 xd[C32_MAXN];                                    // diagonal of X
+  float2* U = GLB ? gU : c32;
+  __shared__ float sjj[MAXN];
+  __shared__ float2 xd[MAXN];                                        // diagonal of X
   __shared__ int s_bad;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   constexpr int NW = C32_THREADS / 32;
@@ -151,9 +155,9 @@ __global__ void __launch_bounds__(C32_THREADS, 1)
     const int rows = n - J1;
     if (rows == 0) break;
     // (b) panel: L_ic = sum_{k=J}^{c} A_ik conj(W_ck); lanes run along i
-    float2 pv[(C32_MAXN * CB + C32_THREADS - 1) / C32_THREADS];
+    float2 pv[(MAXN * CB + C32_THREADS - 1) / C32_THREADS];
 #pragma unroll
-    for (int q = 0; q < (C32_MAXN * CB + C32_THREADS - 1) / C32_THREADS; ++q) {
+    for (int q = 0; q < (MAXN * CB + C32_THREADS - 1) / C32_THREADS; ++q) {
       const int idx = t + q * C32_THREADS;
       pv[q] = make_float2(0.f, 0.f);
       if (idx < rows * jb) {
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(C32_THREADS, 1)
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < (C32_MAXN * CB + C32_THREADS - 1) / C32_THREADS; ++q) {
+    for (int q = 0; q < (MAXN * CB + C32_THREADS - 1) / C32_THREADS; ++q) {
       const int idx = t + q * C32_THREADS;
       if (idx < rows * jb) UL(J1 + idx % rows, J + idx / rows) = pv[q];
     }
@@ -222,9 +226,9 @@ __global__ void __launch_bounds__(C32_THREADS, 1)
     }
     __syncthreads();
     // X_rc = -sum_{r'=I0}^{r} W_I[r][r'] T_r'c
-    float2 xv[(CB * C32_MAXN + C32_THREADS - 1) / C32_THREADS];
+    float2 xv[(CB * MAXN + C32_THREADS - 1) / C32_THREADS];
 #pragma unroll
-    for (int q = 0; q < (CB * C32_MAXN + C32_THREADS - 1) / C32_THREADS; ++q) {
+    for (int q = 0; q < (CB * MAXN + C32_THREADS - 1) / C32_THREADS; ++q) {
       const int idx = t + q * C32_THREADS;
       xv[q] = make_float2(0.f, 0.f);
       if (idx < ib * I0) {
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(C32_THREADS, 1)
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < (CB * C32_MAXN + C32_THREADS - 1) / C32_THREADS; ++q) {
+    for (int q = 0; q < (CB * MAXN + C32_THREADS - 1) / C32_THREADS; ++q) {
       const int idx = t + q * C32_THREADS;
       if (idx < ib * I0) XU(I0 + idx % ib, idx / ib) = xv[q];
     }
@@ -353,30 +357,40 @@ __global__ void __launch_bounds__(64) k_tri_product(const double2* __restrict__ 
 
 }  // namespace
 
-size_t cholesky_mixed_workspace(int n) { return (size_t)3 * n * n; }
+// M1, T, S2 (n^2 complex128 each), then for n > C32_MAXN the FP32 square array in global memory
+size_t cholesky_mixed_workspace(int n) {
+  return (size_t)3 * n * n + (n > C32_MAXN ? ((size_t)n * (n + 1) + 1) / 2 : 0);
+}
 
 void cholesky_inverse_mixed(const double2* S, double2* M, int n, double tol, double2* work, int* status,
                             cudaStream_t s, float2* M32, bool refine) {
-  if (n > C32_MAXN) fail(KS_ERR_ARG, "cholesky_inverse_mixed: n=%d > %d", n, C32_MAXN);
-  const size_t smem = (size_t)n * (n + 1) * sizeof(float2);           // square [n][n+1]
+  if (n > C32_MAXN_GLOBAL) fail(KS_ERR_ARG, "cholesky_inverse_mixed: n=%d > %d", n, C32_MAXN_GLOBAL);
+  const bool glb = n > C32_MAXN;
+  const size_t smem = glb ? 0 : (size_t)n * (n + 1) * sizeof(float2);   // square [n][n+1]
   static bool attr_set = false;
   if (!attr_set) {
-    KS_CUDA(cudaFuncSetAttribute(k_chol32_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    KS_CUDA(cudaFuncSetAttribute(k_chol32_inverse<C32_MAXN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)((size_t)C32_MAXN * (C32_MAXN + 1) * sizeof(float2))));
     attr_set = true;
   }
   double2* M1 = work;
   double2* T = work + (size_t)n * n;
   double2* S2 = work + (size_t)2 * n * n;
-  if (!refine) {                                                     // the FP32 factor itself
-    k_chol32_inverse<<<1, C32_THREADS, smem, s>>>(S, n, tol, 1, status, M, M32);
+  float2* gU = reinterpret_cast<float2*>(work + (size_t)3 * n * n);
+  auto factor = [&](int conj_out, double2* out, float2* out32) {
+    if (glb)
+      k_chol32_inverse<C32_MAXN_GLOBAL, true><<<1, C32_THREADS, 0, s>>>(S, n, tol, conj_out, status, out, out32, gU);
+    else
+      k_chol32_inverse<C32_MAXN, false><<<1, C32_THREADS, smem, s>>>(S, n, tol, conj_out, status, out, out32, nullptr);
     KS_CHECK_LAUNCH();
+  };
+  if (!refine) {                                                     // the FP32 factor itself
+    factor(1, M, M32);
     return;
   }
   const int nt = (n + 7) / 8;
   const dim3 grid(nt, nt);
-  k_chol32_inverse<<<1, C32_THREADS, smem, s>>>(S, n, tol, 0, status, M1, nullptr);
-  KS_CHECK_LAUNCH();
+  factor(0, M1, nullptr);
   k_tri_product<0><<<grid, 64, 0, s>>>(S, M1, n, status, T, nullptr);
   KS_CHECK_LAUNCH();
   k_tri_product<1><<<grid, 64, 0, s>>>(M1, T, n, status, S2, nullptr);   // S2 = M1 S M1^H (lower)

@@ -313,6 +313,110 @@ __global__ void __launch_bounds__(1024) k_jacobi(double2* __restrict__ A, double
   }
 }
 
+// The same parallel round-robin Jacobi in FP32 for the mixed path's subspace problems of
+// 128 < n <= 256 (the one-CTA Householder solver holds n <= 128 in shared memory): A (FP32,
+// destroyed) and the eigenvector columns V in global memory, L2-resident; rotations of pairs
+// whose coupling is below 1e-6 |A|_F are skipped (FP32 rounding of a rotated entry is ~6e-8
+// |A|), so the sweeps stop once the off-diagonal part is at FP32 level.  No sorting: the caller
+// takes FP64 Rayleigh quotients of the vectors, then sorts (eigh_jacobi_mixed).
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 cconjf(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscalef(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+__global__ void __launch_bounds__(1024) k_jacobi32(float2* __restrict__ A, float2* __restrict__ V, int n) {
+  __shared__ int sp[256], sq[256];
+  __shared__ float sc[256], ss[256];
+  __shared__ float2 se[256];
+  __shared__ int srot;
+  __shared__ float sthr;
+  __shared__ float red[32];
+  const int P = n + (n & 1);
+  const int np = P / 2;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = make_float2((e / n == e % n) ? 1.f : 0.f, 0.f);
+  float f = 0.f;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) f += A[e].x * A[e].x + A[e].y * A[e].y;
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += red[w];
+    sthr = 1e-6f * sqrtf(t);
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (threadIdx.x == 0) srot = 0;
+    __syncthreads();
+    for (int r = 0; r < P - 1; ++r) {
+      if (threadIdx.x < np) {
+        const int k = threadIdx.x;
+        const int pa = k, pb = P - 1 - k;
+        const int ua = (pa == 0) ? 0 : 1 + ((pa - 1 + r) % (P - 1));
+        const int ub = (pb == 0) ? 0 : 1 + ((pb - 1 + r) % (P - 1));
+        const int p = min(ua, ub), q = max(ua, ub);
+        int active = 0;
+        if (q < n) {
+          const float2 b = A[(size_t)p * n + q];
+          const float mag = hypotf(b.x, b.y);
+          if (mag > sthr) {
+            const float alpha = A[(size_t)p * n + p].x, gamma = A[(size_t)q * n + q].x;
+            const float tau = (gamma - alpha) / (2.f * mag);
+            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            const float c = 1.f / sqrtf(1.f + t * t);
+            sc[k] = c;
+            ss[k] = t * c;
+            se[k] = make_float2(b.x / mag, b.y / mag);
+            active = 1;
+            srot = 1;
+          }
+        }
+        sp[k] = p;
+        sq[k] = active ? q : -1;
+      }
+      __syncthreads();
+      for (int job = threadIdx.x; job < np * n; job += blockDim.x) {     // rows: A <- J^H A
+        const int k = job / n, j = job % n;
+        const int q = sq[k];
+        if (q < 0) continue;
+        const int p = sp[k];
+        const float c = sc[k], sv = ss[k];
+        const float2 e = se[k];
+        const float2 ap = A[(size_t)p * n + j], aq = A[(size_t)q * n + j];
+        A[(size_t)p * n + j] = cscalef(ap, c) - cscalef(cmulf(e, aq), sv);
+        A[(size_t)q * n + j] = cscalef(cmulf(cconjf(e), ap), sv) + cscalef(aq, c);
+      }
+      __syncthreads();
+      for (int job = threadIdx.x; job < np * n; job += blockDim.x) {     // columns: A <- A J, V <- V J
+        const int k = job / n, i = job % n;
+        const int q = sq[k];
+        if (q < 0) continue;
+        const int p = sp[k];
+        const float c = sc[k], sv = ss[k];
+        const float2 e = se[k];
+        float2 ap = A[(size_t)i * n + p], aq = A[(size_t)i * n + q];
+        A[(size_t)i * n + p] = cscalef(ap, c) - cscalef(cmulf(cconjf(e), aq), sv);
+        A[(size_t)i * n + q] = cscalef(cmulf(e, ap), sv) + cscalef(aq, c);
+        ap = V[(size_t)i * n + p];
+        aq = V[(size_t)i * n + q];
+        V[(size_t)i * n + p] = cscalef(ap, c) - cscalef(cmulf(cconjf(e), aq), sv);
+        V[(size_t)i * n + q] = cscalef(cmulf(e, ap), sv) + cscalef(aq, c);
+      }
+      __syncthreads();
+    }
+    if (srot == 0) break;
+    __syncthreads();
+  }
+}
+
+__global__ void k_c128_to_c64(const double2* __restrict__ in, float2* __restrict__ out, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = make_float2((float)in[e].x, (float)in[e].y);
+}
+__global__ void k_c64_to_c128(const float2* __restrict__ in, double2* __restrict__ out, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = make_double2((double)in[e].x, (double)in[e].y);
+}
+
 // lam[i] = v_i^H H v_i / v_i^H v_i in FP64 (column i of V), one CTA per i.
 __global__ void k_rayleigh_quotients(const double2* __restrict__ H, const double2* __restrict__ V, int n,
                                      double* __restrict__ lam) {
@@ -483,6 +587,25 @@ void cholesky_inverse(double2* A, double2* M, int n, int* status, cudaStream_t s
 void cholesky_inverse_tol(double2* A, double2* M, int n, double tol, int* status, cudaStream_t s) {
   if (n > 512) fail(KS_ERR_ARG, "cholesky: n=%d > 512", n);
   k_cholesky_inverse<<<1, 512, 0, s>>>(A, M, n, tol, status);
+  KS_CHECK_LAUNCH();
+}
+
+void eigh_jacobi_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, float2* work, int n,
+                       cudaStream_t s) {
+  if (n > 256 || n < 1) fail(KS_ERR_ARG, "eigh_jacobi_mixed: n=%d not in [1, 256]", n);
+  const size_t nn = (size_t)n * n;
+  float2* A32 = work;
+  float2* V32 = work + nn;
+  const unsigned nb = (unsigned)std::min<size_t>((nn + 255) / 256, 1024);
+  k_c128_to_c64<<<nb, 256, 0, s>>>(A, A32, nn);
+  KS_CHECK_LAUNCH();
+  k_jacobi32<<<1, 1024, 0, s>>>(A32, V32, n);
+  KS_CHECK_LAUNCH();
+  k_c64_to_c128<<<nb, 256, 0, s>>>(V32, V, nn);
+  KS_CHECK_LAUNCH();
+  k_rayleigh_quotients<<<n, 256, 0, s>>>(A, V, n, lam);
+  KS_CHECK_LAUNCH();
+  k_sort_vectors<<<1, 128, 0, s>>>(lam, V, n, eig, Vt);
   KS_CHECK_LAUNCH();
 }
 

@@ -545,10 +545,7 @@ template <typename T> class Engine final : public EngineBase {
     }
     {
       ProfScope p(prof, "eigh", s);
-      if (sizeof(T) == 4 && n <= 128 && !fp64_subspace_)
-        eigh_mixed(mA_, mV_, lam_, eig_, mM_, n, s);
-      else
-        jacobi_eigh(mA_, mV_, eig_, mM_, n, s);
+      eigh_sub(n, mM_, s);
     }
     ProfScope p(prof, "rotate", s);
     C* o1 = spare(psi_, hpsi_);
@@ -635,10 +632,7 @@ template <typename T> class Engine final : public EngineBase {
         }
         {
           ProfScope p(prof, "eigh", aux_);
-          if (mixed_sub && n <= 128)
-            eigh_mixed(mA_, mV_, lam_, eig_, mT_, n, aux_);
-          else
-            jacobi_eigh(mA_, mV_, eig_, mT_, n, aux_);
+          eigh_sub(n, mT_, aux_);
         }
         {
           ProfScope p(prof, "subspace", aux_);
@@ -1288,7 +1282,18 @@ template <typename T> class Engine final : public EngineBase {
     fail(KS_ERR_STATE, "internal: no spare state buffer");
   }
   bool use_tc() const { return sizeof(T) == 4 && prec_ == KS_MIXED_BF16X3; }
-  bool mixed_cholesky() const { return sizeof(T) == 4 && ns_ <= 160; }
+  bool mixed_cholesky() const { return sizeof(T) == 4 && ns_ <= 256; }
+  // the mixed path's FP32 eigensolver: one-CTA Householder for n <= 128, one-CTA FP32 Jacobi up
+  // to 256 (both finished by FP64 Rayleigh quotients); FP64 Jacobi beyond, or with
+  // KS_OPT_FP64_SUBSPACE
+  void eigh_sub(int n, double2* Vt, cudaStream_t s) {
+    if (sizeof(T) == 4 && !fp64_subspace_ && n <= 128)
+      eigh_mixed(mA_, mV_, lam_, eig_, Vt, n, s);
+    else if (sizeof(T) == 4 && !fp64_subspace_ && n <= 256)
+      eigh_jacobi_mixed(mA_, mV_, lam_, eig_, Vt, reinterpret_cast<float2*>(mF_), n, s);
+    else
+      jacobi_eigh(mA_, mV_, eig_, Vt, n, s);
+  }
   // KS_OPT_FP64_SUBSPACE on a mixed handle: the Cholesky factor of S, the subspace products and
   // the Rayleigh-Ritz eigensolver in FP64 (as on the FP64 path), the states and their GEMMs mixed
   bool fp64_subspace_ = false;

@@ -171,6 +171,11 @@ void eigh_householder_f32(const double2* A, double2* V, int n, cudaStream_t s);
 // FP64 Rayleigh quotients of the FP32 vectors on A; same outputs as jacobi_eigh.
 // V is n*n workspace, lam n doubles of workspace.
 void eigh_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, int n, cudaStream_t s);
+// Mixed path for 128 < n <= 256: FP32 parallel Jacobi on a copy of A (one CTA, matrix in
+// global memory), eigenvalues = FP64 Rayleigh quotients of the FP32 vectors on A; same outputs
+// as eigh_mixed.  work: 2 n^2 complex64.
+void eigh_jacobi_mixed(const double2* A, double2* V, double* lam, double* eig, double2* Vt, float2* work, int n,
+                       cudaStream_t s);
 // Rayleigh-Ritz step of the mixed block iteration in one CTA (n <= 128), FP32 in and out:
 // H_sub = conj(M) Hraw M^T (Hermitian part, exported to Aout), its eigenpairs, C = Vt M and
 // Mcat = [(I + alpha Lambda) C | -alpha C] (n x 2n) with rows in ascending eigenvalue order;

@@ -101,6 +101,9 @@ struct ks_server_s {
   int running = 0;
   bool stop = false;
   int device = 0;
+  // worker seconds by activity, and the real-time group steps (ks_serve_stats)
+  double t_start = 0, t_gs = 0, t_td = 0, t_finish = 0;
+  long n_start = 0, n_gs = 0, n_td_steps = 0, n_td_members = 0;
 };
 
 namespace ks {
@@ -219,8 +222,11 @@ void worker_loop(ks_server_s* s) {
     ks_status st = KS_OK;
     std::string err;
     std::vector<bool> complete(group.size(), false);
+    const auto t0 = Clock::now();
+    int activity = 0;                                               // 0 start, 1 ground state, 2 real time
     try {
       if (group.size() > 1) {
+        activity = 2;
         td_group_quantum(group);
         for (size_t i = 0; i < group.size(); ++i) complete[i] = ++group[i]->done >= group[i]->count;
       } else if (r->done < 0) {
@@ -228,6 +234,7 @@ void worker_loop(ks_server_s* s) {
         start(s, r);
         complete[0] = r->count <= 0;
       } else {
+        activity = r->kind == 0 ? 1 : 2;
         complete[0] = quantum(r);
       }
     } catch (const Error& e) {
@@ -239,9 +246,24 @@ void worker_loop(ks_server_s* s) {
       err = "request failed";
       complete.assign(group.size(), true);
     }
+    const auto t1 = Clock::now();
     for (size_t i = 0; i < group.size(); ++i)
       if (complete[i]) finish(s, group[i], st, err);
+    const auto t2 = Clock::now();
     lk.lock();
+    const double dq = std::chrono::duration<double>(t1 - t0).count();
+    if (activity == 0) {
+      s->t_start += dq;
+      ++s->n_start;
+    } else if (activity == 1) {
+      s->t_gs += dq;
+      ++s->n_gs;
+    } else {
+      s->t_td += dq;
+      ++s->n_td_steps;
+      s->n_td_members += (long)group.size();
+    }
+    s->t_finish += std::chrono::duration<double>(t2 - t1).count();
     s->running -= (int)group.size();
     for (size_t i = 0; i < group.size(); ++i)
       if (!complete[i]) s->ready.push_back(group[i]);
@@ -276,7 +298,7 @@ ks_status ks_serve_create_ex(size_t mem_budget_bytes, int workers, ks_server* ou
     }
     s->budget = mem_budget_bytes;
     s->pool.reset(new ks::DevicePool(size_t(1) << 30));
-    const int nworkers = workers > 0 ? workers : 4;
+    const int nworkers = workers > 0 ? workers : 16;
     for (int i = 0; i < nworkers; ++i) s->workers.emplace_back(ks::worker_loop, s.get());
     *out = s.release();
     return KS_OK;
@@ -346,6 +368,19 @@ ks_status ks_serve_submit(ks_server s, const ks_cell_desc* desc, const double* c
     ks::set_last_error("ks_serve_submit: unexpected error");
     return KS_ERR_CUDA;
   }
+}
+
+ks_status ks_serve_stats(ks_server s, double* out, int nout) {
+  if (!s || (!out && nout > 0) || nout < 0) {
+    ks::set_last_error("server/out is NULL or nout < 0");
+    return KS_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  const double v[9] = {s->t_start, s->t_gs, s->t_td, s->t_finish, (double)s->n_start, (double)s->n_gs,
+                       (double)s->n_td_steps, (double)s->n_td_members,
+                       s->pool ? (double)s->pool->reserved() : 0.0};
+  for (int i = 0; i < nout && i < 9; ++i) out[i] = v[i];
+  return KS_OK;
 }
 
 ks_status ks_serve_result_info(ks_server s, uint64_t ticket, int* nresult, int* nstates, int* nG) {

@@ -25,7 +25,7 @@ EXPORTS = ["ks_count_gvectors", "ks_grid_create", "ks_grid_destroy", "ks_grid_gv
            "ks_get_vloc", "ks_set_states", "ks_get_states", "ks_states_device", "ks_apply_h", "ks_apply_h_host",
            "ks_density", "ks_orthonormalize", "ks_rayleigh_ritz", "ks_block_iteration", "ks_block_iteration_pc", "ks_set_option", "ks_scf", "ks_td_step", "ks_td_step_dipole", "ks_kick", "ks_dipole", "ks_forces",
            "ks_set_positions", "ks_get_positions", "ks_ehrenfest",
-           "ks_serve_create", "ks_serve_create_ex", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info",
+           "ks_serve_create", "ks_serve_create_ex", "ks_serve_destroy", "ks_serve_submit", "ks_serve_poll", "ks_serve_result_info", "ks_serve_stats",
            "ks_profile", "ks_profile_read", "ks_profile_span", "ks_kernel_launches", "ks_tc_status_check", "ks_autotune_report", "ks_overlap_noalloc", "ks_last_error"]
 
 
@@ -97,6 +97,7 @@ def load():
         "ks_tc_status_check": [ct.c_int],
         "ks_autotune_report": [ct.c_char_p, ct.c_size_t, ct.POINTER(ct.c_size_t)],
         "ks_serve_create_ex": [ct.c_size_t, ct.c_int, ct.POINTER(P)],
+        "ks_serve_stats": [P, dp, ct.c_int],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -408,6 +409,14 @@ class Server:
                                      if arr is not None else None, int(kind), int(count), float(dt), ct.byref(t)))
         self._descs[t.value] = d
         return t.value
+
+    def stats(self):
+        """Worker seconds by activity and group counts since creation (ks_serve_stats)."""
+        v = np.zeros(9)
+        check(load().ks_serve_stats(self.h, _dptr(v), 9))
+        keys = ("start_s", "ground_state_s", "realtime_s", "retire_s", "starts", "ground_state_quanta",
+                "realtime_group_steps", "realtime_request_steps", "pool_bytes")
+        return dict(zip(keys, v.tolist()))
 
     def poll(self, ticket, timeout_ms=0, want_states=False):
         """(status, result, states or None, latency_s); status KS_PENDING while running."""

@@ -213,7 +213,7 @@ def test_orthonormalize_rejects_dependent_states(ks, prec, meas):
     g.close()
 
 
-@pytest.mark.parametrize("n", [64, 150])
+@pytest.mark.parametrize("n", [64, 150, 256])
 def test_mixed_cholesky_matches_fp64_factor_of_same_S(ks, n, meas):
     """The two-pass FP32 factor against an FP64 Cholesky of the very S the GPU formed, on a
     block with cond(S) ~ 1e4: one FP32 pass would be off by ~eps_32 cond(S) ~ 1e-3."""
@@ -565,6 +565,36 @@ def test_block_iteration_mixed_beyond_128_states(ks, meas):
     s = ko.gram(q)
     # not orthonormal (the SD step follows the rotation), but Hermitian positive definite
     assert np.all(np.linalg.eigvalsh(0.5 * (s + s.conj().T)) > 0)
+    g.close()
+
+
+@pytest.mark.parametrize("n", [200, 256])
+def test_mixed_subspace_129_to_256_states(ks, meas, n):
+    """Blocks of 129-256 states on the mixed path: the FP32 Cholesky with its square array in
+    global memory (n > 160) and the FP32 parallel Jacobi eigensolver (n > 128), finished by FP64
+    refinement and FP64 Rayleigh quotients.  CholQR, Rayleigh-Ritz and two block iterations
+    against the oracle at the mixed path's tolerances."""
+    cell = inputs.small_cell(14.0, 32, 3, n, 70 + n, depth=-3.0)
+    ref = ko.Cell(cell)
+    g = ks.Grid(cell, prec="bf16x3")
+    c = inputs.random_coeffs(70 + n, n, ref.nG)
+    g.set_states(c)
+    S = g.orthonormalize(want_S=True)
+    S_ref = ko.gram(c)
+    meas("n=%d Gram S, max |d| / max |S|" % n, np.max(np.abs(S - S_ref)) / np.max(np.abs(S_ref)), 2e-5)
+    q = g.get_states()
+    meas("n=%d CholQR orthonormality" % n, np.max(np.abs(ko.gram(q) - np.eye(n))), 1e-4)
+    eps = g.rayleigh_ritz()
+    e_ref, _, _, _ = ko.rayleigh_ritz(q, ko.apply_h(ref, q))
+    # FP32 H_sub entries carry ~1e-6 relative error of ||H||; an eigenvalue moves by at most the
+    # 2-norm of the perturbation, ~sqrt(n) entry errors: the 12-state bound 2.5e-5 Ha scaled by
+    # sqrt(n / 12) (measured 7.9e-6 at n = 12 and 4.0e-5 at n = 200, the same ratio)
+    meas("n=%d Rayleigh-Ritz, max |d eps|" % n, np.max(np.abs(eps - e_ref)), 2.5e-5 * np.sqrt(n / 12.0))
+    g.set_states(c)
+    eps = g.block_iteration(2)
+    eps_ref, _ = ko.block_iteration(ref, c, 2)
+    meas("n=%d block iteration, max |d eps|" % n, np.max(np.abs(eps - eps_ref)),
+         1e-4 * max(1.0, np.max(np.abs(eps_ref))))
     g.close()
 
 
