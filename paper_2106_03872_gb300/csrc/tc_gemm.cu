@@ -191,7 +191,7 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
 
 
 // ------------------------------------------------------------------------------------------------
-// Overlap: part[ks][i][j] = sum_{k in chunk ks} conj(A[i][k]) B[j][k] (FP32), tile 128 (i) x 128 (j).
+// Overlap: part[ks][j][i] = sum_{k in chunk ks} conj(A[i][k]) B[j][k] (FP32), tile 128 (i) x 128 (j).
 // Warp roles: warps 0-15 load the FP32 rows of a K-chunk of 16 complex into registers (two
 // chunks ahead; rows are only 8-byte aligned when the row length is odd), split them into the
 // bf16 hi/lo operand stages and arrive on the stage's `full` barrier; warp 16 issues the MMAs
@@ -355,12 +355,13 @@ __global__ void __launch_bounds__(PREP ? O_THREADS_PREP : O_THREADS, PREP ? 2 : 
     for (int c0 = 64 * (w >> 2); c0 < 64 * (w >> 2) + 64; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + c0, v);
+      // partials column-major (part[z][j][i]): a warp's store covers 32 consecutive i
       if (i < m) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int j = j0 + c0 / 2 + q;
           if (j < n)
-            part[((size_t)blockIdx.z * m + i) * n + j] =
+            part[((size_t)blockIdx.z * n + j) * m + i] =
                 nk > 0 ? make_float2(v[2 * q], v[2 * q + 1]) : make_float2(0.f, 0.f);
         }
       }
@@ -584,12 +585,13 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
   s = t;
 }
 
-// out[e] = sum_k part[k][e]: FP32 partials (exact copies of the TMEM accumulators) summed
-// with compensated FP32 arithmetic, so the sum carries about twice FP32's precision without
-// the FP64 pipe.  A CTA covers 32 elements; warp w takes partials w, w + 8, ...; the eight
-// (sum, error) pairs are combined in a fixed order, so the result is deterministic.
-__global__ void __launch_bounds__(256) k_reduce_parts_tc(const float2* __restrict__ part, int nks, size_t mn,
-                                                         double2* __restrict__ out, float2* __restrict__ out32) {
+// out[i][j] = sum_k part[k][j][i]: FP32 partials (exact copies of the TMEM accumulators)
+// summed with compensated FP32 arithmetic, so the sum carries about twice FP32's precision
+// without the FP64 pipe.  A CTA covers 32 elements e = j m + i (consecutive in the partials);
+// warp w takes partials w, w + 8, ...; the eight (sum, error) pairs are combined in a fixed
+// order, so the result is deterministic.
+__global__ void __launch_bounds__(256) k_reduce_parts_tc(const float2* __restrict__ part, int nks, int m, size_t mn,
+                                                         int n, double2* __restrict__ out, float2* __restrict__ out32) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const size_t e = (size_t)blockIdx.x * 32 + lane;
   __shared__ float4 red[8][32];
@@ -613,8 +615,9 @@ __global__ void __launch_bounds__(256) k_reduce_parts_tc(const float2* __restric
       ly += r.w;
     }
     const double x = (double)hx + (double)lx, y = (double)hy + (double)ly;
-    out[e] = make_double2(x, y);
-    if (out32) out32[e] = make_float2((float)x, (float)y);
+    const size_t o = (e % (size_t)m) * n + e / (size_t)m;             // row-major out[i][j]
+    out[o] = make_double2(x, y);
+    if (out32) out32[o] = make_float2((float)x, (float)y);
   }
 }
 
@@ -717,7 +720,7 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
     k_tc_overlap<false><<<g, O_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err);
   KS_CHECK_LAUNCH();
   const size_t mn = (size_t)m * n;
-  k_reduce_parts_tc<<<(unsigned)((mn + 31) / 32), 256, 0, s>>>(p32, ks, mn, out, out32);
+  k_reduce_parts_tc<<<(unsigned)((mn + 31) / 32), 256, 0, s>>>(p32, ks, m, mn, n, out, out32);
   KS_CHECK_LAUNCH();
 }
 

@@ -411,6 +411,25 @@ def test_orthonormalize_parity_two_tiles(ks, prec, meas):
     g.close()
 
 
+@pytest.mark.parametrize("L,nstates", [(24.0, 40), (30.0, 21)])
+def test_orthonormalize_parity_multi_pass(ks, L, nstates, meas):
+    """96^3 grids with 59k and 115k plane waves: the persistent rotation kernel gives each CTA
+    several passes over its share of grid rows (ragged shares, a ragged last chunk of states)."""
+    cell = inputs.small_cell(L, 96, 2, nstates, 23)
+    ref = ko.Cell(cell)
+    assert ref.nG > 148 * 256
+    g = ks.Grid(cell, prec="bf16x3")
+    c = inputs.random_coeffs(23, nstates, ref.nG)
+    g.set_states(c)
+    S = g.orthonormalize(want_S=True)
+    q_ref, S_ref = ko.cholqr(c)
+    meas("np.max(np.abs(S - S_ref))", np.max(np.abs(S - S_ref)), 2e-5 * np.max(np.abs(S_ref)))
+    q = g.get_states()
+    meas("rel(q, q_ref)", rel(q, q_ref), 1e-4)
+    meas("np.max(np.abs(ko.gram(q) - np.eye(nstates)))", np.max(np.abs(ko.gram(q) - np.eye(nstates))), 1e-4)
+    g.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 @pytest.mark.parametrize("m2max,nshell", [(2, 19), (5, 57), (9, 123)])
 def test_rayleigh_ritz_degenerate_shells(ks, prec, m2max, nshell, meas):
