@@ -22,9 +22,11 @@
 // Operand tiles use the K-major no-swizzle canonical layout (8-row x 16-byte core
 // matrices; LBO = distance between core matrices along K, SBO = along rows).
 // Every mbarrier wait is bounded; on expiry the kernel records an error code and returns.
+#include <cuda.h>   // driver types only: cuTensorMapEncodeTiled is looked up at run time
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "kernels.h"
 
@@ -373,6 +375,255 @@ __global__ void __launch_bounds__(PREP ? O_THREADS_PREP : O_THREADS, PREP ? 2 : 
 }
 
 // ------------------------------------------------------------------------------------------------
+// The same overlap with the state rows fed by TMA.  Rows are only 8-byte aligned when the row
+// length is odd, so one tensor map cannot describe them; the even and the odd rows each form a
+// matrix whose row stride (two rows) is a multiple of 16 bytes.  When the row length is odd,
+// the odd rows' map starts 8 bytes early, so that its element x + 1 is complex x of the row
+// (shift 1).  Per chunk of 16 complex one loader thread issues, per operand and row parity, one
+// tiled copy of a 64-row x 18-complex box (coordinates: the chunk's first complex, which is even,
+// and the tile's first row / 2) into a raw ring; the split warps read each row's 16 complex from
+// shared memory (zero past the CTA's K range; the copies zero-fill outside the operand).  Nothing
+// of the rows streams through L1 or registers.  Warps 0-15 split, warp 16 issues the MMAs,
+// warp 17 loads, and in the PREP form warp 18 copies A's pre-split operand tiles.
+// ------------------------------------------------------------------------------------------------
+constexpr int OT_BOX_X = 18, OT_BOX_Y = 64;
+constexpr int OT_PITCH = OT_BOX_X * 8;                       // 144 bytes per row of a box
+constexpr int OT_BOX_BYTES = OT_PITCH * OT_BOX_Y;            // 9 KB
+constexpr int OT_RAW_OPER = 2 * OT_BOX_BYTES;                // both parities of 128 rows
+constexpr int OT_NOP = 2;                                    // operand stages
+
+template <bool SAME, bool PREP>
+struct OTCfg {
+  static constexpr int NOPER = (SAME || PREP) ? 1 : 2;       // operands in the raw ring
+  static constexpr int RAW_STAGE = NOPER * OT_RAW_OPER;
+  static constexpr int NRAW = NOPER == 1 ? 4 : 3;            // raw stages (72 or 108 KB)
+  static constexpr int WARPS = O_SPLIT_WARPS + 2 + (PREP ? 1 : 0);
+  static constexpr int THREADS = 32 * WARPS;
+  static constexpr int OP_RING = OT_NOP * O_OP_STAGE;        // 96 KB
+  static constexpr int RING = OP_RING + NRAW * RAW_STAGE;
+  static constexpr int SMEM = RING + 1024;                   // + barriers and the TMEM slot
+};
+
+// Tensor maps of up to two operands ([operand][row parity]), the odd rows' shift and the rows
+// of each parity.
+struct OTMaps {
+  CUtensorMap map[2][2];
+  int shift[2];
+  int rows[2][2];
+};
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ float2 lds64(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+
+template <bool SAME, bool PREP = false>
+__global__ void __launch_bounds__(OTCfg<SAME, PREP>::THREADS, 1)
+    k_tc_overlap_tma(const __grid_constant__ OTMaps maps, int m, int n, int K, int kchunk, float2* __restrict__ part,
+                     int* __restrict__ err, const uint4* __restrict__ Aimg, int nchunks) {
+  using CF = OTCfg<SAME, PREP>;
+  constexpr int NOP = OT_NOP, NRAW = CF::NRAW, NOPER = CF::NOPER;
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  const uint32_t op0 = smem_u32(tsm), raw0 = op0 + CF::OP_RING;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + CF::RING);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(tsm + CF::RING + 256);
+  const uint32_t full = smem_u32(bars), empty = full + 8 * NOP, raw_full = empty + 8 * NOP,
+                 raw_empty = raw_full + 8 * NRAW, done = raw_empty + 8 * NRAW;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  if (t == 0) {
+    for (int i = 0; i < NOP; ++i) {
+      mbar_init(full + 8 * i, 32 * O_SPLIT_WARPS + (PREP ? 1 : 0));
+      mbar_init(empty + 8 * i, 1);
+    }
+    for (int i = 0; i < NRAW; ++i) {
+      mbar_init(raw_full + 8 * i, 1);
+      mbar_init(raw_empty + 8 * i, 32 * O_SPLIT_WARPS);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (w == 0) tmem_alloc(smem_u32(slot), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const int i0 = blockIdx.y * TC_M, j0 = blockIdx.x * (TC_N / 2);
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int nk = (kend - kbeg + O_KC - 1) / O_KC;
+  bool ok = true;
+  // raw operand o: B in the PREP form, else A (o = 0) and B (o = 1, not SAME)
+  auto first_row = [&](int o) { return (PREP || (!SAME && o == 1)) ? j0 : i0; };
+  auto nrows = [&](int o) { return (PREP || (!SAME && o == 1)) ? n : m; };
+
+  if (w < O_SPLIT_WARPS) {
+    // thread (row r, lane-in-row l): complex l, l + 4, l + 8, l + 12 of the chunk for row r of
+    // each operand (raw box of parity r % 2, box row r / 2); each complex becomes one 4-byte
+    // (re, im) bf16 pair in K-group u of the tile, and a warp's eight rows fill one core matrix
+    // per store
+    const int r = t >> 2, l = t & 3, par = r & 1;
+    bool rv[NOPER];
+    uint32_t rowoff[NOPER];
+#pragma unroll
+    for (int o = 0; o < NOPER; ++o) {
+      rv[o] = first_row(o) + r < nrows(o);
+      rowoff[o] = o * OT_RAW_OPER + par * OT_BOX_BYTES + (r >> 1) * OT_PITCH + 8 * (par ? maps.shift[o] : 0);
+    }
+    for (int c = 0; c < nk && ok; ++c) {
+      const int rs = c % NRAW, st = c % NOP;
+      ok = mbar_wait_bounded(raw_full + 8 * rs, (c / NRAW) & 1);
+      if (ok && c >= NOP) ok = mbar_wait_bounded(empty + 8 * st, ((c / NOP) - 1) & 1);
+      if (!ok) break;
+      const int nc = min(O_KC, kend - (kbeg + c * O_KC));
+      float2 x[NOPER][4];
+#pragma unroll
+      for (int o = 0; o < NOPER; ++o)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = l + 4 * u;
+          x[o][u] = (rv[o] && k < nc) ? lds64(raw0 + rs * CF::RAW_STAGE + rowoff[o] + 8 * k) : make_float2(0.f, 0.f);
+        }
+      const uint32_t oa_hi = op0 + st * O_OP_STAGE, oa_lo = oa_hi + O_A_BYTES;
+      const uint32_t ob_hi = oa_hi + 2 * O_A_BYTES, ob_lo = ob_hi + O_B_BYTES;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int kr = 8 * u + 2 * l;        // real K index of the pair
+        float h0, l0, h1, l1;
+        uint32_t o;
+        if (!PREP) {
+          split1(x[0][u].x, h0, l0);
+          split1(x[0][u].y, h1, l1);
+          o = tile_off(TC_M, r, kr);
+          sts32(oa_hi + o, pack_bf16(h0, h1));
+          sts32(oa_lo + o, pack_bf16(l0, l1));
+        }
+        // B real row 2j <- (re, im), row 2j+1 <- (im, -re)
+        const float2 xb = x[NOPER - 1][u];
+        split1(xb.x, h0, l0);
+        split1(xb.y, h1, l1);
+        o = tile_off(TC_N, 2 * r, kr);
+        sts32(ob_hi + o, pack_bf16(h0, h1));
+        sts32(ob_lo + o, pack_bf16(l0, l1));
+        o = tile_off(TC_N, 2 * r + 1, kr);
+        sts32(ob_hi + o, pack_bf16(h1, -h0));
+        sts32(ob_lo + o, pack_bf16(l1, -l0));
+      }
+      fence_proxy_async();
+      mbar_arrive(full + 8 * st);
+      mbar_arrive(raw_empty + 8 * rs);
+    }
+  } else if (w == O_SPLIT_WARPS + 1) {
+    if (lane == 0) {
+      // boxes of this CTA's tiles: row parity p of operand o starts at box row first_row(o) / 2;
+      // a box wholly past the parity's rows is not copied (its rows are not read)
+      bool has[NOPER][2];
+      uint32_t bytes = 0;
+#pragma unroll
+      for (int o = 0; o < NOPER; ++o)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          has[o][p] = first_row(o) / 2 < maps.rows[o][p];
+          if (has[o][p]) bytes += OT_BOX_BYTES;
+        }
+      int issued = 0;
+      for (int c = 0; c < nk; ++c) {
+        const int rs = c % NRAW;
+        if (c >= NRAW) {
+          ok = mbar_wait_bounded(raw_empty + 8 * rs, ((c / NRAW) - 1) & 1);
+          if (!ok) break;
+        }
+        mbar_expect_tx(raw_full + 8 * rs, bytes);
+        const int k0 = kbeg + c * O_KC;
+#pragma unroll
+        for (int o = 0; o < NOPER; ++o)
+#pragma unroll
+          for (int p = 0; p < 2; ++p)
+            if (has[o][p])
+              tma_load_2d(raw0 + rs * CF::RAW_STAGE + o * OT_RAW_OPER + p * OT_BOX_BYTES, &maps.map[o][p], k0,
+                          first_row(o) / 2, raw_full + 8 * rs);
+        issued = c + 1;
+      }
+      // copies still in flight land before the CTA exits (the normal path has consumed them all)
+      for (int c = max(0, issued - NRAW); c < issued; ++c)
+        mbar_wait_bounded(raw_full + 8 * (c % NRAW), (c / NRAW) & 1);
+    }
+  } else if (PREP && w == O_SPLIT_WARPS + 2) {
+    // A chunks of this CTA's tile: global chunk kbeg / O_KC + c of the image
+    if (lane == 0) {
+      int issued = 0;
+      const uint4* src = Aimg + ((size_t)blockIdx.y * nchunks + kbeg / O_KC) * (2 * O_A_BYTES / 16);
+      for (int c = 0; c < nk; ++c) {
+        const int st = c % NOP;
+        if (c >= NOP) {
+          ok = mbar_wait_bounded(empty + 8 * st, ((c / NOP) - 1) & 1);
+          if (!ok) break;
+        }
+        mbar_expect_tx(full + 8 * st, 2 * O_A_BYTES);
+        bulk_g2s(op0 + st * O_OP_STAGE, src + (size_t)c * (2 * O_A_BYTES / 16), 2 * O_A_BYTES, full + 8 * st);
+        issued = c + 1;
+      }
+      for (int c = max(0, issued - NOP); c < issued; ++c) mbar_wait_bounded(full + 8 * (c % NOP), (c / NOP) & 1);
+    }
+  } else if (w == O_SPLIT_WARPS && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+    constexpr uint32_t a_lbo = TC_M * 16, b_lbo = TC_N * 16;
+    for (int c = 0; c < nk; ++c) {
+      const int st = c % NOP;
+      ok = mbar_wait_bounded(full + 8 * st, (c / NOP) & 1);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t oa_hi = op0 + st * O_OP_STAGE, oa_lo = oa_hi + O_A_BYTES;
+      const uint32_t ob_hi = oa_hi + 2 * O_A_BYTES, ob_lo = ob_hi + O_B_BYTES;
+#pragma unroll
+      for (int q = 0; q < O_KR / 16; ++q) {
+        const uint32_t ao = 2 * q * a_lbo, bo = 2 * q * b_lbo;
+        const uint64_t ahi = smem_desc(oa_hi + ao, a_lbo, 128), alo = smem_desc(oa_lo + ao, a_lbo, 128);
+        const uint64_t bhi = smem_desc(ob_hi + bo, b_lbo, 128), blo = smem_desc(ob_lo + bo, b_lbo, 128);
+        mma_bf16(tmem, ahi, bhi, idesc, (c == 0 && q == 0) ? 0u : 1u);
+        mma_bf16(tmem, ahi, blo, idesc, 1u);
+        mma_bf16(tmem, alo, bhi, idesc, 1u);
+      }
+      mma_commit(empty + 8 * st);
+    }
+    mma_commit(done);                        // also when nothing was issued
+  }
+  ok = mbar_wait_bounded(done, 0) && ok;
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok && t == 0) atomicExch(err, 1);
+  tc_fence_after();
+  // epilogue (split warps): warp w reads TMEM lanes 32 (w % 4).., columns [64 (w / 4), +64);
+  // partials column-major (part[z][j][i]): a warp's store covers 32 consecutive i
+  if (ok && w < O_SPLIT_WARPS) {
+    const int i = i0 + 32 * (w & 3) + lane;
+    for (int c0 = 64 * (w >> 2); c0 < 64 * (w >> 2) + 64; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + c0, v);
+      if (i < m) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = j0 + c0 / 2 + q;
+          if (j < n)
+            part[((size_t)blockIdx.z * n + j) * m + i] =
+                nk > 0 ? make_float2(v[2 * q], v[2 * q + 1]) : make_float2(0.f, 0.f);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (w == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ------------------------------------------------------------------------------------------------
 // Rotation: Y[i][k] = sum_j M[i][j] X[j][k].  CTA: 256 grid columns k (two MMA tiles of 128)
 // x 128 outputs i.  Mb holds M pre-split into the B-tile images, per (i-tile, j-chunk of 16
 // states): the three bf16 terms one after the other.  Per chunk and tile (two K16 steps) the
@@ -621,9 +872,88 @@ __global__ void __launch_bounds__(256) k_reduce_parts_tc(const float2* __restric
   }
 }
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link against the driver
+// library); null when the driver does not offer it.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn f = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiledFn) nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(fn);
+  }();
+  return f;
+}
+
+// The row-parity maps of one operand (rows x K, leading dimension ld): false when they cannot
+// be formed (operand not 16-byte aligned, or the encoder refuses the shape), in which case the
+// overlap runs the register-fed kernel.  The last few operands' maps are kept per host thread.
+struct ParityMaps {
+  const float2* P = nullptr;
+  int ld = 0, rows = 0, K = 0;
+  bool ok = false;
+  CUtensorMap map[2];
+  int shift = 0, prow[2] = {0, 0};
+};
+const ParityMaps& parity_maps(const float2* P, int ld, int rows, int K) {
+  thread_local ParityMaps cache[8];
+  thread_local int next = 0;
+  for (const ParityMaps& c : cache)
+    if (c.P == P && c.ld == ld && c.rows == rows && c.K == K) return c;
+  ParityMaps& e = cache[next];
+  next = (next + 1) % 8;
+  e.P = P;
+  e.ld = ld;
+  e.rows = rows;
+  e.K = K;
+  e.ok = false;
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc || (reinterpret_cast<uintptr_t>(P) & 15) || rows < 1 || K < 1 || ld < K) return e;
+  e.shift = ld & 1;
+  for (int p = 0; p < 2; ++p) {
+    e.prow[p] = p == 0 ? (rows + 1) / 2 : rows / 2;
+    if (e.prow[p] == 0) {                    // no odd rows: never copied
+      e.map[1] = e.map[0];
+      continue;
+    }
+    char* base = reinterpret_cast<char*>(const_cast<float2*>(P)) + (p ? 8 * ((size_t)ld - e.shift) : 0);
+    const cuuint64_t dims[2] = {(cuuint64_t)K + (p ? e.shift : 0), (cuuint64_t)e.prow[p]};
+    const cuuint64_t strides[1] = {(cuuint64_t)16 * ld};
+    const cuuint32_t box[2] = {OT_BOX_X, OT_BOX_Y}, estr[2] = {1, 1};
+    if (enc(&e.map[p], CU_TENSOR_MAP_DATA_TYPE_INT64, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return e;
+  }
+  e.ok = true;
+  return e;
+}
+bool fill_maps(OTMaps& mp, int o, const float2* P, int ld, int rows, int K) {
+  const ParityMaps& e = parity_maps(P, ld, rows, K);
+  if (!e.ok) return false;
+  mp.map[o][0] = e.map[0];
+  mp.map[o][1] = e.map[1];
+  mp.shift[o] = e.shift;
+  mp.rows[o][0] = e.prow[0];
+  mp.rows[o][1] = e.prow[1];
+  return true;
+}
+
 bool g_attr_done = false;
 void set_attrs() {
   if (g_attr_done) return;
+  KS_CUDA(cudaFuncSetAttribute(k_tc_overlap_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               OTCfg<false, false>::SMEM));
+  KS_CUDA(cudaFuncSetAttribute(k_tc_overlap_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               OTCfg<true, false>::SMEM));
+  KS_CUDA(cudaFuncSetAttribute(k_tc_overlap_tma<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               OTCfg<false, true>::SMEM));
   KS_CUDA(cudaFuncSetAttribute(k_tc_overlap<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
   KS_CUDA(cudaFuncSetAttribute(k_tc_overlap<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
   KS_CUDA(cudaFuncSetAttribute(k_tc_overlap<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM_PREP));
@@ -700,7 +1030,19 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
                 size_t part_elems, double2* out, int* err, cudaStream_t s, float2* out32, const void* Aimg) {
   set_attrs();
   const int tm = (m + TC_M - 1) / TC_M, tn = (n + TC_N / 2 - 1) / (TC_N / 2);
-  int ks = std::max(1, (Aimg ? 2 : 1) * sm_count() / (tm * tn));   // the prepared form runs two CTAs per SM
+  const bool same = A == B && lda == ldb && m == n && tm == 1 && tn == 1;
+  // TMA-fed kernel when the operands' tensor maps can be formed (one CTA per SM)
+  OTMaps mp;
+  std::memset(&mp, 0, sizeof(mp));
+  bool tma;
+  if (Aimg)
+    tma = fill_maps(mp, 0, B, ldb, n, K);
+  else if (same)
+    tma = fill_maps(mp, 0, A, lda, m, K);
+  else
+    tma = fill_maps(mp, 0, A, lda, m, K) && fill_maps(mp, 1, B, ldb, n, K);
+  // the register-fed prepared form runs two CTAs per SM
+  int ks = std::max(1, (Aimg && !tma ? 2 : 1) * sm_count() / (tm * tn));
   ks = std::min(ks, std::max(1, K / (4 * O_KC)));
   ks = (int)std::min<long>(ks, (long)(part_elems / ((size_t)m * n)));
   if (ks < 1) fail(KS_ERR_ARG, "tc_overlap: partial buffer too small");
@@ -710,11 +1052,21 @@ void tc_overlap(const float2* A, int lda, const float2* B, int ldb, int m, int n
   dim3 g(tn, tm, ks);
   float2* p32 = reinterpret_cast<float2*>(part);                      // FP32 partials
   // one output tile of A^H A: both operands are the same rows
-  if (Aimg)
+  if (tma) {
+    if (Aimg)
+      k_tc_overlap_tma<false, true><<<g, OTCfg<false, true>::THREADS, OTCfg<false, true>::SMEM, s>>>(
+          mp, m, n, K, kchunk, p32, err, static_cast<const uint4*>(Aimg), (K + O_KC - 1) / O_KC);
+    else if (same)
+      k_tc_overlap_tma<true><<<g, OTCfg<true, false>::THREADS, OTCfg<true, false>::SMEM, s>>>(mp, m, n, K, kchunk, p32,
+                                                                                           err, nullptr, 0);
+    else
+      k_tc_overlap_tma<false><<<g, OTCfg<false, false>::THREADS, OTCfg<false, false>::SMEM, s>>>(
+          mp, m, n, K, kchunk, p32, err, nullptr, 0);
+  } else if (Aimg)
     k_tc_overlap<false, true><<<g, O_THREADS_PREP, O_SMEM_PREP, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err,
                                                                 static_cast<const uint4*>(Aimg),
                                                                 (K + O_KC - 1) / O_KC);
-  else if (A == B && lda == ldb && m == n && tm == 1 && tn == 1)
+  else if (same)
     k_tc_overlap<true><<<g, O_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err);
   else
     k_tc_overlap<false><<<g, O_THREADS, O_SMEM, s>>>(A, lda, B, ldb, m, n, K, kchunk, p32, err);
