@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(PREP ? O_THREADS_PREP : O_THREADS, PREP ? 2 : 
     // of A and complex row r of B, so four lanes read 32 contiguous bytes of a row; each
     // complex becomes one 4-byte (re, im) bf16 pair in K-group u of the tile, and a warp's
     // eight rows fill one core matrix per store
-    const int r = t >> 2, l = t & 3;
+    const int r = t >> 2, l = t & 3, sw = (r >> 2) & 1;
     const bool ra = i0 + r < m, rb = j0 + r < n;
     const float2* pa = A + (size_t)(ra ? i0 + r : 0) * lda;
     const float2* pb = B + (size_t)(rb ? j0 + r : 0) * ldb;
@@ -292,12 +292,16 @@ __global__ void __launch_bounds__(PREP ? O_THREADS_PREP : O_THREADS, PREP ? 2 : 
         // B real row 2j <- (re, im), row 2j+1 <- (im, -re)
         split1(x[4 + u].x, h0, l0);
         split1(x[4 + u].y, h1, l1);
-        o = tile_off(TC_N, 2 * r, kr);
-        sts32(ob_hi + o, pack_bf16(h0, h1));
-        sts32(ob_lo + o, pack_bf16(l0, l1));
-        o = tile_off(TC_N, 2 * r + 1, kr);
-        sts32(ob_hi + o, pack_bf16(h1, -h0));
-        sts32(ob_lo + o, pack_bf16(l1, -l0));
+        // rows r and r + 4 of a warp write B's two rows in opposite order, so that each store of
+        // the warp falls into 32 distinct banks
+        const uint32_t e_hi = pack_bf16(h0, h1), e_lo = pack_bf16(l0, l1);
+        const uint32_t d_hi = pack_bf16(h1, -h0), d_lo = pack_bf16(l1, -l0);
+        o = tile_off(TC_N, 2 * r + sw, kr);
+        sts32(ob_hi + o, sw ? d_hi : e_hi);
+        sts32(ob_lo + o, sw ? d_lo : e_lo);
+        o = tile_off(TC_N, 2 * r + 1 - sw, kr);
+        sts32(ob_hi + o, sw ? e_hi : d_hi);
+        sts32(ob_lo + o, sw ? e_lo : d_lo);
       }
       fence_proxy_async();
       mbar_arrive(full + 8 * st);
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__(OTCfg<SAME, PREP>::THREADS, 1)
     // each operand (raw box of parity r % 2, box row r / 2); each complex becomes one 4-byte
     // (re, im) bf16 pair in K-group u of the tile, and a warp's eight rows fill one core matrix
     // per store
-    const int r = t >> 2, l = t & 3, par = r & 1;
+    const int r = t >> 2, l = t & 3, par = r & 1, sw = (r >> 2) & 1;
     bool rv[NOPER];
     uint32_t rowoff[NOPER];
 #pragma unroll
@@ -510,12 +514,16 @@ __global__ void __launch_bounds__(OTCfg<SAME, PREP>::THREADS, 1)
         const float2 xb = x[NOPER - 1][u];
         split1(xb.x, h0, l0);
         split1(xb.y, h1, l1);
-        o = tile_off(TC_N, 2 * r, kr);
-        sts32(ob_hi + o, pack_bf16(h0, h1));
-        sts32(ob_lo + o, pack_bf16(l0, l1));
-        o = tile_off(TC_N, 2 * r + 1, kr);
-        sts32(ob_hi + o, pack_bf16(h1, -h0));
-        sts32(ob_lo + o, pack_bf16(l1, -l0));
+        // rows r and r + 4 of a warp write B's two rows in opposite order, so that each store of
+        // the warp falls into 32 distinct banks
+        const uint32_t e_hi = pack_bf16(h0, h1), e_lo = pack_bf16(l0, l1);
+        const uint32_t d_hi = pack_bf16(h1, -h0), d_lo = pack_bf16(l1, -l0);
+        o = tile_off(TC_N, 2 * r + sw, kr);
+        sts32(ob_hi + o, sw ? d_hi : e_hi);
+        sts32(ob_lo + o, sw ? d_lo : e_lo);
+        o = tile_off(TC_N, 2 * r + 1 - sw, kr);
+        sts32(ob_hi + o, sw ? e_hi : d_hi);
+        sts32(ob_lo + o, sw ? e_lo : d_lo);
       }
       fence_proxy_async();
       mbar_arrive(full + 8 * st);

@@ -473,6 +473,28 @@ def test_apply_h_plain_path_grids(ks, N, L, natoms, meas):
     g.close()
 
 
+def test_apply_h_block_only_8_byte_aligned(ks, meas):
+    """States that start one state into a buffer with an odd |S| are only 8-byte aligned: the
+    projections then take the register-fed overlap kernel (the TMA-fed one needs 16-byte
+    aligned operands); same operator, same tolerance."""
+    cell = inputs.small_cell(10.0, 24, 4, 5, 43)
+    ref = ko.Cell(cell)
+    assert ref.nG % 2 == 1
+    g = ks.Grid(cell, prec="bf16x3")
+    c = inputs.random_coeffs(43, 5, ref.nG)
+    buf = torch.zeros((6, ref.nG), dtype=torch.complex64, device="cuda")
+    buf[1:] = torch.from_numpy(c).to("cuda", torch.complex64)
+    out = torch.zeros_like(buf)
+    psi, h = buf[1:], out[1:]
+    assert psi.data_ptr() % 16 == 8 and h.data_ptr() % 16 == 8
+    g.apply_h(psi.data_ptr(), h.data_ptr(), 5)
+    torch.cuda.synchronize()
+    got = h.cpu().numpy().astype(np.complex128)
+    meas("rel(H psi at 8-byte aligned rows, oracle)", rel(got, ko.apply_h(ref, c)), 2e-5)
+    assert torch.all(out[0] == 0)
+    g.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_apply_h_partial_block_and_empty(ks, prec, meas):
     """ks_apply_h on the first n of the handle's states (n = 0 is a no-op)."""
