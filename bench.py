@@ -275,7 +275,7 @@ def _rate(name, ms, count, geo, pk, peak_scale=1.0):
 # FP32 CUDA-core rate measured by an FMA-chain probe over all 152 SMs (the derived 80.5 TFLOP/s
 # assumes every lane issues an FMA every cycle at the maximum clock)
 FP32_PROBE_TFLOPS = 69.5
-HPSI_STAGES = ("plane", "zinv", "zfwd", "proj_gemm")
+HPSI_STAGES = ("plane", "zinv", "zfwd", "proj_gemm", "nl_values")
 
 
 def hpsi_algorithmic_bytes(geo):

@@ -411,11 +411,28 @@ template <int SIGN> __device__ __forceinline__ float2 twiddle(const float2* tw, 
   return w;
 }
 
+// Every element of a line holds data.
+struct AllElems {
+  __device__ __forceinline__ bool operator()(int, int) const { return true; }
+};
+// Band row g of a plane holds the sphere's columns at |m_y| <= ym[g] only (a column (m_x, m_y)
+// exists iff m_x^2 + m_y^2 fits the sphere, a contiguous m_y range per row; ym[g] = -1: none);
+// the other elements are read as zeros, so the plane needs no clearing before the scatter.
+template <int N> struct ColMask {
+  const int* ym;
+  __device__ __forceinline__ bool operator()(int g, int y) const {
+    const int m = ym[g];
+    return y <= m || y >= N - m;
+  }
+};
+
 // A two-stage transform (R1 then R2, the inverse plan; SIGN selects the exponent) of the lines
-// of one team.  Line l at P + off(l), element e at e * KS.  Ends without a barrier: stage B
-// writes back only the elements the same thread read.
-template <int N, int SIGN, int KS, class Off>
-__device__ __forceinline__ void team_lines(float2* P, int nlines, const Off& off, const float2* tw) {
+// of one team.  Line l at P + off(l), element e at e * KS; stage A reads element e only where
+// has(l, e), else zero.  Ends without a barrier: stage B writes back only the elements the same
+// thread read.
+template <int N, int SIGN, int KS, class Off, class Has = AllElems>
+__device__ __forceinline__ void team_lines(float2* P, int nlines, const Off& off, const float2* tw,
+                                           const Has& has = Has{}) {
   using TP = TPlan<N>;
   constexpr int R1 = TP::R1, R2 = TP::R2, W = TP::W, QA = R2 / W, QB = R1 / W;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -430,7 +447,8 @@ __device__ __forceinline__ void team_lines(float2* P, int nlines, const Off& off
     for (int q = 0; q < QA; ++q) {
       const int j = wi + W * q;
 #pragma unroll
-      for (int r = 0; r < R1; ++r) v[q][r] = act ? p[(j + r * R2) * KS] : make_float2(0.f, 0.f);
+      for (int r = 0; r < R1; ++r)
+        v[q][r] = (act && has(l, j + r * R2)) ? p[(j + r * R2) * KS] : make_float2(0.f, 0.f);
       SmallDft<R1, float2>::run(v[q], SIGN);
     }
     team_bar(team, 32 * W);
@@ -561,15 +579,11 @@ __device__ __forceinline__ void team_x_roundtrip(float2* P, int xr, const float*
     // in words < k
     static_assert(32 % R1 == 0, "bitmap word of e = j + R1 r");
     uint32_t wbits[NW];
-    int pre[NW];
+    int lo = 0;
     if (act) {
-      int acc = loff[l];
+      lo = loff[l];
 #pragma unroll
-      for (int k = 0; k < NW; ++k) {
-        wbits[k] = bits[l * NW + k];
-        pre[k] = acc;
-        acc += __popc(wbits[k]);
-      }
+      for (int k = 0; k < NW; ++k) wbits[k] = bits[l * NW + k];
     }
     float2 v[QB][R2];
 #pragma unroll
@@ -597,7 +611,10 @@ __device__ __forceinline__ void team_x_roundtrip(float2* P, int xr, const float*
           const uint32_t word = wbits[(R1 * r) >> 5];
           const int bit = ((R1 * r) & 31) + j;
           if ((word >> bit) & 1u) {
-            const float2 a = nlv[pre[(R1 * r) >> 5] + __popc(word & ((1u << bit) - 1u))];
+            int before = lo;                                  // points of this line in earlier words
+#pragma unroll
+            for (int k = 0; k < (R1 * r) >> 5; ++k) before += __popc(wbits[k]);
+            const float2 a = nlv[before + __popc(word & ((1u << bit) - 1u))];
             u.x += a.x;
             u.y += a.y;
           }
@@ -637,76 +654,68 @@ __device__ __forceinline__ void team_x_roundtrip(float2* P, int xr, const float*
   }
 }
 
-// Dynamic shared memory: twiddles [N], plane [N][N+1], projections [nprojtot] (this state),
-// covered-point values [cap], bitmap [N][NW], line offsets [N].
-template <int N> size_t team_smem(int nprojtot, int cap) {
-  return (size_t)(N + N * (N + 1) + nprojtot + cap) * sizeof(float2) +
-         (size_t)N * TCfg<N>::NW * sizeof(uint32_t) + (size_t)N * sizeof(int);
+// Dynamic shared memory: twiddles [N], plane [N][N+1], covered-point values [cap] (rounded up to
+// an even count, so that the bitmap is 16-byte aligned), bitmap [N][NW], line offsets [N], row
+// column ranges [N].
+template <int N> size_t team_smem(int cap) {
+  return (size_t)(N + N * (N + 1) + ((cap + 1) & ~1)) * sizeof(float2) +
+         (size_t)N * TCfg<N>::NW * sizeof(uint32_t) + 2 * (size_t)N * sizeof(int);
 }
+
+// Inputs of the projector add for the team plane kernel: the values sum_{I,l} D Omega^{1/2}
+// beta_Il(r) p_Il at the covered points r of every plane, per state (k_nl_values, [state][point],
+// points in plane order), the per-plane bitmap of covered points [z][jy][NW] and the per-plane
+// y-line offsets of the point list.
+struct TeamNL {
+  const float2* val;
+  const uint32_t* bits;
+  const int* pt_off;
+  const int* line_off;
+  int npts;
+};
 
 template <int N>
 __device__ __forceinline__ void plane_team_body(const float2* __restrict__ colbuf1, float2* __restrict__ colbuf2,
                                                 int ncols, const int* __restrict__ col_xy, int xr,
-                                                const float* __restrict__ vplane, const PlaneNL& nl,
-                                                const float2* __restrict__ pf, int nprojtot, int cap_layout,
-                                                const float2* __restrict__ twg, int z, int b) {
+                                                const int* __restrict__ rowym, const float* __restrict__ vplane,
+                                                const TeamNL& nl, int cap_layout, const float2* __restrict__ twg,
+                                                int z, int b) {
   constexpr int ld = N + 1, PT = TCfg<N>::PT, NW = TCfg<N>::NW;
   extern __shared__ __align__(16) float2 psm[];
   float2* tw = psm;
   float2* P = tw + N;
-  float2* pfs = P + N * ld;
-  float2* nlv = pfs + nprojtot;
-  uint32_t* bits = reinterpret_cast<uint32_t*>(nlv + cap_layout);
+  float2* nlv = P + N * ld;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(nlv + ((cap_layout + 1) & ~1));
   int* loff = reinterpret_cast<int*>(bits + N * NW);
-  for (int q = threadIdx.x; q < nprojtot; q += PT) cp_async8(pfs + q, pf + (size_t)b * nprojtot + q);
-  cp_async_commit();
-  for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
-  int pt0 = 0, pt1 = 0;
-  if (nprojtot > 0) {
-    pt0 = nl.pt_off[z];
-    pt1 = nl.pt_off[z + 1];
-  }
-  for (int e = threadIdx.x; e < N * NW; e += PT) bits[e] = 0u;
-  for (int e = threadIdx.x; e < N; e += PT) loff[e] = nprojtot > 0 ? nl.line_off[(size_t)z * (N + 1) + e] : 0;
-  // zero the band rows (the only rows the inverse transforms read before writing them)
-  const int nband = 2 * xr + 1;
-  for (int e = threadIdx.x; e < nband * N; e += PT) {
-    const int g = e / N, y = e - g * N;
-    P[(g <= xr ? g : g + N - 2 * xr - 1) * ld + y] = make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  // the columns land in the zeroed band rows by asynchronous copies while the projector values
-  // are formed
+  int* yms = loff + N;
+  // everything the transforms need arrives by asynchronous copies: the columns of this (state,
+  // z-plane) into the band rows (no clearing: the inverse y transform reads a row's column range
+  // only), the plane's projector values and its bitmap of covered points
   const size_t row = ((size_t)b * N + z) * ncols;
   for (int c = threadIdx.x; c < ncols; c += PT) {
     const int xy = col_xy[c];
     const int jx = xy / N, jy = xy - jx * N;
     cp_async8(P + jx * ld + jy, colbuf1 + row + c);
   }
-  cp_async_commit();
-  cp_async_wait_group1();                                              // the projections (first group)
-  __syncthreads();
-  // values of the projector add at the plane's covered points: sum_{I,l} D Omega^{1/2} beta_Il p_Il
-  for (int pt = pt0 + threadIdx.x; pt < pt1; pt += PT) {
-    const int e0 = nl.ent_off[pt], e1 = nl.ent_off[pt + 1];
-    float ax = 0.f, ay = 0.f;
-    for (int e = e0; e < e1; ++e) {
-      const float2* pp = pfs + nl.ent_proj[e];
-      const float* bt = nl.ent_beta + (size_t)e * nl.nproj;
-      for (int q = 0; q < nl.nproj; ++q) {
-        ax += bt[q] * pp[q].x;
-        ay += bt[q] * pp[q].y;
-      }
-    }
-    nlv[pt - pt0] = make_float2(ax, ay);
-    const int xy = nl.pt_xy[pt];
-    const int jx = xy / N, jy = xy - jx * N;
-    atomicOr(&bits[jy * NW + (jx >> 5)], 1u << (jx & 31));
+  if (cap_layout > 0) {
+    const int pt0 = nl.pt_off[z], pt1 = nl.pt_off[z + 1];
+    const float2* src = nl.val + (size_t)b * nl.npts + pt0;
+    for (int q = threadIdx.x; q < pt1 - pt0; q += PT) cp_async8(nlv + q, src + q);
+    const uint32_t* bsrc = nl.bits + (size_t)z * N * NW;              // N * NW words: a multiple of 4
+    for (int q = threadIdx.x; q < N * NW / 4; q += PT) cp_async16(bits + 4 * q, bsrc + 4 * q);
+    for (int e = threadIdx.x; e < N; e += PT) loff[e] = nl.line_off[(size_t)z * (N + 1) + e];
+  } else {
+    for (int e = threadIdx.x; e < N * NW; e += PT) bits[e] = 0u;
+    for (int e = threadIdx.x; e < N; e += PT) loff[e] = 0;
   }
+  cp_async_commit();
+  for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
+  const int nband = 2 * xr + 1;
+  for (int g = threadIdx.x; g < nband; g += PT) yms[g] = rowym[g];
   cp_async_wait_all();
   __syncthreads();
   // inverse y transforms of the band rows
-  team_lines<N, +1, 1>(P, nband, RowOff<N>{xr}, tw);
+  team_lines<N, +1, 1>(P, nband, RowOff<N>{xr}, tw, ColMask<N>{yms});
   __syncthreads();
   team_x_roundtrip<N>(P, xr, vplane + (size_t)z * N * N, nlv, bits, loff, tw);
   __syncthreads();
@@ -719,13 +728,45 @@ __device__ __forceinline__ void plane_team_body(const float2* __restrict__ colbu
   }
 }
 
+// nlval[b][pt] = sum over the point's sphere entries e (in list order) and projectors q of
+// beta_e[q] pf[b][proj_e + q]: the projector add of Eq. 9 at every covered point, per state
+// (pf = D Omega^{1/2} p).  One thread per point for NLB consecutive states.
+constexpr int NLB = 8;
+__global__ void __launch_bounds__(256) k_nl_values(const float2* __restrict__ pf, int nprojtot, int n, PlaneNL nl,
+                                                   int npts, float2* __restrict__ nlval) {
+  const int pt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= npts) return;
+  const int b0 = blockIdx.y * NLB, nb = min(NLB, n - b0);
+  float ax[NLB], ay[NLB];
+#pragma unroll
+  for (int k = 0; k < NLB; ++k) ax[k] = ay[k] = 0.f;
+  const int e0 = nl.ent_off[pt], e1 = nl.ent_off[pt + 1];
+  for (int e = e0; e < e1; ++e) {
+    const float* bt = nl.ent_beta + (size_t)e * nl.nproj;
+    const float2* pp = pf + (size_t)b0 * nprojtot + nl.ent_proj[e];
+    for (int q = 0; q < nl.nproj; ++q) {
+      const float bq = bt[q];
+#pragma unroll
+      for (int k = 0; k < NLB; ++k) {
+        if (k < nb) {
+          const float2 v = pp[(size_t)k * nprojtot + q];
+          ax[k] += bq * v.x;
+          ay[k] += bq * v.y;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NLB; ++k)
+    if (k < nb) nlval[(size_t)(b0 + k) * npts + pt] = make_float2(ax[k], ay[k]);
+}
+
 template <int N>
 __global__ void __launch_bounds__(TCfg<N>::PT, TCfg<N>::PMIN)
     k_plane_team(const float2* __restrict__ colbuf1, float2* __restrict__ colbuf2, int ncols,
-                 const int* __restrict__ col_xy, int xr, const float* __restrict__ vplane, PlaneNL nl,
-                 const float2* __restrict__ pf, int nprojtot, const float2* __restrict__ twg) {
-  plane_team_body<N>(colbuf1, colbuf2, ncols, col_xy, xr, vplane, nl, pf, nprojtot, nl.cap, twg, blockIdx.x,
-                     blockIdx.y);
+                 const int* __restrict__ col_xy, int xr, const int* __restrict__ rowym,
+                 const float* __restrict__ vplane, TeamNL nl, int cap, const float2* __restrict__ twg) {
+  plane_team_body<N>(colbuf1, colbuf2, ncols, col_xy, xr, rowym, vplane, nl, cap, twg, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -740,10 +781,9 @@ struct GMember {
   float2* cb1;
   float2* cb2;
   const float* vplane;
-  PlaneNL nl;
-  const float2* pf;
+  TeamNL nl;
   TaylorEpi te;
-  int nprojtot, n, s0, z0;
+  int cap, n, s0, z0;
 };
 constexpr int GMAX = 8;
 struct GDesc {
@@ -774,9 +814,9 @@ __global__ void __launch_bounds__(FCfg<N>::ZT, 2) k_zinv_group(const __grid_cons
 template <int N>
 __global__ void __launch_bounds__(TCfg<N>::PT, TCfg<N>::PMIN)
     k_plane_team_group(const __grid_constant__ GDesc gd, int ncols, const int* __restrict__ col_xy, int xr,
-                       const float2* __restrict__ twg) {
+                       const int* __restrict__ rowym, const float2* __restrict__ twg) {
   const GMember& M = gd.m[member_by_state(gd, blockIdx.y)];
-  plane_team_body<N>(M.cb1, M.cb2, ncols, col_xy, xr, M.vplane, M.nl, M.pf, M.nprojtot, M.nl.cap, twg, blockIdx.x,
+  plane_team_body<N>(M.cb1, M.cb2, ncols, col_xy, xr, rowym, M.vplane, M.nl, M.cap, twg, blockIdx.x,
                      blockIdx.y - M.s0);
 }
 
@@ -799,7 +839,8 @@ __global__ void __launch_bounds__(FCfg<N>::ZT, 2) k_zfwd_group(const __grid_cons
 template <int N>
 __global__ void __launch_bounds__(TCfg<N>::PT, TCfg<N>::PMIN)
     k_plane_density_team(const float2* __restrict__ colbuf1, int ncols, const int* __restrict__ col_xy, int xr,
-                         int nstates, int chunk, const double* __restrict__ occ, float scale,
+                         const int* __restrict__ rowym, int nstates, int chunk, const double* __restrict__ occ,
+                         float scale,
                          float* __restrict__ partial, const float2* __restrict__ twg) {
   using TP = TPlan<N>;
   constexpr int R1 = TP::R1, R2 = TP::R2, W = TP::W, QA = R2 / W, QB = R1 / W;
@@ -811,6 +852,7 @@ __global__ void __launch_bounds__(TCfg<N>::PT, TCfg<N>::PMIN)
   float2* tw = psm;
   float2* P = tw + N;
   float* accs = reinterpret_cast<float*>(P + N * ld);
+  int* yms = reinterpret_cast<int*>(accs + (ACC_SMEM ? N * N : 0));
   const int z = blockIdx.x, ch = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int team = warp / W, wi = warp - team * W;
@@ -818,6 +860,7 @@ __global__ void __launch_bounds__(TCfg<N>::PT, TCfg<N>::PMIN)
   const bool act = l < N;
   for (int t = threadIdx.x; t < N; t += PT) tw[t] = twg[t];
   const int nband = 2 * xr + 1;
+  for (int g = threadIdx.x; g < nband; g += PT) yms[g] = rowym[g];
   auto band = [&](int e) { return e <= xr || e >= N - xr; };
   float acc[ACC_SMEM ? 1 : QB][ACC_SMEM ? 1 : R2];
   if constexpr (ACC_SMEM) {
@@ -831,11 +874,6 @@ __global__ void __launch_bounds__(TCfg<N>::PT, TCfg<N>::PMIN)
   const int b0 = ch * chunk, b1 = min(nstates, b0 + chunk);
 #pragma unroll 1
   for (int b = b0; b < b1; ++b) {
-    for (int e = threadIdx.x; e < nband * N; e += PT) {
-      const int g = e / N, y = e - g * N;
-      P[(g <= xr ? g : g + N - 2 * xr - 1) * ld + y] = make_float2(0.f, 0.f);
-    }
-    __syncthreads();
     const float2* src = colbuf1 + ((size_t)b * N + z) * ncols;
     for (int c = threadIdx.x; c < ncols; c += PT) {
       const int xy = col_xy[c];
@@ -843,7 +881,7 @@ __global__ void __launch_bounds__(TCfg<N>::PT, TCfg<N>::PMIN)
       P[jx * ld + jy] = src[c];
     }
     __syncthreads();
-    team_lines<N, +1, 1>(P, nband, RowOff<N>{xr}, tw);
+    team_lines<N, +1, 1>(P, nband, RowOff<N>{xr}, tw, ColMask<N>{yms});
     __syncthreads();
     float2* p = P + (act ? l : 0);
     {
@@ -1156,6 +1194,7 @@ class FusedImpl final : public FusedOps {
     ncols_ = g.ncols;
     nprojtot_ = g.natoms * g.nproj;
     const size_t N3 = (size_t)N_ * N_ * N_;
+    build_row_ranges();
     build_plane_lists();
     // buffers
     colbuf1_ = alloc<float2>((size_t)ns_ * N_ * ncols_);
@@ -1181,11 +1220,19 @@ class FusedImpl final : public FusedOps {
     k_to_planes<<<nblk(N3, 256), 256, 0, s>>>(v, N_, vplane_);
     KS_CHECK_LAUNCH();
     if (nprojtot_ > 0) {
-      ProfScope ps(prof_, "proj_gemm", s);
-      tc_overlap(B_, g_.nG, psi, g_.nG, nprojtot_, n, g_.nG, part_, part_elems_, pout_, err_, s, nullptr, Bimg_);
-      const float scale = (float)(g_.D * std::sqrt(g_.omega));
-      k_proj_to_states<<<nblk((size_t)nprojtot_ * n, 256), 256, 0, s>>>(pout_, nprojtot_, n, scale, pf_);
-      KS_CHECK_LAUNCH();
+      {
+        ProfScope ps(prof_, "proj_gemm", s);
+        tc_overlap(B_, g_.nG, psi, g_.nG, nprojtot_, n, g_.nG, part_, part_elems_, pout_, err_, s, nullptr, Bimg_);
+        const float scale = (float)(g_.D * std::sqrt(g_.omega));
+        k_proj_to_states<<<nblk((size_t)nprojtot_ * n, 256), 256, 0, s>>>(pout_, nprojtot_, n, scale, pf_);
+        KS_CHECK_LAUNCH();
+      }
+      if (npts_ > 0 && nlval_) {
+        ProfScope ps(prof_, "nl_values", s);
+        k_nl_values<<<dim3((npts_ + 255) / 256, (n + NLB - 1) / NLB), 256, 0, s>>>(pf_, nprojtot_, n, nl_, npts_,
+                                                                                nlval_);
+        KS_CHECK_LAUNCH();
+      }
     }
   }
 
@@ -1239,17 +1286,15 @@ class FusedImpl final : public FusedOps {
           m.cb1 = f->colbuf1_;
           m.cb2 = f->colbuf2_;
           m.vplane = f->vplane_;
-          m.nl = f->nl_;
-          if (f->nprojtot_ == 0) m.nl.cap = 0;
-          m.pf = f->pf_;
+          m.nl = f->team_nl();
+          m.cap = f->team_cap();
           m.te = it.te;
-          m.nprojtot = f->nprojtot_;
           m.n = it.n;
           m.s0 = s0;
           m.z0 = z0;
           s0 += it.n;
           z0 += (it.n + ZSB - 1) / ZSB;
-          smem = std::max(smem, team_smem<N>(m.nprojtot, m.nl.cap));
+          smem = std::max(smem, team_smem<N>(m.cap));
         }
         if (smem > SMEM_MAX) fail(KS_ERR_ARG, "packed H application: %zu bytes of shared memory", smem);
         {
@@ -1261,7 +1306,7 @@ class FusedImpl final : public FusedOps {
         {
           ProfScope ps(f0->prof_, "plane", s);
           k_plane_team_group<N><<<dim3(N, s0), TCfg<N>::PT, smem, s>>>(gd, f0->ncols_, f0->t_.col_xy, f0->g_.xr,
-                                                                       f0->t_.tw);
+                                                                       f0->rowym_, f0->t_.tw);
           KS_CHECK_LAUNCH();
         }
         {
@@ -1315,6 +1360,7 @@ class FusedImpl final : public FusedOps {
     arena_.release(nl_.ent_proj);
     arena_.release(nl_.ent_beta);
     arena_.release(nl_.line_off);
+    arena_.release(nlbits_);
     upload_plane_lists();
     if (nprojtot_ > 0) build_projector_block();
   }
@@ -1380,7 +1426,7 @@ class FusedImpl final : public FusedOps {
   // where both exist.
   template <int N> int plane_variant(int n, cudaStream_t s) {
     if constexpr (TPlan<N>::ok) {
-      if (team_smem<N>(nprojtot_, nprojtot_ > 0 ? nl_.cap : 0) > SMEM_MAX) return 1;
+      if (team_smem<N>(team_cap()) > SMEM_MAX) return 1;
       static const char* names[2] = {"team", "cta"};
       return tune_choice(tune_key("plane", n), 2, [&](int c) { launch_plane<N>(n, colbuf1_, pf_, s, c); }, s,
                          names);
@@ -1397,17 +1443,15 @@ class FusedImpl final : public FusedOps {
 
   template <int N> void launch_plane(int n, const float2* cb1, const float2* pf, cudaStream_t s, int variant = 0) {
     if constexpr (TPlan<N>::ok) {
-      const size_t smem = team_smem<N>(nprojtot_, nprojtot_ > 0 ? nl_.cap : 0);
+      const size_t smem = team_smem<N>(team_cap());
       if (smem <= SMEM_MAX && variant == 0) {
         static bool tattr = false;
         if (!tattr) {
           KS_CUDA(cudaFuncSetAttribute(k_plane_team<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX));
           tattr = true;
         }
-        PlaneNL nl = nl_;
-        if (nprojtot_ == 0) nl.cap = 0;
-        k_plane_team<N><<<dim3(N, n), TCfg<N>::PT, smem, s>>>(cb1, colbuf2_, ncols_, t_.col_xy, g_.xr, vplane_, nl,
-                                                              pf, nprojtot_, t_.tw);
+        k_plane_team<N><<<dim3(N, n), TCfg<N>::PT, smem, s>>>(cb1, colbuf2_, ncols_, t_.col_xy, g_.xr, rowym_,
+                                                              vplane_, team_nl(), team_cap(), t_.tw);
         KS_CHECK_LAUNCH();
         return;
       }
@@ -1463,9 +1507,10 @@ class FusedImpl final : public FusedOps {
                                        (int)SMEM_MAX));
           attr = true;
         }
-        const size_t tsmem = plane_smem<N>() + (N == 96 ? (size_t)N * N * sizeof(float) : 0);
-        k_plane_density_team<N><<<dim3(N, nch), TCfg<N>::PT, tsmem, s>>>(
-            colbuf1_, ncols_, t_.col_xy, g_.xr, n, density_chunk(0), occ, (float)(1.0 / g_.omega), dpartial_, t_.tw);
+        const size_t tsmem = plane_smem<N>() + (N == 96 ? (size_t)N * N * sizeof(float) : 0) + N * sizeof(int);
+        k_plane_density_team<N><<<dim3(N, nch), TCfg<N>::PT, tsmem, s>>>(colbuf1_, ncols_, t_.col_xy, g_.xr, rowym_, n,
+                                                                         density_chunk(0), occ,
+                                                                         (float)(1.0 / g_.omega), dpartial_, t_.tw);
         KS_CHECK_LAUNCH();
         return;
       }
@@ -1547,7 +1592,44 @@ class FusedImpl final : public FusedOps {
     nl_.line_off = upload(h_line_off_);
     nl_.nproj = g_.nproj;
     nl_.cap = nl_cap_;
+    // per-plane bitmap of the covered points ([z][jy][NW], bit jx) for the team plane kernel, and
+    // the projector values of every covered point per state (grown when the atoms move)
+    const int NW = (N_ + 31) / 32;
+    std::vector<uint32_t> bits((size_t)N_ * N_ * NW, 0u);
+    for (int z = 0; z < N_; ++z)
+      for (int pt = h_pt_off_[z]; pt < h_pt_off_[z + 1]; ++pt) {
+        const int jx = h_pt_xy_[pt] / N_, jy = h_pt_xy_[pt] % N_;
+        bits[((size_t)z * N_ + jy) * NW + (jx >> 5)] |= 1u << (jx & 31);
+      }
+    nlbits_ = upload(bits);
+    npts_ = h_pt_off_[N_];
+    if (nprojtot_ > 0 && (size_t)npts_ > nlval_pts_) {
+      if (nlval_) arena_.release(nlval_);
+      nlval_pts_ = (size_t)npts_ + npts_ / 8;                      // room for moves that cover more points
+      nlval_ = alloc<float2>((size_t)ns_ * nlval_pts_);
+    }
   }
+
+  // ym[g] of band row g (m_x = g for g <= xr, else g - 2 xr - 1): the largest |m_y| of the
+  // sphere's columns in that row, whose columns are exactly |m_y| <= ym[g]
+  void build_row_ranges() {
+    const int nband = 2 * g_.xr + 1;
+    std::vector<int> ym(nband, -1), cnt(nband, 0);
+    for (int xy : g_.col_xy) {
+      const int jx = xy / N_, jy = xy % N_;
+      const int mx = jx < (N_ + 1) / 2 ? jx : jx - N_, my = jy < (N_ + 1) / 2 ? jy : jy - N_;
+      const int gr = mx >= 0 ? mx : mx + nband;
+      if (gr < 0 || gr >= nband) fail(KS_ERR_ARG, "plane kernel: column outside the band (m_x = %d)", mx);
+      ym[gr] = std::max(ym[gr], std::abs(my));
+      cnt[gr]++;
+    }
+    for (int gr = 0; gr < nband; ++gr)
+      if (cnt[gr] != (ym[gr] < 0 ? 0 : 2 * ym[gr] + 1) || 2 * ym[gr] + 1 > N_)
+        fail(KS_ERR_ARG, "plane kernel: the columns of band row %d are not one m_y range", gr);
+    rowym_ = upload(ym);
+  }
+  TeamNL team_nl() const { return TeamNL{nlval_, nlbits_, nl_.pt_off, nl_.line_off, npts_}; }
+  int team_cap() const { return nprojtot_ > 0 ? nl_cap_ : 0; }
 
   // B[atom*nproj + l][G] = c_G[beta_Il] = Omega^{1/2} N^-3 sum_j exp(-iG.r_j) beta_Il(r_j), by the
   // separable DFT over each atom's box (k_box_dft_*), FP32.
@@ -1643,6 +1725,11 @@ class FusedImpl final : public FusedOps {
   void* Bimg_ = nullptr;             // B_ split into bf16 hi/lo operand tiles
   double2* pout_ = nullptr;
   float2* pf_ = nullptr;
+  const int* rowym_ = nullptr;       // [2 xr + 1] column range of each band row
+  const uint32_t* nlbits_ = nullptr; // [N][N][NW] covered points of each plane
+  float2* nlval_ = nullptr;          // [ns][nlval_pts_] projector values of the covered points
+  size_t nlval_pts_ = 0;
+  int npts_ = 0;                     // covered points of all planes
   double2* part_ = nullptr;
   size_t part_elems_ = 0;
   int nch_max_ = 1;

@@ -79,6 +79,9 @@ size_t estimate_bytes(const ks_cell_desc& d) {
     b += 2 * ns * d.N * ncols * 8 + N3 * 4 * 2;       // column buffers, planes, density partials
     const size_t np = (size_t)d.natoms * d.nproj;
     b += 2 * np * nG * 8 + np * ns * 32 + np * ns * 16 * 40;   // projector block and its split image
+    // projector values of the covered points per state (sphere points of every atom, 1/8 spare)
+    const double rp = d.proj_rc * d.N / d.L;
+    b += (size_t)(ns * (size_t)d.natoms * (4.19 * rp * rp * rp * 1.15 + 64.0)) * 8;
   }
   b += (size_t)d.natoms * 1400 * (d.nproj + 4) * 8;   // projector tables
   return b + (size_t(64) << 20);
