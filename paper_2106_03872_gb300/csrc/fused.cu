@@ -65,13 +65,14 @@ template <int N> struct FCfg {
 // Column c of the sphere holds 2h+1 consecutive coefficients (h = col_half[c]) starting at
 // col_off[c], z-indices 0..h then N-h..N-1: coefficient k has z = k for k <= h, else
 // k + N - 2h - 1.  The z-kernels derive a coefficient's (column, z) from these two numbers.
-// k_zinv takes ZSB consecutive states per CTA for one block of CT columns and keeps two
-// column blocks in shared memory: while one state's block is transformed, the next state's
+// k_zinv takes ZSB consecutive states per CTA for one block of CT columns and keeps ZNB
+// column blocks in shared memory: while one state's block is transformed, the next states'
 // coefficients arrive by asynchronous copies (software pipelining hides the load latency that
-// one block per CTA left exposed).  Dynamic shared memory: twiddles [N], then the two blocks
+// one block per CTA left exposed).  Dynamic shared memory: twiddles [N], then the ZNB blocks
 // [CT][N + 1].
 constexpr int ZSB = 4;
-template <int N> constexpr size_t zsmem() { return (size_t)(N + 2 * FCfg<N>::CT * (N + 1)) * sizeof(float2); }
+constexpr int ZNB = 3;
+template <int N> constexpr size_t zsmem() { return (size_t)(N + ZNB * FCfg<N>::CT * (N + 1)) * sizeof(float2); }
 
 template <int N>
 __device__ __forceinline__ void zinv_body(const float2* __restrict__ psi, int nG, const int* __restrict__ col_off,
@@ -80,7 +81,9 @@ __device__ __forceinline__ void zinv_body(const float2* __restrict__ psi, int nG
   constexpr int CT = FCfg<N>::CT, ld = N + 1, ZT = FCfg<N>::ZT;
   extern __shared__ __align__(16) float2 zsm[];
   float2* tw = zsm;
-  float2* sb[2] = {zsm + N, zsm + N + CT * ld};
+  float2* sb[ZNB];
+#pragma unroll
+  for (int i = 0; i < ZNB; ++i) sb[i] = zsm + N + i * CT * ld;
   __shared__ int coff[CT], chalf[CT];
   const int b0 = yblk * ZSB;
   const int nb = min(ZSB, nstates - b0);
@@ -102,15 +105,15 @@ __device__ __forceinline__ void zinv_body(const float2* __restrict__ psi, int nG
     for (int q = 0; q < SLOTS; ++q) {
       const int z = sub + q * TPC;
       if (z < N && z > h && z < N - h) {
-        sb[0][l * ld + z] = make_float2(0.f, 0.f);
-        sb[1][l * ld + z] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < ZNB; ++i) sb[i][l * ld + z] = make_float2(0.f, 0.f);
       }
     }
   }
-  auto issue = [&](int i) {                                          // state b0 + i -> block i & 1
+  auto issue = [&](int i) {                                          // state b0 + i -> block i % ZNB
     if (l >= nl) return;
     const float2* col = psi + (size_t)(b0 + i) * nG + g0;
-    float2* dst = sb[i & 1] + l * ld;
+    float2* dst = sb[i % ZNB] + l * ld;
 #pragma unroll
     for (int q = 0; q < SLOTS; ++q) {
       const int z = sub + q * TPC;
@@ -120,18 +123,19 @@ __device__ __forceinline__ void zinv_body(const float2* __restrict__ psi, int nG
       }
     }
   };
-  issue(0);
-  cp_async_commit();
+  // ZNB - 1 states in flight ahead of the one transformed; one commit group per state (empty
+  // groups past the last state keep the count)
+#pragma unroll
+  for (int i = 0; i < ZNB - 1; ++i) {
+    if (i < nb) issue(i);
+    cp_async_commit();
+  }
   for (int i = 0; i < nb; ++i) {
-    if (i + 1 < nb) {
-      issue(i + 1);
-      cp_async_commit();
-      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    } else {
-      cp_async_wait_all();
-    }
+    if (i + ZNB - 1 < nb) issue(i + ZNB - 1);
+    cp_async_commit();
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(ZNB - 1) : "memory");
     __syncthreads();
-    float2* s = sb[i & 1];
+    float2* s = sb[i % ZNB];
     cfft_lines<N, ZT, CT, true, +1>(s, nl, ld, 1, tw);
     // transpose out: element e = z * CT + lc; slots outside the column's range go back to zero
     float2* out = colbuf + (size_t)(b0 + i) * N * ncols + c0;
@@ -145,7 +149,7 @@ __device__ __forceinline__ void zinv_body(const float2* __restrict__ psi, int nG
         if (z > hc && z < N - hc) s[lc * ld + z] = make_float2(0.f, 0.f);
       }
     }
-    __syncthreads();                                                  // block i & 1 free for state i + 2
+    __syncthreads();                                                  // block i % ZNB free for state i + ZNB
   }
 }
 
@@ -730,8 +734,11 @@ __device__ __forceinline__ void plane_team_body(const float2* __restrict__ colbu
 
 // nlval[b][pt] = sum over the point's sphere entries e (in list order) and projectors q of
 // beta_e[q] pf[b][proj_e + q]: the projector add of Eq. 9 at every covered point, per state
-// (pf = D Omega^{1/2} p).  One thread per point for NLB consecutive states.
+// (pf = D Omega^{1/2} p).  One thread per point for NLB consecutive states; with four projectors
+// per atom an entry's beta and each state's four projections are 16-byte loads (pf rows and the
+// projector offsets are multiples of four).
 constexpr int NLB = 8;
+template <bool P4>
 __global__ void __launch_bounds__(256) k_nl_values(const float2* __restrict__ pf, int nprojtot, int n, PlaneNL nl,
                                                    int npts, float2* __restrict__ nlval) {
   const int pt = blockIdx.x * blockDim.x + threadIdx.x;
@@ -742,16 +749,35 @@ __global__ void __launch_bounds__(256) k_nl_values(const float2* __restrict__ pf
   for (int k = 0; k < NLB; ++k) ax[k] = ay[k] = 0.f;
   const int e0 = nl.ent_off[pt], e1 = nl.ent_off[pt + 1];
   for (int e = e0; e < e1; ++e) {
-    const float* bt = nl.ent_beta + (size_t)e * nl.nproj;
     const float2* pp = pf + (size_t)b0 * nprojtot + nl.ent_proj[e];
-    for (int q = 0; q < nl.nproj; ++q) {
-      const float bq = bt[q];
+    if constexpr (P4) {
+      const float4 bt = *reinterpret_cast<const float4*>(nl.ent_beta + (size_t)e * 4);
 #pragma unroll
       for (int k = 0; k < NLB; ++k) {
         if (k < nb) {
-          const float2 v = pp[(size_t)k * nprojtot + q];
-          ax[k] += bq * v.x;
-          ay[k] += bq * v.y;
+          const float4 v01 = *reinterpret_cast<const float4*>(pp + (size_t)k * nprojtot);
+          const float4 v23 = *reinterpret_cast<const float4*>(pp + (size_t)k * nprojtot + 2);
+          ax[k] += bt.x * v01.x;
+          ay[k] += bt.x * v01.y;
+          ax[k] += bt.y * v01.z;
+          ay[k] += bt.y * v01.w;
+          ax[k] += bt.z * v23.x;
+          ay[k] += bt.z * v23.y;
+          ax[k] += bt.w * v23.z;
+          ay[k] += bt.w * v23.w;
+        }
+      }
+    } else {
+      const float* bt = nl.ent_beta + (size_t)e * nl.nproj;
+      for (int q = 0; q < nl.nproj; ++q) {
+        const float bq = bt[q];
+#pragma unroll
+        for (int k = 0; k < NLB; ++k) {
+          if (k < nb) {
+            const float2 v = pp[(size_t)k * nprojtot + q];
+            ax[k] += bq * v.x;
+            ay[k] += bq * v.y;
+          }
         }
       }
     }
@@ -1229,8 +1255,11 @@ class FusedImpl final : public FusedOps {
       }
       if (npts_ > 0 && nlval_) {
         ProfScope ps(prof_, "nl_values", s);
-        k_nl_values<<<dim3((npts_ + 255) / 256, (n + NLB - 1) / NLB), 256, 0, s>>>(pf_, nprojtot_, n, nl_, npts_,
-                                                                                nlval_);
+        const dim3 grid((npts_ + 255) / 256, (n + NLB - 1) / NLB);
+        if (g_.nproj == 4)
+          k_nl_values<true><<<grid, 256, 0, s>>>(pf_, nprojtot_, n, nl_, npts_, nlval_);
+        else
+          k_nl_values<false><<<grid, 256, 0, s>>>(pf_, nprojtot_, n, nl_, npts_, nlval_);
         KS_CHECK_LAUNCH();
       }
     }
