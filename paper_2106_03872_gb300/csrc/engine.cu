@@ -1101,6 +1101,14 @@ template <typename T> class Engine final : public EngineBase {
  public:
   static void td_step_group(const std::vector<Engine*>& es, double dt, int propagator, int hartree_xc, int slot,
                             bool dipole, const std::function<void()>* mid, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+      bool fused = true;
+      for (Engine* e : es) fused = fused && e->fused_ != nullptr;
+      if (fused) {
+        td_step_group_powers(es, dt, propagator, hartree_xc, slot, dipole, mid, s);
+        return;
+      }
+    }
     const size_t ne = es.size();
     std::vector<C*> wa(ne), wb(ne), acc_full(ne), acc_half(ne), wn(ne);
     std::vector<const C*> w(ne), base(ne);
@@ -1171,6 +1179,111 @@ template <typename T> class Engine final : public EngineBase {
   }
 
  private:
+  // td_step_group on the fused path: the first three powers of each Taylor series are kept in
+  // three buffers, and the fourth power's epilogue forms the accumulators from them at once
+  // (TaylorEpi power-sum form), so the accumulators are written once per series instead of read
+  // and written at every power: 15 state-array passes per ETRS step instead of 27, with the same
+  // FP32 operations in the same order.
+  static void td_step_group_powers(const std::vector<Engine*>& es, double dt, int propagator, int hartree_xc,
+                                   int slot, bool dipole, const std::function<void()>* mid, cudaStream_t s) {
+    const size_t ne = es.size();
+    std::vector<C*> p1(ne), p2(ne), p3(ne), acc_full(ne), acc_half(ne);
+    for (size_t i = 0; i < ne; ++i) {
+      Engine* e = es[i];
+      const int n = e->ns_, nG = e->g_.nG;
+      // roles: psi, three powers, acc_full, acc_half
+      C* others[5];
+      int k = 0;
+      for (int q = 0; q < 6; ++q)
+        if (e->buf_[q] != e->psi_) others[k++] = e->buf_[q];
+      p1[i] = others[0];
+      p2[i] = others[1];
+      p3[i] = others[2];
+      acc_full[i] = others[3];
+      acc_half[i] = others[4];
+      if (hartree_xc || dipole) e->density_of(e->psi_, n, e->dens_, s);
+      if (dipole) ks::dipole<T>(e->dens_, e->g_.N, e->g_.L, e->dip_partials_, HXC_BLOCKS, e->dipoles_dev_ + 3 * slot, s);
+      if (hartree_xc) e->update_potential(e->dens_, s);
+      state_dots<T>(e->psi_, e->psi_, nG, n, e->dots_, s);
+      weighted_energy(e->dots_, e->occ_, n, nullptr, e->norms_dev_ + slot, s);
+    }
+    // coefficients (-i dt)^k / k! and (-i dt / 2)^k / k!, k = 1..4, formed in FP64 as a running
+    // product and rounded to FP32 each
+    float2 cf[4], ch[4];
+    {
+      double2 af = make_double2(1, 0), ah = make_double2(1, 0);
+      for (int kk = 1; kk <= 4; ++kk) {
+        af = cmul_scalar(af, make_double2(0, -dt / kk));
+        ah = cmul_scalar(ah, make_double2(0, -0.5 * dt / kk));
+        cf[kk - 1] = make_float2((float)af.x, (float)af.y);
+        ch[kk - 1] = make_float2((float)ah.x, (float)ah.y);
+      }
+    }
+    // one Taylor-4 series from the blocks x_i: powers into p1, p2, p3, then out1 (and out2 when
+    // set) = x + sum_k c_k H^k x in the fourth power's epilogue
+    auto series = [&](const std::vector<const C*>& x, const std::vector<C*>& out1, const float2* c1,
+                      const std::vector<C*>* out2, const float2* c2, bool energies) {
+      std::vector<FusedGroupItem> items(ne);
+      const std::vector<C*>* outs[3] = {&p1, &p2, &p3};
+      for (int kk = 1; kk <= 4; ++kk) {
+        for (size_t i = 0; i < ne; ++i) {
+          FusedGroupItem& it = items[i];
+          it = FusedGroupItem{};
+          it.ops = es[i]->fused_.get();
+          it.psi = kk == 1 ? x[i] : (*outs[kk - 2])[i];
+          it.n = es[i]->ns_;
+          it.v = es[i]->vtot_;
+          if (kk < 4) {
+            it.hpsi = (*outs[kk - 1])[i];
+          } else {
+            it.hpsi = nullptr;                 // the fourth power is not stored (skip_h)
+            it.te.skip_h = 1;
+            it.te.nsum = 4;
+            it.te.base = x[i];
+            it.te.w1 = p1[i];
+            it.te.w2 = p2[i];
+            it.te.acc1 = out1[i];
+            it.te.acc2 = out2 ? (*out2)[i] : nullptr;
+            for (int k = 0; k < 4; ++k) {
+              it.te.c1[k] = c1[k];
+              it.te.c2[k] = c2 ? c2[k] : make_float2(0.f, 0.f);
+            }
+          }
+        }
+        {
+          ProfScope scope(es[0]->prof, "apply_h", s);
+          fused_apply_h_group(items, s);
+        }
+        if (energies && kk == 1)
+          for (size_t i = 0; i < ne; ++i) {
+            Engine* e = es[i];
+            state_dots<T>(e->psi_, p1[i], e->g_.nG, e->ns_, e->dots_, s);
+            weighted_energy(e->dots_, e->occ_, e->ns_, hartree_xc ? e->parts_ : nullptr, e->energies_dev_ + slot,
+                            s);
+          }
+      }
+    };
+    std::vector<const C*> x(ne);
+    for (size_t i = 0; i < ne; ++i) x[i] = es[i]->psi_;
+    series(x, acc_full, cf, propagator == 0 ? &acc_half : nullptr, ch, true);
+    if (propagator == 1) {
+      for (size_t i = 0; i < ne; ++i) es[i]->psi_ = acc_full[i];
+      return;
+    }
+    if (mid) (*mid)();
+    for (size_t i = 0; i < ne; ++i) {
+      Engine* e = es[i];
+      if (hartree_xc) {
+        e->density_of(acc_full[i], e->ns_, e->dens_, s);
+        e->update_potential(e->dens_, s);
+      }
+      x[i] = acc_half[i];
+    }
+    // second half: psi(t + dt) = acc_half + sum_k (-i dt/2)^k/k! H(t+dt)^k acc_half
+    series(x, acc_full, ch, nullptr, nullptr, false);
+    for (size_t i = 0; i < ne; ++i) es[i]->psi_ = acc_full[i];
+  }
+
   // wn_i = H w_i for every engine, with acc1_i <- base_i + a1 wn_i and acc2_i <- base_i + a2 wn_i
   // (base null: each accumulator's own value): one packed fused launch per kernel when every
   // engine has the fused path, else engine by engine (H application, then one accumulation pass).

@@ -219,7 +219,27 @@ __device__ __forceinline__ void zfwd_body(const float2* __restrict__ colbuf, con
       const float2 h = make_float2(u.x * scale + kv[q] * pv[q].x, u.y * scale + kv[q] * pv[q].y);
       const size_t i = off + g0 + k;
       if (!te.skip_h) hpsi[i] = h;
-      if (te.acc1) {
+      if (te.nsum) {
+        // acc <- base + c[0] w1 + c[1] w2 + c[2] psi + c[3] h, term by term
+        const float2 b0 = te.base[i], v1 = te.w1[i], v2 = te.w2[i];
+        const float2 tv[4] = {v1, v2, pv[q], h};
+        float2 b = b0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          b.x += te.c1[k].x * tv[k].x - te.c1[k].y * tv[k].y;
+          b.y += te.c1[k].x * tv[k].y + te.c1[k].y * tv[k].x;
+        }
+        te.acc1[i] = b;
+        if (te.acc2) {
+          float2 c = b0;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            c.x += te.c2[k].x * tv[k].x - te.c2[k].y * tv[k].y;
+            c.y += te.c2[k].x * tv[k].y + te.c2[k].y * tv[k].x;
+          }
+          te.acc2[i] = c;
+        }
+      } else if (te.acc1) {
         // the accumulators of the Taylor series (Eq. 8): acc <- base + a h
         float2 b = te.base_is_psi ? pv[q] : (te.base ? te.base[i] : te.acc1[i]);
         b.x += te.a1.x * h.x - te.a1.y * h.y;

@@ -17,6 +17,10 @@ namespace ks {
 // is set, acc2 <- base + a2 h, with base the given block, or each accumulator's own old value when
 // base is null.  base_is_psi: base is the H application's own input (its values are already in
 // registers).  skip_h: H psi itself is not stored (the last power of a Taylor series).
+// Power-sum form (nsum = 4, the fourth power of a Taylor-4 series whose earlier powers were
+// kept): acc1 <- base + c1[0] w1 + c1[1] w2 + c1[2] psi + c1[3] h, with psi the H application's
+// input (the third power, in registers), and acc2 likewise with c2 when set; the terms are added
+// in this order, the same FP32 operations as four incremental updates of a stored accumulator.
 struct TaylorEpi {
   float2* acc1 = nullptr;
   float2 a1{0.f, 0.f};
@@ -25,6 +29,11 @@ struct TaylorEpi {
   const float2* base = nullptr;
   int base_is_psi = 0;
   int skip_h = 0;
+  int nsum = 0;
+  const float2* w1 = nullptr;
+  const float2* w2 = nullptr;
+  float2 c1[4] = {};
+  float2 c2[4] = {};
 };
 
 class FusedOps {
