@@ -416,7 +416,7 @@ template <> struct TPlan<32> { static constexpr bool ok = true; static constexpr
 template <> struct TPlan<48> { static constexpr bool ok = true; static constexpr int R1 = 4, R2 = 12, W = 4; };
 template <> struct TPlan<64> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 8, W = 4; };
 template <> struct TPlan<96> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 12, W = 4; };
-template <> struct TPlan<128> { static constexpr bool ok = true; static constexpr int R1 = 16, R2 = 8, W = 8; };
+template <> struct TPlan<128> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 16, W = 8; };
 
 template <int N> struct TCfg {
   static constexpr int TEAMS = (N + 31) / 32;
