@@ -418,6 +418,18 @@ template <> struct TPlan<64> { static constexpr bool ok = true; static constexpr
 template <> struct TPlan<96> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 12, W = 4; };
 template <> struct TPlan<128> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 16, W = 8; };
 
+// Which compiled form of the team plane kernel runs where both would do (the two forms are the
+// same code, plane_team_body, and give bitwise the same results; their register allocations
+// differ at the 80- and 64-register bounds): at N = 96 the single-cell kernel (no spills) runs
+// for every member of a packed H application too, the packed kernel spilling 68 bytes and taking
+// 0.683 against 0.614 ms per gs96-sized block; at N = 128 the packed kernel (20 bytes of spills)
+// runs for single-cell H applications too, the single-cell one spilling 112 bytes and taking
+// 6.75 against 6.44 ms per td128 block.
+template <int N> struct PlaneForm {
+  static constexpr bool single_per_member = N == 96;
+  static constexpr bool packed_for_single = N == 128;
+};
+
 template <int N> struct TCfg {
   static constexpr int TEAMS = (N + 31) / 32;
   static constexpr int PT = 32 * TPlan<N>::W * TEAMS;
@@ -1354,9 +1366,16 @@ class FusedImpl final : public FusedOps {
         }
         {
           ProfScope ps(f0->prof_, "plane", s);
-          k_plane_team_group<N><<<dim3(N, s0), TCfg<N>::PT, smem, s>>>(gd, f0->ncols_, f0->t_.col_xy, f0->g_.xr,
-                                                                       f0->rowym_, f0->t_.tw);
-          KS_CHECK_LAUNCH();
+          if constexpr (PlaneForm<N>::single_per_member) {
+            for (size_t k = a; k < std::min(items.size(), a + GMAX); ++k) {
+              FusedImpl* f = static_cast<FusedImpl*>(items[k].ops);
+              f->template launch_plane_team_single<N>(items[k].n, s);
+            }
+          } else {
+            k_plane_team_group<N><<<dim3(N, s0), TCfg<N>::PT, smem, s>>>(gd, f0->ncols_, f0->t_.col_xy, f0->g_.xr,
+                                                                         f0->rowym_, f0->t_.tw);
+            KS_CHECK_LAUNCH();
+          }
         }
         {
           ProfScope ps(f0->prof_, "zfwd", s);
@@ -1494,14 +1513,28 @@ class FusedImpl final : public FusedOps {
     if constexpr (TPlan<N>::ok) {
       const size_t smem = team_smem<N>(team_cap());
       if (smem <= SMEM_MAX && variant == 0) {
-        static bool tattr = false;
-        if (!tattr) {
-          KS_CUDA(cudaFuncSetAttribute(k_plane_team<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX));
-          tattr = true;
+        if constexpr (PlaneForm<N>::packed_for_single) {
+          static bool gattr = false;
+          if (!gattr) {
+            KS_CUDA(cudaFuncSetAttribute(k_plane_team_group<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_MAX));
+            gattr = true;
+          }
+          GDesc gd{};
+          gd.nm = 1;
+          GMember& m = gd.m[0];
+          m.cb1 = const_cast<float2*>(cb1);
+          m.cb2 = colbuf2_;
+          m.vplane = vplane_;
+          m.nl = team_nl();
+          m.cap = team_cap();
+          m.n = n;
+          k_plane_team_group<N><<<dim3(N, n), TCfg<N>::PT, smem, s>>>(gd, ncols_, t_.col_xy, g_.xr, rowym_, t_.tw);
+          KS_CHECK_LAUNCH();
+          return;
         }
-        k_plane_team<N><<<dim3(N, n), TCfg<N>::PT, smem, s>>>(cb1, colbuf2_, ncols_, t_.col_xy, g_.xr, rowym_,
-                                                              vplane_, team_nl(), team_cap(), t_.tw);
-        KS_CHECK_LAUNCH();
+        if (cb1 != colbuf1_) fail(KS_ERR_ARG, "plane kernel: column buffer");
+        launch_plane_team_single<N>(n, s);
         return;
       }
     }
@@ -1518,6 +1551,21 @@ class FusedImpl final : public FusedOps {
     k_plane<N><<<grid, FCfg<N>::PT, pf_smem ? with_pf : base, s>>>(cb1, colbuf2_, ncols_, t_.col_xy, g_.xr,
                                                                    vplane_, nl_, pf, nprojtot_, pf_smem, t_.tw);
     KS_CHECK_LAUNCH();
+  }
+  // The single-cell team plane kernel over n states of this cell's column buffers.
+  template <int N> void launch_plane_team_single(int n, cudaStream_t s) {
+    if constexpr (TPlan<N>::ok) {
+      static bool tattr = false;
+      if (!tattr) {
+        KS_CUDA(cudaFuncSetAttribute(k_plane_team<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX));
+        tattr = true;
+      }
+      const size_t smem = team_smem<N>(team_cap());
+      if (smem > SMEM_MAX) fail(KS_ERR_ARG, "plane kernel: %zu bytes of shared memory for N=%d", smem, N);
+      k_plane_team<N><<<dim3(N, n), TCfg<N>::PT, smem, s>>>(colbuf1_, colbuf2_, ncols_, t_.col_xy, g_.xr, rowym_,
+                                                            vplane_, team_nl(), team_cap(), t_.tw);
+      KS_CHECK_LAUNCH();
+    }
   }
   template <int N> void launch_plane_inverse(int n, float2* out, cudaStream_t s) {
     static bool attr = false;
