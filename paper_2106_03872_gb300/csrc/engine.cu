@@ -1222,7 +1222,7 @@ template <typename T> class Engine final : public EngineBase {
     // one Taylor-4 series from the blocks x_i: powers into p1, p2, p3, then out1 (and out2 when
     // set) = x + sum_k c_k H^k x in the fourth power's epilogue
     auto series = [&](const std::vector<const C*>& x, const std::vector<C*>& out1, const float2* c1,
-                      const std::vector<C*>* out2, const float2* c2, bool energies) {
+                      const std::vector<C*>* out2, const float2* c2, bool energies, bool cols_ready) {
       std::vector<FusedGroupItem> items(ne);
       const std::vector<C*>* outs[3] = {&p1, &p2, &p3};
       for (int kk = 1; kk <= 4; ++kk) {
@@ -1232,6 +1232,7 @@ template <typename T> class Engine final : public EngineBase {
           it.ops = es[i]->fused_.get();
           it.psi = kk == 1 ? x[i] : (*outs[kk - 2])[i];
           it.n = es[i]->ns_;
+          it.cols_ready = kk == 1 && cols_ready;
           it.v = es[i]->vtot_;
           if (kk < 4) {
             it.hpsi = (*outs[kk - 1])[i];
@@ -1265,7 +1266,9 @@ template <typename T> class Engine final : public EngineBase {
     };
     std::vector<const C*> x(ne);
     for (size_t i = 0; i < ne; ++i) x[i] = es[i]->psi_;
-    series(x, acc_full, cf, propagator == 0 ? &acc_half : nullptr, ch, true);
+    // the density of psi just ran on the fused path and left the z transform of psi in each
+    // cell's column buffer: the first H application of psi starts from it
+    series(x, acc_full, cf, propagator == 0 ? &acc_half : nullptr, ch, true, hartree_xc || dipole);
     if (propagator == 1) {
       for (size_t i = 0; i < ne; ++i) es[i]->psi_ = acc_full[i];
       return;
@@ -1280,7 +1283,7 @@ template <typename T> class Engine final : public EngineBase {
       x[i] = acc_half[i];
     }
     // second half: psi(t + dt) = acc_half + sum_k (-i dt/2)^k/k! H(t+dt)^k acc_half
-    series(x, acc_full, ch, nullptr, nullptr, false);
+    series(x, acc_full, ch, nullptr, nullptr, false, false);
     for (size_t i = 0; i < ne; ++i) es[i]->psi_ = acc_full[i];
   }
 

@@ -1321,7 +1321,7 @@ class FusedImpl final : public FusedOps {
     if constexpr (!TPlan<N>::ok) {
       for (const auto& it : items) {
         FusedImpl* f = static_cast<FusedImpl*>(it.ops);
-        f->zinv(it.psi, it.n, s);
+        if (!it.cols_ready) f->zinv(it.psi, it.n, s);
         f->template launch_plane<N>(it.n, f->colbuf1_, f->pf_, s);
         f->template launch_zfwd<N>(it.psi, it.hpsi, it.n, it.te, s);
       }
@@ -1358,7 +1358,9 @@ class FusedImpl final : public FusedOps {
           smem = std::max(smem, team_smem<N>(m.cap));
         }
         if (smem > SMEM_MAX) fail(KS_ERR_ARG, "packed H application: %zu bytes of shared memory", smem);
-        {
+        bool cols_ready = true;
+        for (size_t k = a; k < std::min(items.size(), a + GMAX); ++k) cols_ready = cols_ready && items[k].cols_ready;
+        if (!cols_ready) {
           ProfScope ps(f0->prof_, "zinv", s);
           k_zinv_group<N><<<dim3(ncb, z0), FCfg<N>::ZT, zsmem<N>(), s>>>(gd, f0->g_.nG, f0->t_.col_off,
                                                                          f0->t_.col_half, f0->ncols_, f0->t_.tw);

@@ -66,6 +66,10 @@ struct FusedGroupItem {
   int n = 0;
   const float* v = nullptr;
   TaylorEpi te{};
+  // the cell's first column buffer already holds the z transform of these n states (a density
+  // of the same block was the cell's last use of it): the z-transform launch is skipped when
+  // every member of a launch has it
+  bool cols_ready = false;
 };
 
 // H psi of several cells' blocks that share one grid geometry (same L, N and cutoff, so the same
