@@ -292,6 +292,29 @@ def hpsi_fft_flops(geo):
     return geo["nstates"] * 2 * 5.0 * N ** 3 * math.log2(N ** 3)
 
 
+def tensor_gemms(entries, geo, pk, steps, nprojtot):
+    """Tensor-core GEMM stages of one block iteration: their tensor work (split-BF16: three bf16
+    products per real product for the overlaps, four for the rotations) over their device time,
+    against the measured bf16 peak.  The stage timers cover every launch of the stage (the split-K
+    reductions included), so the fraction is a lower bound of the MMA pipe's busy time."""
+    n, K = geo["nstates"], geo["nG"]
+    # algorithmic flops per launch: 8 real flops per complex MAC
+    model = {"gram": (8.0 * n * n * K, 3, 2),            # S and H_raw: two launches per step
+             "proj_gemm": (8.0 * nprojtot * n * K, 3, 1),  # projections onto the projector block
+             "rotate": (8.0 * n * 2 * n * K, 4, 2)}        # psi and H psi rotated from [psi; H psi; H^2 psi]
+    out = {}
+    for name, (alg, split, per_step) in model.items():
+        if name not in entries:
+            continue
+        ms = entries[name][0] / steps
+        tens = alg * split * per_step
+        out[name] = {"ms_per_step": ms, "launches_per_step": per_step, "flops_algorithmic_per_step": alg * per_step,
+                     "split_products": split, "flops_tensor_per_step": tens,
+                     "tflops_tensor": tens / (ms * 1e-3) / 1e12,
+                     "frac_of_bf16_peak": tens / (ms * 1e-3) / 1e12 / pk["bf16"], "peak_src": pk["src"]}
+    return out
+
+
 def roofline(entries, geo, pk, steps):
     """The dominant kernel: the main-stream stage with the most device time.  A stage of the H psi
     pipeline is rated against HBM on the algorithmic bytes of the whole H psi it serves (one launch
@@ -429,6 +452,7 @@ def main_gpu(args):
     value = replica_throughput(world, ns * N ** 3 * args.steps, total_ms)
 
     rl, rl_name, rl_side = roofline(entries, geo, pk, args.steps)
+    tgemm = tensor_gemms(entries, geo, pk, args.steps, int(np.asarray(cell["pos"]).reshape(-1, 3).shape[0]) * cell["nproj"])
 
     # ---- H psi alone (device buffers)
     psi = torch.from_numpy(c0).to("cuda", torch.complex64)
@@ -587,7 +611,7 @@ def main_gpu(args):
                    "global_batch": ns * world, "grid": N, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed (256 MB device write) before the timed call of K steps; one step's working set "
                          "(psi, H psi, H^2 psi: 354 MB) exceeds the 126 MB L2"},
-        "roofline": rl, "side_stream_roofline": rl_side,
+        "roofline": rl, "side_stream_roofline": rl_side, "tensor_gemms": tgemm,
         "cpu_baseline": cpu_baseline_obj(cpu, cpu_all) if cpu else None, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk.summary(), "hpsi_only": hpsi_only, "fp64_gpu": fp64, "fp64_subspace": fp64_sub, "td": td,
         "small_cell": small, "autotune": ks.autotune_report(),
