@@ -43,7 +43,7 @@ constexpr int C32_THREADS = 1024;
 //       over rows i; conj(L_kJ) held in registers).
 // Then the off-diagonal blocks of X by block rows I: T_IJ = sum_{K=J}^{I-1} L_IK X_KJ,
 // X_IJ = -W_I T_IJ for all J < I at once.
-constexpr int CB = 16;
+constexpr int CB = 8;
 
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ float2 c_mulc(float2 a, float2 b) {   // a * conj(b)

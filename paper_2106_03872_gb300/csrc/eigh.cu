@@ -93,98 +93,95 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
 }
 
 // Phase 0 of the Rayleigh-Ritz variant: A = conj(M) H_raw M^T (FP32), Hermitian part, in the
-// [n][ld] matrix region; R (EH_RREG float2) stages operand rows.  M is lower triangular.
+// [n][ld] matrix region; R (EH_RREG float2) stages operand chunks.  M is lower triangular.
+// Thread (warp w, lane): rows 4w + u (u < 4), columns lane + 32v (v < 4), 16 accumulators; each
+// element's sum runs over k in ascending order (terms of M's zero triangle add exact zeros).
+constexpr int RR_KC = 16, RR_MLD = EH_MAXN + 1;
 __device__ __forceinline__ void subspace_matrix(const float2* __restrict__ Hraw, const float2* __restrict__ M, int n,
                                                 float2* A, float2* R, float2* __restrict__ Aout) {
   const int ld = n + 1;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const float2 zero = make_float2(0.f, 0.f);
-  // T = H_raw M^T: T_ij = sum_{k <= j} H_ik M_jk, in two halves of 64 rows.  Thread: rows
-  // r0 + warp + 32u (u < 2), columns lane + 32v (v < 4); K staged 32 at a time.
-  constexpr int KC = 32, MLD = EH_MAXN + 1;
-  float2* Hs = R;                                                    // [64][KC]
-  float2* Mt = R + 64 * KC;                                          // [KC][MLD]: Mt[kk][j] = M_j,k0+kk
-  for (int r0 = 0; r0 < n; r0 += 64) {
-    float2 acc[2][4];
+  float2 acc[4][4];
+  // T = H_raw M^T: T_ij = sum_k H_ik M_jk
+  float2* Hs = R;                                                    // [EH_MAXN][RR_KC]: H_i,k0+kk
+  float2* Mt = R + EH_MAXN * RR_KC;                                  // [RR_KC][RR_MLD]: M_j,k0+kk
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = zero;
-    for (int k0 = 0; k0 < n; k0 += KC) {
-      const int c = k0 / KC;
-      __syncthreads();
-      for (int e = t; e < 64 * KC; e += EH_THREADS) {
-        const int i = r0 + (e >> 5), k = k0 + (e & 31);
-        Hs[e] = (i < n && k < n) ? Hraw[i * n + k] : zero;
-      }
-      for (int e = t; e < EH_MAXN * KC; e += EH_THREADS) {
-        const int j = e >> 5, kk = e & 31, k = k0 + kk;
-        Mt[kk * MLD + j] = (j < n && k < n) ? M[j * n + k] : zero;
-      }
-      __syncthreads();
+    for (int v = 0; v < 4; ++v) acc[u][v] = zero;
+  for (int k0 = 0; k0 < n; k0 += RR_KC) {
+    __syncthreads();
+    for (int e = t; e < EH_MAXN * RR_KC; e += EH_THREADS) {
+      const int i = e / RR_KC, k = k0 + e % RR_KC;
+      Hs[e] = (i < n && k < n) ? Hraw[i * n + k] : zero;
+    }
+    for (int e = t; e < EH_MAXN * RR_KC; e += EH_THREADS) {
+      const int j = e / RR_KC, kk = e % RR_KC, k = k0 + kk;
+      Mt[kk * RR_MLD + j] = (j < n && k < n) ? M[j * n + k] : zero;
+    }
+    __syncthreads();
 #pragma unroll 4
-      for (int kk = 0; kk < KC; ++kk) {
-        float2 hv[2], mv[4];
+    for (int kk = 0; kk < RR_KC; ++kk) {
+      float2 hv[4], mv[4];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) hv[u] = Hs[(warp + 32 * u) * KC + kk];
+      for (int u = 0; u < 4; ++u) hv[u] = Hs[(4 * warp + u) * RR_KC + kk];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) mv[v] = Mt[kk * MLD + lane + 32 * v];
+      for (int v = 0; v < 4; ++v) mv[v] = Mt[kk * RR_MLD + lane + 32 * v];
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-          if (v >= c)                                                // M_jk = 0 for j < k0
+      for (int v = 0; v < 4; ++v)
+        if (32 * v + 31 >= k0)                                       // M_jk = 0 for every j of group v
 #pragma unroll
-            for (int u = 0; u < 2; ++u) acc[u][v] = cfma(acc[u][v], hv[u], mv[v]);
-      }
+          for (int u = 0; u < 4; ++u) acc[u][v] = cfma(acc[u][v], hv[u], mv[v]);
     }
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int i = r0 + warp + 32 * u, j = lane + 32 * v;
-        if (i < n && j < n) A[i * ld + j] = acc[u][v];
-      }
   }
-  // A = conj(M) T in place: A_ij = sum_{k <= i} conj(M_ik) T_kj.  Row blocks of 64 from the
-  // bottom up: block b reads T rows < its end only, so it may overwrite its own rows.
-  float2* Ms = R;                                                    // [64][EH_MAXN]
-  for (int i0 = ((n - 1) / 64) * 64; i0 >= 0; i0 -= 64) {
-    const int kend = min(n, i0 + 64);
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = 4 * warp + u, j = lane + 32 * v;
+      if (i < n && j < n) A[i * ld + j] = acc[u][v];
+    }
+  // A = conj(M) T: A_ij = sum_{k <= i} conj(M_ik) T_kj, all rows at once (written after the sums)
+  float2* Ms = R;                                                    // [EH_MAXN][RR_KC]: M_i,k0+kk
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = zero;
+  for (int k0 = 0; k0 < n; k0 += RR_KC) {
     __syncthreads();
-    for (int e = t; e < 64 * EH_MAXN; e += EH_THREADS) {
-      const int i = i0 + (e >> 7), k = e & (EH_MAXN - 1);
-      Ms[e] = (i < n && k < kend) ? M[i * n + k] : zero;
+    for (int e = t; e < EH_MAXN * RR_KC; e += EH_THREADS) {
+      const int i = e / RR_KC, k = k0 + e % RR_KC;
+      Ms[e] = (i < n && k < n) ? M[i * n + k] : zero;
     }
     __syncthreads();
-    float2 acc[2][4];
+    const int kend = min(RR_KC, n - k0);
+    if (4 * warp + 3 >= k0) {                                        // M_ik = 0 for every row i of the warp
+      for (int kk = 0; kk < kend; ++kk) {
+        const int k = k0 + kk;
+        float2 ma[4], tv[4];
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+        for (int u = 0; u < 4; ++u) ma[u] = Ms[(4 * warp + u) * RR_KC + kk];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = zero;
-    const int ia = i0 + warp, ib = i0 + 32 + warp;
-    for (int k = 0; k < kend; ++k) {
-      float2 tv[4];
+        for (int v = 0; v < 4; ++v) {
+          const int j = lane + 32 * v;
+          tv[v] = j < n ? A[k * ld + j] : zero;
+        }
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int j = lane + 32 * v;
-        tv[v] = j < n ? A[k * ld + j] : zero;
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = cfmac(acc[u][v], ma[u], tv[v]);
       }
-      const float2 ma = Ms[warp * EH_MAXN + k], mb = Ms[(32 + warp) * EH_MAXN + k];
-      if (k <= ia)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[0][v] = cfmac(acc[0][v], ma, tv[v]);
-      if (k <= ib)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[1][v] = cfmac(acc[1][v], mb, tv[v]);
     }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int i = i0 + warp + 32 * u, j = lane + 32 * v;
-        if (i < n && j < n) A[i * ld + j] = acc[u][v];
-      }
   }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = 4 * warp + u, j = lane + 32 * v;
+      if (i < n && j < n) A[i * ld + j] = acc[u][v];
+    }
   __syncthreads();
   // Hermitian part (one thread per pair), real diagonal
   for (int i = warp; i < n; i += EH_WARPS)
@@ -200,54 +197,56 @@ __device__ __forceinline__ void subspace_matrix(const float2* __restrict__ Hraw,
 }
 
 // Phase 5 of the Rayleigh-Ritz variant: with V staged in the matrix region (V_kr at k ld + r),
-// C = Vt M (C_rj = sum_{k >= j} V_kr M_kj) and Mcat row rank(r) = [(1 + alpha lam_r) C_r | -alpha C_r].
+// C = Vt M (C_rj = sum_{k >= j} V_kr M_kj, k ascending) and Mcat row rank(r) =
+// [(1 + alpha lam_r) C_r | -alpha C_r].  Thread: rows r = 4w + u, columns lane + 32v.
 __device__ __forceinline__ void step_matrix(const float2* Vs, const float2* __restrict__ M, int n, const float* lam,
                                             const int* rank, float alpha, float2* R, float2* __restrict__ Mcat) {
   const int ld = n + 1;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const float2 zero = make_float2(0.f, 0.f);
-  float2* Ms = R;                                                    // [64][EH_MAXN]: M rows k0..
-  for (int pass = 0; pass < 2; ++pass) {
-    float2 acc[2][4];
+  float2* Ms = R;                                                    // [RR_KC][EH_MAXN]: M rows k0..
+  float2 acc[4][4];
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = zero;
-    for (int k0 = 0; k0 < n; k0 += 64) {
-      __syncthreads();
-      for (int e = t; e < 64 * EH_MAXN; e += EH_THREADS) {
-        const int k = k0 + (e >> 7), j = e & (EH_MAXN - 1);
-        Ms[e] = (k < n && j < n) ? M[k * n + j] : zero;
-      }
-      __syncthreads();
-      const int kend = min(64, n - k0);
-      for (int kr = 0; kr < kend; ++kr) {
-        const int k = k0 + kr;
-        float2 vr[2], mv[4];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) vr[u] = Vs[k * ld + warp + 32 * (2 * pass + u)];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) mv[v] = Ms[kr * EH_MAXN + lane + 32 * v];
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-          if (32 * v <= k)                                           // M_kj = 0 for j > k
-#pragma unroll
-            for (int u = 0; u < 2; ++u) acc[u][v] = cfma(acc[u][v], vr[u], mv[v]);
-      }
+    for (int v = 0; v < 4; ++v) acc[u][v] = zero;
+  for (int k0 = 0; k0 < n; k0 += RR_KC) {
+    __syncthreads();
+    for (int e = t; e < RR_KC * EH_MAXN; e += EH_THREADS) {
+      const int k = k0 + e / EH_MAXN, j = e % EH_MAXN;
+      Ms[e] = (k < n && j < n) ? M[k * n + j] : zero;
     }
+    __syncthreads();
+    const int kend = min(RR_KC, n - k0);
+    for (int kr = 0; kr < kend; ++kr) {
+      const int k = k0 + kr;
+      float2 vr[4], mv[4];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int r = warp + 32 * (2 * pass + u);
-      if (r < n) {
-        const float f = 1.f + alpha * lam[r];
-        float2* row = Mcat + (size_t)rank[r] * 2 * n;
+      for (int u = 0; u < 4; ++u) {
+        const int r = 4 * warp + u;
+        vr[u] = r < n ? Vs[k * ld + r] : zero;
+      }
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const int j = lane + 32 * v;
-          if (j < n) {
-            row[j] = make_float2(f * acc[u][v].x, f * acc[u][v].y);
-            row[n + j] = make_float2(-alpha * acc[u][v].x, -alpha * acc[u][v].y);
-          }
+      for (int v = 0; v < 4; ++v) mv[v] = Ms[kr * EH_MAXN + lane + 32 * v];
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (32 * v <= k)                                             // M_kj = 0 for j > k
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u][v] = cfma(acc[u][v], vr[u], mv[v]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = 4 * warp + u;
+    if (r < n) {
+      const float f = 1.f + alpha * lam[r];
+      float2* row = Mcat + (size_t)rank[r] * 2 * n;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int j = lane + 32 * v;
+        if (j < n) {
+          row[j] = make_float2(f * acc[u][v].x, f * acc[u][v].y);
+          row[n + j] = make_float2(-alpha * acc[u][v].x, -alpha * acc[u][v].y);
         }
       }
     }
