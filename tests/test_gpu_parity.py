@@ -336,6 +336,25 @@ def test_block_iteration_converged_eigenvalues_after_refinement(ks, meas):
     g.close()
 
 
+def test_td_step_parity_96_grid(ks, meas):
+    """A real-time step on the 96^3 grid of the ground-state workload (3 states, Hartree +
+    Slater): the mixed path's packed H applications at N = 96 (the single-cell plane kernel per
+    member), the kept Taylor powers summed in the fourth power's epilogue, and the first H
+    application starting from the density's z transform, against the oracle."""
+    cell = inputs.cell("gs96", nstates=3)
+    ref = ko.Cell(cell)
+    q, _ = ko.cholqr(inputs.random_coeffs(cell["seed"], 3, ref.nG))
+    g = ks.Grid(cell, prec="bf16x3")
+    g.set_states(q)
+    norms, energies = g.td_step(0.05, 1, "etrs", True)
+    c_ref, n_ref, e_ref = ko.td_run(ref, q, 0.05, 1, "etrs", True)
+    got = g.get_states()
+    meas("rel(got, c_ref)", rel(got, c_ref), 5e-5)
+    meas("np.max(np.abs(norms - n_ref))", np.max(np.abs(norms - n_ref)), 1e-5 * n_ref[0])
+    meas("np.max(np.abs(energies - e_ref))", np.max(np.abs(energies - e_ref)), 1e-4 * max(1, np.max(np.abs(e_ref))))
+    g.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 @pytest.mark.parametrize("propagator", ["etrs", "taylor"])
 @pytest.mark.parametrize("hxc", [True, False])
