@@ -306,7 +306,9 @@ ks_status ks_serve_poll(ks_server s, uint64_t ticket, int timeout_ms, double* re
  * (block iterations), in real-time steps (each group step counted once), in retiring requests;
  * then the number of request starts, ground-state quanta, real-time group steps, request-steps
  * in those groups (their ratio is the mean group size), and the bytes the server's device pool
- * holds.  nout <= 9. */
+ * holds; then the parts of the start time (engine creation, initial states, orthonormalisation
+ * of real-time requests), the number of slabs the device pool obtained from the device and the
+ * seconds spent obtaining them.  nout <= 14. */
 ks_status ks_serve_stats(ks_server s, double* out, int nout);
 
 /* Result sizes for a ticket: number of doubles in result_out, nstates, nG. */

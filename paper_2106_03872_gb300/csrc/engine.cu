@@ -2,6 +2,7 @@
 // composed from the kernels.  T = double is the FP64 path; T = float the mixed path
 // (its fused Hamiltonian lives in fused.cu and plugs in through FusedOps).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <functional>
 #include <cstring>
@@ -17,9 +18,39 @@ DevicePool::~DevicePool() {
   for (auto& sl : slabs_) cudaFree(sl.base);
 }
 
+// First fit in the slabs; a new slab when none has room.  The slab is obtained from the device
+// without the lock held (cudaMalloc of a slab can take tens of milliseconds on a busy device,
+// and every other engine's allocations and releases would wait behind it).
 void* DevicePool::alloc(size_t bytes) {
   bytes = std::max<size_t>(256, (bytes + 255) / 256 * 256);
-  std::lock_guard<std::mutex> lk(mu_);
+  std::unique_lock<std::mutex> lk(mu_);
+  if (void* p = take(bytes)) return p;
+  lk.unlock();
+  Slab sl;
+  sl.size = std::max(slab_bytes_, bytes);
+  void* base = nullptr;
+  const auto g0 = std::chrono::steady_clock::now();
+  const cudaError_t e = cudaMalloc(&base, sl.size);
+  const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - g0).count();
+  lk.lock();
+  grow_s_ += dt;
+  ++grows_;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (void* p = take(bytes)) return p;                             // another thread's slab may fit
+    fail(KS_ERR_NOMEM, "device pool: cudaMalloc of a %zu-byte slab failed (%s)", sl.size, cudaGetErrorString(e));
+  }
+  sl.base = static_cast<char*>(base);
+  sl.free_blocks[0] = sl.size;
+  slabs_.push_back(std::move(sl));
+  reserved_ += slabs_.back().size;
+  void* p = take(bytes);
+  if (!p) fail(KS_ERR_STATE, "internal: device pool slab without room");
+  return p;
+}
+
+// A block of `bytes` from the first slab with a free block that large (lock held), or null.
+void* DevicePool::take(size_t bytes) {
   for (int si = 0; si < (int)slabs_.size(); ++si) {
     Slab& sl = slabs_[si];
     for (auto it = sl.free_blocks.begin(); it != sl.free_blocks.end(); ++it) {
@@ -33,23 +64,7 @@ void* DevicePool::alloc(size_t bytes) {
       return p;
     }
   }
-  // grow: a new slab of at least slab_bytes_
-  Slab sl;
-  sl.size = std::max(slab_bytes_, bytes);
-  void* base = nullptr;
-  const cudaError_t e = cudaMalloc(&base, sl.size);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    fail(KS_ERR_NOMEM, "device pool: cudaMalloc of a %zu-byte slab failed (%s)", sl.size, cudaGetErrorString(e));
-  }
-  sl.base = static_cast<char*>(base);
-  if (sl.size > bytes) sl.free_blocks[bytes] = sl.size - bytes;
-  slabs_.push_back(std::move(sl));
-  reserved_ += slabs_.back().size;
-  char* p = slabs_.back().base;
-  used_[p] = {(int)slabs_.size() - 1, bytes};
-  in_use_ += bytes;
-  return p;
+  return nullptr;
 }
 
 void DevicePool::free(void* vp) {
@@ -85,6 +100,16 @@ size_t DevicePool::reserved() const {
 size_t DevicePool::in_use() const {
   std::lock_guard<std::mutex> lk(mu_);
   return in_use_;
+}
+
+long DevicePool::grows() const {
+  std::lock_guard<std::mutex> lk(mu_);
+  return grows_;
+}
+
+double DevicePool::grow_seconds() const {
+  std::lock_guard<std::mutex> lk(mu_);
+  return grow_s_;
 }
 
 DeviceArena::~DeviceArena() {
@@ -215,6 +240,13 @@ template <typename T> class Engine final : public EngineBase {
 
   explicit Engine(const ks_cell_desc& d, DevicePool* pool = nullptr) : prec_(d.prec), ns_(d.nstates) {
     arena_.set_pool(pool);
+    // side stream (highest priority, non-blocking): the CholQR factor that overlaps H psi, and
+    // the setup work here and at atom moves (table uploads, V_loc, the projector block), which
+    // so neither waits behind other engines' kernels nor serialises on the legacy stream
+    int lo = 0, hi = 0;
+    KS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    KS_CUDA(cudaStreamCreateWithPriority(&aux_, cudaStreamNonBlocking, hi));
+    setup_ = aux_;
     build_geometry(d, g_);
     const int N = g_.N, nG = g_.nG;
     const size_t N3 = (size_t)N * N * N;
@@ -255,15 +287,15 @@ template <typename T> class Engine final : public EngineBase {
     // ---- states: 6 buffers (resident psi, H psi, and 4 work buffers for the real-time step)
     for (int i = 0; i < 6; ++i) {
       buf_[i] = alloc<C>(sn);
-      KS_CUDA(cudaMemset(buf_[i], 0, sn * sizeof(C)));
+      KS_CUDA(cudaMemsetAsync(buf_[i], 0, sn * sizeof(C), setup_));
     }
     psi_ = buf_[0];
     hpsi_ = buf_[1];
     staging_ = alloc<double2>(sn);
     // ---- Hamiltonian work
     status_ = alloc<int>(4);
-    KS_CUDA(cudaMemset(status_, 0, 4 * sizeof(int)));
-    fused_ = make_fused_for(g_, t_, ns_, arena_, prof, status_ + 1);
+    KS_CUDA(cudaMemsetAsync(status_, 0, 4 * sizeof(int), setup_));
+    fused_ = make_fused_for(g_, t_, ns_, arena_, prof, status_ + 1, setup_);
     if (!fused_) {
       batch_ = (int)full_grid_batch<T>(N, ns_);
       grid_ = alloc<C>((size_t)batch_ * N3);
@@ -310,15 +342,11 @@ template <typename T> class Engine final : public EngineBase {
     dots_ = alloc<double2>(ns_);
     norms_dev_ = alloc<double>(MAX_STEPS_CHUNK);
     energies_dev_ = alloc<double>(MAX_STEPS_CHUNK);
-    // side stream (highest priority) for the CholQR factor that overlaps H psi
-    int lo = 0, hi = 0;
-    KS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    KS_CUDA(cudaStreamCreateWithPriority(&aux_, cudaStreamNonBlocking, hi));
     KS_CUDA(cudaEventCreateWithFlags(&ev_gram_, cudaEventDisableTiming));
     KS_CUDA(cudaEventCreateWithFlags(&ev_hraw_, cudaEventDisableTiming));
     KS_CUDA(cudaEventCreateWithFlags(&ev_chol_, cudaEventDisableTiming));
     KS_CUDA(cudaEventCreateWithFlags(&ev_ritz_, cudaEventDisableTiming));
-    update_vloc(nullptr);
+    update_vloc(setup_);                                             // ends with a synchronisation
   }
 
   ~Engine() override {
@@ -1025,7 +1053,6 @@ template <typename T> class Engine final : public EngineBase {
     // other engines keep running)
     KS_CUDA(cudaStreamSynchronize(s));
     KS_CUDA(cudaStreamSynchronize(aux_));
-    KS_CUDA(cudaStreamSynchronize(nullptr));
     ProfScope p(prof, "set_positions", s);
     // projector sphere lists (their sizes change as grid points enter and leave the spheres)
     for (const void* q : {(const void*)t_.sph_off, (const void*)t_.sph_idx, (const void*)t_.sph_atom,
@@ -1041,6 +1068,7 @@ template <typename T> class Engine final : public EngineBase {
     t_.cov_off = upload(g_.cov_off);
     t_.cov_ent = upload(g_.cov_ent);
     t_.ncov = (int)g_.cov_idx.size();
+    KS_CUDA(cudaStreamSynchronize(setup_));                           // the new lists have landed
     update_vloc(s);
     if constexpr (sizeof(T) == 4) {
       if (fused_) fused_->set_atoms(t_);
@@ -1336,7 +1364,7 @@ template <typename T> class Engine final : public EngineBase {
   void update_vloc(cudaStream_t s) {
     const int N = g_.N;
     const size_t N3 = (size_t)N * N * N;
-    build_axis_tables();
+    build_axis_tables(s);
     vloc_from_axes<T>(fxyz_, g_.natoms, N, g_.vloc_depth, vloc_, vloc64_, s);
     KS_CUDA(cudaMemcpyAsync(vtot_, vloc_, N3 * sizeof(T), cudaMemcpyDeviceToDevice, s));
     minmax(vloc64_, N3, hxc_partials_, HXC_BLOCKS, vmm_, s);
@@ -1370,7 +1398,7 @@ template <typename T> class Engine final : public EngineBase {
 
   // Per atom and axis: X_a(x) = sum_{s = -1, 0, 1} exp(-(x - R_a - L s)^2 / (2 w^2)) on the
   // grid; V_loc = A sum_a X_a(x) Y_a(y) Z_a(z) and the local force both use them.
-  void build_axis_tables() {
+  void build_axis_tables(cudaStream_t s) {
     const int N = g_.N, na = g_.natoms;
     if (!fxyz_) fxyz_ = alloc<double>(std::max<size_t>(1, 3 * (size_t)na * N));
     std::vector<double> xyz(3 * (size_t)na * N);
@@ -1385,7 +1413,7 @@ template <typename T> class Engine final : public EngineBase {
           }
           xyz[((size_t)I * 3 + a) * N + j] = v;
         }
-    KS_CUDA(cudaMemcpy(fxyz_, xyz.data(), xyz.size() * sizeof(double), cudaMemcpyHostToDevice));
+    KS_CUDA(cudaMemcpyAsync(fxyz_, xyz.data(), xyz.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   }
   static double2 cmul_scalar(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -1470,7 +1498,7 @@ template <typename T> class Engine final : public EngineBase {
   template <typename U> U* alloc(size_t n) { return static_cast<U*>(arena_.alloc(n * sizeof(U))); }
   template <typename U> const U* upload(const std::vector<U>& v) {
     U* p = alloc<U>(std::max<size_t>(v.size(), 1));
-    if (!v.empty()) KS_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice));
+    if (!v.empty()) KS_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice, setup_));
     return p;
   }
   const T* upload_real(const std::vector<double>& v) {
@@ -1507,6 +1535,7 @@ template <typename T> class Engine final : public EngineBase {
   // one-CTA Rayleigh-Ritz step of the block iteration (FP32 operands and results)
   float2 *hraw32_ = nullptr, *m32_ = nullptr, *mcat32_ = nullptr, *aexp_ = nullptr, *vexp_ = nullptr;
   int* perm_ = nullptr;
+  cudaStream_t setup_ = nullptr;     // = aux_: setup work at creation and at atom moves
   // hpsi_ = H psi_ for the resident block (kept by the block iteration between calls); after
   // HPSI_REFRESH iterations that derived it by recurrence, H is applied to psi_ afresh.
   static constexpr int HPSI_REFRESH = 16;

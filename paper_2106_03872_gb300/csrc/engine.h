@@ -24,6 +24,8 @@ class DevicePool {
   void free(void* p);
   size_t reserved() const;   // bytes obtained from the device
   size_t in_use() const;     // bytes handed out
+  long grows() const;        // slabs obtained (cudaMalloc calls)
+  double grow_seconds() const;   // time spent in them
 
  private:
   struct Slab {
@@ -31,11 +33,14 @@ class DevicePool {
     size_t size = 0;
     std::map<size_t, size_t> free_blocks;   // offset -> size, coalesced
   };
+  void* take(size_t bytes);   // first fit in the existing slabs (lock held), or null
   size_t slab_bytes_;
   mutable std::mutex mu_;
   std::vector<Slab> slabs_;
   std::map<char*, std::pair<int, size_t>> used_;   // address -> (slab, size)
   size_t reserved_ = 0, in_use_ = 0;
+  long grows_ = 0;
+  double grow_s_ = 0;
 };
 
 // Device allocation owned by an engine; every allocation is counted for admission.  With a pool,

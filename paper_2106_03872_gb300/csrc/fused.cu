@@ -1246,8 +1246,8 @@ class FusedImpl final : public FusedOps {
   }
 
   FusedImpl(const HostGeometry& g, const DevTables<float>& t, int nstates, DeviceArena& arena, StageProfiler& prof,
-            int* err)
-      : g_(g), t_(t), ns_(nstates), arena_(arena), prof_(prof), err_(err) {
+            int* err, cudaStream_t setup)
+      : g_(g), t_(t), ns_(nstates), arena_(arena), prof_(prof), err_(err), setup_(setup) {
     N_ = g.N;
     ncols_ = g.ncols;
     nprojtot_ = g.natoms * g.nproj;
@@ -1269,6 +1269,7 @@ class FusedImpl final : public FusedOps {
     }
     nch_max_ = std::max((ns_ + density_chunk(0) - 1) / density_chunk(0), (ns_ + density_chunk(1) - 1) / density_chunk(1));
     dpartial_ = alloc<float>((size_t)nch_max_ * N3);
+    KS_CUDA(cudaStreamSynchronize(setup_));                           // the uploaded tables have landed
   }
 
   // The per-cell part of an H application: V re-laid per z-plane and the projections
@@ -1433,6 +1434,7 @@ class FusedImpl final : public FusedOps {
     arena_.release(nlbits_);
     upload_plane_lists();
     if (nprojtot_ > 0) build_projector_block();
+    KS_CUDA(cudaStreamSynchronize(setup_));                           // the new lists have landed
   }
 
   void density(const float2* psi, int n, const double* occ, float* nout, cudaStream_t s) override {
@@ -1774,23 +1776,23 @@ class FusedImpl final : public FusedOps {
     int* dlo = alloc<int>(std::max<size_t>(1, lo.size()));
     float2* T1 = alloc<float2>((size_t)chunk * B * B * M);
     float2* T2 = alloc<float2>((size_t)chunk * B * M * M);
-    KS_CUDA(cudaMemcpy(dbox, box.data(), box.size() * sizeof(float), cudaMemcpyHostToDevice));
-    KS_CUDA(cudaMemcpy(dlo, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice));
+    KS_CUDA(cudaMemcpyAsync(dbox, box.data(), box.size() * sizeof(float), cudaMemcpyHostToDevice, setup_));
+    KS_CUDA(cudaMemcpyAsync(dlo, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice, setup_));
     const float scale = (float)(std::sqrt(g.omega) / ((double)N * N * N));
     for (int r0 = 0; r0 < nprojtot_; r0 += chunk) {                   // r0: a multiple of np
       const int nr = std::min(chunk, nprojtot_ - r0);
       const int* clo = dlo + 3 * (r0 / np);
-      k_box_dft_z<<<nblk((size_t)nr * B * B * M, 256), 256>>>(dbox + (size_t)r0 * B * B * B, clo, np, nr, B, xr, N,
-                                                               tw, T1);
+      k_box_dft_z<<<nblk((size_t)nr * B * B * M, 256), 256, 0, setup_>>>(dbox + (size_t)r0 * B * B * B, clo, np, nr,
+                                                                          B, xr, N, tw, T1);
       KS_CHECK_LAUNCH();
-      k_box_dft_y<<<nblk((size_t)nr * B * M * M, 256), 256>>>(T1, clo, np, nr, B, xr, N, tw, T2);
+      k_box_dft_y<<<nblk((size_t)nr * B * M * M, 256), 256, 0, setup_>>>(T1, clo, np, nr, B, xr, N, tw, T2);
       KS_CHECK_LAUNCH();
-      k_box_dft_x<<<nblk((size_t)nr * g.nG, 256), 256>>>(T2, clo, t_.gidx, np, nr, B, xr, N, g.nG, scale, tw,
-                                                         B_ + (size_t)r0 * g.nG);
+      k_box_dft_x<<<nblk((size_t)nr * g.nG, 256), 256, 0, setup_>>>(T2, clo, t_.gidx, np, nr, B, xr, N, g.nG, scale,
+                                                                    tw, B_ + (size_t)r0 * g.nG);
       KS_CHECK_LAUNCH();
     }
-    tc_overlap_prepare_a(B_, g.nG, nprojtot_, g.nG, Bimg_, nullptr);   // the operand split once
-    KS_CUDA(cudaStreamSynchronize(nullptr));                           // the temporaries are idle
+    tc_overlap_prepare_a(B_, g.nG, nprojtot_, g.nG, Bimg_, setup_);    // the operand split once
+    KS_CUDA(cudaStreamSynchronize(setup_));                            // the temporaries are idle
     arena_.release(dbox);
     arena_.release(dlo);
     arena_.release(T1);
@@ -1800,7 +1802,7 @@ class FusedImpl final : public FusedOps {
   template <typename U> U* alloc(size_t n) { return static_cast<U*>(arena_.alloc(n * sizeof(U))); }
   template <typename U> const U* upload(const std::vector<U>& v) {
     U* p = alloc<U>(std::max<size_t>(v.size(), 1));
-    if (!v.empty()) KS_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice));
+    if (!v.empty()) KS_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice, setup_));
     return p;
   }
 
@@ -1810,6 +1812,7 @@ class FusedImpl final : public FusedOps {
   DeviceArena& arena_;
   StageProfiler& prof_;
   int* err_;
+  cudaStream_t setup_;
   int N_ = 0, ncols_ = 0, nprojtot_ = 0;
   PlaneNL nl_{};
   std::vector<int> h_pt_off_, h_pt_xy_, h_ent_off_, h_ent_proj_;   // host copies of the plane lists
@@ -1846,9 +1849,9 @@ bool fused_same_geometry(const FusedOps* a, const FusedOps* b) {
 }
 
 std::unique_ptr<FusedOps> make_fused_ops(const HostGeometry& g, const DevTables<float>& t, int nstates,
-                                         DeviceArena& arena, StageProfiler& prof, int* err) {
+                                         DeviceArena& arena, StageProfiler& prof, int* err, cudaStream_t setup) {
   if (!FusedImpl::supported(g.N)) return nullptr;
-  return std::unique_ptr<FusedOps>(new FusedImpl(g, t, nstates, arena, prof, err));
+  return std::unique_ptr<FusedOps>(new FusedImpl(g, t, nstates, arena, prof, err, setup));
 }
 
 }  // namespace ks

@@ -81,18 +81,21 @@ void fused_apply_h_group(const std::vector<FusedGroupItem>& items, cudaStream_t 
 // True when two fused paths may share a packed launch.
 bool fused_same_geometry(const FusedOps* a, const FusedOps* b);
 
+// setup: the stream of the setup work (table uploads, the projector block) at creation and at
+// atom moves; each setup ends with a synchronisation of it.
 std::unique_ptr<FusedOps> make_fused_ops(const HostGeometry& g, const DevTables<float>& t, int nstates,
-                                         DeviceArena& arena, StageProfiler& prof, int* err);
+                                         DeviceArena& arena, StageProfiler& prof, int* err, cudaStream_t setup);
 
 template <typename T>
 inline std::unique_ptr<FusedOps> make_fused_for(const HostGeometry&, const DevTables<T>&, int, DeviceArena&,
-                                                StageProfiler&, int*) {
+                                                StageProfiler&, int*, cudaStream_t) {
   return nullptr;
 }
 template <>
 inline std::unique_ptr<FusedOps> make_fused_for<float>(const HostGeometry& g, const DevTables<float>& t, int n,
-                                                       DeviceArena& a, StageProfiler& prof, int* err) {
-  return make_fused_ops(g, t, n, a, prof, err);
+                                                       DeviceArena& a, StageProfiler& prof, int* err,
+                                                       cudaStream_t setup) {
+  return make_fused_ops(g, t, n, a, prof, err, setup);
 }
 
 }  // namespace ks

@@ -44,6 +44,7 @@ struct Request {
   size_t bytes = 0;
   // running state
   std::unique_ptr<EngineBase> eng;
+  double t_create = 0, t_init = 0, t_orth = 0;   // seconds of the start's parts
   cudaStream_t stream = nullptr;
   int done = 0;
   std::vector<double> result, cout;
@@ -106,6 +107,7 @@ struct ks_server_s {
   int device = 0;
   // worker seconds by activity, and the real-time group steps (ks_serve_stats)
   double t_start = 0, t_gs = 0, t_td = 0, t_finish = 0;
+  double t_create = 0, t_init = 0, t_orth = 0;   // parts of t_start
   long n_start = 0, n_gs = 0, n_td_steps = 0, n_td_members = 0;
 };
 
@@ -142,8 +144,10 @@ void finish(ks_server_s* s, Request* r, ks_status st, const std::string& err) {
 
 // Create the engine and initial states of an admitted request (worker thread, no lock).
 void start(ks_server_s* s, Request* r) {
+  const auto t0 = Clock::now();
   KS_CUDA(cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking));
   r->eng = make_engine(r->desc, s->pool.get());
+  const auto t1 = Clock::now();
   if (!r->c0.empty()) {
     r->eng->set_states(r->c0.data(), r->stream);
     r->c0.clear();
@@ -151,8 +155,13 @@ void start(ks_server_s* s, Request* r) {
   } else {
     r->eng->randomize_states(0x9E3779B97F4A7C15ull ^ r->id, r->stream);
   }
+  const auto t2 = Clock::now();
   if (r->kind == 1) r->eng->orthonormalize(nullptr, r->stream);
   if (r->kind == 0) r->result.assign(r->desc.nstates, 0.0);
+  const auto t3 = Clock::now();
+  r->t_create = std::chrono::duration<double>(t1 - t0).count();
+  r->t_init = std::chrono::duration<double>(t2 - t1).count();
+  r->t_orth = std::chrono::duration<double>(t3 - t2).count();
 }
 
 // One ETRS step of a group of started real-time requests in lockstep (td_step_engines) on the
@@ -258,6 +267,9 @@ void worker_loop(ks_server_s* s) {
     if (activity == 0) {
       s->t_start += dq;
       ++s->n_start;
+      s->t_create += r->t_create;
+      s->t_init += r->t_init;
+      s->t_orth += r->t_orth;
     } else if (activity == 1) {
       s->t_gs += dq;
       ++s->n_gs;
@@ -300,7 +312,7 @@ ks_status ks_serve_create_ex(size_t mem_budget_bytes, int workers, ks_server* ou
       mem_budget_bytes = (size_t)(0.8 * (double)fr);
     }
     s->budget = mem_budget_bytes;
-    s->pool.reset(new ks::DevicePool(size_t(1) << 30));
+    s->pool.reset(new ks::DevicePool(size_t(4) << 30));             // 4 GB slabs
     const int nworkers = workers > 0 ? workers : 16;
     for (int i = 0; i < nworkers; ++i) s->workers.emplace_back(ks::worker_loop, s.get());
     *out = s.release();
@@ -379,10 +391,11 @@ ks_status ks_serve_stats(ks_server s, double* out, int nout) {
     return KS_ERR_ARG;
   }
   std::lock_guard<std::mutex> lk(s->mu);
-  const double v[9] = {s->t_start, s->t_gs, s->t_td, s->t_finish, (double)s->n_start, (double)s->n_gs,
-                       (double)s->n_td_steps, (double)s->n_td_members,
-                       s->pool ? (double)s->pool->reserved() : 0.0};
-  for (int i = 0; i < nout && i < 9; ++i) out[i] = v[i];
+  const double v[14] = {s->t_start, s->t_gs, s->t_td, s->t_finish, (double)s->n_start, (double)s->n_gs,
+                        (double)s->n_td_steps, (double)s->n_td_members,
+                        s->pool ? (double)s->pool->reserved() : 0.0, s->t_create, s->t_init, s->t_orth,
+                        s->pool ? (double)s->pool->grows() : 0.0, s->pool ? s->pool->grow_seconds() : 0.0};
+  for (int i = 0; i < nout && i < 14; ++i) out[i] = v[i];
   return KS_OK;
 }
 

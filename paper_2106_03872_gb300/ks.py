@@ -412,10 +412,11 @@ class Server:
 
     def stats(self):
         """Worker seconds by activity and group counts since creation (ks_serve_stats)."""
-        v = np.zeros(9)
-        check(load().ks_serve_stats(self.h, _dptr(v), 9))
+        v = np.zeros(14)
+        check(load().ks_serve_stats(self.h, _dptr(v), 14))
         keys = ("start_s", "ground_state_s", "realtime_s", "retire_s", "starts", "ground_state_quanta",
-                "realtime_group_steps", "realtime_request_steps", "pool_bytes")
+                "realtime_group_steps", "realtime_request_steps", "pool_bytes", "start_create_s", "start_init_s",
+                "start_orthonormalize_s", "pool_slabs_allocated", "pool_alloc_s")
         return dict(zip(keys, v.tolist()))
 
     def poll(self, ticket, timeout_ms=0, want_states=False):
