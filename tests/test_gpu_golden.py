@@ -11,7 +11,7 @@ hours, too long to repeat in a test):
 * td128_sample_etrs.json: 2 such steps of the 128^3 / 128-atom real-time cell with 8 of its
   states (the 128^3 Poisson and exchange path).
 
-Tolerances: the FP64 path 1e-12 relative (the benchmark spec), except where a stated error-growth
+Tolerances: the FP64 path 1e-12 relative (the accuracy target of the FP64 path), except where a stated error-growth
 bound over many steps applies; the mixed path by the FP32 rounding arguments beside each check.
 """
 import json
