@@ -48,7 +48,6 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Per-size launch shapes: plane kernel threads (and CTAs per SM), lines per FFT call
 // (at most 8 complex values per thread per stage), z-kernel columns per CTA.
@@ -447,10 +446,6 @@ template <int SIGN> __device__ __forceinline__ float2 twiddle(const float2* tw, 
   return w;
 }
 
-// Every element of a line holds data.
-struct AllElems {
-  __device__ __forceinline__ bool operator()(int, int) const { return true; }
-};
 // Band row g of a plane holds the sphere's columns at |m_y| <= ym[g] only (a column (m_x, m_y)
 // exists iff m_x^2 + m_y^2 fits the sphere, a contiguous m_y range per row; ym[g] = -1: none);
 // the other elements are read as zeros, so the plane needs no clearing before the scatter.
@@ -466,9 +461,8 @@ template <int N> struct ColMask {
 // of one team.  Line l at P + off(l), element e at e * KS; stage A reads element e only where
 // has(l, e), else zero.  Ends without a barrier: stage B writes back only the elements the same
 // thread read.
-template <int N, int SIGN, int KS, class Off, class Has = AllElems>
-__device__ __forceinline__ void team_lines(float2* P, int nlines, const Off& off, const float2* tw,
-                                           const Has& has = Has{}) {
+template <int N, int SIGN, int KS, class Off, class Has>
+__device__ __forceinline__ void team_lines(float2* P, int nlines, const Off& off, const float2* tw, const Has& has) {
   using TP = TPlan<N>;
   constexpr int R1 = TP::R1, R2 = TP::R2, W = TP::W, QA = R2 / W, QB = R1 / W;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
