@@ -63,4 +63,11 @@ def test_requests_complete_or_fail_without_hanging(ks):
         else:
             assert st in (ks.KS_ERR_CUDA, ks.KS_ERR_NOMEM)
             assert b"request failed" in ks.load().ks_last_error()
+    # the counters: every request was started once, and the parts of the start time add up to
+    # at most the start time itself
+    stats = srv.stats()
+    assert len(stats) == 14 and stats["starts"] == 4
+    parts = stats["start_create_s"] + stats["start_init_s"] + stats["start_orthonormalize_s"]
+    assert 0.0 <= parts <= stats["start_s"] + 1e-9
+    assert stats["pool_slabs_allocated"] >= 0 and stats["pool_alloc_s"] >= 0.0
     srv.close()
