@@ -39,6 +39,8 @@ def main(argv=None):
         torch.cuda.synchronize()
         g.profile(1)
         g.profile(3)
+    if args.iterations == 0 and args.td_steps > 0:
+        g.orthonormalize()                 # the real-time step propagates an orthonormal block
     t0 = time.perf_counter()
     eps = g.block_iteration(args.iterations) if args.iterations > 0 else None
     if args.td_steps > 0:
