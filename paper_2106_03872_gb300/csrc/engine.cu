@@ -240,6 +240,7 @@ template <typename T> class Engine final : public EngineBase {
 
   explicit Engine(const ks_cell_desc& d, DevicePool* pool = nullptr) : prec_(d.prec), ns_(d.nstates) {
     arena_.set_pool(pool);
+    build_geometry(d, g_);                                            // validates the cell (KS_ERR_ARG)
     // side stream (highest priority, non-blocking): the CholQR factor that overlaps H psi, and
     // the setup work here and at atom moves (table uploads, V_loc, the projector block), which
     // so neither waits behind other engines' kernels nor serialises on the legacy stream
@@ -247,7 +248,6 @@ template <typename T> class Engine final : public EngineBase {
     KS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     KS_CUDA(cudaStreamCreateWithPriority(&aux_, cudaStreamNonBlocking, hi));
     setup_ = aux_;
-    build_geometry(d, g_);
     const int N = g_.N, nG = g_.nG;
     const size_t N3 = (size_t)N * N * N;
     const size_t sn = (size_t)ns_ * nG;
