@@ -19,6 +19,7 @@ workload, one block iteration on a bounded sample of the states per step.
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -61,6 +62,25 @@ def cpu_leg(nsteps, warmup, nsample):
         ko.block_iteration(ref, c, 1)
         times.append(time.perf_counter() - t0)
     return dict(times=times, nsample=nsample, N=ref.N)
+
+
+def cpu_td_leg(nsample=2):
+    """The oracle's real-time step on the td128 cell (ETRS + Taylor 4 with Hartree + Slater,
+    dt = 0.05) for a sample of its states, one step, one thread; the full 512-state step time
+    is extrapolated by the state count (the H applications and the density are per state; the
+    per-step potential, counted once per sample, makes this an upper estimate).  Opt-in
+    (--cpu-td-leg): a full-size oracle step takes hours."""
+    from oracle import ks_oracle as ko
+    from paper_2106_03872_gb300 import inputs
+    cell = inputs.cell("td128")
+    ref = ko.Cell(cell)
+    q, _ = ko.cholqr(inputs.random_coeffs(cell["seed"], nsample, ref.nG))
+    t0 = time.perf_counter()
+    ko.td_run(ref, q, 0.05, 1, "etrs", True)
+    dt = time.perf_counter() - t0
+    return {"cell": "td128", "sample_states": nsample, "s_per_sample_step": dt,
+            "extrapolated_s_per_step": dt / nsample * cell["nstates"], "nstates": cell["nstates"], "threads": 1,
+            "kind": "oracle", "host": platform.machine()}
 
 
 def run_cpu_leg(nsteps, warmup, nsample):
@@ -732,6 +752,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-leg", action="store_true")
+    ap.add_argument("--cpu-td-leg", action="store_true",
+                    help="time the oracle's td128 real-time step on a sample of states (one thread) and exit")
     ap.add_argument("--sample", type=int, default=CPU_SAMPLE_STATES)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
@@ -744,6 +766,9 @@ def main():
     args = ap.parse_args()
     if args.cpu_leg:
         print(json.dumps(cpu_leg(args.steps, args.warmup, args.sample)))
+        return
+    if args.cpu_td_leg:
+        print(json.dumps(cpu_td_leg()))
         return
     if args.impl == "reference":
         main_reference(args)
