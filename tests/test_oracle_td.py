@@ -24,6 +24,29 @@ def test_hartree_of_cosine_density():
     assert abs(parts["eh"] - 0.5 * 4 * np.pi / (q @ q) * cell.omega / 2) < 1e-10
 
 
+@pytest.mark.parametrize("L,N,sigma", [(20.0, 64, 1.0), (16.0, 48, 0.8)])
+def test_hartree_of_gaussian_charge(L, N, sigma):
+    """A unit Gaussian charge in the periodic cell with the neutralising background of
+    v_H(G=0) = 0: near the charge, v(r) - v(0) = erf(r / (sqrt(2) sigma)) / r - sqrt(2/pi) / sigma
+    (the isolated charge) + (2 pi / (3 Omega)) r^2 (the uniform background, Laplacian 4 pi / Omega),
+    up to the images' cubic term ~ r^4 / L^5; along an axis and along the cube diagonal."""
+    from math import erf, pi, sqrt
+    cell = ko.Cell(dict(L=L, N=N, ecut=20.0, pos=np.zeros((0, 3)), vloc_depth=-2.0, vloc_width=0.8, nproj=4,
+                        proj_sigma=0.5, proj_rc=2.0, proj_D=0.5))
+    r = cell.grid_points()
+    d = r - L / 2                                # grid points lie in [0, L): the displacement from the centre
+    n = (2 * pi * sigma ** 2) ** -1.5 * np.exp(-np.sum(d * d, axis=-1) / (2 * sigma ** 2))
+    v = ko.hartree(cell, n).reshape(N, N, N)
+    h, i0 = L / N, N // 2
+
+    def closed(x):
+        return erf(x / (sqrt(2) * sigma)) / x - sqrt(2 / pi) / sigma + 2 * pi / (3 * L ** 3) * x * x
+
+    axis = max(abs(v[i0 + k, i0, i0] - v[i0, i0, i0] - closed(k * h)) for k in range(1, N // 6))
+    diag = max(abs(v[i0 + k, i0 + k, i0 + k] - v[i0, i0, i0] - closed(sqrt(3) * k * h)) for k in range(1, N // 10))
+    assert axis < 2e-4 and diag < 2e-4, (axis, diag)
+
+
 def test_slater_exchange_uniform_gas():
     """Textbook uniform-gas exchange: eps_x = -0.458165293 / r_s Ha, v_x = 4/3 eps_x,
     with n = 3 / (4 pi r_s^3)."""
